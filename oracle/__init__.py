@@ -1,0 +1,238 @@
+"""Serial FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product library never does, and this package imports nothing from it.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, compiled without
+fused multiply-add); this module compiles it with gcc and marshals
+arguments through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+# Observable sums returned by or_stats, in order (26 words).
+STAT_FIELDS = (["n"] + [f"m{a}" for a in "xyz"] + [f"m2{a}" for a in "xyz"]
+               + [f"mabs{a}" for a in "xyz"] + ["ml", "ml2", "ml4", "e", "e2",
+               "e_ex", "e_u", "e_c", "e_z"] + [f"tq{a}" for a in "xyz"]
+               + [f"tq2{a}" for a in "xyz"])
+SAMPLE_WORDS = 14
+
+PERIODIC, OPEN, PINNED = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        vp, i32, u32, i64, u64, dbl = C.c_void_p, C.c_int, C.c_uint32, C.c_int64, C.c_uint64, C.c_double
+        P = C.POINTER
+        L.or_philox.argtypes = [P(u32), P(u32), P(u32)]
+        L.or_exp.argtypes = [dbl]; L.or_exp.restype = dbl
+        L.or_cone_trial.argtypes = [P(dbl), i32, u32, u32, u32, P(u32), P(dbl), P(dbl)]
+        L.or_cone_trial.restype = i32
+        L.or_create.argtypes = [P(i32), P(i32), dbl, dbl, P(dbl), dbl, P(dbl), dbl, u64, i32, i32, i32]
+        L.or_create.restype = vp
+        L.or_destroy.argtypes = [vp]
+        L.or_set_spins.argtypes = [vp, P(dbl)]
+        L.or_get_spins.argtypes = [vp, P(dbl)]
+        L.or_set_temperature.argtypes = [vp, dbl]
+        L.or_theta.argtypes = [vp]; L.or_theta.restype = i32
+        L.or_sweep_count.argtypes = [vp]; L.or_sweep_count.restype = u32
+        L.or_last_accepted.argtypes = [vp]; L.or_last_accepted.restype = i64
+        L.or_n_mov.argtypes = [vp]; L.or_n_mov.restype = i64
+        L.or_set_bonds.argtypes = [vp, P(C.c_uint8)]
+        L.or_set_grains.argtypes = [vp, P(C.c_int32), P(dbl), i32]
+        L.or_delta_e.argtypes = [vp, i64, P(dbl)]; L.or_delta_e.restype = dbl
+        L.or_stats.argtypes = [vp, P(dbl)]
+        L.or_samples.argtypes = [vp, P(dbl), i64]; L.or_samples.restype = i64
+        L.or_profile.argtypes = [vp, P(dbl)]
+        L.or_reset_stats.argtypes = [vp]
+        L.or_sweep.argtypes = [vp, i32, i32]; L.or_sweep.restype = i32
+        L.or_sweep_serial.argtypes = [vp, i32, i32]; L.or_sweep_serial.restype = i32
+        L.or_fixed_sum.argtypes = [P(dbl), i64]; L.or_fixed_sum.restype = dbl
+        L.or_constraint_frame.argtypes = [dbl, dbl, P(dbl)]
+        L.or_m_long.argtypes = [vp, dbl, dbl]; L.or_m_long.restype = dbl
+        L.or_permutation.argtypes = [u32, u32, i32, P(u32), P(u32)]
+        L.or_constrained_sweep.argtypes = [vp, dbl, dbl, i32, i32]; L.or_constrained_sweep.restype = i32
+        L.or_constrained_sweep_serial.argtypes = [vp, dbl, dbl, i32, i32]
+        L.or_constrained_sweep_serial.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return out
+
+
+def exp(x: float) -> float:
+    return lib().or_exp(float(x))
+
+
+def cone_trial(S, theta_deg: int, idx: int, sweep: int, tag: int, key):
+    s = np.ascontiguousarray(S, dtype=np.float64)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(3)
+    P = C.c_double()
+    ok = lib().or_cone_trial(_p(s, C.c_double), int(theta_deg), idx, sweep, tag,
+                             _p(k, C.c_uint32), _p(out, C.c_double), C.byref(P))
+    return bool(ok), out, P.value
+
+
+def fixed_sum(t) -> float:
+    a = np.ascontiguousarray(t, dtype=np.float64)
+    return lib().or_fixed_sum(_p(a, C.c_double), a.size)
+
+
+def constraint_frame(theta_deg: float, phi_deg: float) -> np.ndarray:
+    R = np.zeros(9)
+    lib().or_constraint_frame(float(theta_deg), float(phi_deg), _p(R, C.c_double))
+    return R.reshape(3, 3)
+
+
+def permutation(n: int, sweep: int, colour: int, key) -> np.ndarray:
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(n, np.uint32)
+    lib().or_permutation(n, sweep, colour, _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return out
+
+
+class Lattice:
+    """One lattice of the serial oracle.  Spins are (N, 3) FP64 in site order
+    x + Lx (y + Ly z).  bc per axis: 0 periodic, 1 open, 2 pinned."""
+
+    def __init__(self, dims, J=1.0, Ku=0.0, axis=(0.0, 0.0, 1.0), Kc=0.0, H=(0.0, 0.0, 0.0),
+                 T=1.0, seed=0, bc=(0, 0, 0), theta0=30, adapt_in_measure=1, ring_cap=1):
+        self.dims = tuple(int(d) for d in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        d = np.array(self.dims, np.int32)
+        b = np.array(bc, np.int32)
+        ax = np.array(axis, np.float64)
+        h = np.array(H, np.float64)
+        self._h = lib().or_create(_p(d, C.c_int), _p(b, C.c_int), float(J), float(Ku),
+                                  _p(ax, C.c_double), float(Kc), _p(h, C.c_double), float(T),
+                                  int(seed) & (2**64 - 1), int(theta0), int(adapt_in_measure),
+                                  int(ring_cap))
+        if not self._h:
+            raise MemoryError("or_create failed")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_destroy(h)
+            self._h = None
+
+    # state -------------------------------------------------------------
+    def set_spins(self, S: np.ndarray) -> None:
+        a = np.ascontiguousarray(S, dtype=np.float64).reshape(self.N, 3)
+        lib().or_set_spins(self._h, _p(a, C.c_double))
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.N, 3))
+        lib().or_get_spins(self._h, _p(out, C.c_double))
+        return out
+
+    def set_temperature(self, T: float) -> None:
+        lib().or_set_temperature(self._h, float(T))
+
+    def set_bonds(self, mask: np.ndarray) -> None:
+        self._bonds = np.ascontiguousarray(mask, dtype=np.uint8).reshape(self.N)
+        lib().or_set_bonds(self._h, _p(self._bonds, C.c_uint8))
+
+    def set_grains(self, gid: np.ndarray, axes: np.ndarray) -> None:
+        g = np.ascontiguousarray(gid, dtype=np.int32).reshape(self.N)
+        a = np.ascontiguousarray(axes, dtype=np.float64).reshape(-1, 3)
+        lib().or_set_grains(self._h, _p(g, C.c_int32), _p(a, C.c_double), a.shape[0])
+
+    @property
+    def theta(self) -> int:
+        return lib().or_theta(self._h)
+
+    @property
+    def sweep_count(self) -> int:
+        return lib().or_sweep_count(self._h)
+
+    @property
+    def last_accepted(self) -> int:
+        return lib().or_last_accepted(self._h)
+
+    @property
+    def n_mov(self) -> int:
+        return lib().or_n_mov(self._h)
+
+    # method ------------------------------------------------------------
+    def sweep(self, n: int, measure: bool = False) -> None:
+        lib().or_sweep(self._h, int(n), int(bool(measure)))
+
+    def sweep_serial(self, n: int, measure: bool = False) -> None:
+        lib().or_sweep_serial(self._h, int(n), int(bool(measure)))
+
+    def constrained_sweep(self, theta_c: float, phi_c: float, n: int, measure: bool = False) -> None:
+        rc = lib().or_constrained_sweep(self._h, float(theta_c), float(phi_c), int(n), int(bool(measure)))
+        if rc != 0:
+            raise RuntimeError(f"or_constrained_sweep returned {rc}")
+
+    def constrained_sweep_serial(self, theta_c: float, phi_c: float, n: int, measure: bool = False) -> None:
+        rc = lib().or_constrained_sweep_serial(self._h, float(theta_c), float(phi_c), int(n), int(bool(measure)))
+        if rc != 0:
+            raise RuntimeError(f"or_constrained_sweep_serial returned {rc}")
+
+    def delta_e(self, i: int, Sn) -> float:
+        s = np.ascontiguousarray(Sn, dtype=np.float64)
+        return lib().or_delta_e(self._h, int(i), _p(s, C.c_double))
+
+    def m_long(self, theta_c: float, phi_c: float) -> float:
+        return lib().or_m_long(self._h, float(theta_c), float(phi_c))
+
+    # measurements ------------------------------------------------------
+    def stats(self) -> dict:
+        out = np.zeros(len(STAT_FIELDS))
+        lib().or_stats(self._h, _p(out, C.c_double))
+        return dict(zip(STAT_FIELDS, out.tolist()))
+
+    def samples(self, max_n: int = 1 << 20) -> np.ndarray:
+        out = np.zeros((max_n, SAMPLE_WORDS))
+        n = lib().or_samples(self._h, _p(out, C.c_double), max_n)
+        return out[:n]
+
+    def profile(self) -> np.ndarray:
+        out = np.zeros(self.dims[0])
+        lib().or_profile(self._h, _p(out, C.c_double))
+        return out
+
+    def reset_stats(self) -> None:
+        lib().or_reset_stats(self._h)

@@ -1,0 +1,242 @@
+"""Unit pins of the oracle's building blocks against things other than itself.
+
+* Philox4x32-10 against Triton's independent implementation (run on the CPU
+  by the Triton interpreter).
+* exp (Cody-Waite + Taylor) against libm, within 2 ulp, and its limits.
+* The cone trial move (Table A1 UniformRandom_RotateSpin) against the
+  closed-form marginals of a direction uniform on a spherical cap.
+* The energy change of Eq. 2 against a brute-force total-energy difference.
+* The shuffle of Table A2 (keyed Feistel permutation) is a bijection.
+* The exact M_L sum is order-independent and within n 2^-52 of fsum.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------------- Philox
+def test_philox_matches_triton_reference():
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(2024)
+    cases = []
+    for seed in (0, 1, 0xFFFFFFFF, 0x123456789ABCDEF0, int(rng.integers(0, 2**63))):
+        ctr = rng.integers(0, 2**32, size=(64, 4), dtype=np.uint64)
+        ctr[0] = 0
+        ctr[1] = 0xFFFFFFFF
+        ctr[2] = (7, 3, 1, 0)
+        cases.append((int(seed), ctr.astype(np.uint32).tolist()))
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    res = subprocess.run([sys.executable, os.path.join(HERE, "_philox_triton.py")],
+                         input=json.dumps(cases), capture_output=True, text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        pytest.skip("Triton interpreter unavailable: " + res.stderr[-300:])
+    ref = json.loads(res.stdout)
+    for (seed, ctrs), words in zip(cases, ref):
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for c, w in zip(ctrs, words):
+            assert oracle.philox(c, key).tolist() == [int(v) for v in w], (seed, c)
+
+
+# ------------------------------------------------------------------------ exp
+def _ulp_diff(a, b):
+    return np.abs(np.asarray(a, np.float64).view(np.int64) - np.asarray(b, np.float64).view(np.int64))
+
+
+def test_exp_within_two_ulp_of_libm():
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([rng.uniform(-708.0, 709.0, 100000), rng.uniform(-1.0, 1.0, 50000),
+                         rng.uniform(-60.0, 0.0, 50000), np.linspace(-0.35, 0.35, 2001)])
+    mine = np.array([oracle.exp(x) for x in xs])
+    ref = np.array([math.exp(x) for x in xs])
+    assert _ulp_diff(mine, ref).max() <= 2
+
+
+def test_exp_special_values_and_subnormals():
+    assert oracle.exp(0.0) == 1.0
+    assert oracle.exp(-800.0) == 0.0
+    assert oracle.exp(800.0) == math.inf
+    assert math.isnan(oracle.exp(math.nan))
+    for x in np.linspace(-745.0, -708.5, 301):
+        a, b = oracle.exp(x), math.exp(x)
+        # gradual underflow: within one unit of the subnormal spacing 2^-1074
+        assert abs(a - b) <= 2.0 ** -1074 * 1.0 + abs(b) * 2.3e-16
+
+
+# ----------------------------------------------------------------- cone move
+def _perp_basis(S):
+    S = np.asarray(S, float)
+    t = np.array([1.0, 0.0, 0.0]) if abs(S[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    u = t - S * (S @ t)
+    u /= np.linalg.norm(u)
+    v = np.cross(S, u)
+    return u, v
+
+
+@pytest.mark.parametrize("theta", [3, 30, 90, 150, 180])
+def test_cone_trial_marginals(theta):
+    rng = np.random.default_rng(theta)
+    S = rng.standard_normal(3)
+    S /= np.linalg.norm(S)
+    key = (11, 22)
+    n = 40000
+    cz = np.empty(n)
+    phi = np.empty(n)
+    u, v = _perp_basis(S)
+    for i in range(n):
+        ok, Sn, P = oracle.cone_trial(S, theta, i, 5, 0, key)
+        assert ok
+        assert abs(np.linalg.norm(Sn) - 1.0) < 4e-16
+        cz[i] = Sn @ S
+        phi[i] = math.atan2(Sn @ v, Sn @ u)
+    ct = math.cos(math.radians(theta))
+    # z' = S.S' uniform on [cos theta, 1]: chi-square on 20 bins
+    assert cz.min() >= ct - 1e-12 and cz.max() <= 1.0 + 1e-12
+    h, _ = np.histogram(cz, bins=20, range=(ct, 1.0))
+    chi2 = ((h - n / 20) ** 2 / (n / 20)).sum()
+    assert chi2 < 50.0  # 19 dof, p ~ 1e-4
+    h, _ = np.histogram(phi, bins=24, range=(-math.pi, math.pi))
+    chi2 = ((h - n / 24) ** 2 / (n / 24)).sum()
+    assert chi2 < 60.0  # 23 dof
+
+
+def test_cone_trial_p_is_uniform():
+    key = (3, 4)
+    P = np.array([oracle.cone_trial((0, 0, 1.0), 30, i, 0, 0, key)[2] for i in range(20000)])
+    assert P.min() >= 0.0 and P.max() < 1.0
+    h, _ = np.histogram(P, bins=20, range=(0, 1))
+    assert ((h - 1000) ** 2 / 1000).sum() < 50.0
+
+
+# --------------------------------------------------------- energy change, Eq. 2
+def _total_energy(S, dims, bc, J, Ku, axis, Kc, H, bonds=None, gid=None, gaxes=None):
+    """Brute-force E of Eq. 2 summed over the lattice: every bond once
+    (the +x, +y, +z neighbour of each site), all single-site terms."""
+    Lx, Ly, Lz = dims
+    S3 = S.reshape(Lz, Ly, Lx, 3)
+    E = 0.0
+    for z in range(Lz):
+        for y in range(Ly):
+            for x in range(Lx):
+                s = S3[z, y, x]
+                i = x + Lx * (y + Ly * z)
+                for ax, d in ((0, 1), (1, 3), (2, 5)):
+                    c = [x, y, z]
+                    c[ax] += 1
+                    L = dims[ax]
+                    if c[ax] >= L:
+                        if bc[ax] != 0:
+                            continue
+                        c[ax] -= L
+                    if bonds is not None and not (bonds[i] >> d) & 1:
+                        continue
+                    E -= J * float(s @ S3[c[2], c[1], c[0]])
+                e = axis if gid is None else gaxes[gid[i]]
+                E -= Ku * float(s @ e) ** 2
+                E += Kc * (s[0] ** 2 * s[1] ** 2 + s[0] ** 2 * s[2] ** 2 + s[1] ** 2 * s[2] ** 2)
+                E -= float(np.dot(H, s))
+    return E
+
+
+@pytest.mark.parametrize("dims,bc", [((4, 4, 4), (0, 0, 0)), ((4, 2, 6), (1, 0, 2)), ((6, 3, 1), (0, 1, 1)),
+                                     ((2, 4, 2), (0, 0, 0))])
+def test_delta_e_equals_total_energy_difference(dims, bc):
+    rng = np.random.default_rng(sum(dims))
+    N = dims[0] * dims[1] * dims[2]
+    J, Ku, Kc = 1.3, 0.4, -0.7
+    axis = rng.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    H = rng.standard_normal(3) * 0.5
+    S = rng.standard_normal((N, 3))
+    S /= np.linalg.norm(S, axis=1, keepdims=True)
+    lat = oracle.Lattice(dims, J=J, Ku=Ku, axis=axis, Kc=Kc, H=H, bc=bc)
+    lat.set_spins(S)
+    E0 = _total_energy(S, dims, bc, J, Ku, axis, Kc, H)
+    for _ in range(25):
+        i = int(rng.integers(N))
+        Sn = rng.standard_normal(3)
+        Sn /= np.linalg.norm(Sn)
+        S1 = S.copy()
+        S1[i] = Sn
+        dE = _total_energy(S1, dims, bc, J, Ku, axis, Kc, H) - E0
+        assert abs(lat.delta_e(i, Sn) - dE) < 1e-12 * max(1.0, abs(E0))
+
+
+def test_delta_e_with_bond_mask_and_grain_axes():
+    rng = np.random.default_rng(5)
+    dims = (4, 4, 3)
+    bc = (0, 0, 1)
+    N = 48
+    gid = rng.integers(0, 3, N).astype(np.int32)
+    gaxes = rng.standard_normal((3, 3))
+    gaxes /= np.linalg.norm(gaxes, axis=1, keepdims=True)
+    # bonds only inside a grain, consistent from both ends
+    g3 = gid.reshape(3, 4, 4)
+    mask = np.zeros((3, 4, 4), np.uint8)
+    mask |= (g3 == np.roll(g3, 1, axis=2)).astype(np.uint8) << 0
+    mask |= (g3 == np.roll(g3, -1, axis=2)).astype(np.uint8) << 1
+    mask |= (g3 == np.roll(g3, 1, axis=1)).astype(np.uint8) << 2
+    mask |= (g3 == np.roll(g3, -1, axis=1)).astype(np.uint8) << 3
+    mask |= (g3 == np.roll(g3, 1, axis=0)).astype(np.uint8) << 4
+    mask |= (g3 == np.roll(g3, -1, axis=0)).astype(np.uint8) << 5
+    mask = mask.reshape(-1)
+    S = rng.standard_normal((N, 3))
+    S /= np.linalg.norm(S, axis=1, keepdims=True)
+    H = np.array([0.1, -0.2, 0.3])
+    lat = oracle.Lattice(dims, J=1.0, Ku=0.5, Kc=0.2, H=H, bc=bc)
+    lat.set_spins(S)
+    lat.set_bonds(mask)
+    lat.set_grains(gid, gaxes)
+    E0 = _total_energy(S, dims, bc, 1.0, 0.5, None, 0.2, H, mask, gid, gaxes)
+    for i in range(N):
+        Sn = rng.standard_normal(3)
+        Sn /= np.linalg.norm(Sn)
+        S1 = S.copy()
+        S1[i] = Sn
+        dE = _total_energy(S1, dims, bc, 1.0, 0.5, None, 0.2, H, mask, gid, gaxes) - E0
+        assert abs(lat.delta_e(i, Sn) - dE) < 1e-12
+
+
+# ---------------------------------------------------------- shuffle, Table A2
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 63, 64, 100, 1000, 4097, 131072, 250001])
+def test_permutation_is_bijection(n):
+    for colour in (0, 1):
+        p = oracle.permutation(n, 17, colour, (9, 9))
+        assert np.array_equal(np.sort(p), np.arange(n, dtype=np.uint32))
+
+
+def test_permutation_changes_with_sweep():
+    a = oracle.permutation(4096, 0, 0, (1, 2))
+    b = oracle.permutation(4096, 1, 0, (1, 2))
+    c = oracle.permutation(4096, 0, 1, (1, 2))
+    assert (a != b).mean() > 0.9 and (a != c).mean() > 0.9
+
+
+# ------------------------------------------------------------ exact M_L sum
+def test_fixed_sum_order_independent_and_accurate():
+    rng = np.random.default_rng(3)
+    t = rng.uniform(-1.0, 1.0, 200001)
+    t[:10] = [1.0, -1.0, 0.0, -0.0, 1e-300, -1e-17, 0.5, 2.0**-52, -(2.0**-53), 0.999999999]
+    a = oracle.fixed_sum(t)
+    for k in range(3):
+        b = oracle.fixed_sum(rng.permutation(t))
+        assert a == b
+    assert abs(a - math.fsum(t)) <= t.size * 2.0 ** -52 + 1e-12
+
+
+def test_constraint_frame_orthonormal():
+    for th, ph in ((0, 0), (30, 0), (45, 45), (90, 45), (73.5, -20)):
+        R = oracle.constraint_frame(th, ph)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-15)
+        t, p = math.radians(th), math.radians(ph)
+        assert np.allclose(R[0], [math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)], atol=1e-15)
+        assert np.allclose(np.cross(R[0], R[1]), R[2], atol=1e-15)
