@@ -1,0 +1,392 @@
+"""Throughput of the batched parallel Metropolis sweep on GB300.
+
+Workload (one step = one measurement sweep of the whole batch: red pass, black
+pass with the fused sample, cone adaptation, for every lattice):
+32 independent periodic simple-cubic lattices, L = 16, 32, 64, 128 cycled,
+T_i = 0.05 (i + 1), J = 1, K_u = 0.01 along z, FP32 spins with FP64
+accumulators, 19,169,280 spins in total (230 MB of spins: larger than L2, so
+no flush is needed between steps), advanced by one graph-replayed launch per
+colour pass.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank advances its own copy of the batch (weak
+scaling, no collective on the data path); the time is the max over ranks.
+`--impl reference` times the serial FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "spin-updates/s & HBM roofline frac (128^3 FP32); served m(T) req/s, p50/p99"
+UNIT = "spin-updates/s"
+BYTES_PER_UPDATE = 24          # FP32: read + write 3 x 4 B of every spin once per sweep
+FALLBACK_HBM_GBS = 6800.0
+LATSTATE_BYTES = 384           # device state block read back by mc_measure
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "colour_pass_f32_batched_mT.txt")
+KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/pass_impl.cuh", "paper_2103_03517_gb300/csrc/device_common.cuh",
+                  "paper_2103_03517_gb300/csrc/kernels_f32.cu", "paper_2103_03517_gb300/csrc/mc_internal.h"]
+
+
+def workload_config():
+    specs = workloads.config2()
+    n = sum(s.N for s in specs)
+    return specs, n, {
+        "workload": "batched m(T) sweep: 32 periodic sc lattices 16^3/32^3/64^3/128^3 cycled, "
+                    "T = 0.05..1.60, J = 1, K_u = 0.01 z; FP32 spins, FP64 accumulators; "
+                    "one measurement sweep per step",
+        "lattices": len(specs),
+        "spins": n,
+        "l2": "inputs larger than L2 (230 MB of spins), no flush",
+    }
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """Per-launch DRAM bytes of the colour-pass kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    try:
+        kv = {}
+        with open(PROFILE_SUMMARY) as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle legs
+def _oracle_worker(args):
+    idx, n_warm, n_steps, barrier = args
+    import oracle
+
+    specs = workloads.config2()
+    lats = []
+    for i in idx:
+        s = specs[i]
+        lats.append(oracle.Lattice(s.dims, Ku=s.Ku, T=s.T, seed=s.seed, ring_cap=1))
+    for o in lats:
+        o.sweep(n_warm, measure=True)
+    if barrier is not None:
+        barrier.wait()
+    t = time.perf_counter()
+    for o in lats:
+        o.sweep(n_steps, measure=True)
+    return time.perf_counter() - t
+
+
+def run_oracle(lattice_ids, n_warm, n_steps):
+    """Run the serial oracle on the given config-2 lattices, one process per
+    core (spawned), every lattice n_warm + n_steps measurement sweeps; return
+    (updates per second over the timed sweeps, cores used)."""
+    import oracle
+    oracle.build()
+    specs = workloads.config2()
+    cores = max(1, min(len(lattice_ids), os.cpu_count() or 1))
+    # balance by size: largest first onto the least loaded core
+    bins = [[] for _ in range(cores)]
+    load = [0] * cores
+    for i in sorted(lattice_ids, key=lambda i: -specs[i].N):
+        k = load.index(min(load))
+        bins[k].append(i)
+        load[k] += specs[i].N
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(cores + 1)
+        with ctx.Pool(cores) as pool:
+            res = pool.map_async(_oracle_worker, [(b, n_warm, n_steps, barrier) for b in bins])
+            barrier.wait()
+            t = time.perf_counter()
+            res.get()
+            wall = time.perf_counter() - t
+    updates = sum(specs[i].N for i in lattice_ids) * n_steps
+    return updates / wall, cores
+
+
+def reference_arm(args, cfg):
+    """--impl reference: the serial FP64 oracle on the host cores.  One step =
+    one measurement sweep of every 16^3 and 32^3 lattice of the workload (a
+    bounded sample: 294,912 updates per step), lattices spread over cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = [i for i in range(32) if i % 4 in (0, 1)]
+    rate, cores = run_oracle(sample, args.warmup, args.steps)
+    specs = workloads.config2()
+    per_step = sum(specs[i].N for i in sample)
+    sample_desc = f"{len(sample)} lattices (the 16^3 and 32^3 ones), {args.steps} measurement sweeps each"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step / rate * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+def gpu_arm(args, cfg):
+    import torch
+
+    import paper_2103_03517_gb300 as mc
+    from paper_2103_03517_gb300 import build as libbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    libbuild.build()
+    specs, n_spins, _ = workload_config()
+
+    # cpu baseline first (spawned pool; rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores = run_oracle(list(range(32)), 1, 4)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "all 32 lattices of the workload, 4 measurement sweeps each after 1 warm-up "
+                         "(76.7M updates), one spawned process per core"}
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP32,
+                                           ring_capacity=16, stream=stream.cuda_stream, device=local))
+              for s in specs]
+        g = mc.mc_group_create(hs)
+        mc.mc_group_sweep(g, args.warmup, measure=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        try:
+            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            gpu_id = str(local)
+        with Clocks(gpu_id) as clk:
+            torch.cuda.synchronize()
+            start.record(stream)
+            mc.mc_group_sweep(g, args.steps, measure=True)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        ms = start.elapsed_time(stop)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * n_spins * args.steps / (ms * 1e-3)
+
+        # dominant kernel: the colour pass, timed launch by launch
+        avg_ms, launches = mc.mc_group_time_passes(g, max(8, min(args.steps, 200)), measure=True)
+        bytes_per_launch = (n_spins // 2) * BYTES_PER_UPDATE
+        achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+        peak, peak_kind = measured_peak()
+        traffic = read_traffic()
+
+        # end to end through the C ABI with host buffers: per step the whole
+        # spin state goes host -> device from pinned memory, one measurement
+        # sweep runs, and every lattice's observables come back
+        sizes = [mc.mc_state_bytes(h) for h in hs]
+        host = [torch.empty(b, dtype=torch.uint8, pin_memory=True) for b in sizes]
+        for h, buf, b in zip(hs, host, sizes):
+            mc.mc_export_state(h, buf.data_ptr(), b)
+        e2e_steps = max(3, min(args.steps, 50))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for h, buf, b in zip(hs, host, sizes):
+                mc.mc_import_state(h, buf.data_ptr(), b)
+            mc.mc_group_sweep(g, 1, measure=True)
+            for h in hs:
+                mc.mc_measure(h)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * n_spins * e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(sizes)), "d2h_bytes_per_step": LATSTATE_BYTES * len(hs)}
+
+        extra = {}
+        if rank == 0 and not args.quick:
+            extra = secondary(mc, torch, stream, local)
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "colour_pass_kernel<float>", "launch_avg_ms": avg_ms,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def secondary(mc, torch, stream, dev):
+    """Side measurements reported with the headline: the same batch as 32
+    sequential one-lattice FP64 runs (per-launch baseline of the batched
+    path), and the constrained workload (80 x 64^3 pair sweeps)."""
+    out = {}
+    specs = workloads.config2()
+    n = sum(s.N for s in specs)
+    sweeps = 10
+    hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP64,
+                                       ring_capacity=16, stream=stream.cuda_stream, device=dev)) for s in specs]
+    for h in hs:
+        mc.mc_sweep(h, 2, measure=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for h in hs:
+        mc.mc_sweep(h, sweeps, measure=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["fp64_per_lattice"] = {"value": n * sweeps / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
+                               "workload": "same 32 lattices, FP64, one lattice per launch sequence"}
+    for h in hs:
+        mc.mc_destroy(h)
+    runs = workloads.config3()
+    hs = []
+    for spec, th, ph in runs:
+        t, p = math.radians(th), math.radians(ph)
+        e = (math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t))
+        hs.append(mc.mc_create_ex(mc.make_desc(spec.dims, K_u=spec.Ku, K_c=spec.Kc, T=spec.T, seed=spec.seed,
+                                               init_dir=e, ring_capacity=16, stream=stream.cuda_stream,
+                                               device=dev)))
+    g = mc.mc_group_create(hs)
+    th = [r[1] for r in runs]
+    ph = [r[2] for r in runs]
+    mc.mc_group_constrained_sweep(g, th, ph, 4, measure=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    mc.mc_group_constrained_sweep(g, th, ph, sweeps, measure=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    nc = sum(r[0].N for r in runs)
+    out["constrained"] = {"value": nc * sweeps / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
+                          "workload": "80 x 64^3 constrained runs (theta_c 0..90, phi_c 0/45, 4 T), FP32, "
+                                      "pair halves counted as updates"}
+    mc.mc_group_destroy(g)
+    for h in hs:
+        mc.mc_destroy(h)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    _, _, cfg = workload_config()
+    if args.impl == "reference":
+        reference_arm(args, cfg)
+    else:
+        gpu_arm(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,290 @@
+/*
+ * mc.h -- C ABI of libmc, a GB300 (sm_103a) implementation of the parallel
+ * checkerboard Metropolis algorithm and the parallel constrained Monte Carlo
+ * algorithm for the classical Heisenberg model on a simple-cubic lattice,
+ * after Lepadatu et al., arXiv:2103.03517.
+ *
+ * Model (Sec. 2, Eq. 2), reduced units (k_B = 1, mu_S = 1; the Zeeman field
+ * H is an energy, H = mu0 mu_S H_a of Eq. 2):
+ *   E_i = -J sum_{j in NN(i)} S_i.S_j - K_u (S_i.e_i)^2
+ *         + K_c (Sx^2 Sy^2 + Sx^2 Sz^2 + Sy^2 Sz^2) - H.S_i
+ * Acceptance (Eq. 1): a trial S' is accepted iff P < exp(-(E(S') - E(S))/T),
+ * P uniform on [0, 1).
+ *
+ * Conventions for every entry point:
+ *  - Return value is an mc_status: MC_OK (0), MC_PENDING (1) or a negative
+ *    error code.  mc_last_error() returns a message for the last error of
+ *    the calling thread.
+ *  - Pointers named host_* or documented as host memory are read or written
+ *    synchronously before the call returns; the library never keeps them.
+ *  - The library owns all device memory of a lattice, from mc_create* until
+ *    mc_destroy.  Handles are not thread safe: use one handle per thread.
+ *    A server (mc_server_*) is internally synchronised.
+ *  - mc_sweep, mc_constrained_sweep and mc_group_sweep are asynchronous on
+ *    the lattice's CUDA stream; errors found on the device (MC_ERR_TIMEOUT,
+ *    MC_ERR_CONSTRAINT) are reported by the next synchronising call
+ *    (mc_measure, mc_samples, mc_profile, mc_get_spins, mc_sync, mc_save).
+ *  - Site order of every host spin array is x + Lx (y + Ly z), three
+ *    components per site (N x 3, row major).
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_API __attribute__((visibility("default")))
+
+typedef enum mc_status {
+    MC_OK = 0,
+    MC_PENDING = 1,
+    MC_ERR_ARG = -1,        /* invalid argument (checked on the host)            */
+    MC_ERR_NOMEM = -2,      /* device memory exhausted / job can never fit       */
+    MC_ERR_CUDA = -3,       /* a CUDA call failed (message in mc_last_error)     */
+    MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up                     */
+    MC_ERR_CONSTRAINT = -5, /* constrained run with M_L <= 0 (Table A2)          */
+    MC_ERR_STATE = -6,      /* call not valid in the current state               */
+    MC_ERR_IO = -7          /* checkpoint file could not be read or written      */
+} mc_status;
+
+typedef enum mc_precision { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
+
+/* Boundary mode of one axis.  PERIODIC needs an even size (two-colouring).
+ * OPEN drops bonds across the face.  PINNED is OPEN and, in addition, the
+ * two end planes of that axis are never updated (fixed by the initial
+ * state: e.g. a Bloch wall held by +z / -z end planes). */
+typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2 } mc_boundary;
+
+typedef enum mc_init {
+    MC_INIT_UNIFORM = 0, /* every spin along init_dir (default +z)             */
+    MC_INIT_WALL = 1     /* +z for x < Lx/2, -z otherwise (Bloch wall start)    */
+} mc_init;
+
+typedef struct mc_lattice* mc_handle;
+typedef struct mc_group* mc_group_handle;
+typedef struct mc_server mc_server;
+
+/* Full description of one lattice (mc_create_ex).  Zero-initialise and fill
+ * what is needed; mc_desc_default() gives the documented defaults. */
+typedef struct mc_desc {
+    int dims[3];            /* Lx, Ly, Lz >= 1; Lx must be even                   */
+    int boundary[3];        /* mc_boundary per axis                               */
+    int precision;          /* mc_precision: FP32 spins (FP64 accumulators) or FP64 */
+    double J;               /* nearest-neighbour exchange                         */
+    double K_u;             /* uniaxial anisotropy constant                       */
+    double axis[3];         /* uniaxial easy axis (normalised by the library)     */
+    double K_c;             /* cubic anisotropy constant (axes x, y, z)           */
+    double H[3];            /* Zeeman field (energy units)                        */
+    double T;               /* temperature, > 0                                   */
+    uint64_t seed;          /* Philox key                                         */
+    int theta0_deg;         /* initial cone half-angle, 1..180 (default 30)       */
+    int adapt_in_measure;   /* 1: cone angle adapts in measurement sweeps too     */
+    int init;               /* mc_init                                            */
+    double init_dir[3];     /* direction for MC_INIT_UNIFORM (default +z)         */
+    int ring_capacity;      /* per-sweep samples kept (default 4096)              */
+    /* optional granular-film tables, host memory, copied at create:            */
+    const uint8_t* bond_mask;   /* N entries or NULL; bit d set = bond present,   */
+                                /* d = 0..5 for -x,+x,-y,+y,-z,+z; must be        */
+                                /* symmetric (bond i->j iff j->i)                 */
+    const int32_t* grain_id;    /* N entries or NULL: per-site easy axis index    */
+    const double* grain_axis;   /* n_grains x 3 easy axes (normalised here)       */
+    int n_grains;
+    void* stream;           /* cudaStream_t to run on, or NULL for a library stream */
+    int device;             /* CUDA device ordinal                                */
+} mc_desc;
+
+/* Ensemble averages over the measurement sweeps since the last reset
+ * (Sec. 3).  Means are per sample; m is the normalised magnetisation of
+ * one sample, energies and torques are per spin. */
+typedef struct mc_observables {
+    int64_t n_samples;
+    int64_t sweeps_done;     /* sweeps run since create (both kinds)              */
+    int theta_deg;           /* current cone half-angle                           */
+    int error;               /* sticky device error (mc_status), 0 if none        */
+    double accept_last;      /* acceptance rate of the last sweep                 */
+    double m[3];             /* <m_a>                                             */
+    double m2[3];            /* <m_a^2>                                           */
+    double m_abs[3];         /* <|m_a|>                                           */
+    double ml, ml2, ml4;     /* <|m|>, <|m|^2>, <|m|^4>                           */
+    double e, e2;            /* <E/N>, <(E/N)^2>                                  */
+    double e_parts[4];       /* <E_ex/N>, <E_u/N>, <E_c/N>, <E_Z/N>               */
+    double torque[3];        /* <tau/N>, tau = sum_i S_i x (-dE_anis,Z/dS_i)      */
+    double torque2[3];       /* <(tau_a/N)^2>                                     */
+    double chi[4];           /* Eq. 6 in reduced units: N/T (<m_a^2> - <m_a>^2)   */
+                             /* for a = l (|m|), x, y, z                          */
+    double binder;           /* 1 - <|m|^4> / (3 <|m|^2>^2)                       */
+} mc_observables;
+
+/* One measurement sweep (the per-sweep time series). */
+typedef struct mc_sample {
+    int64_t sweep;           /* index of the sweep this sample closed             */
+    int32_t theta_deg;       /* cone angle after this sweep's adaptation          */
+    int32_t pad;
+    int64_t accepted;        /* accepted single-spin moves (pairs count 2)        */
+    double m[3];
+    double e_parts[4];       /* per spin: exchange, uniaxial, cubic, Zeeman       */
+    double torque[3];        /* per spin                                          */
+} mc_sample;
+
+/* ---------------------------------------------------------------- lattice */
+
+/* Defaults: 16^3 periodic FP32, J = 1, all other couplings 0, axis z, T = 1,
+ * seed 0, theta0 30, adapt_in_measure 1, uniform +z start, ring 4096. */
+MC_API void mc_desc_default(mc_desc* d);
+
+/* Create a lattice (Eq. 2 parameters; Sec. 2).  dims: Lx, Ly, Lz, all
+ * periodic; FP32 spins with FP64 accumulators; spins start along +z.
+ * Errors: MC_ERR_ARG (odd periodic size, T <= 0, |axis| = 0, ...),
+ * MC_ERR_NOMEM, MC_ERR_CUDA.  *out is set only on MC_OK. */
+MC_API int mc_create(const int dims[3], double J, double K_u, const double axis[3], double K_c,
+                     const double H[3], double T, uint64_t seed, mc_handle* out);
+
+/* Create a lattice from a full description (see mc_desc). */
+MC_API int mc_create_ex(const mc_desc* d, mc_handle* out);
+
+/* Free every device and host resource of the lattice.  NULL is ignored. */
+MC_API int mc_destroy(mc_handle h);
+
+/* Change T (> 0) or H for the following sweeps (Eq. 1, Eq. 2).  Ordered on
+ * the lattice's stream after the sweeps already queued. */
+MC_API int mc_set_temperature(mc_handle h, double T);
+MC_API int mc_set_field(mc_handle h, const double H[3]);
+
+/* Queue n_sweeps iterations of the parallel algorithm of Table A1: red pass,
+ * black pass, then the cone angle moves one degree toward 50% acceptance.
+ * measure != 0 takes one sample per sweep (fused into the black pass).
+ * n_sweeps >= 0.  Asynchronous. */
+MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure);
+
+/* Queue n_sweeps iterations of the parallel constrained algorithm of
+ * Table A2 with the constraint direction e_C = (sin t cos p, sin t sin p,
+ * cos t), t = theta_c_deg in [0, 180], p = phi_c_deg: M_L = sum S.e_C once
+ * per iteration (exact, order-independent), shuffled same-colour pairs,
+ * pair moves that keep the transverse magnetisation.  Not allowed with
+ * pinned boundaries.  M_L <= 0 stops the run with MC_ERR_CONSTRAINT. */
+MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_deg, int n_sweeps,
+                                int measure);
+
+/* Wait for the lattice's queued work; returns the sticky device error. */
+MC_API int mc_sync(mc_handle h);
+
+/* Ensemble averages since the last mc_reset_stats (Sec. 3, Eq. 6).
+ * Synchronises.  out: caller-owned. */
+MC_API int mc_measure(mc_handle h, mc_observables* out);
+
+/* Slice-averaged profile <m_a(x)> = <(1/(Ly Lz)) sum_{y,z} S_a> for every
+ * x-plane (Sec. 3, domain-wall profile), averaged over the profile samples
+ * taken by mc_profile_sample.  axis: component a (0, 1, 2).  out: len >= Lx
+ * doubles, caller-owned.  Synchronises. */
+MC_API int mc_profile(mc_handle h, int component, double* out, int len);
+
+/* Queue one profile sample of the current state (all three components). */
+MC_API int mc_profile_sample(mc_handle h);
+
+/* Copy up to max of the most recent per-sweep samples (oldest first) into
+ * out; *n receives the count.  Synchronises. */
+MC_API int mc_samples(mc_handle h, mc_sample* out, int max, int* n);
+
+/* Zero the accumulators, the sample ring and the profile sums. */
+MC_API int mc_reset_stats(mc_handle h);
+
+/* Spins as FP64 host arrays of n = N sites (site order x + Lx(y + Ly z)).
+ * mc_set_spins normalises nothing: pass unit vectors.  Synchronises. */
+MC_API int mc_get_spins(mc_handle h, double* host_xyz, size_t n);
+MC_API int mc_set_spins(mc_handle h, const double* host_xyz, size_t n);
+
+/* Raw device-layout state (colour-split structure of arrays in the
+ * lattice's precision): bytes = mc_state_bytes(h).  For fast transfer and
+ * checkpointing; host memory, pinned or pageable. */
+MC_API size_t mc_state_bytes(mc_handle h);
+MC_API int mc_export_state(mc_handle h, void* host_buf, size_t bytes);
+MC_API int mc_import_state(mc_handle h, const void* host_buf, size_t bytes);
+
+/* Current cone angle and sweep counter (synchronises). */
+MC_API int mc_get_theta(mc_handle h, int* theta_deg, int64_t* sweeps_done);
+
+/* Checkpoint: description, counters, cone angle, accumulators, sample ring
+ * and spins.  The generator is counter-based, so a resumed run is bit-exact
+ * with an uninterrupted one.  mc_load creates a new handle (stream NULL). */
+MC_API int mc_save(mc_handle h, const char* path);
+MC_API int mc_load(const char* path, mc_handle* out);
+
+/* ------------------------------------------------------------ batching */
+
+/* A group advances many independent lattices (same precision, same device)
+ * with one kernel launch per colour pass, replayed from a captured CUDA
+ * graph.  The lattices keep their own state; mc_measure etc. work on each.
+ * The group runs on the first lattice's stream.  The caller keeps the
+ * handles alive until mc_group_destroy. */
+MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* out);
+MC_API int mc_group_destroy(mc_group_handle g);
+
+/* n_sweeps of Table A1 for every lattice of the group. */
+MC_API int mc_group_sweep(mc_group_handle g, int n_sweeps, int measure);
+
+/* n_sweeps of Table A2 for every lattice of the group; lattice i uses the
+ * constraint direction (theta_c_deg[i], phi_c_deg[i]). */
+MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_deg,
+                                      const double* phi_c_deg, int n_sweeps, int measure);
+
+/* Time the colour-pass kernels of the group: the next n_sweeps sweeps record
+ * CUDA events around every colour-pass launch; *avg_ms receives the mean
+ * duration of one launch and *launches the count.  Synchronises. */
+MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms,
+                                int* launches);
+
+MC_API int mc_group_sync(mc_group_handle g);
+
+/* ------------------------------------------------------------- serving */
+
+typedef struct mc_server_desc {
+    int device;
+    size_t memory_budget;    /* bytes of device memory the server may hold; 0 =  */
+                             /* 90% of free memory at create                      */
+    int max_resident;        /* lattices resident at once (default 256)           */
+    int max_epoch_sweeps;    /* sweeps per batched epoch (default 50)             */
+} mc_server_desc;
+
+typedef enum mc_job_kind { MC_JOB_SWEEP = 0, MC_JOB_CONSTRAINED = 1 } mc_job_kind;
+
+typedef struct mc_job {
+    mc_desc lattice;         /* film tables are copied at submit                  */
+    int kind;                /* mc_job_kind                                       */
+    double theta_c_deg, phi_c_deg;  /* constrained jobs                           */
+    int n_equilibrate;       /* sweeps before measuring                           */
+    int n_measure;           /* measurement sweeps                                */
+} mc_job;
+
+typedef struct mc_result {
+    mc_observables obs;
+    double t_submit, t_admit, t_finish;  /* seconds on the server's clock         */
+    int status;              /* MC_OK or the job's error                          */
+} mc_result;
+
+MC_API int mc_server_create(const mc_server_desc* d, mc_server** out);
+MC_API int mc_server_destroy(mc_server* s);
+
+/* Queue a job; non-blocking.  MC_ERR_NOMEM if the job can never fit in the
+ * server's memory budget, MC_ERR_ARG for an invalid description. */
+MC_API int mc_submit(mc_server* s, const mc_job* job, uint64_t* job_id);
+
+/* MC_PENDING while queued or running; MC_OK and *out once finished (the
+ * result stays available); MC_ERR_ARG for an unknown id. */
+MC_API int mc_poll(mc_server* s, uint64_t job_id, mc_result* out);
+
+/* Current server clock (seconds), jobs queued / resident, bytes in use. */
+MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident, size_t* bytes);
+
+/* -------------------------------------------------------------- misc */
+
+MC_API const char* mc_last_error(void);
+MC_API const char* mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

@@ -1,0 +1,388 @@
+"""ctypes binding of libmc (include/mc.h): the same entry points under the same
+names, argument marshalling only.  Every step of the Monte Carlo path runs in
+the CUDA library; if libmc.so is missing or cannot be loaded this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmc.so")
+
+MC_OK, MC_PENDING = 0, 1
+MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR_STATE, MC_ERR_IO = (
+    -1, -2, -3, -4, -5, -6, -7)
+MC_FP32, MC_FP64 = 0, 1
+MC_PERIODIC, MC_OPEN, MC_PINNED = 0, 1, 2
+MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
+MC_JOB_SWEEP, MC_JOB_CONSTRAINED = 0, 1
+
+
+class MCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmc error {code}: {msg}")
+        self.code = code
+
+
+class mc_desc(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("boundary", C.c_int * 3), ("precision", C.c_int),
+                ("J", C.c_double), ("K_u", C.c_double), ("axis", C.c_double * 3), ("K_c", C.c_double),
+                ("H", C.c_double * 3), ("T", C.c_double), ("seed", C.c_uint64),
+                ("theta0_deg", C.c_int), ("adapt_in_measure", C.c_int), ("init", C.c_int),
+                ("init_dir", C.c_double * 3), ("ring_capacity", C.c_int),
+                ("bond_mask", C.POINTER(C.c_uint8)), ("grain_id", C.POINTER(C.c_int32)),
+                ("grain_axis", C.POINTER(C.c_double)), ("n_grains", C.c_int),
+                ("stream", C.c_void_p), ("device", C.c_int)]
+
+
+class mc_observables(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("sweeps_done", C.c_int64), ("theta_deg", C.c_int),
+                ("error", C.c_int), ("accept_last", C.c_double), ("m", C.c_double * 3),
+                ("m2", C.c_double * 3), ("m_abs", C.c_double * 3), ("ml", C.c_double), ("ml2", C.c_double),
+                ("ml4", C.c_double), ("e", C.c_double), ("e2", C.c_double), ("e_parts", C.c_double * 4),
+                ("torque", C.c_double * 3), ("torque2", C.c_double * 3), ("chi", C.c_double * 4),
+                ("binder", C.c_double)]
+
+    def asdict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+class mc_sample(C.Structure):
+    _fields_ = [("sweep", C.c_int64), ("theta_deg", C.c_int32), ("pad", C.c_int32), ("accepted", C.c_int64),
+                ("m", C.c_double * 3), ("e_parts", C.c_double * 4), ("torque", C.c_double * 3)]
+
+
+class mc_server_desc(C.Structure):
+    _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("max_resident", C.c_int),
+                ("max_epoch_sweeps", C.c_int)]
+
+
+class mc_job(C.Structure):
+    _fields_ = [("lattice", mc_desc), ("kind", C.c_int), ("theta_c_deg", C.c_double), ("phi_c_deg", C.c_double),
+                ("n_equilibrate", C.c_int), ("n_measure", C.c_int)]
+
+
+class mc_result(C.Structure):
+    _fields_ = [("obs", mc_observables), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_finish", C.c_double), ("status", C.c_int)]
+
+
+# every entry point of include/mc.h: name -> (restype, argtypes)
+_P = C.POINTER
+_SIGS = {
+    "mc_desc_default": (None, [_P(mc_desc)]),
+    "mc_create": (C.c_int, [_P(C.c_int), C.c_double, C.c_double, _P(C.c_double), C.c_double, _P(C.c_double),
+                            C.c_double, C.c_uint64, _P(C.c_void_p)]),
+    "mc_create_ex": (C.c_int, [_P(mc_desc), _P(C.c_void_p)]),
+    "mc_destroy": (C.c_int, [C.c_void_p]),
+    "mc_set_temperature": (C.c_int, [C.c_void_p, C.c_double]),
+    "mc_set_field": (C.c_int, [C.c_void_p, _P(C.c_double)]),
+    "mc_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mc_constrained_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int]),
+    "mc_sync": (C.c_int, [C.c_void_p]),
+    "mc_measure": (C.c_int, [C.c_void_p, _P(mc_observables)]),
+    "mc_profile": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_double), C.c_int]),
+    "mc_profile_sample": (C.c_int, [C.c_void_p]),
+    "mc_samples": (C.c_int, [C.c_void_p, _P(mc_sample), C.c_int, _P(C.c_int)]),
+    "mc_reset_stats": (C.c_int, [C.c_void_p]),
+    "mc_get_spins": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_size_t]),
+    "mc_set_spins": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_size_t]),
+    "mc_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "mc_export_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mc_import_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mc_get_theta": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int64)]),
+    "mc_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "mc_load": (C.c_int, [C.c_char_p, _P(C.c_void_p)]),
+    "mc_group_create": (C.c_int, [_P(C.c_void_p), C.c_int, _P(C.c_void_p)]),
+    "mc_group_destroy": (C.c_int, [C.c_void_p]),
+    "mc_group_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mc_group_constrained_sweep": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double), C.c_int, C.c_int]),
+    "mc_group_time_passes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
+    "mc_group_sync": (C.c_int, [C.c_void_p]),
+    "mc_server_create": (C.c_int, [_P(mc_server_desc), _P(C.c_void_p)]),
+    "mc_server_destroy": (C.c_int, [C.c_void_p]),
+    "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
+    "mc_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(mc_result)]),
+    "mc_server_stats": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
+    "mc_last_error": (C.c_char_p, []),
+    "mc_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libmc.so (built by build.py / __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmc.so not found at {LIB_PATH}: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise MCError(rc, lib().mc_last_error().decode(errors="replace"))
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _vec3(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+# ------------------------------------------------------------------ lattice
+def mc_desc_default() -> mc_desc:
+    d = mc_desc()
+    lib().mc_desc_default(C.byref(d))
+    return d
+
+
+def make_desc(dims, J=1.0, K_u=0.0, axis=(0.0, 0.0, 1.0), K_c=0.0, H=(0.0, 0.0, 0.0), T=1.0, seed=0,
+              precision=MC_FP32, boundary=(0, 0, 0), theta0_deg=30, adapt_in_measure=1, init=MC_INIT_UNIFORM,
+              init_dir=(0.0, 0.0, 1.0), ring_capacity=4096, bond_mask=None, grain_id=None, grain_axis=None,
+              stream=None, device=0) -> mc_desc:
+    """Fill an mc_desc.  Film tables (numpy arrays) are referenced, not
+    copied, until mc_create_ex / mc_submit copies them; keep them alive."""
+    d = mc_desc_default()
+    for a in range(3):
+        d.dims[a] = int(dims[a])
+        d.boundary[a] = int(boundary[a])
+        d.axis[a] = float(axis[a])
+        d.H[a] = float(H[a])
+        d.init_dir[a] = float(init_dir[a])
+    d.precision = int(precision)
+    d.J, d.K_u, d.K_c, d.T = float(J), float(K_u), float(K_c), float(T)
+    d.seed = int(seed) & (2 ** 64 - 1)
+    d.theta0_deg = int(theta0_deg)
+    d.adapt_in_measure = int(adapt_in_measure)
+    d.init = int(init)
+    d.ring_capacity = int(ring_capacity)
+    d._keep = []
+    if bond_mask is not None:
+        bm = np.ascontiguousarray(bond_mask, dtype=np.uint8)
+        d._keep.append(bm)
+        d.bond_mask = bm.ctypes.data_as(C.POINTER(C.c_uint8))
+    if grain_id is not None:
+        gi = np.ascontiguousarray(grain_id, dtype=np.int32)
+        ga = np.ascontiguousarray(grain_axis, dtype=np.float64).reshape(-1, 3)
+        d._keep += [gi, ga]
+        d.grain_id = gi.ctypes.data_as(C.POINTER(C.c_int32))
+        d.grain_axis = _dp(ga)
+        d.n_grains = ga.shape[0]
+    d.stream = stream
+    d.device = int(device)
+    return d
+
+
+def mc_create(dims, J, K_u, axis, K_c, H, T, seed) -> int:
+    h = C.c_void_p()
+    d = (C.c_int * 3)(*[int(x) for x in dims])
+    _check(lib().mc_create(d, float(J), float(K_u), _vec3(axis), float(K_c), _vec3(H), float(T),
+                           int(seed) & (2 ** 64 - 1), C.byref(h)))
+    return h.value
+
+
+def mc_create_ex(desc: mc_desc) -> int:
+    h = C.c_void_p()
+    _check(lib().mc_create_ex(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def mc_destroy(h) -> None:
+    _check(lib().mc_destroy(h))
+
+
+def mc_set_temperature(h, T) -> None:
+    _check(lib().mc_set_temperature(h, float(T)))
+
+
+def mc_set_field(h, H) -> None:
+    _check(lib().mc_set_field(h, _vec3(H)))
+
+
+def mc_sweep(h, n_sweeps: int, measure: bool = False) -> None:
+    _check(lib().mc_sweep(h, int(n_sweeps), int(bool(measure))))
+
+
+def mc_constrained_sweep(h, theta_c_deg, phi_c_deg, n_sweeps: int, measure: bool = False) -> None:
+    _check(lib().mc_constrained_sweep(h, float(theta_c_deg), float(phi_c_deg), int(n_sweeps), int(bool(measure))))
+
+
+def mc_sync(h) -> None:
+    _check(lib().mc_sync(h))
+
+
+def mc_measure(h) -> mc_observables:
+    o = mc_observables()
+    _check(lib().mc_measure(h, C.byref(o)))
+    return o
+
+
+def mc_profile_sample(h) -> None:
+    _check(lib().mc_profile_sample(h))
+
+
+def mc_profile(h, component: int, Lx: int) -> np.ndarray:
+    out = np.zeros(Lx)
+    _check(lib().mc_profile(h, int(component), _dp(out), Lx))
+    return out
+
+
+def mc_samples(h, max_n: int) -> np.ndarray:
+    """Per-sweep samples as a structured numpy array (fields of mc_sample)."""
+    buf = (mc_sample * max_n)()
+    n = C.c_int()
+    _check(lib().mc_samples(h, buf, int(max_n), C.byref(n)))
+    arr = np.ctypeslib.as_array(buf)[: n.value].copy()
+    return arr
+
+
+def mc_reset_stats(h) -> None:
+    _check(lib().mc_reset_stats(h))
+
+
+def mc_get_spins(h, N: int) -> np.ndarray:
+    out = np.zeros((N, 3))
+    _check(lib().mc_get_spins(h, _dp(out), N))
+    return out
+
+
+def mc_set_spins(h, xyz: np.ndarray) -> None:
+    a = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    _check(lib().mc_set_spins(h, _dp(a), a.shape[0]))
+
+
+def mc_state_bytes(h) -> int:
+    return int(lib().mc_state_bytes(h))
+
+
+def mc_export_state(h, host_ptr: int, nbytes: int) -> None:
+    _check(lib().mc_export_state(h, C.c_void_p(host_ptr), nbytes))
+
+
+def mc_import_state(h, host_ptr: int, nbytes: int) -> None:
+    _check(lib().mc_import_state(h, C.c_void_p(host_ptr), nbytes))
+
+
+def mc_get_theta(h):
+    t = C.c_int()
+    s = C.c_int64()
+    _check(lib().mc_get_theta(h, C.byref(t), C.byref(s)))
+    return t.value, s.value
+
+
+def mc_save(h, path: str) -> None:
+    _check(lib().mc_save(h, path.encode()))
+
+
+def mc_load(path: str) -> int:
+    h = C.c_void_p()
+    _check(lib().mc_load(path.encode(), C.byref(h)))
+    return h.value
+
+
+# ---------------------------------------------------------------- batching
+def mc_group_create(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    g = C.c_void_p()
+    _check(lib().mc_group_create(arr, len(handles), C.byref(g)))
+    return g.value
+
+
+def mc_group_destroy(g) -> None:
+    _check(lib().mc_group_destroy(g))
+
+
+def mc_group_sweep(g, n_sweeps: int, measure: bool = False) -> None:
+    _check(lib().mc_group_sweep(g, int(n_sweeps), int(bool(measure))))
+
+
+def mc_group_constrained_sweep(g, theta_c_deg, phi_c_deg, n_sweeps: int, measure: bool = False) -> None:
+    th = np.ascontiguousarray(theta_c_deg, dtype=np.float64)
+    ph = np.ascontiguousarray(phi_c_deg, dtype=np.float64)
+    _check(lib().mc_group_constrained_sweep(g, _dp(th), _dp(ph), int(n_sweeps), int(bool(measure))))
+
+
+def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):
+    avg = C.c_double()
+    n = C.c_int()
+    _check(lib().mc_group_time_passes(g, int(n_sweeps), int(bool(measure)), C.byref(avg), C.byref(n)))
+    return avg.value, n.value
+
+
+def mc_group_sync(g) -> None:
+    _check(lib().mc_group_sync(g))
+
+
+# ----------------------------------------------------------------- serving
+def mc_server_create(device=0, memory_budget=0, max_resident=256, max_epoch_sweeps=50) -> int:
+    d = mc_server_desc(int(device), int(memory_budget), int(max_resident), int(max_epoch_sweeps))
+    s = C.c_void_p()
+    _check(lib().mc_server_create(C.byref(d), C.byref(s)))
+    return s.value
+
+
+def mc_server_destroy(s) -> None:
+    _check(lib().mc_server_destroy(s))
+
+
+def make_job(desc: mc_desc, kind=MC_JOB_SWEEP, theta_c_deg=0.0, phi_c_deg=0.0, n_equilibrate=0,
+             n_measure=0) -> mc_job:
+    j = mc_job()
+    j.lattice = desc
+    j.kind = int(kind)
+    j.theta_c_deg = float(theta_c_deg)
+    j.phi_c_deg = float(phi_c_deg)
+    j.n_equilibrate = int(n_equilibrate)
+    j.n_measure = int(n_measure)
+    j._keep = getattr(desc, "_keep", [])
+    return j
+
+
+def mc_submit(s, job: mc_job) -> int:
+    jid = C.c_uint64()
+    _check(lib().mc_submit(s, C.byref(job), C.byref(jid)))
+    return jid.value
+
+
+def mc_poll(s, job_id: int):
+    """(status, mc_result or None): status MC_PENDING or MC_OK."""
+    r = mc_result()
+    rc = _check(lib().mc_poll(s, int(job_id), C.byref(r)))
+    return rc, (r if rc == MC_OK else None)
+
+
+def mc_server_stats(s):
+    now = C.c_double()
+    q = C.c_int()
+    r = C.c_int()
+    b = C.c_size_t()
+    _check(lib().mc_server_stats(s, C.byref(now), C.byref(q), C.byref(r), C.byref(b)))
+    return now.value, q.value, r.value, b.value
+
+
+def mc_last_error() -> str:
+    return lib().mc_last_error().decode(errors="replace")
+
+
+def mc_version() -> str:
+    return lib().mc_version().decode()

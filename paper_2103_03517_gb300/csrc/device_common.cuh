@@ -1,0 +1,91 @@
+// device_common.cuh -- device primitives of libmc: counter-based RNG, the
+// FP64 exponential of the Metropolis test, fast division, spin algebra.
+#pragma once
+#include <stdint.h>
+
+#include "mc_internal.h"
+
+namespace mcgb {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// S-box, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl increments 0x9E3779B9 /
+// 0xBB67AE85.  Counter = (site or pair, sweep, tag, draw), key = seed.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Philox stream tags: bit 0 = colour, bits 1.. = purpose.
+enum { kPurposeMove = 0, kPurposePair = 1, kPurposePerm = 2 };
+__device__ __forceinline__ uint32_t tag_of(int colour, int purpose) {
+    return uint32_t(colour) | (uint32_t(purpose) << 1);
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+    const uint32_t t = __umulhi(n, f.mul);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// exp(x) in FP64 with a fixed operation sequence, so that every IEEE
+// machine returns the same bits: Cody-Waite reduction x = k ln2 + r with a
+// 32-bit head of ln2, the degree-13 Taylor polynomial of e^r by Horner's
+// rule (|r| <= ln2/2), and scaling by 2^k as two exact powers of two.
+// Constants are the nearest doubles to ln2 (head/tail), 1/ln2 and 1/n!.
+// Used for the Metropolis test of Eq. 1 in the FP64 mode.
+__device__ __forceinline__ double pow2_bits(int k) {
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__device__ inline double exp_fp64(double x) {
+    if (x != x) return x;
+    if (x < -746.0) return 0.0;
+    if (x > 709.79) return __longlong_as_double(0x7FF0000000000000LL);
+    const double kf = floor(x * 0x1.71547652b82fep+0 + 0.5);
+    const int k = (int)kf;
+    const double r = (x - kf * 0x1.62e42ff000000p-1) - kf * -0x1.718432a1b0e26p-35;
+    double p = 0x1.6124613a86d09p-33;      // 1/13!
+    p = p * r + 0x1.1eed8eff8d898p-29;     // 1/12!
+    p = p * r + 0x1.ae64567f544e4p-26;     // 1/11!
+    p = p * r + 0x1.27e4fb7789f5cp-22;     // 1/10!
+    p = p * r + 0x1.71de3a556c734p-19;     // 1/9!
+    p = p * r + 0x1.a01a01a01a01ap-16;     // 1/8!
+    p = p * r + 0x1.a01a01a01a01ap-13;     // 1/7!
+    p = p * r + 0x1.6c16c16c16c17p-10;     // 1/6!
+    p = p * r + 0x1.1111111111111p-7;      // 1/5!
+    p = p * r + 0x1.5555555555555p-5;      // 1/4!
+    p = p * r + 0x1.5555555555555p-3;      // 1/3!
+    p = p * r + 0x1.0000000000000p-1;      // 1/2!
+    p = p * r + 1.0;                       // 1/1!
+    p = p * r + 1.0;                       // 1/0!
+    const int k1 = k / 2;
+    const int k2 = k - k1;
+    return (p * pow2_bits(k1)) * pow2_bits(k2);
+}
+
+template <typename R>
+struct V3 {
+    R x, y, z;
+};
+
+// Fixed-point conversion of a block partial sum (round to nearest).
+__device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * kFixScale); }
+
+// Locate the lattice that owns blockIdx.x in a batched launch.
+__device__ __forceinline__ int find_lattice(const GroupArgs& g) {
+    int lo = 0, hi = g.n - 1;
+    const uint32_t b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.start[mid]) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace mcgb

@@ -1,0 +1,196 @@
+// groups.cpp -- batched advance of many independent lattices: one launch per
+// colour pass for the whole group, replayed from captured CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace mcgb;
+
+namespace {
+constexpr int kGraphSweeps = 16;  // sweeps per captured graph
+}
+
+struct mc_group {
+    std::vector<mc_handle> lats;
+    std::vector<cudaStream_t> member_streams;  // restored at destroy
+    int device = 0;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    void* d_mem = nullptr;
+    LatDev** d_lats = nullptr;
+    uint32_t* d_start_site = nullptr;
+    uint32_t* d_start_pair = nullptr;
+    uint32_t nb_site = 0, nb_pair = 0;
+    const void* cone = nullptr;
+    // captured graphs: [constrained][measure]
+    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+
+    GroupArgs site_args() const { return GroupArgs{d_lats, d_start_site, int(lats.size())}; }
+    GroupArgs pair_args() const { return GroupArgs{d_lats, d_start_pair, int(lats.size())}; }
+};
+
+static int group_graph(mc_group* g, bool constrained, int measure, cudaGraphExec_t* out) {
+    cudaGraphExec_t& ex = g->exec[constrained][measure];
+    if (!ex) {
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        int rc = enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair,
+                                g->cone, kGraphSweeps, measure, constrained, g->stream, nullptr);
+        e = cudaStreamEndCapture(g->stream, &graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { ex = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    }
+    *out = ex;
+    return MC_OK;
+}
+
+static int group_run(mc_group* g, int n, int measure, bool constrained) {
+    cudaSetDevice(g->device);
+    const int reps = n / kGraphSweeps;
+    if (reps > 0) {
+        cudaGraphExec_t ex;
+        int rc = group_graph(g, constrained, measure, &ex);
+        if (rc) return rc;
+        for (int r = 0; r < reps; ++r) {
+            cudaError_t e = cudaGraphLaunch(ex, g->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        }
+    }
+    return enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair, g->cone,
+                          n - reps * kGraphSweeps, measure, constrained, g->stream, nullptr);
+}
+
+extern "C" {
+
+MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* out) {
+    if (!lattices || n < 1 || !out) return fail(MC_ERR_ARG, "invalid argument");
+    mc_group* g = new mc_group();
+    g->lats.assign(lattices, lattices + n);
+    g->device = lattices[0]->device;
+    g->precision = lattices[0]->hp.precision;
+    g->stream = lattices[0]->stream;
+    g->cone = lattices[0]->cone;
+    for (int i = 0; i < n; ++i) {
+        if (!lattices[i] || lattices[i]->device != g->device || lattices[i]->hp.precision != g->precision) {
+            delete g;
+            return fail(MC_ERR_ARG, "group members must share device and precision");
+        }
+    }
+    std::vector<LatDev*> ptrs(n);
+    std::vector<uint32_t> ss(n + 1), sp(n + 1);
+    for (int i = 0; i < n; ++i) {
+        ptrs[i] = lattices[i]->d_lat;
+        ss[i + 1] = ss[i] + lattices[i]->hp.nblocks_site;
+        sp[i + 1] = sp[i] + lattices[i]->hp.nblocks_pair;
+    }
+    g->nb_site = ss[n];
+    g->nb_pair = sp[n];
+    cudaSetDevice(g->device);
+    const size_t b_ptrs = (sizeof(LatDev*) * n + 255) & ~size_t(255);
+    const size_t b_idx = (sizeof(uint32_t) * (n + 1) + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc(&g->d_mem, b_ptrs + 2 * b_idx);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(group)"); }
+    g->d_lats = static_cast<LatDev**>(g->d_mem);
+    g->d_start_site = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptrs);
+    g->d_start_pair = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptrs + b_idx);
+    // the members' queued work must be complete before the group uses them;
+    // from now on every member runs on the group stream, so that calls on a
+    // member order after the group's work
+    for (int i = 0; i < n; ++i) {
+        cudaStreamSynchronize(lattices[i]->stream);
+        g->member_streams.push_back(lattices[i]->stream);
+        lattices[i]->stream = g->stream;
+    }
+    bool ok = cudaMemcpy(g->d_lats, ptrs.data(), sizeof(LatDev*) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(g->d_start_site, ss.data(), 4 * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(g->d_start_pair, sp.data(), 4 * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        for (int i = 0; i < n; ++i) lattices[i]->stream = g->member_streams[i];
+        cudaFree(g->d_mem);
+        delete g;
+        return fail(MC_ERR_CUDA, "group table upload failed");
+    }
+    *out = g;
+    return MC_OK;
+}
+
+MC_API int mc_group_destroy(mc_group_handle g) {
+    if (!g) return MC_OK;
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    for (auto& row : g->exec)
+        for (auto& ex : row)
+            if (ex) cudaGraphExecDestroy(ex);
+    cudaFree(g->d_mem);
+    for (size_t i = 0; i < g->lats.size(); ++i) g->lats[i]->stream = g->member_streams[i];
+    delete g;
+    return MC_OK;
+}
+
+MC_API int mc_group_sweep(mc_group_handle g, int n_sweeps, int measure) {
+    if (!g || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    return group_run(g, n_sweeps, measure ? 1 : 0, false);
+}
+
+MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_deg, const double* phi_c_deg,
+                                      int n_sweeps, int measure) {
+    if (!g || !theta_c_deg || !phi_c_deg || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(g->device);
+    for (size_t i = 0; i < g->lats.size(); ++i) {
+        mc_handle h = g->lats[i];
+        if (!(theta_c_deg[i] >= 0.0 && theta_c_deg[i] <= 180.0) || !std::isfinite(phi_c_deg[i]))
+            return fail(MC_ERR_ARG, "constraint angle %zu invalid", i);
+        for (int a = 0; a < 3; ++a)
+            if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
+        constraint_frame(theta_c_deg[i], phi_c_deg[i], h->hp.R);
+        int rc = upload_params(h);  // on the group stream (members adopt it)
+        if (rc) return rc;
+    }
+    return group_run(g, n_sweeps, measure ? 1 : 0, true);
+}
+
+MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms, int* launches) {
+    if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(g->device);
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    int rc = enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair,
+                            g->cone, n_sweeps, measure ? 1 : 0, false, g->stream, &ev);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    double total = 0.0;
+    for (auto& pr : ev) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        total += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "time_passes sync");
+    *launches = int(ev.size());
+    *avg_ms = ev.empty() ? 0.0 : total / double(ev.size());
+    return MC_OK;
+}
+
+MC_API int mc_group_sync(mc_group_handle g) {
+    if (!g) return fail(MC_ERR_ARG, "null group");
+    cudaSetDevice(g->device);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "group sync");
+    for (mc_handle h : g->lats) {
+        LatState st;
+        int rc = read_state(h, &st);
+        if (rc) return rc;
+        if (st.error) return fail(st.error, "device reported error %d", st.error);
+    }
+    return MC_OK;
+}
+
+}  // extern "C"

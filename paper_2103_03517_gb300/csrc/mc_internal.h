@@ -1,0 +1,113 @@
+// mc_internal.h -- device-resident lattice descriptor shared by the host
+// runtime and the kernels of libmc.
+//
+// Spin layout in HBM (both precisions): colour-split structure of arrays.
+// Colour c = (x + y + z) mod 2 (0 = red, Sec. 2 checkerboard).  A site
+// (x, y, z) of colour c has the colour index q = (x >> 1) + Lh (y + Ly z),
+// Lh = Lx / 2, and component a of its spin lives at
+//     spins[(3 c + a) * stride + q],   stride = Nc rounded up to 64.
+// In row (y, z) the colour-c sites sit at x = ((y + z + c) & 1) + 2k, so the
+// other colour's -x / +x neighbours of (k, y, z) are colour indices
+// k + xoff - 1 and k + xoff in the same row, and the -y/+y/-z/+z neighbours
+// share k in the adjacent rows.
+#pragma once
+#include <stdint.h>
+
+namespace mcgb {
+
+constexpr int kBlock = 256;          // threads per block of every pass kernel
+constexpr int kNumSums = 12;         // per-sample lattice sums, see kSum*
+constexpr int kRingWords = 14;       // doubles per ring sample
+constexpr int kMomentWords = 26;     // running sums of per-sample observables
+constexpr double kFixScale = 268435456.0;   // 2^28: fixed point of the sums
+
+// Per-sample lattice sums (dimensionless, each bounded by 3 N):
+enum {
+    kSumMx = 0, kSumMy, kSumMz,      // sum S
+    kSumEx,                          // sum over bonds S_i.S_j
+    kSumU,                           // sum (S.e)^2
+    kSumC,                           // sum Sx^2Sy^2 + Sx^2Sz^2 + Sy^2Sz^2
+    kSumTux, kSumTuy, kSumTuz,       // sum (S.e)(S x e)
+    kSumTcx, kSumTcy, kSumTcz        // sum S x c(S)
+};
+
+// Moment words (running sums over samples), same order as the oracle.
+enum {
+    kMomN = 0, kMomM = 1, kMomM2 = 4, kMomMabs = 7, kMomMl = 10, kMomMl2 = 11,
+    kMomMl4 = 12, kMomE = 13, kMomE2 = 14, kMomParts = 15, kMomTq = 19, kMomTq2 = 22
+};
+
+// Unsigned 32-bit division by a runtime constant with a multiply
+// (Granlund & Montgomery, PLDI 1994; round-up variant with the 33-bit
+// correction of Hacker's Delight ch. 10): exact for every n < 2^32.
+struct FastDiv {
+    uint32_t d, mul, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.mul = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    f.s1 = l > 0 ? 1 : 0;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+struct LatParams {
+    int Lx, Ly, Lz, Lh;
+    int bc[3];
+    int precision;
+    uint32_t Nc;            // sites per colour = N / 2
+    uint32_t stride;        // Nc rounded up to 64
+    uint32_t n_pairs;       // Nc / 2
+    int perm_h;             // Feistel half width in bits (domain 2^(2h) >= Nc)
+    long long N, n_mov;
+    int adapt_in_measure;
+    uint32_t key0, key1;
+    FastDiv div_lh, div_ly;
+    uint32_t nblocks_site;  // blocks of a site pass of this lattice
+    uint32_t nblocks_pair;  // blocks of a pair pass of this lattice
+    void* spins;
+    const uint8_t* bonds;   // [2][stride] or null
+    const int32_t* grain;   // [2][stride] or null
+    const void* gaxis;      // [n_grains][4] in the lattice precision, or null
+    double* ring;           // [ring_cap][kRingWords]
+    int ring_cap;
+    long long* profile;     // [3][Lx] fixed-point sums
+    double J, Ku, e[3], Kc, H[3], T;
+    float fJ, fKu, fe[3], fKc, fH[3], fT;
+    double R[9];            // constraint frame rows e1 = e_C, e2, e3
+    float fR[9];
+};
+
+struct LatState {
+    unsigned long long acc;         // accepted moves in the current sweep
+    unsigned int done[4];           // finished blocks: red, black, M_L, measure
+    int theta;                      // cone half-angle, degrees
+    uint32_t sweep;                 // sweeps completed
+    int error;                      // sticky mc_status
+    int pad;
+    long long last_acc;
+    long long sums[kNumSums];       // fixed-point lattice sums of this sample
+    long long ml_hi, ml_lo;         // exact M_L of this constrained sweep
+    long long ring_count;
+    long long prof_samples;
+    double moments[kMomentWords];
+};
+
+struct LatDev {
+    LatParams p;
+    LatState st;
+};
+
+// Arguments of a batched launch: lattice l owns blocks
+// [start[l], start[l+1]) of the grid.
+struct GroupArgs {
+    LatDev* const* lats;
+    const uint32_t* start;
+    int n;
+};
+
+}  // namespace mcgb

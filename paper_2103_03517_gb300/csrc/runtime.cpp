@@ -1,0 +1,753 @@
+// runtime.cpp -- lattices, groups, observables and checkpoints of libmc
+// (the C ABI of include/mc.h, except the server).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mc.h"
+#include "mc_internal.h"
+#include "runtime.h"
+
+namespace mcgb {
+
+// ----------------------------------------------------------------- errors
+static thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? MC_ERR_NOMEM : MC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// ------------------------------------------------------ per-device tables
+// c(theta) = 1 - cos(theta) = 2 sin^2(theta / 2) for integer degrees (cone
+// half-angle of Table A1), in both precisions, computed on the host.
+struct DeviceTables {
+    double* cone64 = nullptr;
+    float* cone32 = nullptr;
+};
+
+static std::mutex g_tables_mu;
+static std::vector<DeviceTables> g_tables;
+
+int device_tables(int device, const double** c64, const float** c32) {
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if ((int)g_tables.size() <= device) g_tables.resize(device + 1);
+    DeviceTables& t = g_tables[device];
+    if (!t.cone64) {
+        double h64[181];
+        float h32[181];
+        for (int d = 0; d <= 180; ++d) {
+            const double s = std::sin((double)d * (M_PI / 360.0));
+            h64[d] = 2.0 * (s * s);
+            h32[d] = (float)h64[d];
+        }
+        CK(cudaMalloc(&t.cone64, sizeof h64));
+        CK(cudaMalloc(&t.cone32, sizeof h32));
+        CK(cudaMemcpy(t.cone64, h64, sizeof h64, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(t.cone32, h32, sizeof h32, cudaMemcpyHostToDevice));
+    }
+    *c64 = t.cone64;
+    *c32 = t.cone32;
+    return MC_OK;
+}
+
+// Constraint frame of Table A2 (x-axis along e_C): rows e1 = e_C,
+// e2 = (-sin phi, cos phi, 0), e3 = e1 x e2.
+void constraint_frame(double theta_deg, double phi_deg, double R[9]) {
+    const double th = theta_deg * (M_PI / 180.0), ph = phi_deg * (M_PI / 180.0);
+    const double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
+    R[0] = st * cp;  R[1] = st * sp;  R[2] = ct;
+    R[3] = -sp;      R[4] = cp;       R[5] = 0.0;
+    R[6] = -ct * cp; R[7] = -ct * sp; R[8] = st;
+}
+
+static int feistel_half_bits(uint32_t n) {
+    int h = 1;
+    while ((uint64_t(1) << (2 * h)) < uint64_t(n)) ++h;
+    return h;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------- lattices
+static void set_float_params(LatParams& p) {
+    p.fJ = (float)p.J; p.fKu = (float)p.Ku; p.fKc = (float)p.Kc; p.fT = (float)p.T;
+    for (int a = 0; a < 3; ++a) { p.fe[a] = (float)p.e[a]; p.fH[a] = (float)p.H[a]; }
+    for (int a = 0; a < 9; ++a) p.fR[a] = (float)p.R[a];
+}
+
+size_t lattice_bytes(const mc_desc* d) {
+    const uint64_t N = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
+    const uint64_t Nc = N / 2;
+    const uint64_t stride = (Nc + 63) / 64 * 64;
+    const size_t rs = d->precision == MC_FP64 ? 8 : 4;
+    size_t b = align256(sizeof(LatDev));
+    b += align256(6 * stride * rs);
+    if (d->bond_mask) b += align256(2 * stride);
+    if (d->grain_id) b += align256(2 * stride * 4) + align256(4 * size_t(std::max(d->n_grains, 1)) * rs);
+    const int cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
+    b += align256(size_t(cap) * kRingWords * 8);
+    b += align256(3 * size_t(d->dims[0]) * 8);
+    b += align256(3 * sizeof(void*) + 4 * sizeof(uint32_t));  // group-of-one tables
+    return b;
+}
+
+int validate_desc(const mc_desc* d) {
+    for (int a = 0; a < 3; ++a) {
+        if (d->dims[a] < 1) return fail(MC_ERR_ARG, "dims[%d] = %d < 1", a, d->dims[a]);
+        if (d->boundary[a] < 0 || d->boundary[a] > 2) return fail(MC_ERR_ARG, "boundary[%d] invalid", a);
+        if (d->boundary[a] == MC_PERIODIC && (d->dims[a] % 2))
+            return fail(MC_ERR_ARG, "periodic axis %d has odd size %d (breaks the two-colouring)", a, d->dims[a]);
+    }
+    if (d->dims[0] % 2) return fail(MC_ERR_ARG, "Lx = %d must be even", d->dims[0]);
+    const uint64_t N = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
+    if (N >= (uint64_t(1) << 32)) return fail(MC_ERR_ARG, "N = %llu spins exceeds 2^32 - 1", (unsigned long long)N);
+    if (!(d->T > 0.0) || !std::isfinite(d->T)) return fail(MC_ERR_ARG, "T must be > 0");
+    const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
+    if (!(an > 0.0)) return fail(MC_ERR_ARG, "|axis| = 0");
+    if (d->precision != MC_FP32 && d->precision != MC_FP64) return fail(MC_ERR_ARG, "precision invalid");
+    if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
+    if (d->init != MC_INIT_UNIFORM && d->init != MC_INIT_WALL) return fail(MC_ERR_ARG, "init invalid");
+    if (d->init == MC_INIT_UNIFORM) {
+        const double n = std::sqrt(d->init_dir[0] * d->init_dir[0] + d->init_dir[1] * d->init_dir[1] +
+                                   d->init_dir[2] * d->init_dir[2]);
+        if (!(n > 0.0)) return fail(MC_ERR_ARG, "|init_dir| = 0");
+    }
+    if (d->grain_id && (!d->grain_axis || d->n_grains < 1)) return fail(MC_ERR_ARG, "grain tables incomplete");
+    if (d->grain_id)
+        for (uint64_t i = 0; i < N; ++i)
+            if (d->grain_id[i] < 0 || d->grain_id[i] >= d->n_grains) return fail(MC_ERR_ARG, "grain id out of range");
+    if (d->bond_mask) {
+        // every bond must be present from both ends
+        const int L[3] = {d->dims[0], d->dims[1], d->dims[2]};
+        for (int z = 0; z < L[2]; ++z)
+            for (int y = 0; y < L[1]; ++y)
+                for (int x = 0; x < L[0]; ++x) {
+                    const uint64_t i = x + uint64_t(L[0]) * (y + uint64_t(L[1]) * z);
+                    const int c[3] = {x, y, z};
+                    for (int ax = 0; ax < 3; ++ax) {
+                        int cc[3] = {c[0], c[1], c[2]};
+                        if (cc[ax] + 1 >= L[ax] && d->boundary[ax] != MC_PERIODIC) continue;
+                        cc[ax] = (cc[ax] + 1) % L[ax];
+                        const uint64_t j = cc[0] + uint64_t(L[0]) * (cc[1] + uint64_t(L[1]) * cc[2]);
+                        const int fwd = (d->bond_mask[i] >> (2 * ax + 1)) & 1;
+                        const int bwd = (d->bond_mask[j] >> (2 * ax)) & 1;
+                        if (fwd != bwd) return fail(MC_ERR_ARG, "bond mask not symmetric at site %llu", (unsigned long long)i);
+                    }
+                }
+    }
+    return MC_OK;
+}
+
+template <typename R>
+static void to_device_layout(const LatParams& p, const double* xyz, R* out) {
+    for (int z = 0; z < p.Lz; ++z)
+        for (int y = 0; y < p.Ly; ++y)
+            for (int x = 0; x < p.Lx; ++x) {
+                const size_t i = x + size_t(p.Lx) * (y + size_t(p.Ly) * z);
+                const int c = (x + y + z) & 1;
+                const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
+                for (int a = 0; a < 3; ++a) out[(3 * c + a) * size_t(p.stride) + q] = (R)xyz[3 * i + a];
+            }
+}
+
+template <typename R>
+static void from_device_layout(const LatParams& p, const R* in, double* xyz) {
+    for (int z = 0; z < p.Lz; ++z)
+        for (int y = 0; y < p.Ly; ++y)
+            for (int x = 0; x < p.Lx; ++x) {
+                const size_t i = x + size_t(p.Lx) * (y + size_t(p.Ly) * z);
+                const int c = (x + y + z) & 1;
+                const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
+                for (int a = 0; a < 3; ++a) xyz[3 * i + a] = (double)in[(3 * c + a) * size_t(p.stride) + q];
+            }
+}
+
+static void per_site_colour_split(const LatParams& p, const void* src, size_t elem, void* dst) {
+    for (int z = 0; z < p.Lz; ++z)
+        for (int y = 0; y < p.Ly; ++y)
+            for (int x = 0; x < p.Lx; ++x) {
+                const size_t i = x + size_t(p.Lx) * (y + size_t(p.Ly) * z);
+                const int c = (x + y + z) & 1;
+                const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
+                std::memcpy(static_cast<char*>(dst) + (c * size_t(p.stride) + q) * elem,
+                            static_cast<const char*>(src) + i * elem, elem);
+            }
+}
+
+const KernelSet& kernel_set(int precision) { return precision == MC_FP64 ? kernels_f64() : kernels_f32(); }
+
+int upload_params(mc_lattice* h) {
+    set_float_params(h->hp);
+    CK(cudaMemcpyAsync(&h->d_lat->p, &h->hp, sizeof(LatParams), cudaMemcpyHostToDevice, h->stream));
+    return MC_OK;
+}
+
+int create_lattice(const mc_desc* din, mc_handle* out) {
+    if (!din || !out) return fail(MC_ERR_ARG, "null argument");
+    int rc = validate_desc(din);
+    if (rc) return rc;
+    mc_lattice* h = new mc_lattice();
+    h->desc = *din;
+    h->desc.bond_mask = nullptr;
+    h->desc.grain_id = nullptr;
+    h->desc.grain_axis = nullptr;
+    const mc_desc* d = din;
+    h->device = d->device;
+    if (cudaSetDevice(d->device) != cudaSuccess) { delete h; return fail(MC_ERR_CUDA, "cudaSetDevice(%d) failed", d->device); }
+    if (d->stream) {
+        h->stream = static_cast<cudaStream_t>(d->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(MC_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        h->owned_stream = h->stream;
+    }
+    LatParams& p = h->hp;
+    std::memset(&p, 0, sizeof p);
+    p.Lx = d->dims[0]; p.Ly = d->dims[1]; p.Lz = d->dims[2]; p.Lh = p.Lx / 2;
+    for (int a = 0; a < 3; ++a) p.bc[a] = d->boundary[a];
+    p.precision = d->precision;
+    p.N = (long long)p.Lx * p.Ly * p.Lz;
+    p.Nc = uint32_t(p.N / 2);
+    p.stride = (p.Nc + 63) / 64 * 64;
+    p.n_pairs = p.Nc / 2;
+    p.perm_h = feistel_half_bits(p.Nc);
+    long long pinned = 0;
+    for (int z = 0; z < p.Lz; ++z)
+        for (int y = 0; y < p.Ly; ++y)
+            for (int x = 0; x < p.Lx; ++x) {
+                const int c[3] = {x, y, z};
+                const int L[3] = {p.Lx, p.Ly, p.Lz};
+                bool pin = false;
+                for (int a = 0; a < 3; ++a) pin |= p.bc[a] == MC_PINNED && (c[a] == 0 || c[a] == L[a] - 1);
+                pinned += pin;
+            }
+    p.n_mov = p.N - pinned;
+    p.adapt_in_measure = d->adapt_in_measure;
+    p.key0 = uint32_t(d->seed);
+    p.key1 = uint32_t(d->seed >> 32);
+    p.div_lh = make_fastdiv(uint32_t(p.Lh));
+    p.div_ly = make_fastdiv(uint32_t(p.Ly));
+    p.nblocks_site = (p.Nc + kBlock - 1) / kBlock;
+    p.nblocks_pair = (p.n_pairs + kBlock - 1) / kBlock;
+    if (p.nblocks_pair == 0) p.nblocks_pair = 1;
+    p.J = d->J; p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
+    const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
+    for (int a = 0; a < 3; ++a) { p.e[a] = d->axis[a] / an; p.H[a] = d->H[a]; }
+    constraint_frame(0.0, 0.0, p.R);
+    p.ring_cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
+    h->desc.ring_capacity = p.ring_cap;
+    const size_t rs = d->precision == MC_FP64 ? 8 : 4;
+
+    // one allocation, carved into 256-byte aligned pieces
+    h->bytes = lattice_bytes(d);
+    cudaError_t e = cudaMalloc(&h->d_base, h->bytes);
+    if (e != cudaSuccess) {
+        if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
+        delete h;
+        return cuda_fail(e, "cudaMalloc(lattice)");
+    }
+    char* cur = static_cast<char*>(h->d_base);
+    auto take = [&](size_t b) { char* r = cur; cur += align256(b); return r; };
+    h->d_lat = reinterpret_cast<LatDev*>(take(sizeof(LatDev)));
+    p.spins = take(6 * size_t(p.stride) * rs);
+    std::vector<uint8_t> hb;
+    if (din->bond_mask) {
+        hb.assign(2 * size_t(p.stride), 0);
+        per_site_colour_split(p, din->bond_mask, 1, hb.data());
+        p.bonds = reinterpret_cast<const uint8_t*>(take(2 * size_t(p.stride)));
+        h->film_bonds.assign(din->bond_mask, din->bond_mask + p.N);
+    }
+    std::vector<int32_t> hg;
+    std::vector<char> hax;
+    if (din->grain_id) {
+        hg.assign(2 * size_t(p.stride), 0);
+        per_site_colour_split(p, din->grain_id, 4, hg.data());
+        p.grain = reinterpret_cast<const int32_t*>(take(2 * size_t(p.stride) * 4));
+        hax.assign(4 * size_t(d->n_grains) * rs, 0);
+        for (int g = 0; g < d->n_grains; ++g) {
+            const double* v = &din->grain_axis[3 * g];
+            const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            for (int a = 0; a < 3; ++a) {
+                if (rs == 8) reinterpret_cast<double*>(hax.data())[4 * g + a] = v[a] / n;
+                else reinterpret_cast<float*>(hax.data())[4 * g + a] = (float)(v[a] / n);
+            }
+        }
+        p.gaxis = take(4 * size_t(d->n_grains) * rs);
+        h->film_grain.assign(din->grain_id, din->grain_id + p.N);
+        h->film_axes.assign(din->grain_axis, din->grain_axis + 3 * size_t(d->n_grains));
+    }
+    p.ring = reinterpret_cast<double*>(take(size_t(p.ring_cap) * kRingWords * 8));
+    p.profile = reinterpret_cast<long long*>(take(3 * size_t(p.Lx) * 8));
+    h->d_group_lats = reinterpret_cast<LatDev**>(take(sizeof(void*)));
+    h->d_group_start = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
+    h->d_group_start_pair = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
+
+    // initial state
+    std::vector<double> xyz(size_t(p.N) * 3);
+    for (long long i = 0; i < p.N; ++i) {
+        if (d->init == MC_INIT_WALL) {
+            const int x = int(i % p.Lx);
+            xyz[3 * i] = 0; xyz[3 * i + 1] = 0; xyz[3 * i + 2] = x < p.Lx / 2 ? 1.0 : -1.0;
+        } else {
+            const double n = std::sqrt(d->init_dir[0] * d->init_dir[0] + d->init_dir[1] * d->init_dir[1] +
+                                       d->init_dir[2] * d->init_dir[2]);
+            for (int a = 0; a < 3; ++a) xyz[3 * i + a] = d->init_dir[a] / n;
+        }
+    }
+    std::vector<char> hs(6 * size_t(p.stride) * rs, 0);
+    if (rs == 8) to_device_layout(p, xyz.data(), reinterpret_cast<double*>(hs.data()));
+    else to_device_layout(p, xyz.data(), reinterpret_cast<float*>(hs.data()));
+
+    LatDev init;
+    std::memset(&init, 0, sizeof init);
+    init.st.theta = d->theta0_deg;
+    rc = MC_OK;
+    auto up = [&](void* dst, const void* src, size_t b) {
+        if (rc == MC_OK) {
+            cudaError_t ee = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, h->stream);
+            if (ee != cudaSuccess) rc = cuda_fail(ee, "cudaMemcpyAsync(init)");
+        }
+    };
+    set_float_params(p);
+    init.p = p;
+    up(h->d_lat, &init, sizeof init);
+    up(p.spins, hs.data(), hs.size());
+    if (!hb.empty()) up(const_cast<uint8_t*>(p.bonds), hb.data(), hb.size());
+    if (!hg.empty()) {
+        up(const_cast<int32_t*>(p.grain), hg.data(), hg.size() * 4);
+        up(const_cast<void*>(p.gaxis), hax.data(), hax.size());
+    }
+    if (rc == MC_OK && cudaMemsetAsync(p.ring, 0, size_t(p.ring_cap) * kRingWords * 8, h->stream) != cudaSuccess)
+        rc = fail(MC_ERR_CUDA, "memset ring");
+    if (rc == MC_OK && cudaMemsetAsync(p.profile, 0, 3 * size_t(p.Lx) * 8, h->stream) != cudaSuccess)
+        rc = fail(MC_ERR_CUDA, "memset profile");
+    LatDev* one = h->d_lat;
+    const uint32_t st_site[2] = {0, p.nblocks_site};
+    const uint32_t st_pair[2] = {0, p.nblocks_pair};
+    up(h->d_group_lats, &one, sizeof one);
+    up(h->d_group_start, st_site, sizeof st_site);
+    up(h->d_group_start_pair, st_pair, sizeof st_pair);
+    if (rc == MC_OK) {
+        const double* c64;
+        const float* c32;
+        rc = device_tables(h->device, &c64, &c32);
+        h->cone = d->precision == MC_FP64 ? (const void*)c64 : (const void*)c32;
+    }
+    if (rc == MC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(MC_ERR_CUDA, "init sync");
+    if (rc != MC_OK) {
+        cudaFree(h->d_base);
+        if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MC_OK;
+}
+
+GroupArgs single_args(mc_lattice* h, bool pair) {
+    GroupArgs g;
+    g.lats = h->d_group_lats;
+    g.start = pair ? h->d_group_start_pair : h->d_group_start;
+    g.n = 1;
+    return g;
+}
+
+// Enqueue n sweeps of a set of lattices described by (site, pair) launch
+// arguments; with events != nullptr every pass launch is bracketed by events.
+int enqueue_sweeps(const KernelSet& k, const GroupArgs& gs, uint32_t nb_site, const GroupArgs& gp,
+                   uint32_t nb_pair, const void* cone, int n, int measure, bool constrained, cudaStream_t s,
+                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events) {
+    auto timed = [&](auto&& launch) {
+        if (events) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+            launch();
+            cudaEventRecord(b, s);
+            events->emplace_back(a, b);
+        } else {
+            launch();
+        }
+    };
+    for (int i = 0; i < n; ++i) {
+        if (!constrained) {
+            timed([&] { k.colour_pass(gs, nb_site, cone, 0, 0, s); });
+            timed([&] { k.colour_pass(gs, nb_site, cone, 1, measure, s); });
+        } else {
+            k.mlong(gs, nb_site, s);
+            timed([&] { k.pair_pass(gp, nb_pair, cone, 0, 0, 0, s); });
+            timed([&] { k.pair_pass(gp, nb_pair, cone, 1, measure ? 0 : 1, 0, s); });
+            if (measure) k.measure(gs, nb_site, s);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return MC_OK;
+}
+
+int read_state(mc_lattice* h, LatState* st) {
+    CK(cudaMemcpyAsync(st, &h->d_lat->st, sizeof(LatState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+}  // namespace mcgb
+
+using namespace mcgb;
+
+// ===================================================================== ABI
+extern "C" {
+
+MC_API const char* mc_last_error(void) { return g_error.c_str(); }
+MC_API const char* mc_version(void) { return "libmc 1.0 (sm_103a)"; }
+
+MC_API void mc_desc_default(mc_desc* d) {
+    if (!d) return;
+    std::memset(d, 0, sizeof *d);
+    d->dims[0] = d->dims[1] = d->dims[2] = 16;
+    d->precision = MC_FP32;
+    d->J = 1.0;
+    d->axis[2] = 1.0;
+    d->T = 1.0;
+    d->theta0_deg = 30;
+    d->adapt_in_measure = 1;
+    d->init = MC_INIT_UNIFORM;
+    d->init_dir[2] = 1.0;
+    d->ring_capacity = 4096;
+}
+
+MC_API int mc_create(const int dims[3], double J, double K_u, const double axis[3], double K_c, const double H[3],
+                     double T, uint64_t seed, mc_handle* out) {
+    if (!dims || !axis || !H) return fail(MC_ERR_ARG, "null argument");
+    mc_desc d;
+    mc_desc_default(&d);
+    for (int a = 0; a < 3; ++a) { d.dims[a] = dims[a]; d.axis[a] = axis[a]; d.H[a] = H[a]; }
+    d.J = J; d.K_u = K_u; d.K_c = K_c; d.T = T; d.seed = seed;
+    return create_lattice(&d, out);
+}
+
+MC_API int mc_create_ex(const mc_desc* d, mc_handle* out) { return create_lattice(d, out); }
+
+MC_API int mc_destroy(mc_handle h) {
+    if (!h) return MC_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_base);
+    if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
+    delete h;
+    return MC_OK;
+}
+
+MC_API int mc_set_temperature(mc_handle h, double T) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(MC_ERR_ARG, "T must be > 0");
+    h->hp.T = T;
+    h->desc.T = T;
+    return upload_params(h);
+}
+
+MC_API int mc_set_field(mc_handle h, const double H[3]) {
+    if (!h || !H) return fail(MC_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; ++a) { h->hp.H[a] = H[a]; h->desc.H[a] = H[a]; }
+    return upload_params(h);
+}
+
+MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
+    if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(h->device);
+    const KernelSet& k = kernel_set(h->hp.precision);
+    return enqueue_sweeps(k, single_args(h, false), h->hp.nblocks_site, single_args(h, true), h->hp.nblocks_pair,
+                          h->cone, n_sweeps, measure ? 1 : 0, false, h->stream, nullptr);
+}
+
+MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_deg, int n_sweeps, int measure) {
+    if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    if (!(theta_c_deg >= 0.0 && theta_c_deg <= 180.0)) return fail(MC_ERR_ARG, "theta_c outside [0, 180]");
+    if (!std::isfinite(phi_c_deg)) return fail(MC_ERR_ARG, "phi_c not finite");
+    for (int a = 0; a < 3; ++a)
+        if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
+    cudaSetDevice(h->device);
+    constraint_frame(theta_c_deg, phi_c_deg, h->hp.R);
+    int rc = upload_params(h);
+    if (rc) return rc;
+    const KernelSet& k = kernel_set(h->hp.precision);
+    return enqueue_sweeps(k, single_args(h, false), h->hp.nblocks_site, single_args(h, true), h->hp.nblocks_pair,
+                          h->cone, n_sweeps, measure ? 1 : 0, true, h->stream, nullptr);
+}
+
+MC_API int mc_sync(mc_handle h) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    cudaSetDevice(h->device);
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    if (st.error) return fail(st.error, "device reported error %d", st.error);
+    return MC_OK;
+}
+
+MC_API int mc_measure(mc_handle h, mc_observables* out) {
+    if (!h || !out) return fail(MC_ERR_ARG, "null argument");
+    cudaSetDevice(h->device);
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof *out);
+    const double* mo = st.moments;
+    const double n = mo[kMomN];
+    out->n_samples = (int64_t)n;
+    out->sweeps_done = st.sweep;
+    out->theta_deg = st.theta;
+    out->error = st.error;
+    out->accept_last = double(st.last_acc) / double(h->hp.n_mov > 0 ? h->hp.n_mov : 1);
+    if (n > 0) {
+        for (int a = 0; a < 3; ++a) {
+            out->m[a] = mo[kMomM + a] / n;
+            out->m2[a] = mo[kMomM2 + a] / n;
+            out->m_abs[a] = mo[kMomMabs + a] / n;
+            out->torque[a] = mo[kMomTq + a] / n;
+            out->torque2[a] = mo[kMomTq2 + a] / n;
+        }
+        out->ml = mo[kMomMl] / n;
+        out->ml2 = mo[kMomMl2] / n;
+        out->ml4 = mo[kMomMl4] / n;
+        out->e = mo[kMomE] / n;
+        out->e2 = mo[kMomE2] / n;
+        for (int a = 0; a < 4; ++a) out->e_parts[a] = mo[kMomParts + a] / n;
+        const double NT = double(h->hp.N) / h->hp.T;
+        out->chi[0] = NT * (out->ml2 - out->ml * out->ml);
+        for (int a = 0; a < 3; ++a) out->chi[1 + a] = NT * (out->m2[a] - out->m[a] * out->m[a]);
+        out->binder = out->ml2 > 0 ? 1.0 - out->ml4 / (3.0 * out->ml2 * out->ml2) : 0.0;
+    }
+    if (st.error) return fail(st.error, "device reported error %d", st.error);
+    return MC_OK;
+}
+
+MC_API int mc_profile_sample(mc_handle h) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    cudaSetDevice(h->device);
+    kernel_set(h->hp.precision).profile(h->d_lat, uint32_t(h->hp.Lh), uint32_t(h->hp.Ly) * h->hp.Lz, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "profile launch");
+    return MC_OK;
+}
+
+MC_API int mc_profile(mc_handle h, int component, double* out, int len) {
+    if (!h || !out || component < 0 || component > 2 || len < h->hp.Lx) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(h->device);
+    std::vector<long long> sums(size_t(h->hp.Lx));
+    CK(cudaMemcpyAsync(sums.data(), h->hp.profile + size_t(component) * h->hp.Lx, sums.size() * 8,
+                       cudaMemcpyDeviceToHost, h->stream));
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    const double denom = double(st.prof_samples) * h->hp.Ly * h->hp.Lz;
+    for (int x = 0; x < h->hp.Lx; ++x) out[x] = denom > 0 ? double(sums[x]) / kFixScale / denom : 0.0;
+    return MC_OK;
+}
+
+MC_API int mc_samples(mc_handle h, mc_sample* out, int max, int* n) {
+    if (!h || !n || (max > 0 && !out)) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(h->device);
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    const int cap = h->hp.ring_cap;
+    const long long have = std::min<long long>(st.ring_count, cap);
+    const long long cnt = std::min<long long>(have, max);
+    std::vector<double> ring(size_t(cap) * kRingWords);
+    CK(cudaMemcpy(ring.data(), h->hp.ring, ring.size() * 8, cudaMemcpyDeviceToHost));
+    const long long first = st.ring_count - cnt;
+    for (long long s = 0; s < cnt; ++s) {
+        const double* r = &ring[size_t((first + s) % cap) * kRingWords];
+        mc_sample& o = out[s];
+        o.sweep = (int64_t)r[0];
+        o.theta_deg = (int32_t)r[1];
+        o.pad = 0;
+        o.accepted = (int64_t)r[2];
+        for (int a = 0; a < 3; ++a) o.m[a] = r[3 + a];
+        for (int a = 0; a < 4; ++a) o.e_parts[a] = r[6 + a];
+        for (int a = 0; a < 3; ++a) o.torque[a] = r[10 + a];
+    }
+    *n = (int)cnt;
+    return MC_OK;
+}
+
+MC_API int mc_reset_stats(mc_handle h) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    cudaSetDevice(h->device);
+    LatDev* d = h->d_lat;
+    CK(cudaMemsetAsync(d->st.moments, 0, sizeof(d->st.moments), h->stream));
+    CK(cudaMemsetAsync(&d->st.ring_count, 0, sizeof(long long), h->stream));
+    CK(cudaMemsetAsync(&d->st.prof_samples, 0, sizeof(long long), h->stream));
+    CK(cudaMemsetAsync(h->hp.profile, 0, 3 * size_t(h->hp.Lx) * 8, h->stream));
+    return MC_OK;
+}
+
+MC_API size_t mc_state_bytes(mc_handle h) {
+    if (!h) return 0;
+    return 6 * size_t(h->hp.stride) * (h->hp.precision == MC_FP64 ? 8 : 4);
+}
+
+MC_API int mc_export_state(mc_handle h, void* host_buf, size_t bytes) {
+    if (!h || !host_buf || bytes != mc_state_bytes(h)) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(h->device);
+    CK(cudaMemcpyAsync(host_buf, h->hp.spins, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+MC_API int mc_import_state(mc_handle h, const void* host_buf, size_t bytes) {
+    if (!h || !host_buf || bytes != mc_state_bytes(h)) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(h->device);
+    CK(cudaMemcpyAsync(h->hp.spins, host_buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    return MC_OK;
+}
+
+MC_API int mc_get_spins(mc_handle h, double* host_xyz, size_t n) {
+    if (!h || !host_xyz || n != size_t(h->hp.N)) return fail(MC_ERR_ARG, "invalid argument");
+    std::vector<char> buf(mc_state_bytes(h));
+    int rc = mc_export_state(h, buf.data(), buf.size());
+    if (rc) return rc;
+    if (h->hp.precision == MC_FP64) from_device_layout(h->hp, reinterpret_cast<const double*>(buf.data()), host_xyz);
+    else from_device_layout(h->hp, reinterpret_cast<const float*>(buf.data()), host_xyz);
+    return MC_OK;
+}
+
+MC_API int mc_set_spins(mc_handle h, const double* host_xyz, size_t n) {
+    if (!h || !host_xyz || n != size_t(h->hp.N)) return fail(MC_ERR_ARG, "invalid argument");
+    std::vector<char> buf(mc_state_bytes(h), 0);
+    if (h->hp.precision == MC_FP64) to_device_layout(h->hp, host_xyz, reinterpret_cast<double*>(buf.data()));
+    else to_device_layout(h->hp, host_xyz, reinterpret_cast<float*>(buf.data()));
+    int rc = mc_import_state(h, buf.data(), buf.size());
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+MC_API int mc_get_theta(mc_handle h, int* theta_deg, int64_t* sweeps_done) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    cudaSetDevice(h->device);
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    if (theta_deg) *theta_deg = st.theta;
+    if (sweeps_done) *sweeps_done = st.sweep;
+    return MC_OK;
+}
+
+// ------------------------------------------------------------- checkpoint
+static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '1'};
+
+MC_API int mc_save(mc_handle h, const char* path) {
+    if (!h || !path) return fail(MC_ERR_ARG, "null argument");
+    cudaSetDevice(h->device);
+    LatState st;
+    int rc = read_state(h, &st);
+    if (rc) return rc;
+    std::vector<char> spins(mc_state_bytes(h));
+    rc = mc_export_state(h, spins.data(), spins.size());
+    if (rc) return rc;
+    std::vector<double> ring(size_t(h->hp.ring_cap) * kRingWords);
+    std::vector<long long> prof(3 * size_t(h->hp.Lx));
+    CK(cudaMemcpy(ring.data(), h->hp.ring, ring.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(prof.data(), h->hp.profile, prof.size() * 8, cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(MC_ERR_IO, "cannot open %s for writing", path);
+    mc_desc d = h->desc;
+    d.stream = nullptr;
+    d.bond_mask = nullptr;
+    d.grain_id = nullptr;
+    d.grain_axis = nullptr;
+    const uint64_t nb = h->film_bonds.size(), ng = h->film_grain.size(), na = h->film_axes.size();
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&d, sizeof d, 1, f) == 1 &&
+              std::fwrite(&h->hp.R, sizeof h->hp.R, 1, f) == 1 && std::fwrite(&st, sizeof st, 1, f) == 1 &&
+              std::fwrite(&nb, 8, 1, f) == 1 && std::fwrite(&ng, 8, 1, f) == 1 && std::fwrite(&na, 8, 1, f) == 1;
+    if (ok && nb) ok = std::fwrite(h->film_bonds.data(), 1, nb, f) == nb;
+    if (ok && ng) ok = std::fwrite(h->film_grain.data(), 4, ng, f) == ng;
+    if (ok && na) ok = std::fwrite(h->film_axes.data(), 8, na, f) == na;
+    ok = ok && std::fwrite(ring.data(), 8, ring.size(), f) == ring.size() &&
+         std::fwrite(prof.data(), 8, prof.size(), f) == prof.size() &&
+         std::fwrite(spins.data(), 1, spins.size(), f) == spins.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MC_OK : fail(MC_ERR_IO, "write to %s failed", path);
+}
+
+MC_API int mc_load(const char* path, mc_handle* out) {
+    if (!path || !out) return fail(MC_ERR_ARG, "null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(MC_ERR_IO, "cannot open %s", path);
+    char magic[8];
+    mc_desc d;
+    double R[9];
+    LatState st;
+    uint64_t nb = 0, ng = 0, na = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&d, sizeof d, 1, f) == 1 && std::fread(R, sizeof R, 1, f) == 1 &&
+              std::fread(&st, sizeof st, 1, f) == 1 && std::fread(&nb, 8, 1, f) == 1 &&
+              std::fread(&ng, 8, 1, f) == 1 && std::fread(&na, 8, 1, f) == 1;
+    const uint64_t N = ok ? uint64_t(d.dims[0]) * d.dims[1] * d.dims[2] : 0;
+    ok = ok && (nb == 0 || nb == N) && (ng == 0 || ng == N) && na == 3 * uint64_t(ng ? d.n_grains : 0);
+    std::vector<uint8_t> bonds(ok ? nb : 0);
+    std::vector<int32_t> grain(ok ? ng : 0);
+    std::vector<double> axes(ok ? na : 0);
+    if (ok && nb) ok = std::fread(bonds.data(), 1, nb, f) == nb;
+    if (ok && ng) ok = std::fread(grain.data(), 4, ng, f) == ng;
+    if (ok && na) ok = std::fread(axes.data(), 8, na, f) == na;
+    if (!ok) { std::fclose(f); return fail(MC_ERR_IO, "%s is not a valid checkpoint", path); }
+    d.stream = nullptr;
+    d.bond_mask = nb ? bonds.data() : nullptr;
+    d.grain_id = ng ? grain.data() : nullptr;
+    d.grain_axis = ng ? axes.data() : nullptr;
+    if (!ng) d.n_grains = 0;
+    mc_handle h = nullptr;
+    int rc = create_lattice(&d, &h);
+    if (rc) { std::fclose(f); return rc; }
+    std::vector<double> ring(size_t(h->hp.ring_cap) * kRingWords);
+    std::vector<long long> prof(3 * size_t(h->hp.Lx));
+    std::vector<char> spins(mc_state_bytes(h));
+    ok = std::fread(ring.data(), 8, ring.size(), f) == ring.size() &&
+         std::fread(prof.data(), 8, prof.size(), f) == prof.size() &&
+         std::fread(spins.data(), 1, spins.size(), f) == spins.size();
+    std::fclose(f);
+    if (!ok) { mc_destroy(h); return fail(MC_ERR_IO, "%s is truncated", path); }
+    std::memcpy(h->hp.R, R, sizeof R);
+    rc = upload_params(h);
+    if (!rc && cudaMemcpy(&h->d_lat->st, &st, sizeof st, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (!rc && cudaMemcpy(h->hp.ring, ring.data(), ring.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (!rc && cudaMemcpy(h->hp.profile, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (!rc) rc = mc_import_state(h, spins.data(), spins.size());
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (rc) { mc_destroy(h); return rc == MC_ERR_CUDA ? fail(rc, "restoring %s failed", path) : rc; }
+    *out = h;
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// runtime.h -- host-side objects shared by the runtime, groups and server.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+#include "mc.h"
+#include "mc_internal.h"
+
+struct mc_lattice {
+    mc_desc desc;                 // copy (film pointers cleared)
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t owned_stream = nullptr;   // created by the library, destroyed with it
+    mcgb::LatParams hp;           // host copy of the device parameters
+    void* d_base = nullptr;       // the lattice's single device allocation
+    size_t bytes = 0;
+    mcgb::LatDev* d_lat = nullptr;
+    mcgb::LatDev** d_group_lats = nullptr;   // launch tables of the lattice alone
+    uint32_t* d_group_start = nullptr;
+    uint32_t* d_group_start_pair = nullptr;
+    const void* cone = nullptr;   // c(theta) table of the precision
+    std::vector<uint8_t> film_bonds;   // kept for checkpoints
+    std::vector<int32_t> film_grain;
+    std::vector<double> film_axes;
+};
+
+namespace mcgb {
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int create_lattice(const mc_desc* d, mc_handle* out);
+int validate_desc(const mc_desc* d);
+size_t lattice_bytes(const mc_desc* d);
+int upload_params(mc_lattice* h);
+void constraint_frame(double theta_deg, double phi_deg, double R[9]);
+const KernelSet& kernel_set(int precision);
+int read_state(mc_lattice* h, LatState* st);
+int enqueue_sweeps(const KernelSet& k, const GroupArgs& gs, uint32_t nb_site, const GroupArgs& gp,
+                   uint32_t nb_pair, const void* cone, int n, int measure, bool constrained, cudaStream_t s,
+                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
+
+}  // namespace mcgb

@@ -1,0 +1,454 @@
+"""Parity of the CUDA path (through the C ABI) with the serial FP64 oracle.
+
+FP64 mode: the spin trajectory, the cone angle and the per-sweep accepted
+counts are bit-identical to the oracle's, on every geometry (ragged tails,
+open, pinned and periodic axes, films, constrained pairs) and at the full
+batched workload; observables agree to 1e-9 relative.  FP32 mode: ensemble
+averages agree within |delta| <= 2e-3 and 3 sigma of the sampling error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_03517_gb300 as mc
+import workloads
+from _stats import blocking_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2103_03517_gb300 import build as libbuild
+    libbuild.build()
+    oracle.build()
+
+
+def make_pair(dims, prec=mc.MC_FP64, J=1.0, Ku=0.0, axis=(0, 0, 1.0), Kc=0.0, H=(0, 0, 0), T=1.0, seed=0,
+              bc=(0, 0, 0), theta0=30, adapt=1, ring=4096, spins=None, film=None):
+    kw = {}
+    if film is not None:
+        gid, mask, axes = film
+        kw = dict(bond_mask=mask, grain_id=gid, grain_axis=axes)
+    d = mc.make_desc(dims, J=J, K_u=Ku, axis=axis, K_c=Kc, H=H, T=T, seed=seed, precision=prec, boundary=bc,
+                     theta0_deg=theta0, adapt_in_measure=adapt, ring_capacity=ring, **kw)
+    h = mc.mc_create_ex(d)
+    o = oracle.Lattice(dims, J=J, Ku=Ku, axis=axis, Kc=Kc, H=H, T=T, seed=seed, bc=bc, theta0=theta0,
+                       adapt_in_measure=adapt, ring_cap=ring)
+    if film is not None:
+        o.set_bonds(film[1])
+        o.set_grains(film[0], film[2])
+    if spins is not None:
+        mc.mc_set_spins(h, spins)
+        o.set_spins(spins)
+    return h, o
+
+
+def assert_same_state(h, o, where=""):
+    N = o.N
+    g = mc.mc_get_spins(h, N)
+    r = o.spins()
+    diff = np.any(g != r, axis=1)
+    assert not diff.any(), f"{where}: {diff.sum()} sites differ, first {int(np.argmax(diff))}: {g[diff][0]} vs {r[diff][0]}"
+    theta, sweeps = mc.mc_get_theta(h)
+    assert theta == o.theta, f"{where}: theta {theta} vs {o.theta}"
+    assert sweeps == o.sweep_count
+
+
+def assert_same_samples(h, o, n):
+    gs = mc.mc_samples(h, n)
+    os_ = o.samples(n)
+    assert len(gs) == len(os_) == n
+    assert np.array_equal(gs["sweep"], os_[:, 0].astype(np.int64))
+    assert np.array_equal(gs["theta_deg"], os_[:, 1].astype(np.int32))
+    assert np.array_equal(gs["accepted"], os_[:, 2].astype(np.int64))
+    np.testing.assert_allclose(gs["m"], os_[:, 3:6], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(gs["e_parts"], os_[:, 6:10], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(gs["torque"], os_[:, 10:13], rtol=0, atol=1e-9)
+
+
+def assert_same_stats(h, o):
+    ob = mc.mc_measure(h)
+    s = o.stats()
+    n = s["n"]
+    assert ob.n_samples == n
+    if n == 0:
+        return
+    pairs = [(ob.ml, s["ml"]), (ob.ml2, s["ml2"]), (ob.ml4, s["ml4"]), (ob.e, s["e"]), (ob.e2, s["e2"])]
+    pairs += [(ob.m[a], s["m" + c]) for a, c in enumerate("xyz")]
+    pairs += [(ob.m2[a], s["m2" + c]) for a, c in enumerate("xyz")]
+    pairs += [(ob.m_abs[a], s["mabs" + c]) for a, c in enumerate("xyz")]
+    pairs += [(ob.torque[a], s["tq" + c]) for a, c in enumerate("xyz")]
+    pairs += [(ob.e_parts[k], s[f]) for k, f in enumerate(("e_ex", "e_u", "e_c", "e_z"))]
+    for g, r in pairs:
+        assert abs(g - r / n) <= 1e-9 * max(1.0, abs(r / n)), (g, r / n)
+
+
+# ------------------------------------------------------- FP64 bit-exactness
+def test_fp64_config1_bit_exact():
+    """16^3 periodic, K_u = 0.01 z, T = 0.5, seed 0, all +z: 1, 10 and
+    1000 + 1000 sweeps."""
+    c = workloads.config1()
+    h, o = make_pair(c.dims, Ku=c.Ku, T=c.T, seed=c.seed, ring=1000)
+    try:
+        mc.mc_sweep(h, 1)
+        o.sweep(1)
+        assert_same_state(h, o, "after 1 sweep")
+        mc.mc_sweep(h, 9)
+        o.sweep(9)
+        assert_same_state(h, o, "after 10 sweeps")
+        mc.mc_sweep(h, 990)
+        o.sweep(990)
+        mc.mc_sweep(h, 1000, measure=True)
+        o.sweep(1000, measure=True)
+        assert_same_state(h, o, "after 2000 sweeps")
+        assert_same_samples(h, o, 1000)
+        assert_same_stats(h, o)
+    finally:
+        mc.mc_destroy(h)
+
+
+GEOMETRIES = [
+    ((24, 18, 10), (0, 0, 0)),   # several blocks per colour, ragged tail
+    ((6, 3, 1), (1, 1, 1)),      # all open, odd sizes, a single plane
+    ((4, 2, 6), (2, 0, 1)),      # pinned x planes, open z
+    ((2, 1, 1), (1, 1, 1)),      # two spins
+    ((2, 2, 2), (0, 0, 0)),      # every neighbour doubled by the wrap
+    ((10, 6, 4), (0, 1, 0)),
+    ((34, 1, 1), (0, 1, 1)),     # a periodic chain
+]
+
+
+@pytest.mark.parametrize("dims,bc", GEOMETRIES)
+@pytest.mark.parametrize("measure_all", [False, True])
+def test_fp64_geometries_bit_exact(dims, bc, measure_all):
+    N = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(N)
+    axis = rng.standard_normal(3)
+    spins = workloads.random_spins(N, N + 1)
+    h, o = make_pair(dims, J=1.0, Ku=0.3, axis=axis, Kc=0.2, H=(0.1, -0.2, 0.15), T=0.8, seed=N * 7 + 1, bc=bc,
+                     spins=spins, ring=64)
+    try:
+        mc.mc_sweep(h, 7, measure=measure_all)
+        o.sweep(7, measure=measure_all)
+        assert_same_state(h, o, f"{dims} {bc}")
+        mc.mc_sweep(h, 23, measure=True)
+        o.sweep(23, measure=True)
+        assert_same_state(h, o, f"{dims} {bc}")
+        assert_same_samples(h, o, 23)
+        assert_same_stats(h, o)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_fp64_film_bit_exact():
+    film = workloads.voronoi_film(32, 32, 4, 8.0, seed=3)
+    h, o = make_pair((32, 32, 4), J=1.0, Ku=0.02, T=0.6, seed=11, bc=(0, 0, 1), film=film, ring=64)
+    try:
+        mc.mc_sweep(h, 10)
+        o.sweep(10)
+        mc.mc_sweep(h, 20, measure=True)
+        o.sweep(20, measure=True)
+        assert_same_state(h, o, "film")
+        assert_same_samples(h, o, 20)
+        assert_same_stats(h, o)
+    finally:
+        mc.mc_destroy(h)
+
+
+@pytest.mark.parametrize("dims,th,ph", [((16, 16, 16), 30.0, 20.0), ((12, 10, 8), 60.0, 45.0),
+                                        ((6, 3, 1), 90.0, 0.0), ((34, 6, 6), 0.0, 0.0)])
+def test_fp64_constrained_bit_exact(dims, th, ph):
+    N = dims[0] * dims[1] * dims[2]
+    bc = tuple(0 if d % 2 == 0 else 1 for d in dims)
+    R = oracle.constraint_frame(th, ph)
+    spins = workloads.uniform_spins(N, R[0])
+    h, o = make_pair(dims, J=1.0, Ku=0.05, Kc=0.02, H=(0.0, 0.05, 0.0), T=0.6, seed=5, bc=bc, spins=spins, ring=64)
+    try:
+        mc.mc_constrained_sweep(h, th, ph, 20)
+        o.constrained_sweep(th, ph, 20)
+        assert_same_state(h, o, "constrained")
+        mc.mc_constrained_sweep(h, th, ph, 30, measure=True)
+        o.constrained_sweep(th, ph, 30, measure=True)
+        assert_same_state(h, o, "constrained measured")
+        assert_same_samples(h, o, 30)
+        assert_same_stats(h, o)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_fp64_mixed_constrained_and_free_sweeps():
+    dims = (8, 8, 8)
+    h, o = make_pair(dims, Ku=0.05, T=0.9, seed=21, ring=64)
+    try:
+        for k in range(3):
+            mc.mc_sweep(h, 5, measure=k == 2)
+            o.sweep(5, measure=k == 2)
+            mc.mc_constrained_sweep(h, 10.0 * k, 5.0, 5, measure=k == 1)
+            o.constrained_sweep(10.0 * k, 5.0, 5, measure=k == 1)
+        assert_same_state(h, o, "mixed")
+        assert_same_stats(h, o)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_fp64_temperature_and_field_changes():
+    dims = (8, 6, 4)
+    h, o = make_pair(dims, Ku=0.05, T=0.9, seed=2, ring=64)
+    try:
+        mc.mc_sweep(h, 5)
+        o.sweep(5)
+        mc.mc_set_temperature(h, 0.3)
+        o.set_temperature(0.3)
+        mc.mc_sweep(h, 5)
+        o.sweep(5)
+        assert_same_state(h, o, "after T change")
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_fp64_wall_profile():
+    """Slice-averaged profile (Sec. 3 domain-wall profile) of a pinned wall:
+    three samples at different times equal the mean of the oracle's slice
+    averages of the same (bit-identical) states."""
+    dims = (32, 8, 8)
+    h, o = make_pair(dims, Ku=0.05, T=0.4, seed=9, bc=(2, 0, 0), spins=workloads.wall_spins(dims))
+    try:
+        ref = []
+        for k in range(3):
+            mc.mc_sweep(h, 10)
+            o.sweep(10)
+            mc.mc_profile_sample(h)
+            S = o.spins().reshape(dims[2], dims[1], dims[0], 3)
+            ref.append(S.mean(axis=(0, 1)))
+        assert_same_state(h, o, "wall")
+        ref = np.mean(ref, axis=0)
+        for a in range(3):
+            np.testing.assert_allclose(mc.mc_profile(h, a, dims[0]), ref[:, a], rtol=0, atol=1e-8)
+        prof = mc.mc_profile(h, 2, dims[0])
+        assert prof[0] == pytest.approx(1.0) and prof[-1] == pytest.approx(-1.0)
+        mc.mc_reset_stats(h)
+        assert np.all(mc.mc_profile(h, 2, dims[0]) == 0.0)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_zero_sweeps_is_a_no_op():
+    h, o = make_pair((4, 4, 4), T=0.5)
+    try:
+        mc.mc_sweep(h, 0)
+        mc.mc_constrained_sweep(h, 0.0, 0.0, 0)
+        assert_same_state(h, o, "no-op")
+        assert mc.mc_measure(h).n_samples == 0
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_constraint_violation_reported():
+    dims = (8, 8, 8)
+    h = mc.mc_create_ex(mc.make_desc(dims, precision=mc.MC_FP64, init_dir=(0, 0, -1.0)))
+    try:
+        mc.mc_constrained_sweep(h, 0.0, 0.0, 2)  # M_L = -N <= 0
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_sync(h)
+        assert e.value.code == mc.MC_ERR_CONSTRAINT
+    finally:
+        mc.mc_destroy(h)
+
+
+# ---------------------------------------------------------------- batching
+@pytest.mark.parametrize("prec", [mc.MC_FP64, mc.MC_FP32])
+def test_group_equals_alone_bitwise(prec):
+    specs = [((16, 16, 16), 0.5, 1), ((8, 8, 6), 1.1, 2), ((32, 16, 16), 0.9, 3), ((6, 3, 1), 0.4, 4)]
+    def make(dims, T, seed):
+        bc = tuple(0 if d % 2 == 0 else 1 for d in dims)
+        return mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.01, T=T, seed=seed, precision=prec, boundary=bc,
+                                            ring_capacity=64))
+    grouped = [make(*s) for s in specs]
+    alone = [make(*s) for s in specs]
+    g = mc.mc_group_create(grouped)
+    try:
+        mc.mc_group_sweep(g, 37)
+        mc.mc_group_sweep(g, 21, measure=True)
+        mc.mc_group_sync(g)
+        for h in alone:
+            mc.mc_sweep(h, 37)
+            mc.mc_sweep(h, 21, measure=True)
+        for (dims, _, _), a, b in zip(specs, grouped, alone):
+            N = dims[0] * dims[1] * dims[2]
+            assert np.array_equal(mc.mc_get_spins(a, N), mc.mc_get_spins(b, N))
+            oa, ob = mc.mc_measure(a).asdict(), mc.mc_measure(b).asdict()
+            assert oa == ob
+    finally:
+        mc.mc_group_destroy(g)
+        for h in grouped + alone:
+            mc.mc_destroy(h)
+
+
+def test_group_constrained_equals_alone_bitwise():
+    specs = [((16, 16, 16), 0.5, 30.0, 0.0), ((12, 10, 8), 0.8, 60.0, 45.0)]
+    hs, al = [], []
+    for dims, T, th, ph in specs:
+        R = oracle.constraint_frame(th, ph)
+        for lst in (hs, al):
+            h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, T=T, seed=4, precision=mc.MC_FP64,
+                                             init_dir=tuple(R[0]), ring_capacity=64))
+            lst.append(h)
+    g = mc.mc_group_create(hs)
+    try:
+        mc.mc_group_constrained_sweep(g, [s[2] for s in specs], [s[3] for s in specs], 20, measure=True)
+        mc.mc_group_sync(g)
+        for h, s in zip(al, specs):
+            mc.mc_constrained_sweep(h, s[2], s[3], 20, measure=True)
+        for (dims, *_), a, b in zip(specs, hs, al):
+            N = dims[0] * dims[1] * dims[2]
+            assert np.array_equal(mc.mc_get_spins(a, N), mc.mc_get_spins(b, N))
+            assert mc.mc_measure(a).asdict() == mc.mc_measure(b).asdict()
+    finally:
+        mc.mc_group_destroy(g)
+        for h in hs + al:
+            mc.mc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [mc.MC_FP64, mc.MC_FP32])
+def test_checkpoint_resume_is_bit_exact(prec, tmp_path):
+    dims = (16, 12, 8)
+    d = mc.make_desc(dims, K_u=0.05, T=0.7, seed=13, precision=prec, ring_capacity=64)
+    a = mc.mc_create_ex(d)
+    b = mc.mc_create_ex(d)
+    try:
+        mc.mc_sweep(a, 60)
+        mc.mc_sweep(a, 40, measure=True)
+        mc.mc_sweep(b, 60)
+        mc.mc_sweep(b, 10, measure=True)
+        path = str(tmp_path / "ck.bin")
+        mc.mc_save(b, path)
+        c = mc.mc_load(path)
+        mc.mc_sweep(c, 30, measure=True)
+        N = dims[0] * dims[1] * dims[2]
+        assert np.array_equal(mc.mc_get_spins(a, N), mc.mc_get_spins(c, N))
+        assert mc.mc_measure(a).asdict() == mc.mc_measure(c).asdict()
+        mc.mc_destroy(c)
+    finally:
+        mc.mc_destroy(a)
+        mc.mc_destroy(b)
+
+
+# ------------------------------------------- full size, bench launch config
+def test_config2_full_size_fp64_two_sweeps_bit_exact():
+    """All 32 lattices of the batched m(T) workload (19,169,280 spins) in one
+    group, FP64: two sweeps agree with the oracle bit for bit."""
+    specs = workloads.config2()
+    hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP64,
+                                       ring_capacity=4)) for s in specs]
+    g = mc.mc_group_create(hs)
+    try:
+        mc.mc_group_sweep(g, 1)
+        mc.mc_group_sweep(g, 1, measure=True)
+        mc.mc_group_sync(g)
+        for s, h in zip(specs, hs):
+            o = oracle.Lattice(s.dims, Ku=s.Ku, T=s.T, seed=s.seed, ring_cap=4)
+            o.sweep(1)
+            o.sweep(1, measure=True)
+            assert_same_state(h, o, f"config2 L={s.dims[0]} T={s.T:.2f}")
+            assert_same_stats(h, o)
+    finally:
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+
+
+def test_config2_full_size_fp32_properties():
+    """The bench's FP32 group of 32 lattices: after 400 sweeps every spin is a
+    unit vector, cone angles settled with acceptance near one half, and the
+    coldest lattice obeys equipartition E/N = -3J - K_u + T (any size)."""
+    specs = workloads.config2()
+    hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, ring_capacity=256)) for s in specs]
+    g = mc.mc_group_create(hs)
+    try:
+        mc.mc_group_sweep(g, 200)
+        mc.mc_group_sweep(g, 200, measure=True)
+        mc.mc_group_sync(g)
+        for s, h in zip(specs, hs):
+            S = mc.mc_get_spins(h, s.N)
+            assert np.abs(np.linalg.norm(S, axis=1) - 1.0).max() < 2e-6
+            ob = mc.mc_measure(h)
+            samp = mc.mc_samples(h, 200)
+            acc = samp["accepted"] / s.N
+            if ob.theta_deg < 180:  # below the cap the cone angle holds acceptance at one half
+                assert 1 < ob.theta_deg and abs(acc.mean() - 0.5) < 0.05, (s.dims, s.T, acc.mean())
+            else:
+                assert acc.mean() > 0.45
+        cold = mc.mc_measure(hs[0])  # T = 0.05, 16^3
+        assert abs((cold.e + 3.01) / 0.05 - 1.0) < 0.05
+        big = mc.mc_measure(hs[3])   # T = 0.2, 128^3: harmonic spin waves
+        L = 128
+        k = 2 * np.pi * np.arange(L) / L
+        c = np.cos(k)
+        eps = (3 - c[:, None, None] - c[None, :, None] - c[None, None, :]).ravel()[1:]
+        W = (1 / (eps + 0.01)).sum() / L ** 3  # transverse modes gapped by K_u
+        ratio = (1 - big.ml) / (0.2 / 2 * W)
+        assert 1.0 < ratio < 1.12, ratio  # anharmonic correction ~ +0.3 T
+    finally:
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+
+
+# ------------------------------------------------------ FP32 ensembles
+def _oracle_series(dims, Ku, T, seed, n_eq, n_meas, constrained=None, Kc=0.0):
+    o = oracle.Lattice(dims, Ku=Ku, Kc=Kc, T=T, seed=seed, ring_cap=n_meas)
+    if constrained:
+        th, ph = constrained
+        R = oracle.constraint_frame(th, ph)
+        o.set_spins(workloads.uniform_spins(o.N, R[0]))
+        o.constrained_sweep(th, ph, n_eq)
+        o.constrained_sweep(th, ph, n_meas, measure=True)
+    else:
+        o.sweep(n_eq)
+        o.sweep(n_meas, measure=True)
+    return o.samples()
+
+
+@pytest.mark.parametrize("T", [0.5, 1.2])
+def test_fp32_ensemble_matches_oracle(T):
+    dims, Ku = (16, 16, 16), 0.01
+    n_eq, n_meas = 2000, 8000
+    h = mc.mc_create_ex(mc.make_desc(dims, K_u=Ku, T=T, seed=1, ring_capacity=n_meas))
+    try:
+        mc.mc_sweep(h, n_eq)
+        mc.mc_sweep(h, n_meas, measure=True)
+        g = mc.mc_samples(h, n_meas)
+    finally:
+        mc.mc_destroy(h)
+    r = _oracle_series(dims, Ku, T, 2, n_eq, n_meas)
+    gm = np.linalg.norm(g["m"], axis=1)
+    rm = np.linalg.norm(r[:, 3:6], axis=1)
+    ge, re_ = g["e_parts"].sum(axis=1), r[:, 6:10].sum(axis=1)
+    # magnetisation: |delta| <= 2e-3 and <= 3 sigma (blocking errors of both)
+    for a, b in ((gm, rm), (np.abs(g["m"][:, 2]), np.abs(r[:, 5]))):
+        sig = math.hypot(blocking_error(a), blocking_error(b))
+        d = abs(a.mean() - b.mean())
+        assert d <= 2e-3 and d <= 3 * sig, (T, a.mean(), b.mean(), sig)
+    sig = math.hypot(blocking_error(ge), blocking_error(re_))
+    assert abs(ge.mean() - re_.mean()) <= 3 * sig, (T, ge.mean(), re_.mean(), sig)
+
+
+def test_fp32_constrained_torque_matches_oracle():
+    dims, T, th = (16, 16, 16), 0.5, 45.0
+    n_eq, n_meas = 500, 3000
+    R = oracle.constraint_frame(th, 0.0)
+    h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, T=T, seed=3, init_dir=tuple(R[0]),
+                                     ring_capacity=n_meas))
+    try:
+        mc.mc_constrained_sweep(h, th, 0.0, n_eq)
+        mc.mc_constrained_sweep(h, th, 0.0, n_meas, measure=True)
+        g = mc.mc_samples(h, n_meas)
+    finally:
+        mc.mc_destroy(h)
+    r = _oracle_series(dims, 0.05, T, 4, n_eq, n_meas, constrained=(th, 0.0), Kc=0.02)
+    gt, rt = g["torque"][:, 1], r[:, 11]
+    sig = math.hypot(blocking_error(gt), blocking_error(rt))
+    assert abs(gt.mean() - rt.mean()) <= 3.5 * sig + 1e-6, (gt.mean(), rt.mean(), sig)
