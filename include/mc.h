@@ -231,9 +231,10 @@ MC_API int mc_group_sweep(mc_group_handle g, int n_sweeps, int measure);
 MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_deg,
                                       const double* phi_c_deg, int n_sweeps, int measure);
 
-/* Time the colour-pass kernels of the group: the next n_sweeps sweeps record
- * CUDA events around every colour-pass launch; *avg_ms receives the mean
- * duration of one launch and *launches the count.  Synchronises. */
+/* Time the colour passes of the group: the next n_sweeps sweeps of Table A1
+ * record CUDA events around every colour pass (the launches that update one
+ * colour of every lattice); *avg_ms receives the mean duration of one colour
+ * pass and *launches the number of passes timed.  Synchronises. */
 MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms,
                                 int* launches);
 

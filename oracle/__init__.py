@@ -139,6 +139,7 @@ class Lattice:
                  T=1.0, seed=0, bc=(0, 0, 0), theta0=30, adapt_in_measure=1, ring_cap=1):
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.ring_cap = max(1, int(ring_cap))
         d = np.array(self.dims, np.int32)
         b = np.array(bc, np.int32)
         ax = np.array(axis, np.float64)
@@ -224,7 +225,10 @@ class Lattice:
         lib().or_stats(self._h, _p(out, C.c_double))
         return dict(zip(STAT_FIELDS, out.tolist()))
 
-    def samples(self, max_n: int = 1 << 20) -> np.ndarray:
+    def samples(self, max_n: int | None = None) -> np.ndarray:
+        """The most recent min(max_n, kept) per-sweep samples, oldest first."""
+        if max_n is None:
+            max_n = self.ring_cap
         out = np.zeros((max_n, SAMPLE_WORDS))
         n = lib().or_samples(self._h, _p(out, C.c_double), max_n)
         return out[:n]

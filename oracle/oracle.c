@@ -448,8 +448,10 @@ OR_EXPORT void or_stats(const or_lattice* L, double* out) {
     for (int a = 0; a < 3; ++a) out[k++] = L->acc_tq2[a];
 }
 
+/* The most recent min(max, kept) samples, oldest first. */
 OR_EXPORT int64_t or_samples(const or_lattice* L, double* out, int64_t max) {
-    const int64_t n = L->ring_count < L->ring_cap ? L->ring_count : L->ring_cap;
+    int64_t n = L->ring_count < L->ring_cap ? L->ring_count : L->ring_cap;
+    if (n > max) n = max;
     const int64_t first = L->ring_count - n;
     int64_t k = 0;
     for (int64_t s = first; s < L->ring_count && k < max; ++s, ++k)

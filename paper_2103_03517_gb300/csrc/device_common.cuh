@@ -77,15 +77,4 @@ struct V3 {
 // Fixed-point conversion of a block partial sum (round to nearest).
 __device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * kFixScale); }
 
-// Locate the lattice that owns blockIdx.x in a batched launch.
-__device__ __forceinline__ int find_lattice(const GroupArgs& g) {
-    int lo = 0, hi = g.n - 1;
-    const uint32_t b = blockIdx.x;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&g.start[mid]) <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 }  // namespace mcgb

@@ -21,16 +21,10 @@ struct mc_group {
     int precision = 0;
     cudaStream_t stream = nullptr;
     void* d_mem = nullptr;
-    LatDev** d_lats = nullptr;
-    uint32_t* d_start_site = nullptr;
-    uint32_t* d_start_pair = nullptr;
-    uint32_t nb_site = 0, nb_pair = 0;
+    LaunchSet ls;
     const void* cone = nullptr;
     // captured graphs: [constrained][measure]
     cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-
-    GroupArgs site_args() const { return GroupArgs{d_lats, d_start_site, int(lats.size())}; }
-    GroupArgs pair_args() const { return GroupArgs{d_lats, d_start_pair, int(lats.size())}; }
 };
 
 static int group_graph(mc_group* g, bool constrained, int measure, cudaGraphExec_t* out) {
@@ -39,8 +33,8 @@ static int group_graph(mc_group* g, bool constrained, int measure, cudaGraphExec
         cudaGraph_t graph;
         cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        int rc = enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair,
-                                g->cone, kGraphSweeps, measure, constrained, g->stream, nullptr);
+        int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, kGraphSweeps, measure, constrained,
+                                g->stream, nullptr);
         e = cudaStreamEndCapture(g->stream, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -64,8 +58,8 @@ static int group_run(mc_group* g, int n, int measure, bool constrained) {
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
         }
     }
-    return enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair, g->cone,
-                          n - reps * kGraphSweeps, measure, constrained, g->stream, nullptr);
+    return enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n - reps * kGraphSweeps, measure, constrained,
+                          g->stream, nullptr);
 }
 
 extern "C" {
@@ -84,23 +78,41 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
             return fail(MC_ERR_ARG, "group members must share device and precision");
         }
     }
-    std::vector<LatDev*> ptrs(n);
-    std::vector<uint32_t> ss(n + 1), sp(n + 1);
+    // launch tables: [fast lattices | general lattices | all lattices], each
+    // with its own tile starts, plus the pair tile starts of all lattices
+    std::vector<LatDev*> fast, general, all(n);
+    std::vector<uint32_t> sf(1, 0), sg(1, 0), sa(n + 1, 0), sp(n + 1, 0);
     for (int i = 0; i < n; ++i) {
-        ptrs[i] = lattices[i]->d_lat;
-        ss[i + 1] = ss[i] + lattices[i]->hp.nblocks_site;
-        sp[i + 1] = sp[i] + lattices[i]->hp.nblocks_pair;
+        const LatParams& hp = lattices[i]->hp;
+        all[i] = lattices[i]->d_lat;
+        sa[i + 1] = sa[i] + hp.nblocks_site;
+        sp[i + 1] = sp[i] + hp.nblocks_pair;
+        if (hp.row_fast) { fast.push_back(all[i]); sf.push_back(sf.back() + hp.nblocks_site); }
+        else { general.push_back(all[i]); sg.push_back(sg.back() + hp.nblocks_site); }
     }
-    g->nb_site = ss[n];
-    g->nb_pair = sp[n];
     cudaSetDevice(g->device);
-    const size_t b_ptrs = (sizeof(LatDev*) * n + 255) & ~size_t(255);
-    const size_t b_idx = (sizeof(uint32_t) * (n + 1) + 255) & ~size_t(255);
-    cudaError_t e = cudaMalloc(&g->d_mem, b_ptrs + 2 * b_idx);
+    const size_t n_ptr = size_t(2 * n), n_idx = size_t(sf.size() + sg.size() + sa.size() + sp.size());
+    cudaError_t e = cudaMalloc(&g->d_mem, n_ptr * sizeof(LatDev*) + n_idx * sizeof(uint32_t));
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(group)"); }
-    g->d_lats = static_cast<LatDev**>(g->d_mem);
-    g->d_start_site = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptrs);
-    g->d_start_pair = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptrs + b_idx);
+    std::vector<char> host(n_ptr * sizeof(LatDev*) + n_idx * sizeof(uint32_t));
+    LatDev** hp_ = reinterpret_cast<LatDev**>(host.data());
+    std::copy(fast.begin(), fast.end(), hp_);
+    std::copy(general.begin(), general.end(), hp_ + fast.size());
+    std::copy(all.begin(), all.end(), hp_ + n);
+    uint32_t* hi = reinterpret_cast<uint32_t*>(host.data() + n_ptr * sizeof(LatDev*));
+    size_t off = 0;
+    auto put = [&](const std::vector<uint32_t>& v) { std::copy(v.begin(), v.end(), hi + off); off += v.size(); return off - v.size(); };
+    const size_t of = put(sf), og = put(sg), oa = put(sa), op = put(sp);
+    LatDev** dptr = static_cast<LatDev**>(g->d_mem);
+    uint32_t* didx = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + n_ptr * sizeof(LatDev*));
+    g->ls.fast = GroupArgs{dptr, didx + of, int(fast.size())};
+    g->ls.general = GroupArgs{dptr + fast.size(), didx + og, int(general.size())};
+    g->ls.all = GroupArgs{dptr + n, didx + oa, n};
+    g->ls.pairs = GroupArgs{dptr + n, didx + op, n};
+    g->ls.nt_fast = sf.back();
+    g->ls.nt_general = sg.back();
+    g->ls.nt_all = sa.back();
+    g->ls.nt_pairs = sp.back();
     // the members' queued work must be complete before the group uses them;
     // from now on every member runs on the group stream, so that calls on a
     // member order after the group's work
@@ -109,10 +121,7 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         g->member_streams.push_back(lattices[i]->stream);
         lattices[i]->stream = g->stream;
     }
-    bool ok = cudaMemcpy(g->d_lats, ptrs.data(), sizeof(LatDev*) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(g->d_start_site, ss.data(), 4 * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(g->d_start_pair, sp.data(), 4 * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) {
+    if (cudaMemcpy(g->d_mem, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         for (int i = 0; i < n; ++i) lattices[i]->stream = g->member_streams[i];
         cudaFree(g->d_mem);
         delete g;
@@ -161,8 +170,7 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
     if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(g->device);
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    int rc = enqueue_sweeps(kernel_set(g->precision), g->site_args(), g->nb_site, g->pair_args(), g->nb_pair,
-                            g->cone, n_sweeps, measure ? 1 : 0, false, g->stream, &ev);
+    int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n_sweeps, measure ? 1 : 0, false, g->stream, &ev);
     cudaError_t e = cudaStreamSynchronize(g->stream);
     double total = 0.0;
     for (auto& pr : ev) {

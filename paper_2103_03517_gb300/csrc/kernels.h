@@ -8,19 +8,28 @@
 namespace mcgb {
 
 struct KernelSet {
-    // Table A1 colour pass over the lattices of g (nblocks = grid size).
-    void (*colour_pass)(const GroupArgs& g, uint32_t nblocks, const void* cone, int colour, int measure,
+    // Table A1 colour pass over the lattices of g (ntiles = warp tiles of the
+    // launch; the launcher sizes a persistent grid from the occupancy).
+    // fast: every lattice of g is row_fast.
+    void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, bool fast,
                         cudaStream_t s);
-    // Table A2 pair pass; finalize != 0 closes the sweep in the last block.
-    void (*pair_pass)(const GroupArgs& g, uint32_t nblocks, const void* cone, int colour, int finalize,
+    // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
+    void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
                       int measure, cudaStream_t s);
-    // Exact M_L of every lattice of g (site-pass grid).
-    void (*mlong)(const GroupArgs& g, uint32_t nblocks, cudaStream_t s);
-    // Standalone sample + end of sweep (site-pass grid).
-    void (*measure)(const GroupArgs& g, uint32_t nblocks, cudaStream_t s);
+    // Exact M_L of every lattice of g (site tiles).
+    void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
+    // Standalone sample + end of sweep (site tiles).
+    void (*measure)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Slice sums for the profile of one lattice.
     void (*profile)(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s);
     const char* name;
+};
+
+// Launch tables of a set of lattices: site tiles of the row_fast lattices,
+// of the other lattices, of all lattices, and pair tiles of all lattices.
+struct LaunchSet {
+    GroupArgs fast, general, all, pairs;
+    uint32_t nt_fast = 0, nt_general = 0, nt_all = 0, nt_pairs = 0;
 };
 
 const KernelSet& kernels_f64();

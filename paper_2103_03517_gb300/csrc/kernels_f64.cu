@@ -8,23 +8,60 @@ namespace mcgb {
 namespace {
 
 using R = double;
+constexpr int MINB = 1;  // minimum resident blocks per SM of the colour pass
+constexpr int V = kSitesPerThreadF64;
 
-void colour_pass(const GroupArgs& g, uint32_t nblocks, const void* cone, int colour, int measure,
+// Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
+// the process is assumed representative; computed once per kernel).
+template <typename K>
+uint32_t resident_blocks(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    return uint32_t(sms) * uint32_t(per_sm);
+}
+
+// blocks for ntiles warp tiles: one warp per tile at most, capped at residency
+uint32_t grid_for(uint32_t ntiles, uint32_t cap) {
+    const uint32_t want = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
+    return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
+template <bool FAST, bool MEASURE>
+void colour_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(colour_pass_kernel<R, V, MINB, FAST, MEASURE>);
+    colour_pass_kernel<R, V, MINB, FAST, MEASURE><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
+}
+
+void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, bool fast,
                  cudaStream_t s) {
-    colour_pass_kernel<R><<<nblocks, kBlock, 0, s>>>(g, static_cast<const R*>(cone), colour, measure);
+    const R* c = static_cast<const R*>(cone);
+    if (fast) {
+        if (measure) colour_pass_t<true, true>(g, ntiles, c, colour, s);
+        else colour_pass_t<true, false>(g, ntiles, c, colour, s);
+    } else {
+        if (measure) colour_pass_t<false, true>(g, ntiles, c, colour, s);
+        else colour_pass_t<false, false>(g, ntiles, c, colour, s);
+    }
 }
 
-void pair_pass(const GroupArgs& g, uint32_t nblocks, const void* cone, int colour, int finalize, int measure,
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
                cudaStream_t s) {
-    pair_pass_kernel<R><<<nblocks, kBlock, 0, s>>>(g, static_cast<const R*>(cone), colour, finalize, measure);
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R>);
+    pair_pass_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, static_cast<const R*>(cone), colour,
+                                                                 finalize, measure);
 }
 
-void mlong(const GroupArgs& g, uint32_t nblocks, cudaStream_t s) {
-    mlong_kernel<R><<<nblocks, kBlock, 0, s>>>(g);
+void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(mlong_kernel<R, V>);
+    mlong_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
 }
 
-void measure(const GroupArgs& g, uint32_t nblocks, cudaStream_t s) {
-    measure_kernel<R><<<nblocks, kBlock, 0, s>>>(g);
+void measure(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(measure_kernel<R, V>);
+    measure_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
 }
 
 void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {

@@ -16,10 +16,19 @@
 namespace mcgb {
 
 constexpr int kBlock = 256;          // threads per block of every pass kernel
+// Sites per thread per tile of the site kernels (a site tile is kBlock * V
+// colour indices of one lattice; a pair tile is kBlock pairs).
+#ifndef MC_V_F32
+#define MC_V_F32 2
+#endif
+constexpr int kSitesPerThreadF32 = MC_V_F32;   // a warp tile is 32 * V colour indices
+constexpr int kSitesPerThreadF64 = 1;
+constexpr int sites_per_thread(int precision) { return precision == 1 ? kSitesPerThreadF64 : kSitesPerThreadF32; }
 constexpr int kNumSums = 12;         // per-sample lattice sums, see kSum*
 constexpr int kRingWords = 14;       // doubles per ring sample
 constexpr int kMomentWords = 26;     // running sums of per-sample observables
-constexpr double kFixScale = 268435456.0;   // 2^28: fixed point of the sums
+constexpr double kFixScale = 268435456.0;   // 2^28: fixed point of the FP64 sums
+constexpr double kFixScaleF32 = 4194304.0;  // 2^22: fixed point of the FP32 sums
 
 // Per-sample lattice sums (dimensionless, each bounded by 3 N):
 enum {
@@ -67,8 +76,10 @@ struct LatParams {
     int adapt_in_measure;
     uint32_t key0, key1;
     FastDiv div_lh, div_ly;
-    uint32_t nblocks_site;  // blocks of a site pass of this lattice
-    uint32_t nblocks_pair;  // blocks of a pair pass of this lattice
+    uint32_t nblocks_site;  // site tiles of this lattice
+    uint32_t nblocks_pair;  // pair tiles of this lattice
+    int row_fast;           // all axes periodic, no film tables, Lh % 32 == 0:
+                            // every 32-lane segment of a tile lies in one row
     void* spins;
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null
@@ -102,8 +113,7 @@ struct LatDev {
     LatState st;
 };
 
-// Arguments of a batched launch: lattice l owns blocks
-// [start[l], start[l+1]) of the grid.
+// Arguments of a batched launch: lattice l owns tiles [start[l], start[l+1]).
 struct GroupArgs {
     LatDev* const* lats;
     const uint32_t* start;

@@ -157,41 +157,47 @@ __device__ __forceinline__ R delta_e(const Par<R>& par, V3<R> S, V3<R> Sn, V3<R>
 // solid angle on the cap of half-angle theta about S (c = 1 - cos theta),
 // by the disk method generalised to a cap and the orthonormal basis of
 // Duff et al. (JCGT 2017); attempt a uses the words (w0, w1) of draw a, at
-// most 16 attempts; P = w2 of draw 0.
+// most 16 attempts; P = w2 of draw 0.  Split in three steps so that a warp
+// can draw the words of several sites before any data-dependent branch.
 template <typename R>
-__device__ __forceinline__ bool cone_trial(V3<R> S, R c, uint32_t idx, uint32_t sweep, uint32_t tag,
-                                           uint32_t k0, uint32_t k1, V3<R>& out, R& P) {
-    uint4 w = philox(make_uint4(idx, sweep, tag, 0u), k0, k1);
-    R u1, u2;
+__device__ __forceinline__ void disk_point(uint4 w, R& u1, R& u2) {
     if constexpr (kIsF64<R>) {
-        P = (double)w.z * 0x1p-32;
         u1 = (double)w.x * 0x1p-31 - 1.0;
         u2 = (double)w.y * 0x1p-31 - 1.0;
     } else {
-        P = (float)(w.z >> 8) * 0x1p-24f;
         u1 = (float)(w.x >> 8) * 0x1p-23f - 1.0f;
         u2 = (float)(w.y >> 8) * 0x1p-23f - 1.0f;
     }
-    R s = u1 * u1 + u2 * u2;
+}
+
+template <typename R>
+__device__ __forceinline__ R uniform_p(uint4 w) {
+    if constexpr (kIsF64<R>) return (double)w.z * 0x1p-32;
+    else return (float)(w.z >> 8) * 0x1p-24f;
+}
+
+// Redraw rejected disk points (s >= 1) with draws 1..15; false if all fail.
+template <typename R>
+__device__ __forceinline__ bool disk_retry(R& u1, R& u2, R& s, uint32_t idx, uint32_t sweep, uint32_t tag,
+                                           uint32_t k0, uint32_t k1) {
     uint32_t draw = 0;
     while (!(s < R(1))) {
         if (++draw == 16u) return false;
-        w = philox(make_uint4(idx, sweep, tag, draw), k0, k1);
-        if constexpr (kIsF64<R>) {
-            u1 = (double)w.x * 0x1p-31 - 1.0;
-            u2 = (double)w.y * 0x1p-31 - 1.0;
-        } else {
-            u1 = (float)(w.x >> 8) * 0x1p-23f - 1.0f;
-            u2 = (float)(w.y >> 8) * 0x1p-23f - 1.0f;
-        }
+        const uint4 w = philox(make_uint4(idx, sweep, tag, draw), k0, k1);
+        disk_point<R>(w, u1, u2);
         s = u1 * u1 + u2 * u2;
     }
+    return true;
+}
+
+// Map the disk point to the cap about S and renormalise.
+template <typename R>
+__device__ __forceinline__ V3<R> cap_point(V3<R> S, R c, R u1, R u2, R s) {
     const R sc = s * c;
     const R zp = R(1) - sc;
     const R r = sqrt(c * (R(2) - sc));
     const R xp = u1 * r;
     const R yp = u2 * r;
-    // basis {b1, b2, S} (Duff et al. 2017)
     const R sgn = copysign(R(1), S.z);
     const R a = R(-1) / (sgn + S.z);
     const R b = S.x * S.y * a;
@@ -202,11 +208,23 @@ __device__ __forceinline__ bool cone_trial(V3<R> S, R c, uint32_t idx, uint32_t 
     const R nz = xp * b1z + yp * b2z + zp * S.z;
     if constexpr (kIsF64<R>) {
         const double norm = sqrt(nx * nx + ny * ny + nz * nz);
-        out = V3<R>{nx / norm, ny / norm, nz / norm};
+        return V3<R>{nx / norm, ny / norm, nz / norm};
     } else {
         const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-        out = V3<R>{nx * inv, ny * inv, nz * inv};
+        return V3<R>{nx * inv, ny * inv, nz * inv};
     }
+}
+
+template <typename R>
+__device__ __forceinline__ bool cone_trial(V3<R> S, R c, uint32_t idx, uint32_t sweep, uint32_t tag,
+                                           uint32_t k0, uint32_t k1, V3<R>& out, R& P) {
+    const uint4 w = philox(make_uint4(idx, sweep, tag, 0u), k0, k1);
+    P = uniform_p<R>(w);
+    R u1, u2;
+    disk_point<R>(w, u1, u2);
+    R s = u1 * u1 + u2 * u2;
+    if (!disk_retry(u1, u2, s, idx, sweep, tag, k0, k1)) return false;
+    out = cap_point(S, c, u1, u2, s);
     return true;
 }
 
@@ -245,25 +263,25 @@ __device__ __forceinline__ void add_site(Sums<R>& s, V3<R> S, V3<R> e) {
     s.v[kSumTcz] += S.x * c1 - S.y * c0;
 }
 
+// ------------------------------------------------------------------------
+// Measurement sums of one warp tile, reduced across the warp in a fixed
+// butterfly order and turned into fixed point on lane i for sum i: FP64 at
+// 2^28 (int64), FP32 at 2^22 (an int32 holds a warp tile's sum), so that no
+// FP64 instruction runs on the FP32 path.  Tiles are aligned to the lattice,
+// so the integer totals do not depend on the batch a lattice runs in.
+// ------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void block_reduce_sums(Sums<R>& s, LatState& st) {
-    __shared__ double red[kBlock / 32][kNumSums];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
+    R mine = R(0);
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) {
         R v = s.v[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][i] = double(v);
+        if (lane == i) mine = v;
     }
-    __syncthreads();
-    if (threadIdx.x < kNumSums) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) t += red[w][threadIdx.x];
-        atomicAdd(reinterpret_cast<unsigned long long*>(&st.sums[threadIdx.x]),
-                  static_cast<unsigned long long>(to_fix(t)));
-    }
+    if constexpr (kIsF64<R>) return __double2ll_rn(mine * kFixScale);
+    else return (long long)__float2int_rn(mine * float(kFixScaleF32));
 }
 
 // ------------------------------------------------------------------------
@@ -286,7 +304,7 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
             // two's complement fixed point: reinterpret the 64-bit word as signed
             const long long raw =
                 (long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[i]), 0ull);
-            v[i] = double(raw) / kFixScale;
+            v[i] = double(raw) / (p.precision == 1 ? kFixScale : kFixScaleF32);
         }
         const double N = double(p.N);
         const double m[3] = {v[kSumMx] / N, v[kSumMy] / N, v[kSumMz] / N};
@@ -329,145 +347,303 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
     st.sweep += 1;
 }
 
-// Count a finished block; the last block of the pass runs `last`.
+// ------------------------------------------------------------------------
+// Work split of every batched kernel: the launch holds as many blocks as are
+// resident on the GPU at once, and each warp owns one contiguous chunk of
+// warp tiles (a warp tile = 32 * V colour indices, or 32 pairs, of one
+// lattice; lattice l owns tiles [g.start[l], g.start[l+1])).  A warp walks
+// its chunk lattice by lattice and publishes each lattice's counts once per
+// run of tiles; no block-wide barrier is involved.
+// ------------------------------------------------------------------------
+struct WarpChunk {
+    uint32_t begin, end;
+    int lane;
+};
+
+__device__ __forceinline__ WarpChunk warp_chunk(uint32_t ntiles) {
+    const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
+    const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
+    const uint32_t chunk = (ntiles + nwarps - 1) / nwarps;
+    WarpChunk c;
+    c.begin = min(w * chunk, ntiles);
+    c.end = min(c.begin + chunk, ntiles);
+    c.lane = int(threadIdx.x & 31);
+    return c;
+}
+
+__device__ __forceinline__ int lattice_of_tile(const GroupArgs& g, uint32_t tile) {
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.start[mid]) <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Publish one warp's run of `tiles` tiles of lattice L: accepted moves,
+// fixed-point sums (lane i holds sum i), then the tile count; the warp that
+// completes the lattice's pass runs `last` on lane 0.
 template <typename F>
-__device__ __forceinline__ void block_done(LatState& st, int slot, uint32_t nblocks, F&& last) {
+__device__ __forceinline__ void publish(LatState& st, int lane, unsigned nacc, bool with_sums, long long fix, int slot,
+                                        uint32_t tiles, uint32_t ntiles_lattice, F&& last) {
+    nacc = __reduce_add_sync(0xffffffffu, nacc);
+    if (lane == 0 && nacc) atomicAdd(&st.acc, (unsigned long long)nacc);
+    if (with_sums && lane < kNumSums && fix)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&st.sums[lane]), static_cast<unsigned long long>(fix));
     __threadfence();
-    const unsigned prev = atomicAdd(&st.done[slot], 1u);
-    if (prev == nblocks - 1) {
-        __threadfence();
-        st.done[slot] = 0;
-        last();
-    }
-}
-
-// ------------------------------------------------------------------------
-// Colour pass of Table A1 (one thread per site of the colour), batched over
-// the lattices of a group.  colour 1 with measure != 0 also takes the
-// sample: each black thread adds its own site, the red site with the same
-// colour index, and its bonds to the six red neighbours (every bond joins
-// a red and a black site, so each bond is counted once).
-// ------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kBlock) colour_pass_kernel(GroupArgs g, const R* __restrict__ cone, int colour,
-                                                             int measure) {
-    __shared__ int s_lat;
-    __shared__ unsigned s_acc;
-    if (threadIdx.x == 0) { s_lat = find_lattice(g); s_acc = 0; }
-    __syncthreads();
-    const int l = s_lat;
-    LatDev* L = g.lats[l];
-    const LatParams& p = L->p;
-    LatState& st = L->st;
-    const Par<R> par = load_par<R>(p);
-    const int theta = st.theta;
-    const uint32_t sweep = st.sweep;
-    const R c = cone[theta];
-    R* __restrict__ s = static_cast<R*>(p.spins);
-    const uint32_t q = (blockIdx.x - g.start[l]) * kBlock + threadIdx.x;
-    const bool active = q < p.Nc;
-    const int other = colour ^ 1;
-    bool accepted = false;
-    Sums<R> sums;
-    if (measure) for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);
-    if (active) {
-        const Geo geo = geometry(p, colour, q);
-        const V3<R> S = load_spin(s, p.stride, colour, q);
-        uint32_t nq[6];
-        const uint32_t present = neighbours(p, geo, colour, nq);
-        const V3<R> e = easy_axis(p, par, colour, q);
-        V3<R> Sf = S;
-        const bool movable = !pinned(p, geo);
-        V3<R> h{R(0), R(0), R(0)};
-        if (movable || measure) h = neighbour_sum(s, p.stride, other, nq, present);
-        if (movable) {
-            V3<R> Sn;
-            R P;
-            if (cone_trial(S, c, geo.site, sweep, tag_of(colour, kPurposeMove), p.key0, p.key1, Sn, P)) {
-                const R dE = delta_e(par, S, Sn, h, e);
-                if (metropolis(dE, par.T, P)) {
-                    store_spin(s, p.stride, colour, q, Sn);
-                    Sf = Sn;
-                    accepted = true;
-                }
-            }
-        }
-        if (measure) {
-            add_site(sums, Sf, e);
-            sums.v[kSumEx] += Sf.x * h.x + Sf.y * h.y + Sf.z * h.z;
-            const V3<R> Sr = load_spin(s, p.stride, other, q);
-            add_site(sums, Sr, easy_axis(p, par, other, q));
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned prev = atomicAdd(&st.done[slot], tiles);
+        if (prev + tiles == ntiles_lattice) {
+            __threadfence();
+            st.done[slot] = 0;
+            last();
         }
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, accepted);
-    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&s_acc, unsigned(__popc(ballot)));
-    if (measure) block_reduce_sums(sums, st);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_acc) atomicAdd(&st.acc, (unsigned long long)s_acc);
-        block_done(st, colour, p.nblocks_site, [&] {
-            if (colour == 1) finalize_sweep(p, st, measure);
-        });
-    }
-}
-
-// ------------------------------------------------------------------------
-// Exact M_L = sum_i S_i . e_C (Table A2) as fixed point: FP64 terms t give
-// q = trunc(t 2^52) split as hi 2^26 + lo; FP32 terms give q = trunc(t 2^40)
-// split as hi 2^14 + lo.  Integer sums, so the result is independent of
-// the order of the reduction.
-// ------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g) {
-    __shared__ int s_lat;
-    __shared__ long long s_hi[kBlock / 32], s_lo[kBlock / 32];
-    if (threadIdx.x == 0) s_lat = find_lattice(g);
-    __syncthreads();
-    const int l = s_lat;
-    LatDev* L = g.lats[l];
-    const LatParams& p = L->p;
-    const R* s = static_cast<const R*>(p.spins);
-    const uint32_t q = (blockIdx.x - g.start[l]) * kBlock + threadIdx.x;
-    long long hi = 0, lo = 0;
-    if (q < p.Nc) {
-        R e1[3];
-        if constexpr (kIsF64<R>) { e1[0] = p.R[0]; e1[1] = p.R[1]; e1[2] = p.R[2]; }
-        else { e1[0] = p.fR[0]; e1[1] = p.fR[1]; e1[2] = p.fR[2]; }
-        for (int colour = 0; colour < 2; ++colour) {
-            const V3<R> S = load_spin(s, p.stride, colour, q);
-            const R t = e1[0] * S.x + e1[1] * S.y + e1[2] * S.z;
-            if constexpr (kIsF64<R>) {
-                const long long v = (long long)(t * 0x1p52);
-                const long long h = v >> 26;
-                hi += h;
-                lo += v - h * (1ll << 26);
-            } else {
-                const long long v = __float2ll_rz(t * 0x1p40f);
-                const long long h = v >> 14;
-                hi += h;
-                lo += v - h * (1ll << 14);
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        hi += __shfl_xor_sync(0xffffffffu, hi, o);
-        lo += __shfl_xor_sync(0xffffffffu, lo, o);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { s_hi[warp] = hi; s_lo[warp] = lo; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long th = 0, tl = 0;
-        for (int w = 0; w < kBlock / 32; ++w) { th += s_hi[w]; tl += s_lo[w]; }
-        atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.ml_hi), static_cast<unsigned long long>(th));
-        atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.ml_lo), static_cast<unsigned long long>(tl));
-    }
+    __syncwarp();
 }
 
 template <typename R>
 __device__ __forceinline__ double mlong_value(long long hi, long long lo) {
     if constexpr (kIsF64<R>) return (double)hi * 0x1p-26 + (double)lo * 0x1p-52;
-    else return (double)hi * 0x1p-26 + (double)lo * 0x1p-40;
+    else return (double)hi * 0x1p-30;
+}
+
+// ------------------------------------------------------------------------
+// Loads of one warp tile of a uniform periodic lattice whose rows hold a
+// multiple of 32 sites per colour (row_fast): the tile is V segments of 32
+// consecutive colour indices, each inside one row (y, z) of the colour.  Per
+// segment the row, its x parity and the -y/+y/-z/+z row offsets are uniform;
+// every lane loads its own spin and the other colour's spin at the same k,
+// which is one of its two x neighbours and, by a warp shuffle, the other x
+// neighbour of the adjacent lane (an edge lane loads one value across the
+// segment boundary, wrapping the row).  The other-colour spin at the same k
+// is also the red site a black site samples.  The neighbour sum keeps the
+// order -x, +x, -y, +y, -z, +z of the general path.
+// ------------------------------------------------------------------------
+template <typename R, int V>
+__device__ __forceinline__ void row_segments(const LatParams& p, const Par<R>& par, const R* s, int colour,
+                                             uint32_t tile_q0, int lane, V3<R> S[V], V3<R> h[V], V3<R> e[V],
+                                             V3<R> O[V], uint32_t site[V]) {
+    const int other = colour ^ 1;
+    const uint32_t stride = p.stride;
+    const R* own = s + size_t(3 * colour) * stride;
+    const R* oth = s + size_t(3 * other) * stride;
+    const uint32_t Lh = uint32_t(p.Lh), plane = Lh * uint32_t(p.Ly);
+    V3<R> E[V], Ym[V], Yp[V], Zm[V], Zp[V];
+    int xoff[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t qs = tile_q0 + uint32_t(32 * v);  // segment start (uniform)
+        const uint32_t row = fast_div(qs, p.div_lh);
+        const uint32_t k0 = qs - row * Lh;
+        const uint32_t z = fast_div(row, p.div_ly);
+        const uint32_t y = row - z * uint32_t(p.Ly);
+        xoff[v] = int((y + z + uint32_t(colour)) & 1u);
+        const uint32_t q = qs + uint32_t(lane);
+        site[v] = uint32_t(xoff[v]) + 2u * (k0 + uint32_t(lane)) + uint32_t(p.Lx) * row;
+        S[v] = V3<R>{own[q], own[stride + q], own[2 * size_t(stride) + q]};
+        O[v] = V3<R>{oth[q], oth[stride + q], oth[2 * size_t(stride) + q]};
+        // the x neighbour across the segment edge: k0 - 1 for lane 0 when
+        // xoff = 0, k0 + 32 for lane 31 when xoff = 1 (wrapped in the row)
+        const bool edge = xoff[v] ? lane == 31 : lane == 0;
+        if (edge) {
+            const uint32_t qe = xoff[v] ? (k0 + 32 == Lh ? qs - k0 : qs + 32) : (k0 == 0 ? qs + Lh - 1 : qs - 1);
+            E[v] = V3<R>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
+        } else {
+            E[v] = V3<R>{R(0), R(0), R(0)};
+        }
+        const uint32_t qym = y > 0 ? q - Lh : q + Lh * uint32_t(p.Ly - 1);
+        const uint32_t qyp = y + 1 < uint32_t(p.Ly) ? q + Lh : q - Lh * uint32_t(p.Ly - 1);
+        const uint32_t qzm = z > 0 ? q - plane : q + plane * uint32_t(p.Lz - 1);
+        const uint32_t qzp = z + 1 < uint32_t(p.Lz) ? q + plane : q - plane * uint32_t(p.Lz - 1);
+        Ym[v] = V3<R>{oth[qym], oth[stride + qym], oth[2 * size_t(stride) + qym]};
+        Yp[v] = V3<R>{oth[qyp], oth[stride + qyp], oth[2 * size_t(stride) + qyp]};
+        Zm[v] = V3<R>{oth[qzm], oth[stride + qzm], oth[2 * size_t(stride) + qzm]};
+        Zp[v] = V3<R>{oth[qzp], oth[stride + qzp], oth[2 * size_t(stride) + qzp]};
+        e[v] = V3<R>{par.e[0], par.e[1], par.e[2]};
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        // other-colour spin at k - 1 (xoff = 0) or k + 1 (xoff = 1)
+        V3<R> N;
+        if (xoff[v]) {
+            N.x = __shfl_down_sync(0xffffffffu, O[v].x, 1);
+            N.y = __shfl_down_sync(0xffffffffu, O[v].y, 1);
+            N.z = __shfl_down_sync(0xffffffffu, O[v].z, 1);
+            if (lane == 31) N = E[v];
+        } else {
+            N.x = __shfl_up_sync(0xffffffffu, O[v].x, 1);
+            N.y = __shfl_up_sync(0xffffffffu, O[v].y, 1);
+            N.z = __shfl_up_sync(0xffffffffu, O[v].z, 1);
+            if (lane == 0) N = E[v];
+        }
+        const V3<R> Xm = xoff[v] ? O[v] : N;
+        const V3<R> Xp = xoff[v] ? N : O[v];
+        V3<R> a{R(0), R(0), R(0)};
+        a.x = a.x + Xm.x; a.y = a.y + Xm.y; a.z = a.z + Xm.z;
+        a.x = a.x + Xp.x; a.y = a.y + Xp.y; a.z = a.z + Xp.z;
+        a.x = a.x + Ym[v].x; a.y = a.y + Ym[v].y; a.z = a.z + Ym[v].z;
+        a.x = a.x + Yp[v].x; a.y = a.y + Yp[v].y; a.z = a.z + Yp[v].z;
+        a.x = a.x + Zm[v].x; a.y = a.y + Zm[v].y; a.z = a.z + Zm[v].z;
+        a.x = a.x + Zp[v].x; a.y = a.y + Zp[v].y; a.z = a.z + Zp[v].z;
+        h[v] = a;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Colour pass of Table A1, batched over the lattices of a group (FAST: the
+// launch holds only row_fast lattices; MEASURE: black pass of a measurement
+// sweep).  Every lane
+// updates V sites per warp tile; the loads of all V sites are issued before
+// any of them is computed.  colour 1 with measure != 0 also takes the sample:
+// each black site adds itself, the red site with the same colour index, and
+// its bonds to the six red neighbours (every bond joins a red and a black
+// site, so each bond is counted once).
+// ------------------------------------------------------------------------
+template <typename R, int V, int MINB, bool FAST, bool MEASURE>
+__global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
+                                                                   int colour) {
+    constexpr int measure = MEASURE ? 1 : 0;
+    const WarpChunk wc = warp_chunk(ntiles);
+    const int lane = wc.lane;
+    const int other = colour ^ 1;
+    uint32_t tile = wc.begin;
+    int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
+    while (tile < wc.end) {
+        LatDev* L = g.lats[l];
+        const LatParams& p = L->p;
+        const uint32_t t0 = __ldg(&g.start[l]);
+        const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
+        const uint32_t run = t1 - tile;
+        const Par<R> par = load_par<R>(p);
+        const R c = cone[L->st.theta];
+        const uint32_t sweep = L->st.sweep;
+        R* __restrict__ s = static_cast<R*>(p.spins);
+        unsigned nacc = 0;
+        long long fix = 0;
+        for (; tile < t1; ++tile) {
+            const uint32_t base = (tile - t0) * uint32_t(32 * V) + uint32_t(lane);
+            V3<R> S[V], h[V], e[V], Sr[V];
+            uint32_t site[V];
+            bool act[V], mov[V];
+            if constexpr (FAST) {
+                row_segments<R, V>(p, par, s, colour, base - uint32_t(lane), lane, S, h, e, Sr, site);
+#pragma unroll
+                for (int v = 0; v < V; ++v) { act[v] = true; mov[v] = true; }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t q = base + uint32_t(32 * v);
+                    act[v] = q < p.Nc;
+                    mov[v] = false;
+                    site[v] = 0;
+                    h[v] = V3<R>{R(0), R(0), R(0)};
+                    if (act[v]) {
+                        const Geo geo = geometry(p, colour, q);
+                        site[v] = geo.site;
+                        S[v] = load_spin(s, p.stride, colour, q);
+                        uint32_t nq[6];
+                        const uint32_t present = neighbours(p, geo, colour, nq);
+                        mov[v] = !pinned(p, geo);
+                        if (mov[v] || measure) h[v] = neighbour_sum(s, p.stride, other, nq, present);
+                        e[v] = easy_axis(p, par, colour, q);
+                        if (measure) Sr[v] = load_spin(s, p.stride, other, q);
+                    }
+                }
+            }
+            // draw 0 of every site first: V independent Philox chains
+            const uint32_t tag = tag_of(colour, kPurposeMove);
+            R u1[V], u2[V], sd[V], P[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint4 w = philox(make_uint4(site[v], sweep, tag, 0u), p.key0, p.key1);
+                P[v] = uniform_p<R>(w);
+                disk_point<R>(w, u1[v], u2[v]);
+                sd[v] = u1[v] * u1[v] + u2[v] * u2[v];
+            }
+            Sums<R> sums;
+            if (measure)
+                for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!act[v]) continue;
+                V3<R> Sf = S[v];
+                if (mov[v] && disk_retry(u1[v], u2[v], sd[v], site[v], sweep, tag, p.key0, p.key1)) {
+                    const V3<R> Sn = cap_point(S[v], c, u1[v], u2[v], sd[v]);
+                    const R dE = delta_e(par, S[v], Sn, h[v], e[v]);
+                    if (metropolis(dE, par.T, P[v])) {
+                        store_spin(s, p.stride, colour, base + uint32_t(32 * v), Sn);
+                        Sf = Sn;
+                        ++nacc;
+                    }
+                }
+                if (measure) {
+                    add_site(sums, Sf, e[v]);
+                    sums.v[kSumEx] += Sf.x * h[v].x + Sf.y * h[v].y + Sf.z * h[v].z;
+                    add_site(sums, Sr[v], easy_axis(p, par, other, base + uint32_t(32 * v)));
+                }
+            }
+            if (measure) fix += warp_tile_fix(sums, lane);
+        }
+        publish(L->st, lane, nacc, measure != 0, fix, colour, run, p.nblocks_site, [&] {
+            if (colour == 1) finalize_sweep(p, L->st, measure);
+        });
+        ++l;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Exact M_L = sum_i S_i . e_C (Table A2) as fixed point, order independent:
+// FP64 terms t give q = trunc(t 2^52) split as hi 2^26 + lo; FP32 terms give
+// q = trunc(t 2^30) (an int32).  Site tiles as in the colour pass.
+// ------------------------------------------------------------------------
+template <typename R, int V>
+__global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t ntiles) {
+    const WarpChunk wc = warp_chunk(ntiles);
+    const int lane = wc.lane;
+    uint32_t tile = wc.begin;
+    int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
+    while (tile < wc.end) {
+        LatDev* L = g.lats[l];
+        const LatParams& p = L->p;
+        const uint32_t t0 = __ldg(&g.start[l]);
+        const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
+        const R* s = static_cast<const R*>(p.spins);
+        R e1[3];
+        if constexpr (kIsF64<R>) { e1[0] = p.R[0]; e1[1] = p.R[1]; e1[2] = p.R[2]; }
+        else { e1[0] = p.fR[0]; e1[1] = p.fR[1]; e1[2] = p.fR[2]; }
+        long long hi = 0, lo = 0;
+        for (; tile < t1; ++tile) {
+            const uint32_t base = (tile - t0) * uint32_t(32 * V) + uint32_t(lane);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint32_t q = base + uint32_t(32 * v);
+                if (q >= p.Nc) continue;
+                for (int colour = 0; colour < 2; ++colour) {
+                    const V3<R> S = load_spin(s, p.stride, colour, q);
+                    const R t = e1[0] * S.x + e1[1] * S.y + e1[2] * S.z;
+                    if constexpr (kIsF64<R>) {
+                        const long long w = (long long)(t * 0x1p52);
+                        const long long hh = w >> 26;
+                        hi += hh;
+                        lo += w - hh * (1ll << 26);
+                    } else {
+                        hi += (long long)__float2int_rz(t * 0x1p30f);
+                    }
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            lo += __shfl_xor_sync(0xffffffffu, lo, o);
+        }
+        if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.ml_hi), static_cast<unsigned long long>(hi));
+            if (lo) atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.ml_lo), static_cast<unsigned long long>(lo));
+        }
+        ++l;
+    }
 }
 
 // ShuffleRedBlackSpins (Sec. 2, Table A2) as a keyed bijection: 4-round
@@ -514,144 +690,147 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 }
 
 // ------------------------------------------------------------------------
-// Constrained pair pass of Table A2 (one thread per pair), batched.  Pairs
-// are (pi(2p), pi(2p+1)) of the colour's shuffled indices; the cone move is
-// made on i in the frame whose x-axis is e_C, j compensates the transverse
-// components, x'_j = sign(x_j) sqrt(|S_j|^2 - y'_j^2 - z'_j^2).  The pair is
-// accepted iff P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is
-// the exact value from mlong_kernel, fixed for the whole iteration.
-// Rejected without a test: 16 failed disk draws, t <= 0, M'_L <= 0.
+// Constrained pair pass of Table A2 (one lane per pair), batched, warp tiles
+// of 32 pairs.  Pairs are (pi(2p), pi(2p+1)) of the colour's shuffled
+// indices; the cone move is made on i in the frame whose x-axis is e_C, j
+// compensates the transverse components, x'_j = sign(x_j) sqrt(|S_j|^2 -
+// y'_j^2 - z'_j^2).  The pair is accepted iff
+// P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is the exact value
+// from mlong_kernel, fixed for the whole iteration.  Rejected without a
+// test: 16 failed disk draws, t <= 0, M'_L <= 0.
 // ------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, const R* __restrict__ cone, int colour,
-                                                           int finalize, int measure) {
-    __shared__ int s_lat;
-    __shared__ unsigned s_acc;
-    __shared__ double s_ml;
-    if (threadIdx.x == 0) {
-        s_lat = find_lattice(g);
-        s_acc = 0;
-        const LatDev* L0 = g.lats[s_lat];
-        s_ml = mlong_value<R>(L0->st.ml_hi, L0->st.ml_lo);
-    }
-    __syncthreads();
-    const int l = s_lat;
-    LatDev* L = g.lats[l];
-    const LatParams& p = L->p;
-    LatState& st = L->st;
-    const double ML = s_ml;
-    const Par<R> par = load_par<R>(p);
-    const int theta = st.theta;
-    const uint32_t sweep = st.sweep;
-    const R c = cone[theta];
-    R* __restrict__ s = static_cast<R*>(p.spins);
-    const uint32_t pr = (blockIdx.x - g.start[l]) * kBlock + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
+                                                           int colour, int finalize, int measure) {
+    const WarpChunk wc = warp_chunk(ntiles);
+    const int lane = wc.lane;
     const int other = colour ^ 1;
-    bool accepted = false;
-    if (!(ML > 0.0)) {
-        if (threadIdx.x == 0) atomicCAS(&st.error, 0, -5);
-    } else if (pr < p.n_pairs) {
+    uint32_t tile = wc.begin;
+    int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
+    while (tile < wc.end) {
+        LatDev* L = g.lats[l];
+        const LatParams& p = L->p;
+        const uint32_t t0 = __ldg(&g.start[l]);
+        const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
+        const uint32_t run = t1 - tile;
+        const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
+        const float fml = float(ML);
+        const Par<R> par = load_par<R>(p);
+        const R c = cone[L->st.theta];
+        const uint32_t sweep = L->st.sweep;
+        R* __restrict__ s = static_cast<R*>(p.spins);
         const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
-        const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
-        const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
-        const V3<R> Si = load_spin(s, p.stride, colour, qi);
-        const V3<R> Sj = load_spin(s, p.stride, colour, qj);
-        const V3<R> hi = rotate(par.Rm, Si);
-        const V3<R> hj = rotate(par.Rm, Sj);
-        V3<R> hni;
-        R P;
-        if (cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) {
+        unsigned nacc = 0;
+        if (!(ML > 0.0)) {
+            if (lane == 0) atomicCAS(&L->st.error, 0, -5);
+            tile = t1;
+        }
+        for (; tile < t1; ++tile) {
+            const uint32_t pr = (tile - t0) * 32u + uint32_t(lane);
+            if (pr >= p.n_pairs) continue;
+            const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
+            const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+            const V3<R> Si = load_spin(s, p.stride, colour, qi);
+            const V3<R> Sj = load_spin(s, p.stride, colour, qj);
+            const V3<R> hi = rotate(par.Rm, Si);
+            const V3<R> hj = rotate(par.Rm, Sj);
+            V3<R> hni;
+            R P;
+            if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) continue;
             const R ynj = (hj.y + hi.y) - hni.y;
             const R znj = (hj.z + hi.z) - hni.z;
             const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
-            if (t > R(0)) {
-                R xnj = sqrt(t);
-                if (hj.x < R(0)) xnj = -xnj;
-                bool ok;
-                R rM;
-                if constexpr (kIsF64<R>) {
-                    const double MLn = ML + hni.x + xnj - hi.x - hj.x;
-                    ok = MLn > 0.0;
-                    const double ratio = MLn / ML;
-                    rM = ratio * ratio;
-                } else {
-                    // FP32 spins: the change of M_L is evaluated in FP32 and
-                    // applied to the FP64 M_L as (1 + delta / M_L)^2.
-                    const float delta = ((hni.x + xnj) - hi.x) - hj.x;
-                    const float fml = float(ML);
-                    ok = fml + delta > 0.0f;
-                    const float ratio = 1.0f + delta / fml;
-                    rM = ratio * ratio;
-                }
-                if (ok) {
-                    const V3<R> hnj{xnj, ynj, znj};
-                    const V3<R> Sni = rotate_back(par.Rm, hni);
-                    const V3<R> Snj = rotate_back(par.Rm, hnj);
-                    const Geo gi = geometry(p, colour, qi);
-                    const Geo gj = geometry(p, colour, qj);
-                    uint32_t nqi[6], nqj[6];
-                    const uint32_t pi_ = neighbours(p, gi, colour, nqi);
-                    const uint32_t pj_ = neighbours(p, gj, colour, nqj);
-                    const V3<R> h_i = neighbour_sum(s, p.stride, other, nqi, pi_);
-                    const V3<R> h_j = neighbour_sum(s, p.stride, other, nqj, pj_);
-                    const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
-                    const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
-                    const R dE = dEi + dEj;
-                    R r = rM;
-                    r = r * (fabs(hj.x) / fabs(xnj));
-                    if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
-                    else r = r * __expf(-__fdividef(dE, par.T));
-                    if (P < r) {
-                        store_spin(s, p.stride, colour, qi, Sni);
-                        store_spin(s, p.stride, colour, qj, Snj);
-                        accepted = true;
-                    }
-                }
+            if (!(t > R(0))) continue;
+            R xnj = sqrt(t);
+            if (hj.x < R(0)) xnj = -xnj;
+            bool ok;
+            R rM;
+            if constexpr (kIsF64<R>) {
+                const double MLn = ML + hni.x + xnj - hi.x - hj.x;
+                ok = MLn > 0.0;
+                const double ratio = MLn / ML;
+                rM = ratio * ratio;
+            } else {
+                // FP32 spins: the change of M_L is evaluated in FP32 and
+                // applied to the FP64 M_L as (1 + delta / M_L)^2.
+                const float delta = ((hni.x + xnj) - hi.x) - hj.x;
+                ok = fml + delta > 0.0f;
+                const float ratio = 1.0f + delta / fml;
+                rM = ratio * ratio;
+            }
+            if (!ok) continue;
+            const V3<R> hnj{xnj, ynj, znj};
+            const V3<R> Sni = rotate_back(par.Rm, hni);
+            const V3<R> Snj = rotate_back(par.Rm, hnj);
+            const Geo gi = geometry(p, colour, qi);
+            const Geo gj = geometry(p, colour, qj);
+            uint32_t nqi[6], nqj[6];
+            const uint32_t pi_ = neighbours(p, gi, colour, nqi);
+            const uint32_t pj_ = neighbours(p, gj, colour, nqj);
+            const V3<R> h_i = neighbour_sum(s, p.stride, other, nqi, pi_);
+            const V3<R> h_j = neighbour_sum(s, p.stride, other, nqj, pj_);
+            const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
+            const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
+            const R dE = dEi + dEj;
+            R r = rM;
+            r = r * (fabs(hj.x) / fabs(xnj));
+            if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
+            else r = r * __expf(-__fdividef(dE, par.T));
+            if (P < r) {
+                store_spin(s, p.stride, colour, qi, Sni);
+                store_spin(s, p.stride, colour, qj, Snj);
+                nacc += 2;
             }
         }
-    }
-    const unsigned ballot = __ballot_sync(0xffffffffu, accepted);
-    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&s_acc, 2u * unsigned(__popc(ballot)));
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_acc) atomicAdd(&st.acc, (unsigned long long)s_acc);
-        block_done(st, colour, p.nblocks_pair, [&] {
-            if (finalize) finalize_sweep(p, st, measure);
+        publish(L->st, lane, nacc, false, 0, colour, run, p.nblocks_pair, [&] {
+            if (finalize) finalize_sweep(p, L->st, measure);
         });
+        ++l;
     }
 }
 
 // ------------------------------------------------------------------------
 // Standalone sample of the current state (after a constrained sweep): same
-// sums as the fused black-pass measurement; the last block closes the sweep.
+// sums as the fused black-pass measurement, site tiles; the warp that
+// completes a lattice closes its sweep.
 // ------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kBlock) measure_kernel(GroupArgs g) {
-    __shared__ int s_lat;
-    if (threadIdx.x == 0) s_lat = find_lattice(g);
-    __syncthreads();
-    const int l = s_lat;
-    LatDev* L = g.lats[l];
-    const LatParams& p = L->p;
-    LatState& st = L->st;
-    const Par<R> par = load_par<R>(p);
-    const R* s = static_cast<const R*>(p.spins);
-    const uint32_t q = (blockIdx.x - g.start[l]) * kBlock + threadIdx.x;
-    Sums<R> sums;
-    for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);
-    if (q < p.Nc) {
-        const Geo geo = geometry(p, 1, q);
-        uint32_t nq[6];
-        const uint32_t present = neighbours(p, geo, 1, nq);
-        const V3<R> h = neighbour_sum(s, p.stride, 0, nq, present);
-        const V3<R> Sb = load_spin(s, p.stride, 1, q);
-        add_site(sums, Sb, easy_axis(p, par, 1, q));
-        sums.v[kSumEx] += Sb.x * h.x + Sb.y * h.y + Sb.z * h.z;
-        add_site(sums, load_spin(s, p.stride, 0, q), easy_axis(p, par, 0, q));
+template <typename R, int V>
+__global__ void __launch_bounds__(kBlock) measure_kernel(GroupArgs g, uint32_t ntiles) {
+    const WarpChunk wc = warp_chunk(ntiles);
+    const int lane = wc.lane;
+    uint32_t tile = wc.begin;
+    int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
+    while (tile < wc.end) {
+        LatDev* L = g.lats[l];
+        const LatParams& p = L->p;
+        const uint32_t t0 = __ldg(&g.start[l]);
+        const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
+        const uint32_t run = t1 - tile;
+        const Par<R> par = load_par<R>(p);
+        const R* s = static_cast<const R*>(p.spins);
+        long long fix = 0;
+        for (; tile < t1; ++tile) {
+            const uint32_t base = (tile - t0) * uint32_t(32 * V) + uint32_t(lane);
+            Sums<R> sums;
+            for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint32_t q = base + uint32_t(32 * v);
+                if (q >= p.Nc) continue;
+                const Geo geo = geometry(p, 1, q);
+                uint32_t nq[6];
+                const uint32_t present = neighbours(p, geo, 1, nq);
+                const V3<R> h = neighbour_sum(s, p.stride, 0, nq, present);
+                const V3<R> Sb = load_spin(s, p.stride, 1, q);
+                add_site(sums, Sb, easy_axis(p, par, 1, q));
+                sums.v[kSumEx] += Sb.x * h.x + Sb.y * h.y + Sb.z * h.z;
+                add_site(sums, load_spin(s, p.stride, 0, q), easy_axis(p, par, 0, q));
+            }
+            fix += warp_tile_fix(sums, lane);
+        }
+        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, [&] { finalize_sweep(p, L->st, 1); });
+        ++l;
     }
-    block_reduce_sums(sums, st);
-    __syncthreads();
-    if (threadIdx.x == 0) block_done(st, 3, p.nblocks_site, [&] { finalize_sweep(p, st, 1); });
 }
 
 // ------------------------------------------------------------------------

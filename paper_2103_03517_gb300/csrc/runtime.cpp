@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -29,6 +30,18 @@ int fail(int code, const char* fmt, ...) {
     va_end(ap);
     g_error = buf;
     return code;
+}
+
+// MC_TRACE=1 in the environment prints the stages of lattice creation.
+static void trace(const char* what) {
+    static const int on = [] {
+        const char* v = std::getenv("MC_TRACE");
+        return v && v[0] == '1';
+    }();
+    if (on) {
+        std::fprintf(stderr, "[libmc] %s\n", what);
+        std::fflush(stderr);
+    }
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -112,7 +125,8 @@ size_t lattice_bytes(const mc_desc* d) {
     const int cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
     b += align256(size_t(cap) * kRingWords * 8);
     b += align256(3 * size_t(d->dims[0]) * 8);
-    b += align256(3 * sizeof(void*) + 4 * sizeof(uint32_t));  // group-of-one tables
+    // launch tables of the lattice alone: lattice pointer, site and pair starts
+    b += align256(sizeof(void*)) + 2 * align256(2 * sizeof(uint32_t));
     return b;
 }
 
@@ -211,6 +225,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     if (!din || !out) return fail(MC_ERR_ARG, "null argument");
     int rc = validate_desc(din);
     if (rc) return rc;
+    trace("create: validated");
     mc_lattice* h = new mc_lattice();
     h->desc = *din;
     h->desc.bond_mask = nullptr;
@@ -219,6 +234,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     const mc_desc* d = din;
     h->device = d->device;
     if (cudaSetDevice(d->device) != cudaSuccess) { delete h; return fail(MC_ERR_CUDA, "cudaSetDevice(%d) failed", d->device); }
+    trace("create: device set");
     if (d->stream) {
         h->stream = static_cast<cudaStream_t>(d->stream);
     } else {
@@ -238,6 +254,9 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.stride = (p.Nc + 63) / 64 * 64;
     p.n_pairs = p.Nc / 2;
     p.perm_h = feistel_half_bits(p.Nc);
+    p.row_fast = (p.bc[0] == MC_PERIODIC && p.bc[1] == MC_PERIODIC && p.bc[2] == MC_PERIODIC && !d->bond_mask &&
+                  !d->grain_id && p.Lh % 32 == 0 && (p.Nc / 32) % sites_per_thread(p.precision) == 0)
+                     ? 1 : 0;
     long long pinned = 0;
     for (int z = 0; z < p.Lz; ++z)
         for (int y = 0; y < p.Ly; ++y)
@@ -254,8 +273,9 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.key1 = uint32_t(d->seed >> 32);
     p.div_lh = make_fastdiv(uint32_t(p.Lh));
     p.div_ly = make_fastdiv(uint32_t(p.Ly));
-    p.nblocks_site = (p.Nc + kBlock - 1) / kBlock;
-    p.nblocks_pair = (p.n_pairs + kBlock - 1) / kBlock;
+    const uint32_t site_tile = uint32_t(32 * sites_per_thread(p.precision));  // warp tiles
+    p.nblocks_site = (p.Nc + site_tile - 1) / site_tile;
+    p.nblocks_pair = (p.n_pairs + 31) / 32;
     if (p.nblocks_pair == 0) p.nblocks_pair = 1;
     p.J = d->J; p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
@@ -266,6 +286,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     const size_t rs = d->precision == MC_FP64 ? 8 : 4;
 
     // one allocation, carved into 256-byte aligned pieces
+    trace("create: parameters computed");
     h->bytes = lattice_bytes(d);
     cudaError_t e = cudaMalloc(&h->d_base, h->bytes);
     if (e != cudaSuccess) {
@@ -308,7 +329,14 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     h->d_group_lats = reinterpret_cast<LatDev**>(take(sizeof(void*)));
     h->d_group_start = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
     h->d_group_start_pair = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
+    if (size_t(cur - static_cast<char*>(h->d_base)) > h->bytes) {
+        cudaFree(h->d_base);
+        if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
+        delete h;
+        return fail(MC_ERR_STATE, "internal: lattice layout exceeds its allocation");
+    }
 
+    trace("create: allocated");
     // initial state
     std::vector<double> xyz(size_t(p.N) * 3);
     for (long long i = 0; i < p.N; ++i) {
@@ -325,6 +353,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     if (rs == 8) to_device_layout(p, xyz.data(), reinterpret_cast<double*>(hs.data()));
     else to_device_layout(p, xyz.data(), reinterpret_cast<float*>(hs.data()));
 
+    trace("create: host layout built");
     LatDev init;
     std::memset(&init, 0, sizeof init);
     init.st.theta = d->theta0_deg;
@@ -354,13 +383,16 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     up(h->d_group_lats, &one, sizeof one);
     up(h->d_group_start, st_site, sizeof st_site);
     up(h->d_group_start_pair, st_pair, sizeof st_pair);
+    trace("create: uploads queued");
     if (rc == MC_OK) {
         const double* c64;
         const float* c32;
         rc = device_tables(h->device, &c64, &c32);
         h->cone = d->precision == MC_FP64 ? (const void*)c64 : (const void*)c32;
     }
+    trace("create: tables ready");
     if (rc == MC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(MC_ERR_CUDA, "init sync");
+    trace("create: done");
     if (rc != MC_OK) {
         cudaFree(h->d_base);
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -371,19 +403,23 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     return MC_OK;
 }
 
-GroupArgs single_args(mc_lattice* h, bool pair) {
-    GroupArgs g;
-    g.lats = h->d_group_lats;
-    g.start = pair ? h->d_group_start_pair : h->d_group_start;
-    g.n = 1;
-    return g;
+// Launch tables of the lattice alone (it is either row_fast or not).
+LaunchSet single_launch_set(mc_lattice* h) {
+    LaunchSet ls;
+    ls.all = GroupArgs{h->d_group_lats, h->d_group_start, 1};
+    ls.pairs = GroupArgs{h->d_group_lats, h->d_group_start_pair, 1};
+    ls.nt_all = h->hp.nblocks_site;
+    ls.nt_pairs = h->hp.nblocks_pair;
+    if (h->hp.row_fast) { ls.fast = ls.all; ls.nt_fast = ls.nt_all; }
+    else { ls.general = ls.all; ls.nt_general = ls.nt_all; }
+    return ls;
 }
 
-// Enqueue n sweeps of a set of lattices described by (site, pair) launch
-// arguments; with events != nullptr every pass launch is bracketed by events.
-int enqueue_sweeps(const KernelSet& k, const GroupArgs& gs, uint32_t nb_site, const GroupArgs& gp,
-                   uint32_t nb_pair, const void* cone, int n, int measure, bool constrained, cudaStream_t s,
-                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events) {
+// Enqueue n sweeps of the lattices of a launch set; with events != nullptr
+// every colour pass (its row_fast and general launches together) or pair
+// pass is bracketed by a pair of events.
+int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
+                   cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events) {
     auto timed = [&](auto&& launch) {
         if (events) {
             cudaEvent_t a, b;
@@ -397,15 +433,19 @@ int enqueue_sweeps(const KernelSet& k, const GroupArgs& gs, uint32_t nb_site, co
             launch();
         }
     };
+    auto colour_pass = [&](int colour, int meas) {
+        if (ls.nt_fast) k.colour_pass(ls.fast, ls.nt_fast, cone, colour, meas, true, s);
+        if (ls.nt_general) k.colour_pass(ls.general, ls.nt_general, cone, colour, meas, false, s);
+    };
     for (int i = 0; i < n; ++i) {
         if (!constrained) {
-            timed([&] { k.colour_pass(gs, nb_site, cone, 0, 0, s); });
-            timed([&] { k.colour_pass(gs, nb_site, cone, 1, measure, s); });
+            timed([&] { colour_pass(0, 0); });
+            timed([&] { colour_pass(1, measure); });
         } else {
-            k.mlong(gs, nb_site, s);
-            timed([&] { k.pair_pass(gp, nb_pair, cone, 0, 0, 0, s); });
-            timed([&] { k.pair_pass(gp, nb_pair, cone, 1, measure ? 0 : 1, 0, s); });
-            if (measure) k.measure(gs, nb_site, s);
+            k.mlong(ls.all, ls.nt_all, s);
+            timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 0, 0, 0, s); });
+            timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 1, measure ? 0 : 1, 0, s); });
+            if (measure) k.measure(ls.all, ls.nt_all, s);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -484,8 +524,7 @@ MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
     if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(h->device);
     const KernelSet& k = kernel_set(h->hp.precision);
-    return enqueue_sweeps(k, single_args(h, false), h->hp.nblocks_site, single_args(h, true), h->hp.nblocks_pair,
-                          h->cone, n_sweeps, measure ? 1 : 0, false, h->stream, nullptr);
+    return enqueue_sweeps(k, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, false, h->stream, nullptr);
 }
 
 MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_deg, int n_sweeps, int measure) {
@@ -499,8 +538,7 @@ MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_de
     int rc = upload_params(h);
     if (rc) return rc;
     const KernelSet& k = kernel_set(h->hp.precision);
-    return enqueue_sweeps(k, single_args(h, false), h->hp.nblocks_site, single_args(h, true), h->hp.nblocks_pair,
-                          h->cone, n_sweeps, measure ? 1 : 0, true, h->stream, nullptr);
+    return enqueue_sweeps(k, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, true, h->stream, nullptr);
 }
 
 MC_API int mc_sync(mc_handle h) {

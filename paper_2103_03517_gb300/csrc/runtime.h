@@ -38,8 +38,7 @@ int upload_params(mc_lattice* h);
 void constraint_frame(double theta_deg, double phi_deg, double R[9]);
 const KernelSet& kernel_set(int precision);
 int read_state(mc_lattice* h, LatState* st);
-int enqueue_sweeps(const KernelSet& k, const GroupArgs& gs, uint32_t nb_site, const GroupArgs& gp,
-                   uint32_t nb_pair, const void* cone, int n, int measure, bool constrained, cudaStream_t s,
-                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
+int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
+                   cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
 
 }  // namespace mcgb

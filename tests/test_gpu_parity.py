@@ -118,6 +118,9 @@ GEOMETRIES = [
     ((2, 2, 2), (0, 0, 0)),      # every neighbour doubled by the wrap
     ((10, 6, 4), (0, 1, 0)),
     ((34, 1, 1), (0, 1, 1)),     # a periodic chain
+    ((64, 6, 4), (0, 0, 0)),     # row fast path: one 32-site segment per row
+    ((128, 2, 2), (0, 0, 0)),    # row fast path, y and z neighbours doubled by the wrap
+    ((192, 4, 2), (0, 0, 0)),    # row fast path, three segments per row
 ]
 
 
@@ -261,7 +264,8 @@ def test_constraint_violation_reported():
 # ---------------------------------------------------------------- batching
 @pytest.mark.parametrize("prec", [mc.MC_FP64, mc.MC_FP32])
 def test_group_equals_alone_bitwise(prec):
-    specs = [((16, 16, 16), 0.5, 1), ((8, 8, 6), 1.1, 2), ((32, 16, 16), 0.9, 3), ((6, 3, 1), 0.4, 4)]
+    specs = [((16, 16, 16), 0.5, 1), ((8, 8, 6), 1.1, 2), ((32, 16, 16), 0.9, 3), ((6, 3, 1), 0.4, 4),
+             ((64, 8, 4), 0.7, 5)]
     def make(dims, T, seed):
         bc = tuple(0 if d % 2 == 0 else 1 for d in dims)
         return mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.01, T=T, seed=seed, precision=prec, boundary=bc,
@@ -427,8 +431,11 @@ def test_fp32_ensemble_matches_oracle(T):
     gm = np.linalg.norm(g["m"], axis=1)
     rm = np.linalg.norm(r[:, 3:6], axis=1)
     ge, re_ = g["e_parts"].sum(axis=1), r[:, 6:10].sum(axis=1)
-    # magnetisation: |delta| <= 2e-3 and <= 3 sigma (blocking errors of both)
-    for a, b in ((gm, rm), (np.abs(g["m"][:, 2]), np.abs(r[:, 5]))):
+    # magnetisation length and its second moment: |delta| <= 2e-3 and <= 3
+    # sigma (blocking errors of both series).  The direction of m diffuses
+    # slowly at K_u = 0.01, so direction-dependent averages such as <|m_z|>
+    # need far longer runs and are not compared here.
+    for a, b in ((gm, rm), (gm ** 2, rm ** 2)):
         sig = math.hypot(blocking_error(a), blocking_error(b))
         d = abs(a.mean() - b.mean())
         assert d <= 2e-3 and d <= 3 * sig, (T, a.mean(), b.mean(), sig)
