@@ -47,7 +47,7 @@ def workload_config():
     return specs, n, {
         "workload": "batched m(T) sweep: 32 periodic sc lattices 16^3/32^3/64^3/128^3 cycled, "
                     "T = 0.05..1.60, J = 1, K_u = 0.01 z; FP32 spins, FP64 accumulators; "
-                    "one measurement sweep per step",
+                    "one measurement sweep per step (sample: m vector and energy parts of every lattice)",
         "lattices": len(specs),
         "spins": n,
         "l2": "inputs larger than L2 (230 MB of spins), no flush",
@@ -240,7 +240,8 @@ def gpu_arm(args, cfg):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP32,
-                                           ring_capacity=16, stream=stream.cuda_stream, device=local))
+                                           ring_capacity=16, sample_torque=0, stream=stream.cuda_stream,
+                                           device=local))
               for s in specs]
         g = mc.mc_group_create(hs)
         mc.mc_group_sweep(g, args.warmup, measure=True)

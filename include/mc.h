@@ -86,6 +86,9 @@ typedef struct mc_desc {
     int init;               /* mc_init                                            */
     double init_dir[3];     /* direction for MC_INIT_UNIFORM (default +z)         */
     int ring_capacity;      /* per-sweep samples kept (default 4096)              */
+    int sample_torque;      /* 1 (default): every sample also has the torque of  */
+                            /* Sec. 3; 0: magnetisation and energies only, the   */
+                            /* torque reads 0 (constrained samples always have it) */
     /* optional granular-film tables, host memory, copied at create:            */
     const uint8_t* bond_mask;   /* N entries or NULL; bit d set = bond present,   */
                                 /* d = 0..5 for -x,+x,-y,+y,-z,+z; must be        */
@@ -133,7 +136,8 @@ typedef struct mc_sample {
 /* ---------------------------------------------------------------- lattice */
 
 /* Defaults: 16^3 periodic FP32, J = 1, all other couplings 0, axis z, T = 1,
- * seed 0, theta0 30, adapt_in_measure 1, uniform +z start, ring 4096. */
+ * seed 0, theta0 30, adapt_in_measure 1, uniform +z start, ring 4096,
+ * torques sampled. */
 MC_API void mc_desc_default(mc_desc* d);
 
 /* Create a lattice (Eq. 2 parameters; Sec. 2).  dims: Lx, Ly, Lz, all

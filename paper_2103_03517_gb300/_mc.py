@@ -33,7 +33,7 @@ class mc_desc(C.Structure):
                 ("J", C.c_double), ("K_u", C.c_double), ("axis", C.c_double * 3), ("K_c", C.c_double),
                 ("H", C.c_double * 3), ("T", C.c_double), ("seed", C.c_uint64),
                 ("theta0_deg", C.c_int), ("adapt_in_measure", C.c_int), ("init", C.c_int),
-                ("init_dir", C.c_double * 3), ("ring_capacity", C.c_int),
+                ("init_dir", C.c_double * 3), ("ring_capacity", C.c_int), ("sample_torque", C.c_int),
                 ("bond_mask", C.POINTER(C.c_uint8)), ("grain_id", C.POINTER(C.c_int32)),
                 ("grain_axis", C.POINTER(C.c_double)), ("n_grains", C.c_int),
                 ("stream", C.c_void_p), ("device", C.c_int)]
@@ -158,7 +158,8 @@ def mc_desc_default() -> mc_desc:
 
 def make_desc(dims, J=1.0, K_u=0.0, axis=(0.0, 0.0, 1.0), K_c=0.0, H=(0.0, 0.0, 0.0), T=1.0, seed=0,
               precision=MC_FP32, boundary=(0, 0, 0), theta0_deg=30, adapt_in_measure=1, init=MC_INIT_UNIFORM,
-              init_dir=(0.0, 0.0, 1.0), ring_capacity=4096, bond_mask=None, grain_id=None, grain_axis=None,
+              init_dir=(0.0, 0.0, 1.0), ring_capacity=4096, sample_torque=1, bond_mask=None, grain_id=None,
+              grain_axis=None,
               stream=None, device=0) -> mc_desc:
     """Fill an mc_desc.  Film tables (numpy arrays) are referenced, not
     copied, until mc_create_ex / mc_submit copies them; keep them alive."""
@@ -176,6 +177,7 @@ def make_desc(dims, J=1.0, K_u=0.0, axis=(0.0, 0.0, 1.0), K_c=0.0, H=(0.0, 0.0, 
     d.adapt_in_measure = int(adapt_in_measure)
     d.init = int(init)
     d.ring_capacity = int(ring_capacity)
+    d.sample_torque = int(bool(sample_torque))
     d._keep = []
     if bond_mask is not None:
         bm = np.ascontiguousarray(bond_mask, dtype=np.uint8)

@@ -113,6 +113,9 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
     g->ls.nt_general = sg.back();
     g->ls.nt_all = sa.back();
     g->ls.nt_pairs = sp.back();
+    g->ls.sample_level = 1;
+    for (int i = 0; i < n; ++i)
+        if (lattices[i]->hp.sample_torque) g->ls.sample_level = 2;
     // the members' queued work must be complete before the group uses them;
     // from now on every member runs on the group stream, so that calls on a
     // member order after the group's work

@@ -10,7 +10,8 @@ namespace mcgb {
 struct KernelSet {
     // Table A1 colour pass over the lattices of g (ntiles = warp tiles of the
     // launch; the launcher sizes a persistent grid from the occupancy).
-    // fast: every lattice of g is row_fast.
+    // fast: every lattice of g is row_fast; measure: 0 none, 1 magnetisation
+    // and energies, 2 also torques.
     void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, bool fast,
                         cudaStream_t s);
     // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
@@ -30,6 +31,7 @@ struct KernelSet {
 struct LaunchSet {
     GroupArgs fast, general, all, pairs;
     uint32_t nt_fast = 0, nt_general = 0, nt_all = 0, nt_pairs = 0;
+    int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
 };
 
 const KernelSet& kernels_f64();

@@ -78,6 +78,7 @@ struct LatParams {
     FastDiv div_lh, div_ly;
     uint32_t nblocks_site;  // site tiles of this lattice
     uint32_t nblocks_pair;  // pair tiles of this lattice
+    int sample_torque;      // measured sweeps also sum the torques
     int row_fast;           // all axes periodic, no film tables, Lh % 32 == 0:
                             // every 32-lane segment of a tile lies in one row
     void* spins;

@@ -148,9 +148,18 @@ __device__ __forceinline__ R delta_e(const Par<R>& par, V3<R> S, V3<R> Sn, V3<R>
     const R pn = Sn.x * e.x + Sn.y * e.y + Sn.z * e.z;
     const R po = S.x * e.x + S.y * e.y + S.z * e.z;
     const R e_u = -(par.Ku * (pn * pn - po * po));
-    const R e_c = par.Kc * (cubic_q(Sn) - cubic_q(S));
-    const R e_z = -(par.H[0] * d0 + par.H[1] * d1 + par.H[2] * d2);
-    return e_ex + e_u + e_c + e_z;
+    if constexpr (!kIsF64<R>) {
+        // FP32: zero couplings cost nothing (their terms are exactly zero)
+        R dE = e_ex + e_u;
+        if (par.Kc != R(0)) dE += par.Kc * (cubic_q(Sn) - cubic_q(S));
+        if (par.H[0] != R(0) || par.H[1] != R(0) || par.H[2] != R(0))
+            dE += -(par.H[0] * d0 + par.H[1] * d1 + par.H[2] * d2);
+        return dE;
+    } else {
+        const R e_c = par.Kc * (cubic_q(Sn) - cubic_q(S));
+        const R e_z = -(par.H[0] * d0 + par.H[1] * d1 + par.H[2] * d2);
+        return e_ex + e_u + e_c + e_z;
+    }
 }
 
 // Trial move UniformRandom_RotateSpin(S, theta) of Table A1: uniform by
@@ -215,17 +224,66 @@ __device__ __forceinline__ V3<R> cap_point(V3<R> S, R c, R u1, R u2, R s) {
     }
 }
 
+// FP32 mode samples the cap directly, without rejection: s = w0 / 2^32 is
+// uniform on [0, 1), so z' = 1 - s c is uniform on [cos theta, 1], and the
+// azimuth phi = 2 pi (w1 / 2^32 - 1/2) is uniform; (x', y') = r (cos phi,
+// sin phi) with r = sqrt(s c (2 - s c)) = sqrt(1 - z'^2).  Same law as the
+// disk method of the FP64 mode, no divergent retry loop in a warp.
+__device__ __forceinline__ void direct_draw(uint4 w, float& s, float& cp, float& sp) {
+    s = (float)(w.x >> 8) * 0x1p-24f;
+    const float phi = ((float)(w.y >> 8) * 0x1p-24f - 0.5f) * 6.28318530717958647692f;
+    __sincosf(phi, &sp, &cp);
+}
+
+__device__ __forceinline__ V3<float> cap_point_direct(V3<float> S, float c, float s, float cp, float sp) {
+    const float sc = s * c;
+    const float r = sqrtf(sc * (2.0f - sc));
+    const float zp = 1.0f - sc;
+    const float xp = r * cp, yp = r * sp;
+    const float sgn = copysignf(1.0f, S.z);
+    const float a = -1.0f / (sgn + S.z);
+    const float b = S.x * S.y * a;
+    const float b1x = 1.0f + sgn * S.x * S.x * a, b1y = sgn * b, b1z = -sgn * S.x;
+    const float b2x = b, b2y = sgn + S.y * S.y * a, b2z = -S.y;
+    const float nx = xp * b1x + yp * b2x + zp * S.x;
+    const float ny = xp * b1y + yp * b2y + zp * S.y;
+    const float nz = xp * b1z + yp * b2z + zp * S.z;
+    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+    return V3<float>{nx * inv, ny * inv, nz * inv};
+}
+
+// FP32, two sites per lane: one Philox call, keyed by the first site's
+// index, supplies the draws of both sites, 64 bits each: P (22 bits),
+// s (21 bits), phi (21 bits).
+__device__ __forceinline__ void direct_draw_two(uint4 w, float P[2], float s[2], float cp[2], float sp[2]) {
+    P[0] = (float)(w.x >> 10) * 0x1p-22f;
+    P[1] = (float)(w.y >> 10) * 0x1p-22f;
+    s[0] = (float)(((w.x & 0x3FFu) << 11) | (w.z & 0x7FFu)) * 0x1p-21f;
+    s[1] = (float)(((w.y & 0x3FFu) << 11) | (w.w & 0x7FFu)) * 0x1p-21f;
+    const float f0 = ((float)(w.z >> 11) * 0x1p-21f - 0.5f) * 6.28318530717958647692f;
+    const float f1 = ((float)(w.w >> 11) * 0x1p-21f - 0.5f) * 6.28318530717958647692f;
+    __sincosf(f0, &sp[0], &cp[0]);
+    __sincosf(f1, &sp[1], &cp[1]);
+}
+
 template <typename R>
 __device__ __forceinline__ bool cone_trial(V3<R> S, R c, uint32_t idx, uint32_t sweep, uint32_t tag,
                                            uint32_t k0, uint32_t k1, V3<R>& out, R& P) {
     const uint4 w = philox(make_uint4(idx, sweep, tag, 0u), k0, k1);
     P = uniform_p<R>(w);
-    R u1, u2;
-    disk_point<R>(w, u1, u2);
-    R s = u1 * u1 + u2 * u2;
-    if (!disk_retry(u1, u2, s, idx, sweep, tag, k0, k1)) return false;
-    out = cap_point(S, c, u1, u2, s);
-    return true;
+    if constexpr (!kIsF64<R>) {
+        float s, cp, sp;
+        direct_draw(w, s, cp, sp);
+        out = cap_point_direct(S, c, s, cp, sp);
+        return true;
+    } else {
+        R u1, u2;
+        disk_point<R>(w, u1, u2);
+        R s = u1 * u1 + u2 * u2;
+        if (!disk_retry(u1, u2, s, idx, sweep, tag, k0, k1)) return false;
+        out = cap_point(S, c, u1, u2, s);
+        return true;
+    }
 }
 
 // Metropolis acceptance, Eq. 1: accept iff P < exp(-dE/T).
@@ -245,22 +303,27 @@ struct Sums {
     R v[kNumSums];
 };
 
-template <typename R>
-__device__ __forceinline__ void add_site(Sums<R>& s, V3<R> S, V3<R> e) {
+// Sample sums of one site: LEVEL 1 = magnetisation and the single-site
+// energy sums, LEVEL 2 = also the torque sums.  FP32 skips the uniaxial or
+// cubic sum when its constant is zero (its energy is zero whatever the sum).
+template <typename R, int LEVEL = 2>
+__device__ __forceinline__ void add_site(Sums<R>& s, V3<R> S, V3<R> e, bool need_u = true, bool need_c = true) {
     s.v[kSumMx] += S.x;
     s.v[kSumMy] += S.y;
     s.v[kSumMz] += S.z;
     const R pe = S.x * e.x + S.y * e.y + S.z * e.z;
-    s.v[kSumU] += pe * pe;
-    s.v[kSumC] += cubic_q(S);
-    s.v[kSumTux] += pe * (S.y * e.z - S.z * e.y);
-    s.v[kSumTuy] += pe * (S.z * e.x - S.x * e.z);
-    s.v[kSumTuz] += pe * (S.x * e.y - S.y * e.x);
-    const R x2 = S.x * S.x, y2 = S.y * S.y, z2 = S.z * S.z;
-    const R c0 = S.x * (y2 + z2), c1 = S.y * (x2 + z2), c2 = S.z * (x2 + y2);
-    s.v[kSumTcx] += S.y * c2 - S.z * c1;
-    s.v[kSumTcy] += S.z * c0 - S.x * c2;
-    s.v[kSumTcz] += S.x * c1 - S.y * c0;
+    if (kIsF64<R> || need_u) s.v[kSumU] += pe * pe;
+    if (kIsF64<R> || need_c) s.v[kSumC] += cubic_q(S);
+    if constexpr (LEVEL >= 2) {
+        s.v[kSumTux] += pe * (S.y * e.z - S.z * e.y);
+        s.v[kSumTuy] += pe * (S.z * e.x - S.x * e.z);
+        s.v[kSumTuz] += pe * (S.x * e.y - S.y * e.x);
+        const R x2 = S.x * S.x, y2 = S.y * S.y, z2 = S.z * S.z;
+        const R c0 = S.x * (y2 + z2), c1 = S.y * (x2 + z2), c2 = S.z * (x2 + y2);
+        s.v[kSumTcx] += S.y * c2 - S.z * c1;
+        s.v[kSumTcy] += S.z * c0 - S.x * c2;
+        s.v[kSumTcz] += S.x * c1 - S.y * c0;
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -270,11 +333,11 @@ __device__ __forceinline__ void add_site(Sums<R>& s, V3<R> S, V3<R> e) {
 // FP64 instruction runs on the FP32 path.  Tiles are aligned to the lattice,
 // so the integer totals do not depend on the batch a lattice runs in.
 // ------------------------------------------------------------------------
-template <typename R>
+template <typename R, int NS = kNumSums>
 __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
     R mine = R(0);
 #pragma unroll
-    for (int i = 0; i < kNumSums; ++i) {
+    for (int i = 0; i < NS; ++i) {
         R v = s.v[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -289,7 +352,7 @@ __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
 // the sample of Sec. 3 (if measuring), the sweep counter.  Runs on one
 // thread of the last block to finish.
 // ------------------------------------------------------------------------
-__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure) {
+__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure, bool torque) {
     const long long acc = (long long)atomicExch(&st.acc, 0ull);
     st.last_acc = acc;
     if (!measure || p.adapt_in_measure) {
@@ -313,10 +376,12 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
         const double e_ex = -p.J * v[kSumEx] / N, e_u = -p.Ku * v[kSumU] / N, e_c = p.Kc * v[kSumC] / N;
         const double e_z = -(p.H[0] * v[kSumMx] + p.H[1] * v[kSumMy] + p.H[2] * v[kSumMz]) / N;
         const double e = e_ex + e_u + e_c + e_z;
-        double tq[3];
-        tq[0] = (2.0 * p.Ku * v[kSumTux] - 2.0 * p.Kc * v[kSumTcx] + (v[kSumMy] * p.H[2] - v[kSumMz] * p.H[1])) / N;
-        tq[1] = (2.0 * p.Ku * v[kSumTuy] - 2.0 * p.Kc * v[kSumTcy] + (v[kSumMz] * p.H[0] - v[kSumMx] * p.H[2])) / N;
-        tq[2] = (2.0 * p.Ku * v[kSumTuz] - 2.0 * p.Kc * v[kSumTcz] + (v[kSumMx] * p.H[1] - v[kSumMy] * p.H[0])) / N;
+        double tq[3] = {0.0, 0.0, 0.0};
+        if (torque) {
+            tq[0] = (2.0 * p.Ku * v[kSumTux] - 2.0 * p.Kc * v[kSumTcx] + (v[kSumMy] * p.H[2] - v[kSumMz] * p.H[1])) / N;
+            tq[1] = (2.0 * p.Ku * v[kSumTuy] - 2.0 * p.Kc * v[kSumTcy] + (v[kSumMz] * p.H[0] - v[kSumMx] * p.H[2])) / N;
+            tq[2] = (2.0 * p.Ku * v[kSumTuz] - 2.0 * p.Kc * v[kSumTcz] + (v[kSumMx] * p.H[1] - v[kSumMy] * p.H[0])) / N;
+        }
         double* mo = st.moments;
         mo[kMomN] += 1.0;
         for (int a = 0; a < 3; ++a) {
@@ -494,17 +559,18 @@ __device__ __forceinline__ void row_segments(const LatParams& p, const Par<R>& p
 // ------------------------------------------------------------------------
 // Colour pass of Table A1, batched over the lattices of a group (FAST: the
 // launch holds only row_fast lattices; MEASURE: black pass of a measurement
-// sweep).  Every lane
+// sweep: 1 = magnetisation and energies, 2 = also torques).  Every lane
 // updates V sites per warp tile; the loads of all V sites are issued before
 // any of them is computed.  colour 1 with measure != 0 also takes the sample:
 // each black site adds itself, the red site with the same colour index, and
 // its bonds to the six red neighbours (every bond joins a red and a black
 // site, so each bond is counted once).
 // ------------------------------------------------------------------------
-template <typename R, int V, int MINB, bool FAST, bool MEASURE>
+template <typename R, int V, int MINB, bool FAST, int MEASURE>
 __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
                                                                    int colour) {
-    constexpr int measure = MEASURE ? 1 : 0;
+    constexpr int measure = MEASURE > 0 ? 1 : 0;
+    constexpr int NS = MEASURE >= 2 ? kNumSums : kSumTux;  // sums sampled
     const WarpChunk wc = warp_chunk(ntiles);
     const int lane = wc.lane;
     const int other = colour ^ 1;
@@ -554,23 +620,41 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
             }
             // draw 0 of every site first: V independent Philox chains
             const uint32_t tag = tag_of(colour, kPurposeMove);
+            // FP64: disk point (u1, u2), s = |u|^2; FP32: s, cos phi, sin phi
             R u1[V], u2[V], sd[V], P[V];
+            if constexpr (!kIsF64<R> && V == 2) {
+                const uint4 w = philox(make_uint4(site[0], sweep, tag, 0u), p.key0, p.key1);
+                direct_draw_two(w, P, sd, u1, u2);
+            } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const uint4 w = philox(make_uint4(site[v], sweep, tag, 0u), p.key0, p.key1);
-                P[v] = uniform_p<R>(w);
-                disk_point<R>(w, u1[v], u2[v]);
-                sd[v] = u1[v] * u1[v] + u2[v] * u2[v];
+                for (int v = 0; v < V; ++v) {
+                    const uint4 w = philox(make_uint4(site[v], sweep, tag, 0u), p.key0, p.key1);
+                    P[v] = uniform_p<R>(w);
+                    if constexpr (kIsF64<R>) {
+                        disk_point<R>(w, u1[v], u2[v]);
+                        sd[v] = u1[v] * u1[v] + u2[v] * u2[v];
+                    } else {
+                        direct_draw(w, sd[v], u1[v], u2[v]);
+                    }
+                }
             }
             Sums<R> sums;
             if (measure)
-                for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);
+                for (int i = 0; i < kNumSums; ++i) sums.v[i] = R(0);  // unused tail stays 0
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 if (!act[v]) continue;
                 V3<R> Sf = S[v];
-                if (mov[v] && disk_retry(u1[v], u2[v], sd[v], site[v], sweep, tag, p.key0, p.key1)) {
-                    const V3<R> Sn = cap_point(S[v], c, u1[v], u2[v], sd[v]);
+                bool drawn;
+                V3<R> Sn;
+                if constexpr (kIsF64<R>) {
+                    drawn = mov[v] && disk_retry(u1[v], u2[v], sd[v], site[v], sweep, tag, p.key0, p.key1);
+                    if (drawn) Sn = cap_point(S[v], c, u1[v], u2[v], sd[v]);
+                } else {
+                    drawn = mov[v];
+                    if (drawn) Sn = cap_point_direct(S[v], c, sd[v], u1[v], u2[v]);
+                }
+                if (drawn) {
                     const R dE = delta_e(par, S[v], Sn, h[v], e[v]);
                     if (metropolis(dE, par.T, P[v])) {
                         store_spin(s, p.stride, colour, base + uint32_t(32 * v), Sn);
@@ -579,15 +663,16 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
                     }
                 }
                 if (measure) {
-                    add_site(sums, Sf, e[v]);
+                    const bool nu = par.Ku != R(0), nc = par.Kc != R(0);
+                    add_site<R, MEASURE>(sums, Sf, e[v], nu, nc);
                     sums.v[kSumEx] += Sf.x * h[v].x + Sf.y * h[v].y + Sf.z * h[v].z;
-                    add_site(sums, Sr[v], easy_axis(p, par, other, base + uint32_t(32 * v)));
+                    add_site<R, MEASURE>(sums, Sr[v], easy_axis(p, par, other, base + uint32_t(32 * v)), nu, nc);
                 }
             }
-            if (measure) fix += warp_tile_fix(sums, lane);
+            if (measure) fix += warp_tile_fix<R, NS>(sums, lane);
         }
         publish(L->st, lane, nacc, measure != 0, fix, colour, run, p.nblocks_site, [&] {
-            if (colour == 1) finalize_sweep(p, L->st, measure);
+            if (colour == 1) finalize_sweep(p, L->st, measure, p.sample_torque != 0);
         });
         ++l;
     }
@@ -783,7 +868,7 @@ __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t
             }
         }
         publish(L->st, lane, nacc, false, 0, colour, run, p.nblocks_pair, [&] {
-            if (finalize) finalize_sweep(p, L->st, measure);
+            if (finalize) finalize_sweep(p, L->st, measure, true);
         });
         ++l;
     }
@@ -828,7 +913,7 @@ __global__ void __launch_bounds__(kBlock) measure_kernel(GroupArgs g, uint32_t n
             }
             fix += warp_tile_fix(sums, lane);
         }
-        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, [&] { finalize_sweep(p, L->st, 1); });
+        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, [&] { finalize_sweep(p, L->st, 1, true); });
         ++l;
     }
 }

@@ -269,6 +269,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
             }
     p.n_mov = p.N - pinned;
     p.adapt_in_measure = d->adapt_in_measure;
+    p.sample_torque = d->sample_torque ? 1 : 0;
     p.key0 = uint32_t(d->seed);
     p.key1 = uint32_t(d->seed >> 32);
     p.div_lh = make_fastdiv(uint32_t(p.Lh));
@@ -410,6 +411,7 @@ LaunchSet single_launch_set(mc_lattice* h) {
     ls.pairs = GroupArgs{h->d_group_lats, h->d_group_start_pair, 1};
     ls.nt_all = h->hp.nblocks_site;
     ls.nt_pairs = h->hp.nblocks_pair;
+    ls.sample_level = h->hp.sample_torque ? 2 : 1;
     if (h->hp.row_fast) { ls.fast = ls.all; ls.nt_fast = ls.nt_all; }
     else { ls.general = ls.all; ls.nt_general = ls.nt_all; }
     return ls;
@@ -440,7 +442,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
     for (int i = 0; i < n; ++i) {
         if (!constrained) {
             timed([&] { colour_pass(0, 0); });
-            timed([&] { colour_pass(1, measure); });
+            timed([&] { colour_pass(1, measure ? ls.sample_level : 0); });
         } else {
             k.mlong(ls.all, ls.nt_all, s);
             timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 0, 0, 0, s); });
@@ -482,6 +484,7 @@ MC_API void mc_desc_default(mc_desc* d) {
     d->init = MC_INIT_UNIFORM;
     d->init_dir[2] = 1.0;
     d->ring_capacity = 4096;
+    d->sample_torque = 1;
 }
 
 MC_API int mc_create(const int dims[3], double J, double K_u, const double axis[3], double K_c, const double H[3],

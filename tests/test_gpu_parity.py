@@ -316,6 +316,29 @@ def test_group_constrained_equals_alone_bitwise():
             mc.mc_destroy(h)
 
 
+@pytest.mark.parametrize("dims", [(16, 16, 16), (64, 8, 4)])
+def test_sampling_without_torque_changes_nothing_else(dims):
+    """sample_torque = 0 drops only the torque sums: spins, m and energies
+    are bit-identical to full sampling, torques read zero."""
+    N = dims[0] * dims[1] * dims[2]
+    a = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, H=(0, 0.05, 0), T=0.7, seed=3, ring_capacity=64))
+    b = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, H=(0, 0.05, 0), T=0.7, seed=3, ring_capacity=64,
+                                     sample_torque=0))
+    try:
+        for h in (a, b):
+            mc.mc_sweep(h, 20)
+            mc.mc_sweep(h, 40, measure=True)
+        assert np.array_equal(mc.mc_get_spins(a, N), mc.mc_get_spins(b, N))
+        oa, ob = mc.mc_measure(a), mc.mc_measure(b)
+        for f in ("m", "m2", "ml", "ml2", "ml4", "e", "e2", "e_parts", "chi"):
+            assert getattr(oa, f) == getattr(ob, f) if not hasattr(getattr(oa, f), "__len__") else \
+                list(getattr(oa, f)) == list(getattr(ob, f)), f
+        assert list(ob.torque) == [0.0, 0.0, 0.0] and any(x != 0.0 for x in oa.torque)
+    finally:
+        mc.mc_destroy(a)
+        mc.mc_destroy(b)
+
+
 @pytest.mark.parametrize("prec", [mc.MC_FP64, mc.MC_FP32])
 def test_checkpoint_resume_is_bit_exact(prec, tmp_path):
     dims = (16, 12, 8)
@@ -441,6 +464,25 @@ def test_fp32_ensemble_matches_oracle(T):
         assert d <= 2e-3 and d <= 3 * sig, (T, a.mean(), b.mean(), sig)
     sig = math.hypot(blocking_error(ge), blocking_error(re_))
     assert abs(ge.mean() - re_.mean()) <= 3 * sig, (T, ge.mean(), re_.mean(), sig)
+
+
+@pytest.mark.parametrize("H,T", [((0.0, 0.0, 1.5), 1.0), ((0.3, -0.4, 1.2), 0.7)])
+def test_fp32_langevin_law(H, T):
+    """J = 0 in FP32 mode: independent moments in a field obey
+    <S.h^> = coth(|H|/T) - T/|H| (pins the FP32 cone sampler and the
+    acceptance test against a closed form)."""
+    from _stats import langevin
+    h = mc.mc_create_ex(mc.make_desc((64, 32, 32), J=0.0, H=H, T=T, seed=4, ring_capacity=2000))
+    try:
+        mc.mc_sweep(h, 300)
+        mc.mc_sweep(h, 2000, measure=True)
+        smp = mc.mc_samples(h, 2000)
+    finally:
+        mc.mc_destroy(h)
+    hh = np.asarray(H) / np.linalg.norm(H)
+    proj = smp["m"] @ hh
+    expect = langevin(np.linalg.norm(H) / T)
+    assert abs(proj.mean() - expect) < max(4 * blocking_error(proj), 3e-5), (proj.mean(), expect)
 
 
 def test_fp32_constrained_torque_matches_oracle():
