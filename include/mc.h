@@ -284,6 +284,44 @@ MC_API int mc_poll(mc_server* s, uint64_t job_id, mc_result* out);
 /* Current server clock (seconds), jobs queued / resident, bytes in use. */
 MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident, size_t* bytes);
 
+/* ------------------------------------------------------ no allocation */
+
+/* FP32 sweeps of Table A1 on a lattice whose spin memory the caller owns,
+ * for callers that cannot allocate device memory: code that runs while a
+ * framework's memory pool owns the whole device, inside another library's
+ * loop that forbids allocation (and the synchronisation cudaMalloc implies),
+ * or in a process whose allocator is not the CUDA runtime's.  The paper has
+ * no counterpart; this is a deployment variant of mc_sweep.
+ *
+ * The entry point allocates nothing: no cudaMalloc, no cudaFree, no stream,
+ * no library routine that allocates.  The scratch the sweep kernels need
+ * (lattice descriptor with its counters and sums, launch tables, cone table,
+ * sample ring) is one static 32 KiB device array inside libmc, reserved on
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up the array's device address once (make that first
+ * call before any stream capture).  Every call rewrites the whole scratch
+ * and clears its counters; calls that overlap on the GPU (on different
+ * streams, or from different threads) race on it.
+ *
+ * spins     device memory, FP32, colour-split layout of mc_export_state:
+ *           6 * stride floats, stride = N/2 rounded up to a multiple of 64,
+ *           component a of colour c at spins[(3c + a) stride + q]; updated
+ *           in place
+ * dims...   a periodic lattice as for mc_create (every size even)
+ * first_sweep  sweep counter of the chain (0 for a new chain; a continuing
+ *           chain passes the previous first_sweep + n_sweeps)
+ * theta_deg host in/out: cone half-angle (1..180) before and after
+ * samples   NULL, or device memory for n_sweeps samples of 14 doubles each
+ *           (sweep, theta, accepted, m[3], energies[4], torque[3], 0); with
+ *           samples every sweep is a measurement sweep
+ * stream    cudaStream_t (NULL = default stream); the call synchronises it
+ *           before returning (to read theta back)
+ * Errors: MC_ERR_ARG for invalid sizes or parameters, and for n_sweeps > 256
+ * with samples (the scratch holds 256 samples per call); MC_ERR_CUDA. */
+MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J, double K_u, const double axis[3],
+                            double K_c, const double H[3], double T, uint64_t seed, int64_t first_sweep,
+                            int n_sweeps, int* theta_deg, double* samples, void* stream);
+
 /* -------------------------------------------------------------- misc */
 
 MC_API const char* mc_last_error(void);

@@ -112,6 +112,9 @@ _SIGS = {
     "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
     "mc_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(mc_result)]),
     "mc_server_stats": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
+    "mc_sweep_noalloc": (C.c_int, [C.c_void_p, _P(C.c_int), C.c_double, C.c_double, _P(C.c_double), C.c_double,
+                                   _P(C.c_double), C.c_double, C.c_uint64, C.c_int64, C.c_int, _P(C.c_int),
+                                   C.c_void_p, C.c_void_p]),
     "mc_last_error": (C.c_char_p, []),
     "mc_version": (C.c_char_p, []),
 }
@@ -380,6 +383,20 @@ def mc_server_stats(s):
     b = C.c_size_t()
     _check(lib().mc_server_stats(s, C.byref(now), C.byref(q), C.byref(r), C.byref(b)))
     return now.value, q.value, r.value, b.value
+
+
+# ------------------------------------------------------------ no allocation
+def mc_sweep_noalloc(spins_ptr: int, dims, J, K_u, axis, K_c, H, T, seed, first_sweep: int, n_sweeps: int,
+                     theta_deg: int, samples_ptr: int | None = None, stream: int | None = None) -> int:
+    """FP32 sweeps on caller-owned device spins (colour-split layout) without
+    any device allocation; returns the cone angle after the sweeps."""
+    d = (C.c_int * 3)(*[int(x) for x in dims])
+    th = C.c_int(int(theta_deg))
+    _check(lib().mc_sweep_noalloc(C.c_void_p(spins_ptr), d, float(J), float(K_u), _vec3(axis), float(K_c), _vec3(H),
+                                  float(T), int(seed) & (2 ** 64 - 1), int(first_sweep), int(n_sweeps), C.byref(th),
+                                  C.c_void_p(samples_ptr) if samples_ptr else None,
+                                  C.c_void_p(stream) if stream else None))
+    return th.value
 
 
 def mc_last_error() -> str:

@@ -30,6 +30,7 @@ SOURCES = {
     "runtime.cpp": [],
     "groups.cpp": [],
     "server.cpp": [],
+    "noalloc.cu": [],
 }
 
 
