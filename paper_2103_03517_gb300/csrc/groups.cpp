@@ -78,39 +78,36 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
             return fail(MC_ERR_ARG, "group members must share device and precision");
         }
     }
-    // launch tables: [fast lattices | general lattices | all lattices], each
-    // with its own tile starts, plus the pair tile starts of all lattices
-    std::vector<LatDev*> fast, general, all(n);
-    std::vector<uint32_t> sf(1, 0), sg(1, 0), sa(n + 1, 0), sp(n + 1, 0);
-    for (int i = 0; i < n; ++i) {
-        const LatParams& hp = lattices[i]->hp;
-        all[i] = lattices[i]->d_lat;
-        sa[i + 1] = sa[i] + hp.nblocks_site;
-        sp[i + 1] = sp[i] + hp.nblocks_pair;
-        if (hp.row_fast) { fast.push_back(all[i]); sf.push_back(sf.back() + hp.nblocks_site); }
-        else { general.push_back(all[i]); sg.push_back(sg.back() + hp.nblocks_site); }
+    // launch tables: the lattices in launch order (general-path and small
+    // lattices first, so their few tiles start early and overlap the rest),
+    // with their site-tile and pair-tile starts
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const LatParams &pa = lattices[a]->hp, &pb = lattices[b]->hp;
+        if (pa.row_fast != pb.row_fast) return pa.row_fast < pb.row_fast;
+        return pa.N < pb.N;
+    });
+    std::vector<LatDev*> all(n);
+    std::vector<uint32_t> sa(n + 1, 0), sp(n + 1, 0);
+    for (int j = 0; j < n; ++j) {
+        const LatParams& hp = lattices[order[j]]->hp;
+        all[j] = lattices[order[j]]->d_lat;
+        sa[j + 1] = sa[j] + hp.nblocks_site;
+        sp[j + 1] = sp[j] + hp.nblocks_pair;
     }
     cudaSetDevice(g->device);
-    const size_t n_ptr = size_t(2 * n), n_idx = size_t(sf.size() + sg.size() + sa.size() + sp.size());
-    cudaError_t e = cudaMalloc(&g->d_mem, n_ptr * sizeof(LatDev*) + n_idx * sizeof(uint32_t));
+    const size_t b_ptr = (sizeof(LatDev*) * n + 255) & ~size_t(255);
+    const size_t b_idx = (sizeof(uint32_t) * (n + 1) + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc(&g->d_mem, b_ptr + 2 * b_idx);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(group)"); }
-    std::vector<char> host(n_ptr * sizeof(LatDev*) + n_idx * sizeof(uint32_t));
-    LatDev** hp_ = reinterpret_cast<LatDev**>(host.data());
-    std::copy(fast.begin(), fast.end(), hp_);
-    std::copy(general.begin(), general.end(), hp_ + fast.size());
-    std::copy(all.begin(), all.end(), hp_ + n);
-    uint32_t* hi = reinterpret_cast<uint32_t*>(host.data() + n_ptr * sizeof(LatDev*));
-    size_t off = 0;
-    auto put = [&](const std::vector<uint32_t>& v) { std::copy(v.begin(), v.end(), hi + off); off += v.size(); return off - v.size(); };
-    const size_t of = put(sf), og = put(sg), oa = put(sa), op = put(sp);
+    std::vector<char> host(b_ptr + 2 * b_idx, 0);
+    std::copy(all.begin(), all.end(), reinterpret_cast<LatDev**>(host.data()));
+    std::copy(sa.begin(), sa.end(), reinterpret_cast<uint32_t*>(host.data() + b_ptr));
+    std::copy(sp.begin(), sp.end(), reinterpret_cast<uint32_t*>(host.data() + b_ptr + b_idx));
     LatDev** dptr = static_cast<LatDev**>(g->d_mem);
-    uint32_t* didx = reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + n_ptr * sizeof(LatDev*));
-    g->ls.fast = GroupArgs{dptr, didx + of, int(fast.size())};
-    g->ls.general = GroupArgs{dptr + fast.size(), didx + og, int(general.size())};
-    g->ls.all = GroupArgs{dptr + n, didx + oa, n};
-    g->ls.pairs = GroupArgs{dptr + n, didx + op, n};
-    g->ls.nt_fast = sf.back();
-    g->ls.nt_general = sg.back();
+    g->ls.all = GroupArgs{dptr, reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptr), n};
+    g->ls.pairs = GroupArgs{dptr, reinterpret_cast<uint32_t*>(static_cast<char*>(g->d_mem) + b_ptr + b_idx), n};
     g->ls.nt_all = sa.back();
     g->ls.nt_pairs = sp.back();
     g->ls.sample_level = 1;

@@ -10,9 +10,8 @@ namespace mcgb {
 struct KernelSet {
     // Table A1 colour pass over the lattices of g (ntiles = warp tiles of the
     // launch; the launcher sizes a persistent grid from the occupancy).
-    // fast: every lattice of g is row_fast; measure: 0 none, 1 magnetisation
-    // and energies, 2 also torques.
-    void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, bool fast,
+    // measure: 0 none, 1 magnetisation and energies, 2 also torques.
+    void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
                         cudaStream_t s);
     // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
@@ -26,11 +25,11 @@ struct KernelSet {
     const char* name;
 };
 
-// Launch tables of a set of lattices: site tiles of the row_fast lattices,
-// of the other lattices, of all lattices, and pair tiles of all lattices.
+// Launch tables of a set of lattices: site tiles and pair tiles of every
+// lattice (lattice l owns tiles [start[l], start[l+1])).
 struct LaunchSet {
-    GroupArgs fast, general, all, pairs;
-    uint32_t nt_fast = 0, nt_general = 0, nt_all = 0, nt_pairs = 0;
+    GroupArgs all, pairs;
+    uint32_t nt_all = 0, nt_pairs = 0;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
 };
 

@@ -2,7 +2,7 @@
 // FP32 spins and energies (fast intrinsics: rsqrtf, __expf, __fdividef);
 // FP64 for the sample, torque and M_L bookkeeping.
 #ifndef MC_MINB_F32
-#define MC_MINB_F32 2
+#define MC_MINB_F32 3
 #endif
 #include "kernels.h"
 #include "pass_impl.cuh"
@@ -32,25 +32,18 @@ uint32_t grid_for(uint32_t ntiles, uint32_t cap) {
     return want < cap ? (want > 0 ? want : 1) : cap;
 }
 
-template <bool FAST, int MEASURE>
+template <int MEASURE>
 void colour_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(colour_pass_kernel<R, V, MINB, FAST, MEASURE>);
-    colour_pass_kernel<R, V, MINB, FAST, MEASURE><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
+    static const uint32_t cap = resident_blocks(colour_pass_kernel<R, V, MINB, MEASURE>);
+    colour_pass_kernel<R, V, MINB, MEASURE><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
 }
 
 // measure: 0 none, 1 magnetisation and energies, 2 also torques
-void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, bool fast,
-                 cudaStream_t s) {
+void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, cudaStream_t s) {
     const R* c = static_cast<const R*>(cone);
-    if (fast) {
-        if (measure >= 2) colour_pass_t<true, 2>(g, ntiles, c, colour, s);
-        else if (measure == 1) colour_pass_t<true, 1>(g, ntiles, c, colour, s);
-        else colour_pass_t<true, 0>(g, ntiles, c, colour, s);
-    } else {
-        if (measure >= 2) colour_pass_t<false, 2>(g, ntiles, c, colour, s);
-        else if (measure == 1) colour_pass_t<false, 1>(g, ntiles, c, colour, s);
-        else colour_pass_t<false, 0>(g, ntiles, c, colour, s);
-    }
+    if (measure >= 2) colour_pass_t<2>(g, ntiles, c, colour, s);
+    else if (measure == 1) colour_pass_t<1>(g, ntiles, c, colour, s);
+    else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,

@@ -79,8 +79,10 @@ struct LatParams {
     uint32_t nblocks_site;  // site tiles of this lattice
     uint32_t nblocks_pair;  // pair tiles of this lattice
     int sample_torque;      // measured sweeps also sum the torques
-    int row_fast;           // all axes periodic, no film tables, Lh % 32 == 0:
-                            // every 32-lane segment of a tile lies in one row
+    int row_fast;           // all axes periodic and no film tables, and (FP64)
+                            // Lh % 32 == 0, or (FP32) Lh a power of two <= 64 or a
+                            // multiple of 64, Nc % 64 == 0: the row paths apply
+    int row_lanes;          // FP32 row path: lanes per row group, min(Lh/2, 32)
     void* spins;
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null

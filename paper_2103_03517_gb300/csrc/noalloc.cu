@@ -102,7 +102,8 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     p.nblocks_site = (p.Nc + site_tile - 1) / site_tile;
     p.nblocks_pair = (p.n_pairs + 31) / 32 > 0 ? (p.n_pairs + 31) / 32 : 1;
     p.sample_torque = 1;
-    p.row_fast = (p.Lh % 32 == 0 && (p.Nc / 32) % sites_per_thread(MC_FP32) == 0) ? 1 : 0;
+    p.row_fast = row_fast(p, false);
+    p.row_lanes = p.Lh / 2 < 32 ? (p.Lh / 2 > 0 ? p.Lh / 2 : 1) : 32;
     p.spins = spins;
     p.ring = reinterpret_cast<double*>(base + kOffRing);
     p.ring_cap = kMaxSamples;
@@ -135,8 +136,6 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     ls.nt_all = p.nblocks_site;
     ls.nt_pairs = p.nblocks_pair;
     ls.sample_level = 2;
-    if (p.row_fast) { ls.fast = ls.all; ls.nt_fast = ls.nt_all; }
-    else { ls.general = ls.all; ls.nt_general = ls.nt_all; }
     rc = enqueue_sweeps(kernels_f32(), ls, base + kOffCone, n_sweeps, samples ? 1 : 0, false, s, nullptr);
     if (rc) return rc;
     if (samples) {

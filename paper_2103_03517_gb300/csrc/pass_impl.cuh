@@ -557,16 +557,96 @@ __device__ __forceinline__ void row_segments(const LatParams& p, const Par<R>& p
 }
 
 // ------------------------------------------------------------------------
-// Colour pass of Table A1, batched over the lattices of a group (FAST: the
-// launch holds only row_fast lattices; MEASURE: black pass of a measurement
-// sweep: 1 = magnetisation and energies, 2 = also torques).  Every lane
-// updates V sites per warp tile; the loads of all V sites are issued before
+// FP32 row path (row_fast lattices in FP32): lane L of a 64-site tile takes
+// the two adjacent colour indices q = q0 + 2L and q + 1 of one row, so every
+// spin is read as a float2 (one load instruction per component for both
+// sites).  Rows of Lh <= 64 sites per colour are covered by groups of
+// G = Lh/2 lanes (row_lanes), rows of Lh > 64 by segments of 64.  The other
+// colour's spins at k and k+1 give three of the four x neighbours of the
+// pair; the fourth, at k-1 or k+2, is the neighbouring lane's pair, taken by
+// a warp shuffle inside the row group (wrapping the row) or, at the ends of
+// a 64-site segment of a longer row, loaded.  The neighbour sum keeps the
+// order -x, +x, -y, +y, -z, +z.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float2 ld2(const float* a, uint32_t i) {
+    return *reinterpret_cast<const float2*>(a + i);
+}
+
+__device__ __forceinline__ void row_pairs(const LatParams& p, const float* s, int colour, uint32_t tile_q0, int lane,
+                                          V3<float> S[2], V3<float> h[2], V3<float> O[2], uint32_t site[2],
+                                          uint32_t qv[2]) {
+    const int other = colour ^ 1;
+    const uint32_t stride = p.stride;
+    const float* own = s + size_t(3 * colour) * stride;
+    const float* oth = s + size_t(3 * other) * stride;
+    const uint32_t Lh = uint32_t(p.Lh), Ly = uint32_t(p.Ly), Lz = uint32_t(p.Lz), plane = Lh * Ly;
+    const uint32_t q = tile_q0 + 2u * uint32_t(lane);
+    const uint32_t row = fast_div(q, p.div_lh);
+    const uint32_t k = q - row * Lh;
+    const uint32_t z = fast_div(row, p.div_ly);
+    const uint32_t y = row - z * Ly;
+    const bool xoff = ((y + z + uint32_t(colour)) & 1u) != 0;
+    const int G = p.row_lanes;
+    const int gbase = lane & ~(G - 1);
+    const int left = gbase | ((lane - 1) & (G - 1));
+    const int right = gbase | ((lane + 1) & (G - 1));
+    const float2 sx = ld2(own, q), sy = ld2(own + stride, q), sz = ld2(own + 2 * size_t(stride), q);
+    const float2 ox = ld2(oth, q), oy = ld2(oth + stride, q), oz = ld2(oth + 2 * size_t(stride), q);
+    const uint32_t qym = y > 0 ? q - Lh : q + Lh * (Ly - 1);
+    const uint32_t qyp = y + 1 < Ly ? q + Lh : q - Lh * (Ly - 1);
+    const uint32_t qzm = z > 0 ? q - plane : q + plane * (Lz - 1);
+    const uint32_t qzp = z + 1 < Lz ? q + plane : q - plane * (Lz - 1);
+    const float2 ymx = ld2(oth, qym), ymy = ld2(oth + stride, qym), ymz = ld2(oth + 2 * size_t(stride), qym);
+    const float2 ypx = ld2(oth, qyp), ypy = ld2(oth + stride, qyp), ypz = ld2(oth + 2 * size_t(stride), qyp);
+    const float2 zmx = ld2(oth, qzm), zmy = ld2(oth + stride, qzm), zmz = ld2(oth + 2 * size_t(stride), qzm);
+    const float2 zpx = ld2(oth, qzp), zpy = ld2(oth + stride, qzp), zpz = ld2(oth + 2 * size_t(stride), qzp);
+    // other colour at k - 1 (left lane's second) and k + 2 (right lane's first)
+    V3<float> lft{__shfl_sync(0xffffffffu, ox.y, left), __shfl_sync(0xffffffffu, oy.y, left),
+                  __shfl_sync(0xffffffffu, oz.y, left)};
+    V3<float> rgt{__shfl_sync(0xffffffffu, ox.x, right), __shfl_sync(0xffffffffu, oy.x, right),
+                  __shfl_sync(0xffffffffu, oz.x, right)};
+    if (Lh > 64u) {  // ends of a 64-site segment of a longer row
+        if (lane == 0) {
+            const uint32_t qe = k == 0 ? q + Lh - 1 : q - 1;
+            lft = V3<float>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
+        }
+        if (lane == 31) {
+            const uint32_t qe = k + 2 == Lh ? q + 2 - Lh : q + 2;
+            rgt = V3<float>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
+        }
+    }
+    const V3<float> o0{ox.x, oy.x, oz.x}, o1{ox.y, oy.y, oz.y};
+    const V3<float> xm0 = xoff ? o0 : lft, xp0 = xoff ? o1 : o0;
+    const V3<float> xm1 = xoff ? o1 : o0, xp1 = xoff ? rgt : o1;
+    h[0].x = ((((xm0.x + xp0.x) + ymx.x) + ypx.x) + zmx.x) + zpx.x;
+    h[0].y = ((((xm0.y + xp0.y) + ymy.x) + ypy.x) + zmy.x) + zpy.x;
+    h[0].z = ((((xm0.z + xp0.z) + ymz.x) + ypz.x) + zmz.x) + zpz.x;
+    h[1].x = ((((xm1.x + xp1.x) + ymx.y) + ypx.y) + zmx.y) + zpx.y;
+    h[1].y = ((((xm1.y + xp1.y) + ymy.y) + ypy.y) + zmy.y) + zpy.y;
+    h[1].z = ((((xm1.z + xp1.z) + ymz.y) + ypz.y) + zmz.y) + zpz.y;
+    S[0] = V3<float>{sx.x, sy.x, sz.x};
+    S[1] = V3<float>{sx.y, sy.y, sz.y};
+    O[0] = o0;
+    O[1] = o1;
+    const uint32_t x0 = uint32_t(xoff) + 2u * k;
+    site[0] = x0 + uint32_t(p.Lx) * row;
+    site[1] = site[0] + 2u;
+    qv[0] = q;
+    qv[1] = q + 1;
+}
+
+// ------------------------------------------------------------------------
+// Colour pass of Table A1, batched over the lattices of a group (MEASURE:
+// black pass of a measurement sweep: 1 = magnetisation and energies, 2 = also
+// torques).  row_fast lattices take a row path (FP32: adjacent pairs, FP64:
+// 32-site segments), the others the general path.  Every lane updates V
+// adjacent sites per warp tile; the loads of all V sites are issued before
 // any of them is computed.  colour 1 with measure != 0 also takes the sample:
 // each black site adds itself, the red site with the same colour index, and
 // its bonds to the six red neighbours (every bond joins a red and a black
 // site, so each bond is counted once).
 // ------------------------------------------------------------------------
-template <typename R, int V, int MINB, bool FAST, int MEASURE>
+template <typename R, int V, int MINB, int MEASURE>
 __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
                                                                    int colour) {
     constexpr int measure = MEASURE > 0 ? 1 : 0;
@@ -591,16 +671,29 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
         for (; tile < t1; ++tile) {
             const uint32_t base = (tile - t0) * uint32_t(32 * V) + uint32_t(lane);
             V3<R> S[V], h[V], e[V], Sr[V];
-            uint32_t site[V];
+            uint32_t site[V], qv[V];
             bool act[V], mov[V];
-            if constexpr (FAST) {
-                row_segments<R, V>(p, par, s, colour, base - uint32_t(lane), lane, S, h, e, Sr, site);
+            if (p.row_fast) {
+                if constexpr (!kIsF64<R> && V == 2) {
+                    row_pairs(p, s, colour, base - uint32_t(lane), lane, S, h, Sr, site, qv);
+                } else {
+                    row_segments<R, V>(p, par, s, colour, base - uint32_t(lane), lane, S, h, e, Sr, site);
 #pragma unroll
-                for (int v = 0; v < V; ++v) { act[v] = true; mov[v] = true; }
-            } else {
+                    for (int v = 0; v < V; ++v) qv[v] = base + uint32_t(32 * v);
+                }
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const uint32_t q = base + uint32_t(32 * v);
+                    act[v] = true;
+                    mov[v] = true;
+                    e[v] = V3<R>{par.e[0], par.e[1], par.e[2]};
+                }
+            } else {
+                // a lane's V sites are adjacent colour indices, as on the row
+                // paths, so both paths key the same draws to the same sites
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t q = (base - uint32_t(lane)) + uint32_t(V * lane + v);
+                    qv[v] = q;
                     act[v] = q < p.Nc;
                     mov[v] = false;
                     site[v] = 0;
@@ -657,7 +750,7 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
                 if (drawn) {
                     const R dE = delta_e(par, S[v], Sn, h[v], e[v]);
                     if (metropolis(dE, par.T, P[v])) {
-                        store_spin(s, p.stride, colour, base + uint32_t(32 * v), Sn);
+                        store_spin(s, p.stride, colour, qv[v], Sn);
                         Sf = Sn;
                         ++nacc;
                     }
@@ -666,7 +759,7 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
                     const bool nu = par.Ku != R(0), nc = par.Kc != R(0);
                     add_site<R, MEASURE>(sums, Sf, e[v], nu, nc);
                     sums.v[kSumEx] += Sf.x * h[v].x + Sf.y * h[v].y + Sf.z * h[v].z;
-                    add_site<R, MEASURE>(sums, Sr[v], easy_axis(p, par, other, base + uint32_t(32 * v)), nu, nc);
+                    add_site<R, MEASURE>(sums, Sr[v], easy_axis(p, par, other, qv[v]), nu, nc);
                 }
             }
             if (measure) fix += warp_tile_fix<R, NS>(sums, lane);

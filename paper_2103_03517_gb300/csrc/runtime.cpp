@@ -106,6 +106,15 @@ static int feistel_half_bits(uint32_t n) {
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Whether a lattice takes the row paths of the colour pass (see LatParams).
+int row_fast(const LatParams& p, bool film) {
+    if (film || p.bc[0] != MC_PERIODIC || p.bc[1] != MC_PERIODIC || p.bc[2] != MC_PERIODIC) return 0;
+    if (p.precision == MC_FP64) return p.Lh % 32 == 0 ? 1 : 0;
+    const bool pow2_small = p.Lh >= 2 && p.Lh <= 64 && (p.Lh & (p.Lh - 1)) == 0;
+    const bool long_rows = p.Lh % 64 == 0;
+    return (pow2_small || long_rows) && p.Nc % 64 == 0 ? 1 : 0;
+}
+
 // ------------------------------------------------------------- lattices
 static void set_float_params(LatParams& p) {
     p.fJ = (float)p.J; p.fKu = (float)p.Ku; p.fKc = (float)p.Kc; p.fT = (float)p.T;
@@ -254,9 +263,8 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.stride = (p.Nc + 63) / 64 * 64;
     p.n_pairs = p.Nc / 2;
     p.perm_h = feistel_half_bits(p.Nc);
-    p.row_fast = (p.bc[0] == MC_PERIODIC && p.bc[1] == MC_PERIODIC && p.bc[2] == MC_PERIODIC && !d->bond_mask &&
-                  !d->grain_id && p.Lh % 32 == 0 && (p.Nc / 32) % sites_per_thread(p.precision) == 0)
-                     ? 1 : 0;
+    p.row_fast = row_fast(p, d->bond_mask != nullptr || d->grain_id != nullptr);
+    p.row_lanes = p.Lh / 2 < 32 ? (p.Lh / 2 > 0 ? p.Lh / 2 : 1) : 32;
     long long pinned = 0;
     for (int z = 0; z < p.Lz; ++z)
         for (int y = 0; y < p.Ly; ++y)
@@ -412,14 +420,11 @@ LaunchSet single_launch_set(mc_lattice* h) {
     ls.nt_all = h->hp.nblocks_site;
     ls.nt_pairs = h->hp.nblocks_pair;
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
-    if (h->hp.row_fast) { ls.fast = ls.all; ls.nt_fast = ls.nt_all; }
-    else { ls.general = ls.all; ls.nt_general = ls.nt_all; }
     return ls;
 }
 
 // Enqueue n sweeps of the lattices of a launch set; with events != nullptr
-// every colour pass (its row_fast and general launches together) or pair
-// pass is bracketed by a pair of events.
+// every colour pass or pair pass is bracketed by a pair of events.
 int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events) {
     auto timed = [&](auto&& launch) {
@@ -435,10 +440,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             launch();
         }
     };
-    auto colour_pass = [&](int colour, int meas) {
-        if (ls.nt_fast) k.colour_pass(ls.fast, ls.nt_fast, cone, colour, meas, true, s);
-        if (ls.nt_general) k.colour_pass(ls.general, ls.nt_general, cone, colour, meas, false, s);
-    };
+    auto colour_pass = [&](int colour, int meas) { k.colour_pass(ls.all, ls.nt_all, cone, colour, meas, s); };
     for (int i = 0; i < n; ++i) {
         if (!constrained) {
             timed([&] { colour_pass(0, 0); });

@@ -33,6 +33,7 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int create_lattice(const mc_desc* d, mc_handle* out);
 int validate_desc(const mc_desc* d);
+int row_fast(const LatParams& p, bool film);
 size_t lattice_bytes(const mc_desc* d);
 int upload_params(mc_lattice* h);
 void constraint_frame(double theta_deg, double phi_deg, double R[9]);

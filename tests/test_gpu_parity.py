@@ -316,6 +316,33 @@ def test_group_constrained_equals_alone_bitwise():
             mc.mc_destroy(h)
 
 
+@pytest.mark.parametrize("dims", [(16, 16, 16), (8, 8, 8), (4, 4, 8), (64, 32, 8), (128, 8, 4), (256, 4, 4),
+                                  (384, 2, 2)])
+def test_fp32_row_path_matches_general_path(dims):
+    """FP32: a periodic lattice takes the row path; the same lattice with an
+    all-ones bond mask (identical physics) takes the general path.  Both key
+    the same draws to the same sites, so one sweep gives the same spins up to
+    FP32 rounding; a wrong neighbour would change many sites by O(1)."""
+    N = dims[0] * dims[1] * dims[2]
+    spins = workloads.random_spins(N, 7)
+    kw = dict(K_u=0.05, K_c=0.02, H=(0.02, 0.0, 0.05), T=0.9, seed=12, ring_capacity=8)
+    a = mc.mc_create_ex(mc.make_desc(dims, **kw))
+    b = mc.mc_create_ex(mc.make_desc(dims, bond_mask=np.full(N, 0x3F, np.uint8), **kw))
+    try:
+        for h in (a, b):
+            mc.mc_set_spins(h, spins)
+            mc.mc_sweep(h, 1, measure=True)
+        sa, sb = mc.mc_get_spins(a, N), mc.mc_get_spins(b, N)
+        moved = np.any(sa != spins, axis=1).mean()
+        assert moved > 0.2
+        close = np.all(np.abs(sa - sb) < 1e-5, axis=1)
+        assert close.mean() > 0.999, (dims, close.mean())
+        assert abs(mc.mc_measure(a).e - mc.mc_measure(b).e) < 1e-5
+    finally:
+        mc.mc_destroy(a)
+        mc.mc_destroy(b)
+
+
 @pytest.mark.parametrize("dims", [(16, 16, 16), (64, 8, 4)])
 def test_sampling_without_torque_changes_nothing_else(dims):
     """sample_torque = 0 drops only the torque sums: spins, m and energies
