@@ -297,6 +297,7 @@ def gpu_arm(args, cfg):
         extra = {}
         if rank == 0 and not args.quick:
             extra = secondary(mc, torch, stream, local)
+            extra["serving"] = serving(mc)
         mc.mc_group_destroy(g)
         for h in hs:
             mc.mc_destroy(h)
@@ -369,6 +370,60 @@ def secondary(mc, torch, stream, dev):
     for h in hs:
         mc.mc_destroy(h)
     return out
+
+
+def serving(mc, n_requests=40, rate=20.0, n_eq=200, n_meas=500):
+    """Config-5 style trace: Poisson arrivals (rate, seed 1) of m(T) points,
+    constrained points and granular films (45/45/10%), cubes L in
+    {8, ..., 256}, T uniform in (0.05, 1.6), 200 + 500 sweeps per job,
+    submitted at their arrival times to one server; latency = finish -
+    arrival on the server's clock."""
+    trace = workloads.poisson_trace(rate, n_requests, seed=1)
+    gid, mask, axes = workloads.voronoi_film(1024, 1024, 15, 10.0, seed=1)
+    jobs, work = [], 0
+    for r in trace:
+        if r["kind"] == "film":
+            d = mc.make_desc((1024, 1024, 15), K_u=0.02, T=r["T"], seed=r["seed"], boundary=(0, 0, 1),
+                             bond_mask=mask, grain_id=gid, grain_axis=axes, ring_capacity=16, sample_torque=0)
+            jobs.append(mc.make_job(d, mc.MC_JOB_SWEEP, n_equilibrate=n_eq, n_measure=n_meas))
+            work += 1024 * 1024 * 15 * (n_eq + n_meas)
+        elif r["kind"] == "constrained":
+            t = math.radians(r["theta_c"])
+            d = mc.make_desc((r["L"],) * 3, K_u=0.05, K_c=0.02, T=r["T"], seed=r["seed"], ring_capacity=16,
+                             init_dir=(math.sin(t), 0.0, math.cos(t)))
+            jobs.append(mc.make_job(d, mc.MC_JOB_CONSTRAINED, theta_c_deg=r["theta_c"], phi_c_deg=0.0,
+                                    n_equilibrate=n_eq, n_measure=n_meas))
+            work += r["L"] ** 3 * (n_eq + n_meas)
+        else:
+            d = mc.make_desc((r["L"],) * 3, K_u=0.01, T=r["T"], seed=r["seed"], ring_capacity=16, sample_torque=0)
+            jobs.append(mc.make_job(d, mc.MC_JOB_SWEEP, n_equilibrate=n_eq, n_measure=n_meas))
+            work += r["L"] ** 3 * (n_eq + n_meas)
+    srv = mc.mc_server_create(max_epoch_sweeps=50)
+    try:
+        ids = []
+        t0 = time.perf_counter()
+        for r, j in zip(trace, jobs):
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0005)
+            ids.append(mc.mc_submit(srv, j))
+        done = {}
+        while len(done) < len(ids):
+            for i in ids:
+                if i not in done:
+                    rc, res = mc.mc_poll(srv, i)
+                    if rc == mc.MC_OK:
+                        done[i] = res
+            time.sleep(0.002)
+    finally:
+        mc.mc_server_destroy(srv)
+    res = [done[i] for i in ids]
+    lat = sorted(r.t_finish - r.t_submit for r in res)
+    span = max(r.t_finish for r in res) - min(r.t_submit for r in res)
+    q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    return {"requests": n_requests, "rate_per_s": rate, "req_per_s": n_requests / span, "p50_s": q(0.5),
+            "p99_s": q(0.99), "updates_per_s": work / span, "ok": sum(r.status == 0 for r in res),
+            "workload": "Poisson trace (seed 1) of m(T) / constrained / film jobs 45/45/10%, cubes 8^3..256^3, "
+                        "films 1024x1024x15 Voronoi (d = 10), 200 + 500 sweeps per job"}
 
 
 def main():

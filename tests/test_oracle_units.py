@@ -240,3 +240,41 @@ def test_constraint_frame_orthonormal():
         t, p = math.radians(th), math.radians(ph)
         assert np.allclose(R[0], [math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)], atol=1e-15)
         assert np.allclose(np.cross(R[0], R[1]), R[2], atol=1e-15)
+
+
+# --------------------------------------------------------- observables, Sec. 3
+def test_sample_energies_equal_brute_force_total_energy():
+    """The per-sample energy parts of a measured sweep sum to E/N of Eq. 2
+    computed brute force over the final state (all couplings on, open and
+    periodic axes, a field)."""
+    rng = np.random.default_rng(11)
+    dims, bc = (6, 4, 3), (0, 0, 1)
+    J, Ku, Kc = 1.1, 0.3, -0.4
+    axis = rng.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    H = np.array([0.2, -0.1, 0.3])
+    lat = oracle.Lattice(dims, J=J, Ku=Ku, axis=axis, Kc=Kc, H=H, T=0.7, bc=bc, seed=4, ring_cap=3)
+    lat.set_spins(workloads_random(72, 5))
+    lat.sweep(3, measure=True)
+    S = lat.spins()
+    E = _total_energy(S, dims, bc, J, Ku, axis, Kc, H)
+    smp = lat.samples(1)[0]
+    assert abs(smp[6:10].sum() - E / 72) < 1e-13
+    assert np.allclose(smp[3:6], S.mean(axis=0), atol=1e-15)
+
+
+def test_profile_is_the_slice_average():
+    dims = (10, 4, 6)
+    lat = oracle.Lattice(dims, J=1.0, Ku=0.05, T=0.8, bc=(2, 0, 0), seed=2, ring_cap=1)
+    import workloads
+    lat.set_spins(workloads.wall_spins(dims))
+    acc = np.zeros(dims[0])
+    for _ in range(4):
+        lat.sweep(1, measure=True)
+        acc += lat.spins().reshape(dims[2], dims[1], dims[0], 3)[..., 2].mean(axis=(0, 1))
+    assert np.allclose(lat.profile(), acc / 4, atol=1e-15)
+
+
+def workloads_random(n, seed):
+    import workloads
+    return workloads.random_spins(n, seed)
