@@ -141,6 +141,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------ ranks
+def job_time_and_value(ms_local: float, updates_per_rank: float, world: int, reduce_max=None):
+    """Whole-job numbers of a weak-scaling run: every rank advances its own
+    batch; the job time is the max over ranks (reduce_max, a collective, is
+    given for world > 1) and the value is the updates of all ranks over it."""
+    ms = reduce_max(ms_local) if world > 1 else ms_local
+    return ms, world * updates_per_rank / (ms * 1e-3)
+
+
+def torch_reduce_max(device):
+    import torch
+    import torch.distributed as dist
+
+    def f(x):
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return f
+
+
 # ------------------------------------------------------------ oracle legs
 def _oracle_worker(args):
     idx, n_warm, n_steps, barrier = args
@@ -259,12 +279,8 @@ def gpu_arm(args, cfg):
             mc.mc_group_sweep(g, args.steps, measure=True)
             stop.record(stream)
             torch.cuda.synchronize()
-        ms = start.elapsed_time(stop)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * n_spins * args.steps / (ms * 1e-3)
+        ms, value = job_time_and_value(start.elapsed_time(stop), n_spins * args.steps, world,
+                                       torch_reduce_max("cuda") if world > 1 else None)
 
         # dominant kernel: the colour pass, timed launch by launch
         avg_ms, launches = mc.mc_group_time_passes(g, max(8, min(args.steps, 200)), measure=True)
