@@ -68,7 +68,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f64() {
-    static const KernelSet k{colour_pass, pair_pass, mlong, measure, profile, "f64"};
+    static const KernelSet k{colour_pass, nullptr, pair_pass, mlong, measure, profile, "f64"};
     return k;
 }
 
