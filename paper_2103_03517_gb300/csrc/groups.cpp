@@ -96,17 +96,15 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         sa[j + 1] = sa[j] + hp.nblocks_site;
         sp[j + 1] = sp[j] + hp.nblocks_pair;
     }
-    // colour passes: the TMA lattices (work-item starts) and the others
-    // (tile starts), each in launch order
-    std::vector<LatDev*> tma, rest;
-    std::vector<uint32_t> st(1, 0), sr(1, 0);
-    uint32_t slot_floats = 0;
+    // colour passes: the FP32 row_fast lattices and the rest (tile starts),
+    // each in launch order
+    std::vector<LatDev*> row, rest;
+    std::vector<uint32_t> srw(1, 0), sr(1, 0);
     for (int j = 0; j < n; ++j) {
         const LatParams& hp = lattices[order[j]]->hp;
-        if (hp.tma_ok) {
-            tma.push_back(all[j]);
-            st.push_back(st.back() + hp.nblocks_tma);
-            slot_floats = std::max(slot_floats, uint32_t(3 * (512 + 2 * hp.Lh)));
+        if (hp.precision == MC_FP32 && hp.row_fast) {
+            row.push_back(all[j]);
+            srw.push_back(srw.back() + hp.nblocks_site);
         } else {
             rest.push_back(all[j]);
             sr.push_back(sr.back() + hp.nblocks_site);
@@ -123,24 +121,23 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
     char* hb = host.data();
     char* db = static_cast<char*>(g->d_mem);
     std::copy(all.begin(), all.end(), reinterpret_cast<LatDev**>(hb));
-    std::copy(tma.begin(), tma.end(), reinterpret_cast<LatDev**>(hb + b_ptr));
+    std::copy(row.begin(), row.end(), reinterpret_cast<LatDev**>(hb + b_ptr));
     std::copy(rest.begin(), rest.end(), reinterpret_cast<LatDev**>(hb + 2 * b_ptr));
     const size_t o0 = 3 * b_ptr;
     std::copy(sa.begin(), sa.end(), reinterpret_cast<uint32_t*>(hb + o0));
     std::copy(sp.begin(), sp.end(), reinterpret_cast<uint32_t*>(hb + o0 + b_idx));
-    std::copy(st.begin(), st.end(), reinterpret_cast<uint32_t*>(hb + o0 + 2 * b_idx));
+    std::copy(srw.begin(), srw.end(), reinterpret_cast<uint32_t*>(hb + o0 + 2 * b_idx));
     std::copy(sr.begin(), sr.end(), reinterpret_cast<uint32_t*>(hb + o0 + 3 * b_idx));
     g->ls.all = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0), n};
     g->ls.pairs = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0 + b_idx), n};
-    g->ls.tma = GroupArgs{reinterpret_cast<LatDev**>(db + b_ptr), reinterpret_cast<uint32_t*>(db + o0 + 2 * b_idx),
-                          int(tma.size())};
+    g->ls.row = GroupArgs{reinterpret_cast<LatDev**>(db + b_ptr), reinterpret_cast<uint32_t*>(db + o0 + 2 * b_idx),
+                          int(row.size())};
     g->ls.rest = GroupArgs{reinterpret_cast<LatDev**>(db + 2 * b_ptr),
                            reinterpret_cast<uint32_t*>(db + o0 + 3 * b_idx), int(rest.size())};
     g->ls.nt_all = sa.back();
     g->ls.nt_pairs = sp.back();
-    g->ls.nt_tma = st.back();
+    g->ls.nt_row = srw.back();
     g->ls.nt_rest = sr.back();
-    g->ls.tma_slot_floats = slot_floats;
     g->ls.sample_level = 1;
     for (int i = 0; i < n; ++i)
         if (lattices[i]->hp.sample_torque) g->ls.sample_level = 2;

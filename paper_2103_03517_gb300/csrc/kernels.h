@@ -13,11 +13,10 @@ struct KernelSet {
     // measure: 0 none, 1 magnetisation and energies, 2 also torques.
     void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
                         cudaStream_t s);
-    // FP32 colour pass with TMA-staged planes over tma_ok lattices (nitems
-    // work items; slot_floats = shared floats of one other-colour plane slot).
+    // FP32 colour pass over row_fast lattices (adjacent site pairs per lane).
     // Null in the FP64 set.
-    void (*tma_pass)(const GroupArgs& g, uint32_t nitems, const void* cone, int colour, int measure,
-                     uint32_t slot_floats, cudaStream_t s);
+    void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
+                     cudaStream_t s);
     // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
                       int measure, cudaStream_t s);
@@ -32,13 +31,13 @@ struct KernelSet {
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every
 // lattice (lattice l owns tiles [start[l], start[l+1])), and for the colour
-// passes the split into TMA lattices and the others.
+// passes the split into FP32 row_fast lattices and the others.
 struct LaunchSet {
     GroupArgs all, pairs;
     uint32_t nt_all = 0, nt_pairs = 0;
-    // colour passes: the tma_ok lattices (work items) and the rest (tiles)
-    GroupArgs tma, rest;
-    uint32_t nt_tma = 0, nt_rest = 0, tma_slot_floats = 0;
+    // colour passes: the FP32 row_fast lattices and the rest (tiles)
+    GroupArgs row, rest;
+    uint32_t nt_row = 0, nt_rest = 0;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
 };
 

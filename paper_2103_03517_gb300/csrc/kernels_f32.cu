@@ -6,7 +6,7 @@
 #endif
 #include "kernels.h"
 #include "pass_impl.cuh"
-#include "tma_pass.cuh"
+#include "row_pass.cuh"
 
 namespace mcgb {
 namespace {
@@ -47,32 +47,17 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
-// 128 bytes of alignment slack + mbarriers + the own-plane buffers + the other-colour slots
-constexpr size_t kTmaSmemMax =
-    256 + kTmaOwnBufs * 3 * kTmaSitesPerPlane * 4 + kTmaOthSlots * 3 * (kTmaSitesPerPlane + 2 * 256) * 4;
-
 template <int MEASURE>
-void tma_pass_t(const GroupArgs& g, uint32_t nitems, const float* cone, int colour, uint32_t slot_floats,
-                cudaStream_t s) {
-    static const uint32_t cap = [] {
-        cudaFuncSetAttribute(tma_pass_kernel<MEASURE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax));
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_pass_kernel<MEASURE>, kTmaThreads, kTmaSmemMax);
-        return uint32_t(sms) * uint32_t(per_sm < 1 ? 1 : per_sm);
-    }();
-    const size_t smem = 256 + size_t(kTmaOwnBufs * 3 * kTmaSitesPerPlane) * 4 + size_t(kTmaOthSlots) * slot_floats * 4;
-    const uint32_t grid = nitems < cap ? nitems : cap;
-    tma_pass_kernel<MEASURE><<<grid, kTmaThreads, smem, s>>>(g, nitems, cone, colour, slot_floats);
+void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(row_pass_kernel<MINB, MEASURE>);
+    row_pass_kernel<MINB, MEASURE><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
 }
 
-void tma_pass(const GroupArgs& g, uint32_t nitems, const void* cone, int colour, int measure, uint32_t slot_floats,
-              cudaStream_t s) {
-    const float* c = static_cast<const float*>(cone);
-    if (measure >= 2) tma_pass_t<2>(g, nitems, c, colour, slot_floats, s);
-    else if (measure == 1) tma_pass_t<1>(g, nitems, c, colour, slot_floats, s);
-    else tma_pass_t<0>(g, nitems, c, colour, slot_floats, s);
+void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, cudaStream_t s) {
+    const R* c = static_cast<const R*>(cone);
+    if (measure >= 2) row_pass_t<2>(g, ntiles, c, colour, s);
+    else if (measure == 1) row_pass_t<1>(g, ntiles, c, colour, s);
+    else row_pass_t<0>(g, ntiles, c, colour, s);
 }
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
@@ -100,7 +85,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, tma_pass, pair_pass, mlong, measure, profile, "f32"};
+    static const KernelSet k{colour_pass, row_pass, pair_pass, mlong, measure, profile, "f32"};
     return k;
 }
 

@@ -83,9 +83,6 @@ struct LatParams {
                             // Lh % 32 == 0, or (FP32) Lh a power of two <= 64 or a
                             // multiple of 64, Nc % 64 == 0: the row paths apply
     int row_lanes;          // FP32 row path: lanes per row group, min(Lh/2, 32)
-    int tma_ok;             // FP32 TMA pass applies (row_fast, Lh in 32..256, Ly % (512/Lh) == 0, Lz % 16 == 0)
-    uint32_t nblocks_tma;   // TMA work items of this lattice
-    const void* tmaps;      // device copy of its tensor maps (TmaMaps) or null
     void* spins;
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null

@@ -136,8 +136,13 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     ls.nt_all = p.nblocks_site;
     ls.nt_pairs = p.nblocks_pair;
     ls.sample_level = 2;
-    ls.rest = ls.all;  // row or general path (no tensor maps in the scratch)
-    ls.nt_rest = ls.nt_all;
+    if (p.row_fast) {  // row or general path (no tensor maps in the scratch)
+        ls.row = ls.all;
+        ls.nt_row = ls.nt_all;
+    } else {
+        ls.rest = ls.all;
+        ls.nt_rest = ls.nt_all;
+    }
     rc = enqueue_sweeps(kernels_f32(), ls, base + kOffCone, n_sweeps, samples ? 1 : 0, false, s, nullptr);
     if (rc) return rc;
     if (samples) {

@@ -327,24 +327,37 @@ __device__ __forceinline__ void add_site(Sums<R>& s, V3<R> S, V3<R> e, bool need
 }
 
 // ------------------------------------------------------------------------
-// Measurement sums of one warp tile, reduced across the warp in a fixed
-// butterfly order and turned into fixed point on lane i for sum i: FP64 at
-// 2^28 (int64), FP32 at 2^22 (an int32 holds a warp tile's sum), so that no
-// FP64 instruction runs on the FP32 path.  Tiles are aligned to the lattice,
-// so the integer totals do not depend on the batch a lattice runs in.
+// Measurement sums of one warp tile as fixed point on lane i for sum i.
+// FP64: reduced across the warp in a fixed butterfly order, then rounded at
+// 2^28 (int64).  FP32: each lane rounds its own part at 2^22 and the warp
+// adds the integers (one redux per sum), so that no FP64 instruction runs on
+// the FP32 path.  A lane's part covers at most two sites of each colour, so
+// it is below 16 in magnitude (the bond sum S.h is at most 6 a site) and the
+// warp total fits an int32.  Tiles are aligned to the lattice and integer
+// sums commute, so the totals do not depend on the batch a lattice runs in.
 // ------------------------------------------------------------------------
 template <typename R, int NS = kNumSums>
 __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
-    R mine = R(0);
+    if constexpr (kIsF64<R>) {
+        R mine = R(0);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        R v = s.v[i];
+        for (int i = 0; i < NS; ++i) {
+            R v = s.v[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == i) mine = v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == i) mine = v;
+        }
+        return __double2ll_rn(mine * kFixScale);
+    } else {
+        static_assert(kSitesPerThreadF32 <= 2, "a lane's FP32 sample part must stay below 16");
+        int mine = 0;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const int t = __reduce_add_sync(0xffffffffu, __float2int_rn(s.v[i] * float(kFixScaleF32)));
+            if (lane == i) mine = t;
+        }
+        return (long long)mine;
     }
-    if constexpr (kIsF64<R>) return __double2ll_rn(mine * kFixScale);
-    else return (long long)__float2int_rn(mine * float(kFixScaleF32));
 }
 
 // ------------------------------------------------------------------------
@@ -557,89 +570,11 @@ __device__ __forceinline__ void row_segments(const LatParams& p, const Par<R>& p
 }
 
 // ------------------------------------------------------------------------
-// FP32 row path (row_fast lattices in FP32): lane L of a 64-site tile takes
-// the two adjacent colour indices q = q0 + 2L and q + 1 of one row, so every
-// spin is read as a float2 (one load instruction per component for both
-// sites).  Rows of Lh <= 64 sites per colour are covered by groups of
-// G = Lh/2 lanes (row_lanes), rows of Lh > 64 by segments of 64.  The other
-// colour's spins at k and k+1 give three of the four x neighbours of the
-// pair; the fourth, at k-1 or k+2, is the neighbouring lane's pair, taken by
-// a warp shuffle inside the row group (wrapping the row) or, at the ends of
-// a 64-site segment of a longer row, loaded.  The neighbour sum keeps the
-// order -x, +x, -y, +y, -z, +z.
-// ------------------------------------------------------------------------
-__device__ __forceinline__ float2 ld2(const float* a, uint32_t i) {
-    return *reinterpret_cast<const float2*>(a + i);
-}
-
-__device__ __forceinline__ void row_pairs(const LatParams& p, const float* s, int colour, uint32_t tile_q0, int lane,
-                                          V3<float> S[2], V3<float> h[2], V3<float> O[2], uint32_t site[2],
-                                          uint32_t qv[2]) {
-    const int other = colour ^ 1;
-    const uint32_t stride = p.stride;
-    const float* own = s + size_t(3 * colour) * stride;
-    const float* oth = s + size_t(3 * other) * stride;
-    const uint32_t Lh = uint32_t(p.Lh), Ly = uint32_t(p.Ly), Lz = uint32_t(p.Lz), plane = Lh * Ly;
-    const uint32_t q = tile_q0 + 2u * uint32_t(lane);
-    const uint32_t row = fast_div(q, p.div_lh);
-    const uint32_t k = q - row * Lh;
-    const uint32_t z = fast_div(row, p.div_ly);
-    const uint32_t y = row - z * Ly;
-    const bool xoff = ((y + z + uint32_t(colour)) & 1u) != 0;
-    const int G = p.row_lanes;
-    const int gbase = lane & ~(G - 1);
-    const int left = gbase | ((lane - 1) & (G - 1));
-    const int right = gbase | ((lane + 1) & (G - 1));
-    const float2 sx = ld2(own, q), sy = ld2(own + stride, q), sz = ld2(own + 2 * size_t(stride), q);
-    const float2 ox = ld2(oth, q), oy = ld2(oth + stride, q), oz = ld2(oth + 2 * size_t(stride), q);
-    const uint32_t qym = y > 0 ? q - Lh : q + Lh * (Ly - 1);
-    const uint32_t qyp = y + 1 < Ly ? q + Lh : q - Lh * (Ly - 1);
-    const uint32_t qzm = z > 0 ? q - plane : q + plane * (Lz - 1);
-    const uint32_t qzp = z + 1 < Lz ? q + plane : q - plane * (Lz - 1);
-    const float2 ymx = ld2(oth, qym), ymy = ld2(oth + stride, qym), ymz = ld2(oth + 2 * size_t(stride), qym);
-    const float2 ypx = ld2(oth, qyp), ypy = ld2(oth + stride, qyp), ypz = ld2(oth + 2 * size_t(stride), qyp);
-    const float2 zmx = ld2(oth, qzm), zmy = ld2(oth + stride, qzm), zmz = ld2(oth + 2 * size_t(stride), qzm);
-    const float2 zpx = ld2(oth, qzp), zpy = ld2(oth + stride, qzp), zpz = ld2(oth + 2 * size_t(stride), qzp);
-    // other colour at k - 1 (left lane's second) and k + 2 (right lane's first)
-    V3<float> lft{__shfl_sync(0xffffffffu, ox.y, left), __shfl_sync(0xffffffffu, oy.y, left),
-                  __shfl_sync(0xffffffffu, oz.y, left)};
-    V3<float> rgt{__shfl_sync(0xffffffffu, ox.x, right), __shfl_sync(0xffffffffu, oy.x, right),
-                  __shfl_sync(0xffffffffu, oz.x, right)};
-    if (Lh > 64u) {  // ends of a 64-site segment of a longer row
-        if (lane == 0) {
-            const uint32_t qe = k == 0 ? q + Lh - 1 : q - 1;
-            lft = V3<float>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
-        }
-        if (lane == 31) {
-            const uint32_t qe = k + 2 == Lh ? q + 2 - Lh : q + 2;
-            rgt = V3<float>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
-        }
-    }
-    const V3<float> o0{ox.x, oy.x, oz.x}, o1{ox.y, oy.y, oz.y};
-    const V3<float> xm0 = xoff ? o0 : lft, xp0 = xoff ? o1 : o0;
-    const V3<float> xm1 = xoff ? o1 : o0, xp1 = xoff ? rgt : o1;
-    h[0].x = ((((xm0.x + xp0.x) + ymx.x) + ypx.x) + zmx.x) + zpx.x;
-    h[0].y = ((((xm0.y + xp0.y) + ymy.x) + ypy.x) + zmy.x) + zpy.x;
-    h[0].z = ((((xm0.z + xp0.z) + ymz.x) + ypz.x) + zmz.x) + zpz.x;
-    h[1].x = ((((xm1.x + xp1.x) + ymx.y) + ypx.y) + zmx.y) + zpx.y;
-    h[1].y = ((((xm1.y + xp1.y) + ymy.y) + ypy.y) + zmy.y) + zpy.y;
-    h[1].z = ((((xm1.z + xp1.z) + ymz.y) + ypz.y) + zmz.y) + zpz.y;
-    S[0] = V3<float>{sx.x, sy.x, sz.x};
-    S[1] = V3<float>{sx.y, sy.y, sz.y};
-    O[0] = o0;
-    O[1] = o1;
-    const uint32_t x0 = uint32_t(xoff) + 2u * k;
-    site[0] = x0 + uint32_t(p.Lx) * row;
-    site[1] = site[0] + 2u;
-    qv[0] = q;
-    qv[1] = q + 1;
-}
-
-// ------------------------------------------------------------------------
 // Colour pass of Table A1, batched over the lattices of a group (MEASURE:
 // black pass of a measurement sweep: 1 = magnetisation and energies, 2 = also
-// torques).  row_fast lattices take a row path (FP32: adjacent pairs, FP64:
-// 32-site segments), the others the general path.  Every lane updates V
+// torques).  FP64 row_fast lattices take the row path of 32-site segments,
+// the others the general path; FP32 row_fast lattices are launched on
+// row_pass_kernel instead.  Every lane updates V
 // adjacent sites per warp tile; the loads of all V sites are issued before
 // any of them is computed.  colour 1 with measure != 0 also takes the sample:
 // each black site adds itself, the red site with the same colour index, and
@@ -673,14 +608,10 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
             V3<R> S[V], h[V], e[V], Sr[V];
             uint32_t site[V], qv[V];
             bool act[V], mov[V];
-            if (p.row_fast) {
-                if constexpr (!kIsF64<R> && V == 2) {
-                    row_pairs(p, s, colour, base - uint32_t(lane), lane, S, h, Sr, site, qv);
-                } else {
-                    row_segments<R, V>(p, par, s, colour, base - uint32_t(lane), lane, S, h, e, Sr, site);
+            if (kIsF64<R> && p.row_fast) {  // FP32 row_fast lattices take row_pass_kernel
+                row_segments<R, V>(p, par, s, colour, base - uint32_t(lane), lane, S, h, e, Sr, site);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) qv[v] = base + uint32_t(32 * v);
-                }
+                for (int v = 0; v < V; ++v) qv[v] = base + uint32_t(32 * v);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     act[v] = true;

@@ -1,6 +1,5 @@
 // runtime.cpp -- lattices, groups, observables and checkpoints of libmc
 // (the C ABI of include/mc.h, except the server).
-#include <cuda.h>  // tensor-map types; the driver function is reached through the runtime
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -107,61 +106,6 @@ static int feistel_half_bits(uint32_t n) {
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// ------------------------------------------------------------ tensor maps
-constexpr int kTmaSitesPerPlaneHost = 512;  // sites of one brick plane (BY * Lh)
-constexpr int kTmaZChunkHost = 16;          // planes per TMA work item
-constexpr size_t kTmaMapBytes = 6 * sizeof(CUtensorMap);
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_tiled() {
-    static const EncodeTiledFn fn = [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess || q != cudaDriverEntryPointSuccess)
-            return EncodeTiledFn(nullptr);
-        return reinterpret_cast<EncodeTiledFn>(f);
-    }();
-    return fn;
-}
-
-// Whether the FP32 TMA colour pass applies: a row_fast FP32 lattice whose
-// rows hold 32..256 sites per colour (a power of two), with whole bricks of
-// 512 / Lh rows in y and whole 16-plane chunks in z.
-static int tma_eligible(const LatParams& p) {
-    if (p.precision != MC_FP32 || !p.row_fast) return 0;
-    if (p.Lh < 32 || p.Lh > 256 || (p.Lh & (p.Lh - 1))) return 0;
-    const int by = kTmaSitesPerPlaneHost / p.Lh;
-    return (p.Ly % by == 0 && p.Lz % kTmaZChunkHost == 0) ? 1 : 0;
-}
-
-// Six tensor maps over the colour arrays, viewed as [3][Lz][Ly][Lh] floats:
-// per colour the own-plane box (Lh, BY, 1, 3), one component of the brick's
-// rows (Lh, BY, 1, 1) and one row (Lh, 1, 1, 1).
-static int encode_maps(const LatParams& p, CUtensorMap out[6]) {
-    EncodeTiledFn fn = encode_tiled();
-    if (!fn) return fail(MC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    const int by = kTmaSitesPerPlaneHost / p.Lh;
-    const cuuint64_t dims[4] = {cuuint64_t(p.Lh), cuuint64_t(p.Ly), cuuint64_t(p.Lz), 3};
-    const cuuint64_t strides[3] = {cuuint64_t(p.Lh) * 4, cuuint64_t(p.Lh) * p.Ly * 4, cuuint64_t(p.stride) * 4};
-    const cuuint32_t boxes[3][4] = {{cuuint32_t(p.Lh), cuuint32_t(by), 1, 3},
-                                    {cuuint32_t(p.Lh), cuuint32_t(by), 1, 1},
-                                    {cuuint32_t(p.Lh), 1, 1, 1}};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int c = 0; c < 2; ++c)
-        for (int b = 0; b < 3; ++b) {
-            void* base = static_cast<float*>(p.spins) + size_t(3 * c) * p.stride;
-            const CUresult r = fn(&out[3 * c + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, boxes[b],
-                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return fail(MC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
-        }
-    return MC_OK;
-}
-
 // Whether a lattice takes the row paths of the colour pass (see LatParams).
 int row_fast(const LatParams& p, bool film) {
     if (film || p.bc[0] != MC_PERIODIC || p.bc[1] != MC_PERIODIC || p.bc[2] != MC_PERIODIC) return 0;
@@ -190,10 +134,8 @@ size_t lattice_bytes(const mc_desc* d) {
     const int cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
     b += align256(size_t(cap) * kRingWords * 8);
     b += align256(3 * size_t(d->dims[0]) * 8);
-    // launch tables of the lattice alone: lattice pointer, site, pair and
-    // TMA-item starts; tensor maps
-    b += align256(sizeof(void*)) + 3 * align256(2 * sizeof(uint32_t));
-    b += align256(kTmaMapBytes);
+    // launch tables of the lattice alone: lattice pointer, site and pair starts
+    b += align256(sizeof(void*)) + 2 * align256(2 * sizeof(uint32_t));
     return b;
 }
 
@@ -396,13 +338,6 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     h->d_group_lats = reinterpret_cast<LatDev**>(take(sizeof(void*)));
     h->d_group_start = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
     h->d_group_start_pair = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
-    h->d_group_start_tma = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
-    void* d_maps = take(kTmaMapBytes);
-    p.tma_ok = tma_eligible(p);
-    p.nblocks_tma = p.tma_ok ? uint32_t(p.Ly / (kTmaSitesPerPlaneHost / p.Lh)) * uint32_t(p.Lz / kTmaZChunkHost) : 0;  // bricks x z chunks
-    CUtensorMap maps[6];
-    if (p.tma_ok && encode_maps(p, maps) != MC_OK) p.tma_ok = 0;  // fall back to the row path
-    p.tmaps = p.tma_ok ? d_maps : nullptr;
     if (size_t(cur - static_cast<char*>(h->d_base)) > h->bytes) {
         cudaFree(h->d_base);
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -457,9 +392,6 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     up(h->d_group_lats, &one, sizeof one);
     up(h->d_group_start, st_site, sizeof st_site);
     up(h->d_group_start_pair, st_pair, sizeof st_pair);
-    const uint32_t st_tma[2] = {0, p.nblocks_tma};
-    up(h->d_group_start_tma, st_tma, sizeof st_tma);
-    if (p.tma_ok) up(d_maps, maps, kTmaMapBytes);
     trace("create: uploads queued");
     if (rc == MC_OK) {
         const double* c64;
@@ -488,10 +420,9 @@ LaunchSet single_launch_set(mc_lattice* h) {
     ls.nt_all = h->hp.nblocks_site;
     ls.nt_pairs = h->hp.nblocks_pair;
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
-    if (h->hp.tma_ok) {
-        ls.tma = GroupArgs{h->d_group_lats, h->d_group_start_tma, 1};
-        ls.nt_tma = h->hp.nblocks_tma;
-        ls.tma_slot_floats = uint32_t(3 * (kTmaSitesPerPlaneHost + 2 * h->hp.Lh));
+    if (h->hp.precision == MC_FP32 && h->hp.row_fast) {
+        ls.row = ls.all;
+        ls.nt_row = ls.nt_all;
     } else {
         ls.rest = ls.all;
         ls.nt_rest = ls.nt_all;
@@ -517,7 +448,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto colour_pass = [&](int colour, int meas) {
-        if (ls.nt_tma) k.tma_pass(ls.tma, ls.nt_tma, cone, colour, meas, ls.tma_slot_floats, s);
+        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, s);
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
     for (int i = 0; i < n; ++i) {

@@ -21,7 +21,6 @@ struct mc_lattice {
     mcgb::LatDev** d_group_lats = nullptr;   // launch tables of the lattice alone
     uint32_t* d_group_start = nullptr;
     uint32_t* d_group_start_pair = nullptr;
-    uint32_t* d_group_start_tma = nullptr;
     const void* cone = nullptr;   // c(theta) table of the precision
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;

@@ -318,10 +318,10 @@ def test_group_constrained_equals_alone_bitwise():
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (8, 8, 8), (4, 4, 8), (64, 32, 8), (128, 8, 4), (256, 4, 4),
                                   (384, 2, 2),
-                                  # TMA pass (rows of 32..256 sites per colour, whole bricks and 16-plane chunks)
+                                  # rows of 32..256 sites per colour on larger bricks
                                   (64, 64, 16), (128, 16, 32), (128, 8, 16), (256, 8, 16), (512, 4, 16), (512, 2, 32)])
 def test_fp32_row_path_matches_general_path(dims):
-    """FP32: a periodic lattice takes the row path (or the TMA pass); the same lattice with an
+    """FP32: a periodic lattice takes the row kernel; the same lattice with an
     all-ones bond mask (identical physics) takes the general path.  Both key
     the same draws to the same sites, so one sweep gives the same spins up to
     FP32 rounding; a wrong neighbour would change many sites by O(1)."""
