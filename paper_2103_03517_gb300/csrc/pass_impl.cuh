@@ -811,90 +811,88 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
                                                            int colour, int finalize, int measure) {
-    const WarpChunk wc = warp_chunk(ntiles);
-    const int lane = wc.lane;
+    // Tiles in grid-stride order: at any moment the warps hold a window of
+    // about one tile each, one or two lattices of the batch, so that the
+    // random gathers of partners and their neighbours stay in L2.
+    const int lane = int(threadIdx.x & 31);
     const int other = colour ^ 1;
-    uint32_t tile = wc.begin;
-    int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
-    while (tile < wc.end) {
+    const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
+    int l = 0;
+    for (uint32_t tile = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
+        while (__ldg(&g.start[l + 1]) <= tile) ++l;
         LatDev* L = g.lats[l];
         const LatParams& p = L->p;
-        const uint32_t t0 = __ldg(&g.start[l]);
-        const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
-        const uint32_t run = t1 - tile;
+        const uint32_t pr = (tile - __ldg(&g.start[l])) * 32u + uint32_t(lane);
         const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
-        const float fml = float(ML);
-        const Par<R> par = load_par<R>(p);
-        const R c = cone[L->st.theta];
-        const uint32_t sweep = L->st.sweep;
-        R* __restrict__ s = static_cast<R*>(p.spins);
-        const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
         unsigned nacc = 0;
         if (!(ML > 0.0)) {
             if (lane == 0) atomicCAS(&L->st.error, 0, -5);
-            tile = t1;
+        } else if (pr < p.n_pairs) {
+            const float fml = float(ML);
+            const Par<R> par = load_par<R>(p);
+            const R c = cone[L->st.theta];
+            const uint32_t sweep = L->st.sweep;
+            R* __restrict__ s = static_cast<R*>(p.spins);
+            const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
+            [&] {
+                const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
+                const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+                const V3<R> Si = load_spin(s, p.stride, colour, qi);
+                const V3<R> Sj = load_spin(s, p.stride, colour, qj);
+                const V3<R> hi = rotate(par.Rm, Si);
+                const V3<R> hj = rotate(par.Rm, Sj);
+                V3<R> hni;
+                R P;
+                if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) return;
+                const R ynj = (hj.y + hi.y) - hni.y;
+                const R znj = (hj.z + hi.z) - hni.z;
+                const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
+                if (!(t > R(0))) return;
+                R xnj = sqrt(t);
+                if (hj.x < R(0)) xnj = -xnj;
+                bool ok;
+                R rM;
+                if constexpr (kIsF64<R>) {
+                    const double MLn = ML + hni.x + xnj - hi.x - hj.x;
+                    ok = MLn > 0.0;
+                    const double ratio = MLn / ML;
+                    rM = ratio * ratio;
+                } else {
+                    // FP32 spins: the change of M_L is evaluated in FP32 and
+                    // applied to the FP64 M_L as (1 + delta / M_L)^2.
+                    const float delta = ((hni.x + xnj) - hi.x) - hj.x;
+                    ok = fml + delta > 0.0f;
+                    const float ratio = 1.0f + delta / fml;
+                    rM = ratio * ratio;
+                }
+                if (!ok) return;
+                const V3<R> hnj{xnj, ynj, znj};
+                const V3<R> Sni = rotate_back(par.Rm, hni);
+                const V3<R> Snj = rotate_back(par.Rm, hnj);
+                const Geo gi = geometry(p, colour, qi);
+                const Geo gj = geometry(p, colour, qj);
+                uint32_t nqi[6], nqj[6];
+                const uint32_t pi_ = neighbours(p, gi, colour, nqi);
+                const uint32_t pj_ = neighbours(p, gj, colour, nqj);
+                const V3<R> h_i = neighbour_sum(s, p.stride, other, nqi, pi_);
+                const V3<R> h_j = neighbour_sum(s, p.stride, other, nqj, pj_);
+                const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
+                const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
+                const R dE = dEi + dEj;
+                R r = rM;
+                r = r * (fabs(hj.x) / fabs(xnj));
+                if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
+                else r = r * __expf(-__fdividef(dE, par.T));
+                if (P < r) {
+                    store_spin(s, p.stride, colour, qi, Sni);
+                    store_spin(s, p.stride, colour, qj, Snj);
+                    nacc += 2;
+                }
+            }();
         }
-        for (; tile < t1; ++tile) {
-            const uint32_t pr = (tile - t0) * 32u + uint32_t(lane);
-            if (pr >= p.n_pairs) continue;
-            const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
-            const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
-            const V3<R> Si = load_spin(s, p.stride, colour, qi);
-            const V3<R> Sj = load_spin(s, p.stride, colour, qj);
-            const V3<R> hi = rotate(par.Rm, Si);
-            const V3<R> hj = rotate(par.Rm, Sj);
-            V3<R> hni;
-            R P;
-            if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) continue;
-            const R ynj = (hj.y + hi.y) - hni.y;
-            const R znj = (hj.z + hi.z) - hni.z;
-            const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
-            if (!(t > R(0))) continue;
-            R xnj = sqrt(t);
-            if (hj.x < R(0)) xnj = -xnj;
-            bool ok;
-            R rM;
-            if constexpr (kIsF64<R>) {
-                const double MLn = ML + hni.x + xnj - hi.x - hj.x;
-                ok = MLn > 0.0;
-                const double ratio = MLn / ML;
-                rM = ratio * ratio;
-            } else {
-                // FP32 spins: the change of M_L is evaluated in FP32 and
-                // applied to the FP64 M_L as (1 + delta / M_L)^2.
-                const float delta = ((hni.x + xnj) - hi.x) - hj.x;
-                ok = fml + delta > 0.0f;
-                const float ratio = 1.0f + delta / fml;
-                rM = ratio * ratio;
-            }
-            if (!ok) continue;
-            const V3<R> hnj{xnj, ynj, znj};
-            const V3<R> Sni = rotate_back(par.Rm, hni);
-            const V3<R> Snj = rotate_back(par.Rm, hnj);
-            const Geo gi = geometry(p, colour, qi);
-            const Geo gj = geometry(p, colour, qj);
-            uint32_t nqi[6], nqj[6];
-            const uint32_t pi_ = neighbours(p, gi, colour, nqi);
-            const uint32_t pj_ = neighbours(p, gj, colour, nqj);
-            const V3<R> h_i = neighbour_sum(s, p.stride, other, nqi, pi_);
-            const V3<R> h_j = neighbour_sum(s, p.stride, other, nqj, pj_);
-            const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
-            const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
-            const R dE = dEi + dEj;
-            R r = rM;
-            r = r * (fabs(hj.x) / fabs(xnj));
-            if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
-            else r = r * __expf(-__fdividef(dE, par.T));
-            if (P < r) {
-                store_spin(s, p.stride, colour, qi, Sni);
-                store_spin(s, p.stride, colour, qj, Snj);
-                nacc += 2;
-            }
-        }
-        publish(L->st, lane, nacc, false, 0, colour, run, p.nblocks_pair, [&] {
+        publish(L->st, lane, nacc, false, 0, colour, 1, p.nblocks_pair, [&] {
             if (finalize) finalize_sweep(p, L->st, measure, true);
         });
-        ++l;
     }
 }
 

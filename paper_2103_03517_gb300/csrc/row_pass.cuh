@@ -65,14 +65,15 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
         }
     }
     const V3<float> o0{v[3].x, v[4].x, v[5].x}, o1{v[3].y, v[4].y, v[5].y};
-    const V3<float> xm0 = xoff ? o0 : lft, xp0 = xoff ? o1 : o0;
-    const V3<float> xm1 = xoff ? o1 : o0, xp1 = xoff ? rgt : o1;
-    h[0].x = ((((xm0.x + xp0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
-    h[0].y = ((((xm0.y + xp0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
-    h[0].z = ((((xm0.z + xp0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
-    h[1].x = ((((xm1.x + xp1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
-    h[1].y = ((((xm1.y + xp1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
-    h[1].z = ((((xm1.z + xp1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
+    // x neighbours: site 0 has o0 and (xoff ? o1 : lft), site 1 has o1 and
+    // (xoff ? rgt : o0); the -x + +x sum is the same either way round
+    const V3<float> a0 = xoff ? o1 : lft, a1 = xoff ? rgt : o0;
+    h[0].x = ((((o0.x + a0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
+    h[0].y = ((((o0.y + a0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
+    h[0].z = ((((o0.z + a0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
+    h[1].x = ((((o1.x + a1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
+    h[1].y = ((((o1.y + a1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
+    h[1].z = ((((o1.z + a1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
     S[0] = V3<float>{v[0].x, v[1].x, v[2].x};
     S[1] = V3<float>{v[0].y, v[1].y, v[2].y};
     O[0] = o0;
