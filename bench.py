@@ -3,12 +3,13 @@
 Workload (one step = one measurement sweep of the whole batch: red pass, black
 pass with the fused sample, cone adaptation, for every lattice):
 32 independent periodic simple-cubic lattices, L = 16, 32, 64, 128 cycled,
-T_i = 0.05 (i + 1), J = 1, K_u = 0.01 along z, FP32 spins with FP64
-accumulators, 19,169,280 spins in total (230 MB of spins: larger than L2, so
+T_i = 0.05 (i + 1), J = 1, K_u = 0.01 along z, FP32 spins with fixed-point
+sample sums, 19,169,280 spins in total (230 MB of spins: larger than L2, so
 no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--side all|none|fp64|constrained|serving] [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
 `--impl reference` times the serial FP64 CPU oracle on the host cores instead.
@@ -36,9 +37,10 @@ UNIT = "spin-updates/s"
 BYTES_PER_UPDATE = 24          # FP32: read + write 3 x 4 B of every spin once per sweep
 FALLBACK_HBM_GBS = 6800.0
 LATSTATE_BYTES = 384           # device state block read back by mc_measure
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "colour_pass_f32_batched_mT.txt")
-KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/pass_impl.cuh", "paper_2103_03517_gb300/csrc/device_common.cuh",
-                  "paper_2103_03517_gb300/csrc/kernels_f32.cu", "paper_2103_03517_gb300/csrc/mc_internal.h"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "row_pass_f32_batched_mT.txt")
+KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/row_pass.cuh", "paper_2103_03517_gb300/csrc/pass_impl.cuh",
+                  "paper_2103_03517_gb300/csrc/device_common.cuh", "paper_2103_03517_gb300/csrc/kernels_f32.cu",
+                  "paper_2103_03517_gb300/csrc/mc_internal.h"]
 
 
 def workload_config():
@@ -46,7 +48,7 @@ def workload_config():
     n = sum(s.N for s in specs)
     return specs, n, {
         "workload": "batched m(T) sweep: 32 periodic sc lattices 16^3/32^3/64^3/128^3 cycled, "
-                    "T = 0.05..1.60, J = 1, K_u = 0.01 z; FP32 spins, FP64 accumulators; "
+                    "T = 0.05..1.60, J = 1, K_u = 0.01 z; FP32 spins, fixed-point sample sums; "
                     "one measurement sweep per step (sample: m vector and energy parts of every lattice)",
         "lattices": len(specs),
         "spins": n,
@@ -63,7 +65,7 @@ def kernel_hash() -> str:
 
 
 def read_traffic():
-    """Per-launch DRAM bytes of the colour-pass kernel from the committed ncu
+    """Per-launch DRAM bytes of the row colour-pass kernel from the committed ncu
     summary, or None if absent or taken on a different kernel source."""
     try:
         kv = {}
@@ -311,9 +313,11 @@ def gpu_arm(args, cfg):
                "h2d_bytes_per_step": int(sum(sizes)), "d2h_bytes_per_step": LATSTATE_BYTES * len(hs)}
 
         extra = {}
-        if rank == 0 and not args.quick:
-            extra = secondary(mc, torch, stream, local)
-            extra["serving"] = serving(mc)
+        side = "none" if args.quick else args.side
+        if rank == 0 and side != "none":
+            extra = secondary(mc, torch, stream, local, side)
+            if side in ("all", "serving"):
+                extra["serving"] = serving(mc)
         mc.mc_group_destroy(g)
         for h in hs:
             mc.mc_destroy(h)
@@ -325,7 +329,7 @@ def gpu_arm(args, cfg):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "colour_pass_kernel<float>", "launch_avg_ms": avg_ms,
+                         "kernel": "row_pass_kernel<float>", "launch_avg_ms": avg_ms,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -338,10 +342,19 @@ def gpu_arm(args, cfg):
         torch.distributed.destroy_process_group()
 
 
-def secondary(mc, torch, stream, dev):
+def secondary(mc, torch, stream, dev, side="all"):
     """Side measurements reported with the headline: the same batch as 32
     sequential one-lattice FP64 runs (per-launch baseline of the batched
     path), and the constrained workload (80 x 64^3 pair sweeps)."""
+    out = {}
+    if side in ("all", "fp64"):
+        out.update(fp64_per_lattice(mc, torch, stream, dev))
+    if side in ("all", "constrained"):
+        out.update(constrained(mc, torch, stream, dev))
+    return out
+
+
+def fp64_per_lattice(mc, torch, stream, dev):
     out = {}
     specs = workloads.config2()
     n = sum(s.N for s in specs)
@@ -361,6 +374,13 @@ def secondary(mc, torch, stream, dev):
                                "workload": "same 32 lattices, FP64, one lattice per launch sequence"}
     for h in hs:
         mc.mc_destroy(h)
+    return out
+
+
+def constrained(mc, torch, stream, dev):
+    out = {}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweeps = 10
     runs = workloads.config3()
     hs = []
     for spec, th, ph in runs:
@@ -449,7 +469,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
+    ap.add_argument("--side", default="all", choices=["all", "none", "fp64", "constrained", "serving"],
+                    help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
