@@ -187,8 +187,10 @@ MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_d
             return fail(MC_ERR_ARG, "constraint angle %zu invalid", i);
         for (int a = 0; a < 3; ++a)
             if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
+        int rc = ensure_aos(h);
+        if (rc) return rc;
         constraint_frame(theta_c_deg[i], phi_c_deg[i], h->hp.R);
-        int rc = upload_params(h);  // on the group stream (members adopt it)
+        rc = upload_params(h);  // on the group stream (members adopt it)
         if (rc) return rc;
     }
     return group_run(g, n_sweeps, measure ? 1 : 0, true);

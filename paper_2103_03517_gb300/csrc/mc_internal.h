@@ -90,6 +90,10 @@ struct LatParams {
     double* ring;           // [ring_cap][kRingWords]
     int ring_cap;
     long long* profile;     // [3][Lx] fixed-point sums
+    void* aos;              // constrained sweeps: [2][stride] (x, y, z, 0) copy of the
+                            // spins (Spin4), written by mlong_kernel at the start of each
+                            // sweep and kept in step by the pair passes; null until the
+                            // lattice's first constrained sweep
     double J, Ku, e[3], Kc, H[3], T;
     float fJ, fKu, fe[3], fKc, fH[3], fT;
     double R[9];            // constraint frame rows e1 = e_C, e2, e3

@@ -106,6 +106,13 @@ __device__ __forceinline__ void store_spin(R* s, uint32_t stride, int colour, ui
     b[2 * size_t(stride) + q] = v.z;
 }
 
+// (x, y, z, 0) of one site: the packed spin copy of constrained sweeps, one
+// 16-byte (FP32) or 32-byte (FP64) load per site.
+template <typename R>
+struct alignas(4 * sizeof(R)) Spin4 {
+    R x, y, z, w;
+};
+
 // Sum of the present other-colour neighbours, accumulated -x,+x,-y,+y,-z,+z.
 template <typename R>
 __device__ __forceinline__ V3<R> neighbour_sum(const R* s, uint32_t stride, int other, const uint32_t nq[6],
@@ -118,6 +125,22 @@ __device__ __forceinline__ V3<R> neighbour_sum(const R* s, uint32_t stride, int 
             h.x = h.x + b[nq[d]];
             h.y = h.y + b[stride + nq[d]];
             h.z = h.z + b[2 * size_t(stride) + nq[d]];
+        }
+    }
+    return h;
+}
+
+// The same sum from the packed copy of the other colour.
+template <typename R>
+__device__ __forceinline__ V3<R> neighbour_sum4(const Spin4<R>* a, const uint32_t nq[6], uint32_t present) {
+    V3<R> h{R(0), R(0), R(0)};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (present & (1u << d)) {
+            const Spin4<R> v = a[nq[d]];
+            h.x = h.x + v.x;
+            h.y = h.y + v.y;
+            h.z = h.z + v.z;
         }
     }
     return h;
@@ -705,7 +728,9 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
 // ------------------------------------------------------------------------
 // Exact M_L = sum_i S_i . e_C (Table A2) as fixed point, order independent:
 // FP64 terms t give q = trunc(t 2^52) split as hi 2^26 + lo; FP32 terms give
-// q = trunc(t 2^30) (an int32).  Site tiles as in the colour pass.
+// q = trunc(t 2^30) (an int32).  Site tiles as in the colour pass.  It also
+// writes the packed (x, y, z, 0) copy of both colours that the pair passes
+// of the same sweep gather from.
 // ------------------------------------------------------------------------
 template <typename R, int V>
 __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t ntiles) {
@@ -719,6 +744,7 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
         const uint32_t t0 = __ldg(&g.start[l]);
         const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
         const R* s = static_cast<const R*>(p.spins);
+        Spin4<R>* a4 = static_cast<Spin4<R>*>(p.aos);
         R e1[3];
         if constexpr (kIsF64<R>) { e1[0] = p.R[0]; e1[1] = p.R[1]; e1[2] = p.R[2]; }
         else { e1[0] = p.fR[0]; e1[1] = p.fR[1]; e1[2] = p.fR[2]; }
@@ -731,6 +757,7 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
                 if (q >= p.Nc) continue;
                 for (int colour = 0; colour < 2; ++colour) {
                     const V3<R> S = load_spin(s, p.stride, colour, q);
+                    if (a4) a4[size_t(colour) * p.stride + q] = Spin4<R>{S.x, S.y, S.z, R(0)};
                     const R t = e1[0] * S.x + e1[1] * S.y + e1[2] * S.z;
                     if constexpr (kIsF64<R>) {
                         const long long w = (long long)(t * 0x1p52);
@@ -806,7 +833,9 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // y'_j^2 - z'_j^2).  The pair is accepted iff
 // P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is the exact value
 // from mlong_kernel, fixed for the whole iteration.  Rejected without a
-// test: 16 failed disk draws, t <= 0, M'_L <= 0.
+// test: 16 failed disk draws, t <= 0, M'_L <= 0.  Spins are gathered from the
+// packed copy (one sector per site instead of one per component); accepted
+// moves are written to the spins and to the copy of the pass's colour.
 // ------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
@@ -824,9 +853,12 @@ __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t
         const LatParams& p = L->p;
         const uint32_t pr = (tile - __ldg(&g.start[l])) * 32u + uint32_t(lane);
         const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
+        Spin4<R>* a4 = static_cast<Spin4<R>*>(p.aos);
         unsigned nacc = 0;
         if (!(ML > 0.0)) {
             if (lane == 0) atomicCAS(&L->st.error, 0, -5);
+        } else if (!a4) {
+            if (lane == 0) atomicCAS(&L->st.error, 0, -6);
         } else if (pr < p.n_pairs) {
             const float fml = float(ML);
             const Par<R> par = load_par<R>(p);
@@ -837,8 +869,11 @@ __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t
             [&] {
                 const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
                 const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
-                const V3<R> Si = load_spin(s, p.stride, colour, qi);
-                const V3<R> Sj = load_spin(s, p.stride, colour, qj);
+                Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
+                const Spin4<R>* oth4 = a4 + size_t(other) * p.stride;
+                const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
+                const V3<R> Si{si4.x, si4.y, si4.z};
+                const V3<R> Sj{sj4.x, sj4.y, sj4.z};
                 const V3<R> hi = rotate(par.Rm, Si);
                 const V3<R> hj = rotate(par.Rm, Sj);
                 V3<R> hni;
@@ -874,8 +909,8 @@ __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t
                 uint32_t nqi[6], nqj[6];
                 const uint32_t pi_ = neighbours(p, gi, colour, nqi);
                 const uint32_t pj_ = neighbours(p, gj, colour, nqj);
-                const V3<R> h_i = neighbour_sum(s, p.stride, other, nqi, pi_);
-                const V3<R> h_j = neighbour_sum(s, p.stride, other, nqj, pj_);
+                const V3<R> h_i = neighbour_sum4(oth4, nqi, pi_);
+                const V3<R> h_j = neighbour_sum4(oth4, nqj, pj_);
                 const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
                 const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
                 const R dE = dEi + dEj;
@@ -886,6 +921,8 @@ __global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t
                 if (P < r) {
                     store_spin(s, p.stride, colour, qi, Sni);
                     store_spin(s, p.stride, colour, qj, Snj);
+                    own4[qi] = Spin4<R>{Sni.x, Sni.y, Sni.z, R(0)};
+                    own4[qj] = Spin4<R>{Snj.x, Snj.y, Snj.z, R(0)};
                     nacc += 2;
                 }
             }();

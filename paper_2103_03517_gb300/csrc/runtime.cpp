@@ -224,6 +224,27 @@ static void per_site_colour_split(const LatParams& p, const void* src, size_t el
 
 const KernelSet& kernel_set(int precision) { return precision == MC_FP64 ? kernels_f64() : kernels_f32(); }
 
+// Bytes of the packed (x, y, z, 0) spin copy that constrained sweeps gather
+// from: one 4-vector per site of each colour.
+size_t aos_bytes(const mc_desc* d) {
+    const uint64_t Nc = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2] / 2;
+    const uint64_t stride = (Nc + 63) / 64 * 64;
+    return size_t(2 * stride * 4) * (d->precision == MC_FP64 ? 8 : 4);
+}
+
+// Allocate the packed copy on the lattice's first constrained sweep (the
+// parameters that point to it are uploaded by the caller).
+int ensure_aos(mc_lattice* h) {
+    if (h->d_aos) return MC_OK;
+    const cudaError_t e = cudaMalloc(&h->d_aos, aos_bytes(&h->desc));
+    if (e != cudaSuccess) {
+        h->d_aos = nullptr;
+        return cuda_fail(e, "cudaMalloc(packed spin copy)");
+    }
+    h->hp.aos = h->d_aos;
+    return MC_OK;
+}
+
 int upload_params(mc_lattice* h) {
     set_float_params(h->hp);
     CK(cudaMemcpyAsync(&h->d_lat->p, &h->hp, sizeof(LatParams), cudaMemcpyHostToDevice, h->stream));
@@ -516,6 +537,7 @@ MC_API int mc_destroy(mc_handle h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->d_base);
+    if (h->d_aos) cudaFree(h->d_aos);
     if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
     delete h;
     return MC_OK;
@@ -549,8 +571,10 @@ MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_de
     for (int a = 0; a < 3; ++a)
         if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
     cudaSetDevice(h->device);
+    int rc = ensure_aos(h);
+    if (rc) return rc;
     constraint_frame(theta_c_deg, phi_c_deg, h->hp.R);
-    int rc = upload_params(h);
+    rc = upload_params(h);
     if (rc) return rc;
     const KernelSet& k = kernel_set(h->hp.precision);
     return enqueue_sweeps(k, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, true, h->stream, nullptr);

@@ -21,6 +21,7 @@ struct mc_lattice {
     mcgb::LatDev** d_group_lats = nullptr;   // launch tables of the lattice alone
     uint32_t* d_group_start = nullptr;
     uint32_t* d_group_start_pair = nullptr;
+    void* d_aos = nullptr;        // packed spin copy of constrained sweeps (LatParams::aos)
     const void* cone = nullptr;   // c(theta) table of the precision
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;
@@ -36,6 +37,8 @@ int validate_desc(const mc_desc* d);
 int row_fast(const LatParams& p, bool film);
 size_t lattice_bytes(const mc_desc* d);
 int upload_params(mc_lattice* h);
+size_t aos_bytes(const mc_desc* d);
+int ensure_aos(mc_lattice* h);
 void constraint_frame(double theta_deg, double phi_deg, double R[9]);
 const KernelSet& kernel_set(int precision);
 int read_state(mc_lattice* h, LatState* st);

@@ -224,7 +224,7 @@ MC_API int mc_submit(mc_server* s, const mc_job* job, uint64_t* job_id) {
     j->job.lattice.bond_mask = nullptr;
     j->job.lattice.grain_id = nullptr;
     j->job.lattice.grain_axis = nullptr;
-    j->bytes = lattice_bytes(&d);
+    j->bytes = lattice_bytes(&d) + (job->kind == MC_JOB_CONSTRAINED ? aos_bytes(&d) : 0);
     std::lock_guard<std::mutex> lk(s->mu);
     if (j->bytes > s->budget) return fail(MC_ERR_NOMEM, "job needs %zu bytes, budget is %zu", j->bytes, s->budget);
     j->id = s->next_id++;
