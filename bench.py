@@ -9,7 +9,7 @@ no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--side all|none|fp64|constrained|serving] [--no-cpu]
+                       [--side all|none|fp64|constrained|anisotropy|serving] [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
 `--impl reference` times the serial FP64 CPU oracle on the host cores instead.
@@ -351,6 +351,8 @@ def secondary(mc, torch, stream, dev, side="all"):
         out.update(fp64_per_lattice(mc, torch, stream, dev))
     if side in ("all", "constrained"):
         out.update(constrained(mc, torch, stream, dev))
+    if side in ("all", "anisotropy"):
+        out.update(anisotropy(mc, torch, stream, dev))
     return out
 
 
@@ -406,6 +408,47 @@ def constrained(mc, torch, stream, dev):
     for h in hs:
         mc.mc_destroy(h)
     return out
+
+
+def anisotropy(mc, torch, stream, dev, n_eq=200, n_meas=500):
+    """Anisotropy scaling k_u(T) at 8 temperatures, 64^3 FP32, K_u = 0.05
+    along z: by Eq. 4 from standard sweeps, against the constrained torque at
+    theta_c = 45 deg (tau_theta / N = -K(T) sin 2 theta); the same sweep
+    counts, timed with CUDA events."""
+    K, dims = 0.05, (64, 64, 64)
+    Ts = [round(0.1 + 0.15 * i, 2) for i in range(8)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for route in ("eq4", "torque"):
+        init = (1 / math.sqrt(2), 0.0, 1 / math.sqrt(2)) if route == "torque" else (0.0, 0.0, 1.0)
+        hs = [mc.mc_create_ex(mc.make_desc(dims, K_u=K, T=T, seed=i, init_dir=init, ring_capacity=16,
+                                           stream=stream.cuda_stream, device=dev)) for i, T in enumerate(Ts)]
+        g = mc.mc_group_create(hs)
+        torch.cuda.synchronize()
+        a.record(stream)
+        if route == "eq4":
+            mc.mc_group_sweep(g, n_eq)
+            mc.mc_group_sweep(g, n_meas, measure=True)
+        else:
+            th, ph = [45.0] * len(Ts), [0.0] * len(Ts)
+            mc.mc_group_constrained_sweep(g, th, ph, n_eq)
+            mc.mc_group_constrained_sweep(g, th, ph, n_meas, measure=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if route == "eq4":
+            k = [mc.mc_anisotropy_scaling(h)[0] for h in hs]
+        else:
+            k = [-mc.mc_measure(h).torque[1] / K for h in hs]
+        res[route] = {"ms": a.elapsed_time(b), "k_u": [round(x, 4) for x in k]}
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+    return {"anisotropy": {
+        "workload": f"k_u(T) of 8 x 64^3 FP32 lattices, K_u = 0.05, T = {Ts[0]}..{Ts[-1]}, "
+                    f"{n_eq} + {n_meas} sweeps per route",
+        "temperatures": Ts, "eq4": res["eq4"], "torque": res["torque"],
+        "torque_over_eq4_time": res["torque"]["ms"] / res["eq4"]["ms"],
+        "max_abs_diff": max(abs(x - y) for x, y in zip(res["eq4"]["k_u"], res["torque"]["k_u"]))}}
 
 
 def serving(mc, n_requests=40, rate=20.0, n_eq=200, n_meas=500):
@@ -470,7 +513,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
-    ap.add_argument("--side", default="all", choices=["all", "none", "fp64", "constrained", "serving"],
+    ap.add_argument("--side", default="all", choices=["all", "none", "fp64", "constrained", "anisotropy", "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -180,6 +180,20 @@ MC_API int mc_sync(mc_handle h);
  * Synchronises.  out: caller-owned. */
 MC_API int mc_measure(mc_handle h, mc_observables* out);
 
+/* Temperature scaling of the anisotropy by Eq. 4 (Sec. 3), from the mean
+ * easy-axis anisotropy energy of the samples since the last mc_reset_stats
+ * (standard sweeps, no constraint).  K_easy = mean anisotropy energy per
+ * spin above its T = 0 value along the easy direction; K_0,hard = T = 0
+ * energy per spin of the hard direction above the easy one.
+ *   uniaxial (E_u = -K_u (S.e)^2, K_u > 0):  K_easy = <E_u/N> + K_u,
+ *     K_0,hard = K_u,      out[0] = k_u = 1 - 3 K_easy / (2 K_0,hard);
+ *   cubic (E_c = K_c q(S), K_c > 0: easy <100>, hard <111>, the long cube
+ *     diagonal):  K_easy = <E_c/N>,  K_0,hard = K_c / 3,
+ *                          out[1] = k_c = 1 - 5 K_easy / (3 K_0,hard).
+ * Either is NaN when its constant is zero.  Synchronises.  out: caller-owned
+ * double[2].  Errors: MC_ERR_ARG (null), MC_ERR_STATE (no samples). */
+MC_API int mc_anisotropy_scaling(mc_handle h, double out[2]);
+
 /* Slice-averaged profile <m_a(x)> = <(1/(Ly Lz)) sum_{y,z} S_a> for every
  * x-plane (Sec. 3, domain-wall profile), averaged over the profile samples
  * taken by mc_profile_sample.  axis: component a (0, 1, 2).  out: len >= Lx

@@ -72,6 +72,7 @@ def lib() -> C.CDLL:
         L.or_delta_e.argtypes = [vp, i64, P(dbl)]; L.or_delta_e.restype = dbl
         L.or_stats.argtypes = [vp, P(dbl)]
         L.or_samples.argtypes = [vp, P(dbl), i64]; L.or_samples.restype = i64
+        L.or_anisotropy_scaling.argtypes = [vp, P(dbl)]
         L.or_profile.argtypes = [vp, P(dbl)]
         L.or_reset_stats.argtypes = [vp]
         L.or_sweep.argtypes = [vp, i32, i32]; L.or_sweep.restype = i32
@@ -224,6 +225,13 @@ class Lattice:
         out = np.zeros(len(STAT_FIELDS))
         lib().or_stats(self._h, _p(out, C.c_double))
         return dict(zip(STAT_FIELDS, out.tolist()))
+
+    def anisotropy_scaling(self) -> np.ndarray:
+        """(k_u, k_c) of Eq. 4 from the mean anisotropy energies (NaN where
+        the constant is zero or nothing was sampled)."""
+        out = np.zeros(2)
+        lib().or_anisotropy_scaling(self._h, _p(out, C.c_double))
+        return out
 
     def samples(self, max_n: int | None = None) -> np.ndarray:
         """The most recent min(max_n, kept) per-sweep samples, oldest first."""

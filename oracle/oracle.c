@@ -448,6 +448,32 @@ OR_EXPORT void or_stats(const or_lattice* L, double* out) {
     for (int a = 0; a < 3; ++a) out[k++] = L->acc_tq2[a];
 }
 
+/* Eq. 4 (Sec. 3): temperature scaling of the anisotropy from the mean
+ * easy-axis anisotropy energy of the standard algorithm.  K_easy is the mean
+ * anisotropy energy per spin above its T = 0 value (all spins on the easy
+ * direction); K_0,hard is the T = 0 energy per spin of the hard direction
+ * above the easy one.  Uniaxial, E_u = -K_u (S.e)^2: K_easy = <E_u/N> + K_u,
+ * K_0,hard = K_u, k_u = 1 - 3 K_easy / (2 K_0,hard).  Cubic, E_c = K_c q(S)
+ * with K_c > 0 (easy <100>, q = 0; hard <111>, q = 1/3): K_easy = <E_c/N>,
+ * K_0,hard = K_c / 3, k_c = 1 - 5 K_easy / (3 K_0,hard).  out[0] = k_u,
+ * out[1] = k_c; NaN where the constant is zero or no sample was taken. */
+OR_EXPORT void or_anisotropy_scaling(const or_lattice* L, double* out) {
+    out[0] = NAN;
+    out[1] = NAN;
+    if (L->n_samples == 0) return;
+    const double n = (double)L->n_samples;
+    if (L->Ku != 0.0) {
+        const double k_easy = L->acc_parts[1] / n + L->Ku;
+        const double k0_hard = L->Ku;
+        out[0] = 1.0 - 3.0 * k_easy / (2.0 * k0_hard);
+    }
+    if (L->Kc != 0.0) {
+        const double k_easy = L->acc_parts[2] / n;
+        const double k0_hard = L->Kc / 3.0;
+        out[1] = 1.0 - 5.0 * k_easy / (3.0 * k0_hard);
+    }
+}
+
 /* The most recent min(max, kept) samples, oldest first. */
 OR_EXPORT int64_t or_samples(const or_lattice* L, double* out, int64_t max) {
     int64_t n = L->ring_count < L->ring_cap ? L->ring_count : L->ring_cap;

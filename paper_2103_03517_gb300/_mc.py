@@ -89,6 +89,7 @@ _SIGS = {
     "mc_constrained_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int]),
     "mc_sync": (C.c_int, [C.c_void_p]),
     "mc_measure": (C.c_int, [C.c_void_p, _P(mc_observables)]),
+    "mc_anisotropy_scaling": (C.c_int, [C.c_void_p, _P(C.c_double)]),
     "mc_profile": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_double), C.c_int]),
     "mc_profile_sample": (C.c_int, [C.c_void_p]),
     "mc_samples": (C.c_int, [C.c_void_p, _P(mc_sample), C.c_int, _P(C.c_int)]),
@@ -240,6 +241,13 @@ def mc_measure(h) -> mc_observables:
     o = mc_observables()
     _check(lib().mc_measure(h, C.byref(o)))
     return o
+
+
+def mc_anisotropy_scaling(h) -> np.ndarray:
+    """(k_u, k_c) of Eq. 4 from the samples since the last reset."""
+    out = np.zeros(2)
+    _check(lib().mc_anisotropy_scaling(h, _dp(out)))
+    return out
 
 
 def mc_profile_sample(h) -> None:

@@ -590,6 +590,18 @@ MC_API int mc_sync(mc_handle h) {
     return MC_OK;
 }
 
+MC_API int mc_anisotropy_scaling(mc_handle h, double out[2]) {
+    if (!h || !out) return fail(MC_ERR_ARG, "null argument");
+    mc_observables o;
+    const int rc = mc_measure(h, &o);
+    if (rc) return rc;
+    if (o.n_samples == 0) return fail(MC_ERR_STATE, "no samples since the last reset");
+    const double Ku = h->hp.Ku, Kc = h->hp.Kc;
+    out[0] = Ku != 0.0 ? 1.0 - 3.0 * (o.e_parts[1] + Ku) / (2.0 * Ku) : std::nan("");
+    out[1] = Kc != 0.0 ? 1.0 - 5.0 * o.e_parts[2] / (3.0 * (Kc / 3.0)) : std::nan("");
+    return MC_OK;
+}
+
 MC_API int mc_measure(mc_handle h, mc_observables* out) {
     if (!h || !out) return fail(MC_ERR_ARG, "null argument");
     cudaSetDevice(h->device);

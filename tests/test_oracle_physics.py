@@ -276,3 +276,68 @@ def test_parallel_constrained_matches_serial_asselin():
         res.append((tau.mean(), blocking_error(tau)))
     (a, ea), (b, eb) = res
     assert abs(a - b) < 4 * math.hypot(ea, eb), res
+
+
+# ------------------------------------------------------ Eq. 4 anisotropy scaling
+def _sphere_average(f, weight, n_t=200, n_phi=400):
+    """<f> under the weight over the unit sphere: Gauss-Legendre in cos(theta),
+    periodic trapezoid in phi."""
+    t, w = np.polynomial.legendre.leggauss(n_t)
+    phi = np.linspace(0.0, 2 * np.pi, n_phi, endpoint=False)
+    T, P = np.meshgrid(t, phi, indexing="ij")
+    r = np.sqrt(1 - T ** 2)
+    x, y, z = r * np.cos(P), r * np.sin(P), T
+    b = weight(x, y, z) * w[:, None]
+    return float((b * f(x, y, z)).sum() / b.sum())
+
+
+def test_eq4_uniaxial_single_spin_is_p2():
+    """One spin, uniaxial only: Eq. 4 with K_easy = <E_u> + K_u and K_0,hard =
+    K_u gives k_u = (3 <cos^2> - 1) / 2, the Boltzmann average of P_2 by
+    quadrature."""
+    K, T = 1.0, 0.4
+    o = oracle.Lattice((1, 1, 1), Ku=K, T=T, bc=(1, 1, 1), seed=19, ring_cap=300000)
+    o.sweep(1000)
+    o.sweep(300000, measure=True)
+    k_u, k_c = o.anisotropy_scaling()
+    assert math.isnan(k_c)
+    per_sweep = 1 - 3 * (_series(o, 7) + K) / (2 * K)
+    expect = _sphere_average(lambda x, y, z: 1.5 * z ** 2 - 0.5, lambda x, y, z: np.exp(K * z ** 2 / T))
+    assert abs(k_u - expect) < max(5 * blocking_error(per_sweep), 1e-3), (k_u, expect)
+
+
+def test_eq4_cubic_single_spin_quadrature():
+    """One spin, cubic only (K_c > 0, easy <100>): k_c = 1 - 5 <q> with q =
+    x^2 y^2 + x^2 z^2 + y^2 z^2 averaged by quadrature over the sphere."""
+    K, T = 1.0, 0.15
+    o = oracle.Lattice((1, 1, 1), Kc=K, T=T, bc=(1, 1, 1), seed=23, ring_cap=300000)
+    o.sweep(1000)
+    o.sweep(300000, measure=True)
+    k_u, k_c = o.anisotropy_scaling()
+    assert math.isnan(k_u)
+    q = lambda x, y, z: x * x * y * y + x * x * z * z + y * y * z * z  # noqa: E731
+    expect = 1 - 5 * _sphere_average(q, lambda x, y, z: np.exp(-K * q(x, y, z) / T))
+    per_sweep = 1 - 5 * _series(o, 8) / K
+    assert 0.2 < expect < 0.9
+    assert abs(k_c - expect) < max(5 * blocking_error(per_sweep), 1e-3), (k_c, expect)
+
+
+def test_eq4_limits():
+    """Eq. 4 is 1 at T -> 0 (every spin on the easy axis) and 0 in the
+    paramagnetic limit (<cos^2> = 1/3, <q> = 1/5 for spins uniform on the
+    sphere), for both constants at once."""
+    # at T = 1e-4 the thermal softening (k_c ~ 1 - 5 <delta^2>, <delta^2> ~ T)
+    # is about 2e-4
+    cold = oracle.Lattice((8, 8, 8), J=1.0, Ku=0.05, Kc=0.02, T=1e-4, seed=3, ring_cap=1)
+    cold.sweep(50)
+    cold.sweep(200, measure=True)
+    k_u, k_c = cold.anisotropy_scaling()
+    assert abs(k_u - 1) < 1e-3 and abs(k_c - 1) < 1e-3, (k_u, k_c)
+    hot = oracle.Lattice((8, 8, 8), J=0.0, Ku=1.0, Kc=1.0, T=1e3, seed=4, ring_cap=4000)
+    hot.sweep(200)
+    hot.sweep(4000, measure=True)
+    k_u, k_c = hot.anisotropy_scaling()
+    s = hot.samples()
+    err_u = blocking_error(1 - 3 * (s[:, 7] + 1.0) / 2)
+    err_c = blocking_error(1 - 5 * s[:, 8])
+    assert abs(k_u) < 5 * err_u + 2e-3 and abs(k_c) < 5 * err_c + 2e-3, (k_u, k_c, err_u, err_c)
