@@ -56,8 +56,10 @@ typedef enum mc_precision { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
 /* Boundary mode of one axis.  PERIODIC needs an even size (two-colouring).
  * OPEN drops bonds across the face.  PINNED is OPEN and, in addition, the
  * two end planes of that axis are never updated (fixed by the initial
- * state: e.g. a Bloch wall held by +z / -z end planes). */
-typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2 } mc_boundary;
+ * state: e.g. a Bloch wall held by +z / -z end planes).  ANTIPERIODIC wraps
+ * like PERIODIC (even size) but a bond across the face couples S_i to -S_j,
+ * i.e. S(x + L) = -S(x): the wall setup of Sec. 3, which holds one wall. */
+typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIPERIODIC = 3 } mc_boundary;
 
 typedef enum mc_init {
     MC_INIT_UNIFORM = 0, /* every spin along init_dir (default +z)             */

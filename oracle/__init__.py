@@ -27,7 +27,7 @@ STAT_FIELDS = (["n"] + [f"m{a}" for a in "xyz"] + [f"m2{a}" for a in "xyz"]
                + [f"tq2{a}" for a in "xyz"])
 SAMPLE_WORDS = 14
 
-PERIODIC, OPEN, PINNED = 0, 1, 2
+PERIODIC, OPEN, PINNED, ANTIPERIODIC = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:

@@ -230,15 +230,19 @@ static int64_t site_of(const or_lattice* L, int x, int y, int z) {
     return (int64_t)x + (int64_t)L->L[0] * ((int64_t)y + (int64_t)L->L[1] * z);
 }
 
-/* neighbour in direction d (0..5 = -x,+x,-y,+y,-z,+z); -1 if absent */
-static int64_t neighbour(const or_lattice* L, int64_t i, int x, int y, int z, int d) {
+/* neighbour in direction d (0..5 = -x,+x,-y,+y,-z,+z); -1 if absent.
+ * Boundary modes: 0 periodic, 1 open, 2 pinned (open), 3 anti-periodic: the
+ * axis wraps and the spin across the face enters as -S, *flip = 1. */
+static int64_t neighbour(const or_lattice* L, int64_t i, int x, int y, int z, int d, int* flip) {
     int c[3] = {x, y, z};
     const int ax = d / 2;
     const int step = (d & 1) ? 1 : -1;
     int v = c[ax] + step;
+    *flip = 0;
     if (v < 0 || v >= L->L[ax]) {
-        if (L->bc[ax] != 0) return -1;
+        if (L->bc[ax] != 0 && L->bc[ax] != 3) return -1;
         v = (v + L->L[ax]) % L->L[ax];
+        *flip = L->bc[ax] == 3;
     }
     if (L->bonds && !((L->bonds[i] >> d) & 1u)) return -1;
     c[ax] = v;
@@ -260,7 +264,7 @@ static double cubic_q(const double s[3]) {
  * neighbours held fixed:  dE = -J d.h - K_u((Sn.e)^2 - (S.e)^2)
  *                               + K_c(q(Sn) - q(S)) - H.d,  d = Sn - S,
  * h = sum of the present nearest neighbours, accumulated in the order
- * -x, +x, -y, +y, -z, +z.
+ * -x, +x, -y, +y, -z, +z (a neighbour across an anti-periodic face as -S).
  */
 static double delta_e(const or_lattice* L, int64_t i, const double S[3], const double Sn[3]) {
     const int x = (int)(i % L->L[0]);
@@ -268,9 +272,10 @@ static double delta_e(const or_lattice* L, int64_t i, const double S[3], const d
     const int z = (int)(i / ((int64_t)L->L[0] * L->L[1]));
     double h[3] = {0.0, 0.0, 0.0};
     for (int d = 0; d < 6; ++d) {
-        const int64_t j = neighbour(L, i, x, y, z, d);
+        int flip;
+        const int64_t j = neighbour(L, i, x, y, z, d, &flip);
         if (j < 0) continue;
-        for (int a = 0; a < 3; ++a) h[a] = h[a] + L->S[3 * j + a];
+        for (int a = 0; a < 3; ++a) h[a] = flip ? h[a] - L->S[3 * j + a] : h[a] + L->S[3 * j + a];
     }
     const double d0 = Sn[0] - S[0], d1 = Sn[1] - S[1], d2 = Sn[2] - S[2];
     const double e_ex = -(L->J * (d0 * h[0] + d1 * h[1] + d2 * h[2]));
@@ -384,10 +389,12 @@ static void measure(or_lattice* L, int64_t accepted) {
         const int z = (int)(i / ((int64_t)L->L[0] * L->L[1]));
         for (int a = 0; a < 3; ++a) M[a] += s[a];
         for (int d = 1; d < 6; d += 2) {
-            const int64_t j = neighbour(L, i, x, y, z, d);
+            int flip;
+            const int64_t j = neighbour(L, i, x, y, z, d, &flip);
             if (j < 0) continue;
             const double* t = &L->S[3 * j];
-            sex += s[0] * t[0] + s[1] * t[1] + s[2] * t[2];
+            const double b = s[0] * t[0] + s[1] * t[1] + s[2] * t[2];
+            sex += flip ? -b : b;
         }
         const double* e = easy_axis(L, i);
         const double pe = s[0] * e[0] + s[1] * e[1] + s[2] * e[2];

@@ -63,32 +63,39 @@ __device__ __forceinline__ bool pinned(const LatParams& p, const Geo& g) {
 }
 
 // Other-colour indices of the six neighbours in the order -x,+x,-y,+y,-z,+z
-// and a presence mask (boundaries and, for films, the bond mask).
+// and a mask: bit d = neighbour d present (boundaries and, for films, the
+// bond mask), bit 8 + d = the bond to it crosses an anti-periodic face and
+// couples to -S (kFlipShift).
+constexpr int kFlipShift = 8;
+
+__device__ __forceinline__ bool wraps(int bc) { return bc == 0 || bc == 3; }
+
 __device__ __forceinline__ uint32_t neighbours(const LatParams& p, const Geo& g, int colour,
                                                uint32_t nq[6]) {
     uint32_t present = 0;
     const uint32_t q = g.q;
     const uint32_t Lh = uint32_t(p.Lh);
     const uint32_t plane = Lh * uint32_t(p.Ly);
+    const uint32_t fx = p.bc[0] == 3 ? 1u : 0u, fy = p.bc[1] == 3 ? 1u : 0u, fz = p.bc[2] == 3 ? 1u : 0u;
     // -x
     if (g.k + g.xoff - 1 >= 0) { nq[0] = q + g.xoff - 1; present |= 1u; }
-    else if (p.bc[0] == 0) { nq[0] = q - g.k + Lh - 1; present |= 1u; }
+    else if (wraps(p.bc[0])) { nq[0] = q - g.k + Lh - 1; present |= 1u | (fx << kFlipShift); }
     // +x
     if (g.k + g.xoff < p.Lh) { nq[1] = q + g.xoff; present |= 2u; }
-    else if (p.bc[0] == 0) { nq[1] = q - g.k; present |= 2u; }
+    else if (wraps(p.bc[0])) { nq[1] = q - g.k; present |= 2u | (fx << (kFlipShift + 1)); }
     // -y
     if (g.y > 0) { nq[2] = q - Lh; present |= 4u; }
-    else if (p.bc[1] == 0) { nq[2] = q + Lh * uint32_t(p.Ly - 1); present |= 4u; }
+    else if (wraps(p.bc[1])) { nq[2] = q + Lh * uint32_t(p.Ly - 1); present |= 4u | (fy << (kFlipShift + 2)); }
     // +y
     if (g.y < p.Ly - 1) { nq[3] = q + Lh; present |= 8u; }
-    else if (p.bc[1] == 0) { nq[3] = q - Lh * uint32_t(p.Ly - 1); present |= 8u; }
+    else if (wraps(p.bc[1])) { nq[3] = q - Lh * uint32_t(p.Ly - 1); present |= 8u | (fy << (kFlipShift + 3)); }
     // -z
     if (g.z > 0) { nq[4] = q - plane; present |= 16u; }
-    else if (p.bc[2] == 0) { nq[4] = q + plane * uint32_t(p.Lz - 1); present |= 16u; }
+    else if (wraps(p.bc[2])) { nq[4] = q + plane * uint32_t(p.Lz - 1); present |= 16u | (fz << (kFlipShift + 4)); }
     // +z
     if (g.z < p.Lz - 1) { nq[5] = q + plane; present |= 32u; }
-    else if (p.bc[2] == 0) { nq[5] = q - plane * uint32_t(p.Lz - 1); present |= 32u; }
-    if (p.bonds) present &= uint32_t(__ldg(&p.bonds[uint32_t(colour) * p.stride + q]));
+    else if (wraps(p.bc[2])) { nq[5] = q - plane * uint32_t(p.Lz - 1); present |= 32u | (fz << (kFlipShift + 5)); }
+    if (p.bonds) present &= uint32_t(__ldg(&p.bonds[uint32_t(colour) * p.stride + q])) | ~0x3Fu;
     return present;
 }
 
@@ -113,7 +120,8 @@ struct alignas(4 * sizeof(R)) Spin4 {
     R x, y, z, w;
 };
 
-// Sum of the present other-colour neighbours, accumulated -x,+x,-y,+y,-z,+z.
+// Sum of the present other-colour neighbours, accumulated -x,+x,-y,+y,-z,+z;
+// a neighbour across an anti-periodic face enters as -S.
 template <typename R>
 __device__ __forceinline__ V3<R> neighbour_sum(const R* s, uint32_t stride, int other, const uint32_t nq[6],
                                                uint32_t present) {
@@ -122,9 +130,16 @@ __device__ __forceinline__ V3<R> neighbour_sum(const R* s, uint32_t stride, int 
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         if (present & (1u << d)) {
-            h.x = h.x + b[nq[d]];
-            h.y = h.y + b[stride + nq[d]];
-            h.z = h.z + b[2 * size_t(stride) + nq[d]];
+            const R vx = b[nq[d]], vy = b[stride + nq[d]], vz = b[2 * size_t(stride) + nq[d]];
+            if (present & (1u << (kFlipShift + d))) {
+                h.x = h.x - vx;
+                h.y = h.y - vy;
+                h.z = h.z - vz;
+            } else {
+                h.x = h.x + vx;
+                h.y = h.y + vy;
+                h.z = h.z + vz;
+            }
         }
     }
     return h;
@@ -138,9 +153,15 @@ __device__ __forceinline__ V3<R> neighbour_sum4(const Spin4<R>* a, const uint32_
     for (int d = 0; d < 6; ++d) {
         if (present & (1u << d)) {
             const Spin4<R> v = a[nq[d]];
-            h.x = h.x + v.x;
-            h.y = h.y + v.y;
-            h.z = h.z + v.z;
+            if (present & (1u << (kFlipShift + d))) {
+                h.x = h.x - v.x;
+                h.y = h.y - v.y;
+                h.z = h.z - v.z;
+            } else {
+                h.x = h.x + v.x;
+                h.y = h.y + v.y;
+                h.z = h.z + v.z;
+            }
         }
     }
     return h;

@@ -142,8 +142,8 @@ size_t lattice_bytes(const mc_desc* d) {
 int validate_desc(const mc_desc* d) {
     for (int a = 0; a < 3; ++a) {
         if (d->dims[a] < 1) return fail(MC_ERR_ARG, "dims[%d] = %d < 1", a, d->dims[a]);
-        if (d->boundary[a] < 0 || d->boundary[a] > 2) return fail(MC_ERR_ARG, "boundary[%d] invalid", a);
-        if (d->boundary[a] == MC_PERIODIC && (d->dims[a] % 2))
+        if (d->boundary[a] < 0 || d->boundary[a] > 3) return fail(MC_ERR_ARG, "boundary[%d] invalid", a);
+        if ((d->boundary[a] == MC_PERIODIC || d->boundary[a] == MC_ANTIPERIODIC) && (d->dims[a] % 2))
             return fail(MC_ERR_ARG, "periodic axis %d has odd size %d (breaks the two-colouring)", a, d->dims[a]);
     }
     if (d->dims[0] % 2) return fail(MC_ERR_ARG, "Lx = %d must be even", d->dims[0]);
@@ -174,7 +174,9 @@ int validate_desc(const mc_desc* d) {
                     const int c[3] = {x, y, z};
                     for (int ax = 0; ax < 3; ++ax) {
                         int cc[3] = {c[0], c[1], c[2]};
-                        if (cc[ax] + 1 >= L[ax] && d->boundary[ax] != MC_PERIODIC) continue;
+                        if (cc[ax] + 1 >= L[ax] && d->boundary[ax] != MC_PERIODIC &&
+                            d->boundary[ax] != MC_ANTIPERIODIC)
+                            continue;
                         cc[ax] = (cc[ax] + 1) % L[ax];
                         const uint64_t j = cc[0] + uint64_t(L[0]) * (cc[1] + uint64_t(L[1]) * cc[2]);
                         const int fwd = (d->bond_mask[i] >> (2 * ax + 1)) & 1;

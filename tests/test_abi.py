@@ -76,6 +76,7 @@ def test_desc_defaults():
     (dict(dims=(15, 16, 16), boundary=(1, 0, 0)), "even"),
     (dict(dims=(15, 16, 16)), "odd size"),
     (dict(dims=(16, 15, 16)), "odd size"),
+    (dict(dims=(16, 16, 15), boundary=(0, 0, 3)), "odd size"),
     (dict(dims=(16, 16, 16), T=0.0), "T must"),
     (dict(dims=(16, 16, 16), T=-1.0), "T must"),
     (dict(dims=(16, 16, 16), axis=(0, 0, 0)), "axis"),

@@ -121,6 +121,10 @@ GEOMETRIES = [
     ((64, 6, 4), (0, 0, 0)),     # row fast path: one 32-site segment per row
     ((128, 2, 2), (0, 0, 0)),    # row fast path, y and z neighbours doubled by the wrap
     ((192, 4, 2), (0, 0, 0)),    # row fast path, three segments per row
+    ((24, 6, 4), (3, 0, 0)),     # anti-periodic x (the wall setup)
+    ((8, 6, 4), (3, 3, 1)),      # anti-periodic x and y, open z
+    ((2, 2, 4), (3, 0, 3)),      # anti-periodic with doubled neighbours
+    ((64, 4, 2), (3, 0, 0)),     # a row-sized lattice that must leave the row path
 ]
 
 
@@ -161,11 +165,14 @@ def test_fp64_film_bit_exact():
         mc.mc_destroy(h)
 
 
-@pytest.mark.parametrize("dims,th,ph", [((16, 16, 16), 30.0, 20.0), ((12, 10, 8), 60.0, 45.0),
-                                        ((6, 3, 1), 90.0, 0.0), ((34, 6, 6), 0.0, 0.0)])
-def test_fp64_constrained_bit_exact(dims, th, ph):
+@pytest.mark.parametrize("dims,th,ph,anti", [((16, 16, 16), 30.0, 20.0, False), ((12, 10, 8), 60.0, 45.0, False),
+                                             ((6, 3, 1), 90.0, 0.0, False), ((34, 6, 6), 0.0, 0.0, False),
+                                             ((12, 6, 4), 45.0, 0.0, True)])
+def test_fp64_constrained_bit_exact(dims, th, ph, anti):
     N = dims[0] * dims[1] * dims[2]
     bc = tuple(0 if d % 2 == 0 else 1 for d in dims)
+    if anti:
+        bc = (3,) + bc[1:]
     R = oracle.constraint_frame(th, ph)
     spins = workloads.uniform_spins(N, R[0])
     h, o = make_pair(dims, J=1.0, Ku=0.05, Kc=0.02, H=(0.0, 0.05, 0.0), T=0.6, seed=5, bc=bc, spins=spins, ring=64)

@@ -341,3 +341,50 @@ def test_eq4_limits():
     err_u = blocking_error(1 - 3 * (s[:, 7] + 1.0) / 2)
     err_c = blocking_error(1 - 5 * s[:, 8])
     assert abs(k_u) < 5 * err_u + 2e-3 and abs(k_c) < 5 * err_c + 2e-3, (k_u, k_c, err_u, err_c)
+
+
+# ------------------------------------------------ anti-periodic wall (Sec. 3)
+def _discrete_wall(Lx, J, K):
+    """Minimum of the 1-D chain energy -J sum cos(phi_{x+1} - phi_x) - K sum
+    cos^2 phi_x with the anti-periodic closure phi_Lx = phi_0 + pi (one
+    Bloch wall), by L-BFGS from a tanh start.  Returns (phi, E_min)."""
+    from scipy.optimize import minimize
+
+    def energy(phi):
+        nxt = np.append(phi[1:], phi[0] + np.pi)
+        d = nxt - phi
+        e = -J * np.cos(d).sum() - K * (np.cos(phi) ** 2).sum()
+        g = -J * np.sin(d) + J * np.roll(np.sin(d), 1) + K * np.sin(2 * phi)
+        return e, g
+
+    x = np.arange(Lx)
+    width = np.pi * math.sqrt(J / (2 * K))
+    phi0 = 2 * np.arctan(np.exp(np.pi * (x - Lx / 2) / width))  # 0 -> pi across the wall
+    r = minimize(energy, phi0, jac=True, method="L-BFGS-B", options={"gtol": 1e-12, "maxiter": 10000})
+    return r.x, r.fun
+
+
+def test_antiperiodic_wall_energy_at_low_temperature():
+    """x anti-periodic holds one Bloch wall.  Started on the discrete
+    minimum of the wall, the chain at T = 1e-3 keeps the minimum energy plus
+    equipartition (two transverse modes per spin: E = E_min + N T); the
+    discrete wall energy is the continuum 4 sqrt(A K) = 2 sqrt(2 J K) to
+    within the lattice correction."""
+    Lx, Ly, Lz, J, K, T = 64, 2, 2, 1.0, 0.05, 1e-3
+    phi, e_chain = _discrete_wall(Lx, J, K)
+    wall = e_chain + (J + K) * Lx
+    assert abs(wall / (2 * math.sqrt(2 * J * K)) - 1) < 0.01
+    N = Lx * Ly * Lz
+    S = np.zeros((N, 3))
+    xs = np.arange(N) % Lx
+    S[:, 0], S[:, 2] = np.sin(phi[xs]), np.cos(phi[xs])
+    o = oracle.Lattice((Lx, Ly, Lz), J=J, Ku=K, T=T, bc=(3, 0, 0), seed=6, ring_cap=1)
+    o.set_spins(S)
+    o.sweep(200)
+    o.sweep(400, measure=True)
+    s = o.stats()
+    e_total = s["e"] / s["n"] * N
+    ground = Ly * Lz * e_chain - 2 * J * N  # y and z bonds aligned
+    assert abs(e_total - (ground + N * T)) < 0.02 * Ly * Lz * wall, (e_total, ground + N * T)
+    mz = o.spins()[:, 2].reshape(Lz, Ly, Lx).mean(axis=(0, 1))
+    assert mz.max() > 0.9 and mz.min() < -0.9  # the wall is still there

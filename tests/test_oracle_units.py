@@ -120,7 +120,9 @@ def test_cone_trial_p_is_uniform():
 # --------------------------------------------------------- energy change, Eq. 2
 def _total_energy(S, dims, bc, J, Ku, axis, Kc, H, bonds=None, gid=None, gaxes=None):
     """Brute-force E of Eq. 2 summed over the lattice: every bond once
-    (the +x, +y, +z neighbour of each site), all single-site terms."""
+    (the +x, +y, +z neighbour of each site), all single-site terms.  bc per
+    axis: 0 periodic, 1 open, 2 pinned (open), 3 anti-periodic (the bond
+    across the face couples S_i to -S_j)."""
     Lx, Ly, Lz = dims
     S3 = S.reshape(Lz, Ly, Lx, 3)
     E = 0.0
@@ -133,13 +135,15 @@ def _total_energy(S, dims, bc, J, Ku, axis, Kc, H, bonds=None, gid=None, gaxes=N
                     c = [x, y, z]
                     c[ax] += 1
                     L = dims[ax]
+                    sign = 1.0
                     if c[ax] >= L:
-                        if bc[ax] != 0:
+                        if bc[ax] not in (0, 3):
                             continue
                         c[ax] -= L
+                        sign = -1.0 if bc[ax] == 3 else 1.0
                     if bonds is not None and not (bonds[i] >> d) & 1:
                         continue
-                    E -= J * float(s @ S3[c[2], c[1], c[0]])
+                    E -= J * sign * float(s @ S3[c[2], c[1], c[0]])
                 e = axis if gid is None else gaxes[gid[i]]
                 E -= Ku * float(s @ e) ** 2
                 E += Kc * (s[0] ** 2 * s[1] ** 2 + s[0] ** 2 * s[2] ** 2 + s[1] ** 2 * s[2] ** 2)
@@ -148,7 +152,8 @@ def _total_energy(S, dims, bc, J, Ku, axis, Kc, H, bonds=None, gid=None, gaxes=N
 
 
 @pytest.mark.parametrize("dims,bc", [((4, 4, 4), (0, 0, 0)), ((4, 2, 6), (1, 0, 2)), ((6, 3, 1), (0, 1, 1)),
-                                     ((2, 4, 2), (0, 0, 0))])
+                                     ((2, 4, 2), (0, 0, 0)), ((4, 4, 4), (3, 0, 0)), ((6, 2, 4), (3, 3, 1)),
+                                     ((2, 4, 2), (3, 0, 3))])
 def test_delta_e_equals_total_energy_difference(dims, bc):
     rng = np.random.default_rng(sum(dims))
     N = dims[0] * dims[1] * dims[2]
@@ -243,23 +248,24 @@ def test_constraint_frame_orthonormal():
 
 
 # --------------------------------------------------------- observables, Sec. 3
-def test_sample_energies_equal_brute_force_total_energy():
+@pytest.mark.parametrize("bc", [(0, 0, 1), (3, 0, 1), (3, 3, 3)])
+def test_sample_energies_equal_brute_force_total_energy(bc):
     """The per-sample energy parts of a measured sweep sum to E/N of Eq. 2
-    computed brute force over the final state (all couplings on, open and
-    periodic axes, a field)."""
+    computed brute force over the final state (all couplings on, open,
+    periodic and anti-periodic axes, a field)."""
     rng = np.random.default_rng(11)
-    dims, bc = (6, 4, 3), (0, 0, 1)
+    dims = (6, 4, 2)
     J, Ku, Kc = 1.1, 0.3, -0.4
     axis = rng.standard_normal(3)
     axis /= np.linalg.norm(axis)
     H = np.array([0.2, -0.1, 0.3])
     lat = oracle.Lattice(dims, J=J, Ku=Ku, axis=axis, Kc=Kc, H=H, T=0.7, bc=bc, seed=4, ring_cap=3)
-    lat.set_spins(workloads_random(72, 5))
+    lat.set_spins(workloads_random(48, 5))
     lat.sweep(3, measure=True)
     S = lat.spins()
     E = _total_energy(S, dims, bc, J, Ku, axis, Kc, H)
     smp = lat.samples(1)[0]
-    assert abs(smp[6:10].sum() - E / 72) < 1e-13
+    assert abs(smp[6:10].sum() - E / 48) < 1e-13
     assert np.allclose(smp[3:6], S.mean(axis=0), atol=1e-15)
 
 
