@@ -9,7 +9,7 @@ no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--side all|none|fp64|constrained|anisotropy|serving] [--no-cpu]
+                       [--side all|none|fp64|constrained|anisotropy|general|serving] [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
 `--impl reference` times the serial FP64 CPU oracle on the host cores instead.
@@ -353,6 +353,8 @@ def secondary(mc, torch, stream, dev, side="all"):
         out.update(constrained(mc, torch, stream, dev))
     if side in ("all", "anisotropy"):
         out.update(anisotropy(mc, torch, stream, dev))
+    if side in ("all", "general"):
+        out.update(general_geometry(mc, torch, stream, dev))
     return out
 
 
@@ -451,6 +453,37 @@ def anisotropy(mc, torch, stream, dev, n_eq=200, n_meas=500):
         "max_abs_diff": max(abs(x - y) for x, y in zip(res["eq4"]["k_u"], res["torque"]["k_u"]))}}
 
 
+def general_geometry(mc, torch, stream, dev, sweeps=40):
+    """FP32 throughput of the lattices that are not all-periodic cubes: the
+    Bloch-wall lattice (1024 x 128 x 128, x pinned, T = 0.66) and a granular
+    film (1024 x 1024 x 15, Voronoi grains of mean diameter 10, bond mask and
+    grain axes, z open), measured sweeps, CUDA events."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    spec = workloads.config4()[3]
+    gid, mask, axes = workloads.voronoi_film(1024, 1024, 15, 10.0, seed=1)
+    cases = [("wall", spec.dims, mc.make_desc(spec.dims, K_u=spec.Ku, T=spec.T, seed=spec.seed, boundary=spec.bc,
+                                              init=mc.MC_INIT_WALL, ring_capacity=16, stream=stream.cuda_stream,
+                                              device=dev)),
+             ("film", (1024, 1024, 15), mc.make_desc((1024, 1024, 15), K_u=0.02, T=0.6, seed=3, boundary=(0, 0, 1),
+                                                     bond_mask=mask, grain_id=gid, grain_axis=axes, ring_capacity=16,
+                                                     stream=stream.cuda_stream, device=dev))]
+    out = {}
+    for name, dims, d in cases:
+        h = mc.mc_create_ex(d)
+        mc.mc_sweep(h, 4, measure=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        mc.mc_sweep(h, sweeps, measure=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        n = dims[0] * dims[1] * dims[2]
+        out[name] = n * sweeps / (a.elapsed_time(b) * 1e-3)
+        mc.mc_destroy(h)
+    return {"general_geometry": {"unit": UNIT, "wall_1024x128x128_pinned_x": out["wall"],
+                                 "film_1024x1024x15": out["film"],
+                                 "workload": f"{sweeps} measured sweeps each, FP32"}}
+
+
 def serving(mc, n_requests=40, rate=20.0, n_eq=200, n_meas=500):
     """Config-5 style trace: Poisson arrivals (rate, seed 1) of m(T) points,
     constrained points and granular films (45/45/10%), cubes L in
@@ -513,7 +546,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
-    ap.add_argument("--side", default="all", choices=["all", "none", "fp64", "constrained", "anisotropy", "serving"],
+    ap.add_argument("--side", default="all",
+                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -61,6 +61,14 @@ typedef enum mc_precision { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
  * i.e. S(x + L) = -S(x): the wall setup of Sec. 3, which holds one wall. */
 typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIPERIODIC = 3 } mc_boundary;
 
+/* Colour-pass kernel of an FP32 lattice.  AUTO takes a row kernel where the
+ * row layout applies (Lh = Lx/2 a power of two <= 64 or a multiple of 64,
+ * Nc a multiple of 64) and the general kernel otherwise; GENERAL always
+ * takes the general kernel.  Both compute the same chain up to FP32
+ * rounding (the draws are keyed to the same sites); GENERAL exists to
+ * compare them.  FP64 lattices always take the general kernel. */
+typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_path;
+
 typedef enum mc_init {
     MC_INIT_UNIFORM = 0, /* every spin along init_dir (default +z)             */
     MC_INIT_WALL = 1     /* +z for x < Lx/2, -z otherwise (Bloch wall start)    */
@@ -100,6 +108,7 @@ typedef struct mc_desc {
     int n_grains;
     void* stream;           /* cudaStream_t to run on, or NULL for a library stream */
     int device;             /* CUDA device ordinal                                */
+    int kernel_path;        /* mc_kernel_path (default MC_PATH_AUTO)              */
 } mc_desc;
 
 /* Ensemble averages over the measurement sweeps since the last reset

@@ -85,7 +85,8 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const LatParams &pa = lattices[a]->hp, &pb = lattices[b]->hp;
-        if (pa.row_fast != pb.row_fast) return pa.row_fast < pb.row_fast;
+        if ((pa.colour_kernel == kColourGeneral) != (pb.colour_kernel == kColourGeneral))
+            return pa.colour_kernel == kColourGeneral;
         return pa.N < pb.N;
     });
     std::vector<LatDev*> all(n);
@@ -96,48 +97,45 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         sa[j + 1] = sa[j] + hp.nblocks_site;
         sp[j + 1] = sp[j] + hp.nblocks_pair;
     }
-    // colour passes: the FP32 row_fast lattices and the rest (tile starts),
-    // each in launch order
-    std::vector<LatDev*> row, rest;
-    std::vector<uint32_t> srw(1, 0), sr(1, 0);
+    // colour passes: one list per colour-pass kernel (LatParams::colour_kernel),
+    // each with its tile starts, in launch order
+    std::vector<LatDev*> sub[3];
+    std::vector<uint32_t> st[3];
+    for (int c = 0; c < 3; ++c) st[c].assign(1, 0);
     for (int j = 0; j < n; ++j) {
         const LatParams& hp = lattices[order[j]]->hp;
-        if (hp.precision == MC_FP32 && hp.row_fast) {
-            row.push_back(all[j]);
-            srw.push_back(srw.back() + hp.nblocks_site);
-        } else {
-            rest.push_back(all[j]);
-            sr.push_back(sr.back() + hp.nblocks_site);
-        }
+        const int c = hp.colour_kernel;
+        sub[c].push_back(all[j]);
+        st[c].push_back(st[c].back() + hp.nblocks_site);
     }
     cudaSetDevice(g->device);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_ptr = al(sizeof(LatDev*) * n);
     const size_t b_idx = al(sizeof(uint32_t) * (n + 1));
-    const size_t total = 3 * b_ptr + 4 * b_idx;
+    const size_t total = 4 * b_ptr + 5 * b_idx;  // all + 3 kernel lists; site, pair + 3 kernel starts
     cudaError_t e = cudaMalloc(&g->d_mem, total);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(group)"); }
     std::vector<char> host(total, 0);
     char* hb = host.data();
     char* db = static_cast<char*>(g->d_mem);
+    const size_t o0 = 4 * b_ptr;
     std::copy(all.begin(), all.end(), reinterpret_cast<LatDev**>(hb));
-    std::copy(row.begin(), row.end(), reinterpret_cast<LatDev**>(hb + b_ptr));
-    std::copy(rest.begin(), rest.end(), reinterpret_cast<LatDev**>(hb + 2 * b_ptr));
-    const size_t o0 = 3 * b_ptr;
     std::copy(sa.begin(), sa.end(), reinterpret_cast<uint32_t*>(hb + o0));
     std::copy(sp.begin(), sp.end(), reinterpret_cast<uint32_t*>(hb + o0 + b_idx));
-    std::copy(srw.begin(), srw.end(), reinterpret_cast<uint32_t*>(hb + o0 + 2 * b_idx));
-    std::copy(sr.begin(), sr.end(), reinterpret_cast<uint32_t*>(hb + o0 + 3 * b_idx));
     g->ls.all = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0), n};
     g->ls.pairs = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0 + b_idx), n};
-    g->ls.row = GroupArgs{reinterpret_cast<LatDev**>(db + b_ptr), reinterpret_cast<uint32_t*>(db + o0 + 2 * b_idx),
-                          int(row.size())};
-    g->ls.rest = GroupArgs{reinterpret_cast<LatDev**>(db + 2 * b_ptr),
-                           reinterpret_cast<uint32_t*>(db + o0 + 3 * b_idx), int(rest.size())};
     g->ls.nt_all = sa.back();
     g->ls.nt_pairs = sp.back();
-    g->ls.nt_row = srw.back();
-    g->ls.nt_rest = sr.back();
+    GroupArgs* lists[3] = {&g->ls.rest, &g->ls.row, &g->ls.rowx};
+    uint32_t* counts[3] = {&g->ls.nt_rest, &g->ls.nt_row, &g->ls.nt_rowx};
+    for (int c = 0; c < 3; ++c) {
+        const size_t op = size_t(1 + c) * b_ptr, oi = o0 + size_t(2 + c) * b_idx;
+        std::copy(sub[c].begin(), sub[c].end(), reinterpret_cast<LatDev**>(hb + op));
+        std::copy(st[c].begin(), st[c].end(), reinterpret_cast<uint32_t*>(hb + oi));
+        *lists[c] = GroupArgs{reinterpret_cast<LatDev**>(db + op), reinterpret_cast<uint32_t*>(db + oi),
+                              int(sub[c].size())};
+        *counts[c] = st[c].back();
+    }
     g->ls.sample_level = 1;
     for (int i = 0; i < n; ++i)
         if (lattices[i]->hp.sample_torque) g->ls.sample_level = 2;

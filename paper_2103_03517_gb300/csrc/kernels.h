@@ -13,9 +13,10 @@ struct KernelSet {
     // measure: 0 none, 1 magnetisation and energies, 2 also torques.
     void (*colour_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
                         cudaStream_t s);
-    // FP32 colour pass over row_fast lattices (adjacent site pairs per lane).
-    // Null in the FP64 set.
-    void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
+    // FP32 colour pass over lattices in the row layout (adjacent site pairs
+    // per lane); gen = 0: all axes periodic, no film tables; gen = 1: any
+    // boundaries and film tables.  Null in the FP64 set.
+    void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
                      cudaStream_t s);
     // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
@@ -31,13 +32,14 @@ struct KernelSet {
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every
 // lattice (lattice l owns tiles [start[l], start[l+1])), and for the colour
-// passes the split into FP32 row_fast lattices and the others.
+// passes the split by colour-pass kernel (LatParams::colour_kernel).
 struct LaunchSet {
     GroupArgs all, pairs;
     uint32_t nt_all = 0, nt_pairs = 0;
-    // colour passes: the FP32 row_fast lattices and the rest (tiles)
-    GroupArgs row, rest;
-    uint32_t nt_row = 0, nt_rest = 0;
+    // colour passes: row kernel, row kernel with boundaries and films, the
+    // general kernel (tiles)
+    GroupArgs row, rowx, rest;
+    uint32_t nt_row = 0, nt_rowx = 0, nt_rest = 0;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
 };
 

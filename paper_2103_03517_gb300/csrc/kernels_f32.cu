@@ -4,6 +4,9 @@
 #ifndef MC_MINB_F32
 #define MC_MINB_F32 3
 #endif
+#ifndef MC_MINB_GEN_F32
+#define MC_MINB_GEN_F32 2
+#endif
 #include "kernels.h"
 #include "pass_impl.cuh"
 #include "row_pass.cuh"
@@ -13,6 +16,7 @@ namespace {
 
 using R = float;
 constexpr int MINB = MC_MINB_F32;  // minimum resident blocks per SM of the colour pass
+constexpr int MINB_GEN = MC_MINB_GEN_F32;  // the same for the row kernel with boundaries and films
 constexpr int V = kSitesPerThreadF32;
 
 // Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
@@ -47,17 +51,25 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
-template <int MEASURE>
+template <int MEASURE, int GEN>
 void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(row_pass_kernel<MINB, MEASURE>);
-    row_pass_kernel<MINB, MEASURE><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
+    constexpr int B = GEN ? MINB_GEN : MINB;
+    static const uint32_t cap = resident_blocks(row_pass_kernel<B, MEASURE, GEN>);
+    row_pass_kernel<B, MEASURE, GEN><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
 }
 
-void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, cudaStream_t s) {
+template <int GEN>
+void row_pass_g(const GroupArgs& g, uint32_t ntiles, const R* c, int colour, int measure, cudaStream_t s) {
+    if (measure >= 2) row_pass_t<2, GEN>(g, ntiles, c, colour, s);
+    else if (measure == 1) row_pass_t<1, GEN>(g, ntiles, c, colour, s);
+    else row_pass_t<0, GEN>(g, ntiles, c, colour, s);
+}
+
+void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
+              cudaStream_t s) {
     const R* c = static_cast<const R*>(cone);
-    if (measure >= 2) row_pass_t<2>(g, ntiles, c, colour, s);
-    else if (measure == 1) row_pass_t<1>(g, ntiles, c, colour, s);
-    else row_pass_t<0>(g, ntiles, c, colour, s);
+    if (gen) row_pass_g<1>(g, ntiles, c, colour, measure, s);
+    else row_pass_g<0>(g, ntiles, c, colour, measure, s);
 }
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,

@@ -64,6 +64,8 @@ inline FastDiv make_fastdiv(uint32_t d) {
     return f;
 }
 
+enum { kColourGeneral = 0, kColourRow = 1, kColourRowGen = 2 };
+
 struct LatParams {
     int Lx, Ly, Lz, Lh;
     int bc[3];
@@ -83,6 +85,9 @@ struct LatParams {
                             // Lh % 32 == 0, or (FP32) Lh a power of two <= 64 or a
                             // multiple of 64, Nc % 64 == 0: the row paths apply
     int row_lanes;          // FP32 row path: lanes per row group, min(Lh/2, 32)
+    int colour_kernel;      // colour-pass kernel: kColourGeneral, kColourRow (FP32 row
+                            // layout, all axes periodic, no film tables) or
+                            // kColourRowGen (FP32 row layout, any boundaries and films)
     void* spins;
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null

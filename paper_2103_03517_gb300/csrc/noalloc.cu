@@ -103,6 +103,7 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     p.nblocks_pair = (p.n_pairs + 31) / 32 > 0 ? (p.n_pairs + 31) / 32 : 1;
     p.sample_torque = 1;
     p.row_fast = row_fast(p, false);
+    p.colour_kernel = colour_kernel(p, false, MC_PATH_AUTO);
     p.row_lanes = p.Lh / 2 < 32 ? (p.Lh / 2 > 0 ? p.Lh / 2 : 1) : 32;
     p.spins = spins;
     p.ring = reinterpret_cast<double*>(base + kOffRing);
@@ -136,7 +137,7 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     ls.nt_all = p.nblocks_site;
     ls.nt_pairs = p.nblocks_pair;
     ls.sample_level = 2;
-    if (p.row_fast) {  // row or general path (no tensor maps in the scratch)
+    if (p.colour_kernel == kColourRow) {  // every axis periodic: the row kernel or the general one
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
     } else {

@@ -1,18 +1,25 @@
-// row_pass.cuh -- FP32 colour pass (Table A1) over row_fast lattices:
-// periodic lattices whose rows of one colour split evenly over the lanes of a
-// warp tile.  The kernel holds no general-geometry code, so that it runs in
-// fewer registers than the general colour pass.
+// row_pass.cuh -- FP32 colour pass (Table A1) over lattices in the row layout:
+// Lx even, rows of Lh = Lx/2 sites per colour a power of two <= 64 or a
+// multiple of 64, and Nc a multiple of 64, so that every warp tile is full
+// and its rows split evenly over the lanes.  Two instances: GEN = 0 for
+// lattices with every axis periodic and no film tables (the batched m(T)
+// workload), GEN = 1 for any boundary modes (open, pinned, anti-periodic),
+// bond masks and per-grain easy axes (walls, granular films).  Neither holds
+// the general-geometry code of the general colour pass, so that they run in
+// fewer registers.
 //
 // Lane L of a tile of 64 colour indices q0 .. q0 + 63 takes the adjacent pair
 // q = q0 + 2L, q + 1 of one row, so that every spin is read as a float2 (one
-// copy per component for both sites) and one Philox call keys the draws of
+// load per component for both sites) and one Philox call keys the draws of
 // both sites to the first.  Rows of Lh <= 64 sites per colour are covered by
 // groups of G = Lh/2 lanes (row_lanes), rows of Lh > 64 by segments of 64.
 // The other colour's spins at k and k+1 give three of the four x neighbours
 // of the pair; the fourth, at k-1 or k+2, is the neighbouring lane's pair,
 // taken by a warp shuffle inside the row group (wrapping the row) or, at the
 // ends of a 64-site segment of a longer row, loaded on its own.  The
-// neighbour sum keeps the order -x, +x, -y, +y, -z, +z.
+// neighbour sum keeps the order -x, +x, -y, +y, -z, +z.  In the GEN instance
+// every neighbour enters with a factor 1, -1 (across an anti-periodic face)
+// or 0 (absent: open face or missing bond), an exact product.
 #pragma once
 #include "pass_impl.cuh"
 
@@ -22,11 +29,16 @@ constexpr int kRowSlots = 18;  // float2 loads per lane per tile
 
 __device__ __forceinline__ float2 ld2(const float* a, size_t i) { return *reinterpret_cast<const float2*>(a + i); }
 
+// Factor of a neighbour across a face of an axis with boundary mode bc.
+__device__ __forceinline__ float face_factor(int bc) { return bc == 0 ? 1.0f : (bc == 3 ? -1.0f : 0.0f); }
+
 // Spins and neighbour sums of lane L's pair in the tile starting at q0;
 // returns the lattice index of the pair's first site (its parity is the
-// row's x offset).
+// row's x offset).  GEN: mov[v] = site v is not on a pinned plane.
+template <int GEN>
 __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const float* s, int colour, uint32_t q0,
-                                                  int lane, V3<float> S[2], V3<float> h[2], V3<float> O[2]) {
+                                                  int lane, V3<float> S[2], V3<float> h[2], V3<float> O[2],
+                                                  bool mov[2]) {
     const uint32_t stride = p.stride;
     const float* own = s + size_t(3 * colour) * stride;
     const float* oth = s + size_t(3 * (colour ^ 1)) * stride;
@@ -50,6 +62,7 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
     const int gbase = lane & ~(G - 1);
     const int left = gbase | ((lane - 1) & (G - 1));
     const int right = gbase | ((lane + 1) & (G - 1));
+    // other colour at k - 1 (left lane's second) and k + 2 (right lane's first)
     V3<float> lft{__shfl_sync(0xffffffffu, v[3].y, left), __shfl_sync(0xffffffffu, v[4].y, left),
                   __shfl_sync(0xffffffffu, v[5].y, left)};
     V3<float> rgt{__shfl_sync(0xffffffffu, v[3].x, right), __shfl_sync(0xffffffffu, v[4].x, right),
@@ -65,15 +78,50 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
         }
     }
     const V3<float> o0{v[3].x, v[4].x, v[5].x}, o1{v[3].y, v[4].y, v[5].y};
-    // x neighbours: site 0 has o0 and (xoff ? o1 : lft), site 1 has o1 and
-    // (xoff ? rgt : o0); the -x + +x sum is the same either way round
-    const V3<float> a0 = xoff ? o1 : lft, a1 = xoff ? rgt : o0;
-    h[0].x = ((((o0.x + a0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
-    h[0].y = ((((o0.y + a0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
-    h[0].z = ((((o0.z + a0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
-    h[1].x = ((((o1.x + a1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
-    h[1].y = ((((o1.y + a1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
-    h[1].z = ((((o1.z + a1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
+    if constexpr (GEN == 0) {
+        // x neighbours: site 0 has o0 and (xoff ? o1 : lft), site 1 has o1 and
+        // (xoff ? rgt : o0); the -x + +x sum is the same either way round
+        const V3<float> a0 = xoff ? o1 : lft, a1 = xoff ? rgt : o0;
+        h[0].x = ((((o0.x + a0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
+        h[0].y = ((((o0.y + a0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
+        h[0].z = ((((o0.z + a0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
+        h[1].x = ((((o1.x + a1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
+        h[1].y = ((((o1.y + a1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
+        h[1].z = ((((o1.z + a1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
+        mov[0] = mov[1] = true;
+    } else {
+        const int bx = p.bc[0], by = p.bc[1], bz = p.bc[2];
+        const uint32_t x0 = xoff + 2u * k;  // x of site 0; site 1 is at x0 + 2
+        // face factors: -x of site 0, +x of site 1, -y, +y, -z, +z of both
+        const float fxm = x0 == 0 ? face_factor(bx) : 1.0f;
+        const float fxp = x0 + 3 == uint32_t(p.Lx) ? face_factor(bx) : 1.0f;
+        const float fym = y > 0 ? 1.0f : face_factor(by), fyp = y + 1 < Ly ? 1.0f : face_factor(by);
+        const float fzm = z > 0 ? 1.0f : face_factor(bz), fzp = z + 1 < Lz ? 1.0f : face_factor(bz);
+        // bond bits of the two sites (adjacent bytes), all present without a mask
+        const uint32_t mm = p.bonds ? uint32_t(__ldg(reinterpret_cast<const unsigned short*>(
+                                          p.bonds + size_t(colour) * stride + q)))
+                                    : 0x3F3Fu;
+        auto fac = [mm](int bit, float base) { return ((mm >> bit) & 1u) ? base : 0.0f; };
+        const V3<float> xm0 = xoff ? o0 : lft, xp0 = xoff ? o1 : o0;
+        const V3<float> xm1 = xoff ? o1 : o0, xp1 = xoff ? rgt : o1;
+        {
+            const float a = fac(0, fxm), b = fac(1, 1.0f), c = fac(2, fym), d = fac(3, fyp), e = fac(4, fzm),
+                        f = fac(5, fzp);
+            h[0].x = ((((a * xm0.x + b * xp0.x) + c * v[6].x) + d * v[9].x) + e * v[12].x) + f * v[15].x;
+            h[0].y = ((((a * xm0.y + b * xp0.y) + c * v[7].x) + d * v[10].x) + e * v[13].x) + f * v[16].x;
+            h[0].z = ((((a * xm0.z + b * xp0.z) + c * v[8].x) + d * v[11].x) + e * v[14].x) + f * v[17].x;
+        }
+        {
+            const float a = fac(8, 1.0f), b = fac(9, fxp), c = fac(10, fym), d = fac(11, fyp), e = fac(12, fzm),
+                        f = fac(13, fzp);
+            h[1].x = ((((a * xm1.x + b * xp1.x) + c * v[6].y) + d * v[9].y) + e * v[12].y) + f * v[15].y;
+            h[1].y = ((((a * xm1.y + b * xp1.y) + c * v[7].y) + d * v[10].y) + e * v[13].y) + f * v[16].y;
+            h[1].z = ((((a * xm1.z + b * xp1.z) + c * v[8].y) + d * v[11].y) + e * v[14].y) + f * v[17].y;
+        }
+        const bool row_pinned = (by == 2 && (y == 0 || y + 1 == Ly)) || (bz == 2 && (z == 0 || z + 1 == Lz));
+        mov[0] = !row_pinned && !(bx == 2 && x0 == 0);
+        mov[1] = !row_pinned && !(bx == 2 && x0 + 3 == uint32_t(p.Lx));
+    }
     S[0] = V3<float>{v[0].x, v[1].x, v[2].x};
     S[1] = V3<float>{v[0].y, v[1].y, v[2].y};
     O[0] = o0;
@@ -81,7 +129,14 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
     return xoff + 2u * k + uint32_t(p.Lx) * row;
 }
 
-template <int MINB, int MEASURE>
+// Easy axis of grain table entry g (float4 rows).
+__device__ __forceinline__ V3<float> grain_axis(const LatParams& p, int colour, uint32_t q) {
+    const int32_t g = __ldg(&p.grain[uint32_t(colour) * p.stride + q]);
+    const float4 a = __ldg(static_cast<const float4*>(p.gaxis) + g);
+    return V3<float>{a.x, a.y, a.z};
+}
+
+template <int MINB, int MEASURE, int GEN>
 __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uint32_t ntiles,
                                                                 const float* __restrict__ cone, int colour) {
     constexpr int NS = MEASURE >= 2 ? kNumSums : kSumTux;  // sums sampled
@@ -104,8 +159,16 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         unsigned nacc = 0;
         long long fix = 0;
         for (; tile < t1; ++tile) {
+            const uint32_t q0 = (tile - t0) * 64u;
             V3<float> S[2], h[2], O[2];
-            const uint32_t site0 = row_pair_sums(p, s, colour, (tile - t0) * 64u, lane, S, h, O);
+            bool mov[2];
+            const uint32_t site0 = row_pair_sums<GEN>(p, s, colour, q0, lane, S, h, O, mov);
+            V3<float> e[2] = {e_ax, e_ax};
+            if constexpr (GEN != 0) {
+                if (p.grain)
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) e[v] = grain_axis(p, colour, q0 + 2u * uint32_t(lane) + v);
+            }
             const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), p.key0, p.key1);
             float P[2], sd[2], cp[2], sp[2];
             direct_draw_two(w, P, sd, cp, sp);
@@ -114,13 +177,13 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
-                const bool acc = metropolis(delta_e(par, S[v], Sn, h[v], e_ax), par.T, P[v]);
+                const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par.T, P[v]);
                 Sf[v] = acc ? Sn : S[v];
                 nacc += acc ? 1u : 0u;
                 any = any || acc;
             }
             if (any) {  // both sites of the pair in one 8-byte store per component
-                float* own = s + size_t(3 * colour) * p.stride + (tile - t0) * 64u + 2u * uint32_t(lane);
+                float* own = s + size_t(3 * colour) * p.stride + q0 + 2u * uint32_t(lane);
                 *reinterpret_cast<float2*>(own) = make_float2(Sf[0].x, Sf[1].x);
                 *reinterpret_cast<float2*>(own + p.stride) = make_float2(Sf[0].y, Sf[1].y);
                 *reinterpret_cast<float2*>(own + 2 * size_t(p.stride)) = make_float2(Sf[0].z, Sf[1].z);
@@ -132,9 +195,12 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                 const bool nu = par.Ku != 0.0f, nc = par.Kc != 0.0f;
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
-                    add_site<float, MEASURE>(sums, Sf[v], e_ax, nu, nc);
+                    V3<float> eo = e_ax;
+                    if constexpr (GEN != 0)
+                        if (p.grain) eo = grain_axis(p, colour ^ 1, q0 + 2u * uint32_t(lane) + v);
+                    add_site<float, MEASURE>(sums, Sf[v], e[v], nu, nc);
                     sums.v[kSumEx] += Sf[v].x * h[v].x + Sf[v].y * h[v].y + Sf[v].z * h[v].z;
-                    add_site<float, MEASURE>(sums, O[v], e_ax, nu, nc);
+                    add_site<float, MEASURE>(sums, O[v], eo, nu, nc);
                 }
                 fix += warp_tile_fix<float, NS>(sums, lane);
             }

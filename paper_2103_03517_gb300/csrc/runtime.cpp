@@ -106,13 +106,26 @@ static int feistel_half_bits(uint32_t n) {
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Whether a lattice takes the row paths of the colour pass (see LatParams).
+// FP32 row layout: rows of Lh sites per colour split evenly over the lanes
+// of a 64-site tile (Lh a power of two <= 64, or a multiple of 64) and
+// whole tiles (Nc % 64 == 0).
+static bool row_layout(const LatParams& p) {
+    const bool pow2_small = p.Lh >= 2 && p.Lh <= 64 && (p.Lh & (p.Lh - 1)) == 0;
+    const bool long_rows = p.Lh % 64 == 0;
+    return (pow2_small || long_rows) && p.Nc % 64 == 0;
+}
+
+// Whether a lattice takes the periodic row paths (see LatParams).
 int row_fast(const LatParams& p, bool film) {
     if (film || p.bc[0] != MC_PERIODIC || p.bc[1] != MC_PERIODIC || p.bc[2] != MC_PERIODIC) return 0;
     if (p.precision == MC_FP64) return p.Lh % 32 == 0 ? 1 : 0;
-    const bool pow2_small = p.Lh >= 2 && p.Lh <= 64 && (p.Lh & (p.Lh - 1)) == 0;
-    const bool long_rows = p.Lh % 64 == 0;
-    return (pow2_small || long_rows) && p.Nc % 64 == 0 ? 1 : 0;
+    return row_layout(p) ? 1 : 0;
+}
+
+// Colour-pass kernel of a lattice (LatParams::colour_kernel).
+int colour_kernel(const LatParams& p, bool film, int path) {
+    if (p.precision != MC_FP32 || path == MC_PATH_GENERAL || !row_layout(p)) return kColourGeneral;
+    return row_fast(p, film) ? kColourRow : kColourRowGen;
 }
 
 // ------------------------------------------------------------- lattices
@@ -153,6 +166,8 @@ int validate_desc(const mc_desc* d) {
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
     if (!(an > 0.0)) return fail(MC_ERR_ARG, "|axis| = 0");
     if (d->precision != MC_FP32 && d->precision != MC_FP64) return fail(MC_ERR_ARG, "precision invalid");
+    if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL)
+        return fail(MC_ERR_ARG, "kernel_path invalid");
     if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
     if (d->init != MC_INIT_UNIFORM && d->init != MC_INIT_WALL) return fail(MC_ERR_ARG, "init invalid");
     if (d->init == MC_INIT_UNIFORM) {
@@ -287,6 +302,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.n_pairs = p.Nc / 2;
     p.perm_h = feistel_half_bits(p.Nc);
     p.row_fast = row_fast(p, d->bond_mask != nullptr || d->grain_id != nullptr);
+    p.colour_kernel = colour_kernel(p, d->bond_mask != nullptr || d->grain_id != nullptr, d->kernel_path);
     p.row_lanes = p.Lh / 2 < 32 ? (p.Lh / 2 > 0 ? p.Lh / 2 : 1) : 32;
     long long pinned = 0;
     for (int z = 0; z < p.Lz; ++z)
@@ -435,7 +451,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     return MC_OK;
 }
 
-// Launch tables of the lattice alone (it is either row_fast or not).
+// Launch tables of the lattice alone (one colour-pass kernel).
 LaunchSet single_launch_set(mc_lattice* h) {
     LaunchSet ls;
     ls.all = GroupArgs{h->d_group_lats, h->d_group_start, 1};
@@ -443,9 +459,12 @@ LaunchSet single_launch_set(mc_lattice* h) {
     ls.nt_all = h->hp.nblocks_site;
     ls.nt_pairs = h->hp.nblocks_pair;
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
-    if (h->hp.precision == MC_FP32 && h->hp.row_fast) {
+    if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
+    } else if (h->hp.colour_kernel == kColourRowGen) {
+        ls.rowx = ls.all;
+        ls.nt_rowx = ls.nt_all;
     } else {
         ls.rest = ls.all;
         ls.nt_rest = ls.nt_all;
@@ -471,7 +490,8 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto colour_pass = [&](int colour, int meas) {
-        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, s);
+        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, 0, s);
+        if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, s);
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
     for (int i = 0; i < n; ++i) {
@@ -755,7 +775,7 @@ MC_API int mc_get_theta(mc_handle h, int* theta_deg, int64_t* sweeps_done) {
 }
 
 // ------------------------------------------------------------- checkpoint
-static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '1'};
+static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '2'};
 
 MC_API int mc_save(mc_handle h, const char* path) {
     if (!h || !path) return fail(MC_ERR_ARG, "null argument");

@@ -323,33 +323,80 @@ def test_group_constrained_equals_alone_bitwise():
             mc.mc_destroy(h)
 
 
+def _one_sweep_pair(dims, kw_a, kw_b, spins, n_sweeps=1):
+    """Spins and energy of two lattices started from the same spins after
+    n_sweeps measured sweeps."""
+    out = []
+    for kw in (kw_a, kw_b):
+        h = mc.mc_create_ex(mc.make_desc(dims, **kw))
+        try:
+            mc.mc_set_spins(h, spins)
+            mc.mc_sweep(h, n_sweeps, measure=True)
+            out.append((mc.mc_get_spins(h, len(spins)), mc.mc_measure(h).e))
+        finally:
+            mc.mc_destroy(h)
+    return out
+
+
+def _assert_same_chain(spins, a, b, label):
+    (sa, ea), (sb, eb) = a, b
+    moved = np.any(sa != spins, axis=1).mean()
+    assert moved > 0.2, (label, moved)
+    close = np.all(np.abs(sa - sb) < 1e-5, axis=1)
+    assert close.mean() > 0.999, (label, close.mean())
+    assert abs(ea - eb) < 1e-5, (label, ea, eb)
+
+
 @pytest.mark.parametrize("dims", [(16, 16, 16), (8, 8, 8), (4, 4, 8), (64, 32, 8), (128, 8, 4), (256, 4, 4),
-                                  (384, 2, 2),
-                                  # rows of 32..256 sites per colour on larger bricks
-                                  (64, 64, 16), (128, 16, 32), (128, 8, 16), (256, 8, 16), (512, 4, 16), (512, 2, 32)])
-def test_fp32_row_path_matches_general_path(dims):
-    """FP32: a periodic lattice takes the row kernel; the same lattice with an
-    all-ones bond mask (identical physics) takes the general path.  Both key
-    the same draws to the same sites, so one sweep gives the same spins up to
-    FP32 rounding; a wrong neighbour would change many sites by O(1)."""
+                                  (384, 2, 2), (64, 64, 16), (128, 16, 32), (128, 8, 16), (256, 8, 16), (512, 4, 16),
+                                  (512, 2, 32)])
+def test_fp32_row_kernels_match_general_kernel(dims):
+    """FP32, every axis periodic: the row kernel (no film tables), the row
+    kernel with boundaries and films (an all-ones bond mask, the same
+    physics) and the general kernel (forced) key the same draws to the same
+    sites, so one sweep gives the same spins up to FP32 rounding; a wrong
+    neighbour would change many sites by O(1)."""
     N = dims[0] * dims[1] * dims[2]
     spins = workloads.random_spins(N, 7)
     kw = dict(K_u=0.05, K_c=0.02, H=(0.02, 0.0, 0.05), T=0.9, seed=12, ring_capacity=8)
-    a = mc.mc_create_ex(mc.make_desc(dims, **kw))
-    b = mc.mc_create_ex(mc.make_desc(dims, bond_mask=np.full(N, 0x3F, np.uint8), **kw))
-    try:
-        for h in (a, b):
-            mc.mc_set_spins(h, spins)
-            mc.mc_sweep(h, 1, measure=True)
-        sa, sb = mc.mc_get_spins(a, N), mc.mc_get_spins(b, N)
-        moved = np.any(sa != spins, axis=1).mean()
-        assert moved > 0.2
-        close = np.all(np.abs(sa - sb) < 1e-5, axis=1)
-        assert close.mean() > 0.999, (dims, close.mean())
-        assert abs(mc.mc_measure(a).e - mc.mc_measure(b).e) < 1e-5
-    finally:
-        mc.mc_destroy(a)
-        mc.mc_destroy(b)
+    row, gen = _one_sweep_pair(dims, kw, dict(kw, kernel_path=mc.MC_PATH_GENERAL), spins)
+    _assert_same_chain(spins, row, gen, f"row {dims}")
+    rowx, gen2 = _one_sweep_pair(dims, dict(kw, bond_mask=np.full(N, 0x3F, np.uint8)),
+                                 dict(kw, kernel_path=mc.MC_PATH_GENERAL), spins)
+    _assert_same_chain(spins, rowx, gen2, f"rowx {dims}")
+
+
+ROWX_CASES = [
+    ((64, 16, 8), (3, 0, 0), False),     # anti-periodic x (the wall setup)
+    ((128, 8, 6), (2, 0, 0), False),     # pinned x planes
+    ((32, 9, 4), (1, 1, 1), False),      # all open, odd Ly
+    ((16, 8, 4), (0, 3, 1), False),      # anti-periodic y, open z
+    ((256, 6, 4), (3, 2, 3), False),     # long rows, pinned y, anti-periodic z
+    ((64, 64, 4), (0, 0, 1), True),      # film: bond mask and grain axes, open z
+    ((128, 32, 3), (3, 0, 1), True),     # film on an anti-periodic x
+]
+
+
+@pytest.mark.parametrize("dims,bc,film", ROWX_CASES)
+def test_fp32_row_kernel_with_boundaries_matches_general_kernel(dims, bc, film):
+    """FP32 lattices in the row layout with open, pinned and anti-periodic
+    faces, bond masks and grain axes: the row kernel and the general kernel
+    (forced) run the same chain."""
+    Lh = dims[0] // 2
+    assert (Lh & (Lh - 1) == 0 and Lh <= 64) or Lh % 64 == 0
+    assert (Lh * dims[1] * dims[2]) % 64 == 0  # the row layout, so AUTO takes the row kernel
+    N = dims[0] * dims[1] * dims[2]
+    spins = workloads.random_spins(N, 3)
+    kw = dict(K_u=0.05, K_c=0.02, H=(0.01, 0.02, 0.05), T=0.8, seed=21, ring_capacity=8, boundary=bc)
+    if film:
+        gid, mask, axes = workloads.voronoi_film(dims[0], dims[1], dims[2], 6.0, seed=2)
+        kw.update(bond_mask=mask, grain_id=gid, grain_axis=axes)
+    for n in (1, 3):
+        a, b = _one_sweep_pair(dims, kw, dict(kw, kernel_path=mc.MC_PATH_GENERAL), spins, n_sweeps=n)
+        if n == 1:
+            _assert_same_chain(spins, a, b, f"{dims} {bc} film={film}")
+        else:  # a few sweeps: still the same chain on nearly every site
+            assert np.all(np.abs(a[0] - b[0]) < 1e-4, axis=1).mean() > 0.99
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (64, 8, 4)])
