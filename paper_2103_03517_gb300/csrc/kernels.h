@@ -25,6 +25,9 @@ struct KernelSet {
     void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Standalone sample + end of sweep (site tiles).
     void (*measure)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
+    // The same over lattices in the row layout (gen as in row_pass).  Null
+    // in the FP64 set.
+    void (*row_sample)(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s);
     // Slice sums for the profile of one lattice.
     void (*profile)(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s);
     const char* name;

@@ -7,6 +7,12 @@
 #ifndef MC_MINB_GEN_F32
 #define MC_MINB_GEN_F32 2
 #endif
+#ifndef MC_MINB_PAIR_F32
+#define MC_MINB_PAIR_F32 3
+#endif
+#ifndef MC_PAIR_CHUNK
+#define MC_PAIR_CHUNK 4
+#endif
 #include "kernels.h"
 #include "pass_impl.cuh"
 #include "row_pass.cuh"
@@ -17,6 +23,8 @@ namespace {
 using R = float;
 constexpr int MINB = MC_MINB_F32;  // minimum resident blocks per SM of the colour pass
 constexpr int MINB_GEN = MC_MINB_GEN_F32;  // the same for the row kernel with boundaries and films
+constexpr int MINB_PAIR = MC_MINB_PAIR_F32;  // the same for the pair pass
+constexpr int kPairChunk = MC_PAIR_CHUNK;    // consecutive pair tiles per grid-stride step
 constexpr int V = kSitesPerThreadF32;
 
 // Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
@@ -72,11 +80,23 @@ void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour,
     else row_pass_g<0>(g, ntiles, c, colour, measure, s);
 }
 
+template <int GEN>
+void row_sample_g(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
+    constexpr int B = GEN ? MINB_GEN : MINB;
+    static const uint32_t cap = resident_blocks(row_pass_kernel<B, 2, GEN, 0>);
+    row_pass_kernel<B, 2, GEN, 0><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, nullptr, 1);
+}
+
+void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
+    if (gen) row_sample_g<1>(g, ntiles, s);
+    else row_sample_g<0>(g, ntiles, s);
+}
+
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
                cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R>);
-    pair_pass_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, static_cast<const R*>(cone), colour,
-                                                                 finalize, measure);
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, MINB_PAIR, kPairChunk>);
+    pair_pass_kernel<R, MINB_PAIR, kPairChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+        g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
 }
 
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
@@ -97,7 +117,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, mlong, measure, profile, "f32"};
+    static const KernelSet k{colour_pass, row_pass, pair_pass, mlong, measure, row_sample, profile, "f32"};
     return k;
 }
 

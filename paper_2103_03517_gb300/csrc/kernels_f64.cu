@@ -10,6 +10,7 @@ namespace {
 using R = double;
 constexpr int MINB = 1;  // minimum resident blocks per SM of the colour pass
 constexpr int V = kSitesPerThreadF64;
+constexpr int kPairChunk = 4;  // consecutive pair tiles per grid-stride step of the pair pass
 
 // Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
 // the process is assumed representative; computed once per kernel).
@@ -45,9 +46,9 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
                cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R>);
-    pair_pass_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, static_cast<const R*>(cone), colour,
-                                                                 finalize, measure);
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, kPairChunk>);
+    pair_pass_kernel<R, 1, kPairChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+        g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
 }
 
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
@@ -68,7 +69,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f64() {
-    static const KernelSet k{colour_pass, nullptr, pair_pass, mlong, measure, profile, "f64"};
+    static const KernelSet k{colour_pass, nullptr, pair_pass, mlong, measure, nullptr, profile, "f64"};
     return k;
 }
 

@@ -848,7 +848,7 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 
 // ------------------------------------------------------------------------
 // Constrained pair pass of Table A2 (one lane per pair), batched, warp tiles
-// of 32 pairs.  Pairs are (pi(2p), pi(2p+1)) of the colour's shuffled
+// of 32 pairs (pair_move below, pair_pass_kernel after it).  Pairs are (pi(2p), pi(2p+1)) of the colour's shuffled
 // indices; the cone move is made on i in the frame whose x-axis is e_C, j
 // compensates the transverse components, x'_j = sign(x_j) sqrt(|S_j|^2 -
 // y'_j^2 - z'_j^2).  The pair is accepted iff
@@ -858,99 +858,118 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // packed copy (one sector per site instead of one per component); accepted
 // moves are written to the spins and to the copy of the pass's colour.
 // ------------------------------------------------------------------------
+// One pair of the pass (pair index pr of the lattice); returns the accepted
+// spin count (0 or 2).  The gathers of both spins and of their neighbours
+// are issued together, before the move is drawn, so that one L2 round trip
+// covers all of them; the move's result does not depend on that order.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) pair_pass_kernel(GroupArgs g, uint32_t ntiles, const R* __restrict__ cone,
-                                                           int colour, int finalize, int measure) {
-    // Tiles in grid-stride order: at any moment the warps hold a window of
-    // about one tile each, one or two lattices of the batch, so that the
-    // random gathers of partners and their neighbours stay in L2.
+__device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
+                                              Spin4<R>* own4, const Spin4<R>* oth4, uint32_t pr, uint4 rk, R c,
+                                              uint32_t sweep, int colour, double ML) {
+    const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
+    const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+    const Geo gi = geometry(p, colour, qi);
+    const Geo gj = geometry(p, colour, qj);
+    uint32_t nqi[6], nqj[6];
+    const uint32_t pi_ = neighbours(p, gi, colour, nqi);
+    const uint32_t pj_ = neighbours(p, gj, colour, nqj);
+    const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
+    const V3<R> h_i = neighbour_sum4(oth4, nqi, pi_);
+    const V3<R> h_j = neighbour_sum4(oth4, nqj, pj_);
+    const V3<R> Si{si4.x, si4.y, si4.z};
+    const V3<R> Sj{sj4.x, sj4.y, sj4.z};
+    const V3<R> hi = rotate(par.Rm, Si);
+    const V3<R> hj = rotate(par.Rm, Sj);
+    V3<R> hni;
+    R P;
+    if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) return 0;
+    const R ynj = (hj.y + hi.y) - hni.y;
+    const R znj = (hj.z + hi.z) - hni.z;
+    const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
+    if (!(t > R(0))) return 0;
+    R xnj = sqrt(t);
+    if (hj.x < R(0)) xnj = -xnj;
+    bool ok;
+    R rM;
+    if constexpr (kIsF64<R>) {
+        const double MLn = ML + hni.x + xnj - hi.x - hj.x;
+        ok = MLn > 0.0;
+        const double ratio = MLn / ML;
+        rM = ratio * ratio;
+    } else {
+        // FP32 spins: the change of M_L is evaluated in FP32 and applied to
+        // the FP64 M_L as (1 + delta / M_L)^2.
+        const float fml = float(ML);
+        const float delta = ((hni.x + xnj) - hi.x) - hj.x;
+        ok = fml + delta > 0.0f;
+        const float ratio = 1.0f + delta / fml;
+        rM = ratio * ratio;
+    }
+    if (!ok) return 0;
+    const V3<R> hnj{xnj, ynj, znj};
+    const V3<R> Sni = rotate_back(par.Rm, hni);
+    const V3<R> Snj = rotate_back(par.Rm, hnj);
+    const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
+    const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
+    const R dE = dEi + dEj;
+    R r = rM;
+    r = r * (fabs(hj.x) / fabs(xnj));
+    if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
+    else r = r * __expf(-__fdividef(dE, par.T));
+    if (!(P < r)) return 0;
+    store_spin(s, p.stride, colour, qi, Sni);
+    store_spin(s, p.stride, colour, qj, Snj);
+    own4[qi] = Spin4<R>{Sni.x, Sni.y, Sni.z, R(0)};
+    own4[qj] = Spin4<R>{Snj.x, Snj.y, Snj.z, R(0)};
+    return 2;
+}
+
+// Tiles are taken in grid-stride order, CHUNK consecutive tiles per step: at
+// any moment the warps hold a window of about CHUNK tiles each, a few
+// lattices of the batch, so that the random gathers of partners and their
+// neighbours stay in L2.  A warp publishes once per lattice in a chunk.
+template <typename R, int MINB, int CHUNK>
+__global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
+                                                                 const R* __restrict__ cone, int colour, int finalize,
+                                                                 int measure) {
     const int lane = int(threadIdx.x & 31);
     const int other = colour ^ 1;
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
+    const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
     int l = 0;
-    for (uint32_t tile = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
-        while (__ldg(&g.start[l + 1]) <= tile) ++l;
-        LatDev* L = g.lats[l];
-        const LatParams& p = L->p;
-        const uint32_t pr = (tile - __ldg(&g.start[l])) * 32u + uint32_t(lane);
-        const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
-        Spin4<R>* a4 = static_cast<Spin4<R>*>(p.aos);
-        unsigned nacc = 0;
-        if (!(ML > 0.0)) {
-            if (lane == 0) atomicCAS(&L->st.error, 0, -5);
-        } else if (!a4) {
-            if (lane == 0) atomicCAS(&L->st.error, 0, -6);
-        } else if (pr < p.n_pairs) {
-            const float fml = float(ML);
-            const Par<R> par = load_par<R>(p);
-            const R c = cone[L->st.theta];
-            const uint32_t sweep = L->st.sweep;
-            R* __restrict__ s = static_cast<R*>(p.spins);
-            const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
-            [&] {
-                const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
-                const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+    for (uint32_t c0 = w * CHUNK; c0 < ntiles; c0 += nwarps * CHUNK) {
+        const uint32_t c1 = min(c0 + uint32_t(CHUNK), ntiles);
+        for (uint32_t tile = c0; tile < c1;) {
+            while (__ldg(&g.start[l + 1]) <= tile) ++l;
+            const uint32_t t0 = __ldg(&g.start[l]);
+            const uint32_t t1 = min(__ldg(&g.start[l + 1]), c1);
+            LatDev* L = g.lats[l];
+            const LatParams& p = L->p;
+            const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
+            Spin4<R>* a4 = static_cast<Spin4<R>*>(p.aos);
+            unsigned nacc = 0;
+            if (!(ML > 0.0)) {
+                if (lane == 0) atomicCAS(&L->st.error, 0, -5);
+            } else if (!a4) {
+                if (lane == 0) atomicCAS(&L->st.error, 0, -6);
+            } else {
+                const Par<R> par = load_par<R>(p);
+                const R c = cone[L->st.theta];
+                const uint32_t sweep = L->st.sweep;
+                R* __restrict__ s = static_cast<R*>(p.spins);
+                const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
                 Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
                 const Spin4<R>* oth4 = a4 + size_t(other) * p.stride;
-                const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
-                const V3<R> Si{si4.x, si4.y, si4.z};
-                const V3<R> Sj{sj4.x, sj4.y, sj4.z};
-                const V3<R> hi = rotate(par.Rm, Si);
-                const V3<R> hj = rotate(par.Rm, Sj);
-                V3<R> hni;
-                R P;
-                if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) return;
-                const R ynj = (hj.y + hi.y) - hni.y;
-                const R znj = (hj.z + hi.z) - hni.z;
-                const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
-                if (!(t > R(0))) return;
-                R xnj = sqrt(t);
-                if (hj.x < R(0)) xnj = -xnj;
-                bool ok;
-                R rM;
-                if constexpr (kIsF64<R>) {
-                    const double MLn = ML + hni.x + xnj - hi.x - hj.x;
-                    ok = MLn > 0.0;
-                    const double ratio = MLn / ML;
-                    rM = ratio * ratio;
-                } else {
-                    // FP32 spins: the change of M_L is evaluated in FP32 and
-                    // applied to the FP64 M_L as (1 + delta / M_L)^2.
-                    const float delta = ((hni.x + xnj) - hi.x) - hj.x;
-                    ok = fml + delta > 0.0f;
-                    const float ratio = 1.0f + delta / fml;
-                    rM = ratio * ratio;
+                for (uint32_t t = tile; t < t1; ++t) {
+                    const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
+                    if (pr < p.n_pairs) nacc += pair_move<R>(p, par, s, own4, oth4, pr, rk, c, sweep, colour, ML);
                 }
-                if (!ok) return;
-                const V3<R> hnj{xnj, ynj, znj};
-                const V3<R> Sni = rotate_back(par.Rm, hni);
-                const V3<R> Snj = rotate_back(par.Rm, hnj);
-                const Geo gi = geometry(p, colour, qi);
-                const Geo gj = geometry(p, colour, qj);
-                uint32_t nqi[6], nqj[6];
-                const uint32_t pi_ = neighbours(p, gi, colour, nqi);
-                const uint32_t pj_ = neighbours(p, gj, colour, nqj);
-                const V3<R> h_i = neighbour_sum4(oth4, nqi, pi_);
-                const V3<R> h_j = neighbour_sum4(oth4, nqj, pj_);
-                const R dEi = delta_e(par, Si, Sni, h_i, easy_axis(p, par, colour, qi));
-                const R dEj = delta_e(par, Sj, Snj, h_j, easy_axis(p, par, colour, qj));
-                const R dE = dEi + dEj;
-                R r = rM;
-                r = r * (fabs(hj.x) / fabs(xnj));
-                if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
-                else r = r * __expf(-__fdividef(dE, par.T));
-                if (P < r) {
-                    store_spin(s, p.stride, colour, qi, Sni);
-                    store_spin(s, p.stride, colour, qj, Snj);
-                    own4[qi] = Spin4<R>{Sni.x, Sni.y, Sni.z, R(0)};
-                    own4[qj] = Spin4<R>{Snj.x, Snj.y, Snj.z, R(0)};
-                    nacc += 2;
-                }
-            }();
+            }
+            publish(L->st, lane, nacc, false, 0, colour, t1 - tile, p.nblocks_pair, [&] {
+                if (finalize) finalize_sweep(p, L->st, measure, true);
+            });
+            tile = t1;
         }
-        publish(L->st, lane, nacc, false, 0, colour, 1, p.nblocks_pair, [&] {
-            if (finalize) finalize_sweep(p, L->st, measure, true);
-        });
     }
 }
 

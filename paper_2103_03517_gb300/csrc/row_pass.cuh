@@ -136,7 +136,10 @@ __device__ __forceinline__ V3<float> grain_axis(const LatParams& p, int colour, 
     return V3<float>{a.x, a.y, a.z};
 }
 
-template <int MINB, int MEASURE, int GEN>
+// MOVE = 0: no moves; the sample of the current state with colour = 1 (each
+// black site, the red site with its index and its six bonds), closing the
+// lattice's sweep as the standalone sample does after a constrained sweep.
+template <int MINB, int MEASURE, int GEN, int MOVE = 1>
 __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uint32_t ntiles,
                                                                 const float* __restrict__ cone, int colour) {
     constexpr int NS = MEASURE >= 2 ? kNumSums : kSumTux;  // sums sampled
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         const uint32_t t1 = min(__ldg(&g.start[l + 1]), wc.end);
         const uint32_t run = t1 - tile;
         const Par<float> par = load_par<float>(p);
-        const float c = cone[L->st.theta];
+        const float c = MOVE ? cone[L->st.theta] : 0.0f;
         const uint32_t sweep = L->st.sweep;
         float* __restrict__ s = static_cast<float*>(p.spins);
         const V3<float> e_ax{par.e[0], par.e[1], par.e[2]};
@@ -169,18 +172,20 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
 #pragma unroll
                     for (int v = 0; v < 2; ++v) e[v] = grain_axis(p, colour, q0 + 2u * uint32_t(lane) + v);
             }
-            const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), p.key0, p.key1);
-            float P[2], sd[2], cp[2], sp[2];
-            direct_draw_two(w, P, sd, cp, sp);
-            V3<float> Sf[2];
+            V3<float> Sf[2] = {S[0], S[1]};
             bool any = false;
+            if constexpr (MOVE != 0) {
+                const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), p.key0, p.key1);
+                float P[2], sd[2], cp[2], sp[2];
+                direct_draw_two(w, P, sd, cp, sp);
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
-                const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par.T, P[v]);
-                Sf[v] = acc ? Sn : S[v];
-                nacc += acc ? 1u : 0u;
-                any = any || acc;
+                for (int v = 0; v < 2; ++v) {
+                    const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
+                    const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par.T, P[v]);
+                    Sf[v] = acc ? Sn : S[v];
+                    nacc += acc ? 1u : 0u;
+                    any = any || acc;
+                }
             }
             if (any) {  // both sites of the pair in one 8-byte store per component
                 float* own = s + size_t(3 * colour) * p.stride + q0 + 2u * uint32_t(lane);
@@ -205,9 +210,13 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                 fix += warp_tile_fix<float, NS>(sums, lane);
             }
         }
-        publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, [&] {
-            if (colour == 1) finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0);
-        });
+        if constexpr (MOVE != 0) {
+            publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, [&] {
+                if (colour == 1) finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0);
+            });
+        } else {
+            publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, [&] { finalize_sweep(p, L->st, 1, true); });
+        }
         ++l;
     }
 }

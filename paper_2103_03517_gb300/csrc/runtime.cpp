@@ -502,7 +502,15 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             k.mlong(ls.all, ls.nt_all, s);
             timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 0, 0, 0, s); });
             timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 1, measure ? 0 : 1, 0, s); });
-            if (measure) k.measure(ls.all, ls.nt_all, s);
+            if (measure) {
+                if (k.row_sample) {  // row-layout lattices sample in the row kernels
+                    if (ls.nt_row) k.row_sample(ls.row, ls.nt_row, 0, s);
+                    if (ls.nt_rowx) k.row_sample(ls.rowx, ls.nt_rowx, 1, s);
+                    if (ls.nt_rest) k.measure(ls.rest, ls.nt_rest, s);
+                } else {
+                    k.measure(ls.all, ls.nt_all, s);
+                }
+            }
         }
     }
     cudaError_t e = cudaGetLastError();
