@@ -101,6 +101,7 @@ struct LatParams {
                             // lattice's first constrained sweep
     double J, Ku, e[3], Kc, H[3], T;
     float fJ, fKu, fe[3], fKc, fH[3], fT;
+    float fBeta2;           // FP32 Metropolis test: -log2(e) / T, so exp(-dE/T) = 2^(dE fBeta2)
     double R[9];            // constraint frame rows e1 = e_C, e2, e3
     float fR[9];
 };

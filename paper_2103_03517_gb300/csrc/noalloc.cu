@@ -112,6 +112,7 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     const double an = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
     for (int a = 0; a < 3; ++a) { p.e[a] = axis[a] / an; p.H[a] = H[a]; }
     p.fJ = (float)p.J; p.fKu = (float)p.Ku; p.fKc = (float)p.Kc; p.fT = (float)p.T;
+    p.fBeta2 = (float)(-1.4426950408889634 / p.T);  // log2(e) = 1 / ln 2
     for (int a = 0; a < 3; ++a) { p.fe[a] = (float)p.e[a]; p.fH[a] = (float)p.H[a]; }
     host.st.theta = *theta_deg;
     host.st.sweep = uint32_t(first_sweep);

@@ -16,6 +16,7 @@ constexpr bool kIsF64 = std::is_same<R, double>::value;
 template <typename R>
 struct Par {
     R J, Ku, e[3], Kc, H[3], T;
+    R beta2;  // FP32: -log2(e) / T (unused in FP64)
     R Rm[9];
 };
 
@@ -24,10 +25,12 @@ __device__ __forceinline__ Par<R> load_par(const LatParams& p) {
     Par<R> q;
     if constexpr (kIsF64<R>) {
         q.J = p.J; q.Ku = p.Ku; q.Kc = p.Kc; q.T = p.T;
+        q.beta2 = 0.0;
         for (int a = 0; a < 3; ++a) { q.e[a] = p.e[a]; q.H[a] = p.H[a]; }
         for (int a = 0; a < 9; ++a) q.Rm[a] = p.R[a];
     } else {
         q.J = p.fJ; q.Ku = p.fKu; q.Kc = p.fKc; q.T = p.fT;
+        q.beta2 = p.fBeta2;
         for (int a = 0; a < 3; ++a) { q.e[a] = p.fe[a]; q.H[a] = p.fH[a]; }
         for (int a = 0; a < 9; ++a) q.Rm[a] = p.fR[a];
     }
@@ -279,19 +282,21 @@ __device__ __forceinline__ void direct_draw(uint4 w, float& s, float& cp, float&
     __sincosf(phi, &sp, &cp);
 }
 
+// FP32 trial point: the cap point at z' = 1 - s c and azimuth phi is built
+// about -sigma z and carried onto S by the Householder reflection of
+// v = S + sigma z, which maps -sigma z to S (sigma = sign(S_z) keeps
+// v.v = 2 (1 + sigma S_z) >= 2).  A reflection maps the uniform cap about
+// -sigma z to the uniform cap about S, so the law is that of the frame of
+// Duff et al. used by the FP64 mode, in fewer operations.
 __device__ __forceinline__ V3<float> cap_point_direct(V3<float> S, float c, float s, float cp, float sp) {
     const float sc = s * c;
     const float r = sqrtf(sc * (2.0f - sc));
-    const float zp = 1.0f - sc;
-    const float xp = r * cp, yp = r * sp;
     const float sgn = copysignf(1.0f, S.z);
-    const float a = -1.0f / (sgn + S.z);
-    const float b = S.x * S.y * a;
-    const float b1x = 1.0f + sgn * S.x * S.x * a, b1y = sgn * b, b1z = -sgn * S.x;
-    const float b2x = b, b2y = sgn + S.y * S.y * a, b2z = -S.y;
-    const float nx = xp * b1x + yp * b2x + zp * S.x;
-    const float ny = xp * b1y + yp * b2y + zp * S.y;
-    const float nz = xp * b1z + yp * b2z + zp * S.z;
+    const float px = r * cp, py = r * sp, pz = -sgn * (1.0f - sc);
+    const float vz = S.z + sgn;
+    const float d = S.x * px + S.y * py + vz * pz;
+    const float k = __fdividef(d, 1.0f + sgn * S.z);
+    const float nx = px - k * S.x, ny = py - k * S.y, nz = pz - k * vz;
     const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
     return V3<float>{nx * inv, ny * inv, nz * inv};
 }
@@ -330,12 +335,19 @@ __device__ __forceinline__ bool cone_trial(V3<R> S, R c, uint32_t idx, uint32_t 
     }
 }
 
-// Metropolis acceptance, Eq. 1: accept iff P < exp(-dE/T).
+// Metropolis acceptance, Eq. 1: accept iff P < exp(-dE/T).  FP32 evaluates
+// exp(-dE/T) as 2^(dE beta2) with beta2 = -log2(e)/T fixed per lattice: one
+// multiply and one hardware exp2.
 template <typename R>
-__device__ __forceinline__ bool metropolis(R dE, R T, R P) {
+__device__ __forceinline__ R boltzmann(R dE, const Par<R>& par) {
+    if constexpr (kIsF64<R>) return exp_fp64(-(dE / par.T));
+    else return exp2f(dE * par.beta2);
+}
+
+template <typename R>
+__device__ __forceinline__ bool metropolis(R dE, const Par<R>& par, R P) {
     if (dE <= R(0)) return true;
-    if constexpr (kIsF64<R>) return P < exp_fp64(-(dE / T));
-    else return P < __expf(-__fdividef(dE, T));
+    return P < boltzmann(dE, par);
 }
 
 // ------------------------------------------------------------------------
@@ -724,7 +736,7 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
                 }
                 if (drawn) {
                     const R dE = delta_e(par, S[v], Sn, h[v], e[v]);
-                    if (metropolis(dE, par.T, P[v])) {
+                    if (metropolis(dE, par, P[v])) {
                         store_spin(s, p.stride, colour, qv[v], Sn);
                         Sf = Sn;
                         ++nacc;
@@ -914,8 +926,7 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     const R dE = dEi + dEj;
     R r = rM;
     r = r * (fabs(hj.x) / fabs(xnj));
-    if constexpr (kIsF64<R>) r = r * exp_fp64(-(dE / par.T));
-    else r = r * __expf(-__fdividef(dE, par.T));
+    r = r * boltzmann(dE, par);
     if (!(P < r)) return 0;
     store_spin(s, p.stride, colour, qi, Sni);
     store_spin(s, p.stride, colour, qj, Snj);

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
-                    const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par.T, P[v]);
+                    const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par, P[v]);
                     Sf[v] = acc ? Sn : S[v];
                     nacc += acc ? 1u : 0u;
                     any = any || acc;

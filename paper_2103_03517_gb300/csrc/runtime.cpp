@@ -131,6 +131,7 @@ int colour_kernel(const LatParams& p, bool film, int path) {
 // ------------------------------------------------------------- lattices
 static void set_float_params(LatParams& p) {
     p.fJ = (float)p.J; p.fKu = (float)p.Ku; p.fKc = (float)p.Kc; p.fT = (float)p.T;
+    p.fBeta2 = (float)(-1.4426950408889634 / p.T);  // log2(e) = 1 / ln 2
     for (int a = 0; a < 3; ++a) { p.fe[a] = (float)p.e[a]; p.fH[a] = (float)p.H[a]; }
     for (int a = 0; a < 9; ++a) p.fR[a] = (float)p.R[a];
 }
