@@ -73,6 +73,16 @@ def lib() -> C.CDLL:
         L.or_stats.argtypes = [vp, P(dbl)]
         L.or_samples.argtypes = [vp, P(dbl), i64]; L.or_samples.restype = i64
         L.or_anisotropy_scaling.argtypes = [vp, P(dbl)]
+        L.or_xtal_create.argtypes = [i32, P(i32), dbl, dbl, dbl, P(dbl), dbl, P(dbl), dbl, u64, i32, i32]
+        L.or_xtal_create.restype = vp
+        L.or_xtal_destroy.argtypes = [vp]
+        L.or_xtal_set_spins.argtypes = [vp, P(dbl)]
+        L.or_xtal_get_spins.argtypes = [vp, P(dbl)]
+        L.or_xtal_theta.argtypes = [vp]; L.or_xtal_theta.restype = i32
+        L.or_xtal_last_accepted.argtypes = [vp]; L.or_xtal_last_accepted.restype = i64
+        L.or_xtal_delta_e.argtypes = [vp, i64, P(dbl)]; L.or_xtal_delta_e.restype = dbl
+        L.or_xtal_sweep.argtypes = [vp, i32, i32]
+        L.or_xtal_stats.argtypes = [vp, P(dbl)]
         L.or_profile.argtypes = [vp, P(dbl)]
         L.or_reset_stats.argtypes = [vp]
         L.or_sweep.argtypes = [vp, i32, i32]; L.or_sweep.restype = i32
@@ -248,3 +258,61 @@ class Lattice:
 
     def reset_stats(self) -> None:
         lib().or_reset_stats(self._h)
+
+
+BCC, FCC = 1, 2
+XTAL_STAT_FIELDS = ("n", "mx", "my", "mz", "ml", "e", "e_ex", "e_u", "e_c", "e_z")
+
+
+class Crystal:
+    """A bcc (kind 1) or fcc (kind 2) lattice of the serial oracle: cells
+    (Lx, Ly, Lz), all periodic; site i = s + nsub (x + Lx (y + Ly z)) for
+    sub-lattice s of cell (x, y, z).  J1 nearest, J2 next-nearest exchange."""
+
+    def __init__(self, kind, cells, J1=1.0, J2=0.0, Ku=0.0, axis=(0.0, 0.0, 1.0), Kc=0.0, H=(0.0, 0.0, 0.0),
+                 T=1.0, seed=0, theta0=30, adapt_in_measure=1):
+        self.kind = int(kind)
+        self.cells = tuple(int(c) for c in cells)
+        self.nsub = 2 if self.kind == BCC else 4
+        self.N = self.nsub * self.cells[0] * self.cells[1] * self.cells[2]
+        d = np.array(self.cells, np.int32)
+        ax = np.array(axis, np.float64)
+        h = np.array(H, np.float64)
+        self._h = lib().or_xtal_create(self.kind, _p(d, C.c_int), float(J1), float(J2), float(Ku),
+                                       _p(ax, C.c_double), float(Kc), _p(h, C.c_double), float(T),
+                                       int(seed) & (2**64 - 1), int(theta0), int(adapt_in_measure))
+        if not self._h:
+            raise ValueError("or_xtal_create failed")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_xtal_destroy(h)
+            self._h = None
+
+    def set_spins(self, S: np.ndarray) -> None:
+        a = np.ascontiguousarray(S, dtype=np.float64).reshape(self.N, 3)
+        lib().or_xtal_set_spins(self._h, _p(a, C.c_double))
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.N, 3))
+        lib().or_xtal_get_spins(self._h, _p(out, C.c_double))
+        return out
+
+    def theta(self) -> int:
+        return lib().or_xtal_theta(self._h)
+
+    def last_accepted(self) -> int:
+        return lib().or_xtal_last_accepted(self._h)
+
+    def delta_e(self, i: int, Sn) -> float:
+        s = np.ascontiguousarray(Sn, dtype=np.float64)
+        return lib().or_xtal_delta_e(self._h, int(i), _p(s, C.c_double))
+
+    def sweep(self, n: int, measure: bool = False) -> None:
+        lib().or_xtal_sweep(self._h, int(n), int(bool(measure)))
+
+    def stats(self) -> dict:
+        out = np.zeros(len(XTAL_STAT_FIELDS))
+        lib().or_xtal_stats(self._h, _p(out, C.c_double))
+        return dict(zip(XTAL_STAT_FIELDS, out.tolist()))

@@ -821,3 +821,213 @@ OR_EXPORT int or_constrained_sweep_serial(or_lattice* L, double theta_deg, doubl
     }
     return 0;
 }
+
+/* --------------------------------------------------------------------- */
+/* Crystal structures (Sec. 2): bcc as 2 interleaved simple cubic          */
+/* sub-lattices, fcc as 4.  Each sub-lattice is split red/black by the      */
+/* parity of its cell (x + y + z), and the sub-sets are visited in turn:    */
+/* sub-lattice 0 red, 0 black, 1 red, 1 black, ...  J1 couples nearest      */
+/* neighbours (other sub-lattices), J2 next-nearest neighbours (the same    */
+/* sub-lattice, one cell away along an axis), so every sub-set is free of   */
+/* internal bonds.  Cells: L[0] x L[1] x L[2], all periodic, even sizes.     */
+/* Site index i = s + nsub (x + L0 (y + L1 z)) for sub-lattice s, cell      */
+/* (x, y, z).  Lengths in units of the cubic cell.                          */
+/* --------------------------------------------------------------------- */
+enum { XTAL_MAX_SUB = 4, XTAL_MAX_NB = 24 };
+
+typedef struct {
+    int nsub;
+    int L[3];
+    int64_t N;
+    int nnb[XTAL_MAX_SUB];                  /* neighbour entries per sub-lattice */
+    int nb_sub[XTAL_MAX_SUB][XTAL_MAX_NB];  /* neighbour's sub-lattice            */
+    int nb_d[XTAL_MAX_SUB][XTAL_MAX_NB][3]; /* its cell offset                    */
+    double nb_J[XTAL_MAX_SUB][XTAL_MAX_NB]; /* its coupling (J1 or J2)            */
+    double Ku, axis[3], Kc, H[3], T;
+    uint32_t key0, key1;
+    int theta, adapt_in_measure;
+    uint32_t sweep;
+    double* S;
+    int64_t last_accepted;
+    int64_t n_samples;
+    double acc_m[3], acc_ml, acc_e, acc_parts[4];
+} or_xtal;
+
+/* Neighbour table from the basis positions: entry (s', d) of sub-lattice s
+ * is a neighbour when |b_s' + d - b_s|^2 equals the nearest-neighbour
+ * distance^2 (bcc 3/4, fcc 1/2; coupling J1) or 1 (next-nearest, J2), for
+ * cell offsets d in {-1, 0, 1}^3.  Entries are ordered by s' ascending,
+ * then d_z, d_y, d_x, each from -1 to 1: the field h is accumulated in this
+ * order. */
+OR_EXPORT or_xtal* or_xtal_create(int type, const int cells[3], double J1, double J2, double Ku, const double axis[3],
+                                  double Kc, const double H[3], double T, uint64_t seed, int theta0,
+                                  int adapt_in_measure) {
+    static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
+    static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    if (type != 1 && type != 2) return NULL;
+    or_xtal* X = (or_xtal*)calloc(1, sizeof(or_xtal));
+    if (!X) return NULL;
+    X->nsub = type == 1 ? 2 : 4;
+    const double(*b)[3] = type == 1 ? bcc : fcc;
+    const double d1 = type == 1 ? 0.75 : 0.5;
+    for (int a = 0; a < 3; ++a) X->L[a] = cells[a];
+    X->N = (int64_t)X->nsub * cells[0] * cells[1] * cells[2];
+    for (int s = 0; s < X->nsub; ++s) {
+        int n = 0;
+        for (int t = 0; t < X->nsub; ++t)
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const double r[3] = {b[t][0] + dx - b[s][0], b[t][1] + dy - b[s][1], b[t][2] + dz - b[s][2]};
+                        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                        double J;
+                        if (fabs(r2 - d1) < 1e-9) J = J1;
+                        else if (fabs(r2 - 1.0) < 1e-9) J = J2;
+                        else continue;
+                        X->nb_sub[s][n] = t;
+                        X->nb_d[s][n][0] = dx; X->nb_d[s][n][1] = dy; X->nb_d[s][n][2] = dz;
+                        X->nb_J[s][n] = J;
+                        ++n;
+                    }
+        X->nnb[s] = n;
+    }
+    X->Ku = Ku; X->Kc = Kc; X->T = T;
+    const double an = sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    for (int a = 0; a < 3; ++a) { X->axis[a] = axis[a] / an; X->H[a] = H[a]; }
+    X->key0 = (uint32_t)seed;
+    X->key1 = (uint32_t)(seed >> 32);
+    X->theta = theta0;
+    X->adapt_in_measure = adapt_in_measure;
+    X->S = (double*)calloc((size_t)X->N * 3, sizeof(double));
+    for (int64_t i = 0; i < X->N; ++i) X->S[3 * i + 2] = 1.0;
+    return X;
+}
+
+OR_EXPORT void or_xtal_destroy(or_xtal* X) {
+    if (!X) return;
+    free(X->S);
+    free(X);
+}
+
+OR_EXPORT void or_xtal_set_spins(or_xtal* X, const double* xyz) { memcpy(X->S, xyz, sizeof(double) * 3 * (size_t)X->N); }
+OR_EXPORT void or_xtal_get_spins(const or_xtal* X, double* xyz) { memcpy(xyz, X->S, sizeof(double) * 3 * (size_t)X->N); }
+OR_EXPORT int or_xtal_theta(const or_xtal* X) { return X->theta; }
+OR_EXPORT int64_t or_xtal_last_accepted(const or_xtal* X) { return X->last_accepted; }
+
+static int64_t xtal_site(const or_xtal* X, int s, int x, int y, int z) {
+    return (int64_t)s + (int64_t)X->nsub * ((int64_t)x + (int64_t)X->L[0] * ((int64_t)y + (int64_t)X->L[1] * z));
+}
+
+/* h_i = sum over the neighbour entries of J_e S_j, in table order. */
+static void xtal_field(const or_xtal* X, int64_t i, double h[3]) {
+    const int s = (int)(i % X->nsub);
+    const int64_t cell = i / X->nsub;
+    const int x = (int)(cell % X->L[0]), y = (int)((cell / X->L[0]) % X->L[1]),
+              z = (int)(cell / ((int64_t)X->L[0] * X->L[1]));
+    h[0] = h[1] = h[2] = 0.0;
+    for (int e = 0; e < X->nnb[s]; ++e) {
+        const int xx = (x + X->nb_d[s][e][0] + X->L[0]) % X->L[0];
+        const int yy = (y + X->nb_d[s][e][1] + X->L[1]) % X->L[1];
+        const int zz = (z + X->nb_d[s][e][2] + X->L[2]) % X->L[2];
+        const double* t = &X->S[3 * xtal_site(X, X->nb_sub[s][e], xx, yy, zz)];
+        const double J = X->nb_J[s][e];
+        for (int a = 0; a < 3; ++a) h[a] = h[a] + J * t[a];
+    }
+}
+
+/* Eq. 2 single-site energy change with the couplings inside h:
+ * dE = -(d.h) - K_u((Sn.e)^2 - (S.e)^2) + K_c(q(Sn) - q(S)) - H.d. */
+static double xtal_delta_e(const or_xtal* X, int64_t i, const double S[3], const double Sn[3]) {
+    double h[3];
+    xtal_field(X, i, h);
+    const double d0 = Sn[0] - S[0], d1 = Sn[1] - S[1], d2 = Sn[2] - S[2];
+    const double e_ex = -(d0 * h[0] + d1 * h[1] + d2 * h[2]);
+    const double* e = X->axis;
+    const double pn = Sn[0] * e[0] + Sn[1] * e[1] + Sn[2] * e[2];
+    const double po = S[0] * e[0] + S[1] * e[1] + S[2] * e[2];
+    const double e_u = -(X->Ku * (pn * pn - po * po));
+    const double e_c = X->Kc * (cubic_q(Sn) - cubic_q(S));
+    const double e_z = -(X->H[0] * d0 + X->H[1] * d1 + X->H[2] * d2);
+    return e_ex + e_u + e_c + e_z;
+}
+
+OR_EXPORT double or_xtal_delta_e(const or_xtal* X, int64_t i, const double Sn[3]) {
+    return xtal_delta_e(X, i, &X->S[3 * i], Sn);
+}
+
+/* One sub-set pass: every site of sub-lattice s whose cell parity is
+ * colour, in index order; the draws are keyed by the site index. */
+static int64_t xtal_pass(or_xtal* X, int s, int colour) {
+    const double c = cone_c(X->theta);
+    const uint32_t tag = tag_of(colour, PURPOSE_MOVE);
+    int64_t accepted = 0;
+    for (int z = 0; z < X->L[2]; ++z)
+        for (int y = 0; y < X->L[1]; ++y)
+            for (int x = 0; x < X->L[0]; ++x) {
+                if (((x + y + z) & 1) != colour) continue;
+                const int64_t i = xtal_site(X, s, x, y, z);
+                double* S = &X->S[3 * i];
+                double Sn[3], P;
+                if (!cone_trial(S, c, (uint32_t)i, X->sweep, tag, X->key0, X->key1, Sn, &P)) continue;
+                if (metropolis(xtal_delta_e(X, i, S, Sn), X->T, P)) {
+                    S[0] = Sn[0]; S[1] = Sn[1]; S[2] = Sn[2];
+                    ++accepted;
+                }
+            }
+    return accepted;
+}
+
+/* Sample (Sec. 3): m = mean spin; exchange energy -1/2 sum_i S_i.h_i (every
+ * bond seen from both ends); uniaxial, cubic and Zeeman energies; per spin. */
+static void xtal_measure(or_xtal* X) {
+    double M[3] = {0, 0, 0}, sh = 0, su = 0, sc = 0;
+    for (int64_t i = 0; i < X->N; ++i) {
+        const double* s = &X->S[3 * i];
+        double h[3];
+        xtal_field(X, i, h);
+        for (int a = 0; a < 3; ++a) M[a] += s[a];
+        sh += s[0] * h[0] + s[1] * h[1] + s[2] * h[2];
+        const double pe = s[0] * X->axis[0] + s[1] * X->axis[1] + s[2] * X->axis[2];
+        su += pe * pe;
+        sc += cubic_q(s);
+    }
+    const double N = (double)X->N;
+    double ml2 = 0;
+    for (int a = 0; a < 3; ++a) {
+        X->acc_m[a] += M[a] / N;
+        ml2 += (M[a] / N) * (M[a] / N);
+    }
+    const double e_ex = -0.5 * sh / N, e_u = -X->Ku * su / N, e_c = X->Kc * sc / N;
+    const double e_z = -(X->H[0] * M[0] + X->H[1] * M[1] + X->H[2] * M[2]) / N;
+    X->acc_ml += sqrt(ml2);
+    X->acc_e += e_ex + e_u + e_c + e_z;
+    X->acc_parts[0] += e_ex; X->acc_parts[1] += e_u; X->acc_parts[2] += e_c; X->acc_parts[3] += e_z;
+    X->n_samples += 1;
+}
+
+/* One iteration: every sub-set in turn, then the cone adaptation of Table
+ * A1 over all N spins and, if measuring, the sample. */
+OR_EXPORT void or_xtal_sweep(or_xtal* X, int n_sweeps, int measure_flag) {
+    for (int k = 0; k < n_sweeps; ++k) {
+        int64_t acc = 0;
+        for (int s = 0; s < X->nsub; ++s)
+            for (int colour = 0; colour < 2; ++colour) acc += xtal_pass(X, s, colour);
+        X->last_accepted = acc;
+        if (!measure_flag || X->adapt_in_measure) {
+            if (2 * acc > X->N) { if (X->theta < 180) X->theta += 1; }
+            else { if (X->theta > 1) X->theta -= 1; }
+        }
+        if (measure_flag) xtal_measure(X);
+        X->sweep += 1;
+    }
+}
+
+/* n, <m_x>, <m_y>, <m_z>, <|m|>, <E/N>, <E_ex/N>, <E_u/N>, <E_c/N>, <E_Z/N> */
+OR_EXPORT void or_xtal_stats(const or_xtal* X, double* out) {
+    const double n = X->n_samples ? (double)X->n_samples : 1.0;
+    out[0] = (double)X->n_samples;
+    for (int a = 0; a < 3; ++a) out[1 + a] = X->acc_m[a] / n;
+    out[4] = X->acc_ml / n;
+    out[5] = X->acc_e / n;
+    for (int a = 0; a < 4; ++a) out[6 + a] = X->acc_parts[a] / n;
+}
