@@ -69,6 +69,18 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * compare them.  FP64 lattices always take the general kernel. */
 typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_path;
 
+/* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the
+ * cells.  BCC / FCC: 2 / 4 simple cubic sub-lattices with basis (0,0,0),
+ * (1/2,1/2,1/2) / (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2); dims
+ * count cubic cells (even, all boundaries PERIODIC); J couples nearest
+ * neighbours (8 / 12, other sub-lattices) and J2 next-nearest ones (6, the
+ * same sub-lattice one cell away).  Each sub-lattice is split red/black by
+ * cell parity and the 2 nsub sub-sets are updated in turn: sub-lattice 0
+ * red, 0 black, 1 red, ...  Site order of spin arrays: i = s + nsub (x + Lx
+ * (y + Ly z)).  BCC / FCC lattices take standard sweeps only: no
+ * constrained sweeps, films, groups, serving or profiles (MC_ERR_ARG). */
+typedef enum mc_lattice_type { MC_SC = 0, MC_BCC = 1, MC_FCC = 2 } mc_lattice_type;
+
 typedef enum mc_init {
     MC_INIT_UNIFORM = 0, /* every spin along init_dir (default +z)             */
     MC_INIT_WALL = 1     /* +z for x < Lx/2, -z otherwise (Bloch wall start)    */
@@ -109,6 +121,8 @@ typedef struct mc_desc {
     void* stream;           /* cudaStream_t to run on, or NULL for a library stream */
     int device;             /* CUDA device ordinal                                */
     int kernel_path;        /* mc_kernel_path (default MC_PATH_AUTO)              */
+    int lattice;            /* mc_lattice_type (default MC_SC)                    */
+    double J2;              /* bcc / fcc: next-nearest exchange (same sub-lattice) */
 } mc_desc;
 
 /* Ensemble averages over the measurement sweeps since the last reset

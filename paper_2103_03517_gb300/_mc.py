@@ -19,6 +19,7 @@ MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR
 MC_FP32, MC_FP64 = 0, 1
 MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
 MC_PATH_AUTO, MC_PATH_GENERAL = 0, 1
+MC_SC, MC_BCC, MC_FCC = 0, 1, 2
 MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
 MC_JOB_SWEEP, MC_JOB_CONSTRAINED = 0, 1
 
@@ -37,7 +38,8 @@ class mc_desc(C.Structure):
                 ("init_dir", C.c_double * 3), ("ring_capacity", C.c_int), ("sample_torque", C.c_int),
                 ("bond_mask", C.POINTER(C.c_uint8)), ("grain_id", C.POINTER(C.c_int32)),
                 ("grain_axis", C.POINTER(C.c_double)), ("n_grains", C.c_int),
-                ("stream", C.c_void_p), ("device", C.c_int), ("kernel_path", C.c_int)]
+                ("stream", C.c_void_p), ("device", C.c_int), ("kernel_path", C.c_int), ("lattice", C.c_int),
+                ("J2", C.c_double)]
 
 
 class mc_observables(C.Structure):
@@ -165,7 +167,7 @@ def make_desc(dims, J=1.0, K_u=0.0, axis=(0.0, 0.0, 1.0), K_c=0.0, H=(0.0, 0.0, 
               precision=MC_FP32, boundary=(0, 0, 0), theta0_deg=30, adapt_in_measure=1, init=MC_INIT_UNIFORM,
               init_dir=(0.0, 0.0, 1.0), ring_capacity=4096, sample_torque=1, bond_mask=None, grain_id=None,
               grain_axis=None,
-              stream=None, device=0, kernel_path=0) -> mc_desc:
+              stream=None, device=0, kernel_path=0, lattice=0, J2=0.0) -> mc_desc:
     """Fill an mc_desc.  Film tables (numpy arrays) are referenced, not
     copied, until mc_create_ex / mc_submit copies them; keep them alive."""
     d = mc_desc_default()
@@ -183,6 +185,8 @@ def make_desc(dims, J=1.0, K_u=0.0, axis=(0.0, 0.0, 1.0), K_c=0.0, H=(0.0, 0.0, 
     d.init = int(init)
     d.ring_capacity = int(ring_capacity)
     d.kernel_path = int(kernel_path)
+    d.lattice = int(lattice)
+    d.J2 = float(J2)
     d.sample_torque = int(bool(sample_torque))
     d._keep = []
     if bond_mask is not None:

@@ -77,6 +77,10 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
             delete g;
             return fail(MC_ERR_ARG, "group members must share device and precision");
         }
+        if (lattices[i]->hp.nsub > 1) {
+            delete g;
+            return fail(MC_ERR_ARG, "group members must be simple cubic lattices");
+        }
     }
     // launch tables: the lattices in launch order (general-path and small
     // lattices first, so their few tiles start early and overlap the rest),

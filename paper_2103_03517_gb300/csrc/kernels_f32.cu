@@ -15,6 +15,7 @@
 #endif
 #include "kernels.h"
 #include "pass_impl.cuh"
+#include "xtal_pass.cuh"
 #include "row_pass.cuh"
 
 namespace mcgb {
@@ -109,6 +110,17 @@ void measure(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     measure_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
 }
 
+void xtal_pass(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(xtal_pass_kernel<R>);
+    xtal_pass_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, static_cast<const R*>(cone), sub, colour,
+                                                                 finalize);
+}
+
+void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(xtal_sample_kernel<R>);
+    xtal_sample_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, tiles_per_subset);
+}
+
 void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
     const uint32_t threads = Lh * ((rows + 31) / 32);
     profile_kernel<R><<<(threads + kBlock - 1) / kBlock, kBlock, 0, s>>>(d);
@@ -117,7 +129,8 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, mlong, measure, row_sample, profile, "f32"};
+    static const KernelSet k{colour_pass, row_pass, pair_pass, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
+                             "f32"};
     return k;
 }
 

@@ -66,11 +66,20 @@ inline FastDiv make_fastdiv(uint32_t d) {
 
 enum { kColourGeneral = 0, kColourRow = 1, kColourRowGen = 2 };
 
+// One neighbour entry of a bcc / fcc sub-lattice: the neighbour's
+// sub-lattice, its cell offset and its coupling (J1 or J2).
+constexpr int kXtalMaxSub = 4, kXtalMaxNb = 24;
+struct XtalNb {
+    int8_t sub, dx, dy, dz;
+    float fJ;
+    double J;
+};
+
 struct LatParams {
     int Lx, Ly, Lz, Lh;
     int bc[3];
     int precision;
-    uint32_t Nc;            // sites per colour = N / 2
+    uint32_t Nc;            // sites per colour (and sub-lattice) = cells / 2
     uint32_t stride;        // Nc rounded up to 64
     uint32_t n_pairs;       // Nc / 2
     int perm_h;             // Feistel half width in bits (domain 2^(2h) >= Nc)
@@ -85,6 +94,9 @@ struct LatParams {
                             // Lh % 32 == 0, or (FP32) Lh a power of two <= 64 or a
                             // multiple of 64, Nc % 64 == 0: the row paths apply
     int row_lanes;          // FP32 row path: lanes per row group, min(Lh/2, 32)
+    int nsub;               // sub-lattices: 1 simple cubic, 2 bcc, 4 fcc
+    int xnb_n[kXtalMaxSub]; // bcc / fcc: neighbour entries per sub-lattice
+    const void* xnb;        // bcc / fcc: [kXtalMaxSub][kXtalMaxNb] XtalNb, or null
     int colour_kernel;      // colour-pass kernel: kColourGeneral, kColourRow (FP32 row
                             // layout, all axes periodic, no film tables) or
                             // kColourRowGen (FP32 row layout, any boundaries and films)

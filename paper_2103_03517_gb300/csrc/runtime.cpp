@@ -136,13 +136,50 @@ static void set_float_params(LatParams& p) {
     for (int a = 0; a < 9; ++a) p.fR[a] = (float)p.R[a];
 }
 
+int sublattices(int lattice) { return lattice == MC_BCC ? 2 : (lattice == MC_FCC ? 4 : 1); }
+
+// Neighbour table of a bcc or fcc lattice from its basis (positions in
+// units of the cubic cell): entry (t, d) of sub-lattice s, d a cell offset
+// in {-1, 0, 1}^3, is a neighbour when |b_t + d - b_s|^2 equals the
+// nearest-neighbour distance^2 (bcc 3/4, fcc 1/2; coupling J) or 1 (the
+// same sub-lattice one cell away; coupling J2).  Entries are ordered by t,
+// then d_z, d_y, d_x from -1 to 1: the order in which the field is summed.
+static void xtal_table(int lattice, double J, double J2, XtalNb out[kXtalMaxSub][kXtalMaxNb], int n[kXtalMaxSub]) {
+    const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
+    const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    const int ns = sublattices(lattice);
+    const double(*b)[3] = lattice == MC_BCC ? bcc : fcc;
+    const double nn2 = lattice == MC_BCC ? 0.75 : 0.5;
+    for (int s = 0; s < ns; ++s) {
+        n[s] = 0;
+        for (int t = 0; t < ns; ++t)
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const double r[3] = {b[t][0] + dx - b[s][0], b[t][1] + dy - b[s][1], b[t][2] + dz - b[s][2]};
+                        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                        const bool nn = std::fabs(r2 - nn2) < 1e-9, nnn = std::fabs(r2 - 1.0) < 1e-9;
+                        if (!nn && !nnn) continue;
+                        XtalNb& e = out[s][n[s]++];
+                        e.sub = int8_t(t);
+                        e.dx = int8_t(dx);
+                        e.dy = int8_t(dy);
+                        e.dz = int8_t(dz);
+                        e.J = nn ? J : J2;
+                        e.fJ = float(e.J);
+                    }
+    }
+}
+
 size_t lattice_bytes(const mc_desc* d) {
-    const uint64_t N = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
-    const uint64_t Nc = N / 2;
+    const uint64_t cells = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
+    const uint64_t Nc = cells / 2;
     const uint64_t stride = (Nc + 63) / 64 * 64;
     const size_t rs = d->precision == MC_FP64 ? 8 : 4;
+    const int nsub = sublattices(d->lattice);
     size_t b = align256(sizeof(LatDev));
-    b += align256(6 * stride * rs);
+    b += align256(size_t(nsub) * 6 * stride * rs);
+    if (nsub > 1) b += align256(sizeof(XtalNb) * kXtalMaxSub * kXtalMaxNb);
     if (d->bond_mask) b += align256(2 * stride);
     if (d->grain_id) b += align256(2 * stride * 4) + align256(4 * size_t(std::max(d->n_grains, 1)) * rs);
     const int cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
@@ -167,6 +204,13 @@ int validate_desc(const mc_desc* d) {
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
     if (!(an > 0.0)) return fail(MC_ERR_ARG, "|axis| = 0");
     if (d->precision != MC_FP32 && d->precision != MC_FP64) return fail(MC_ERR_ARG, "precision invalid");
+    if (d->lattice != MC_SC && d->lattice != MC_BCC && d->lattice != MC_FCC) return fail(MC_ERR_ARG, "lattice invalid");
+    if (d->lattice != MC_SC) {
+        for (int a = 0; a < 3; ++a)
+            if (d->boundary[a] != MC_PERIODIC) return fail(MC_ERR_ARG, "bcc / fcc lattices need periodic cells");
+        if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc lattices take no film tables");
+        if (!std::isfinite(d->J2)) return fail(MC_ERR_ARG, "J2 not finite");
+    }
     if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL)
         return fail(MC_ERR_ARG, "kernel_path invalid");
     if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
@@ -204,28 +248,34 @@ int validate_desc(const mc_desc* d) {
     return MC_OK;
 }
 
-template <typename R>
-static void to_device_layout(const LatParams& p, const double* xyz, R* out) {
+// Site i = s + nsub (x + Lx (y + Ly z)) <-> component a of sub-lattice s,
+// colour c = (x + y + z) & 1, index q = (x >> 1) + Lh (y + Ly z) at
+// ((2 s + c) 3 + a) stride + q (nsub = 1: the simple cubic layout).
+template <typename R, typename F>
+static void for_each_site(const LatParams& p, F&& f) {
     for (int z = 0; z < p.Lz; ++z)
         for (int y = 0; y < p.Ly; ++y)
-            for (int x = 0; x < p.Lx; ++x) {
-                const size_t i = x + size_t(p.Lx) * (y + size_t(p.Ly) * z);
-                const int c = (x + y + z) & 1;
-                const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
-                for (int a = 0; a < 3; ++a) out[(3 * c + a) * size_t(p.stride) + q] = (R)xyz[3 * i + a];
-            }
+            for (int x = 0; x < p.Lx; ++x)
+                for (int s = 0; s < p.nsub; ++s) {
+                    const size_t i = size_t(s) + size_t(p.nsub) * (x + size_t(p.Lx) * (y + size_t(p.Ly) * z));
+                    const int c = (x + y + z) & 1;
+                    const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
+                    f(i, (size_t(s) * 2 + c) * 3 * size_t(p.stride) + q);
+                }
+}
+
+template <typename R>
+static void to_device_layout(const LatParams& p, const double* xyz, R* out) {
+    for_each_site<R>(p, [&](size_t i, size_t o) {
+        for (int a = 0; a < 3; ++a) out[o + a * size_t(p.stride)] = (R)xyz[3 * i + a];
+    });
 }
 
 template <typename R>
 static void from_device_layout(const LatParams& p, const R* in, double* xyz) {
-    for (int z = 0; z < p.Lz; ++z)
-        for (int y = 0; y < p.Ly; ++y)
-            for (int x = 0; x < p.Lx; ++x) {
-                const size_t i = x + size_t(p.Lx) * (y + size_t(p.Ly) * z);
-                const int c = (x + y + z) & 1;
-                const size_t q = size_t(x >> 1) + size_t(p.Lh) * (y + size_t(p.Ly) * z);
-                for (int a = 0; a < 3; ++a) xyz[3 * i + a] = (double)in[(3 * c + a) * size_t(p.stride) + q];
-            }
+    for_each_site<R>(p, [&](size_t i, size_t o) {
+        for (int a = 0; a < 3; ++a) xyz[3 * i + a] = (double)in[o + a * size_t(p.stride)];
+    });
 }
 
 static void per_site_colour_split(const LatParams& p, const void* src, size_t elem, void* dst) {
@@ -297,8 +347,9 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.Lx = d->dims[0]; p.Ly = d->dims[1]; p.Lz = d->dims[2]; p.Lh = p.Lx / 2;
     for (int a = 0; a < 3; ++a) p.bc[a] = d->boundary[a];
     p.precision = d->precision;
-    p.N = (long long)p.Lx * p.Ly * p.Lz;
-    p.Nc = uint32_t(p.N / 2);
+    p.nsub = sublattices(d->lattice);
+    p.N = (long long)p.nsub * p.Lx * p.Ly * p.Lz;
+    p.Nc = uint32_t((long long)p.Lx * p.Ly * p.Lz / 2);
     p.stride = (p.Nc + 63) / 64 * 64;
     p.n_pairs = p.Nc / 2;
     p.perm_h = feistel_half_bits(p.Nc);
@@ -322,11 +373,12 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.key1 = uint32_t(d->seed >> 32);
     p.div_lh = make_fastdiv(uint32_t(p.Lh));
     p.div_ly = make_fastdiv(uint32_t(p.Ly));
-    const uint32_t site_tile = uint32_t(32 * sites_per_thread(p.precision));  // warp tiles
+    const uint32_t site_tile = p.nsub > 1 ? 32u : uint32_t(32 * sites_per_thread(p.precision));  // warp tiles
     p.nblocks_site = (p.Nc + site_tile - 1) / site_tile;
     p.nblocks_pair = (p.n_pairs + 31) / 32;
     if (p.nblocks_pair == 0) p.nblocks_pair = 1;
-    p.J = d->J; p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
+    p.J = p.nsub > 1 ? 1.0 : d->J;  // bcc / fcc: the couplings sit in the neighbour table
+    p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
     for (int a = 0; a < 3; ++a) { p.e[a] = d->axis[a] / an; p.H[a] = d->H[a]; }
     constraint_frame(0.0, 0.0, p.R);
@@ -346,7 +398,12 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     char* cur = static_cast<char*>(h->d_base);
     auto take = [&](size_t b) { char* r = cur; cur += align256(b); return r; };
     h->d_lat = reinterpret_cast<LatDev*>(take(sizeof(LatDev)));
-    p.spins = take(6 * size_t(p.stride) * rs);
+    p.spins = take(size_t(p.nsub) * 6 * size_t(p.stride) * rs);
+    XtalNb xt[kXtalMaxSub][kXtalMaxNb] = {};
+    if (p.nsub > 1) {
+        xtal_table(d->lattice, d->J, d->J2, xt, p.xnb_n);
+        p.xnb = take(sizeof xt);
+    }
     std::vector<uint8_t> hb;
     if (din->bond_mask) {
         hb.assign(2 * size_t(p.stride), 0);
@@ -390,7 +447,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     std::vector<double> xyz(size_t(p.N) * 3);
     for (long long i = 0; i < p.N; ++i) {
         if (d->init == MC_INIT_WALL) {
-            const int x = int(i % p.Lx);
+            const int x = int((i / p.nsub) % p.Lx);
             xyz[3 * i] = 0; xyz[3 * i + 1] = 0; xyz[3 * i + 2] = x < p.Lx / 2 ? 1.0 : -1.0;
         } else {
             const double n = std::sqrt(d->init_dir[0] * d->init_dir[0] + d->init_dir[1] * d->init_dir[1] +
@@ -398,7 +455,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
             for (int a = 0; a < 3; ++a) xyz[3 * i + a] = d->init_dir[a] / n;
         }
     }
-    std::vector<char> hs(6 * size_t(p.stride) * rs, 0);
+    std::vector<char> hs(size_t(p.nsub) * 6 * size_t(p.stride) * rs, 0);
     if (rs == 8) to_device_layout(p, xyz.data(), reinterpret_cast<double*>(hs.data()));
     else to_device_layout(p, xyz.data(), reinterpret_cast<float*>(hs.data()));
 
@@ -418,6 +475,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     up(h->d_lat, &init, sizeof init);
     up(p.spins, hs.data(), hs.size());
     if (!hb.empty()) up(const_cast<uint8_t*>(p.bonds), hb.data(), hb.size());
+    if (p.nsub > 1) up(const_cast<void*>(p.xnb), xt, sizeof xt);
     if (!hg.empty()) {
         up(const_cast<int32_t*>(p.grain), hg.data(), hg.size() * 4);
         up(const_cast<void*>(p.gaxis), hax.data(), hax.size());
@@ -460,7 +518,10 @@ LaunchSet single_launch_set(mc_lattice* h) {
     ls.nt_all = h->hp.nblocks_site;
     ls.nt_pairs = h->hp.nblocks_pair;
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
-    if (h->hp.colour_kernel == kColourRow) {
+    if (h->hp.nsub > 1) {
+        ls.xtal = h->d_lat;
+        ls.nsub = h->hp.nsub;
+    } else if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
     } else if (h->hp.colour_kernel == kColourRowGen) {
@@ -495,6 +556,19 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, s);
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
+    if (ls.xtal) {  // bcc / fcc: the 2 nsub sub-sets in turn, then the sample
+        for (int i = 0; i < n; ++i) {
+            for (int sub = 0; sub < ls.nsub; ++sub)
+                for (int colour = 0; colour < 2; ++colour) {
+                    const bool last = sub == ls.nsub - 1 && colour == 1;
+                    timed([&] { k.xtal_pass(ls.xtal, ls.nt_all, cone, sub, colour, last && !measure ? 1 : 0, s); });
+                }
+            if (measure) k.xtal_sample(ls.xtal, uint32_t(2 * ls.nsub) * ls.nt_all, ls.nt_all, s);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return MC_OK;
+    }
     for (int i = 0; i < n; ++i) {
         if (!constrained) {
             timed([&] { colour_pass(0, 0); });
@@ -601,6 +675,7 @@ MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_de
     if (!std::isfinite(phi_c_deg)) return fail(MC_ERR_ARG, "phi_c not finite");
     for (int a = 0; a < 3; ++a)
         if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
+    if (h->hp.nsub > 1) return fail(MC_ERR_ARG, "constrained sweeps need a simple cubic lattice");
     cudaSetDevice(h->device);
     int rc = ensure_aos(h);
     if (rc) return rc;
@@ -671,6 +746,7 @@ MC_API int mc_measure(mc_handle h, mc_observables* out) {
 }
 
 MC_API int mc_profile_sample(mc_handle h) {
+    if (h && h->hp.nsub > 1) return fail(MC_ERR_ARG, "profiles need a simple cubic lattice");
     if (!h) return fail(MC_ERR_ARG, "null handle");
     cudaSetDevice(h->device);
     kernel_set(h->hp.precision).profile(h->d_lat, uint32_t(h->hp.Lh), uint32_t(h->hp.Ly) * h->hp.Lz, h->stream);
@@ -680,6 +756,7 @@ MC_API int mc_profile_sample(mc_handle h) {
 }
 
 MC_API int mc_profile(mc_handle h, int component, double* out, int len) {
+    if (h && h->hp.nsub > 1) return fail(MC_ERR_ARG, "profiles need a simple cubic lattice");
     if (!h || !out || component < 0 || component > 2 || len < h->hp.Lx) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(h->device);
     std::vector<long long> sums(size_t(h->hp.Lx));
@@ -733,7 +810,7 @@ MC_API int mc_reset_stats(mc_handle h) {
 
 MC_API size_t mc_state_bytes(mc_handle h) {
     if (!h) return 0;
-    return 6 * size_t(h->hp.stride) * (h->hp.precision == MC_FP64 ? 8 : 4);
+    return size_t(h->hp.nsub) * 6 * size_t(h->hp.stride) * (h->hp.precision == MC_FP64 ? 8 : 4);
 }
 
 MC_API int mc_export_state(mc_handle h, void* host_buf, size_t bytes) {

@@ -35,6 +35,7 @@ int cuda_fail(cudaError_t e, const char* what);
 int create_lattice(const mc_desc* d, mc_handle* out);
 int validate_desc(const mc_desc* d);
 int row_fast(const LatParams& p, bool film);
+int sublattices(int lattice);
 int colour_kernel(const LatParams& p, bool film, int path);
 size_t lattice_bytes(const mc_desc* d);
 int upload_params(mc_lattice* h);

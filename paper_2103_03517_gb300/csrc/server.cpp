@@ -212,6 +212,7 @@ MC_API int mc_submit(mc_server* s, const mc_job* job, uint64_t* job_id) {
         for (int a = 0; a < 3; ++a)
             if (job->lattice.boundary[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained jobs need no pinned boundary");
     }
+    if (job->lattice.lattice != MC_SC) return fail(MC_ERR_ARG, "served jobs need a simple cubic lattice");
     auto j = std::make_unique<Job>();
     j->job = *job;
     const mc_desc& d = job->lattice;

@@ -1,0 +1,89 @@
+"""bcc / fcc lattices (Sec. 2: 2 / 4 simple cubic sub-lattices, each split
+red/black, the sub-sets updated in turn) on the GPU: FP64 bit-exact with
+the oracle's chain, FP32 statistically equal to FP64, and the calls that
+stay simple-cubic-only refuse these lattices."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_03517_gb300 as mc
+import workloads
+from _stats import blocking_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2103_03517_gb300 import build as libbuild
+    libbuild.build()
+
+
+KIND = {mc.MC_BCC: oracle.BCC, mc.MC_FCC: oracle.FCC}
+
+
+@pytest.mark.parametrize("lattice,cells,J2", [(mc.MC_BCC, (4, 2, 6), 0.0), (mc.MC_BCC, (6, 4, 2), 0.3),
+                                              (mc.MC_FCC, (2, 4, 2), 0.0), (mc.MC_FCC, (4, 4, 6), -0.2),
+                                              (mc.MC_FCC, (8, 2, 2), 0.1)])
+def test_crystal_fp64_bit_exact(lattice, cells, J2):
+    nsub = 2 if lattice == mc.MC_BCC else 4
+    N = nsub * cells[0] * cells[1] * cells[2]
+    spins = workloads.random_spins(N, N + 3)
+    kw = dict(Ku=0.2, Kc=0.1, H=(0.05, -0.1, 0.1), T=1.3, seed=N)
+    o = oracle.Crystal(KIND[lattice], cells, J1=1.1, J2=J2, axis=(0.2, 0.1, 1.0), **kw)
+    o.set_spins(spins)
+    h = mc.mc_create_ex(mc.make_desc(cells, J=1.1, J2=J2, K_u=kw["Ku"], K_c=kw["Kc"], H=kw["H"], T=kw["T"],
+                                     seed=kw["seed"], axis=(0.2, 0.1, 1.0), precision=mc.MC_FP64, lattice=lattice,
+                                     ring_capacity=32))
+    try:
+        mc.mc_set_spins(h, spins)
+        for n, meas in ((7, False), (13, True)):
+            mc.mc_sweep(h, n, measure=meas)
+            o.sweep(n, measure=meas)
+            got = mc.mc_get_spins(h, N)
+            assert np.array_equal(got, o.spins()), (lattice, cells, int((got != o.spins()).any(axis=1).sum()))
+            assert mc.mc_get_theta(h)[0] == o.theta()
+        ob, st = mc.mc_measure(h), o.stats()
+        assert ob.n_samples == st["n"] == 13
+        np.testing.assert_allclose(list(ob.m), [st["mx"], st["my"], st["mz"]], rtol=0, atol=1e-9)
+        np.testing.assert_allclose([ob.ml, ob.e], [st["ml"], st["e"]], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(list(ob.e_parts), [st["e_ex"], st["e_u"], st["e_c"], st["e_z"]], rtol=0, atol=1e-9)
+    finally:
+        mc.mc_destroy(h)
+
+
+@pytest.mark.parametrize("lattice", [mc.MC_BCC, mc.MC_FCC])
+def test_crystal_fp32_matches_fp64(lattice):
+    """Below T_C (bcc 2.05, fcc 3.18 for J = 1): FP32 and FP64 ensembles agree
+    on <|m|> and <E> within 4 sigma of the blocking errors."""
+    cells, T, n = (8, 8, 8), (1.4 if lattice == mc.MC_BCC else 2.2), 3000
+    hs = [mc.mc_create_ex(mc.make_desc(cells, K_u=0.02, T=T, seed=s, precision=p, lattice=lattice, ring_capacity=n))
+          for s, p in ((1, mc.MC_FP32), (2, mc.MC_FP64))]
+    try:
+        series = []
+        for h in hs:
+            mc.mc_sweep(h, 500)
+            mc.mc_sweep(h, n, measure=True)
+            smp = mc.mc_samples(h, n)
+            series.append((np.linalg.norm(smp["m"], axis=1), smp["e_parts"].sum(axis=1)))
+        for k in range(2):
+            a, b = series[0][k], series[1][k]
+            err = np.hypot(blocking_error(a), blocking_error(b))
+            assert abs(a.mean() - b.mean()) < max(4 * err, 1e-4), (lattice, k, a.mean(), b.mean(), err)
+        assert series[0][0].mean() > 0.3  # ordered
+    finally:
+        for h in hs:
+            mc.mc_destroy(h)
+
+
+def test_crystal_refused_where_simple_cubic_only():
+    h = mc.mc_create_ex(mc.make_desc((4, 4, 4), lattice=mc.MC_FCC))
+    try:
+        with pytest.raises(mc.MCError):
+            mc.mc_constrained_sweep(h, 30.0, 0.0, 1)
+        with pytest.raises(mc.MCError):
+            mc.mc_group_create([h])
+    finally:
+        mc.mc_destroy(h)
+    with pytest.raises(mc.MCError):
+        mc.mc_create_ex(mc.make_desc((4, 4, 4), lattice=mc.MC_BCC, boundary=(1, 0, 0)))
