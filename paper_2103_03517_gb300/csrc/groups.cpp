@@ -10,9 +10,6 @@
 
 using namespace mcgb;
 
-namespace {
-constexpr int kGraphSweeps = 16;  // sweeps per captured graph
-}
 
 struct mc_group {
     std::vector<mc_handle> lats;
@@ -23,43 +20,12 @@ struct mc_group {
     void* d_mem = nullptr;
     LaunchSet ls;
     const void* cone = nullptr;
-    // captured graphs: [constrained][measure]
-    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    SweepGraphs graphs;  // captured sweeps of the whole group
 };
-
-static int group_graph(mc_group* g, bool constrained, int measure, cudaGraphExec_t* out) {
-    cudaGraphExec_t& ex = g->exec[constrained][measure];
-    if (!ex) {
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, kGraphSweeps, measure, constrained,
-                                g->stream, nullptr);
-        e = cudaStreamEndCapture(g->stream, &graph);
-        if (rc) return rc;
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&ex, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) { ex = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
-    }
-    *out = ex;
-    return MC_OK;
-}
 
 static int group_run(mc_group* g, int n, int measure, bool constrained) {
     cudaSetDevice(g->device);
-    const int reps = n / kGraphSweeps;
-    if (reps > 0) {
-        cudaGraphExec_t ex;
-        int rc = group_graph(g, constrained, measure, &ex);
-        if (rc) return rc;
-        for (int r = 0; r < reps; ++r) {
-            cudaError_t e = cudaGraphLaunch(ex, g->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-        }
-    }
-    return enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n - reps * kGraphSweeps, measure, constrained,
-                          g->stream, nullptr);
+    return run_sweeps(g->graphs, g->precision, g->ls, g->cone, n, measure, constrained, g->stream);
 }
 
 extern "C" {
@@ -165,9 +131,7 @@ MC_API int mc_group_destroy(mc_group_handle g) {
     if (!g) return MC_OK;
     cudaSetDevice(g->device);
     cudaStreamSynchronize(g->stream);
-    for (auto& row : g->exec)
-        for (auto& ex : row)
-            if (ex) cudaGraphExecDestroy(ex);
+    destroy_graphs(g->graphs);
     cudaFree(g->d_mem);
     for (size_t i = 0; i < g->lats.size(); ++i) g->lats[i]->stream = g->member_streams[i];
     delete g;

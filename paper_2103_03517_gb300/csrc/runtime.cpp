@@ -593,6 +593,44 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
     return MC_OK;
 }
 
+int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* cone, int n, int measure,
+               bool constrained, cudaStream_t s) {
+    const KernelSet& k = kernel_set(precision);
+    const int reps = n / kGraphSweeps;
+    if (reps > 0) {
+        cudaGraphExec_t& ex = gr.exec[constrained ? 1 : 0][measure ? 1 : 0];
+        if (!ex) {
+            cudaGraph_t graph;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+            const int rc = enqueue_sweeps(k, ls, cone, kGraphSweeps, measure, constrained, s, nullptr);
+            e = cudaStreamEndCapture(s, &graph);
+            if (rc) return rc;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        for (int r = 0; r < reps; ++r) {
+            const cudaError_t e = cudaGraphLaunch(ex, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        }
+    }
+    return enqueue_sweeps(k, ls, cone, n - reps * kGraphSweeps, measure, constrained, s, nullptr);
+}
+
+void destroy_graphs(SweepGraphs& gr) {
+    for (auto& row : gr.exec)
+        for (auto& ex : row)
+            if (ex) {
+                cudaGraphExecDestroy(ex);
+                ex = nullptr;
+            }
+}
+
 int read_state(mc_lattice* h, LatState* st) {
     CK(cudaMemcpyAsync(st, &h->d_lat->st, sizeof(LatState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -641,6 +679,7 @@ MC_API int mc_destroy(mc_handle h) {
     if (!h) return MC_OK;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    destroy_graphs(h->graphs);
     cudaFree(h->d_base);
     if (h->d_aos) cudaFree(h->d_aos);
     if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -665,8 +704,8 @@ MC_API int mc_set_field(mc_handle h, const double H[3]) {
 MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
     if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(h->device);
-    const KernelSet& k = kernel_set(h->hp.precision);
-    return enqueue_sweeps(k, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, false, h->stream, nullptr);
+    return run_sweeps(h->graphs, h->hp.precision, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, false,
+                      h->stream);
 }
 
 MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_deg, int n_sweeps, int measure) {
@@ -682,8 +721,8 @@ MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_de
     constraint_frame(theta_c_deg, phi_c_deg, h->hp.R);
     rc = upload_params(h);
     if (rc) return rc;
-    const KernelSet& k = kernel_set(h->hp.precision);
-    return enqueue_sweeps(k, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, true, h->stream, nullptr);
+    return run_sweeps(h->graphs, h->hp.precision, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, true,
+                      h->stream);
 }
 
 MC_API int mc_sync(mc_handle h) {

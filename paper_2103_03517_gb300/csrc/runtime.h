@@ -9,6 +9,15 @@
 #include "mc.h"
 #include "mc_internal.h"
 
+namespace mcgb {
+// Captured CUDA graphs of kGraphSweeps sweeps of one launch set, by
+// [constrained][measure]; built on first use and replayed.
+constexpr int kGraphSweeps = 16;
+struct SweepGraphs {
+    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+};
+}  // namespace mcgb
+
 struct mc_lattice {
     mc_desc desc;                 // copy (film pointers cleared)
     int device = 0;
@@ -22,6 +31,7 @@ struct mc_lattice {
     uint32_t* d_group_start = nullptr;
     uint32_t* d_group_start_pair = nullptr;
     void* d_aos = nullptr;        // packed spin copy of constrained sweeps (LatParams::aos)
+    mcgb::SweepGraphs graphs;     // sweeps of the lattice alone
     const void* cone = nullptr;   // c(theta) table of the precision
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;
@@ -44,6 +54,11 @@ int ensure_aos(mc_lattice* h);
 void constraint_frame(double theta_deg, double phi_deg, double R[9]);
 const KernelSet& kernel_set(int precision);
 int read_state(mc_lattice* h, LatState* st);
+// n sweeps of a launch set on stream s: whole graphs of kGraphSweeps
+// sweeps, then the remainder launched directly.
+int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* cone, int n, int measure,
+               bool constrained, cudaStream_t s);
+void destroy_graphs(SweepGraphs& gr);
 int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
 
