@@ -61,12 +61,15 @@ typedef enum mc_precision { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
  * i.e. S(x + L) = -S(x): the wall setup of Sec. 3, which holds one wall. */
 typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIPERIODIC = 3 } mc_boundary;
 
-/* Colour-pass kernel of an FP32 lattice.  AUTO takes a row kernel where the
- * row layout applies (Lh = Lx/2 a power of two <= 64 or a multiple of 64,
- * Nc a multiple of 64) and the general kernel otherwise; GENERAL always
- * takes the general kernel.  Both compute the same chain up to FP32
- * rounding (the draws are keyed to the same sites); GENERAL exists to
- * compare them.  FP64 lattices always take the general kernel. */
+/* Kernels of an FP32 lattice.  AUTO takes a row kernel for the colour
+ * passes where the row layout applies (Lh = Lx/2 a power of two <= 64 or a
+ * multiple of 64, Nc a multiple of 64) and the general kernel otherwise,
+ * and walks the constrained pairs in site order when the lattice's spins
+ * and their packed copy exceed 64 MB.  GENERAL always takes the general
+ * colour-pass kernel and the pairs in pair order.  The colour passes agree
+ * up to FP32 rounding (the draws are keyed to the same sites) and the two
+ * pair orders exactly; GENERAL exists to compare them.  FP64 lattices
+ * always take the general kernel and pair order. */
 typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_path;
 
 /* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the

@@ -60,46 +60,46 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         return pa.N < pb.N;
     });
     std::vector<LatDev*> all(n);
-    std::vector<uint32_t> sa(n + 1, 0), sp(n + 1, 0);
+    std::vector<uint32_t> sa(n + 1, 0);
     for (int j = 0; j < n; ++j) {
         const LatParams& hp = lattices[order[j]]->hp;
         all[j] = lattices[order[j]]->d_lat;
         sa[j + 1] = sa[j] + hp.nblocks_site;
-        sp[j + 1] = sp[j] + hp.nblocks_pair;
     }
-    // colour passes: one list per colour-pass kernel (LatParams::colour_kernel),
-    // each with its tile starts, in launch order
-    std::vector<LatDev*> sub[3];
-    std::vector<uint32_t> st[3];
-    for (int c = 0; c < 3; ++c) st[c].assign(1, 0);
+    // colour passes: one list per colour-pass kernel (LatParams::colour_kernel);
+    // constrained pair passes: one list per pair order (LatParams::pair_leader);
+    // each list with its tile starts, in launch order
+    constexpr int kLists = 5;  // general, row, row with films; pairs in pair order, in site order
+    std::vector<LatDev*> sub[kLists];
+    std::vector<uint32_t> st[kLists];
+    for (int c = 0; c < kLists; ++c) st[c].assign(1, 0);
     for (int j = 0; j < n; ++j) {
         const LatParams& hp = lattices[order[j]]->hp;
-        const int c = hp.colour_kernel;
+        const int c = hp.colour_kernel, q = 3 + (hp.pair_leader ? 1 : 0);
         sub[c].push_back(all[j]);
         st[c].push_back(st[c].back() + hp.nblocks_site);
+        sub[q].push_back(all[j]);
+        st[q].push_back(st[q].back() + hp.nblocks_pair);
     }
     cudaSetDevice(g->device);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_ptr = al(sizeof(LatDev*) * n);
     const size_t b_idx = al(sizeof(uint32_t) * (n + 1));
-    const size_t total = 4 * b_ptr + 5 * b_idx;  // all + 3 kernel lists; site, pair + 3 kernel starts
+    const size_t total = (1 + kLists) * b_ptr + (1 + kLists) * b_idx;  // all + lists; site starts + list starts
     cudaError_t e = cudaMalloc(&g->d_mem, total);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(group)"); }
     std::vector<char> host(total, 0);
     char* hb = host.data();
     char* db = static_cast<char*>(g->d_mem);
-    const size_t o0 = 4 * b_ptr;
+    const size_t o0 = (1 + kLists) * b_ptr;
     std::copy(all.begin(), all.end(), reinterpret_cast<LatDev**>(hb));
     std::copy(sa.begin(), sa.end(), reinterpret_cast<uint32_t*>(hb + o0));
-    std::copy(sp.begin(), sp.end(), reinterpret_cast<uint32_t*>(hb + o0 + b_idx));
     g->ls.all = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0), n};
-    g->ls.pairs = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0 + b_idx), n};
     g->ls.nt_all = sa.back();
-    g->ls.nt_pairs = sp.back();
-    GroupArgs* lists[3] = {&g->ls.rest, &g->ls.row, &g->ls.rowx};
-    uint32_t* counts[3] = {&g->ls.nt_rest, &g->ls.nt_row, &g->ls.nt_rowx};
-    for (int c = 0; c < 3; ++c) {
-        const size_t op = size_t(1 + c) * b_ptr, oi = o0 + size_t(2 + c) * b_idx;
+    GroupArgs* lists[kLists] = {&g->ls.rest, &g->ls.row, &g->ls.rowx, &g->ls.pairs, &g->ls.pairs_lead};
+    uint32_t* counts[kLists] = {&g->ls.nt_rest, &g->ls.nt_row, &g->ls.nt_rowx, &g->ls.nt_pairs, &g->ls.nt_pairs_lead};
+    for (int c = 0; c < kLists; ++c) {
+        const size_t op = size_t(1 + c) * b_ptr, oi = o0 + size_t(1 + c) * b_idx;
         std::copy(sub[c].begin(), sub[c].end(), reinterpret_cast<LatDev**>(hb + op));
         std::copy(st[c].begin(), st[c].end(), reinterpret_cast<uint32_t*>(hb + oi));
         *lists[c] = GroupArgs{reinterpret_cast<LatDev**>(db + op), reinterpret_cast<uint32_t*>(db + oi),

@@ -18,9 +18,10 @@ struct KernelSet {
     // boundaries and film tables.  Null in the FP64 set.
     void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
                      cudaStream_t s);
-    // Table A2 pair pass; finalize != 0 closes the sweep in the last warp.
+    // Table A2 pair pass; finalize != 0 closes the sweep in the last warp;
+    // leader != 0 takes the pairs in site order (LatParams::pair_leader).
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
-                      int measure, cudaStream_t s);
+                      int measure, int leader, cudaStream_t s);
     // Exact M_L of every lattice of g (site tiles).
     void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Standalone sample + end of sweep (site tiles).
@@ -43,8 +44,8 @@ struct KernelSet {
 // lattice (lattice l owns tiles [start[l], start[l+1])), and for the colour
 // passes the split by colour-pass kernel (LatParams::colour_kernel).
 struct LaunchSet {
-    GroupArgs all, pairs;
-    uint32_t nt_all = 0, nt_pairs = 0;
+    GroupArgs all, pairs, pairs_lead;
+    uint32_t nt_all = 0, nt_pairs = 0, nt_pairs_lead = 0;  // pair tiles: pair order, site order
     // colour passes: row kernel, row kernel with boundaries and films, the
     // general kernel (tiles)
     GroupArgs row, rowx, rest;

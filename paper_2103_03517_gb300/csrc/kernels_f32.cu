@@ -25,6 +25,7 @@ using R = float;
 constexpr int MINB = MC_MINB_F32;  // minimum resident blocks per SM of the colour pass
 constexpr int MINB_GEN = MC_MINB_GEN_F32;  // the same for the row kernel with boundaries and films
 constexpr int MINB_PAIR = MC_MINB_PAIR_F32;  // the same for the pair pass
+constexpr int MINB_PAIR_LEAD = 2;            // the same for the pair pass in site order
 constexpr int kPairChunk = MC_PAIR_CHUNK;    // consecutive pair tiles per grid-stride step
 constexpr int V = kSitesPerThreadF32;
 
@@ -93,11 +94,19 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
     else row_sample_g<0>(g, ntiles, s);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
-               cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, MINB_PAIR, kPairChunk>);
-    pair_pass_kernel<R, MINB_PAIR, kPairChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+template <bool LEADER>
+void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
+                 cudaStream_t s) {
+    constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, kPairChunk, LEADER>);
+    pair_pass_kernel<R, B, kPairChunk, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
+}
+
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
+               int leader, cudaStream_t s) {
+    if (leader) pair_pass_t<true>(g, ntiles, cone, colour, finalize, measure, s);
+    else pair_pass_t<false>(g, ntiles, cone, colour, finalize, measure, s);
 }
 
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {

@@ -46,9 +46,10 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
 }
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
-               cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, kPairChunk>);
-    pair_pass_kernel<R, 1, kPairChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+               int leader, cudaStream_t s) {
+    (void)leader;  // FP64 lattices always take pair order (LatParams::pair_leader)
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, kPairChunk, false>);
+    pair_pass_kernel<R, 1, kPairChunk, false><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
 }
 

@@ -847,6 +847,42 @@ __device__ __forceinline__ uint32_t permute(uint32_t i, uint32_t n, int h, uint4
     return v;
 }
 
+// Inverse of permute: the Feistel rounds undone in reverse order (a round
+// maps (l, r) to (r, l ^ F(r)), so (l', r') comes from (r' ^ F(l'), l')),
+// with the same cycle-walking: from y = permute(i) the backward walk passes
+// only values >= n until it reaches i.
+__device__ __forceinline__ uint32_t permute_inv(uint32_t y, uint32_t n, int h, uint4 rk) {
+    const uint32_t mask = (1u << h) - 1u;
+    const uint32_t keys[4] = {rk.x, rk.y, rk.z, rk.w};
+    uint32_t v = y;
+    do {
+        uint32_t l = v >> h, r = v & mask;
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            const uint32_t pl = r ^ (hash32(l ^ keys[k]) & mask);
+            r = l;
+            l = pl;
+        }
+        v = (l << h) | r;
+    } while (v >= n);
+    return v;
+}
+
+// Position of the k-th (0-based) set bit of m, k < popc(m).
+__device__ __forceinline__ int select_bit(uint32_t m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int low = __popc(m & ((1u << w) - 1u));
+        if (k >= low) {
+            k -= low;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 template <typename R>
 __device__ __forceinline__ V3<R> rotate(const R* Rm, V3<R> s) {
     return V3<R>{Rm[0] * s.x + Rm[1] * s.y + Rm[2] * s.z, Rm[3] * s.x + Rm[4] * s.y + Rm[5] * s.z,
@@ -876,10 +912,8 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // covers all of them; the move's result does not depend on that order.
 template <typename R>
 __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
-                                              Spin4<R>* own4, const Spin4<R>* oth4, uint32_t pr, uint4 rk, R c,
-                                              uint32_t sweep, int colour, double ML) {
-    const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
-    const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+                                              Spin4<R>* own4, const Spin4<R>* oth4, uint32_t pr, uint32_t qi,
+                                              uint32_t qj, R c, uint32_t sweep, int colour, double ML) {
     const Geo gi = geometry(p, colour, qi);
     const Geo gj = geometry(p, colour, qj);
     uint32_t nqi[6], nqj[6];
@@ -939,7 +973,7 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
 // any moment the warps hold a window of about CHUNK tiles each, a few
 // lattices of the batch, so that the random gathers of partners and their
 // neighbours stay in L2.  A warp publishes once per lattice in a chunk.
-template <typename R, int MINB, int CHUNK>
+template <typename R, int MINB, int CHUNK, bool LEADER>
 __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
                                                                  const R* __restrict__ cone, int colour, int finalize,
                                                                  int measure) {
@@ -972,8 +1006,36 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                 Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
                 const Spin4<R>* oth4 = a4 + size_t(other) * p.stride;
                 for (uint32_t t = tile; t < t1; ++t) {
-                    const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
-                    if (pr < p.n_pairs) nacc += pair_move<R>(p, par, s, own4, oth4, pr, rk, c, sweep, colour, ML);
+                    if constexpr (LEADER) {
+                        // the 64 sites of tile t in index order; each site whose
+                        // position pi^-1(q) is even leads the pair (pi(r), pi(r+1))
+                        const uint32_t qa = (t - t0) * 64u + uint32_t(lane), qb = qa + 32u;
+                        const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_h, rk) : 1u;
+                        const uint32_t rb = qb < p.Nc ? permute_inv(qb, p.Nc, p.perm_h, rk) : 1u;
+                        const uint32_t ma = __ballot_sync(0xffffffffu, !(ra & 1u) && ra + 1u < p.Nc);
+                        const uint32_t mb = __ballot_sync(0xffffffffu, !(rb & 1u) && rb + 1u < p.Nc);
+                        const int ca = __popc(ma), total = ca + __popc(mb);
+                        for (int base = 0; base < total; base += 32) {
+                            const int j = base + lane;
+                            const bool second = j >= ca;
+                            const int src = j < total ? select_bit(second ? mb : ma, second ? j - ca : j) : 0;
+                            const uint32_t r_a = __shfl_sync(0xffffffffu, ra, src);
+                            const uint32_t r_b = __shfl_sync(0xffffffffu, rb, src);
+                            if (j < total) {
+                                const uint32_t r = second ? r_b : r_a;
+                                const uint32_t qi = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
+                                const uint32_t qj = permute(r + 1u, p.Nc, p.perm_h, rk);
+                                nacc += pair_move<R>(p, par, s, own4, oth4, r >> 1, qi, qj, c, sweep, colour, ML);
+                            }
+                        }
+                    } else {
+                        const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
+                        if (pr < p.n_pairs) {
+                            const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
+                            const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+                            nacc += pair_move<R>(p, par, s, own4, oth4, pr, qi, qj, c, sweep, colour, ML);
+                        }
+                    }
                 }
             }
             publish(L->st, lane, nacc, false, 0, colour, t1 - tile, p.nblocks_pair, [&] {

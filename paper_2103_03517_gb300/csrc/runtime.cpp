@@ -375,8 +375,13 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.div_ly = make_fastdiv(uint32_t(p.Ly));
     const uint32_t site_tile = p.nsub > 1 ? 32u : uint32_t(32 * sites_per_thread(p.precision));  // warp tiles
     p.nblocks_site = (p.Nc + site_tile - 1) / site_tile;
-    p.nblocks_pair = (p.n_pairs + 31) / 32;
+    p.nblocks_pair = (p.Nc + 63) / 64;  // pair tiles: 32 pairs, or 64 sites in site order
     if (p.nblocks_pair == 0) p.nblocks_pair = 1;
+    // constrained passes of lattices whose spins and packed copy (28 B a site
+    // in FP32) exceed half of L2 take the pairs in site order: the random
+    // gathers then miss DRAM for the partner side only
+    p.pair_leader =
+        d->kernel_path == MC_PATH_AUTO && p.precision == MC_FP32 && double(p.N) * 28.0 > 64.0 * 1024 * 1024 ? 1 : 0;
     p.J = p.nsub > 1 ? 1.0 : d->J;  // bcc / fcc: the couplings sit in the neighbour table
     p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
@@ -514,9 +519,14 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
 LaunchSet single_launch_set(mc_lattice* h) {
     LaunchSet ls;
     ls.all = GroupArgs{h->d_group_lats, h->d_group_start, 1};
-    ls.pairs = GroupArgs{h->d_group_lats, h->d_group_start_pair, 1};
     ls.nt_all = h->hp.nblocks_site;
-    ls.nt_pairs = h->hp.nblocks_pair;
+    if (h->hp.pair_leader) {
+        ls.pairs_lead = GroupArgs{h->d_group_lats, h->d_group_start_pair, 1};
+        ls.nt_pairs_lead = h->hp.nblocks_pair;
+    } else {
+        ls.pairs = GroupArgs{h->d_group_lats, h->d_group_start_pair, 1};
+        ls.nt_pairs = h->hp.nblocks_pair;
+    }
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
     if (h->hp.nsub > 1) {
         ls.xtal = h->d_lat;
@@ -575,8 +585,13 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             timed([&] { colour_pass(1, measure ? ls.sample_level : 0); });
         } else {
             k.mlong(ls.all, ls.nt_all, s);
-            timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 0, 0, 0, s); });
-            timed([&] { k.pair_pass(ls.pairs, ls.nt_pairs, cone, 1, measure ? 0 : 1, 0, s); });
+            for (int colour = 0; colour < 2; ++colour) {
+                const int fin = colour == 1 && !measure ? 1 : 0;
+                timed([&] {
+                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, fin, 0, 0, s);
+                    if (ls.nt_pairs_lead) k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, fin, 0, 1, s);
+                });
+            }
             if (measure) {
                 if (k.row_sample) {  // row-layout lattices sample in the row kernels
                     if (ls.nt_row) k.row_sample(ls.row, ls.nt_row, 0, s);

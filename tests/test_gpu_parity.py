@@ -584,3 +584,24 @@ def test_fp32_constrained_torque_matches_oracle():
     gt, rt = g["torque"][:, 1], r[:, 11]
     sig = math.hypot(blocking_error(gt), blocking_error(rt))
     assert abs(gt.mean() - rt.mean()) <= 3.5 * sig + 1e-6, (gt.mean(), rt.mean(), sig)
+
+
+def test_fp32_constrained_site_order_equals_pair_order():
+    """A 160^3 FP32 lattice (spins and packed copy above 64 MB) takes its
+    constrained pairs in site order; forced to pair order (MC_PATH_GENERAL)
+    it runs the same pairs with the same draws, so the spins are equal bit
+    for bit."""
+    dims, th = (160, 160, 160), 40.0
+    N = dims[0] * dims[1] * dims[2]
+    R = oracle.constraint_frame(th, 0.0)
+    out = []
+    for path in (mc.MC_PATH_AUTO, mc.MC_PATH_GENERAL):
+        h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, T=0.7, seed=9, init_dir=tuple(R[0]),
+                                         ring_capacity=8, kernel_path=path))
+        try:
+            mc.mc_constrained_sweep(h, th, 0.0, 3, measure=True)
+            out.append((mc.mc_get_spins(h, N), mc.mc_measure(h)))
+        finally:
+            mc.mc_destroy(h)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1].torque[1] == out[1][1].torque[1] and out[0][1].e == out[1][1].e
