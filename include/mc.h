@@ -74,15 +74,19 @@ typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_
 
 /* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the
  * cells.  BCC / FCC: 2 / 4 simple cubic sub-lattices with basis (0,0,0),
- * (1/2,1/2,1/2) / (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2); dims
- * count cubic cells (even, all boundaries PERIODIC); J couples nearest
- * neighbours (8 / 12, other sub-lattices) and J2 next-nearest ones (6, the
- * same sub-lattice one cell away).  Each sub-lattice is split red/black by
- * cell parity and the 2 nsub sub-sets are updated in turn: sub-lattice 0
- * red, 0 black, 1 red, ...  Site order of spin arrays: i = s + nsub (x + Lx
- * (y + Ly z)).  BCC / FCC lattices take standard sweeps only: no
- * constrained sweeps, films, groups, serving or profiles (MC_ERR_ARG). */
-typedef enum mc_lattice_type { MC_SC = 0, MC_BCC = 1, MC_FCC = 2 } mc_lattice_type;
+ * (1/2,1/2,1/2) / (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2) of a cubic
+ * cell; J couples nearest neighbours (8 / 12, other sub-lattices) and J2
+ * next-nearest ones (6, the same sub-lattice one cell away).  HCP: 4 simple
+ * tetragonal sub-lattices (0,0,0), (1/2,1/2,0), (1/2,1/6,1/2), (0,2/3,1/2)
+ * of the orthohexagonal cell (a, sqrt(3) a, c), c/a = sqrt(8/3); J couples
+ * the 12 nearest neighbours (two of them on the same sub-lattice, one cell
+ * away along x); J2 must be 0.  dims count cells (even, all boundaries
+ * PERIODIC).  Each sub-lattice is split red/black by cell parity and the
+ * 2 nsub sub-sets are updated in turn: sub-lattice 0 red, 0 black, 1 red,
+ * ...  Site order of spin arrays: i = s + nsub (x + Lx (y + Ly z)).  These
+ * lattices take standard sweeps only: no constrained sweeps, films, groups,
+ * serving or profiles (MC_ERR_ARG). */
+typedef enum mc_lattice_type { MC_SC = 0, MC_BCC = 1, MC_FCC = 2, MC_HCP = 3 } mc_lattice_type;
 
 typedef enum mc_init {
     MC_INIT_UNIFORM = 0, /* every spin along init_dir (default +z)             */

@@ -260,14 +260,15 @@ class Lattice:
         lib().or_reset_stats(self._h)
 
 
-BCC, FCC = 1, 2
+BCC, FCC, HCP = 1, 2, 3
 XTAL_STAT_FIELDS = ("n", "mx", "my", "mz", "ml", "e", "e_ex", "e_u", "e_c", "e_z")
 
 
 class Crystal:
-    """A bcc (kind 1) or fcc (kind 2) lattice of the serial oracle: cells
-    (Lx, Ly, Lz), all periodic; site i = s + nsub (x + Lx (y + Ly z)) for
-    sub-lattice s of cell (x, y, z).  J1 nearest, J2 next-nearest exchange."""
+    """A bcc (kind 1), fcc (kind 2) or hcp (kind 3, orthohexagonal cells)
+    lattice of the serial oracle: cells (Lx, Ly, Lz), all periodic; site i =
+    s + nsub (x + Lx (y + Ly z)) for sub-lattice s of cell (x, y, z).  J1
+    nearest, J2 next-nearest exchange (bcc, fcc)."""
 
     def __init__(self, kind, cells, J1=1.0, J2=0.0, Ku=0.0, axis=(0.0, 0.0, 1.0), Kc=0.0, H=(0.0, 0.0, 0.0),
                  T=1.0, seed=0, theta0=30, adapt_in_measure=1):

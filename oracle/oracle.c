@@ -824,7 +824,7 @@ OR_EXPORT int or_constrained_sweep_serial(or_lattice* L, double theta_deg, doubl
 
 /* --------------------------------------------------------------------- */
 /* Crystal structures (Sec. 2): bcc as 2 interleaved simple cubic          */
-/* sub-lattices, fcc as 4.  Each sub-lattice is split red/black by the      */
+/* sub-lattices, fcc as 4, hcp as 4 simple tetragonal ones.  Each sub-lattice is split red/black by the      */
 /* parity of its cell (x + y + z), and the sub-sets are visited in turn:    */
 /* sub-lattice 0 red, 0 black, 1 red, 1 black, ...  J1 couples nearest      */
 /* neighbours (other sub-lattices), J2 next-nearest neighbours (the same    */
@@ -853,23 +853,30 @@ typedef struct {
     double acc_m[3], acc_ml, acc_e, acc_parts[4];
 } or_xtal;
 
-/* Neighbour table from the basis positions: entry (s', d) of sub-lattice s
- * is a neighbour when |b_s' + d - b_s|^2 equals the nearest-neighbour
- * distance^2 (bcc 3/4, fcc 1/2; coupling J1) or 1 (next-nearest, J2), for
- * cell offsets d in {-1, 0, 1}^3.  Entries are ordered by s' ascending,
- * then d_z, d_y, d_x, each from -1 to 1: the field h is accumulated in this
- * order. */
+/* Neighbour table from the basis positions (fractions of the cell, cell
+ * lengths ell): entry (s', d) of sub-lattice s is a neighbour when
+ * |(b_s' + d - b_s) ell|^2 equals the nearest-neighbour distance^2 (bcc 3/4,
+ * fcc 1/2, hcp 1; coupling J1) or, for bcc and fcc with J2 != 0, 1 (the same
+ * sub-lattice one cell away; coupling J2), for cell offsets d in
+ * {-1, 0, 1}^3.  Entries are ordered by s' ascending, then d_z, d_y, d_x,
+ * each from -1 to 1: the field h is accumulated in this order.
+ * hcp: the orthohexagonal cell (a, sqrt(3) a, c), c/a = sqrt(8/3), with 4
+ * simple tetragonal sub-lattices (0,0,0), (1/2,1/2,0), (1/2,1/6,1/2),
+ * (0,2/3,1/2); a = 1. */
 OR_EXPORT or_xtal* or_xtal_create(int type, const int cells[3], double J1, double J2, double Ku, const double axis[3],
                                   double Kc, const double H[3], double T, uint64_t seed, int theta0,
                                   int adapt_in_measure) {
     static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
     static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
-    if (type != 1 && type != 2) return NULL;
+    static const double hcp[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 1.0 / 6.0, 0.5}, {0, 2.0 / 3.0, 0.5}};
+    if (type != 1 && type != 2 && type != 3) return NULL;
     or_xtal* X = (or_xtal*)calloc(1, sizeof(or_xtal));
     if (!X) return NULL;
     X->nsub = type == 1 ? 2 : 4;
-    const double(*b)[3] = type == 1 ? bcc : fcc;
-    const double d1 = type == 1 ? 0.75 : 0.5;
+    const double(*b)[3] = type == 1 ? bcc : (type == 2 ? fcc : hcp);
+    const double ell[3] = {1.0, type == 3 ? sqrt(3.0) : 1.0, type == 3 ? sqrt(8.0 / 3.0) : 1.0};
+    const double d1 = type == 1 ? 0.75 : (type == 2 ? 0.5 : 1.0);
+    const int with_j2 = type != 3 && J2 != 0.0;
     for (int a = 0; a < 3; ++a) X->L[a] = cells[a];
     X->N = (int64_t)X->nsub * cells[0] * cells[1] * cells[2];
     for (int s = 0; s < X->nsub; ++s) {
@@ -878,11 +885,12 @@ OR_EXPORT or_xtal* or_xtal_create(int type, const int cells[3], double J1, doubl
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const double r[3] = {b[t][0] + dx - b[s][0], b[t][1] + dy - b[s][1], b[t][2] + dz - b[s][2]};
+                        const double r[3] = {(b[t][0] + dx - b[s][0]) * ell[0], (b[t][1] + dy - b[s][1]) * ell[1],
+                                             (b[t][2] + dz - b[s][2]) * ell[2]};
                         const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
                         double J;
                         if (fabs(r2 - d1) < 1e-9) J = J1;
-                        else if (fabs(r2 - 1.0) < 1e-9) J = J2;
+                        else if (with_j2 && fabs(r2 - 1.0) < 1e-9) J = J2;
                         else continue;
                         X->nb_sub[s][n] = t;
                         X->nb_d[s][n][0] = dx; X->nb_d[s][n][1] = dy; X->nb_d[s][n][2] = dz;

@@ -136,29 +136,36 @@ static void set_float_params(LatParams& p) {
     for (int a = 0; a < 9; ++a) p.fR[a] = (float)p.R[a];
 }
 
-int sublattices(int lattice) { return lattice == MC_BCC ? 2 : (lattice == MC_FCC ? 4 : 1); }
+int sublattices(int lattice) { return lattice == MC_BCC ? 2 : (lattice == MC_FCC || lattice == MC_HCP ? 4 : 1); }
 
-// Neighbour table of a bcc or fcc lattice from its basis (positions in
-// units of the cubic cell): entry (t, d) of sub-lattice s, d a cell offset
-// in {-1, 0, 1}^3, is a neighbour when |b_t + d - b_s|^2 equals the
-// nearest-neighbour distance^2 (bcc 3/4, fcc 1/2; coupling J) or 1 (the
-// same sub-lattice one cell away; coupling J2).  Entries are ordered by t,
-// then d_z, d_y, d_x from -1 to 1: the order in which the field is summed.
+// Neighbour table of a bcc, fcc or hcp lattice from its basis (fractions of
+// the cell; cell lengths ell, a = 1): entry (t, d) of sub-lattice s, d a
+// cell offset in {-1, 0, 1}^3, is a neighbour when |(b_t + d - b_s) ell|^2
+// equals the nearest-neighbour distance^2 (bcc 3/4, fcc 1/2, hcp 1;
+// coupling J) or, for bcc and fcc with J2 != 0, 1 (the same sub-lattice one
+// cell away; coupling J2).  Entries are ordered by t, then d_z, d_y, d_x
+// from -1 to 1: the order in which the field is summed.  hcp: the
+// orthohexagonal cell (1, sqrt 3, sqrt(8/3)) with sub-lattices (0,0,0),
+// (1/2,1/2,0), (1/2,1/6,1/2), (0,2/3,1/2).
 static void xtal_table(int lattice, double J, double J2, XtalNb out[kXtalMaxSub][kXtalMaxNb], int n[kXtalMaxSub]) {
     const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
     const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    const double hcp[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 1.0 / 6.0, 0.5}, {0, 2.0 / 3.0, 0.5}};
     const int ns = sublattices(lattice);
-    const double(*b)[3] = lattice == MC_BCC ? bcc : fcc;
-    const double nn2 = lattice == MC_BCC ? 0.75 : 0.5;
+    const double(*b)[3] = lattice == MC_BCC ? bcc : (lattice == MC_FCC ? fcc : hcp);
+    const double ell[3] = {1.0, lattice == MC_HCP ? std::sqrt(3.0) : 1.0, lattice == MC_HCP ? std::sqrt(8.0 / 3.0) : 1.0};
+    const double nn2 = lattice == MC_BCC ? 0.75 : (lattice == MC_FCC ? 0.5 : 1.0);
+    const bool with_j2 = lattice != MC_HCP && J2 != 0.0;
     for (int s = 0; s < ns; ++s) {
         n[s] = 0;
         for (int t = 0; t < ns; ++t)
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const double r[3] = {b[t][0] + dx - b[s][0], b[t][1] + dy - b[s][1], b[t][2] + dz - b[s][2]};
+                        const double r[3] = {(b[t][0] + dx - b[s][0]) * ell[0], (b[t][1] + dy - b[s][1]) * ell[1],
+                                             (b[t][2] + dz - b[s][2]) * ell[2]};
                         const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                        const bool nn = std::fabs(r2 - nn2) < 1e-9, nnn = std::fabs(r2 - 1.0) < 1e-9;
+                        const bool nn = std::fabs(r2 - nn2) < 1e-9, nnn = with_j2 && std::fabs(r2 - 1.0) < 1e-9;
                         if (!nn && !nnn) continue;
                         XtalNb& e = out[s][n[s]++];
                         e.sub = int8_t(t);
@@ -204,11 +211,12 @@ int validate_desc(const mc_desc* d) {
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
     if (!(an > 0.0)) return fail(MC_ERR_ARG, "|axis| = 0");
     if (d->precision != MC_FP32 && d->precision != MC_FP64) return fail(MC_ERR_ARG, "precision invalid");
-    if (d->lattice != MC_SC && d->lattice != MC_BCC && d->lattice != MC_FCC) return fail(MC_ERR_ARG, "lattice invalid");
+    if (d->lattice < MC_SC || d->lattice > MC_HCP) return fail(MC_ERR_ARG, "lattice invalid");
+    if (d->lattice == MC_HCP && d->J2 != 0.0) return fail(MC_ERR_ARG, "hcp lattices take J2 = 0");
     if (d->lattice != MC_SC) {
         for (int a = 0; a < 3; ++a)
-            if (d->boundary[a] != MC_PERIODIC) return fail(MC_ERR_ARG, "bcc / fcc lattices need periodic cells");
-        if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc lattices take no film tables");
+            if (d->boundary[a] != MC_PERIODIC) return fail(MC_ERR_ARG, "bcc / fcc / hcp lattices need periodic cells");
+        if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc / hcp lattices take no film tables");
         if (!std::isfinite(d->J2)) return fail(MC_ERR_ARG, "J2 not finite");
     }
     if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL)

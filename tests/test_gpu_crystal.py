@@ -1,7 +1,8 @@
-"""bcc / fcc lattices (Sec. 2: 2 / 4 simple cubic sub-lattices, each split
-red/black, the sub-sets updated in turn) on the GPU: FP64 bit-exact with
-the oracle's chain, FP32 statistically equal to FP64, and the calls that
-stay simple-cubic-only refuse these lattices."""
+"""bcc / fcc / hcp lattices (Sec. 2: 2 / 4 simple cubic or 4 simple
+tetragonal sub-lattices, each split red/black, the sub-sets updated in
+turn) on the GPU: FP64 bit-exact with the oracle's chain, FP32
+statistically equal to FP64, and the calls that stay simple-cubic-only
+refuse these lattices."""
 import numpy as np
 import pytest
 
@@ -19,12 +20,13 @@ def _built():
     libbuild.build()
 
 
-KIND = {mc.MC_BCC: oracle.BCC, mc.MC_FCC: oracle.FCC}
+KIND = {mc.MC_BCC: oracle.BCC, mc.MC_FCC: oracle.FCC, mc.MC_HCP: oracle.HCP}
 
 
 @pytest.mark.parametrize("lattice,cells,J2", [(mc.MC_BCC, (4, 2, 6), 0.0), (mc.MC_BCC, (6, 4, 2), 0.3),
                                               (mc.MC_FCC, (2, 4, 2), 0.0), (mc.MC_FCC, (4, 4, 6), -0.2),
-                                              (mc.MC_FCC, (8, 2, 2), 0.1)])
+                                              (mc.MC_FCC, (8, 2, 2), 0.1), (mc.MC_HCP, (4, 2, 6), 0.0),
+                                              (mc.MC_HCP, (2, 4, 2), 0.0)])
 def test_crystal_fp64_bit_exact(lattice, cells, J2):
     nsub = 2 if lattice == mc.MC_BCC else 4
     N = nsub * cells[0] * cells[1] * cells[2]
@@ -52,10 +54,10 @@ def test_crystal_fp64_bit_exact(lattice, cells, J2):
         mc.mc_destroy(h)
 
 
-@pytest.mark.parametrize("lattice", [mc.MC_BCC, mc.MC_FCC])
+@pytest.mark.parametrize("lattice", [mc.MC_BCC, mc.MC_FCC, mc.MC_HCP])
 def test_crystal_fp32_matches_fp64(lattice):
-    """Below T_C (bcc 2.05, fcc 3.18 for J = 1): FP32 and FP64 ensembles agree
-    on <|m|> and <E> within 4 sigma of the blocking errors."""
+    """Below T_C (bcc 2.05, fcc and hcp near 3.2 for J = 1): FP32 and FP64
+    ensembles agree on <|m|> and <E> within 4 sigma of the blocking errors."""
     cells, T, n = (8, 8, 8), (1.4 if lattice == mc.MC_BCC else 2.2), 3000
     hs = [mc.mc_create_ex(mc.make_desc(cells, K_u=0.02, T=T, seed=s, precision=p, lattice=lattice, ring_capacity=n))
           for s, p in ((1, mc.MC_FP32), (2, mc.MC_FP64))]

@@ -1,5 +1,5 @@
-"""Pins of the bcc / fcc oracle (Sec. 2: bcc as 2, fcc as 4 simple cubic
-sub-lattices, each split red/black).  Expected values come from the atomic
+"""Pins of the bcc / fcc / hcp oracle (Sec. 2: bcc as 2, fcc as 4 simple
+cubic sub-lattices, hcp as 4 simple tetragonal ones, each split red/black).  Expected values come from the atomic
 positions, never from the oracle's neighbour table: a brute-force Eq. 2
 energy over all pairs at the nearest and next-nearest distances, the
 ground-state energy, and harmonic spin waves from the bond graph."""
@@ -11,8 +11,13 @@ import pytest
 import oracle
 
 BASIS = {oracle.BCC: [(0, 0, 0), (0.5, 0.5, 0.5)],
-         oracle.FCC: [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]}
-NN2 = {oracle.BCC: 0.75, oracle.FCC: 0.5}
+         oracle.FCC: [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)],
+         oracle.HCP: [(0, 0, 0), (0.5, 0.5, 0), (0.5, 1 / 6, 0.5), (0, 2 / 3, 0.5)]}
+# cell lengths: cubic cells, and the orthohexagonal cell (a, sqrt 3 a, c) with c/a = sqrt(8/3)
+ELL = {oracle.BCC: (1.0, 1.0, 1.0), oracle.FCC: (1.0, 1.0, 1.0),
+       oracle.HCP: (1.0, math.sqrt(3.0), math.sqrt(8.0 / 3.0))}
+NN2 = {oracle.BCC: 0.75, oracle.FCC: 0.5, oracle.HCP: 1.0}
+Z1 = {oracle.BCC: 8, oracle.FCC: 12, oracle.HCP: 12}
 
 
 def positions(kind, cells):
@@ -23,7 +28,7 @@ def positions(kind, cells):
         for y in range(Ly):
             for x in range(Lx):
                 for s in range(len(b)):
-                    out.append(b[s] + (x, y, z))
+                    out.append((b[s] + (x, y, z)) * ELL[kind])
     return np.array(out)  # site i = s + nsub (x + Lx (y + Ly z))
 
 
@@ -32,7 +37,7 @@ def bonds(kind, cells, J1, J2):
     nearest (J1) or next-nearest (distance 1, J2) distance, periodic images
     included, so small cells count a doubled bond twice."""
     pos = positions(kind, cells)
-    L = np.array(cells, float)
+    L = np.array(cells, float) * ELL[kind]
     out = []
     for i in range(len(pos)):
         for j in range(len(pos)):
@@ -55,7 +60,8 @@ def energy(S, bl, Ku, axis, Kc, H):
 
 
 @pytest.mark.parametrize("kind,cells,J2", [(oracle.BCC, (2, 2, 2), 0.0), (oracle.BCC, (4, 2, 2), 0.3),
-                                           (oracle.FCC, (2, 2, 2), 0.0), (oracle.FCC, (2, 4, 2), -0.2)])
+                                           (oracle.FCC, (2, 2, 2), 0.0), (oracle.FCC, (2, 4, 2), -0.2),
+                                           (oracle.HCP, (2, 2, 2), 0.0), (oracle.HCP, (4, 2, 2), 0.0)])
 def test_crystal_delta_e_equals_total_energy_difference(kind, cells, J2):
     rng = np.random.default_rng(int(kind) * 10 + cells[0])
     J1, Ku, Kc = 1.2, 0.3, -0.4
@@ -67,8 +73,7 @@ def test_crystal_delta_e_equals_total_energy_difference(kind, cells, J2):
     S /= np.linalg.norm(S, axis=1, keepdims=True)
     X.set_spins(S)
     bl = bonds(kind, cells, J1, J2)
-    z = {oracle.BCC: 8, oracle.FCC: 12}[kind]
-    assert len([b for b in bl if b[2] == J1]) == z * X.N  # every site has z nearest neighbours
+    assert len([b for b in bl if b[2] == J1]) == Z1[kind] * X.N  # every site has z nearest neighbours
     E0 = energy(S, bl, Ku, axis, Kc, H)
     for _ in range(20):
         i = int(rng.integers(X.N))
@@ -79,23 +84,24 @@ def test_crystal_delta_e_equals_total_energy_difference(kind, cells, J2):
         assert abs(X.delta_e(i, Sn) - (energy(S1, bl, Ku, axis, Kc, H) - E0)) < 1e-12 * max(1.0, abs(E0))
 
 
-@pytest.mark.parametrize("kind", [oracle.BCC, oracle.FCC])
+@pytest.mark.parametrize("kind", [oracle.BCC, oracle.FCC, oracle.HCP])
 def test_crystal_sample_energy_equals_brute_force(kind):
     """The measured energy parts of one sweep sum to the brute-force E/N of
     the final state."""
     cells = (2, 2, 2)
     rng = np.random.default_rng(3)
-    X = oracle.Crystal(kind, cells, J1=1.0, J2=0.25, Ku=0.2, Kc=0.1, H=(0.1, 0.0, -0.2), T=0.8, seed=5)
+    J2 = 0.0 if kind == oracle.HCP else 0.25
+    X = oracle.Crystal(kind, cells, J1=1.0, J2=J2, Ku=0.2, Kc=0.1, H=(0.1, 0.0, -0.2), T=0.8, seed=5)
     S = rng.standard_normal((X.N, 3))
     X.set_spins(S / np.linalg.norm(S, axis=1, keepdims=True))
     X.sweep(1, measure=True)
     st = X.stats()
-    E = energy(X.spins(), bonds(kind, cells, 1.0, 0.25), 0.2, np.array([0, 0, 1.0]), 0.1, (0.1, 0.0, -0.2))
+    E = energy(X.spins(), bonds(kind, cells, 1.0, J2), 0.2, np.array([0, 0, 1.0]), 0.1, (0.1, 0.0, -0.2))
     assert abs(st["e"] - E / X.N) < 1e-13
     assert abs(st["e_ex"] + st["e_u"] + st["e_c"] + st["e_z"] - st["e"]) < 1e-13
 
 
-@pytest.mark.parametrize("kind,J2", [(oracle.BCC, 0.0), (oracle.FCC, 0.0), (oracle.BCC, 0.2)])
+@pytest.mark.parametrize("kind,J2", [(oracle.BCC, 0.0), (oracle.FCC, 0.0), (oracle.BCC, 0.2), (oracle.HCP, 0.0)])
 def test_crystal_harmonic_spin_waves(kind, J2):
     """Low T, uniaxial K along z: E = 1/2 u^T A u per transverse component
     with A = the bond-weighted graph Laplacian + 2K, so equipartition gives
@@ -109,8 +115,7 @@ def test_crystal_harmonic_spin_waves(kind, J2):
         A[i, i] += J
         A[i, j] -= J
     one_minus_m = T / N * np.trace(np.linalg.inv(A))
-    z1 = {oracle.BCC: 8, oracle.FCC: 12}[kind]
-    e0 = -(z1 * 1.0 + 6 * J2) / 2 - K
+    e0 = -(Z1[kind] * 1.0 + 6 * J2) / 2 - K
     X.sweep(500)
     X.sweep(3000, measure=True)
     st = X.stats()
