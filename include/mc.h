@@ -48,7 +48,8 @@ typedef enum mc_status {
     MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up                     */
     MC_ERR_CONSTRAINT = -5, /* constrained run with M_L <= 0 (Table A2)          */
     MC_ERR_STATE = -6,      /* call not valid in the current state               */
-    MC_ERR_IO = -7          /* checkpoint file could not be read or written      */
+    MC_ERR_IO = -7,         /* checkpoint file could not be read or written      */
+    MC_ERR_CANCELLED = -8   /* the job was cancelled (mc_cancel)                  */
 } mc_status;
 
 typedef enum mc_precision { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
@@ -326,6 +327,12 @@ MC_API int mc_submit(mc_server* s, const mc_job* job, uint64_t* job_id);
 /* MC_PENDING while queued or running; MC_OK and *out once finished (the
  * result stays available); MC_ERR_ARG for an unknown id. */
 MC_API int mc_poll(mc_server* s, uint64_t job_id, mc_result* out);
+
+/* Cancel a job.  A queued job is dropped at once; a resident job is retired
+ * at the end of the current epoch (its lattice destroyed, its memory
+ * returned).  Its result then reads status MC_ERR_CANCELLED.  MC_ERR_STATE
+ * if the job has already finished, MC_ERR_ARG for an unknown id. */
+MC_API int mc_cancel(mc_server* s, uint64_t job_id);
 
 /* Current server clock (seconds), jobs queued / resident, bytes in use. */
 MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident, size_t* bytes);

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmc.so")
 MC_OK, MC_PENDING = 0, 1
 MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR_STATE, MC_ERR_IO = (
     -1, -2, -3, -4, -5, -6, -7)
+MC_ERR_CANCELLED = -8
 MC_FP32, MC_FP64 = 0, 1
 MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
 MC_PATH_AUTO, MC_PATH_GENERAL = 0, 1
@@ -115,6 +116,7 @@ _SIGS = {
     "mc_server_destroy": (C.c_int, [C.c_void_p]),
     "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
     "mc_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(mc_result)]),
+    "mc_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mc_server_stats": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
     "mc_sweep_noalloc": (C.c_int, [C.c_void_p, _P(C.c_int), C.c_double, C.c_double, _P(C.c_double), C.c_double,
                                    _P(C.c_double), C.c_double, C.c_uint64, C.c_int64, C.c_int, _P(C.c_int),
@@ -388,6 +390,11 @@ def mc_poll(s, job_id: int):
     r = mc_result()
     rc = _check(lib().mc_poll(s, int(job_id), C.byref(r)))
     return rc, (r if rc == MC_OK else None)
+
+
+def mc_cancel(s, job_id: int) -> None:
+    """Cancel a queued or resident job (its result then reads MC_ERR_CANCELLED)."""
+    _check(lib().mc_cancel(s, int(job_id)))
 
 
 def mc_server_stats(s):

@@ -24,6 +24,7 @@ struct mc_group {
 };
 
 static int group_run(mc_group* g, int n, int measure, bool constrained) {
+    NvtxRange range(constrained ? "mc_group_constrained_sweep" : "mc_group_sweep");
     cudaSetDevice(g->device);
     return run_sweeps(g->graphs, g->precision, g->ls, g->cone, n, measure, constrained, g->stream);
 }

@@ -726,6 +726,7 @@ MC_API int mc_set_field(mc_handle h, const double H[3]) {
 
 MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
     if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    NvtxRange range("mc_sweep");
     cudaSetDevice(h->device);
     return run_sweeps(h->graphs, h->hp.precision, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, false,
                       h->stream);
@@ -733,6 +734,7 @@ MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
 
 MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_deg, int n_sweeps, int measure) {
     if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    NvtxRange range("mc_constrained_sweep");
     if (!(theta_c_deg >= 0.0 && theta_c_deg <= 180.0)) return fail(MC_ERR_ARG, "theta_c outside [0, 180]");
     if (!std::isfinite(phi_c_deg)) return fail(MC_ERR_ARG, "phi_c not finite");
     for (int a = 0; a < 3; ++a)

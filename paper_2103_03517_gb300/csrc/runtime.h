@@ -1,6 +1,7 @@
 // runtime.h -- host-side objects shared by the runtime, groups and server.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <utility>
 #include <vector>
@@ -10,6 +11,14 @@
 #include "mc_internal.h"
 
 namespace mcgb {
+// An NVTX range for the scope of the object (a no-op without a profiler).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Captured CUDA graphs of kGraphSweeps sweeps of one launch set, by
 // [constrained][measure]; built on first use and replayed.
 constexpr int kGraphSweeps = 16;

@@ -34,7 +34,8 @@ struct Job {
     mc_observables obs;
     mc_handle h = nullptr;
     bool measuring = false;
-    int remaining = 0;  // sweeps left in the current phase
+    bool cancel = false;  // retire at the end of the current epoch
+    int remaining = 0;    // sweeps left in the current phase
 };
 
 }  // namespace
@@ -75,6 +76,7 @@ static void finish(mc_server* s, Job* j, int status) {
 }
 
 void mc_server::run_epoch(std::vector<Job*>& res) {
+    NvtxRange range("mc server epoch");
     int n = d.max_epoch_sweeps;
     for (Job* j : res) n = std::min(n, j->remaining);
     if (n < 1) n = 1;
@@ -112,6 +114,10 @@ void mc_server::run_epoch(std::vector<Job*>& res) {
     std::vector<Job*> keep;
     for (Job* j : res) {
         if (j->status != MC_PENDING) continue;
+        if (j->cancel) {
+            finish(this, j, MC_ERR_CANCELLED);
+            continue;
+        }
         j->remaining -= n;
         if (j->remaining <= 0) {
             if (!j->measuring && j->job.n_measure > 0) {
@@ -138,6 +144,7 @@ void mc_server::loop() {
             cv.wait(lk, [&] { return stop || !queue.empty() || !resident.empty(); });
             if (stop) return;
             // admission: FIFO while memory and slots allow
+            NvtxRange range("mc server admission");
             while (!queue.empty() && int(resident.size()) < d.max_resident) {
                 Job* j = queue.front();
                 if (used + j->bytes > budget) break;
@@ -251,6 +258,25 @@ MC_API int mc_poll(mc_server* s, uint64_t job_id, mc_result* out) {
         out->t_finish = j->t_finish;
         out->status = j->status;
     }
+    return MC_OK;
+}
+
+MC_API int mc_cancel(mc_server* s, uint64_t job_id) {
+    if (!s) return fail(MC_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return fail(MC_ERR_ARG, "unknown job id %llu", (unsigned long long)job_id);
+    Job* j = it->second.get();
+    if (j->status != MC_PENDING) return fail(MC_ERR_STATE, "job %llu has finished", (unsigned long long)job_id);
+    auto q = std::find(s->queue.begin(), s->queue.end(), j);
+    if (q != s->queue.end()) {  // not admitted: drop it now
+        s->queue.erase(q);
+        j->t_finish = s->now();
+        j->status = MC_ERR_CANCELLED;
+    } else {
+        j->cancel = true;  // resident: the worker retires it after the epoch
+    }
+    s->cv.notify_all();
     return MC_OK;
 }
 

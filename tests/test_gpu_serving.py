@@ -127,3 +127,38 @@ def test_jobs_overlap_and_memory_is_returned():
             mc.mc_poll(s, 999999)
     finally:
         mc.mc_server_destroy(s)
+
+
+def test_cancel_queued_resident_and_finished_jobs():
+    """Host-side fault injection: a queued job is dropped at once, a
+    resident one is retired after its epoch with its memory returned, and
+    the server carries on with later jobs."""
+    s = mc.mc_server_create(max_resident=1, max_epoch_sweeps=8)
+    try:
+        long_job = mc.make_job(mc.make_desc((64, 64, 64), T=0.7, seed=1), n_equilibrate=100000, n_measure=10)
+        a = mc.mc_submit(s, long_job)
+        b = mc.mc_submit(s, mc.make_job(mc.make_desc((16, 16, 16), seed=2), n_measure=5))
+        t0 = time.time()
+        while mc.mc_server_stats(s)[2] < 1:  # a is resident, b queued behind it
+            assert time.time() - t0 < 30
+            time.sleep(0.002)
+        mc.mc_cancel(s, b)
+        rc, res = mc.mc_poll(s, b)
+        assert rc == mc.MC_OK and res.status == mc.MC_ERR_CANCELLED
+        mc.mc_cancel(s, a)
+        res = _wait(s, [a])[a]
+        assert res.status == mc.MC_ERR_CANCELLED and res.t_finish >= res.t_admit > 0
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_cancel(s, a)
+        assert e.value.code == mc.MC_ERR_STATE
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_cancel(s, 987654)
+        assert e.value.code == mc.MC_ERR_ARG
+        c = mc.mc_submit(s, _probe_job())
+        assert _wait(s, [c])[c].status == mc.MC_OK
+        t0 = time.time()
+        while mc.mc_server_stats(s)[3] != 0:
+            assert time.time() - t0 < 30
+            time.sleep(0.002)
+    finally:
+        mc.mc_server_destroy(s)
