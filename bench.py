@@ -457,7 +457,7 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
     """FP32 throughput of the lattices that are not all-periodic simple
     cubes: the Bloch-wall lattice (1024 x 128 x 128, x pinned, T = 0.66), a
     granular film (1024 x 1024 x 15, Voronoi grains of mean diameter 10, bond
-    mask and grain axes, z open) and an fcc lattice of 64^3 cells (1,048,576
+    mask and grain axes, z open) and an fcc lattice of 128^3 cells (8,388,608
     spins, T = 2.0), measured sweeps, CUDA events."""
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     spec = workloads.config4()[3]
@@ -468,7 +468,7 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
              ("film", (1024, 1024, 15), mc.make_desc((1024, 1024, 15), K_u=0.02, T=0.6, seed=3, boundary=(0, 0, 1),
                                                      bond_mask=mask, grain_id=gid, grain_axis=axes, ring_capacity=16,
                                                      stream=stream.cuda_stream, device=dev)),
-             ("fcc", (64, 64, 64), mc.make_desc((64, 64, 64), K_u=0.02, T=2.0, seed=4, lattice=mc.MC_FCC,
+             ("fcc", (128, 128, 128), mc.make_desc((128, 128, 128), K_u=0.02, T=2.0, seed=4, lattice=mc.MC_FCC,
                                                 ring_capacity=16, stream=stream.cuda_stream, device=dev))]
     out = {}
     for name, dims, d in cases:
@@ -483,7 +483,7 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
         out[name] = n * sweeps / (a.elapsed_time(b) * 1e-3)
         mc.mc_destroy(h)
     return {"general_geometry": {"unit": UNIT, "wall_1024x128x128_pinned_x": out["wall"],
-                                 "film_1024x1024x15": out["film"], "fcc_64c": out["fcc"],
+                                 "film_1024x1024x15": out["film"], "fcc_128c": out["fcc"],
                                  "workload": f"{sweeps} measured sweeps each, FP32"}}
 
 

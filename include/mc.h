@@ -21,11 +21,12 @@
  *    mc_destroy.  Handles are not thread safe: use one handle per thread.
  *    A server (mc_server_*) is internally synchronised.
  *  - mc_sweep, mc_constrained_sweep and mc_group_sweep are asynchronous on
- *    the lattice's CUDA stream; errors found on the device (MC_ERR_TIMEOUT,
- *    MC_ERR_CONSTRAINT) are reported by the next synchronising call
- *    (mc_measure, mc_samples, mc_profile, mc_get_spins, mc_sync, mc_save).
+ *    the lattice's CUDA stream; errors found on the device (MC_ERR_CONSTRAINT,
+ *    MC_ERR_STATE) are reported by the next synchronising call (mc_measure,
+ *    mc_samples, mc_profile, mc_get_spins, mc_sync, mc_save).
  *  - Site order of every host spin array is x + Lx (y + Ly z), three
- *    components per site (N x 3, row major).
+ *    components per site (N x 3, row major); bcc / fcc / hcp lattices put
+ *    the sub-lattice first: s + nsub (x + Lx (y + Ly z)).
  */
 #ifndef MC_H
 #define MC_H
@@ -45,7 +46,8 @@ typedef enum mc_status {
     MC_ERR_ARG = -1,        /* invalid argument (checked on the host)            */
     MC_ERR_NOMEM = -2,      /* device memory exhausted / job can never fit       */
     MC_ERR_CUDA = -3,       /* a CUDA call failed (message in mc_last_error)     */
-    MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up                     */
+    MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up (no kernel waits    */
+                            /* in this version; kept for the ABI)                */
     MC_ERR_CONSTRAINT = -5, /* constrained run with M_L <= 0 (Table A2)          */
     MC_ERR_STATE = -6,      /* call not valid in the current state               */
     MC_ERR_IO = -7,         /* checkpoint file could not be read or written      */
@@ -103,7 +105,8 @@ typedef struct mc_server mc_server;
 typedef struct mc_desc {
     int dims[3];            /* Lx, Ly, Lz >= 1; Lx must be even                   */
     int boundary[3];        /* mc_boundary per axis                               */
-    int precision;          /* mc_precision: FP32 spins (FP64 accumulators) or FP64 */
+    int precision;          /* mc_precision: FP32 spins (fixed-point sample sums, */
+                            /* FP64 moments) or FP64                              */
     double J;               /* nearest-neighbour exchange                         */
     double K_u;             /* uniaxial anisotropy constant                       */
     double axis[3];         /* uniaxial easy axis (normalised by the library)     */
@@ -174,7 +177,8 @@ typedef struct mc_sample {
 MC_API void mc_desc_default(mc_desc* d);
 
 /* Create a lattice (Eq. 2 parameters; Sec. 2).  dims: Lx, Ly, Lz, all
- * periodic; FP32 spins with FP64 accumulators; spins start along +z.
+ * periodic; FP32 spins, fixed-point sample sums and FP64 moments; spins
+ * start along +z.
  * Errors: MC_ERR_ARG (odd periodic size, T <= 0, |axis| = 0, ...),
  * MC_ERR_NOMEM, MC_ERR_CUDA.  *out is set only on MC_OK. */
 MC_API int mc_create(const int dims[3], double J, double K_u, const double axis[3], double K_c,
