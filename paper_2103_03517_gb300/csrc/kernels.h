@@ -22,6 +22,9 @@ struct KernelSet {
     // leader != 0 takes the pairs in site order (LatParams::pair_leader).
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
                       int measure, int leader, cudaStream_t s);
+    // Neighbour field of every site of the given colour into LatParams::pfield
+    // (site tiles), before that colour's pair pass.
+    void (*pair_field)(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s);
     // Exact M_L of every lattice of g (site tiles).
     void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Standalone sample + end of sweep (site tiles).

@@ -53,6 +53,11 @@ void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour
         g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
 }
 
+void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V>);
+    pair_field_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+}
+
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     static const uint32_t cap = resident_blocks(mlong_kernel<R, V>);
     mlong_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
@@ -82,7 +87,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f64() {
-    static const KernelSet k{colour_pass, nullptr, pair_pass, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, nullptr, pair_pass, pair_field, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
                              "f64"};
     return k;
 }

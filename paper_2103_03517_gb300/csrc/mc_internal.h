@@ -112,6 +112,9 @@ struct LatParams {
                             // spins (Spin4), written by mlong_kernel at the start of each
                             // sweep and kept in step by the pair passes; null until the
                             // lattice's first constrained sweep
+    void* pfield;           // constrained sweeps: [stride] (h_x, h_y, h_z, 0) neighbour
+                            // field of every site of the colour being updated, written by
+                            // pair_field_kernel before each pair pass
     double J, Ku, e[3], Kc, H[3], T;
     float fJ, fKu, fe[3], fKc, fH[3], fT;
     float fBeta2;           // FP32 Metropolis test: -log2(e) / T, so exp(-dE/T) = 2^(dE fBeta2)

@@ -906,22 +906,19 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // packed copy (one sector per site instead of one per component); accepted
 // moves are written to the spins and to the copy of the pass's colour.
 // ------------------------------------------------------------------------
-// One pair of the pass (pair index pr of the lattice); returns the accepted
-// spin count (0 or 2).  The gathers of both spins and of their neighbours
-// are issued together, before the move is drawn, so that one L2 round trip
-// covers all of them; the move's result does not depend on that order.
+// One pair of the pass (pair index pr of the lattice, sites qi and qj);
+// returns the accepted spin count (0 or 2).  Each member needs its spin and
+// its neighbour field, both gathered from packed 4-vectors (the field was
+// summed for every site of the colour by pair_field_kernel, in the order of
+// neighbour_sum4), and issued together before the move is drawn.
 template <typename R>
 __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
-                                              Spin4<R>* own4, const Spin4<R>* oth4, uint32_t pr, uint32_t qi,
+                                              Spin4<R>* own4, const Spin4<R>* fld, uint32_t pr, uint32_t qi,
                                               uint32_t qj, R c, uint32_t sweep, int colour, double ML) {
-    const Geo gi = geometry(p, colour, qi);
-    const Geo gj = geometry(p, colour, qj);
-    uint32_t nqi[6], nqj[6];
-    const uint32_t pi_ = neighbours(p, gi, colour, nqi);
-    const uint32_t pj_ = neighbours(p, gj, colour, nqj);
     const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
-    const V3<R> h_i = neighbour_sum4(oth4, nqi, pi_);
-    const V3<R> h_j = neighbour_sum4(oth4, nqj, pj_);
+    const Spin4<R> fi4 = fld[qi], fj4 = fld[qj];
+    const V3<R> h_i{fi4.x, fi4.y, fi4.z};
+    const V3<R> h_j{fj4.x, fj4.y, fj4.z};
     const V3<R> Si{si4.x, si4.y, si4.z};
     const V3<R> Sj{sj4.x, sj4.y, sj4.z};
     const V3<R> hi = rotate(par.Rm, Si);
@@ -978,7 +975,6 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                                                                  const R* __restrict__ cone, int colour, int finalize,
                                                                  int measure) {
     const int lane = int(threadIdx.x & 31);
-    const int other = colour ^ 1;
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
     const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
     int l = 0;
@@ -1004,7 +1000,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                 R* __restrict__ s = static_cast<R*>(p.spins);
                 const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
                 Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
-                const Spin4<R>* oth4 = a4 + size_t(other) * p.stride;
+                const Spin4<R>* fld = static_cast<const Spin4<R>*>(p.pfield);
                 for (uint32_t t = tile; t < t1; ++t) {
                     if constexpr (LEADER) {
                         // the 64 sites of tile t in index order; each site whose
@@ -1025,7 +1021,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                                 const uint32_t r = second ? r_b : r_a;
                                 const uint32_t qi = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
                                 const uint32_t qj = permute(r + 1u, p.Nc, p.perm_h, rk);
-                                nacc += pair_move<R>(p, par, s, own4, oth4, r >> 1, qi, qj, c, sweep, colour, ML);
+                                nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, qi, qj, c, sweep, colour, ML);
                             }
                         }
                     } else {
@@ -1033,7 +1029,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                         if (pr < p.n_pairs) {
                             const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
                             const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
-                            nacc += pair_move<R>(p, par, s, own4, oth4, pr, qi, qj, c, sweep, colour, ML);
+                            nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, ML);
                         }
                     }
                 }
@@ -1042,6 +1038,45 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                 if (finalize) finalize_sweep(p, L->st, measure, true);
             });
             tile = t1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Neighbour field h of every site of one colour (the pair pass of that
+// colour reads it for both members of each pair): the other colour's packed
+// spins summed in the order -x, +x, -y, +y, -z, +z, as neighbour_sum4 does,
+// written as (h_x, h_y, h_z, 0).  The other colour does not change during
+// the pass, so the field holds for all of it.  Tiles are dealt to the warps
+// round-robin, so that the warps in flight cover one compact window of the
+// batch and the +-z planes a tile reads are still in L2 when the tiles two
+// planes on read them again (contiguous runs per warp put those reads a
+// large part of the launch apart, and every plane came from DRAM 3 times).
+// ------------------------------------------------------------------------
+template <typename R, int V>
+__global__ void __launch_bounds__(kBlock) pair_field_kernel(GroupArgs g, uint32_t ntiles, int colour) {
+    const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
+    const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31u;
+    const int other = colour ^ 1;
+    if (w >= ntiles) return;
+    int l = lattice_of_tile(g, w);
+    for (uint32_t tile = w; tile < ntiles; tile += nwarps) {
+        while (tile >= __ldg(&g.start[l + 1])) ++l;  // tiles only move forward
+        const LatParams& p = g.lats[l]->p;
+        const Spin4<R>* oth4 = static_cast<const Spin4<R>*>(p.aos) + size_t(other) * p.stride;
+        Spin4<R>* fld = static_cast<Spin4<R>*>(p.pfield);
+        if (!p.aos || !fld) continue;
+        const uint32_t base = (tile - __ldg(&g.start[l])) * uint32_t(32 * V) + lane;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t q = base + uint32_t(32 * v);
+            if (q >= p.Nc) continue;
+            const Geo geo = geometry(p, colour, q);
+            uint32_t nq[6];
+            const uint32_t present = neighbours(p, geo, colour, nq);
+            const V3<R> h = neighbour_sum4(oth4, nq, present);
+            fld[q] = Spin4<R>{h.x, h.y, h.z, R(0)};
         }
     }
 }

@@ -300,12 +300,13 @@ static void per_site_colour_split(const LatParams& p, const void* src, size_t el
 
 const KernelSet& kernel_set(int precision) { return precision == MC_FP64 ? kernels_f64() : kernels_f32(); }
 
-// Bytes of the packed (x, y, z, 0) spin copy that constrained sweeps gather
-// from: one 4-vector per site of each colour.
+// Bytes of what constrained sweeps gather from: the packed (x, y, z, 0)
+// spin copy (a 4-vector per site of each colour) and the neighbour field of
+// the colour being updated (a 4-vector per site).
 size_t aos_bytes(const mc_desc* d) {
     const uint64_t Nc = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2] / 2;
     const uint64_t stride = (Nc + 63) / 64 * 64;
-    return size_t(2 * stride * 4) * (d->precision == MC_FP64 ? 8 : 4);
+    return size_t(3 * stride * 4) * (d->precision == MC_FP64 ? 8 : 4);
 }
 
 // Allocate the packed copy on the lattice's first constrained sweep (the
@@ -318,6 +319,8 @@ int ensure_aos(mc_lattice* h) {
         return cuda_fail(e, "cudaMalloc(packed spin copy)");
     }
     h->hp.aos = h->d_aos;
+    const size_t rs = h->hp.precision == MC_FP64 ? 8 : 4;
+    h->hp.pfield = static_cast<char*>(h->d_aos) + size_t(2) * h->hp.stride * 4 * rs;
     return MC_OK;
 }
 
@@ -595,6 +598,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             k.mlong(ls.all, ls.nt_all, s);
             for (int colour = 0; colour < 2; ++colour) {
                 const int fin = colour == 1 && !measure ? 1 : 0;
+                k.pair_field(ls.all, ls.nt_all, colour, s);
                 timed([&] {
                     if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, fin, 0, 0, s);
                     if (ls.nt_pairs_lead) k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, fin, 0, 1, s);
