@@ -36,7 +36,7 @@ METRIC = "spin-updates/s & HBM roofline frac (128^3 FP32); served m(T) req/s, p5
 UNIT = "spin-updates/s"
 BYTES_PER_UPDATE = 24          # FP32: read + write 3 x 4 B of every spin once per sweep
 FALLBACK_HBM_GBS = 6800.0
-LATSTATE_BYTES = 384           # device state block read back by mc_measure
+LATSTATE_BYTES = 400           # device state block read back by mc_measure
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "row_pass_f32_batched_mT.txt")
 KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/row_pass.cuh", "paper_2103_03517_gb300/csrc/pass_impl.cuh",
                   "paper_2103_03517_gb300/csrc/device_common.cuh", "paper_2103_03517_gb300/csrc/kernels_f32.cu",

@@ -25,6 +25,8 @@ struct KernelSet {
     // Neighbour field of every site of the given colour into LatParams::pfield
     // (site tiles), before that colour's pair pass.
     void (*pair_field)(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s);
+    // Zero M_L and its carried change of every lattice of g (before mlong).
+    void (*ml_reset)(const GroupArgs& g, cudaStream_t s);
     // Exact M_L of every lattice of g (site tiles).
     void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Standalone sample + end of sweep (site tiles).

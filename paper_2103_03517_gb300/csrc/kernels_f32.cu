@@ -114,6 +114,10 @@ void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s)
     pair_field_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
 }
 
+void ml_reset(const GroupArgs& g, cudaStream_t s) {
+    ml_reset_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
+}
+
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     static const uint32_t cap = resident_blocks(mlong_kernel<R, V>);
     mlong_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
@@ -143,7 +147,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, pair_field, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, row_pass, pair_pass, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
                              "f32"};
     return k;
 }

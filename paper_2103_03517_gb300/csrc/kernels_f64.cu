@@ -58,6 +58,10 @@ void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s)
     pair_field_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
 }
 
+void ml_reset(const GroupArgs& g, cudaStream_t s) {
+    ml_reset_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
+}
+
 void mlong(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     static const uint32_t cap = resident_blocks(mlong_kernel<R, V>);
     mlong_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
@@ -87,7 +91,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f64() {
-    static const KernelSet k{colour_pass, nullptr, pair_pass, pair_field, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, nullptr, pair_pass, pair_field, ml_reset, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
                              "f64"};
     return k;
 }

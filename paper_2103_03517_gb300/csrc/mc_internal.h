@@ -109,9 +109,9 @@ struct LatParams {
     int ring_cap;
     long long* profile;     // [3][Lx] fixed-point sums
     void* aos;              // constrained sweeps: [2][stride] (x, y, z, 0) copy of the
-                            // spins (Spin4), written by mlong_kernel at the start of each
-                            // sweep and kept in step by the pair passes; null until the
-                            // lattice's first constrained sweep
+                            // spins (Spin4), written by mlong_kernel at the start of a run
+                            // of constrained sweeps and kept in step by the pair passes;
+                            // null until the lattice's first constrained sweep
     void* pfield;           // constrained sweeps: [stride] (h_x, h_y, h_z, 0) neighbour
                             // field of every site of the colour being updated, written by
                             // pair_field_kernel before each pair pass
@@ -132,6 +132,8 @@ struct LatState {
     long long last_acc;
     long long sums[kNumSums];       // fixed-point lattice sums of this sample
     long long ml_hi, ml_lo;         // exact M_L of this constrained sweep
+    long long dml_hi, dml_lo;       // its change by this sweep's accepted pairs, carried
+                                    // into ml_hi / ml_lo when the sweep ends
     long long ring_count;
     long long prof_samples;
     double moments[kMomentWords];

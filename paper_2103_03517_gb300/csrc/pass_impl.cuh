@@ -428,8 +428,10 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
         if (2 * acc > p.n_mov) { if (st.theta < 180) st.theta += 1; }
         else { if (st.theta > 1) st.theta -= 1; }
     }
-    st.ml_hi = 0;
-    st.ml_lo = 0;
+    st.ml_hi += st.dml_hi;  // M_L of the next sweep (exact: integer sums)
+    st.ml_lo += st.dml_lo;
+    st.dml_hi = 0;
+    st.dml_lo = 0;
     if (measure) {
         double v[kNumSums];
         for (int i = 0; i < kNumSums; ++i) {
@@ -761,9 +763,35 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
 // ------------------------------------------------------------------------
 // Exact M_L = sum_i S_i . e_C (Table A2) as fixed point, order independent:
 // FP64 terms t give q = trunc(t 2^52) split as hi 2^26 + lo; FP32 terms give
-// q = trunc(t 2^30) (an int32).  Site tiles as in the colour pass.  It also
-// writes the packed (x, y, z, 0) copy of both colours that the pair passes
-// of the same sweep gather from.
+// q = trunc(t 2^30) (an int32).  ml_add adds the term of one spin with sign
+// +1 or -1, so that the pair passes can carry M_L from sweep to sweep as
+// the exact sum over the new state; t is one IEEE operation at a time in
+// both precisions (no contraction), the same wherever it is taken.
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R ml_term(const R* e1, V3<R> S) {
+    if constexpr (kIsF64<R>) {
+        return __dadd_rn(__dadd_rn(__dmul_rn(e1[0], S.x), __dmul_rn(e1[1], S.y)), __dmul_rn(e1[2], S.z));
+    } else {
+        return __fadd_rn(__fadd_rn(__fmul_rn(e1[0], S.x), __fmul_rn(e1[1], S.y)), __fmul_rn(e1[2], S.z));
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void ml_add(long long& hi, long long& lo, R t, int sign) {
+    if constexpr (kIsF64<R>) {
+        const long long w = (long long)(t * 0x1p52);
+        const long long hh = w >> 26;
+        hi += sign * hh;
+        lo += sign * (w - hh * (1ll << 26));
+    } else {
+        hi += sign * (long long)__float2int_rz(t * 0x1p30f);
+    }
+}
+
+// M_L of every lattice of g into the zeroed ml_hi / ml_lo, site tiles as in
+// the colour pass; it also writes the packed (x, y, z, 0) copy of both
+// colours that the pair passes gather from and keep in step.
 // ------------------------------------------------------------------------
 template <typename R, int V>
 __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t ntiles) {
@@ -791,15 +819,7 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
                 for (int colour = 0; colour < 2; ++colour) {
                     const V3<R> S = load_spin(s, p.stride, colour, q);
                     if (a4) a4[size_t(colour) * p.stride + q] = Spin4<R>{S.x, S.y, S.z, R(0)};
-                    const R t = e1[0] * S.x + e1[1] * S.y + e1[2] * S.z;
-                    if constexpr (kIsF64<R>) {
-                        const long long w = (long long)(t * 0x1p52);
-                        const long long hh = w >> 26;
-                        hi += hh;
-                        lo += w - hh * (1ll << 26);
-                    } else {
-                        hi += (long long)__float2int_rz(t * 0x1p30f);
-                    }
+                    ml_add<R>(hi, lo, ml_term<R>(e1, S), 1);
                 }
             }
         }
@@ -813,6 +833,19 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
         }
         ++l;
     }
+}
+
+// Zero M_L and its carried change before mlong_kernel sums M_L afresh (one
+// thread per lattice).
+template <typename R>
+__global__ void ml_reset_kernel(GroupArgs g) {
+    const int l = int(blockIdx.x * blockDim.x + threadIdx.x);
+    if (l >= g.n) return;
+    LatState& st = g.lats[l]->st;
+    st.ml_hi = 0;
+    st.ml_lo = 0;
+    st.dml_hi = 0;
+    st.dml_lo = 0;
 }
 
 // ShuffleRedBlackSpins (Sec. 2, Table A2) as a keyed bijection: 4-round
@@ -900,8 +933,11 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // indices; the cone move is made on i in the frame whose x-axis is e_C, j
 // compensates the transverse components, x'_j = sign(x_j) sqrt(|S_j|^2 -
 // y'_j^2 - z'_j^2).  The pair is accepted iff
-// P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is the exact value
-// from mlong_kernel, fixed for the whole iteration.  Rejected without a
+// P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is the exact sum
+// over the state at the start of the sweep, fixed for the whole iteration
+// (mlong_kernel sums it at the start of a run of sweeps; after that every
+// accepted pair adds the exact change of its two terms, carried into M_L
+// when the sweep ends).  Rejected without a
 // test: 16 failed disk draws, t <= 0, M'_L <= 0.  Spins are gathered from the
 // packed copy (one sector per site instead of one per component); accepted
 // moves are written to the spins and to the copy of the pass's colour.
@@ -914,7 +950,8 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 template <typename R>
 __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
                                               Spin4<R>* own4, const Spin4<R>* fld, uint32_t pr, uint32_t qi,
-                                              uint32_t qj, R c, uint32_t sweep, int colour, double ML) {
+                                              uint32_t qj, R c, uint32_t sweep, int colour, double ML,
+                                              long long& dhi, long long& dlo) {
     const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
     const Spin4<R> fi4 = fld[qi], fj4 = fld[qj];
     const V3<R> h_i{fi4.x, fi4.y, fi4.z};
@@ -963,6 +1000,10 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     store_spin(s, p.stride, colour, qj, Snj);
     own4[qi] = Spin4<R>{Sni.x, Sni.y, Sni.z, R(0)};
     own4[qj] = Spin4<R>{Snj.x, Snj.y, Snj.z, R(0)};
+    ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Sni), 1);  // M_L of the next sweep
+    ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Snj), 1);
+    ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Si), -1);
+    ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Sj), -1);
     return 2;
 }
 
@@ -989,6 +1030,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
             const double ML = mlong_value<R>(L->st.ml_hi, L->st.ml_lo);
             Spin4<R>* a4 = static_cast<Spin4<R>*>(p.aos);
             unsigned nacc = 0;
+            long long dhi = 0, dlo = 0;
             if (!(ML > 0.0)) {
                 if (lane == 0) atomicCAS(&L->st.error, 0, -5);
             } else if (!a4) {
@@ -1021,7 +1063,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                                 const uint32_t r = second ? r_b : r_a;
                                 const uint32_t qi = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
                                 const uint32_t qj = permute(r + 1u, p.Nc, p.perm_h, rk);
-                                nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, qi, qj, c, sweep, colour, ML);
+                                nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, qi, qj, c, sweep, colour, ML,
+                                                     dhi, dlo);
                             }
                         }
                     } else {
@@ -1029,10 +1072,20 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                         if (pr < p.n_pairs) {
                             const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
                             const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
-                            nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, ML);
+                            nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, ML, dhi, dlo);
                         }
                     }
                 }
+            }
+            // the change of M_L, before publish's fence (the sweep's last
+            // warp carries it into M_L)
+            for (int o = 16; o > 0; o >>= 1) {
+                dhi += __shfl_xor_sync(0xffffffffu, dhi, o);
+                dlo += __shfl_xor_sync(0xffffffffu, dlo, o);
+            }
+            if (lane == 0) {
+                if (dhi) atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.dml_hi), (unsigned long long)dhi);
+                if (dlo) atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.dml_lo), (unsigned long long)dlo);
             }
             publish(L->st, lane, nacc, false, 0, colour, t1 - tile, p.nblocks_pair, [&] {
                 if (finalize) finalize_sweep(p, L->st, measure, true);

@@ -595,7 +595,10 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             timed([&] { colour_pass(0, 0); });
             timed([&] { colour_pass(1, measure ? ls.sample_level : 0); });
         } else {
-            k.mlong(ls.all, ls.nt_all, s);
+            if (i == 0) {  // M_L and the packed copy afresh; later sweeps carry both
+                k.ml_reset(ls.all, s);
+                k.mlong(ls.all, ls.nt_all, s);
+            }
             for (int colour = 0; colour < 2; ++colour) {
                 const int fin = colour == 1 && !measure ? 1 : 0;
                 k.pair_field(ls.all, ls.nt_all, colour, s);
@@ -929,7 +932,7 @@ MC_API int mc_get_theta(mc_handle h, int* theta_deg, int64_t* sweeps_done) {
 }
 
 // ------------------------------------------------------------- checkpoint
-static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '2'};
+static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '3'};
 
 MC_API int mc_save(mc_handle h, const char* path) {
     if (!h || !path) return fail(MC_ERR_ARG, "null argument");
