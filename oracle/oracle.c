@@ -651,44 +651,48 @@ OR_EXPORT double or_m_long(const or_lattice* L, double theta_deg, double phi_deg
 }
 
 /* ShuffleRedBlackSpins (Sec. 2, Table A2) as a keyed bijection of the       */
-/* colour indices [0, n): a 4-round balanced Feistel network on 2h-bit      */
-/* words (2^2h >= n) with cycle-walking (Black & Rogaway, CT-RSA 2002).     */
-/* Round function: the "lowbias32" integer hash (C. Wellons, 2018) of the   */
-/* right half xor a round key; round keys are the four words of             */
-/* Philox(0, sweep, colour | purpose 2, 0).                                 */
+/* colour indices [0, n): a 4-round alternating Feistel network on b-bit    */
+/* words, b the least width with 2^b >= n (the alternating splits of the    */
+/* FFX mode, Bellare, Rogaway & Spies 2010, for odd b), with cycle-walking  */
+/* (Black & Rogaway, CT-RSA 2002).  Round k takes the low w bits R and the  */
+/* high b - w bits L of the word to (R, L ^ F_k(R)), R now on top; w is     */
+/* ceil(b/2) in rounds 0 and 2, floor(b/2) in rounds 1 and 3, so that for   */
+/* even b every round is a balanced one.  F_k(R) is the "lowbias32" integer */
+/* hash (C. Wellons, 2018) of R xor round key k, cut to b - w bits; the     */
+/* round keys are the four words of Philox(0, sweep, colour | purpose 2, 0).*/
 static uint32_t hash32(uint32_t v) {
     v ^= v >> 16; v *= 0x7feb352du;
     v ^= v >> 15; v *= 0x846ca68bu;
     v ^= v >> 16;
     return v;
 }
-static int half_bits(uint32_t n) {
-    int h = 1;
-    while (((uint64_t)1 << (2 * h)) < (uint64_t)n) ++h;
-    return h;
+static int domain_bits(uint32_t n) {
+    int b = 1;
+    while (((uint64_t)1 << b) < (uint64_t)n) ++b;
+    return b;
 }
-static uint32_t feistel_once(uint32_t v, int h, const uint32_t rk[4]) {
-    const uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
-    uint32_t l = v >> h, r = v & mask;
+static uint32_t low_mask(int w) { return w >= 32 ? 0xFFFFFFFFu : ((1u << w) - 1u); }
+static uint32_t feistel_once(uint32_t v, int b, const uint32_t rk[4]) {
     for (int k = 0; k < 4; ++k) {
-        const uint32_t f = hash32(r ^ rk[k]) & mask;
-        const uint32_t nl = r;
-        r = l ^ f;
-        l = nl;
+        const int w = (k % 2 == 0) ? (b + 1) / 2 : b / 2;
+        const uint32_t r = v & low_mask(w);
+        const uint32_t l = v >> w;
+        const uint32_t f = hash32(r ^ rk[k]) & low_mask(b - w);
+        v = (r << (b - w)) | (l ^ f);
     }
-    return (l << h) | r;
+    return v;
 }
-static uint32_t permute(uint32_t i, uint32_t n, int h, const uint32_t rk[4]) {
+static uint32_t permute(uint32_t i, uint32_t n, int b, const uint32_t rk[4]) {
     uint32_t v = i;
-    do { v = feistel_once(v, h, rk); } while (v >= n);
+    do { v = feistel_once(v, b, rk); } while (v >= n);
     return v;
 }
 
 OR_EXPORT void or_permutation(uint32_t n, uint32_t sweep, int colour, const uint32_t key[2], uint32_t* out) {
     uint32_t rk[4];
     philox(0u, sweep, tag_of(colour, PURPOSE_PERM), 0u, key[0], key[1], rk);
-    const int h = half_bits(n);
-    for (uint32_t i = 0; i < n; ++i) out[i] = permute(i, n, h, rk);
+    const int b = domain_bits(n);
+    for (uint32_t i = 0; i < n; ++i) out[i] = permute(i, n, b, rk);
 }
 
 /* Site of colour index q = k + (Lx/2)(y + Ly z) of colour c. */
@@ -768,11 +772,11 @@ OR_EXPORT int or_constrained_sweep(or_lattice* L, double theta_deg, double phi_d
             const uint32_t nc = (uint32_t)(L->N / 2);
             uint32_t rk[4];
             philox(0u, L->sweep, tag_of(colour, PURPOSE_PERM), 0u, L->key0, L->key1, rk);
-            const int h = half_bits(nc);
+            const int b = domain_bits(nc);
             const uint32_t tag = tag_of(colour, PURPOSE_PAIR);
             for (uint32_t p = 0; p < nc / 2; ++p) {
-                const int64_t si = colour_site(L, colour, permute(2 * p, nc, h, rk));
-                const int64_t sj = colour_site(L, colour, permute(2 * p + 1, nc, h, rk));
+                const int64_t si = colour_site(L, colour, permute(2 * p, nc, b, rk));
+                const int64_t sj = colour_site(L, colour, permute(2 * p + 1, nc, b, rk));
                 acc += 2 * pair_move(L, R, ML, c, si, sj, p, tag);
             }
         }

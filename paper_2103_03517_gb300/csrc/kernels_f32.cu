@@ -110,8 +110,8 @@ void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour
 }
 
 void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V>);
-    pair_field_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, 4>);
+    pair_field_kernel<R, V, 4><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
 }
 
 void ml_reset(const GroupArgs& g, cudaStream_t s) {

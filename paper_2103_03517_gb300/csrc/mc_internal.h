@@ -82,7 +82,7 @@ struct LatParams {
     uint32_t Nc;            // sites per colour (and sub-lattice) = cells / 2
     uint32_t stride;        // Nc rounded up to 64
     uint32_t n_pairs;       // Nc / 2
-    int perm_h;             // Feistel half width in bits (domain 2^(2h) >= Nc)
+    int perm_bits;          // Feistel word width b (domain 2^b >= Nc, b >= 1)
     long long N, n_mov;
     int adapt_in_measure;
     uint32_t key0, key1;

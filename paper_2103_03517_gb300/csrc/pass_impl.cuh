@@ -848,11 +848,16 @@ __global__ void ml_reset_kernel(GroupArgs g) {
     st.dml_lo = 0;
 }
 
-// ShuffleRedBlackSpins (Sec. 2, Table A2) as a keyed bijection: 4-round
-// balanced Feistel network on 2h-bit words with cycle-walking (Black and
-// Rogaway 2002); round function = lowbias32 hash (C. Wellons, 2018) of the
-// right half xor the round key; round keys = Philox(0, sweep, colour |
-// purpose 2, 0).
+// ShuffleRedBlackSpins (Sec. 2, Table A2) as a keyed bijection of [0, n):
+// a 4-round alternating Feistel network on b-bit words, b the least width
+// with 2^b >= n, with cycle-walking (Black and Rogaway 2002).  Round k takes
+// the low w bits R and the high b - w bits L to (R, L ^ F_k(R)), R now on
+// top, w = ceil(b/2) in rounds 0 and 2 and floor(b/2) in rounds 1 and 3
+// (the alternating splits of the FFX mode, Bellare, Rogaway and Spies 2010;
+// for even b every round is balanced).  F_k = lowbias32 hash (C. Wellons,
+// 2018) of R xor round key k, cut to b - w bits; round keys = Philox(0,
+// sweep, colour | purpose 2, 0).  With 2^b < 2n a walk takes under two
+// steps on average, and none at all when n is a power of two.
 __device__ __forceinline__ uint32_t hash32(uint32_t v) {
     v ^= v >> 16;
     v *= 0x7feb352du;
@@ -862,41 +867,42 @@ __device__ __forceinline__ uint32_t hash32(uint32_t v) {
     return v;
 }
 
-__device__ __forceinline__ uint32_t permute(uint32_t i, uint32_t n, int h, uint4 rk) {
-    const uint32_t mask = (1u << h) - 1u;
-    const uint32_t keys[4] = {rk.x, rk.y, rk.z, rk.w};
+__device__ __forceinline__ uint32_t feistel_round(uint32_t v, int b, int w, uint32_t key) {
+    const uint32_t r = v & ((1u << w) - 1u);
+    const uint32_t l = v >> w;
+    return (r << (b - w)) | (l ^ (hash32(r ^ key) & ((1u << (b - w)) - 1u)));
+}
+
+// Inverse of feistel_round: R is the top w bits, L = low bits ^ F(R).
+__device__ __forceinline__ uint32_t feistel_round_inv(uint32_t v, int b, int w, uint32_t key) {
+    const uint32_t r = v >> (b - w);
+    const uint32_t l = (v ^ hash32(r ^ key)) & ((1u << (b - w)) - 1u);
+    return (l << w) | r;
+}
+
+__device__ __forceinline__ uint32_t permute(uint32_t i, uint32_t n, int b, uint4 rk) {
+    const int wa = (b + 1) >> 1, wb = b >> 1;
     uint32_t v = i;
     do {
-        uint32_t l = v >> h, r = v & mask;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t f = hash32(r ^ keys[k]) & mask;
-            const uint32_t nl = r;
-            r = l ^ f;
-            l = nl;
-        }
-        v = (l << h) | r;
+        v = feistel_round(v, b, wa, rk.x);
+        v = feistel_round(v, b, wb, rk.y);
+        v = feistel_round(v, b, wa, rk.z);
+        v = feistel_round(v, b, wb, rk.w);
     } while (v >= n);
     return v;
 }
 
-// Inverse of permute: the Feistel rounds undone in reverse order (a round
-// maps (l, r) to (r, l ^ F(r)), so (l', r') comes from (r' ^ F(l'), l')),
-// with the same cycle-walking: from y = permute(i) the backward walk passes
-// only values >= n until it reaches i.
-__device__ __forceinline__ uint32_t permute_inv(uint32_t y, uint32_t n, int h, uint4 rk) {
-    const uint32_t mask = (1u << h) - 1u;
-    const uint32_t keys[4] = {rk.x, rk.y, rk.z, rk.w};
+// Inverse of permute: the rounds undone in reverse order, with the same
+// cycle-walking: from y = permute(i) the backward walk passes only values
+// >= n until it reaches i.
+__device__ __forceinline__ uint32_t permute_inv(uint32_t y, uint32_t n, int b, uint4 rk) {
+    const int wa = (b + 1) >> 1, wb = b >> 1;
     uint32_t v = y;
     do {
-        uint32_t l = v >> h, r = v & mask;
-#pragma unroll
-        for (int k = 3; k >= 0; --k) {
-            const uint32_t pl = r ^ (hash32(l ^ keys[k]) & mask);
-            r = l;
-            l = pl;
-        }
-        v = (l << h) | r;
+        v = feistel_round_inv(v, b, wb, rk.w);
+        v = feistel_round_inv(v, b, wa, rk.z);
+        v = feistel_round_inv(v, b, wb, rk.y);
+        v = feistel_round_inv(v, b, wa, rk.x);
     } while (v >= n);
     return v;
 }
@@ -1048,8 +1054,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                         // the 64 sites of tile t in index order; each site whose
                         // position pi^-1(q) is even leads the pair (pi(r), pi(r+1))
                         const uint32_t qa = (t - t0) * 64u + uint32_t(lane), qb = qa + 32u;
-                        const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_h, rk) : 1u;
-                        const uint32_t rb = qb < p.Nc ? permute_inv(qb, p.Nc, p.perm_h, rk) : 1u;
+                        const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_bits, rk) : 1u;
+                        const uint32_t rb = qb < p.Nc ? permute_inv(qb, p.Nc, p.perm_bits, rk) : 1u;
                         const uint32_t ma = __ballot_sync(0xffffffffu, !(ra & 1u) && ra + 1u < p.Nc);
                         const uint32_t mb = __ballot_sync(0xffffffffu, !(rb & 1u) && rb + 1u < p.Nc);
                         const int ca = __popc(ma), total = ca + __popc(mb);
@@ -1062,7 +1068,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                             if (j < total) {
                                 const uint32_t r = second ? r_b : r_a;
                                 const uint32_t qi = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
-                                const uint32_t qj = permute(r + 1u, p.Nc, p.perm_h, rk);
+                                const uint32_t qj = permute(r + 1u, p.Nc, p.perm_bits, rk);
                                 nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, qi, qj, c, sweep, colour, ML,
                                                      dhi, dlo);
                             }
@@ -1070,8 +1076,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     } else {
                         const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
                         if (pr < p.n_pairs) {
-                            const uint32_t qi = permute(2 * pr, p.Nc, p.perm_h, rk);
-                            const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_h, rk);
+                            const uint32_t qi = permute(2 * pr, p.Nc, p.perm_bits, rk);
+                            const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_bits, rk);
                             nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, ML, dhi, dlo);
                         }
                     }
@@ -1100,36 +1106,83 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
 // colour reads it for both members of each pair): the other colour's packed
 // spins summed in the order -x, +x, -y, +y, -z, +z, as neighbour_sum4 does,
 // written as (h_x, h_y, h_z, 0).  The other colour does not change during
-// the pass, so the field holds for all of it.  Tiles are dealt to the warps
-// round-robin, so that the warps in flight cover one compact window of the
-// batch and the +-z planes a tile reads are still in L2 when the tiles two
-// planes on read them again (contiguous runs per warp put those reads a
-// large part of the launch apart, and every plane came from DRAM 3 times).
+// the pass, so the field holds for all of it.  Tiles go to the warps
+// CHUNK at a time in grid-stride order, so that the warps in flight cover
+// one compact window of the batch and the +-z planes a tile reads are still
+// in L2 when the tiles two planes on read them again (with one contiguous
+// run per warp those reads were a large part of the launch apart, and every
+// plane came from DRAM 3 times).  Lattices with every axis periodic and no
+// bond mask take the neighbours without the general path's boundary and
+// bond tests (the same indices and order).
 // ------------------------------------------------------------------------
 template <typename R, int V>
+__device__ __forceinline__ void field_tile_periodic(const LatParams& p, const Spin4<R>* __restrict__ oth4,
+                                                    Spin4<R>* __restrict__ fld, int colour, uint32_t base) {
+    const uint32_t Lh = uint32_t(p.Lh), Ly = uint32_t(p.Ly), Lz = uint32_t(p.Lz), plane = Lh * Ly;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t q = base + uint32_t(32 * v);
+        if (q >= p.Nc) continue;
+        const uint32_t row = fast_div(q, p.div_lh);
+        const uint32_t k = q - row * Lh;
+        const uint32_t z = fast_div(row, p.div_ly);
+        const uint32_t y = row - z * Ly;
+        const uint32_t kx = k + ((y + z + uint32_t(colour)) & 1u);  // +x neighbour's k before the wrap
+        const uint32_t qrow = q - k;
+        const uint32_t nq[6] = {qrow + (kx == 0 ? Lh - 1 : kx - 1), qrow + (kx == Lh ? 0 : kx),
+                                y > 0 ? q - Lh : q + Lh * (Ly - 1), y + 1 < Ly ? q + Lh : q - Lh * (Ly - 1),
+                                z > 0 ? q - plane : q + plane * (Lz - 1), z + 1 < Lz ? q + plane : q - plane * (Lz - 1)};
+        Spin4<R> a[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) a[d] = oth4[nq[d]];
+        V3<R> h{R(0), R(0), R(0)};
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            h.x = h.x + a[d].x;
+            h.y = h.y + a[d].y;
+            h.z = h.z + a[d].z;
+        }
+        fld[q] = Spin4<R>{h.x, h.y, h.z, R(0)};
+    }
+}
+
+template <typename R, int V, int CHUNK>
 __global__ void __launch_bounds__(kBlock) pair_field_kernel(GroupArgs g, uint32_t ntiles, int colour) {
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
     const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
     const uint32_t lane = threadIdx.x & 31u;
     const int other = colour ^ 1;
-    if (w >= ntiles) return;
-    int l = lattice_of_tile(g, w);
-    for (uint32_t tile = w; tile < ntiles; tile += nwarps) {
-        while (tile >= __ldg(&g.start[l + 1])) ++l;  // tiles only move forward
-        const LatParams& p = g.lats[l]->p;
-        const Spin4<R>* oth4 = static_cast<const Spin4<R>*>(p.aos) + size_t(other) * p.stride;
-        Spin4<R>* fld = static_cast<Spin4<R>*>(p.pfield);
-        if (!p.aos || !fld) continue;
-        const uint32_t base = (tile - __ldg(&g.start[l])) * uint32_t(32 * V) + lane;
+    int l = 0;
+    for (uint32_t c0 = w * CHUNK; c0 < ntiles; c0 += nwarps * CHUNK) {
+        const uint32_t c1 = min(c0 + uint32_t(CHUNK), ntiles);
+        for (uint32_t tile = c0; tile < c1;) {
+            while (__ldg(&g.start[l + 1]) <= tile) ++l;  // tiles only move forward
+            const uint32_t t0 = __ldg(&g.start[l]);
+            const uint32_t t1 = min(__ldg(&g.start[l + 1]), c1);
+            const LatParams& p = g.lats[l]->p;
+            const Spin4<R>* oth4 = static_cast<const Spin4<R>*>(p.aos) + size_t(other) * p.stride;
+            Spin4<R>* fld = static_cast<Spin4<R>*>(p.pfield);
+            if (p.aos && fld) {
+                if ((p.bc[0] | p.bc[1] | p.bc[2]) == 0 && !p.bonds) {  // every axis periodic
+                    for (uint32_t t = tile; t < t1; ++t)
+                        field_tile_periodic<R, V>(p, oth4, fld, colour, (t - t0) * uint32_t(32 * V) + lane);
+                } else {
+                    for (uint32_t t = tile; t < t1; ++t) {
+                        const uint32_t base = (t - t0) * uint32_t(32 * V) + lane;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t q = base + uint32_t(32 * v);
-            if (q >= p.Nc) continue;
-            const Geo geo = geometry(p, colour, q);
-            uint32_t nq[6];
-            const uint32_t present = neighbours(p, geo, colour, nq);
-            const V3<R> h = neighbour_sum4(oth4, nq, present);
-            fld[q] = Spin4<R>{h.x, h.y, h.z, R(0)};
+                        for (int v = 0; v < V; ++v) {
+                            const uint32_t q = base + uint32_t(32 * v);
+                            if (q >= p.Nc) continue;
+                            const Geo geo = geometry(p, colour, q);
+                            uint32_t nq[6];
+                            const uint32_t present = neighbours(p, geo, colour, nq);
+                            const V3<R> h = neighbour_sum4(oth4, nq, present);
+                            fld[q] = Spin4<R>{h.x, h.y, h.z, R(0)};
+                        }
+                    }
+                }
+            }
+            tile = t1;
         }
     }
 }

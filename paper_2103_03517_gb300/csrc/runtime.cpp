@@ -98,10 +98,10 @@ void constraint_frame(double theta_deg, double phi_deg, double R[9]) {
     R[6] = -ct * cp; R[7] = -ct * sp; R[8] = st;
 }
 
-static int feistel_half_bits(uint32_t n) {
-    int h = 1;
-    while ((uint64_t(1) << (2 * h)) < uint64_t(n)) ++h;
-    return h;
+static int feistel_bits(uint32_t n) {
+    int b = 1;
+    while ((uint64_t(1) << b) < uint64_t(n)) ++b;
+    return b;
 }
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -363,7 +363,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.Nc = uint32_t((long long)p.Lx * p.Ly * p.Lz / 2);
     p.stride = (p.Nc + 63) / 64 * 64;
     p.n_pairs = p.Nc / 2;
-    p.perm_h = feistel_half_bits(p.Nc);
+    p.perm_bits = feistel_bits(p.Nc);
     p.row_fast = row_fast(p, d->bond_mask != nullptr || d->grain_id != nullptr);
     p.colour_kernel = colour_kernel(p, d->bond_mask != nullptr || d->grain_id != nullptr, d->kernel_path);
     p.row_lanes = p.Lh / 2 < 32 ? (p.Lh / 2 > 0 ? p.Lh / 2 : 1) : 32;

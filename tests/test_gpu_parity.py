@@ -569,21 +569,30 @@ def test_fp32_langevin_law(H, T):
 
 
 def test_fp32_constrained_torque_matches_oracle():
+    """FP32 constrained torque tau_y against the oracle's FP64 chain: six
+    independent runs on each side; the difference of the mean run means lies
+    within the two-sided 99.9% Student-t bound (10 degrees of freedom) of the
+    pooled spread between runs.  One run's blocking error understates the
+    run-to-run spread of this 3000-sample series about twice, so the spread
+    is taken between runs."""
     dims, T, th = (16, 16, 16), 0.5, 45.0
-    n_eq, n_meas = 500, 3000
+    n_eq, n_meas, runs = 500, 3000, 6
     R = oracle.constraint_frame(th, 0.0)
-    h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, T=T, seed=3, init_dir=tuple(R[0]),
-                                     ring_capacity=n_meas))
-    try:
-        mc.mc_constrained_sweep(h, th, 0.0, n_eq)
-        mc.mc_constrained_sweep(h, th, 0.0, n_meas, measure=True)
-        g = mc.mc_samples(h, n_meas)
-    finally:
-        mc.mc_destroy(h)
-    r = _oracle_series(dims, 0.05, T, 4, n_eq, n_meas, constrained=(th, 0.0), Kc=0.02)
-    gt, rt = g["torque"][:, 1], r[:, 11]
-    sig = math.hypot(blocking_error(gt), blocking_error(rt))
-    assert abs(gt.mean() - rt.mean()) <= 3.5 * sig + 1e-6, (gt.mean(), rt.mean(), sig)
+    gm, rm = [], []
+    for k in range(runs):
+        h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, K_c=0.02, T=T, seed=1 + k, init_dir=tuple(R[0]),
+                                         ring_capacity=n_meas))
+        try:
+            mc.mc_constrained_sweep(h, th, 0.0, n_eq)
+            mc.mc_constrained_sweep(h, th, 0.0, n_meas, measure=True)
+            gm.append(mc.mc_samples(h, n_meas)["torque"][:, 1].mean())
+        finally:
+            mc.mc_destroy(h)
+        rm.append(_oracle_series(dims, 0.05, T, 101 + k, n_eq, n_meas, constrained=(th, 0.0), Kc=0.02)[:, 11].mean())
+    gm, rm = np.array(gm), np.array(rm)
+    pooled = math.sqrt((gm.var(ddof=1) + rm.var(ddof=1)) / 2)
+    sig = pooled * math.sqrt(2.0 / runs)
+    assert abs(gm.mean() - rm.mean()) <= 4.59 * sig, (gm.mean(), rm.mean(), sig)
 
 
 def test_fp32_constrained_site_order_equals_pair_order():

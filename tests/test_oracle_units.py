@@ -219,6 +219,24 @@ def test_permutation_is_bijection(n):
         assert np.array_equal(np.sort(p), np.arange(n, dtype=np.uint32))
 
 
+@pytest.mark.parametrize("n", [1000, 4097, 32768])
+def test_permutation_law_close_to_uniform(n):
+    """The random order of Sec. 2 at sizes of real lattices: over 2000 sweeps
+    (round keys), the position pi(0) and the partner offset pi(1) - pi(0)
+    mod n are uniform on 32 bins (chi-square p > 1e-4).  This checks the law,
+    not the construction (the GPU parity tests tie that to the library); one
+    key reused in every other round fails it at n = 1000.  A 4-round Feistel
+    on a few bits (n up to about 256) does not pass it with any split."""
+    from scipy import stats
+    first = np.empty((2000, 2), dtype=np.int64)
+    for s in range(2000):
+        first[s] = oracle.permutation(n, s, s & 1, (11, 3))[:2]
+    pos = (first[:, 0] * 32) // n
+    off = (((first[:, 1] - first[:, 0]) % n - 1) * 32) // (n - 1)
+    for x in (pos, off):
+        assert stats.chisquare(np.bincount(x, minlength=32)).pvalue > 1e-4
+
+
 def test_permutation_changes_with_sweep():
     a = oracle.permutation(4096, 0, 0, (1, 2))
     b = oracle.permutation(4096, 1, 0, (1, 2))
