@@ -67,8 +67,8 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
 /* Kernels of an FP32 lattice.  AUTO takes a row kernel for the colour
  * passes where the row layout applies (Lh = Lx/2 a power of two <= 64 or a
  * multiple of 64, Nc a multiple of 64) and the general kernel otherwise,
- * and walks the constrained pairs in site order when the lattice's spins
- * and their packed copy exceed 64 MB.  GENERAL always takes the general
+ * and walks the constrained pairs in site order (each pair led by the
+ * member whose shuffled position is even).  GENERAL always takes the general
  * colour-pass kernel and the pairs in pair order.  The colour passes agree
  * up to FP32 rounding (the draws are keyed to the same sites) and the two
  * pair orders exactly; GENERAL exists to compare them.  FP64 lattices

@@ -18,10 +18,12 @@ struct KernelSet {
     // boundaries and film tables.  Null in the FP64 set.
     void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
                      cudaStream_t s);
-    // Table A2 pair pass; finalize != 0 closes the sweep in the last warp;
-    // leader != 0 takes the pairs in site order (LatParams::pair_leader).
-    void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize,
-                      int measure, int leader, cudaStream_t s);
+    // Table A2 pair pass; leader != 0 takes the pairs in site order
+    // (LatParams::pair_leader).
+    void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader,
+                      cudaStream_t s);
+    // End of an unmeasured constrained sweep of every lattice of g.
+    void (*sweep_end)(const GroupArgs& g, cudaStream_t s);
     // Neighbour field of every site of the given colour into LatParams::pfield
     // (site tiles), before that colour's pair pass.
     void (*pair_field)(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s);

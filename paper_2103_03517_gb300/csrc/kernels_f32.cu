@@ -95,18 +95,20 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
 }
 
 template <bool LEADER>
-void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
-                 cudaStream_t s) {
+void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, cudaStream_t s) {
     constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
     static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, kPairChunk, LEADER>);
     pair_pass_kernel<R, B, kPairChunk, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
-        g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
+        g, ntiles, static_cast<const R*>(cone), colour);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
-               int leader, cudaStream_t s) {
-    if (leader) pair_pass_t<true>(g, ntiles, cone, colour, finalize, measure, s);
-    else pair_pass_t<false>(g, ntiles, cone, colour, finalize, measure, s);
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, cudaStream_t s) {
+    if (leader) pair_pass_t<true>(g, ntiles, cone, colour, s);
+    else pair_pass_t<false>(g, ntiles, cone, colour, s);
+}
+
+void sweep_end(const GroupArgs& g, cudaStream_t s) {
+    sweep_end_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
 }
 
 void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
@@ -147,7 +149,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, row_pass, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
                              "f32"};
     return k;
 }

@@ -45,12 +45,15 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int finalize, int measure,
-               int leader, cudaStream_t s) {
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, cudaStream_t s) {
     (void)leader;  // FP64 lattices always take pair order (LatParams::pair_leader)
     static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, kPairChunk, false>);
     pair_pass_kernel<R, 1, kPairChunk, false><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
-        g, ntiles, static_cast<const R*>(cone), colour, finalize, measure);
+        g, ntiles, static_cast<const R*>(cone), colour);
+}
+
+void sweep_end(const GroupArgs& g, cudaStream_t s) {
+    sweep_end_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
 }
 
 void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
@@ -91,7 +94,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f64() {
-    static const KernelSet k{colour_pass, nullptr, pair_pass, pair_field, ml_reset, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, nullptr, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, nullptr, xtal_pass, xtal_sample, profile,
                              "f64"};
     return k;
 }

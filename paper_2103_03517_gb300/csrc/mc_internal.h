@@ -95,7 +95,7 @@ struct LatParams {
                             // multiple of 64, Nc % 64 == 0: the row paths apply
     int row_lanes;          // FP32 row path: lanes per row group, min(Lh/2, 32)
     int nsub;               // sub-lattices: 1 simple cubic, 2 bcc, 4 fcc
-    int pair_leader;        // constrained pass in site order (FP32 lattices too big for L2)
+    int pair_leader;        // constrained pass in site order (FP32, automatic kernel path)
     int xnb_n[kXtalMaxSub]; // bcc / fcc: neighbour entries per sub-lattice
     const void* xnb;        // bcc / fcc: [kXtalMaxSub][kXtalMaxNb] XtalNb, or null
     int colour_kernel;      // colour-pass kernel: kColourGeneral, kColourRow (FP32 row

@@ -835,6 +835,16 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
     }
 }
 
+// End of an unmeasured constrained sweep, after its last pair pass (one
+// thread per lattice): cone adaptation, M_L carried, the sweep counter.
+template <typename R>
+__global__ void sweep_end_kernel(GroupArgs g) {
+    const int l = int(blockIdx.x * blockDim.x + threadIdx.x);
+    if (l >= g.n) return;
+    LatDev* L = g.lats[l];
+    finalize_sweep(L->p, L->st, 0, true);
+}
+
 // Zero M_L and its carried change before mlong_kernel sums M_L afresh (one
 // thread per lattice).
 template <typename R>
@@ -1016,11 +1026,11 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
 // Tiles are taken in grid-stride order, CHUNK consecutive tiles per step: at
 // any moment the warps hold a window of about CHUNK tiles each, a few
 // lattices of the batch, so that the random gathers of partners and their
-// neighbours stay in L2.  A warp publishes once per lattice in a chunk.
+// neighbours stay in L2.  A warp adds its accepted moves and M_L change
+// once per lattice in a chunk.
 template <typename R, int MINB, int CHUNK, bool LEADER>
 __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
-                                                                 const R* __restrict__ cone, int colour, int finalize,
-                                                                 int measure) {
+                                                                 const R* __restrict__ cone, int colour) {
     const int lane = int(threadIdx.x & 31);
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
     const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
@@ -1083,19 +1093,19 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     }
                 }
             }
-            // the change of M_L, before publish's fence (the sweep's last
-            // warp carries it into M_L)
+            // accepted moves and the change of M_L of this run of tiles; the
+            // sweep is closed by a later launch (sweep_end_kernel or the
+            // sample), so no warp waits on a fence for its scattered stores
+            nacc = __reduce_add_sync(0xffffffffu, nacc);
             for (int o = 16; o > 0; o >>= 1) {
                 dhi += __shfl_xor_sync(0xffffffffu, dhi, o);
                 dlo += __shfl_xor_sync(0xffffffffu, dlo, o);
             }
             if (lane == 0) {
+                if (nacc) atomicAdd(&L->st.acc, (unsigned long long)nacc);
                 if (dhi) atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.dml_hi), (unsigned long long)dhi);
                 if (dlo) atomicAdd(reinterpret_cast<unsigned long long*>(&L->st.dml_lo), (unsigned long long)dlo);
             }
-            publish(L->st, lane, nacc, false, 0, colour, t1 - tile, p.nblocks_pair, [&] {
-                if (finalize) finalize_sweep(p, L->st, measure, true);
-            });
             tile = t1;
         }
     }

@@ -388,11 +388,10 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.nblocks_site = (p.Nc + site_tile - 1) / site_tile;
     p.nblocks_pair = (p.Nc + 63) / 64;  // pair tiles: 32 pairs, or 64 sites in site order
     if (p.nblocks_pair == 0) p.nblocks_pair = 1;
-    // constrained passes of lattices whose spins and packed copy (28 B a site
-    // in FP32) exceed half of L2 take the pairs in site order: the random
-    // gathers then miss DRAM for the partner side only
-    p.pair_leader =
-        d->kernel_path == MC_PATH_AUTO && p.precision == MC_FP32 && double(p.N) * 28.0 > 64.0 * 1024 * 1024 ? 1 : 0;
+    // FP32 constrained passes take the pairs in site order: the leader side
+    // is then read in index order and only the partner side is a random
+    // gather (MC_PATH_GENERAL keeps pair order; both give the same pairs)
+    p.pair_leader = d->kernel_path == MC_PATH_AUTO && p.precision == MC_FP32 ? 1 : 0;
     p.J = p.nsub > 1 ? 1.0 : d->J;  // bcc / fcc: the couplings sit in the neighbour table
     p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
@@ -600,13 +599,13 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
                 k.mlong(ls.all, ls.nt_all, s);
             }
             for (int colour = 0; colour < 2; ++colour) {
-                const int fin = colour == 1 && !measure ? 1 : 0;
                 k.pair_field(ls.all, ls.nt_all, colour, s);
                 timed([&] {
-                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, fin, 0, 0, s);
-                    if (ls.nt_pairs_lead) k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, fin, 0, 1, s);
+                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, s);
+                    if (ls.nt_pairs_lead) k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, s);
                 });
             }
+            if (!measure) k.sweep_end(ls.all, s);  // a measured sweep ends in its sample
             if (measure) {
                 if (k.row_sample) {  // row-layout lattices sample in the row kernels
                     if (ls.nt_row) k.row_sample(ls.row, ls.nt_row, 0, s);
