@@ -13,6 +13,9 @@
 #ifndef MC_PAIR_CHUNK
 #define MC_PAIR_CHUNK 4
 #endif
+#ifndef MC_PAIR_CHUNK_LEAD
+#define MC_PAIR_CHUNK_LEAD 4
+#endif
 #include "kernels.h"
 #include "pass_impl.cuh"
 #include "xtal_pass.cuh"
@@ -27,6 +30,8 @@ constexpr int MINB_GEN = MC_MINB_GEN_F32;  // the same for the row kernel with b
 constexpr int MINB_PAIR = MC_MINB_PAIR_F32;  // the same for the pair pass
 constexpr int MINB_PAIR_LEAD = 2;            // the same for the pair pass in site order
 constexpr int kPairChunk = MC_PAIR_CHUNK;    // consecutive pair tiles per grid-stride step
+constexpr int kPairChunkLead = MC_PAIR_CHUNK_LEAD;  // the same in site order
+constexpr int kFieldChunk = 4;               // the same for the neighbour-field kernel
 constexpr int V = kSitesPerThreadF32;
 
 // Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
@@ -97,8 +102,9 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
 template <bool LEADER>
 void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, cudaStream_t s) {
     constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, kPairChunk, LEADER>);
-    pair_pass_kernel<R, B, kPairChunk, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+    constexpr int C = LEADER ? kPairChunkLead : kPairChunk;
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER>);
+    pair_pass_kernel<R, B, C, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour);
 }
 
@@ -112,8 +118,8 @@ void sweep_end(const GroupArgs& g, cudaStream_t s) {
 }
 
 void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, 4>);
-    pair_field_kernel<R, V, 4><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, kFieldChunk>);
+    pair_field_kernel<R, V, kFieldChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
 }
 
 void ml_reset(const GroupArgs& g, cudaStream_t s) {

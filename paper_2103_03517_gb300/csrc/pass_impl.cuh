@@ -1059,31 +1059,53 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                 const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
                 Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
                 const Spin4<R>* fld = static_cast<const Spin4<R>*>(p.pfield);
-                for (uint32_t t = tile; t < t1; ++t) {
-                    if constexpr (LEADER) {
-                        // the 64 sites of tile t in index order; each site whose
-                        // position pi^-1(q) is even leads the pair (pi(r), pi(r+1))
+                if constexpr (LEADER) {
+                    // The 64 sites of each tile in index order; each site whose
+                    // position r = pi^-1(q) is even leads the pair (pi(r),
+                    // pi(r+1)).  A tile has about 32 leaders, rarely exactly, so
+                    // leaders wait in a queue (lane j < m holds one) until a
+                    // full warp of them is ready; the queue is emptied at the
+                    // end of the run.  The draws are keyed by pair, so the
+                    // grouping changes no result.
+                    uint32_t wq = 0, wr = 0;
+                    int m = 0;
+                    for (uint32_t t = tile; t < t1; ++t) {
                         const uint32_t qa = (t - t0) * 64u + uint32_t(lane), qb = qa + 32u;
                         const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_bits, rk) : 1u;
                         const uint32_t rb = qb < p.Nc ? permute_inv(qb, p.Nc, p.perm_bits, rk) : 1u;
                         const uint32_t ma = __ballot_sync(0xffffffffu, !(ra & 1u) && ra + 1u < p.Nc);
                         const uint32_t mb = __ballot_sync(0xffffffffu, !(rb & 1u) && rb + 1u < p.Nc);
                         const int ca = __popc(ma), total = ca + __popc(mb);
-                        for (int base = 0; base < total; base += 32) {
-                            const int j = base + lane;
-                            const bool second = j >= ca;
-                            const int src = j < total ? select_bit(second ? mb : ma, second ? j - ca : j) : 0;
+                        // leader k of this tile (0 <= k < total): its site and position
+                        auto leader = [&](int k, uint32_t& q, uint32_t& r) {
+                            const bool second = k >= ca;
+                            const int src = (k >= 0 && k < total) ? select_bit(second ? mb : ma, second ? k - ca : k) : 0;
                             const uint32_t r_a = __shfl_sync(0xffffffffu, ra, src);
                             const uint32_t r_b = __shfl_sync(0xffffffffu, rb, src);
-                            if (j < total) {
-                                const uint32_t r = second ? r_b : r_a;
-                                const uint32_t qi = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
-                                const uint32_t qj = permute(r + 1u, p.Nc, p.perm_bits, rk);
-                                nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, qi, qj, c, sweep, colour, ML,
-                                                     dhi, dlo);
-                            }
+                            r = second ? r_b : r_a;
+                            q = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
+                        };
+                        int used = 0;
+                        while (m + (total - used) >= 32) {  // a full warp: the queue, then this tile's next
+                            uint32_t q, r;
+                            leader(used + lane - m, q, r);
+                            if (lane < m) { q = wq; r = wr; }
+                            const uint32_t qj = permute(r + 1u, p.Nc, p.perm_bits, rk);
+                            nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, q, qj, c, sweep, colour, ML, dhi, dlo);
+                            used += 32 - m;
+                            m = 0;
                         }
-                    } else {
+                        uint32_t q, r;  // the rest of this tile joins the queue
+                        leader(used + lane - m, q, r);
+                        if (lane >= m && lane < m + (total - used)) { wq = q; wr = r; }
+                        m += total - used;
+                    }
+                    if (lane < m) {
+                        const uint32_t qj = permute(wr + 1u, p.Nc, p.perm_bits, rk);
+                        nacc += pair_move<R>(p, par, s, own4, fld, wr >> 1, wq, qj, c, sweep, colour, ML, dhi, dlo);
+                    }
+                } else {
+                    for (uint32_t t = tile; t < t1; ++t) {
                         const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
                         if (pr < p.n_pairs) {
                             const uint32_t qi = permute(2 * pr, p.Nc, p.perm_bits, rk);
