@@ -9,7 +9,7 @@ no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--side all|none|fp64|constrained|anisotropy|general|serving] [--no-cpu]
+                       [--side all|none|fp64|constrained|anisotropy|general|stiffness|serving] [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
 `--impl reference` times the serial FP64 CPU oracle on the host cores instead.
@@ -355,6 +355,8 @@ def secondary(mc, torch, stream, dev, side="all"):
         out.update(anisotropy(mc, torch, stream, dev))
     if side in ("all", "general"):
         out.update(general_geometry(mc, torch, stream, dev))
+    if side in ("all", "stiffness"):
+        out.update(stiffness(mc, torch, stream, dev))
     return out
 
 
@@ -451,6 +453,37 @@ def anisotropy(mc, torch, stream, dev, n_eq=200, n_meas=500):
         "temperatures": Ts, "eq4": res["eq4"], "torque": res["torque"],
         "torque_over_eq4_time": res["torque"]["ms"] / res["eq4"]["ms"],
         "max_abs_diff": max(abs(x - y) for x, y in zip(res["eq4"]["k_u"], res["torque"]["k_u"]))}}
+
+
+def stiffness(mc, torch, stream, dev):
+    """Table I of the paper at reduced size: for K/J = 8.33e-3 .. 4.2e-2 and
+    7 temperatures, a 256 x 64 x 64 wall lattice (x anti-periodic, Bloch-wall
+    start) and a 64^3 uniform lattice per point, 2000 + 4000 sweeps, one
+    profile fit every 20 sweeps; A(T) = K(T) (Delta/pi)^2 with K(T) from
+    Eq. 4, and the exponent of A ~ m^k over m > 0.6.  Wall time of the whole
+    study (sweeps, profile reads and fits)."""
+    from paper_2103_03517_gb300.studies import exchange_stiffness_study
+    table1 = [8.33e-3, 1.67e-2, 2.5e-2, 3.33e-2, 4.2e-2]
+    temps = [0.2, 0.35, 0.5, 0.65, 0.8, 0.95, 1.1]
+    r = exchange_stiffness_study(table1, temps, stream=stream.cuda_stream, device=dev)
+    # the free-energy route of Eq. 5 for K/J = 4.2e-2: walls and uniform
+    # lattices of the same size, from the paramagnet (T = 20) down to 0.2
+    df_temps = [20.0, 10.0, 6.0, 4.0, 3.0, 2.5, 2.0, 1.7, 1.5, 1.35, 1.2, 1.1, 0.95, 0.8, 0.65, 0.5, 0.35, 0.2]
+    f = exchange_stiffness_study([4.2e-2], df_temps, wall_dims=(128, 48, 48), uniform_dims=(128, 48, 48),
+                                 stream=stream.cuda_stream, device=dev)
+    return {"stiffness": {
+        "workload": "Table I at reduced size: 5 K/J x 7 T, wall 256x64x64 (x anti-periodic) + uniform 64^3 "
+                    "per point, FP32, 2000 + 4000 sweeps, profile fit every 20 sweeps",
+        "k": {f"{K:.4g}": [round(v[0], 3), round(v[1], 3)] for K, v in r["exponents"].items()},
+        "paper_k": {"0.00833": 1.48, "0.0167": 1.55, "0.025": 1.75, "0.0333": 1.75, "0.042": 1.79},
+        "seconds": round(r["seconds"], 2), "updates_per_s": r["updates"] / r["seconds"],
+        "points": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in x.items()} for x in r["rows"]],
+        "free_energy_route": {
+            "workload": "K/J = 4.2e-2, wall and uniform 128x48x48 per T, T = 20 .. 0.2 (18 points), "
+                        "2000 + 4000 sweeps",
+            "seconds": round(f["seconds"], 2),
+            "points": [{k: round(x[k], 5) for k in ("T", "m", "K_T", "delta", "A", "dF", "A_dF")}
+                       for x in f["rows"]]}}}
 
 
 def general_geometry(mc, torch, stream, dev, sweeps=40):
@@ -550,7 +583,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
-                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "serving"],
+                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

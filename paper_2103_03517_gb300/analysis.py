@@ -1,0 +1,128 @@
+"""Host analysis of the library's outputs for Sec. 3 of arXiv:2103.03517:
+the domain-wall width fit and the exchange stiffness of Eq. 5, the free-energy
+route dF(T) of Eq. 5, the m^k scaling exponent of Table I, the Bloch law of
+Eq. 3 and the transverse susceptibility of Eq. 7.  Plain numpy / scipy on the
+host; reduced units (J = 1, k_B = 1, mu_S = 1, lattice constant 1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = ["wall_model", "fit_wall", "exchange_stiffness", "free_energy_difference",
+           "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial"]
+
+
+def wall_model(x, m, x0, delta, Lx=None):
+    """Bloch-wall profile of Sec. 3: m_z(x) = m tanh(-pi (x - x0) / delta).
+    With Lx given the profile is anti-periodic, m_z(x + Lx) = -m_z(x) (the
+    wall setup with x anti-periodic): x - x0 is folded into [-Lx/2, Lx/2) and
+    each fold by Lx flips the sign."""
+    x = np.asarray(x, np.float64)
+    d = x - x0
+    sign = np.ones_like(d)
+    if Lx is not None:
+        k = np.floor((d + 0.5 * Lx) / Lx)
+        d = d - k * Lx
+        sign = np.where(np.mod(k, 2) == 0, 1.0, -1.0)
+    return sign * m * np.tanh(-math.pi * d / delta)
+
+
+def fit_wall(mz, antiperiodic=True, x=None):
+    """Least-squares fit of wall_model to a slice profile m_z(x) (one value
+    per x-plane, from mc_profile), returning (m, x0, delta, errors).  The
+    start is the profile's own sign change; with antiperiodic the wall may sit
+    anywhere, the boundary included."""
+    from scipy.optimize import curve_fit
+
+    mz = np.asarray(mz, np.float64)
+    Lx = mz.size
+    x = np.arange(Lx, dtype=np.float64) if x is None else np.asarray(x, np.float64)
+    m0 = max(float(np.abs(mz).max()), 1e-3)
+    # start: the + to - crossing of the (anti-periodically extended) profile
+    ext = np.concatenate([mz, -mz]) if antiperiodic else mz
+    cross = [i for i in range(ext.size - 1) if ext[i] > 0 >= ext[i + 1]]
+    x0 = float(cross[0]) + 0.5 if cross else 0.5 * Lx  # in [Lx, 2 Lx): a reversed wall
+    width = max(2.0, float(np.sum(np.abs(mz) < 0.76 * m0)) * math.pi / 2.0)  # |tanh| < 0.76 over ~delta/pi*2
+    f = (lambda xx, m, c, d: wall_model(xx, m, c, d, Lx)) if antiperiodic else (lambda xx, m, c, d: wall_model(xx, m, c, d))
+    import warnings
+
+    with warnings.catch_warnings():  # a flat profile leaves the covariance undefined (inf errors)
+        warnings.simplefilter("ignore")
+        p, cov = curve_fit(f, x, mz, p0=[m0, x0, width], maxfev=20000)
+    m, c, d = p
+    if d < 0:  # the model is symmetric under (m, delta) -> (-m, -delta)
+        m, d = -m, -d
+    if antiperiodic:  # x0 into [0, Lx); each fold by Lx flips the sign of m
+        k = math.floor(c / Lx)
+        c -= k * Lx
+        m = -m if k % 2 else m
+    err = np.sqrt(np.maximum(np.diag(cov), 0.0))
+    return float(m), float(c), float(d), err
+
+
+def exchange_stiffness(delta, K):
+    """Eq. 5 solved for A: Delta = pi sqrt(A / K), so A = K (Delta / pi)^2."""
+    return np.asarray(K, np.float64) * (np.asarray(delta, np.float64) / math.pi) ** 2
+
+
+def free_energy_difference(T, dU):
+    """dF(T) of a wall from internal energies (Eq. 5 and the text after it):
+    with beta = 1/T, d(beta F)/d beta = U, and at beta = 0 the two states
+    have the same free energy, so beta dF(beta) = int_0^beta dU(b) db.  dU
+    is <E>_wall - <E>_uniform at the temperatures T (any order); at beta = 0
+    every state has the same weight in both, so dU(0) = 0 and the integral is
+    the trapezoid rule over the beta grid from (0, 0)."""
+    T = np.asarray(T, np.float64)
+    dU = np.asarray(dU, np.float64)
+    order = np.argsort(1.0 / T)
+    beta = np.concatenate([[0.0], 1.0 / T[order]])
+    u = np.concatenate([[0.0], dU[order]])
+    integral = np.concatenate([[0.0], np.cumsum(0.5 * (u[1:] + u[:-1]) * np.diff(beta))])
+    dF = np.empty_like(T)
+    dF[order] = integral[1:] / beta[1:]
+    return dF
+
+
+def stiffness_from_free_energy(dF, C, K):
+    """Eq. 5, dF = 4 C sqrt(A K), solved for A = dF^2 / (16 C^2 K); C is the
+    wall's cross-section (Ly Lz)."""
+    return np.asarray(dF, np.float64) ** 2 / (16.0 * float(C) ** 2 * np.asarray(K, np.float64))
+
+
+def power_exponent(m, y, m_min=0.0, sigma_y=None):
+    """Exponent k of y ~ m^k (Table I: A(T) against m(T), low-temperature
+    range m > m_min) by least squares on log y = log c + k log m; returns
+    (k, its standard error, c).  sigma_y weights the points (relative error
+    sigma_y / y in log space)."""
+    m = np.asarray(m, np.float64)
+    y = np.asarray(y, np.float64)
+    sel = (m > m_min) & (y > 0)
+    X = np.stack([np.ones(sel.sum()), np.log(m[sel])], axis=1)
+    Y = np.log(y[sel])
+    w = np.ones(sel.sum()) if sigma_y is None else (y[sel] / np.asarray(sigma_y, np.float64)[sel])
+    Xw, Yw = X * w[:, None], Y * w
+    coef, res, *_ = np.linalg.lstsq(Xw, Yw, rcond=None)
+    dof = max(1, X.shape[0] - 2)
+    s2 = float(np.sum((Yw - Xw @ coef) ** 2)) / dof if sigma_y is None else 1.0
+    cov = s2 * np.linalg.inv(Xw.T @ Xw)
+    return float(coef[1]), float(math.sqrt(cov[1, 1])), float(math.exp(coef[0]))
+
+
+def bloch_fit(T, m, T_max=None):
+    """Eq. 3, m(T) = (1 - T/T_C)^beta, fitted to (T, m) with T < T_max;
+    returns (T_C, beta, errors)."""
+    from scipy.optimize import curve_fit
+
+    T = np.asarray(T, np.float64)
+    m = np.asarray(m, np.float64)
+    sel = T < (T_max if T_max is not None else np.inf)
+    f = lambda t, tc, b: np.power(np.clip(1.0 - t / tc, 1e-12, None), b)
+    p, cov = curve_fit(f, T[sel], m[sel], p0=[1.05 * T[sel].max(), 0.35], maxfev=20000)
+    return float(p[0]), float(p[1]), np.sqrt(np.maximum(np.diag(cov), 0.0))
+
+
+def chi_perp_uniaxial(m, Ku_T, Ms0=1.0):
+    """Eq. 7: transverse susceptibility below T_C, M_S(0) m^2 / (2 K_u(T))."""
+    return float(Ms0) * np.asarray(m, np.float64) ** 2 / (2.0 * np.asarray(Ku_T, np.float64))

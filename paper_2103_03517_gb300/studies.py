@@ -1,0 +1,129 @@
+"""Sec. 3 studies of arXiv:2103.03517 driven through the library's public API:
+the exchange stiffness A(T) by the Bloch-wall method (Eq. 5) with K(T) from
+the easy-axis estimator (Eq. 4), and its low-temperature m^k exponent as a
+function of K/J (Table I).  Every sweep runs in libmc; the fits are host
+post-processing (``analysis``).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import _mc as mc
+from . import analysis as an
+
+__all__ = ["exchange_stiffness_study", "bloch_wall_spins"]
+
+
+def bloch_wall_spins(dims, K, J=1.0):
+    """Spins (N x 3, site order x + Lx (y + Ly z)) of the continuum Bloch wall
+    centred in x: phi(x) = 2 arctan(exp(pi (x - Lx/2) / Delta0)), Delta0 =
+    pi sqrt(J / 2K), S = (0, sin phi, cos phi); with x anti-periodic the
+    closure S(Lx) = -S(0) matches the wall's far side."""
+    Lx, Ly, Lz = dims
+    x = np.arange(Lx, dtype=np.float64) + 0.5
+    phi = 2.0 * np.arctan(np.exp(math.pi * (x - Lx / 2) / (math.pi * math.sqrt(J / (2.0 * K)))))
+    row = np.stack([np.zeros(Lx), np.sin(phi), np.cos(phi)], axis=1)
+    return np.tile(row, (Ly * Lz, 1))
+
+
+def exchange_stiffness_study(K_over_J, temps, wall_dims=(256, 64, 64), uniform_dims=(64, 64, 64), n_eq=2000,
+                             n_meas=4000, every=20, m_min=0.6, seed=1, precision=mc.MC_FP32, stream=None,
+                             device=0):
+    """For every K/J (uniaxial K along z, J = 1) and temperature T:
+
+    * a wall lattice, x anti-periodic and y, z periodic, started on the
+      continuum Bloch wall of width pi sqrt(J / 2K) (the wall setup of Sec. 3,
+      rotating in the y-z plane); every `every` measured sweeps one
+      slice profile m_z(x) is taken and fitted by the tanh of Sec. 3, and the
+      width Delta(T) is the mean of the fits that find a wall (amplitude above
+      0.05, width below Lx; above T_C none does and Delta is NaN);
+    * a uniform periodic lattice, whose samples give m(T) = <|m|> and
+      K(T) = K k_u(T) by Eq. 4;
+    * A(T) = K(T) (Delta / pi)^2 (Eq. 5), and for each K/J the exponent k of
+      A ~ m^k over the points with m > m_min (Table I);
+    * when the uniform lattice has the wall lattice's size, the free-energy
+      route of Eq. 5 as well: dU = N (e_wall - e_uniform), dF(T) from dU over
+      the given temperatures (which should then reach well above T_C, the
+      integral starting at beta = 0), and A_dF = dF^2 / (16 C^2 K(T)) with C
+      = Ly Lz.
+
+    All lattices advance together as one group.  Returns a dict with the
+    per-point table, the exponents, the spin-updates run and the wall time.
+    """
+    K_over_J = [float(k) for k in K_over_J]
+    temps = [float(t) for t in temps]
+    points = [(k, t) for k in K_over_J for t in temps]
+    walls, unis = [], []
+    try:
+        for i, (K, T) in enumerate(points):
+            walls.append(mc.mc_create_ex(mc.make_desc(
+                wall_dims, K_u=K, T=T, seed=seed + 2 * i, precision=precision,
+                boundary=(mc.MC_ANTIPERIODIC, mc.MC_PERIODIC, mc.MC_PERIODIC), ring_capacity=16,
+                sample_torque=0, stream=stream, device=device)))
+            mc.mc_set_spins(walls[-1], bloch_wall_spins(wall_dims, K))
+            unis.append(mc.mc_create_ex(mc.make_desc(
+                uniform_dims, K_u=K, T=T, seed=seed + 2 * i + 1, precision=precision, ring_capacity=16,
+                sample_torque=0, stream=stream, device=device)))
+        g = mc.mc_group_create(walls + unis)
+        t0 = time.perf_counter()
+        try:
+            mc.mc_group_sweep(g, n_eq)
+            for h in walls + unis:
+                mc.mc_reset_stats(h)
+            Lx = wall_dims[0]
+            prev = [np.zeros(Lx) for _ in walls]
+            deltas = [[] for _ in walls]
+            blocks = max(1, n_meas // every)
+            for b in range(blocks):
+                mc.mc_group_sweep(g, every, measure=True)
+                for w, h in enumerate(walls):
+                    mc.mc_profile_sample(h)
+                    avg = mc.mc_profile(h, 2, Lx)  # mean over the b + 1 samples so far
+                    one = avg * (b + 1) - prev[w] * b
+                    prev[w] = avg
+                    try:
+                        m_w, _, d_w, _ = an.fit_wall(one)
+                    except RuntimeError:  # a profile the fit cannot follow (near T_C)
+                        continue
+                    if abs(m_w) > 0.05 and 0.0 < d_w < Lx:  # a wall (none above T_C)
+                        deltas[w].append(d_w)
+            mc.mc_group_sync(g)
+        finally:
+            mc.mc_group_destroy(g)
+        seconds = time.perf_counter() - t0
+        rows = []
+        for w, (K, T) in enumerate(points):
+            ow, ou = mc.mc_measure(walls[w]), mc.mc_measure(unis[w])
+            k_u = float(mc.mc_anisotropy_scaling(unis[w])[0])
+            d = np.asarray(deltas[w])
+            delta = float(d.mean()) if d.size else float("nan")
+            d_err = float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else float("nan")
+            K_T = K * k_u
+            rows.append({"K": K, "T": T, "m": float(ou.ml), "k_u": k_u, "K_T": K_T, "delta": delta,
+                         "delta_err": d_err, "A": float(an.exchange_stiffness(delta, K_T)),
+                         "e_wall": float(ow.e), "e_uniform": float(ou.e), "profiles": int(d.size)})
+    finally:
+        for h in walls + unis:
+            mc.mc_destroy(h)
+    if tuple(uniform_dims) == tuple(wall_dims):  # the free-energy route
+        N, C = int(np.prod(wall_dims)), wall_dims[1] * wall_dims[2]
+        for K in K_over_J:
+            r = [x for x in rows if x["K"] == K]
+            dU = np.array([N * (x["e_wall"] - x["e_uniform"]) for x in r])
+            dF = an.free_energy_difference([x["T"] for x in r], dU)
+            for x, f in zip(r, dF):
+                x["dF"] = float(f)
+                x["A_dF"] = float(an.stiffness_from_free_energy(f, C, x["K_T"])) if x["K_T"] > 0 else float("nan")
+    exponents = {}
+    for K in K_over_J:
+        r = [x for x in rows if x["K"] == K and np.isfinite(x["A"]) and x["A"] > 0]
+        m = np.array([x["m"] for x in r])
+        A = np.array([x["A"] for x in r])
+        if int(np.sum(m > m_min)) >= 3:
+            k, k_err, _ = an.power_exponent(m, A, m_min=m_min)
+            exponents[K] = (k, k_err)
+    updates = len(points) * (n_eq + blocks * every) * (int(np.prod(wall_dims)) + int(np.prod(uniform_dims)))
+    return {"rows": rows, "exponents": exponents, "updates": updates, "seconds": seconds}

@@ -1,0 +1,81 @@
+"""Host analysis of Sec. 3 (paper_2103_03517_gb300.analysis) against closed
+forms and the discrete minimum-energy Bloch wall."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_03517_gb300 import analysis as an
+from test_oracle_physics import _discrete_wall
+
+
+@pytest.mark.parametrize("x0", [64.3, 2.2, 127.6, 0.0])
+@pytest.mark.parametrize("m", [0.8, -0.55])
+def test_fit_wall_recovers_antiperiodic_tanh(x0, m):
+    """An exact anti-periodic tanh profile, the wall anywhere (at the
+    boundary too) and either orientation: m, x0 and the width come back."""
+    Lx, delta = 128, 15.3
+    mz = an.wall_model(np.arange(Lx), m, x0, delta, Lx)
+    mf, cf, df, _ = an.fit_wall(mz)
+    assert abs(df - delta) < 1e-6
+    # x0 comes back in [0, Lx) with the sign of m that goes with it
+    assert abs(mf - m) < 1e-6 and abs((cf - x0 + Lx / 2) % Lx - Lx / 2) < 1e-5, (mf, cf, df)
+
+
+@pytest.mark.parametrize("K", [0.01, 0.04])
+def test_zero_temperature_wall_gives_stiffness_half_J(K):
+    """The discrete minimum-energy wall of the anti-periodic chain (J = 1):
+    its m_z = cos(phi) fitted by the tanh of Sec. 3 gives Delta close to
+    pi sqrt(J / 2K), and Eq. 5 then gives A = J/2 (the continuum stiffness
+    of the simple cubic lattice, a = 1) to the discreteness error."""
+    J, Lx = 1.0, 256
+    phi, _ = _discrete_wall(Lx, J, K)
+    m, x0, delta, _ = an.fit_wall(np.cos(phi))
+    assert abs(delta / (math.pi * math.sqrt(J / (2 * K))) - 1) < 0.02
+    assert abs(an.exchange_stiffness(delta, K) / (J / 2) - 1) < 0.04
+    assert abs(abs(m) - 1) < 1e-3
+
+
+def test_free_energy_difference_closed_forms():
+    """beta dF = int_0^beta dU with dU(0) = 0: dU = c beta (trapezoid-exact)
+    gives dF = c beta / 2, the temperatures in any order; dU = E0 (1 -
+    exp(-beta)) gives dF = E0 (1 - (1 - exp(-beta)) / beta) on a fine grid."""
+    T = np.array([0.5, 2.0, 1.0, 0.25])
+    c = 1.7
+    assert np.allclose(an.free_energy_difference(T, c / T), c / (2 * T), rtol=0, atol=1e-12)
+    beta = np.linspace(0.0, 5.0, 20001)[1:]
+    E0 = 2.3
+    dF = an.free_energy_difference(1.0 / beta, E0 * (1 - np.exp(-beta)))
+    assert np.allclose(dF, E0 * (1 - (1 - np.exp(-beta)) / beta), rtol=0, atol=1e-7)  # O(h^2) trapezoid
+
+
+def test_free_energy_route_at_zero_temperature_gives_half_J():
+    """At T -> 0 the wall's free energy is its energy; for the discrete wall
+    per unit cross-section that is close to 2 sqrt(2 J K), and Eq. 5 turns it
+    into A = J/2."""
+    J, K, Lx = 1.0, 0.02, 256
+    _, e_min = _discrete_wall(Lx, J, K)
+    e_wall = e_min + (J + K) * Lx
+    beta = np.linspace(0.0, 400.0, 4001)[1:]
+    dF = an.free_energy_difference(1.0 / beta, np.full(beta.size, e_wall))
+    assert abs(an.stiffness_from_free_energy(dF[-1], 1.0, K) / (J / 2) - 1) < 0.02
+
+
+def test_power_exponent_and_bloch_law():
+    m = np.linspace(0.3, 0.98, 30)
+    k, err, c = an.power_exponent(m, 2.5 * m ** 1.48, m_min=0.6)
+    assert abs(k - 1.48) < 1e-10 and abs(c - 2.5) < 1e-10 and err < 1e-8
+    T = np.linspace(0.05, 1.35, 40)
+    Tc, beta, _ = an.bloch_fit(T, (1 - T / 1.443) ** 0.34)
+    assert abs(Tc - 1.443) < 1e-6 and abs(beta - 0.34) < 1e-6
+
+
+def test_transverse_susceptibility_low_temperature_single_spin():
+    """Eq. 7 at T -> 0 for one spin with uniaxial K (m = 1, K_u(T) = K): the
+    variance of S_x over the Boltzmann weight exp(K cos^2 theta / T), by
+    quadrature over the sphere, divided by T equals 1 / (2K) to O(T/K)."""
+    K, T = 1.0, 1e-3
+    th = np.linspace(0.0, math.pi, 400001)
+    w = np.exp(K * (np.cos(th) ** 2 - 1) / T) * np.sin(th)
+    sx2 = np.trapezoid(0.5 * np.sin(th) ** 2 * w, th) / np.trapezoid(w, th)  # <cos^2 phi> = 1/2
+    assert abs((sx2 / T) / an.chi_perp_uniaxial(1.0, K) - 1) < 5e-3
