@@ -36,12 +36,13 @@ struct KernelSet {
     // The same over lattices in the row layout (gen as in row_pass).  Null
     // in the FP64 set.
     void (*row_sample)(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s);
-    // bcc / fcc lattice L alone: a pass over sub-set (sub, colour) of ntiles
-    // 32-site tiles (finalize != 0 closes the sweep), and the sample over
-    // the 2 nsub sub-sets (ntiles = 2 nsub tiles_per_subset), which closes it.
-    void (*xtal_pass)(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize,
+    // bcc / fcc / hcp lattice L alone: a pass over sub-set (sub, colour) of
+    // ntiles 32-site tiles (finalize != 0 closes the sweep), and the sample
+    // over the 2 nsub sub-sets (ntiles = 2 nsub tiles_per_subset), which
+    // closes it; nb = the most neighbour entries of a sub-lattice.
+    void (*xtal_pass)(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, int nb,
                       cudaStream_t s);
-    void (*xtal_sample)(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s);
+    void (*xtal_sample)(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, cudaStream_t s);
     // Slice sums for the profile of one lattice.
     void (*profile)(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s);
     const char* name;
@@ -61,6 +62,7 @@ struct LaunchSet {
     // a bcc / fcc lattice alone: its descriptor and sub-lattice count, else null
     LatDev* xtal = nullptr;
     int nsub = 1;
+    int xnb_max = 0;  // most neighbour entries of its sub-lattices
 };
 
 const KernelSet& kernels_f64();

@@ -136,15 +136,40 @@ void measure(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     measure_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles);
 }
 
-void xtal_pass(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(xtal_pass_kernel<R>);
-    xtal_pass_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, static_cast<const R*>(cone), sub, colour,
-                                                                 finalize);
+// Entry bound of the crystal kernels: the smallest instance that holds nb.
+template <template <int> class F, typename... A>
+void by_entries(int nb, A... a) {
+    if (nb <= 8) F<8>::run(a...);
+    else if (nb <= 12) F<12>::run(a...);
+    else if (nb <= 14) F<14>::run(a...);
+    else if (nb <= 18) F<18>::run(a...);
+    else F<kXtalMaxNb>::run(a...);
 }
 
-void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(xtal_sample_kernel<R>);
-    xtal_sample_kernel<R><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, tiles_per_subset);
+template <int NB>
+struct XtalPass {
+    static void run(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, cudaStream_t s) {
+        static const uint32_t cap = resident_blocks(xtal_pass_kernel<R, NB>);
+        xtal_pass_kernel<R, NB><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, static_cast<const R*>(cone), sub,
+                                                                         colour, finalize);
+    }
+};
+
+template <int NB>
+struct XtalSample {
+    static void run(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s) {
+        static const uint32_t cap = resident_blocks(xtal_sample_kernel<R, NB>);
+        xtal_sample_kernel<R, NB><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, tiles_per_subset);
+    }
+};
+
+void xtal_pass(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, int nb,
+               cudaStream_t s) {
+    by_entries<XtalPass>(nb, L, ntiles, cone, sub, colour, finalize, s);
+}
+
+void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, cudaStream_t s) {
+    by_entries<XtalSample>(nb, L, ntiles, tiles_per_subset, s);
 }
 
 void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {

@@ -66,13 +66,18 @@ inline FastDiv make_fastdiv(uint32_t d) {
 
 enum { kColourGeneral = 0, kColourRow = 1, kColourRowGen = 2 };
 
-// One neighbour entry of a bcc / fcc sub-lattice: the neighbour's
-// sub-lattice, its cell offset and its coupling (J1 or J2).
+// One neighbour entry of a bcc / fcc / hcp sub-lattice: the neighbour's
+// sub-lattice, its cell offset and its coupling (J1 or J2), with what the
+// kernels need precomputed for the lattice's size: the offset taken modulo
+// (Lx, Ly, Lz), the parity of dx + dy + dz, and for a site of colour c the
+// element offset of the neighbour's x-component array in the spins.
 constexpr int kXtalMaxSub = 4, kXtalMaxNb = 24;
 struct XtalNb {
     int8_t sub, dx, dy, dz;
     float fJ;
     double J;
+    uint32_t dxw, dyw, dzw, par;
+    uint64_t off[2];
 };
 
 struct LatParams {

@@ -147,7 +147,8 @@ int sublattices(int lattice) { return lattice == MC_BCC ? 2 : (lattice == MC_FCC
 // from -1 to 1: the order in which the field is summed.  hcp: the
 // orthohexagonal cell (1, sqrt 3, sqrt(8/3)) with sub-lattices (0,0,0),
 // (1/2,1/2,0), (1/2,1/6,1/2), (0,2/3,1/2).
-static void xtal_table(int lattice, double J, double J2, XtalNb out[kXtalMaxSub][kXtalMaxNb], int n[kXtalMaxSub]) {
+static void xtal_table(int lattice, double J, double J2, const LatParams& p, XtalNb out[kXtalMaxSub][kXtalMaxNb],
+                       int n[kXtalMaxSub]) {
     const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
     const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
     const double hcp[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 1.0 / 6.0, 0.5}, {0, 2.0 / 3.0, 0.5}};
@@ -174,6 +175,12 @@ static void xtal_table(int lattice, double J, double J2, XtalNb out[kXtalMaxSub]
                         e.dz = int8_t(dz);
                         e.J = nn ? J : J2;
                         e.fJ = float(e.J);
+                        e.dxw = uint32_t((dx + p.Lx) % p.Lx);
+                        e.dyw = uint32_t((dy + p.Ly) % p.Ly);
+                        e.dzw = uint32_t((dz + p.Lz) % p.Lz);
+                        e.par = uint32_t(dx + dy + dz + 4) & 1u;  // + 4 keeps the sum non-negative, parity unchanged
+                        for (int c = 0; c < 2; ++c)
+                            e.off[c] = (uint64_t(t) * 2 + ((uint32_t(c) + e.par) & 1u)) * 3 * uint64_t(p.stride);
                     }
     }
 }
@@ -416,7 +423,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     p.spins = take(size_t(p.nsub) * 6 * size_t(p.stride) * rs);
     XtalNb xt[kXtalMaxSub][kXtalMaxNb] = {};
     if (p.nsub > 1) {
-        xtal_table(d->lattice, d->J, d->J2, xt, p.xnb_n);
+        xtal_table(d->lattice, d->J, d->J2, p, xt, p.xnb_n);
         p.xnb = take(sizeof xt);
     }
     std::vector<uint8_t> hb;
@@ -541,6 +548,7 @@ LaunchSet single_launch_set(mc_lattice* h) {
     if (h->hp.nsub > 1) {
         ls.xtal = h->d_lat;
         ls.nsub = h->hp.nsub;
+        for (int i = 0; i < h->hp.nsub; ++i) ls.xnb_max = std::max(ls.xnb_max, h->hp.xnb_n[i]);
     } else if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
@@ -581,9 +589,11 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             for (int sub = 0; sub < ls.nsub; ++sub)
                 for (int colour = 0; colour < 2; ++colour) {
                     const bool last = sub == ls.nsub - 1 && colour == 1;
-                    timed([&] { k.xtal_pass(ls.xtal, ls.nt_all, cone, sub, colour, last && !measure ? 1 : 0, s); });
+                    timed([&] {
+                        k.xtal_pass(ls.xtal, ls.nt_all, cone, sub, colour, last && !measure ? 1 : 0, ls.xnb_max, s);
+                    });
                 }
-            if (measure) k.xtal_sample(ls.xtal, uint32_t(2 * ls.nsub) * ls.nt_all, ls.nt_all, s);
+            if (measure) k.xtal_sample(ls.xtal, uint32_t(2 * ls.nsub) * ls.nt_all, ls.nt_all, ls.xnb_max, s);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

@@ -6,7 +6,8 @@
 // Ly z) for cell (x, y, z).  Every neighbour comes from the lattice's table
 // (XtalNb: sub-lattice, cell offset, coupling J1 or J2) in its order, with
 // the coupling inside the field h, so the exchange term of Eq. 2 is -(d.h).
-// One lattice per launch, one lane per site, persistent warps.
+// One lattice per launch, one lane per site, persistent warps; the table
+// entries sit in shared memory for the launch.
 #pragma once
 #include "pass_impl.cuh"
 
@@ -26,44 +27,61 @@ __device__ __forceinline__ XCell xtal_cell(const LatParams& p, int colour, uint3
     return XCell{2u * k + xoff, y, z};
 }
 
-__device__ __forceinline__ uint32_t wrap_add(uint32_t v, int d, uint32_t L) {
-    const int w = int(v) + d;
-    return uint32_t(w < 0 ? w + int(L) : (w >= int(L) ? w - int(L) : w));
+// Stage the neighbour entries of sub-lattices [sub0, sub0 + nsub) in shared
+// memory (block-wide; every thread must reach it).
+template <int NMAX>
+__device__ __forceinline__ void xtal_stage(const LatParams& p, int sub0, int nsub, XtalNb* tab) {
+    const XtalNb* src = static_cast<const XtalNb*>(p.xnb);
+    for (int i = threadIdx.x; i < nsub * NMAX; i += blockDim.x) {
+        const int s = i / NMAX, e = i - s * NMAX;
+        if (e < p.xnb_n[sub0 + s]) tab[i] = src[(sub0 + s) * kXtalMaxNb + e];
+    }
+    __syncthreads();
 }
 
-// h = sum over the table entries of sub-lattice sub of J S_j, in table order.
-template <typename R>
-__device__ __forceinline__ V3<R> xtal_field(const LatParams& p, const R* s, int sub, XCell c) {
-    const XtalNb* nb = static_cast<const XtalNb*>(p.xnb) + sub * kXtalMaxNb;
+// h = sum over the n <= NMAX entries tab[0 .. n) of J S_j, in table order;
+// the site is cell c of the given colour.  Each entry's cell offset is taken
+// modulo the lattice size in advance, so a neighbour's cell wraps by one
+// compare per axis; its colour array follows from the entry's parity.
+template <typename R, int NMAX>
+__device__ __forceinline__ V3<R> xtal_field(const LatParams& p, const R* s, const XtalNb* tab, int n, XCell c,
+                                            int colour) {
     const uint32_t Lx = uint32_t(p.Lx), Ly = uint32_t(p.Ly), Lz = uint32_t(p.Lz), Lh = uint32_t(p.Lh);
     const size_t stride = p.stride;
     V3<R> h{R(0), R(0), R(0)};
-    const int n = p.xnb_n[sub];
-    for (int e = 0; e < n; ++e) {
-        const XtalNb t = nb[e];
-        const uint32_t xx = wrap_add(c.x, t.dx, Lx), yy = wrap_add(c.y, t.dy, Ly), zz = wrap_add(c.z, t.dz, Lz);
-        const uint32_t cc = (xx + yy + zz) & 1u;
-        const uint32_t q = (xx >> 1) + Lh * (yy + Ly * zz);
-        const R* b = s + (size_t(t.sub) * 2 + cc) * 3 * stride;
-        R J;
-        if constexpr (kIsF64<R>) J = t.J;
-        else J = t.fJ;
-        h.x = h.x + J * b[q];
-        h.y = h.y + J * b[stride + q];
-        h.z = h.z + J * b[2 * stride + q];
+#pragma unroll
+    for (int e = 0; e < NMAX; ++e) {
+        if (e < n) {
+            const XtalNb& t = tab[e];
+            uint32_t xx = c.x + t.dxw, yy = c.y + t.dyw, zz = c.z + t.dzw;
+            xx = xx >= Lx ? xx - Lx : xx;
+            yy = yy >= Ly ? yy - Ly : yy;
+            zz = zz >= Lz ? zz - Lz : zz;
+            const uint32_t q = (xx >> 1) + Lh * (yy + Ly * zz);
+            const R* b = s + t.off[colour];
+            R J;
+            if constexpr (kIsF64<R>) J = t.J;
+            else J = t.fJ;
+            h.x = h.x + J * b[q];
+            h.y = h.y + J * b[stride + q];
+            h.z = h.z + J * b[2 * stride + q];
+        }
     }
     return h;
 }
 
 // Pass over sub-set (sub, colour); finalize != 0 closes the sweep (the last
-// sub-set of an unmeasured sweep).
-template <typename R>
+// sub-set of an unmeasured sweep).  NMAX bounds the sub-lattice's entries.
+template <typename R, int NMAX>
 __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t ntiles, const R* __restrict__ cone,
                                                            int sub, int colour, int finalize) {
+    __shared__ XtalNb tab[NMAX];
+    const LatParams& p = L->p;
+    xtal_stage<NMAX>(p, sub, 1, tab);
+    const int n = p.xnb_n[sub];
     const WarpChunk wc = warp_chunk(ntiles);
     if (wc.begin >= wc.end) return;
     const int lane = wc.lane;
-    const LatParams& p = L->p;
     const Par<R> par = load_par<R>(p);
     const R c = cone[L->st.theta];
     const uint32_t sweep = L->st.sweep;
@@ -82,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t n
         V3<R> Sn;
         R P;
         if (!cone_trial(S, c, site, sweep, tag, p.key0, p.key1, Sn, P)) continue;
-        const V3<R> h = xtal_field(p, s, sub, cell);
+        const V3<R> h = xtal_field<R, NMAX>(p, s, tab, n, cell, colour);
         if (metropolis(delta_e(par, S, Sn, h, e_ax), par, P)) {
             own[q] = Sn.x;
             own[p.stride + q] = Sn.y;
@@ -101,12 +119,14 @@ __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t n
 // the working precision in a fixed butterfly order and rounded to fixed
 // point on lane i (int64 in both precisions, so that large couplings cannot
 // overflow).
-template <typename R>
+template <typename R, int NMAX>
 __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset) {
+    __shared__ XtalNb tab[kXtalMaxSub * NMAX];
+    const LatParams& p = L->p;
+    xtal_stage<NMAX>(p, 0, p.nsub, tab);
     const WarpChunk wc = warp_chunk(ntiles);
     if (wc.begin >= wc.end) return;
     const int lane = wc.lane;
-    const LatParams& p = L->p;
     const Par<R> par = load_par<R>(p);
     const R* s = static_cast<const R*>(p.spins);
     const V3<R> e_ax{par.e[0], par.e[1], par.e[2]};
@@ -121,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t
             const XCell cell = xtal_cell(p, colour, q);
             const R* own = s + (size_t(sub) * 2 + colour) * 3 * p.stride;
             const V3<R> S{own[q], own[p.stride + q], own[2 * size_t(p.stride) + q]};
-            const V3<R> h = xtal_field(p, s, sub, cell);
+            const V3<R> h = xtal_field<R, NMAX>(p, s, tab + sub * NMAX, p.xnb_n[sub], cell, colour);
             add_site<R, 1>(sums, S, e_ax);
             sums.v[kSumEx] = R(0.5) * (S.x * h.x + S.y * h.y + S.z * h.z);
         }
