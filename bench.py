@@ -9,7 +9,8 @@ no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--side all|none|fp64|constrained|anisotropy|general|stiffness|serving] [--no-cpu]
+                       [--side all|none|fp64|constrained|anisotropy|general|stiffness|films|serving]
+                       [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
 `--impl reference` times the serial FP64 CPU oracle on the host cores instead.
@@ -357,6 +358,8 @@ def secondary(mc, torch, stream, dev, side="all"):
         out.update(general_geometry(mc, torch, stream, dev))
     if side in ("all", "stiffness"):
         out.update(stiffness(mc, torch, stream, dev))
+    if side in ("all", "films"):
+        out.update(films(mc, torch, stream, dev))
     return out
 
 
@@ -486,6 +489,33 @@ def stiffness(mc, torch, stream, dev):
                        for x in f["rows"]]}}}
 
 
+def films(mc, torch, stream, dev):
+    """Sec. 4 at reduced size: granular films 256 x 256 x Lz (Lz = 4, 8; x, y
+    periodic, z open), Voronoi grains of mean diameter 16, 32 and 64 sites
+    with a random easy axis each (K_u = 0.02), m(T) at T = 0.1 .. 1.7 from
+    per-grain samples, and the average Curie temperature of Eq. 8 (20
+    terms); the continuous film of each thickness by Eq. 3.  1000 + 2000
+    sweeps per point, a grain sample every 20; wall time of each study."""
+    from paper_2103_03517_gb300.studies import film_curie_study
+    temps = [round(0.1 * i, 2) for i in range(1, 18)]
+    out = {}
+    for Lz in (4, 8):
+        dims = (256, 256, Lz)
+        c = film_curie_study(dims, None, None, None, temps, stream=stream.cuda_stream, device=dev)
+        row = {"continuous": {"T_C": round(c["fit"]["T_C"], 4), "seconds": round(c["seconds"], 2)}}
+        for d in (16, 32, 64):
+            gid, mask, axes = workloads.voronoi_film(256, 256, Lz, float(d), seed=d + Lz)
+            r = film_curie_study(dims, gid, mask, axes, temps, stream=stream.cuda_stream, device=dev)
+            row[f"grains_d{d}"] = {"grains": int(gid.max()) + 1, "T_C_mean": round(r["fit"]["T_C_mean"], 4),
+                                   "beta": r["fit"]["beta"], "rms": round(r["fit"]["rms"], 5),
+                                   "m": [round(x, 4) for x in r["m"]], "seconds": round(r["seconds"], 2),
+                                   "updates_per_s": r["updates"] / r["seconds"]}
+        out[f"Lz{Lz}"] = row
+    return {"films": {"workload": "Sec. 4 at reduced size: 256x256xLz films, Lz = 4, 8; Voronoi grains d = 16, "
+                                  "32, 64; T = 0.1..1.7 (17 points), 1000 + 2000 sweeps, FP32",
+                      "temperatures": temps, "results": out}}
+
+
 def general_geometry(mc, torch, stream, dev, sweeps=40):
     """FP32 throughput of the lattices that are not all-periodic simple
     cubes: the Bloch-wall lattice (1024 x 128 x 128, x pinned, T = 0.66), a
@@ -583,7 +613,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
-                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "serving"],
+                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "films",
+                             "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

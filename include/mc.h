@@ -240,11 +240,26 @@ MC_API int mc_profile(mc_handle h, int component, double* out, int len);
 /* Queue one profile sample of the current state (all three components). */
 MC_API int mc_profile_sample(mc_handle h);
 
+/* Queue one grain sample of a film lattice (one created with a grain table):
+ * for every grain g, m_g = |sum_{i in g} S_i| / N_g, the magnetisation length
+ * of the grain alone (Sec. 4: each grain contributes its own Bloch term to
+ * Eq. 8, with weight N_g / N for columnar grains).  Asynchronous on the
+ * lattice's stream.  Errors: MC_ERR_ARG (null handle, no grain table). */
+MC_API int mc_grain_sample(mc_handle h);
+
+/* <m_g> over the grain samples since create or the last mc_reset_stats, for
+ * g = 0 .. n_grains - 1 (the ids of the grain table).  out: caller-owned,
+ * len >= n_grains doubles; *n_samples (may be null) receives the number of
+ * samples (0: out is all zero).  Synchronises.  Errors: MC_ERR_ARG (null
+ * handle or out, no grain table, len too small). */
+MC_API int mc_grain_magnetization(mc_handle h, double* out, int len, int64_t* n_samples);
+
 /* Copy up to max of the most recent per-sweep samples (oldest first) into
  * out; *n receives the count.  Synchronises. */
 MC_API int mc_samples(mc_handle h, mc_sample* out, int max, int* n);
 
-/* Zero the accumulators, the sample ring and the profile sums. */
+/* Zero the accumulators, the sample ring, the profile sums and the grain
+ * samples. */
 MC_API int mc_reset_stats(mc_handle h);
 
 /* Spins as FP64 host arrays of n = N sites (site order x + Lx(y + Ly z)).

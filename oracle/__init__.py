@@ -129,6 +129,17 @@ def fixed_sum(t) -> float:
     return lib().or_fixed_sum(_p(a, C.c_double), a.size)
 
 
+def grain_magnetization(spins, grain_id, n_grains: int) -> np.ndarray:
+    """Magnetisation length of every grain of a film (Sec. 4: each grain
+    contributes its own Bloch term to Eq. 8): m_g = |sum_{i in g} S_i| / N_g,
+    from (N, 3) spins and the per-site grain ids (site order)."""
+    S = np.asarray(spins, np.float64).reshape(-1, 3)
+    g = np.asarray(grain_id).reshape(-1)
+    M = np.stack([np.bincount(g, weights=S[:, a], minlength=n_grains) for a in range(3)], axis=1)
+    N = np.bincount(g, minlength=n_grains)
+    return np.linalg.norm(M, axis=1) / np.maximum(N, 1)
+
+
 def constraint_frame(theta_deg: float, phi_deg: float) -> np.ndarray:
     R = np.zeros(9)
     lib().or_constraint_frame(float(theta_deg), float(phi_deg), _p(R, C.c_double))

@@ -96,6 +96,8 @@ _SIGS = {
     "mc_anisotropy_scaling": (C.c_int, [C.c_void_p, _P(C.c_double)]),
     "mc_profile": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_double), C.c_int]),
     "mc_profile_sample": (C.c_int, [C.c_void_p]),
+    "mc_grain_sample": (C.c_int, [C.c_void_p]),
+    "mc_grain_magnetization": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_int, _P(C.c_int64)]),
     "mc_samples": (C.c_int, [C.c_void_p, _P(mc_sample), C.c_int, _P(C.c_int)]),
     "mc_reset_stats": (C.c_int, [C.c_void_p]),
     "mc_get_spins": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_size_t]),
@@ -266,6 +268,18 @@ def mc_profile(h, component: int, Lx: int) -> np.ndarray:
     out = np.zeros(Lx)
     _check(lib().mc_profile(h, int(component), _dp(out), Lx))
     return out
+
+
+def mc_grain_sample(h) -> None:
+    _check(lib().mc_grain_sample(h))
+
+
+def mc_grain_magnetization(h, n_grains: int):
+    """(<m_g> per grain as a numpy array, number of grain samples)."""
+    out = np.zeros(int(n_grains))
+    n = C.c_int64()
+    _check(lib().mc_grain_magnetization(h, _dp(out), int(n_grains), C.byref(n)))
+    return out, n.value
 
 
 def mc_samples(h, max_n: int) -> np.ndarray:

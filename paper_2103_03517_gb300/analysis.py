@@ -1,8 +1,9 @@
-"""Host analysis of the library's outputs for Sec. 3 of arXiv:2103.03517:
+"""Host analysis of the library's outputs for Sec. 3 and 4 of arXiv:2103.03517:
 the domain-wall width fit and the exchange stiffness of Eq. 5, the free-energy
 route dF(T) of Eq. 5, the m^k scaling exponent of Table I, the Bloch law of
-Eq. 3 and the transverse susceptibility of Eq. 7.  Plain numpy / scipy on the
-host; reduced units (J = 1, k_B = 1, mu_S = 1, lattice constant 1).
+Eq. 3, the transverse susceptibility of Eq. 7 and the weighted Bloch series of
+Eq. 8 for granular films.  Plain numpy / scipy on the host; reduced units
+(J = 1, k_B = 1, mu_S = 1, lattice constant 1).
 """
 from __future__ import annotations
 
@@ -11,7 +12,7 @@ import math
 import numpy as np
 
 __all__ = ["wall_model", "fit_wall", "exchange_stiffness", "free_energy_difference",
-           "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial"]
+           "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial", "multi_bloch_fit"]
 
 
 def wall_model(x, m, x0, delta, Lx=None):
@@ -126,3 +127,32 @@ def bloch_fit(T, m, T_max=None):
 def chi_perp_uniaxial(m, Ku_T, Ms0=1.0):
     """Eq. 7: transverse susceptibility below T_C, M_S(0) m^2 / (2 K_u(T))."""
     return float(Ms0) * np.asarray(m, np.float64) ** 2 / (2.0 * np.asarray(Ku_T, np.float64))
+
+
+def multi_bloch_fit(T, m, n_terms, tc_range=None, betas=None):
+    """Eq. 8: m(T) = sum_i w_i (1 - T/T_C,i)^beta_i with sum w_i = 1 (a term
+    is zero above its T_C,i), and the average Curie temperature T_C =
+    sum_i w_i T_C,i.  The paper fixes only the series; this fit places the
+    n_terms values T_C,i on an even grid over tc_range (default: from the
+    lowest T to 1.25 times the highest), gives every term one exponent beta
+    (the best of `betas`, default 0.15 .. 0.80 in steps of 0.01) and finds
+    the weights w_i >= 0 by non-negative least squares with the sum held to 1
+    by a heavily weighted extra row.  More terms refine the grid; the paper's
+    average converges once n_terms exceeds about 10.  Returns a dict: w, T_C,
+    beta, T_C_mean, rms (of the fit)."""
+    from scipy.optimize import nnls
+
+    T = np.asarray(T, np.float64)
+    m = np.asarray(m, np.float64)
+    lo, hi = tc_range if tc_range is not None else (float(T.min()), 1.25 * float(T.max()))
+    Tc = np.linspace(lo, hi, int(n_terms) + 1)[1:]
+    betas = np.round(np.arange(0.15, 0.8001, 0.01), 10) if betas is None else np.asarray(betas, np.float64)
+    lam = 1e3 * math.sqrt(T.size)
+    best = None
+    for b in betas:
+        X = np.clip(1.0 - T[:, None] / Tc[None, :], 0.0, None) ** b
+        w, _ = nnls(np.vstack([X, lam * np.ones(Tc.size)]), np.concatenate([m, [lam]]))
+        rms = float(np.sqrt(np.mean((X @ w - m) ** 2)))
+        if best is None or rms < best["rms"]:
+            best = {"w": w, "T_C": Tc, "beta": float(b), "T_C_mean": float(w @ Tc), "rms": rms}
+    return best

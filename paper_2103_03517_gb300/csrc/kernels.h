@@ -43,6 +43,8 @@ struct KernelSet {
     void (*xtal_pass)(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, int nb,
                       cudaStream_t s);
     void (*xtal_sample)(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, cudaStream_t s);
+    // One grain sample of a film lattice (ntiles site tiles, n_grains grains).
+    void (*grain_sample)(LatDev* L, uint32_t ntiles, int n_grains, cudaStream_t s);
     // Slice sums for the profile of one lattice.
     void (*profile)(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s);
     const char* name;

@@ -172,6 +172,12 @@ void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, 
     by_entries<XtalSample>(nb, L, ntiles, tiles_per_subset, s);
 }
 
+void grain_sample(LatDev* L, uint32_t ntiles, int n_grains, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(grain_sum_kernel<R, V>);
+    grain_sum_kernel<R, V><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles);
+    grain_finish_kernel<R><<<(n_grains + kBlock) / kBlock, kBlock, 0, s>>>(L);
+}
+
 void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
     const uint32_t threads = Lh * ((rows + 31) / 32);
     profile_kernel<R><<<(threads + kBlock - 1) / kBlock, kBlock, 0, s>>>(d);
@@ -180,7 +186,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, profile,
+    static const KernelSet k{colour_pass, row_pass, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, grain_sample, profile,
                              "f32"};
     return k;
 }

@@ -113,6 +113,10 @@ struct LatParams {
     double* ring;           // [ring_cap][kRingWords]
     int ring_cap;
     long long* profile;     // [3][Lx] fixed-point sums
+    int n_grains;           // films: grains of the grain table (0 without one)
+    long long* gsum;        // films: [n_grains][3] fixed-point spin sums of one grain sample
+    const int32_t* gsize;   // films: [n_grains] spins per grain
+    double* gacc;           // films: [n_grains + 1] sums over grain samples of |m_g|, then the count
     void* aos;              // constrained sweeps: [2][stride] (x, y, z, 0) copy of the
                             // spins (Spin4), written by mlong_kernel at the start of a run
                             // of constrained sweeps and kept in step by the pair passes;

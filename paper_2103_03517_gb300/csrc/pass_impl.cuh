@@ -1295,4 +1295,57 @@ __global__ void __launch_bounds__(kBlock) profile_kernel(LatDev* L) {
                       static_cast<unsigned long long>(to_fix(acc[xp][a])));
 }
 
+// ------------------------------------------------------------------------
+// One grain sample of a film (Sec. 4: every grain contributes its own Bloch
+// term to Eq. 8): the spins of each grain summed as fixed point, then
+// m_g = |sum S| / N_g added to the grain's accumulator.  Site tiles over
+// both colours; the lanes of a warp that hold the same grain pool their
+// values (one atomic per grain present in the warp).
+// ------------------------------------------------------------------------
+template <typename R, int V>
+__global__ void __launch_bounds__(kBlock) grain_sum_kernel(LatDev* L, uint32_t ntiles) {
+    const LatParams& p = L->p;
+    const WarpChunk wc = warp_chunk(ntiles);
+    const int lane = wc.lane;
+    const R* s = static_cast<const R*>(p.spins);
+    for (uint32_t tile = wc.begin; tile < wc.end; ++tile) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t q = tile * uint32_t(32 * V) + uint32_t(32 * v + lane);
+            for (int colour = 0; colour < 2; ++colour) {
+                const bool ok = q < p.Nc;
+                const int32_t g = ok ? __ldg(&p.grain[uint32_t(colour) * p.stride + q]) : -1;
+                const V3<R> S = ok ? load_spin(s, p.stride, colour, q) : V3<R>{R(0), R(0), R(0)};
+                const long long f[3] = {to_fix(double(S.x)), to_fix(double(S.y)), to_fix(double(S.z))};
+                const unsigned peers = __match_any_sync(0xffffffffu, g);
+                long long sum[3] = {0, 0, 0};
+                for (unsigned m = peers; m; m &= m - 1u) {
+                    const int src = __ffs(m) - 1;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) sum[a] += __shfl_sync(peers, f[a], src);
+                }
+                if (g >= 0 && lane == __ffs(peers) - 1)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(&p.gsum[3 * size_t(g) + a]),
+                                  static_cast<unsigned long long>(sum[a]));
+            }
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) grain_finish_kernel(LatDev* L) {
+    const LatParams& p = L->p;
+    const int g = int(blockIdx.x * blockDim.x + threadIdx.x);
+    if (g == 0) p.gacc[p.n_grains] += 1.0;
+    if (g >= p.n_grains) return;
+    double M[3];
+    for (int a = 0; a < 3; ++a) {
+        M[a] = double(p.gsum[3 * size_t(g) + a]) / kFixScale;
+        p.gsum[3 * size_t(g) + a] = 0;
+    }
+    p.gacc[g] += sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]) / double(p.gsize[g]);
+}
+
 }  // namespace mcgb

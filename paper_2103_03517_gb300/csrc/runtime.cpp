@@ -195,7 +195,11 @@ size_t lattice_bytes(const mc_desc* d) {
     b += align256(size_t(nsub) * 6 * stride * rs);
     if (nsub > 1) b += align256(sizeof(XtalNb) * kXtalMaxSub * kXtalMaxNb);
     if (d->bond_mask) b += align256(2 * stride);
-    if (d->grain_id) b += align256(2 * stride * 4) + align256(4 * size_t(std::max(d->n_grains, 1)) * rs);
+    if (d->grain_id) {
+        const size_t ng = size_t(std::max(d->n_grains, 1));
+        b += align256(2 * stride * 4) + align256(4 * ng * rs);
+        b += align256(3 * ng * 8) + align256(ng * 4) + align256((ng + 1) * 8);  // grain samples
+    }
     const int cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
     b += align256(size_t(cap) * kRingWords * 8);
     b += align256(3 * size_t(d->dims[0]) * 8);
@@ -433,7 +437,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
         p.bonds = reinterpret_cast<const uint8_t*>(take(2 * size_t(p.stride)));
         h->film_bonds.assign(din->bond_mask, din->bond_mask + p.N);
     }
-    std::vector<int32_t> hg;
+    std::vector<int32_t> hg, hgs;
     std::vector<char> hax;
     if (din->grain_id) {
         hg.assign(2 * size_t(p.stride), 0);
@@ -449,6 +453,12 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
             }
         }
         p.gaxis = take(4 * size_t(d->n_grains) * rs);
+        p.n_grains = d->n_grains;
+        hgs.assign(size_t(d->n_grains), 0);
+        for (long long i = 0; i < p.N; ++i) ++hgs[size_t(din->grain_id[i])];
+        p.gsum = reinterpret_cast<long long*>(take(3 * size_t(d->n_grains) * 8));
+        p.gsize = reinterpret_cast<const int32_t*>(take(size_t(d->n_grains) * 4));
+        p.gacc = reinterpret_cast<double*>(take((size_t(d->n_grains) + 1) * 8));
         h->film_grain.assign(din->grain_id, din->grain_id + p.N);
         h->film_axes.assign(din->grain_axis, din->grain_axis + 3 * size_t(d->n_grains));
     }
@@ -501,6 +511,10 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     if (!hg.empty()) {
         up(const_cast<int32_t*>(p.grain), hg.data(), hg.size() * 4);
         up(const_cast<void*>(p.gaxis), hax.data(), hax.size());
+        up(const_cast<int32_t*>(p.gsize), hgs.data(), hgs.size() * 4);
+        if (rc == MC_OK && (cudaMemsetAsync(p.gsum, 0, 3 * size_t(p.n_grains) * 8, h->stream) != cudaSuccess ||
+                            cudaMemsetAsync(p.gacc, 0, (size_t(p.n_grains) + 1) * 8, h->stream) != cudaSuccess))
+            rc = fail(MC_ERR_CUDA, "memset grain samples");
     }
     if (rc == MC_OK && cudaMemsetAsync(p.ring, 0, size_t(p.ring_cap) * kRingWords * 8, h->stream) != cudaSuccess)
         rc = fail(MC_ERR_CUDA, "memset ring");
@@ -850,6 +864,30 @@ MC_API int mc_profile(mc_handle h, int component, double* out, int len) {
     return MC_OK;
 }
 
+MC_API int mc_grain_sample(mc_handle h) {
+    if (!h) return fail(MC_ERR_ARG, "null handle");
+    if (!h->hp.n_grains) return fail(MC_ERR_ARG, "the lattice has no grain table");
+    cudaSetDevice(h->device);
+    kernel_set(h->hp.precision).grain_sample(h->d_lat, h->hp.nblocks_site, h->hp.n_grains, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "grain sample launch");
+    return MC_OK;
+}
+
+MC_API int mc_grain_magnetization(mc_handle h, double* out, int len, int64_t* n_samples) {
+    if (!h || !out) return fail(MC_ERR_ARG, "null argument");
+    if (!h->hp.n_grains) return fail(MC_ERR_ARG, "the lattice has no grain table");
+    if (len < h->hp.n_grains) return fail(MC_ERR_ARG, "out holds %d < %d grains", len, h->hp.n_grains);
+    cudaSetDevice(h->device);
+    std::vector<double> acc(size_t(h->hp.n_grains) + 1);
+    CK(cudaMemcpyAsync(acc.data(), h->hp.gacc, acc.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double n = acc.back();
+    for (int g = 0; g < h->hp.n_grains; ++g) out[g] = n > 0 ? acc[size_t(g)] / n : 0.0;
+    if (n_samples) *n_samples = int64_t(n);
+    return MC_OK;
+}
+
 MC_API int mc_samples(mc_handle h, mc_sample* out, int max, int* n) {
     if (!h || !n || (max > 0 && !out)) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(h->device);
@@ -885,6 +923,7 @@ MC_API int mc_reset_stats(mc_handle h) {
     CK(cudaMemsetAsync(&d->st.ring_count, 0, sizeof(long long), h->stream));
     CK(cudaMemsetAsync(&d->st.prof_samples, 0, sizeof(long long), h->stream));
     CK(cudaMemsetAsync(h->hp.profile, 0, 3 * size_t(h->hp.Lx) * 8, h->stream));
+    if (h->hp.n_grains) CK(cudaMemsetAsync(h->hp.gacc, 0, (size_t(h->hp.n_grains) + 1) * 8, h->stream));
     return MC_OK;
 }
 
@@ -941,7 +980,7 @@ MC_API int mc_get_theta(mc_handle h, int* theta_deg, int64_t* sweeps_done) {
 }
 
 // ------------------------------------------------------------- checkpoint
-static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '3'};
+static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '4'};
 
 MC_API int mc_save(mc_handle h, const char* path) {
     if (!h || !path) return fail(MC_ERR_ARG, "null argument");
@@ -954,8 +993,10 @@ MC_API int mc_save(mc_handle h, const char* path) {
     if (rc) return rc;
     std::vector<double> ring(size_t(h->hp.ring_cap) * kRingWords);
     std::vector<long long> prof(3 * size_t(h->hp.Lx));
+    std::vector<double> gacc(h->hp.n_grains ? size_t(h->hp.n_grains) + 1 : 0);
     CK(cudaMemcpy(ring.data(), h->hp.ring, ring.size() * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(prof.data(), h->hp.profile, prof.size() * 8, cudaMemcpyDeviceToHost));
+    if (!gacc.empty()) CK(cudaMemcpy(gacc.data(), h->hp.gacc, gacc.size() * 8, cudaMemcpyDeviceToHost));
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(MC_ERR_IO, "cannot open %s for writing", path);
     mc_desc d = h->desc;
@@ -972,6 +1013,7 @@ MC_API int mc_save(mc_handle h, const char* path) {
     if (ok && na) ok = std::fwrite(h->film_axes.data(), 8, na, f) == na;
     ok = ok && std::fwrite(ring.data(), 8, ring.size(), f) == ring.size() &&
          std::fwrite(prof.data(), 8, prof.size(), f) == prof.size() &&
+         std::fwrite(gacc.data(), 8, gacc.size(), f) == gacc.size() &&
          std::fwrite(spins.data(), 1, spins.size(), f) == spins.size();
     ok = (std::fclose(f) == 0) && ok;
     return ok ? MC_OK : fail(MC_ERR_IO, "write to %s failed", path);
@@ -1009,9 +1051,11 @@ MC_API int mc_load(const char* path, mc_handle* out) {
     if (rc) { std::fclose(f); return rc; }
     std::vector<double> ring(size_t(h->hp.ring_cap) * kRingWords);
     std::vector<long long> prof(3 * size_t(h->hp.Lx));
+    std::vector<double> gacc(h->hp.n_grains ? size_t(h->hp.n_grains) + 1 : 0);
     std::vector<char> spins(mc_state_bytes(h));
     ok = std::fread(ring.data(), 8, ring.size(), f) == ring.size() &&
          std::fread(prof.data(), 8, prof.size(), f) == prof.size() &&
+         std::fread(gacc.data(), 8, gacc.size(), f) == gacc.size() &&
          std::fread(spins.data(), 1, spins.size(), f) == spins.size();
     std::fclose(f);
     if (!ok) { mc_destroy(h); return fail(MC_ERR_IO, "%s is truncated", path); }
@@ -1020,6 +1064,9 @@ MC_API int mc_load(const char* path, mc_handle* out) {
     if (!rc && cudaMemcpy(&h->d_lat->st, &st, sizeof st, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
     if (!rc && cudaMemcpy(h->hp.ring, ring.data(), ring.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
     if (!rc && cudaMemcpy(h->hp.profile, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (!rc && !gacc.empty() &&
+        cudaMemcpy(h->hp.gacc, gacc.data(), gacc.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MC_ERR_CUDA;
     if (!rc) rc = mc_import_state(h, spins.data(), spins.size());
     if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = MC_ERR_CUDA;
     if (rc) { mc_destroy(h); return rc == MC_ERR_CUDA ? fail(rc, "restoring %s failed", path) : rc; }

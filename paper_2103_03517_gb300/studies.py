@@ -1,8 +1,9 @@
-"""Sec. 3 studies of arXiv:2103.03517 driven through the library's public API:
-the exchange stiffness A(T) by the Bloch-wall method (Eq. 5) with K(T) from
-the easy-axis estimator (Eq. 4), and its low-temperature m^k exponent as a
-function of K/J (Table I).  Every sweep runs in libmc; the fits are host
-post-processing (``analysis``).
+"""Studies of arXiv:2103.03517 driven through the library's public API: the
+exchange stiffness A(T) by the Bloch-wall method (Sec. 3, Eq. 5) with K(T)
+from the easy-axis estimator (Eq. 4) and its low-temperature m^k exponent as a
+function of K/J (Table I); the average Curie temperature of granular films
+from the weighted Bloch series of Eq. 8 (Sec. 4).  Every sweep and sample runs
+in libmc; the fits are host post-processing (``analysis``).
 """
 from __future__ import annotations
 
@@ -14,7 +15,7 @@ import numpy as np
 from . import _mc as mc
 from . import analysis as an
 
-__all__ = ["exchange_stiffness_study", "bloch_wall_spins"]
+__all__ = ["exchange_stiffness_study", "bloch_wall_spins", "film_curie_study"]
 
 
 def bloch_wall_spins(dims, K, J=1.0):
@@ -127,3 +128,65 @@ def exchange_stiffness_study(K_over_J, temps, wall_dims=(256, 64, 64), uniform_d
             exponents[K] = (k, k_err)
     updates = len(points) * (n_eq + blocks * every) * (int(np.prod(wall_dims)) + int(np.prod(uniform_dims)))
     return {"rows": rows, "exponents": exponents, "updates": updates, "seconds": seconds}
+
+
+def film_curie_study(dims, grain_id, bond_mask, grain_axis, temps, K_u=0.02, n_eq=1000, n_meas=2000, every=20,
+                     n_terms=20, seed=1, precision=mc.MC_FP32, stream=None, device=0):
+    """m(T) of a granular film and its average Curie temperature (Sec. 4,
+    Eq. 8).  The film (x, y periodic, z open; grain tables as for
+    mc_create_ex: bonds only inside a grain, one uniaxial easy axis per
+    grain) is run independently at every temperature, all runs as one group;
+    every `every` measured sweeps each run takes a grain sample.  The film's
+    m(T) = sum_g w_g <m_g>(T), w_g = N_g / N (columnar grains: weight by
+    area), and the weighted Bloch series of Eq. 8 with n_terms terms gives
+    T_C_mean.  With grain_id None the film is continuous (one grain, no bond
+    mask, easy axis z): m(T) = <|m|> and Eq. 3 gives its T_C.  Returns a dict:
+    T, m, the fit, spin-updates and wall time."""
+    temps = [float(t) for t in temps]
+    N = int(np.prod(dims))
+    grains = grain_id is not None
+    if grains:
+        grain_id = np.ascontiguousarray(grain_id, np.int32)
+        ng = int(grain_id.max()) + 1
+        w = np.bincount(grain_id, minlength=ng) / float(N)
+    hs = []
+    try:
+        for i, T in enumerate(temps):
+            kw = dict(bond_mask=bond_mask, grain_id=grain_id, grain_axis=grain_axis) if grains else {}
+            hs.append(mc.mc_create_ex(mc.make_desc(dims, K_u=K_u, T=T, seed=seed + i, precision=precision,
+                                                   boundary=(mc.MC_PERIODIC, mc.MC_PERIODIC, mc.MC_OPEN),
+                                                   ring_capacity=16, sample_torque=0, stream=stream,
+                                                   device=device, **kw)))
+        g = mc.mc_group_create(hs)
+        t0 = time.perf_counter()
+        try:
+            mc.mc_group_sweep(g, n_eq)
+            for h in hs:
+                mc.mc_reset_stats(h)
+            blocks = max(1, n_meas // every)
+            for _ in range(blocks):
+                mc.mc_group_sweep(g, every, measure=True)
+                if grains:
+                    for h in hs:
+                        mc.mc_grain_sample(h)
+            mc.mc_group_sync(g)
+        finally:
+            mc.mc_group_destroy(g)
+        if grains:
+            m = np.array([float(w @ mc.mc_grain_magnetization(h, ng)[0]) for h in hs])
+        else:
+            m = np.array([float(mc.mc_measure(h).ml) for h in hs])
+        seconds = time.perf_counter() - t0
+    finally:
+        for h in hs:
+            mc.mc_destroy(h)
+    T = np.array(temps)
+    if grains:
+        fit = an.multi_bloch_fit(T, m, n_terms)
+        fit = {"T_C_mean": fit["T_C_mean"], "beta": fit["beta"], "rms": fit["rms"],
+               "w": fit["w"].tolist(), "T_C": fit["T_C"].tolist()}
+    else:  # Eq. 3 over the ordered range (m above 0.3, below it the finite film's tail)
+        tc, beta, err = an.bloch_fit(T[m > 0.3], m[m > 0.3])
+        fit = {"T_C": tc, "beta": beta, "errors": err.tolist()}
+    updates = len(temps) * (n_eq + blocks * every) * N
+    return {"T": temps, "m": m.tolist(), "fit": fit, "updates": updates, "seconds": seconds}

@@ -79,3 +79,27 @@ def test_transverse_susceptibility_low_temperature_single_spin():
     w = np.exp(K * (np.cos(th) ** 2 - 1) / T) * np.sin(th)
     sx2 = np.trapezoid(0.5 * np.sin(th) ** 2 * w, th) / np.trapezoid(w, th)  # <cos^2 phi> = 1/2
     assert abs((sx2 / T) / an.chi_perp_uniaxial(1.0, K) - 1) < 5e-3
+
+
+def test_multi_bloch_fit_recovers_one_and_two_terms():
+    """Eq. 8 with the T_C grid holding the true values: one Bloch law comes
+    back as one term (T_C, beta exact), two as their weights."""
+    T = np.linspace(0.05, 1.25, 40)
+    grid = (0.1, 1.6)  # 15 terms: 0.2, 0.3, ..., 1.6
+    f = an.multi_bloch_fit(T, (1 - T / 1.3) ** 0.35, 15, tc_range=grid)
+    assert abs(f["T_C_mean"] - 1.3) < 1e-6 and abs(f["beta"] - 0.35) < 1e-9 and f["rms"] < 1e-6
+    m = 0.6 * np.clip(1 - T / 1.0, 0, None) ** 0.35 + 0.4 * np.clip(1 - T / 1.4, 0, None) ** 0.35
+    f = an.multi_bloch_fit(T, m, 15, tc_range=grid)
+    assert abs(f["T_C_mean"] - 1.16) < 1e-6 and abs(f["w"].sum() - 1) < 1e-6
+
+
+def test_multi_bloch_fit_converges_with_terms():
+    """T_C spread uniformly over [0.9, 1.3] (m(T) by quadrature over the
+    spread): the average of Eq. 8 approaches 1.1 as the number of terms
+    grows, and settles (20 vs 40 terms)."""
+    T = np.linspace(0.05, 1.35, 60)
+    tcs = np.linspace(0.9, 1.3, 4001)
+    m = np.mean(np.clip(1 - T[:, None] / tcs[None, :], 0, None) ** 0.35, axis=1)
+    f20 = an.multi_bloch_fit(T, m, 20, tc_range=(0.5, 1.5))
+    f40 = an.multi_bloch_fit(T, m, 40, tc_range=(0.5, 1.5))
+    assert abs(f40["T_C_mean"] - 1.1) < 0.01 and abs(f20["T_C_mean"] - f40["T_C_mean"]) < 0.01

@@ -302,3 +302,20 @@ def test_profile_is_the_slice_average():
 def workloads_random(n, seed):
     import workloads
     return workloads.random_spins(n, seed)
+
+
+# ----------------------------------------------- grain magnetisation (Sec. 4)
+def test_grain_magnetization_closed_forms():
+    """m_g = |sum S| / N_g: parallel spins give 1, a grain of two antiparallel
+    halves gives 0, and random spins equal a brute-force loop."""
+    rng = np.random.default_rng(5)
+    gid = np.array([0, 0, 1, 1, 1, 1, 2, 2, 2], np.int32)
+    S = np.zeros((9, 3))
+    S[0:2] = (0.0, 0.6, 0.8)
+    S[2:4] = (0.0, 0.0, 1.0)
+    S[4:6] = (0.0, 0.0, -1.0)
+    v = rng.standard_normal((3, 3))
+    S[6:9] = v / np.linalg.norm(v, axis=1, keepdims=True)
+    m = oracle.grain_magnetization(S, gid, 3)
+    assert abs(m[0] - 1.0) < 1e-15 and abs(m[1]) < 1e-15
+    assert abs(m[2] - np.linalg.norm(S[6] + S[7] + S[8]) / 3) < 1e-15
