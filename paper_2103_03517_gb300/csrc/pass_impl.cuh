@@ -944,11 +944,13 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 }
 
 // ------------------------------------------------------------------------
-// Constrained pair pass of Table A2 (one lane per pair), batched, warp tiles
-// of 32 pairs (pair_move below, pair_pass_kernel after it).  Pairs are (pi(2p), pi(2p+1)) of the colour's shuffled
-// indices; the cone move is made on i in the frame whose x-axis is e_C, j
-// compensates the transverse components, x'_j = sign(x_j) sqrt(|S_j|^2 -
-// y'_j^2 - z'_j^2).  The pair is accepted iff
+// Constrained pair pass of Table A2 (one lane per pair), batched
+// (pair_move below, pair_pass_kernel after it).  Pairs are (pi(2p),
+// pi(2p+1)) of the colour's shuffled indices, taken 32 per warp tile in pair
+// order or led by the sites of 64-site tiles in site order; the cone move is
+// made on i in the frame whose x-axis is e_C, j compensates the transverse
+// components, x'_j = sign(x_j) sqrt(|S_j|^2 - y'_j^2 - z'_j^2).  The pair is
+// accepted iff
 // P < (M'_L/M_L)^2 |x_j / x'_j| exp(-(dE_i + dE_j)/T); M_L is the exact sum
 // over the state at the start of the sweep, fixed for the whole iteration
 // (mlong_kernel sums it at the start of a run of sweeps; after that every
