@@ -267,6 +267,10 @@ def gpu_arm(args, cfg):
                                            device=local))
               for s in specs]
         g = mc.mc_group_create(hs)
+        # launch shapes picked by the autotuner (the chains are left unchanged)
+        tuned = mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
+        cfg["autotuned"] = {"row_kernel_blocks_per_sm": [3, 2][tuned["row"]],
+                            "ms_per_sweep": [round(x, 4) for x in tuned["row_ms"][:2]]}
         mc.mc_group_sweep(g, args.warmup, measure=True)
         torch.cuda.synchronize()
         if world > 1:
@@ -402,6 +406,7 @@ def constrained(mc, torch, stream, dev):
     th = [r[1] for r in runs]
     ph = [r[2] for r in runs]
     mc.mc_group_constrained_sweep(g, th, ph, 4, measure=True)
+    tuned = mc.mc_group_autotune(g, 2, mc.MC_TUNE_CONSTRAINED)
     torch.cuda.synchronize()
     a.record(stream)
     mc.mc_group_constrained_sweep(g, th, ph, sweeps, measure=True)
@@ -410,7 +415,11 @@ def constrained(mc, torch, stream, dev):
     nc = sum(r[0].N for r in runs)
     out["constrained"] = {"value": nc * sweeps / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
                           "workload": "80 x 64^3 constrained runs (theta_c 0..90, phi_c 0/45, 4 T), FP32, "
-                                      "pair halves counted as updates"}
+                                      "pair halves counted as updates",
+                          "autotuned": {"field_tiles_per_step": [4, 8, 2][tuned["field"]],
+                                        "pair_tiles_per_step": [4, 8, 2][tuned["pair"]],
+                                        "field_ms": [round(x, 4) for x in tuned["field_ms"][:3]],
+                                        "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:3]]}}
     mc.mc_group_destroy(g)
     for h in hs:
         mc.mc_destroy(h)

@@ -310,6 +310,41 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
 
 MC_API int mc_group_sync(mc_group_handle g);
 
+/* ------------------------------------------------------------- autotuner */
+
+/* Launch-shape autotuning of the batched sweeps (the block and tile shapes of
+ * a persistent launch).  Candidates, in the order of the report's arrays:
+ *   row:   FP32 row kernel, minimum resident blocks per SM (so registers per
+ *          thread): all-periodic lattices {3, 2}, boundaries and films {2, 3};
+ *   field: constrained neighbour-field kernel, tiles per grid-stride step
+ *          {4, 8, 2};
+ *   pair:  constrained pair pass, the same {4, 8, 2}.
+ * what: MC_TUNE_SWEEP tunes the row kernel on sweeps of Table A1,
+ * MC_TUNE_CONSTRAINED the field and pair kernels on sweeps of Table A2 (with
+ * each lattice's present constraint direction; a lattice that has not run a
+ * constrained sweep yet gets its packed copy here), both or-ed together.
+ * Each candidate runs 1 + sweeps sweeps, the last `sweeps` timed with CUDA
+ * events; knobs are tuned one after the other, each at the best choice of the
+ * ones before.  The lattices' spins and device state (theta, sweep counter,
+ * accumulators) are saved first and restored after, so the chains continue as
+ * if no tuning had run; the chosen shapes apply to later sweeps (captured
+ * graphs are rebuilt).  Synchronises.  out (may be null) receives the choices
+ * and the mean ms per sweep of every candidate tried (0 where not tried).
+ * Errors: MC_ERR_ARG (null group, sweeps < 1, what empty), MC_ERR_NOMEM (no
+ * room for the saved state), MC_ERR_CUDA. */
+#define MC_TUNE_SWEEP 1
+#define MC_TUNE_CONSTRAINED 2
+typedef struct mc_tune_report {
+    int row, field, pair;          /* chosen candidate of each knob */
+    int pad;
+    double row_ms[4], field_ms[4], pair_ms[4];
+} mc_tune_report;
+MC_API int mc_group_autotune(mc_group_handle g, int sweeps, int what, mc_tune_report* out);
+
+/* The same for one lattice swept alone (mc_sweep, mc_constrained_sweep).
+ * Crystal lattices (bcc, fcc, hcp) have no tunable shape: MC_ERR_ARG. */
+MC_API int mc_autotune(mc_handle h, int sweeps, int what, mc_tune_report* out);
+
 /* ------------------------------------------------------------- serving */
 
 typedef struct mc_server_desc {

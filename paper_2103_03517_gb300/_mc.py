@@ -22,6 +22,7 @@ MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
 MC_PATH_AUTO, MC_PATH_GENERAL = 0, 1
 MC_SC, MC_BCC, MC_FCC, MC_HCP = 0, 1, 2, 3
 MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
+MC_TUNE_SWEEP, MC_TUNE_CONSTRAINED = 1, 2
 MC_JOB_SWEEP, MC_JOB_CONSTRAINED = 0, 1
 
 
@@ -57,6 +58,15 @@ class mc_observables(C.Structure):
             v = getattr(self, name)
             out[name] = list(v) if hasattr(v, "__len__") else v
         return out
+
+
+class mc_tune_report(C.Structure):
+    _fields_ = [("row", C.c_int), ("field", C.c_int), ("pair", C.c_int), ("pad", C.c_int),
+                ("row_ms", C.c_double * 4), ("field_ms", C.c_double * 4), ("pair_ms", C.c_double * 4)]
+
+    def asdict(self):
+        return {"row": self.row, "field": self.field, "pair": self.pair, "row_ms": list(self.row_ms),
+                "field_ms": list(self.field_ms), "pair_ms": list(self.pair_ms)}
 
 
 class mc_sample(C.Structure):
@@ -114,6 +124,8 @@ _SIGS = {
     "mc_group_constrained_sweep": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double), C.c_int, C.c_int]),
     "mc_group_time_passes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
     "mc_group_sync": (C.c_int, [C.c_void_p]),
+    "mc_group_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
+    "mc_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
     "mc_server_create": (C.c_int, [_P(mc_server_desc), _P(C.c_void_p)]),
     "mc_server_destroy": (C.c_int, [C.c_void_p]),
     "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
@@ -355,6 +367,20 @@ def mc_group_constrained_sweep(g, theta_c_deg, phi_c_deg, n_sweeps: int, measure
     th = np.ascontiguousarray(theta_c_deg, dtype=np.float64)
     ph = np.ascontiguousarray(phi_c_deg, dtype=np.float64)
     _check(lib().mc_group_constrained_sweep(g, _dp(th), _dp(ph), int(n_sweeps), int(bool(measure))))
+
+
+def mc_group_autotune(g, sweeps: int = 4, what: int = MC_TUNE_SWEEP | MC_TUNE_CONSTRAINED) -> dict:
+    """Autotune the group's launch shapes (chains unchanged); returns the report."""
+    r = mc_tune_report()
+    _check(lib().mc_group_autotune(g, int(sweeps), int(what), C.byref(r)))
+    return r.asdict()
+
+
+def mc_autotune(h, sweeps: int = 4, what: int = MC_TUNE_SWEEP | MC_TUNE_CONSTRAINED) -> dict:
+    """Autotune the launch shapes of one lattice swept alone; returns the report."""
+    r = mc_tune_report()
+    _check(lib().mc_autotune(h, int(sweeps), int(what), C.byref(r)))
+    return r.asdict()
 
 
 def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):

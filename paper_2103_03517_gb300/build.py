@@ -29,6 +29,7 @@ SOURCES = {
     "kernels_f32.cu": ["--use_fast_math"],
     "runtime.cpp": [],
     "groups.cpp": [],
+    "tune.cpp": [],
     "server.cpp": [],
     "noalloc.cu": [],
 }

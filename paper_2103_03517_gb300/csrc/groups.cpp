@@ -184,6 +184,16 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
     return MC_OK;
 }
 
+MC_API int mc_group_autotune(mc_group_handle g, int sweeps, int what, mc_tune_report* out) {
+    if (!g) return fail(MC_ERR_ARG, "null group");
+    cudaSetDevice(g->device);
+    NvtxRange range("mc_group_autotune");
+    const int rc = autotune(g->precision, g->ls, g->lats, g->cone, sweeps, what, g->stream, out);
+    if (rc) return rc;
+    destroy_graphs(g->graphs);  // captured with the old shapes
+    return MC_OK;
+}
+
 MC_API int mc_group_sync(mc_group_handle g) {
     if (!g) return fail(MC_ERR_ARG, "null group");
     cudaSetDevice(g->device);

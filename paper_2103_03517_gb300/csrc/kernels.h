@@ -7,6 +7,17 @@
 
 namespace mcgb {
 
+// Launch shapes the autotuner chooses among: an index into each kernel's
+// candidate list (0 = the default, measured best on the batched workloads).
+//   row:   FP32 row kernel, minimum resident blocks per SM (registers per
+//          thread): all-periodic {3, 2}, boundaries and films {2, 3};
+//   pair:  pair pass, consecutive tiles per grid-stride step {4, 8, 2};
+//   field: neighbour-field kernel, the same {4, 8, 2}.
+constexpr int kRowShapes = 2, kPairShapes = 3, kFieldShapes = 3;
+struct LaunchShape {
+    int row = 0, pair = 0, field = 0;
+};
+
 struct KernelSet {
     // Table A1 colour pass over the lattices of g (ntiles = warp tiles of the
     // launch; the launcher sizes a persistent grid from the occupancy).
@@ -17,16 +28,16 @@ struct KernelSet {
     // per lane); gen = 0: all axes periodic, no film tables; gen = 1: any
     // boundaries and film tables.  Null in the FP64 set.
     void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
-                     cudaStream_t s);
+                     int shape, cudaStream_t s);
     // Table A2 pair pass; leader != 0 takes the pairs in site order
     // (LatParams::pair_leader).
-    void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader,
+    void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape,
                       cudaStream_t s);
     // End of an unmeasured constrained sweep of every lattice of g.
     void (*sweep_end)(const GroupArgs& g, cudaStream_t s);
     // Neighbour field of every site of the given colour into LatParams::pfield
     // (site tiles), before that colour's pair pass.
-    void (*pair_field)(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s);
+    void (*pair_field)(const GroupArgs& g, uint32_t ntiles, int colour, int shape, cudaStream_t s);
     // Zero M_L and its carried change of every lattice of g (before mlong).
     void (*ml_reset)(const GroupArgs& g, cudaStream_t s);
     // Exact M_L of every lattice of g (site tiles).
@@ -65,6 +76,7 @@ struct LaunchSet {
     LatDev* xtal = nullptr;
     int nsub = 1;
     int xnb_max = 0;  // most neighbour entries of its sub-lattices
+    LaunchShape shape;  // autotuned launch shapes
 };
 
 const KernelSet& kernels_f64();

@@ -66,25 +66,32 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
-template <int MEASURE, int GEN>
+template <int B, int MEASURE, int GEN>
 void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
-    constexpr int B = GEN ? MINB_GEN : MINB;
     static const uint32_t cap = resident_blocks(row_pass_kernel<B, MEASURE, GEN>);
     row_pass_kernel<B, MEASURE, GEN><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
 }
 
-template <int GEN>
-void row_pass_g(const GroupArgs& g, uint32_t ntiles, const R* c, int colour, int measure, cudaStream_t s) {
-    if (measure >= 2) row_pass_t<2, GEN>(g, ntiles, c, colour, s);
-    else if (measure == 1) row_pass_t<1, GEN>(g, ntiles, c, colour, s);
-    else row_pass_t<0, GEN>(g, ntiles, c, colour, s);
+// launch shape 0: the default blocks per SM of the instance; 1: the other candidate
+template <int GEN, int B0, int B1>
+void row_pass_g(const GroupArgs& g, uint32_t ntiles, const R* c, int colour, int measure, int shape,
+                cudaStream_t s) {
+    if (shape == 1) {
+        if (measure >= 2) row_pass_t<B1, 2, GEN>(g, ntiles, c, colour, s);
+        else if (measure == 1) row_pass_t<B1, 1, GEN>(g, ntiles, c, colour, s);
+        else row_pass_t<B1, 0, GEN>(g, ntiles, c, colour, s);
+    } else {
+        if (measure >= 2) row_pass_t<B0, 2, GEN>(g, ntiles, c, colour, s);
+        else if (measure == 1) row_pass_t<B0, 1, GEN>(g, ntiles, c, colour, s);
+        else row_pass_t<B0, 0, GEN>(g, ntiles, c, colour, s);
+    }
 }
 
-void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
+void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen, int shape,
               cudaStream_t s) {
     const R* c = static_cast<const R*>(cone);
-    if (gen) row_pass_g<1>(g, ntiles, c, colour, measure, s);
-    else row_pass_g<0>(g, ntiles, c, colour, measure, s);
+    if (gen) row_pass_g<1, MINB_GEN, MINB_GEN + 1>(g, ntiles, c, colour, measure, shape, s);
+    else row_pass_g<0, MINB, MINB - 1>(g, ntiles, c, colour, measure, shape, s);
 }
 
 template <int GEN>
@@ -99,27 +106,44 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
     else row_sample_g<0>(g, ntiles, s);
 }
 
-template <bool LEADER>
+template <bool LEADER, int C>
 void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, cudaStream_t s) {
     constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
-    constexpr int C = LEADER ? kPairChunkLead : kPairChunk;
     static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER>);
     pair_pass_kernel<R, B, C, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, cudaStream_t s) {
-    if (leader) pair_pass_t<true>(g, ntiles, cone, colour, s);
-    else pair_pass_t<false>(g, ntiles, cone, colour, s);
+// launch shapes: tiles per grid-stride step {default, 8, 2}
+template <bool LEADER>
+void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int shape, cudaStream_t s) {
+    constexpr int C0 = LEADER ? kPairChunkLead : kPairChunk;
+    if (shape == 1) pair_pass_t<LEADER, 8>(g, ntiles, cone, colour, s);
+    else if (shape == 2) pair_pass_t<LEADER, 2>(g, ntiles, cone, colour, s);
+    else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, s);
+}
+
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape,
+               cudaStream_t s) {
+    if (leader) pair_pass_s<true>(g, ntiles, cone, colour, shape, s);
+    else pair_pass_s<false>(g, ntiles, cone, colour, shape, s);
 }
 
 void sweep_end(const GroupArgs& g, cudaStream_t s) {
     sweep_end_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
 }
 
-void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, kFieldChunk>);
-    pair_field_kernel<R, V, kFieldChunk><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+template <int C>
+void pair_field_t(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, C>);
+    pair_field_kernel<R, V, C><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+}
+
+// launch shapes: tiles per grid-stride step {default, 8, 2}
+void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, int shape, cudaStream_t s) {
+    if (shape == 1) pair_field_t<8>(g, ntiles, colour, s);
+    else if (shape == 2) pair_field_t<2>(g, ntiles, colour, s);
+    else pair_field_t<kFieldChunk>(g, ntiles, colour, s);
 }
 
 void ml_reset(const GroupArgs& g, cudaStream_t s) {

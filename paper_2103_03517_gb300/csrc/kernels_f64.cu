@@ -45,20 +45,38 @@ void colour_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     else colour_pass_t<0>(g, ntiles, c, colour, s);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, cudaStream_t s) {
-    (void)leader;  // FP64 lattices always take pair order (LatParams::pair_leader)
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, kPairChunk, false>);
-    pair_pass_kernel<R, 1, kPairChunk, false><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
-        g, ntiles, static_cast<const R*>(cone), colour);
+template <int C>
+void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, 1, C, false>);
+    pair_pass_kernel<R, 1, C, false><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, static_cast<const R*>(cone),
+                                                                           colour);
+}
+
+// launch shapes: tiles per grid-stride step {default, 8, 2}; FP64 lattices
+// always take pair order (LatParams::pair_leader)
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape,
+               cudaStream_t s) {
+    (void)leader;
+    if (shape == 1) pair_pass_t<8>(g, ntiles, cone, colour, s);
+    else if (shape == 2) pair_pass_t<2>(g, ntiles, cone, colour, s);
+    else pair_pass_t<kPairChunk>(g, ntiles, cone, colour, s);
 }
 
 void sweep_end(const GroupArgs& g, cudaStream_t s) {
     sweep_end_kernel<R><<<(g.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g);
 }
 
-void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, 4>);
-    pair_field_kernel<R, V, 4><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+template <int C>
+void pair_field_t(const GroupArgs& g, uint32_t ntiles, int colour, cudaStream_t s) {
+    static const uint32_t cap = resident_blocks(pair_field_kernel<R, V, C>);
+    pair_field_kernel<R, V, C><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, colour);
+}
+
+// launch shapes: tiles per grid-stride step {4, 8, 2}
+void pair_field(const GroupArgs& g, uint32_t ntiles, int colour, int shape, cudaStream_t s) {
+    if (shape == 1) pair_field_t<8>(g, ntiles, colour, s);
+    else if (shape == 2) pair_field_t<2>(g, ntiles, colour, s);
+    else pair_field_t<4>(g, ntiles, colour, s);
 }
 
 void ml_reset(const GroupArgs& g, cudaStream_t s) {

@@ -559,6 +559,7 @@ LaunchSet single_launch_set(mc_lattice* h) {
         ls.nt_pairs = h->hp.nblocks_pair;
     }
     ls.sample_level = h->hp.sample_torque ? 2 : 1;
+    ls.shape = h->shape;
     if (h->hp.nsub > 1) {
         ls.xtal = h->d_lat;
         ls.nsub = h->hp.nsub;
@@ -594,8 +595,8 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto colour_pass = [&](int colour, int meas) {
-        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, 0, s);
-        if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, s);
+        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, 0, ls.shape.row, s);
+        if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, ls.shape.row, s);
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
     if (ls.xtal) {  // bcc / fcc: the 2 nsub sub-sets in turn, then the sample
@@ -623,10 +624,11 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
                 k.mlong(ls.all, ls.nt_all, s);
             }
             for (int colour = 0; colour < 2; ++colour) {
-                k.pair_field(ls.all, ls.nt_all, colour, s);
+                k.pair_field(ls.all, ls.nt_all, colour, ls.shape.field, s);
                 timed([&] {
-                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, s);
-                    if (ls.nt_pairs_lead) k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, s);
+                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, ls.shape.pair, s);
+                    if (ls.nt_pairs_lead)
+                        k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, ls.shape.pair, s);
                 });
             }
             if (!measure) k.sweep_end(ls.all, s);  // a measured sweep ends in its sample

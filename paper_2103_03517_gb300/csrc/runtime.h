@@ -41,6 +41,7 @@ struct mc_lattice {
     uint32_t* d_group_start_pair = nullptr;
     void* d_aos = nullptr;        // packed spin copy of constrained sweeps (LatParams::aos)
     mcgb::SweepGraphs graphs;     // sweeps of the lattice alone
+    mcgb::LaunchShape shape;      // autotuned launch shapes of the lattice alone
     const void* cone = nullptr;   // c(theta) table of the precision
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;
@@ -68,6 +69,9 @@ int read_state(mc_lattice* h, LatState* st);
 int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* cone, int n, int measure,
                bool constrained, cudaStream_t s);
 void destroy_graphs(SweepGraphs& gr);
+LaunchSet single_launch_set(mc_lattice* h);
+int autotune(int precision, LaunchSet& ls, const std::vector<mc_lattice*>& lats, const void* cone, int sweeps,
+             int what, cudaStream_t s, mc_tune_report* out);
 int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
 
