@@ -9,7 +9,7 @@ no flush is needed between steps), advanced by one graph-replayed launch per
 colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--side all|none|fp64|constrained|anisotropy|general|stiffness|films|serving]
+                       [--side all|none|fp64|constrained|anisotropy|general|stiffness|films|precision|serving]
                        [--no-cpu]
 Under torchrun (N > 1) every rank advances its own copy of the batch (weak
 scaling, no collective on the data path); the time is the max over ranks.
@@ -364,6 +364,8 @@ def secondary(mc, torch, stream, dev, side="all"):
         out.update(stiffness(mc, torch, stream, dev))
     if side in ("all", "films"):
         out.update(films(mc, torch, stream, dev))
+    if side in ("all", "precision"):
+        out.update(precision(mc, torch, stream, dev))
     return out
 
 
@@ -525,6 +527,68 @@ def films(mc, torch, stream, dev):
                       "temperatures": temps, "results": out}}
 
 
+def precision(mc, torch, stream, dev):
+    """FP32 against FP64 (which is the oracle's chain bit for bit), as the
+    north star asks each FP32 result's error to be stated.  Config 1 (16^3,
+    K_u = 0.01, T = 0.5, 1000 + 1000 sweeps) over 8 seeds per precision:
+    differences of the seed means of <|m|>, <m_z>, chi_l and <E/N>, with the
+    standard error of the difference from the spread between seeds.  The 32
+    lattices of config 2 (500 + 1000 sweeps, one run each): the difference of
+    <|m|> per lattice against its blocking error; the largest |difference| and
+    the largest |difference| / sigma."""
+    import numpy as np
+
+    def blocking_error(x):  # Flyvbjerg-Petersen: the largest naive error over levels with >= 32 blocks
+        x, best = np.asarray(x, np.float64), 0.0
+        while x.size >= 32:
+            best = max(best, float(np.sqrt(np.var(x, ddof=1) / x.size)))
+            x = 0.5 * (x[: x.size // 2 * 2: 2] + x[1: x.size // 2 * 2: 2])
+        return best
+
+    out = {}
+    res = {}
+    for prec in (mc.MC_FP32, mc.MC_FP64):
+        hs = [mc.mc_create_ex(mc.make_desc((16, 16, 16), K_u=0.01, T=0.5, seed=s, precision=prec, ring_capacity=16,
+                                           stream=stream.cuda_stream, device=dev)) for s in range(8)]
+        g = mc.mc_group_create(hs)
+        mc.mc_group_sweep(g, 1000)
+        mc.mc_group_sweep(g, 1000, measure=True)
+        mc.mc_group_sync(g)
+        mc.mc_group_destroy(g)
+        obs = [mc.mc_measure(h) for h in hs]
+        res[prec] = {k: np.array(v) for k, v in {"ml": [o.ml for o in obs], "mz": [o.m[2] for o in obs],
+                                                  "chi_l": [o.chi[0] for o in obs], "e": [o.e for o in obs]}.items()}
+        for h in hs:
+            mc.mc_destroy(h)
+    c1 = {}
+    for k in ("ml", "mz", "chi_l", "e"):
+        a, b = res[mc.MC_FP32][k], res[mc.MC_FP64][k]
+        c1[k] = {"fp32": round(float(a.mean()), 6), "fp64": round(float(b.mean()), 6),
+                 "diff": float(a.mean() - b.mean()),
+                 "sigma": float(np.hypot(a.std(ddof=1), b.std(ddof=1)) / np.sqrt(len(a)))}
+    out["config1_16c_T0.5_8_seeds"] = c1
+    specs = workloads.config2()
+    ser = {}
+    for prec in (mc.MC_FP32, mc.MC_FP64):
+        hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=prec, ring_capacity=1000,
+                                           sample_torque=0, stream=stream.cuda_stream, device=dev)) for s in specs]
+        g = mc.mc_group_create(hs)
+        mc.mc_group_sweep(g, 500)
+        mc.mc_group_sweep(g, 1000, measure=True)
+        mc.mc_group_sync(g)
+        mc.mc_group_destroy(g)
+        ser[prec] = [np.linalg.norm(mc.mc_samples(h, 1000)["m"], axis=1) for h in hs]
+        for h in hs:
+            mc.mc_destroy(h)
+    d = np.array([a.mean() - b.mean() for a, b in zip(ser[mc.MC_FP32], ser[mc.MC_FP64])])
+    sg = np.array([np.hypot(blocking_error(a), blocking_error(b)) for a, b in zip(ser[mc.MC_FP32], ser[mc.MC_FP64])])
+    out["config2_32_lattices"] = {"max_abs_diff_ml": float(np.abs(d).max()),
+                                  "max_abs_diff_over_sigma": float(np.abs(d / np.maximum(sg, 1e-12)).max()),
+                                  "lattices_within_2e-3_or_3sigma": int(np.sum((np.abs(d) <= 2e-3) | (np.abs(d) <= 3 * sg))),
+                                  "diff_ml": [round(float(x), 5) for x in d], "sigma": [round(float(x), 5) for x in sg]}
+    return {"precision": out}
+
+
 def general_geometry(mc, torch, stream, dev, sweeps=40):
     """FP32 throughput of the lattices that are not all-periodic simple
     cubes: the Bloch-wall lattice (1024 x 128 x 128, x pinned, T = 0.66), a
@@ -623,7 +687,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
                     choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "films",
-                             "serving"],
+                             "precision", "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:
