@@ -83,6 +83,8 @@ def lib() -> C.CDLL:
         L.or_xtal_delta_e.argtypes = [vp, i64, P(dbl)]; L.or_xtal_delta_e.restype = dbl
         L.or_xtal_sweep.argtypes = [vp, i32, i32]
         L.or_xtal_stats.argtypes = [vp, P(dbl)]
+        L.or_xtal_constrained_sweep.argtypes = [vp, dbl, dbl, i32, i32]
+        L.or_xtal_constrained_sweep.restype = i32
         L.or_profile.argtypes = [vp, P(dbl)]
         L.or_reset_stats.argtypes = [vp]
         L.or_sweep.argtypes = [vp, i32, i32]; L.or_sweep.restype = i32
@@ -272,7 +274,7 @@ class Lattice:
 
 
 BCC, FCC, HCP = 1, 2, 3
-XTAL_STAT_FIELDS = ("n", "mx", "my", "mz", "ml", "e", "e_ex", "e_u", "e_c", "e_z")
+XTAL_STAT_FIELDS = ("n", "mx", "my", "mz", "ml", "e", "e_ex", "e_u", "e_c", "e_z", "tqx", "tqy", "tqz")
 
 
 class Crystal:
@@ -323,6 +325,10 @@ class Crystal:
 
     def sweep(self, n: int, measure: bool = False) -> None:
         lib().or_xtal_sweep(self._h, int(n), int(bool(measure)))
+
+    def constrained_sweep(self, theta_deg: float, phi_deg: float, n: int, measure: bool = False) -> int:
+        """Table A2 over the sub-sets (or_xtal_constrained_sweep); -5 if M_L <= 0."""
+        return lib().or_xtal_constrained_sweep(self._h, float(theta_deg), float(phi_deg), int(n), int(bool(measure)))
 
     def stats(self) -> dict:
         out = np.zeros(len(XTAL_STAT_FIELDS))

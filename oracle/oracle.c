@@ -854,7 +854,7 @@ typedef struct {
     double* S;
     int64_t last_accepted;
     int64_t n_samples;
-    double acc_m[3], acc_ml, acc_e, acc_parts[4];
+    double acc_m[3], acc_ml, acc_e, acc_parts[4], acc_tq[3];
 } or_xtal;
 
 /* Neighbour table from the basis positions (fractions of the cell, cell
@@ -992,16 +992,26 @@ static int64_t xtal_pass(or_xtal* X, int s, int colour) {
 /* Sample (Sec. 3): m = mean spin; exchange energy -1/2 sum_i S_i.h_i (every
  * bond seen from both ends); uniaxial, cubic and Zeeman energies; per spin. */
 static void xtal_measure(or_xtal* X) {
-    double M[3] = {0, 0, 0}, sh = 0, su = 0, sc = 0;
+    double M[3] = {0, 0, 0}, sh = 0, su = 0, sc = 0, tu[3] = {0, 0, 0}, tc[3] = {0, 0, 0};
     for (int64_t i = 0; i < X->N; ++i) {
         const double* s = &X->S[3 * i];
         double h[3];
         xtal_field(X, i, h);
         for (int a = 0; a < 3; ++a) M[a] += s[a];
         sh += s[0] * h[0] + s[1] * h[1] + s[2] * h[2];
-        const double pe = s[0] * X->axis[0] + s[1] * X->axis[1] + s[2] * X->axis[2];
+        const double* e = X->axis;
+        const double pe = s[0] * e[0] + s[1] * e[1] + s[2] * e[2];
         su += pe * pe;
         sc += cubic_q(s);
+        /* torque sums as for the simple cubic sample: (S.e)(S x e), S x c(S) */
+        tu[0] += pe * (s[1] * e[2] - s[2] * e[1]);
+        tu[1] += pe * (s[2] * e[0] - s[0] * e[2]);
+        tu[2] += pe * (s[0] * e[1] - s[1] * e[0]);
+        const double x2 = s[0] * s[0], y2 = s[1] * s[1], z2 = s[2] * s[2];
+        const double c0 = s[0] * (y2 + z2), c1 = s[1] * (x2 + z2), c2 = s[2] * (x2 + y2);
+        tc[0] += s[1] * c2 - s[2] * c1;
+        tc[1] += s[2] * c0 - s[0] * c2;
+        tc[2] += s[0] * c1 - s[1] * c0;
     }
     const double N = (double)X->N;
     double ml2 = 0;
@@ -1014,6 +1024,9 @@ static void xtal_measure(or_xtal* X) {
     X->acc_ml += sqrt(ml2);
     X->acc_e += e_ex + e_u + e_c + e_z;
     X->acc_parts[0] += e_ex; X->acc_parts[1] += e_u; X->acc_parts[2] += e_c; X->acc_parts[3] += e_z;
+    X->acc_tq[0] += (2.0 * X->Ku * tu[0] - 2.0 * X->Kc * tc[0] + (M[1] * X->H[2] - M[2] * X->H[1])) / N;
+    X->acc_tq[1] += (2.0 * X->Ku * tu[1] - 2.0 * X->Kc * tc[1] + (M[2] * X->H[0] - M[0] * X->H[2])) / N;
+    X->acc_tq[2] += (2.0 * X->Ku * tu[2] - 2.0 * X->Kc * tc[2] + (M[0] * X->H[1] - M[1] * X->H[0])) / N;
     X->n_samples += 1;
 }
 
@@ -1034,7 +1047,8 @@ OR_EXPORT void or_xtal_sweep(or_xtal* X, int n_sweeps, int measure_flag) {
     }
 }
 
-/* n, <m_x>, <m_y>, <m_z>, <|m|>, <E/N>, <E_ex/N>, <E_u/N>, <E_c/N>, <E_Z/N> */
+/* n, <m_x>, <m_y>, <m_z>, <|m|>, <E/N>, <E_ex/N>, <E_u/N>, <E_c/N>, <E_Z/N>,
+ * <tau_x/N>, <tau_y/N>, <tau_z/N> */
 OR_EXPORT void or_xtal_stats(const or_xtal* X, double* out) {
     const double n = X->n_samples ? (double)X->n_samples : 1.0;
     out[0] = (double)X->n_samples;
@@ -1042,4 +1056,95 @@ OR_EXPORT void or_xtal_stats(const or_xtal* X, double* out) {
     out[4] = X->acc_ml / n;
     out[5] = X->acc_e / n;
     for (int a = 0; a < 4; ++a) out[6 + a] = X->acc_parts[a] / n;
+    for (int a = 0; a < 3; ++a) out[10 + a] = X->acc_tq[a] / n;
+}
+
+/* Constrained Monte Carlo (Table A2) on a crystal: the same iteration as the
+ * simple cubic one, with the sub-sets of Sec. 2 in place of the two colours.
+ * M_L once per iteration over all N spins; then for every sub-lattice s and
+ * colour c in turn, the sub-set's colour indices q in [0, N_c) (cell (x, y,
+ * z) of parity c, q = (x >> 1) + (L0/2)(y + L1 z)) are shuffled and taken in
+ * pairs (pi(2p), pi(2p+1)).  The sub-set's draws carry s in bits 4.. of the
+ * Philox tag (round keys Philox(0, sweep, c | 2<<1 | s<<4, 0); pair draws
+ * keyed (p, sweep, c | 1<<1 | s<<4, attempt)), so sub-lattice 0 draws what a
+ * simple cubic lattice does.  A sub-set has no internal bonds, so the
+ * partners of a pair are never neighbours. */
+static int64_t xtal_colour_site(const or_xtal* X, int s, int colour, uint32_t q) {
+    const int lh = X->L[0] / 2;
+    const int k = (int)(q % (uint32_t)lh);
+    const uint32_t row = q / (uint32_t)lh;
+    const int y = (int)(row % (uint32_t)X->L[1]);
+    const int z = (int)(row / (uint32_t)X->L[1]);
+    return xtal_site(X, s, ((y + z + colour) & 1) + 2 * k, y, z);
+}
+
+static int xtal_pair_move(or_xtal* X, const double R[9], double ML, double c, int64_t si, int64_t sj,
+                          uint32_t pair, uint32_t tag) {
+    double* Si = &X->S[3 * si];
+    double* Sj = &X->S[3 * sj];
+    double hi[3], hj[3];
+    rotate(R, Si, hi);
+    rotate(R, Sj, hj);
+    double hni[3], P;
+    if (!cone_trial(hi, c, pair, X->sweep, tag, X->key0, X->key1, hni, &P)) return 0;
+    const double ynj = (hj[1] + hi[1]) - hni[1];
+    const double znj = (hj[2] + hi[2]) - hni[2];
+    const double t = (hj[0] * hj[0] + hj[1] * hj[1] + hj[2] * hj[2]) - ynj * ynj - znj * znj;
+    if (!(t > 0.0)) return 0;
+    double xnj = sqrt(t);
+    if (hj[0] < 0.0) xnj = -xnj;
+    const double MLn = ML + hni[0] + xnj - hi[0] - hj[0];
+    if (!(MLn > 0.0)) return 0;
+    const double hnj[3] = {xnj, ynj, znj};
+    double Sni[3], Snj[3];
+    rotate_back(R, hni, Sni);
+    rotate_back(R, hnj, Snj);
+    const double dE = xtal_delta_e(X, si, Si, Sni) + xtal_delta_e(X, sj, Sj, Snj);
+    const double ratio = MLn / ML;
+    double r = ratio * ratio;
+    r = r * (fabs(hj[0]) / fabs(xnj));
+    r = r * exp_own(-(dE / X->T));
+    if (P < r) {
+        Si[0] = Sni[0]; Si[1] = Sni[1]; Si[2] = Sni[2];
+        Sj[0] = Snj[0]; Sj[1] = Snj[1]; Sj[2] = Snj[2];
+        return 1;
+    }
+    return 0;
+}
+
+OR_EXPORT int or_xtal_constrained_sweep(or_xtal* X, double theta_deg, double phi_deg, int n_sweeps, int measure_flag) {
+    double R[9];
+    constraint_frame(theta_deg, phi_deg, R);
+    const uint32_t nc = (uint32_t)((int64_t)X->L[0] * X->L[1] * X->L[2] / 2);
+    for (int k = 0; k < n_sweeps; ++k) {
+        int64_t hi = 0, lo = 0;
+        for (int64_t i = 0; i < X->N; ++i) {
+            const double* s = &X->S[3 * i];
+            fixed_add(R[0] * s[0] + R[1] * s[1] + R[2] * s[2], &hi, &lo);
+        }
+        const double ML = fixed_sum_value(hi, lo);
+        if (!(ML > 0.0)) return -5;
+        const double c = cone_c(X->theta);
+        int64_t acc = 0;
+        for (int s = 0; s < X->nsub; ++s)
+            for (int colour = 0; colour < 2; ++colour) {
+                uint32_t rk[4];
+                philox(0u, X->sweep, tag_of(colour, PURPOSE_PERM) | ((uint32_t)s << 4), 0u, X->key0, X->key1, rk);
+                const int b = domain_bits(nc);
+                const uint32_t tag = tag_of(colour, PURPOSE_PAIR) | ((uint32_t)s << 4);
+                for (uint32_t p = 0; p < nc / 2; ++p) {
+                    const int64_t si = xtal_colour_site(X, s, colour, permute(2 * p, nc, b, rk));
+                    const int64_t sj = xtal_colour_site(X, s, colour, permute(2 * p + 1, nc, b, rk));
+                    acc += 2 * xtal_pair_move(X, R, ML, c, si, sj, p, tag);
+                }
+            }
+        X->last_accepted = acc;
+        if (!measure_flag || X->adapt_in_measure) {
+            if (2 * acc > X->N) { if (X->theta < 180) X->theta += 1; }
+            else { if (X->theta > 1) X->theta -= 1; }
+        }
+        if (measure_flag) xtal_measure(X);
+        X->sweep += 1;
+    }
+    return 0;
 }

@@ -132,3 +132,48 @@ def test_crystal_cone_adaptation_and_order_free_passes():
     assert abs(acc - 0.5) < 0.05
     S = X.spins()
     assert np.allclose(np.linalg.norm(S, axis=1), 1.0, atol=1e-12)
+
+
+# --------------------------------------- constrained sweeps (Table A2, Sec. 2)
+def _uniform(n, d):
+    return np.tile(np.asarray(d, float), (n, 1))
+
+
+@pytest.mark.parametrize("kind,cells", [(oracle.BCC, (4, 4, 4)), (oracle.FCC, (4, 2, 4)), (oracle.HCP, (4, 2, 2))])
+def test_xtal_constrained_conserves_transverse_magnetization(kind, cells):
+    """Every accepted pair compensates the transverse components, so the
+    total transverse magnetisation stays zero and M_L stays positive."""
+    th, ph = 30.0, 20.0
+    R = oracle.constraint_frame(th, ph)
+    o = oracle.Crystal(kind, cells, J1=1.0, J2=0.1 if kind != oracle.HCP else 0.0, Ku=0.05, Kc=0.02, T=0.8, seed=5)
+    o.set_spins(_uniform(o.N, R[0]))
+    for _ in range(10):
+        assert o.constrained_sweep(th, ph, 5) == 0
+        M = o.spins().sum(axis=0)
+        assert abs(M @ R[1]) < 1e-9 * o.N and abs(M @ R[2]) < 1e-9 * o.N and M @ R[0] > 0
+    assert o.last_accepted() > 0
+    assert np.allclose(np.linalg.norm(o.spins(), axis=1), 1.0, atol=1e-10)
+
+
+@pytest.mark.parametrize("kind", [oracle.FCC, oracle.HCP])
+def test_xtal_constrained_low_temperature_torque(kind):
+    """T -> 0 along e_C(theta, phi = 0) on a crystal: the anisotropy is per
+    site, so tau_theta / N = -(K_u sin 2 theta + (K_c / 2) sin 4 theta) as on
+    the simple cubic lattice, reduced by O(T) thermal softening."""
+    Ku, Kc, T = 0.05, 0.02, 0.01
+    for th in (30.0, 60.0):
+        R = oracle.constraint_frame(th, 0.0)
+        o = oracle.Crystal(kind, (4, 2, 4), J1=1.0, Ku=Ku, Kc=Kc, T=T, seed=8)
+        o.set_spins(_uniform(o.N, R[0]))
+        o.constrained_sweep(th, 0.0, 300)
+        o.constrained_sweep(th, 0.0, 1500, measure=True)
+        tau = o.stats()["tqy"]
+        t = math.radians(th)
+        expect = -(Ku * math.sin(2 * t) + 0.5 * Kc * math.sin(4 * t))
+        assert abs(tau / expect - 1) < 0.03, (th, tau, expect)
+
+
+def test_xtal_constrained_refuses_negative_projection():
+    o = oracle.Crystal(oracle.BCC, (2, 2, 2), Ku=0.05, T=0.5)
+    o.set_spins(_uniform(o.N, (0.0, 0.0, -1.0)))
+    assert o.constrained_sweep(0.0, 0.0, 1) == -5
