@@ -86,9 +86,11 @@ typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_
  * away along x); J2 must be 0.  dims count cells (even, all boundaries
  * PERIODIC).  Each sub-lattice is split red/black by cell parity and the
  * 2 nsub sub-sets are updated in turn: sub-lattice 0 red, 0 black, 1 red,
- * ...  Site order of spin arrays: i = s + nsub (x + Lx (y + Ly z)).  These
- * lattices take standard sweeps only: no constrained sweeps, films, groups,
- * serving or profiles (MC_ERR_ARG). */
+ * ...  Site order of spin arrays: i = s + nsub (x + Lx (y + Ly z)).
+ * Constrained sweeps (Table A2) run one sub-set at a time as well, the pairs
+ * shuffled within it, with the sub-lattice index in bits 4.. of the Philox
+ * tag of its draws.  These lattices take no films, groups, serving,
+ * profiles or autotuning (MC_ERR_ARG). */
 typedef enum mc_lattice_type { MC_SC = 0, MC_BCC = 1, MC_FCC = 2, MC_HCP = 3 } mc_lattice_type;
 
 typedef enum mc_init {

@@ -29,10 +29,11 @@ struct KernelSet {
     // boundaries and film tables.  Null in the FP64 set.
     void (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
                      int shape, cudaStream_t s);
-    // Table A2 pair pass; leader != 0 takes the pairs in site order
+    // Table A2 pair pass over sub-set (sub, colour) (sub = 0 for simple cubic
+    // lattices); leader != 0 takes the pairs in site order
     // (LatParams::pair_leader).
     void (*pair_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape,
-                      cudaStream_t s);
+                      int sub, cudaStream_t s);
     // End of an unmeasured constrained sweep of every lattice of g.
     void (*sweep_end)(const GroupArgs& g, cudaStream_t s);
     // Neighbour field of every site of the given colour into LatParams::pfield
@@ -50,10 +51,14 @@ struct KernelSet {
     // bcc / fcc / hcp lattice L alone: a pass over sub-set (sub, colour) of
     // ntiles 32-site tiles (finalize != 0 closes the sweep), and the sample
     // over the 2 nsub sub-sets (ntiles = 2 nsub tiles_per_subset), which
-    // closes it; nb = the most neighbour entries of a sub-lattice.
+    // closes it (level 2: with the torques); nb = the most neighbour entries
+    // of a sub-lattice.
     void (*xtal_pass)(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, int nb,
                       cudaStream_t s);
-    void (*xtal_sample)(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, cudaStream_t s);
+    void (*xtal_sample)(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, int level, cudaStream_t s);
+    // Constrained sweeps of a crystal L: the neighbour field of sub-set (sub,
+    // colour) into LatParams::pfield (ntiles 32-site tiles).
+    void (*xtal_field)(LatDev* L, uint32_t ntiles, int sub, int colour, int nb, cudaStream_t s);
     // One grain sample of a film lattice (ntiles site tiles, n_grains grains).
     void (*grain_sample)(LatDev* L, uint32_t ntiles, int n_grains, cudaStream_t s);
     // Slice sums for the profile of one lattice.

@@ -107,26 +107,27 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
 }
 
 template <bool LEADER, int C>
-void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, cudaStream_t s) {
+void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int sub, cudaStream_t s) {
     constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
     static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER>);
     pair_pass_kernel<R, B, C, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
-        g, ntiles, static_cast<const R*>(cone), colour);
+        g, ntiles, static_cast<const R*>(cone), colour, sub);
 }
 
 // launch shapes: tiles per grid-stride step {default, 8, 2}
 template <bool LEADER>
-void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int shape, cudaStream_t s) {
+void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int shape, int sub,
+                 cudaStream_t s) {
     constexpr int C0 = LEADER ? kPairChunkLead : kPairChunk;
-    if (shape == 1) pair_pass_t<LEADER, 8>(g, ntiles, cone, colour, s);
-    else if (shape == 2) pair_pass_t<LEADER, 2>(g, ntiles, cone, colour, s);
-    else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, s);
+    if (shape == 1) pair_pass_t<LEADER, 8>(g, ntiles, cone, colour, sub, s);
+    else if (shape == 2) pair_pass_t<LEADER, 2>(g, ntiles, cone, colour, sub, s);
+    else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, sub, s);
 }
 
-void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape,
+void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape, int sub,
                cudaStream_t s) {
-    if (leader) pair_pass_s<true>(g, ntiles, cone, colour, shape, s);
-    else pair_pass_s<false>(g, ntiles, cone, colour, shape, s);
+    if (leader) pair_pass_s<true>(g, ntiles, cone, colour, shape, sub, s);
+    else pair_pass_s<false>(g, ntiles, cone, colour, shape, sub, s);
 }
 
 void sweep_end(const GroupArgs& g, cudaStream_t s) {
@@ -181,19 +182,37 @@ struct XtalPass {
 
 template <int NB>
 struct XtalSample {
-    static void run(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s) {
-        static const uint32_t cap = resident_blocks(xtal_sample_kernel<R, NB>);
-        xtal_sample_kernel<R, NB><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, tiles_per_subset);
+    template <int LEVEL>
+    static void go(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, cudaStream_t s) {
+        static const uint32_t cap = resident_blocks(xtal_sample_kernel<R, NB, LEVEL>);
+        xtal_sample_kernel<R, NB, LEVEL><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, tiles_per_subset);
+    }
+    // level 2: with the torque sums
+    static void run(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int level, cudaStream_t s) {
+        if (level >= 2) go<2>(L, ntiles, tiles_per_subset, s);
+        else go<1>(L, ntiles, tiles_per_subset, s);
     }
 };
+
+template <int NB>
+struct XtalField {
+    static void run(LatDev* L, uint32_t ntiles, int sub, int colour, cudaStream_t s) {
+        static const uint32_t cap = resident_blocks(xtal_field_kernel<R, NB>);
+        xtal_field_kernel<R, NB><<<grid_for(ntiles, cap), kBlock, 0, s>>>(L, ntiles, sub, colour);
+    }
+};
+
+void xtal_field_launch(LatDev* L, uint32_t ntiles, int sub, int colour, int nb, cudaStream_t s) {
+    by_entries<XtalField>(nb, L, ntiles, sub, colour, s);
+}
 
 void xtal_pass(LatDev* L, uint32_t ntiles, const void* cone, int sub, int colour, int finalize, int nb,
                cudaStream_t s) {
     by_entries<XtalPass>(nb, L, ntiles, cone, sub, colour, finalize, s);
 }
 
-void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, cudaStream_t s) {
-    by_entries<XtalSample>(nb, L, ntiles, tiles_per_subset, s);
+void xtal_sample(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset, int nb, int level, cudaStream_t s) {
+    by_entries<XtalSample>(nb, L, ntiles, tiles_per_subset, level, s);
 }
 
 void grain_sample(LatDev* L, uint32_t ntiles, int n_grains, cudaStream_t s) {
@@ -210,7 +229,7 @@ void profile(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s) {
 }  // namespace
 
 const KernelSet& kernels_f32() {
-    static const KernelSet k{colour_pass, row_pass, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, grain_sample, profile,
+    static const KernelSet k{colour_pass, row_pass, pair_pass, sweep_end, pair_field, ml_reset, mlong, measure, row_sample, xtal_pass, xtal_sample, xtal_field_launch, grain_sample, profile,
                              "f32"};
     return k;
 }

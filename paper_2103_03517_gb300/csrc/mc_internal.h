@@ -69,8 +69,9 @@ enum { kColourGeneral = 0, kColourRow = 1, kColourRowGen = 2 };
 // One neighbour entry of a bcc / fcc / hcp sub-lattice: the neighbour's
 // sub-lattice, its cell offset and its coupling (J1 or J2), with what the
 // kernels need precomputed for the lattice's size: the offset taken modulo
-// (Lx, Ly, Lz), the parity of dx + dy + dz, and for a site of colour c the
-// element offset of the neighbour's x-component array in the spins.
+// (Lx, Ly, Lz), the parity of dx + dy + dz (bit 0 of par; bit 1 marks a
+// forward entry, one of each entry and its reverse), and for a site of
+// colour c the element offset of the neighbour's x-component array.
 constexpr int kXtalMaxSub = 4, kXtalMaxNb = 24;
 struct XtalNb {
     int8_t sub, dx, dy, dz;
@@ -117,7 +118,7 @@ struct LatParams {
     long long* gsum;        // films: [n_grains][3] fixed-point spin sums of one grain sample
     const int32_t* gsize;   // films: [n_grains] spins per grain
     double* gacc;           // films: [n_grains + 1] sums over grain samples of |m_g|, then the count
-    void* aos;              // constrained sweeps: [2][stride] (x, y, z, 0) copy of the
+    void* aos;              // constrained sweeps: [2 nsub][stride] (x, y, z, 0) copy of the
                             // spins (Spin4), written by mlong_kernel at the start of a run
                             // of constrained sweeps and kept in step by the pair passes;
                             // null until the lattice's first constrained sweep

@@ -790,8 +790,9 @@ __device__ __forceinline__ void ml_add(long long& hi, long long& lo, R t, int si
 }
 
 // M_L of every lattice of g into the zeroed ml_hi / ml_lo, site tiles as in
-// the colour pass; it also writes the packed (x, y, z, 0) copy of both
-// colours that the pair passes gather from and keep in step.
+// the colour pass; it also writes the packed (x, y, z, 0) copy of every
+// sub-set (sub-lattice x colour; the two colours of a simple cubic lattice)
+// that the pair passes gather from and keep in step.
 // ------------------------------------------------------------------------
 template <typename R, int V>
 __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t ntiles) {
@@ -816,9 +817,9 @@ __global__ void __launch_bounds__(kBlock) mlong_kernel(GroupArgs g, uint32_t nti
             for (int v = 0; v < V; ++v) {
                 const uint32_t q = base + uint32_t(32 * v);
                 if (q >= p.Nc) continue;
-                for (int colour = 0; colour < 2; ++colour) {
-                    const V3<R> S = load_spin(s, p.stride, colour, q);
-                    if (a4) a4[size_t(colour) * p.stride + q] = Spin4<R>{S.x, S.y, S.z, R(0)};
+                for (int k = 0; k < 2 * p.nsub; ++k) {  // sub-set k = 2 sub + colour
+                    const V3<R> S = load_spin(s, p.stride, k, q);
+                    if (a4) a4[size_t(k) * p.stride + q] = Spin4<R>{S.x, S.y, S.z, R(0)};
                     ml_add<R>(hi, lo, ml_term<R>(e1, S), 1);
                 }
             }
@@ -968,8 +969,8 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 template <typename R>
 __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
                                               Spin4<R>* own4, const Spin4<R>* fld, uint32_t pr, uint32_t qi,
-                                              uint32_t qj, R c, uint32_t sweep, int colour, double ML,
-                                              long long& dhi, long long& dlo) {
+                                              uint32_t qj, R c, uint32_t sweep, int colour, int set, uint32_t tag,
+                                              double ML, long long& dhi, long long& dlo) {
     const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
     const Spin4<R> fi4 = fld[qi], fj4 = fld[qj];
     const V3<R> h_i{fi4.x, fi4.y, fi4.z};
@@ -980,7 +981,7 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     const V3<R> hj = rotate(par.Rm, Sj);
     V3<R> hni;
     R P;
-    if (!cone_trial(hi, c, pr, sweep, tag_of(colour, kPurposePair), p.key0, p.key1, hni, P)) return 0;
+    if (!cone_trial(hi, c, pr, sweep, tag, p.key0, p.key1, hni, P)) return 0;
     const R ynj = (hj.y + hi.y) - hni.y;
     const R znj = (hj.z + hi.z) - hni.z;
     const R t = (hj.x * hj.x + hj.y * hj.y + hj.z * hj.z) - ynj * ynj - znj * znj;
@@ -1014,8 +1015,8 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     r = r * (fabs(hj.x) / fabs(xnj));
     r = r * boltzmann(dE, par);
     if (!(P < r)) return 0;
-    store_spin(s, p.stride, colour, qi, Sni);
-    store_spin(s, p.stride, colour, qj, Snj);
+    store_spin(s, p.stride, set, qi, Sni);
+    store_spin(s, p.stride, set, qj, Snj);
     own4[qi] = Spin4<R>{Sni.x, Sni.y, Sni.z, R(0)};
     own4[qj] = Spin4<R>{Snj.x, Snj.y, Snj.z, R(0)};
     ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Sni), 1);  // M_L of the next sweep
@@ -1032,7 +1033,7 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
 // once per lattice in a chunk.
 template <typename R, int MINB, int CHUNK, bool LEADER>
 __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
-                                                                 const R* __restrict__ cone, int colour) {
+                                                                 const R* __restrict__ cone, int colour, int sub) {
     const int lane = int(threadIdx.x & 31);
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
     const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
@@ -1058,8 +1059,14 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                 const R c = cone[L->st.theta];
                 const uint32_t sweep = L->st.sweep;
                 R* __restrict__ s = static_cast<R*>(p.spins);
-                const uint4 rk = philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm), 0u), p.key0, p.key1);
-                Spin4<R>* own4 = a4 + size_t(colour) * p.stride;
+                // sub-set set = 2 sub + colour (a simple cubic lattice: sub = 0); a
+                // crystal sub-set's draws carry the sub-lattice in bits 4.. of the tag
+                const int set = 2 * sub + colour;
+                const uint32_t tsub = uint32_t(sub) << 4;
+                const uint4 rk =
+                    philox(make_uint4(0u, sweep, tag_of(colour, kPurposePerm) | tsub, 0u), p.key0, p.key1);
+                const uint32_t tag = tag_of(colour, kPurposePair) | tsub;
+                Spin4<R>* own4 = a4 + size_t(set) * p.stride;
                 const Spin4<R>* fld = static_cast<const Spin4<R>*>(p.pfield);
                 if constexpr (LEADER) {
                     // The 64 sites of each tile in index order; each site whose
@@ -1093,7 +1100,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                             leader(used + lane - m, q, r);
                             if (lane < m) { q = wq; r = wr; }
                             const uint32_t qj = permute(r + 1u, p.Nc, p.perm_bits, rk);
-                            nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, q, qj, c, sweep, colour, ML, dhi, dlo);
+                            nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, q, qj, c, sweep, colour, set, tag, ML,
+                                                 dhi, dlo);
                             used += 32 - m;
                             m = 0;
                         }
@@ -1104,7 +1112,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     }
                     if (lane < m) {
                         const uint32_t qj = permute(wr + 1u, p.Nc, p.perm_bits, rk);
-                        nacc += pair_move<R>(p, par, s, own4, fld, wr >> 1, wq, qj, c, sweep, colour, ML, dhi, dlo);
+                        nacc += pair_move<R>(p, par, s, own4, fld, wr >> 1, wq, qj, c, sweep, colour, set, tag, ML,
+                                             dhi, dlo);
                     }
                 } else {
                     for (uint32_t t = tile; t < t1; ++t) {
@@ -1112,7 +1121,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                         if (pr < p.n_pairs) {
                             const uint32_t qi = permute(2 * pr, p.Nc, p.perm_bits, rk);
                             const uint32_t qj = permute(2 * pr + 1, p.Nc, p.perm_bits, rk);
-                            nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, ML, dhi, dlo);
+                            nacc += pair_move<R>(p, par, s, own4, fld, pr, qi, qj, c, sweep, colour, set, tag, ML, dhi,
+                                                 dlo);
                         }
                     }
                 }

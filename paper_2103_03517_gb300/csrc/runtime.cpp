@@ -181,6 +181,11 @@ static void xtal_table(int lattice, double J, double J2, const LatParams& p, Xta
                         e.par = uint32_t(dx + dy + dz + 4) & 1u;  // + 4 keeps the sum non-negative, parity unchanged
                         for (int c = 0; c < 2; ++c)
                             e.off[c] = (uint64_t(t) * 2 + ((uint32_t(c) + e.par) & 1u)) * 3 * uint64_t(p.stride);
+                        // forward entries (bit 1): one of each entry and its reverse
+                        // (sub-lattice t -> s, offset -d), so that summing S_i.S_j over
+                        // them sees every bond once
+                        const bool fwd = t > s || (t == s && (dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)))));
+                        e.par |= fwd ? 2u : 0u;
                     }
     }
 }
@@ -312,12 +317,13 @@ static void per_site_colour_split(const LatParams& p, const void* src, size_t el
 const KernelSet& kernel_set(int precision) { return precision == MC_FP64 ? kernels_f64() : kernels_f32(); }
 
 // Bytes of what constrained sweeps gather from: the packed (x, y, z, 0)
-// spin copy (a 4-vector per site of each colour) and the neighbour field of
-// the colour being updated (a 4-vector per site).
+// spin copy (a 4-vector per site of each sub-set: sub-lattice x colour) and
+// the neighbour field of the sub-set being updated (a 4-vector per site).
 size_t aos_bytes(const mc_desc* d) {
     const uint64_t Nc = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2] / 2;
     const uint64_t stride = (Nc + 63) / 64 * 64;
-    return size_t(3 * stride * 4) * (d->precision == MC_FP64 ? 8 : 4);
+    const uint64_t sets = 2 * uint64_t(sublattices(d->lattice));
+    return size_t((sets + 1) * stride * 4) * (d->precision == MC_FP64 ? 8 : 4);
 }
 
 // Allocate the packed copy on the lattice's first constrained sweep (the
@@ -331,7 +337,7 @@ int ensure_aos(mc_lattice* h) {
     }
     h->hp.aos = h->d_aos;
     const size_t rs = h->hp.precision == MC_FP64 ? 8 : 4;
-    h->hp.pfield = static_cast<char*>(h->d_aos) + size_t(2) * h->hp.stride * 4 * rs;
+    h->hp.pfield = static_cast<char*>(h->d_aos) + size_t(2 * h->hp.nsub) * h->hp.stride * 4 * rs;
     return MC_OK;
 }
 
@@ -599,16 +605,35 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, ls.shape.row, s);
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
-    if (ls.xtal) {  // bcc / fcc: the 2 nsub sub-sets in turn, then the sample
+    if (ls.xtal) {  // bcc / fcc / hcp: the 2 nsub sub-sets in turn, then the sample
         for (int i = 0; i < n; ++i) {
-            for (int sub = 0; sub < ls.nsub; ++sub)
-                for (int colour = 0; colour < 2; ++colour) {
-                    const bool last = sub == ls.nsub - 1 && colour == 1;
-                    timed([&] {
-                        k.xtal_pass(ls.xtal, ls.nt_all, cone, sub, colour, last && !measure ? 1 : 0, ls.xnb_max, s);
-                    });
+            if (!constrained) {
+                for (int sub = 0; sub < ls.nsub; ++sub)
+                    for (int colour = 0; colour < 2; ++colour) {
+                        const bool last = sub == ls.nsub - 1 && colour == 1;
+                        timed([&] {
+                            k.xtal_pass(ls.xtal, ls.nt_all, cone, sub, colour, last && !measure ? 1 : 0, ls.xnb_max,
+                                        s);
+                        });
+                    }
+            } else {  // Table A2 per sub-set, as for the two colours of a simple cubic lattice
+                if (i == 0) {
+                    k.ml_reset(ls.all, s);
+                    k.mlong(ls.all, ls.nt_all, s);
                 }
-            if (measure) k.xtal_sample(ls.xtal, uint32_t(2 * ls.nsub) * ls.nt_all, ls.nt_all, ls.xnb_max, s);
+                for (int sub = 0; sub < ls.nsub; ++sub)
+                    for (int colour = 0; colour < 2; ++colour) {
+                        k.xtal_field(ls.xtal, ls.nt_all, sub, colour, ls.xnb_max, s);
+                        timed([&] {
+                            if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, ls.shape.pair, sub, s);
+                            if (ls.nt_pairs_lead)
+                                k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, ls.shape.pair, sub, s);
+                        });
+                    }
+                if (!measure) k.sweep_end(ls.all, s);
+            }
+            if (measure)
+                k.xtal_sample(ls.xtal, uint32_t(2 * ls.nsub) * ls.nt_all, ls.nt_all, ls.xnb_max, ls.sample_level, s);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -626,9 +651,9 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             for (int colour = 0; colour < 2; ++colour) {
                 k.pair_field(ls.all, ls.nt_all, colour, ls.shape.field, s);
                 timed([&] {
-                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, ls.shape.pair, s);
+                    if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, ls.shape.pair, 0, s);
                     if (ls.nt_pairs_lead)
-                        k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, ls.shape.pair, s);
+                        k.pair_pass(ls.pairs_lead, ls.nt_pairs_lead, cone, colour, 1, ls.shape.pair, 0, s);
                 });
             }
             if (!measure) k.sweep_end(ls.all, s);  // a measured sweep ends in its sample
@@ -771,7 +796,6 @@ MC_API int mc_constrained_sweep(mc_handle h, double theta_c_deg, double phi_c_de
     if (!std::isfinite(phi_c_deg)) return fail(MC_ERR_ARG, "phi_c not finite");
     for (int a = 0; a < 3; ++a)
         if (h->hp.bc[a] == MC_PINNED) return fail(MC_ERR_ARG, "constrained sweeps need no pinned boundary");
-    if (h->hp.nsub > 1) return fail(MC_ERR_ARG, "constrained sweeps need a simple cubic lattice");
     cudaSetDevice(h->device);
     int rc = ensure_aos(h);
     if (rc) return rc;

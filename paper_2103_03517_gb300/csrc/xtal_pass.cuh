@@ -43,7 +43,8 @@ __device__ __forceinline__ void xtal_stage(const LatParams& p, int sub0, int nsu
 // the site is cell c of the given colour.  Each entry's cell offset is taken
 // modulo the lattice size in advance, so a neighbour's cell wraps by one
 // compare per axis; its colour array follows from the entry's parity.
-template <typename R, int NMAX>
+// HALF: the forward entries only (every bond once over the lattice).
+template <typename R, int NMAX, bool HALF = false>
 __device__ __forceinline__ V3<R> xtal_field(const LatParams& p, const R* s, const XtalNb* tab, int n, XCell c,
                                             int colour) {
     const uint32_t Lx = uint32_t(p.Lx), Ly = uint32_t(p.Ly), Lz = uint32_t(p.Lz), Lh = uint32_t(p.Lh);
@@ -51,7 +52,7 @@ __device__ __forceinline__ V3<R> xtal_field(const LatParams& p, const R* s, cons
     V3<R> h{R(0), R(0), R(0)};
 #pragma unroll
     for (int e = 0; e < NMAX; ++e) {
-        if (e < n) {
+        if (e < n && (!HALF || (tab[e].par & 2u))) {
             const XtalNb& t = tab[e];
             uint32_t xx = c.x + t.dxw, yy = c.y + t.dyw, zz = c.z + t.dzw;
             xx = xx >= Lx ? xx - Lx : xx;
@@ -113,14 +114,38 @@ __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t n
     });
 }
 
-// Sample of the current state: M, the exchange sum 1/2 sum_i S_i.h_i (every
-// bond seen from both ends), the uniaxial and cubic sums; tiles of 32 sites
+// Constrained sweeps (Table A2) of a crystal: the neighbour field of every
+// site of sub-set (sub, colour) into LatParams::pfield as (h_x, h_y, h_z, 0),
+// summed in table order from the spins (which the pair passes keep in step;
+// the sub-set's own spins are not among its neighbours).
+template <typename R, int NMAX>
+__global__ void __launch_bounds__(kBlock) xtal_field_kernel(LatDev* L, uint32_t ntiles, int sub, int colour) {
+    __shared__ XtalNb tab[NMAX];
+    const LatParams& p = L->p;
+    xtal_stage<NMAX>(p, sub, 1, tab);
+    const int n = p.xnb_n[sub];
+    const WarpChunk wc = warp_chunk(ntiles);
+    if (wc.begin >= wc.end) return;
+    const R* s = static_cast<const R*>(p.spins);
+    Spin4<R>* fld = static_cast<Spin4<R>*>(p.pfield);
+    for (uint32_t tile = wc.begin; tile < wc.end; ++tile) {
+        const uint32_t q = tile * 32u + uint32_t(wc.lane);
+        if (q >= p.Nc) continue;
+        const V3<R> h = xtal_field<R, NMAX>(p, s, tab, n, xtal_cell(p, colour, q), colour);
+        fld[q] = Spin4<R>{h.x, h.y, h.z, R(0)};
+    }
+}
+
+// Sample of the current state: M, the exchange sum over every bond once
+// (sum_i S_i . h_i over the forward entries), the uniaxial, cubic and torque
+// sums; tiles of 32 sites
 // over the 2 nsub sub-sets; closes the sweep.  The warp sums are reduced in
 // the working precision in a fixed butterfly order and rounded to fixed
 // point on lane i (int64 in both precisions, so that large couplings cannot
 // overflow).
-template <typename R, int NMAX>
+template <typename R, int NMAX, int LEVEL>
 __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t ntiles, uint32_t tiles_per_subset) {
+    constexpr int NS = LEVEL >= 2 ? kNumSums : kSumTux;  // sums sampled (LEVEL 2: with the torques)
     __shared__ XtalNb tab[kXtalMaxSub * NMAX];
     const LatParams& p = L->p;
     xtal_stage<NMAX>(p, 0, p.nsub, tab);
@@ -141,22 +166,26 @@ __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t
             const XCell cell = xtal_cell(p, colour, q);
             const R* own = s + (size_t(sub) * 2 + colour) * 3 * p.stride;
             const V3<R> S{own[q], own[p.stride + q], own[2 * size_t(p.stride) + q]};
-            const V3<R> h = xtal_field<R, NMAX>(p, s, tab + sub * NMAX, p.xnb_n[sub], cell, colour);
-            add_site<R, 1>(sums, S, e_ax);
-            sums.v[kSumEx] = R(0.5) * (S.x * h.x + S.y * h.y + S.z * h.z);
+            const V3<R> h = xtal_field<R, NMAX, true>(p, s, tab + sub * NMAX, p.xnb_n[sub], cell, colour);
+            add_site<R, LEVEL>(sums, S, e_ax);
+            sums.v[kSumEx] = S.x * h.x + S.y * h.y + S.z * h.z;
         }
-        R mine = R(0);
+        if constexpr (kIsF64<R>) {
+            R mine = R(0);
 #pragma unroll
-        for (int i = 0; i < kSumTux; ++i) {
-            R v = sums.v[i];
+            for (int i = 0; i < NS; ++i) {
+                R v = sums.v[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == i) mine = v;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == i) mine = v;
+            }
+            fix += __double2ll_rn(mine * kFixScale);
+        } else {
+            fix += warp_tile_fix<R, NS>(sums, lane);  // per-lane fixed point, integer warp sums
         }
-        if constexpr (kIsF64<R>) fix += __double2ll_rn(mine * kFixScale);
-        else fix += __float2ll_rn(mine * float(kFixScaleF32));
     }
-    publish(L->st, lane, 0, true, fix, 3, wc.end - wc.begin, ntiles, [&] { finalize_sweep(p, L->st, 1, false); });
+    publish(L->st, lane, 0, true, fix, 3, wc.end - wc.begin, ntiles,
+            [&] { finalize_sweep(p, L->st, 1, LEVEL >= 2); });
 }
 
 }  // namespace mcgb

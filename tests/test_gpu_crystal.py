@@ -82,10 +82,73 @@ def test_crystal_refused_where_simple_cubic_only():
     h = mc.mc_create_ex(mc.make_desc((4, 4, 4), lattice=mc.MC_FCC))
     try:
         with pytest.raises(mc.MCError):
-            mc.mc_constrained_sweep(h, 30.0, 0.0, 1)
-        with pytest.raises(mc.MCError):
             mc.mc_group_create([h])
+        with pytest.raises(mc.MCError):
+            mc.mc_profile_sample(h)
     finally:
         mc.mc_destroy(h)
     with pytest.raises(mc.MCError):
         mc.mc_create_ex(mc.make_desc((4, 4, 4), lattice=mc.MC_BCC, boundary=(1, 0, 0)))
+
+
+
+# --------------------------------------- constrained sweeps (Table A2, Sec. 2)
+@pytest.mark.parametrize("lattice,cells,J2", [(mc.MC_BCC, (4, 2, 6), 0.0), (mc.MC_FCC, (2, 4, 2), 0.15),
+                                              (mc.MC_HCP, (4, 2, 2), 0.0), (mc.MC_FCC, (6, 4, 4), 0.0)])
+def test_crystal_constrained_fp64_bit_exact(lattice, cells, J2):
+    """Constrained sweeps of a crystal, FP64: spins, theta and the samples
+    (torque included) equal the oracle's chain; 7 sweeps enqueued directly,
+    then 20 (one captured graph of 16 and 4 more) with samples."""
+    nsub = 2 if lattice == mc.MC_BCC else 4
+    N = nsub * cells[0] * cells[1] * cells[2]
+    th, ph = 35.0, 20.0
+    R = oracle.constraint_frame(th, ph)
+    kw = dict(Ku=0.2, Kc=0.1, H=(0.02, -0.03, 0.05), T=0.9, seed=N + 1)
+    o = oracle.Crystal(KIND[lattice], cells, J1=1.1, J2=J2, axis=(0.2, 0.1, 1.0), **kw)
+    spins = np.tile(R[0], (N, 1))
+    o.set_spins(spins)
+    h = mc.mc_create_ex(mc.make_desc(cells, J=1.1, J2=J2, K_u=kw["Ku"], K_c=kw["Kc"], H=kw["H"], T=kw["T"],
+                                     seed=kw["seed"], axis=(0.2, 0.1, 1.0), precision=mc.MC_FP64, lattice=lattice,
+                                     ring_capacity=32))
+    try:
+        mc.mc_set_spins(h, spins)
+        for n, meas in ((7, False), (20, True)):
+            mc.mc_constrained_sweep(h, th, ph, n, measure=meas)
+            assert o.constrained_sweep(th, ph, n, measure=meas) == 0
+            got = mc.mc_get_spins(h, N)
+            assert np.array_equal(got, o.spins()), (lattice, cells, int((got != o.spins()).any(axis=1).sum()))
+            assert mc.mc_get_theta(h)[0] == o.theta()
+        ob, st = mc.mc_measure(h), o.stats()
+        assert ob.n_samples == st["n"] == 20
+        np.testing.assert_allclose(list(ob.m), [st["mx"], st["my"], st["mz"]], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(list(ob.torque), [st["tqx"], st["tqy"], st["tqz"]], rtol=0, atol=1e-9)
+        np.testing.assert_allclose([ob.e], [st["e"]], rtol=0, atol=1e-9)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_crystal_constrained_fp32_torque_matches_fp64():
+    """fcc 6^3 cells at T = 0.6, theta_c = 45 deg: the FP32 torque tau_y
+    (site order, FP32 moves) agrees with the FP64 chain's within 4 sigma of
+    the spread between 6 runs per precision; both near the T -> 0 law
+    -(K_u sin 2 theta) softened by temperature."""
+    th, Ku = 45.0, 0.05
+    R = oracle.constraint_frame(th, 0.0)
+    means = {}
+    for prec in (mc.MC_FP32, mc.MC_FP64):
+        vals = []
+        for k in range(6):
+            h = mc.mc_create_ex(mc.make_desc((6, 6, 6), K_u=Ku, T=0.6, seed=40 + k, precision=prec,
+                                             lattice=mc.MC_FCC, init_dir=tuple(R[0]), ring_capacity=16))
+            try:
+                mc.mc_constrained_sweep(h, th, 0.0, 300)
+                mc.mc_reset_stats(h)
+                mc.mc_constrained_sweep(h, th, 0.0, 1500, measure=True)
+                vals.append(mc.mc_measure(h).torque[1])
+            finally:
+                mc.mc_destroy(h)
+        means[prec] = np.array(vals)
+    a, b = means[mc.MC_FP32], means[mc.MC_FP64]
+    sig = np.hypot(a.std(ddof=1), b.std(ddof=1)) / np.sqrt(len(a))
+    assert abs(a.mean() - b.mean()) <= 4 * sig + 1e-5, (a.mean(), b.mean(), sig)
+    assert -Ku < b.mean() < -0.5 * Ku, b.mean()
