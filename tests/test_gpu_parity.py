@@ -619,3 +619,93 @@ def test_fp32_constrained_site_order_equals_pair_order(dims):
     assert np.array_equal(out[0][0], out[1][0])
     assert abs(out[0][1].torque[1] - out[1][1].torque[1]) <= 1e-9
     assert abs(out[0][1].e - out[1][1].e) <= 1e-9
+
+
+# ------------------------- full size: configs 3, 4 and 5 (bench workloads)
+def test_config3_full_size_lattice_fp64_constrained_bit_exact():
+    """One lattice of the constrained workload at its full size (64^3,
+    theta_c = 40, phi_c = 45, T = 0.2), FP64: two constrained sweeps, the
+    second measured, equal the oracle's chain bit for bit (spins, theta,
+    samples with the torque)."""
+    spec, th, ph = workloads.config3()[14]
+    R = oracle.constraint_frame(th, ph)
+    spins = workloads.uniform_spins(spec.N, R[0])
+    h, o = make_pair(spec.dims, Ku=spec.Ku, Kc=spec.Kc, T=spec.T, seed=spec.seed, ring=4, spins=spins)
+    try:
+        mc.mc_constrained_sweep(h, th, ph, 1)
+        o.constrained_sweep(th, ph, 1)
+        mc.mc_constrained_sweep(h, th, ph, 1, measure=True)
+        o.constrained_sweep(th, ph, 1, measure=True)
+        assert_same_state(h, o, "config3 64^3")
+        assert_same_samples(h, o, 1)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_config3_full_size_fp32_batch_properties():
+    """The bench's FP32 constrained batch (80 x 64^3, site order): after 20
+    sweeps every lattice keeps its transverse magnetisation at zero and its
+    projection on e_C positive (to FP32 rounding of the compensation), spins
+    stay unit vectors (the partner is not renormalised: to FP32 rounding),
+    and the acceptance sits at one half or the cone is fully open."""
+    runs = workloads.config3()
+    hs = []
+    for spec, th, ph in runs:
+        R = oracle.constraint_frame(th, ph)
+        hs.append(mc.mc_create_ex(mc.make_desc(spec.dims, K_u=spec.Ku, K_c=spec.Kc, T=spec.T, seed=spec.seed,
+                                               init_dir=tuple(R[0]), ring_capacity=32)))
+    g = mc.mc_group_create(hs)
+    try:
+        mc.mc_group_constrained_sweep(g, [r[1] for r in runs], [r[2] for r in runs], 20, measure=True)
+        mc.mc_group_sync(g)
+        for (spec, th, ph), h in zip(runs, hs):
+            R = oracle.constraint_frame(th, ph)
+            S = mc.mc_get_spins(h, spec.N)
+            M = S.sum(axis=0)
+            assert abs(M @ R[1]) < 1e-3 * spec.N and abs(M @ R[2]) < 1e-3 * spec.N and M @ R[0] > 0, (th, ph, M)
+            assert np.abs(np.linalg.norm(S, axis=1) - 1.0).max() < 1e-4
+            ob = mc.mc_measure(h)
+            acc = mc.mc_samples(h, 20)["accepted"][-10:] / spec.N
+            assert ob.theta_deg == 180 or abs(acc.mean() - 0.5) < 0.1, (spec.T, th, ob.theta_deg, acc.mean())
+    finally:
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+
+
+def test_config4_full_size_wall_fp64_bit_exact():
+    """The Bloch-wall lattice at its full size (1024 x 128 x 128, x pinned,
+    16,777,216 spins, T = 0.66), FP64: one sweep and one measured sweep equal
+    the oracle's chain bit for bit; the pinned planes keep +z and -z."""
+    spec = workloads.config4()[3]
+    spins = workloads.wall_spins(spec.dims)
+    h, o = make_pair(spec.dims, Ku=spec.Ku, T=spec.T, seed=spec.seed, bc=spec.bc, ring=4, spins=spins)
+    try:
+        mc.mc_sweep(h, 1)
+        o.sweep(1)
+        mc.mc_sweep(h, 1, measure=True)
+        o.sweep(1, measure=True)
+        assert_same_state(h, o, "config4 wall")
+        assert_same_samples(h, o, 1)
+        S = mc.mc_get_spins(h, spec.N).reshape(spec.dims[2], spec.dims[1], spec.dims[0], 3)
+        assert np.all(S[:, :, 0, 2] == 1.0) and np.all(S[:, :, -1, 2] == -1.0)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_config5_full_size_film_fp64_bit_exact():
+    """The serving mix's granular film at its full size (1024 x 1024 x 15,
+    Voronoi grains of mean diameter 10, 15,728,640 spins), FP64: one sweep and
+    one measured sweep equal the oracle's chain bit for bit."""
+    dims = (1024, 1024, 15)
+    film = workloads.voronoi_film(*dims, 10.0, seed=1)
+    h, o = make_pair(dims, Ku=0.02, T=0.8, seed=5, bc=(0, 0, 1), ring=4, film=film)
+    try:
+        mc.mc_sweep(h, 1)
+        o.sweep(1)
+        mc.mc_sweep(h, 1, measure=True)
+        o.sweep(1, measure=True)
+        assert_same_state(h, o, "config5 film")
+        assert_same_samples(h, o, 1)
+    finally:
+        mc.mc_destroy(h)
