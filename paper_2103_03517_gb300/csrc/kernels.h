@@ -45,8 +45,9 @@ struct KernelSet {
     void (*mlong)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
     // Standalone sample + end of sweep (site tiles).
     void (*measure)(const GroupArgs& g, uint32_t ntiles, cudaStream_t s);
-    // The same over lattices in the row layout (gen as in row_pass).  Null
-    // in the FP64 set.
+    // The same over lattices in the row layout (gen as in row_pass); with gen
+    // = 0 it also stores the red sites' field for the next constrained sweep
+    // (LatParams::pfield).  Null in the FP64 set.
     void (*row_sample)(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s);
     // bcc / fcc / hcp lattice L alone: a pass over sub-set (sub, colour) of
     // ntiles 32-site tiles (finalize != 0 closes the sweep), and the sample

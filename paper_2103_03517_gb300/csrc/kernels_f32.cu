@@ -94,11 +94,13 @@ void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour,
     else row_pass_g<0, MINB, MINB - 1>(g, ntiles, c, colour, measure, shape, s);
 }
 
+// the all-periodic instance samples red sites first and stores their field
+// (the next constrained sweep's red field); the other keeps black
 template <int GEN>
 void row_sample_g(const GroupArgs& g, uint32_t ntiles, cudaStream_t s) {
     constexpr int B = GEN ? MINB_GEN : MINB;
     static const uint32_t cap = resident_blocks(row_pass_kernel<B, 2, GEN, 0>);
-    row_pass_kernel<B, 2, GEN, 0><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, nullptr, 1);
+    row_pass_kernel<B, 2, GEN, 0><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, nullptr, GEN ? 1 : 0);
 }
 
 void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {

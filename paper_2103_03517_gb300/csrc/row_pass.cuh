@@ -136,9 +136,14 @@ __device__ __forceinline__ V3<float> grain_axis(const LatParams& p, int colour, 
     return V3<float>{a.x, a.y, a.z};
 }
 
-// MOVE = 0: no moves; the sample of the current state with colour = 1 (each
-// black site, the red site with its index and its six bonds), closing the
-// lattice's sweep as the standalone sample does after a constrained sweep.
+// MOVE = 0: no moves; the sample of the current state, closing the lattice's
+// sweep as the standalone sample does after a constrained sweep: with colour
+// c, each site of colour c, the site of the other colour with its index, and
+// the six bonds of the first (every bond has one end of each colour).  With
+// colour 0 and a constrained lattice (LatParams::pfield set) it also stores
+// the red sites' neighbour sums as the field of the next sweep's red pair
+// pass: the same terms in the same order as pair_field_kernel's (the -x, +x
+// pair commutes), so the same bits.
 template <int MINB, int MEASURE, int GEN, int MOVE = 1>
 __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uint32_t ntiles,
                                                                 const float* __restrict__ cone, int colour) {
@@ -185,6 +190,13 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                     Sf[v] = acc ? Sn : S[v];
                     nacc += acc ? 1u : 0u;
                     any = any || acc;
+                }
+            }
+            if constexpr (MOVE == 0 && GEN == 0) {
+                if (colour == 0 && p.pfield) {
+                    Spin4<float>* fld = static_cast<Spin4<float>*>(p.pfield) + q0 + 2u * uint32_t(lane);
+                    fld[0] = Spin4<float>{h[0].x, h[0].y, h[0].z, 0.0f};
+                    fld[1] = Spin4<float>{h[1].x, h[1].y, h[1].z, 0.0f};
                 }
             }
             if (any) {  // both sites of the pair in one 8-byte store per component

@@ -639,6 +639,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return MC_OK;
     }
+    bool red_field_ready = false;  // the next constrained sweep's red field is stored
     for (int i = 0; i < n; ++i) {
         if (!constrained) {
             timed([&] { colour_pass(0, 0); });
@@ -649,7 +650,9 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
                 k.mlong(ls.all, ls.nt_all, s);
             }
             for (int colour = 0; colour < 2; ++colour) {
-                k.pair_field(ls.all, ls.nt_all, colour, ls.shape.field, s);
+                // a measured sweep of all-periodic row lattices leaves the red field
+                // behind in its sample (row_sample); otherwise sum it here
+                if (!(colour == 0 && red_field_ready)) k.pair_field(ls.all, ls.nt_all, colour, ls.shape.field, s);
                 timed([&] {
                     if (ls.nt_pairs) k.pair_pass(ls.pairs, ls.nt_pairs, cone, colour, 0, ls.shape.pair, 0, s);
                     if (ls.nt_pairs_lead)
@@ -657,11 +660,13 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
                 });
             }
             if (!measure) k.sweep_end(ls.all, s);  // a measured sweep ends in its sample
+            red_field_ready = false;
             if (measure) {
                 if (k.row_sample) {  // row-layout lattices sample in the row kernels
                     if (ls.nt_row) k.row_sample(ls.row, ls.nt_row, 0, s);
                     if (ls.nt_rowx) k.row_sample(ls.rowx, ls.nt_rowx, 1, s);
                     if (ls.nt_rest) k.measure(ls.rest, ls.nt_rest, s);
+                    red_field_ready = ls.nt_row && !ls.nt_rowx && !ls.nt_rest;
                 } else {
                     k.measure(ls.all, ls.nt_all, s);
                 }
