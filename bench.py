@@ -41,7 +41,7 @@ LATSTATE_BYTES = 400           # device state block read back by mc_measure
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "row_pass_f32_batched_mT.txt")
 KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/row_pass.cuh", "paper_2103_03517_gb300/csrc/pass_impl.cuh",
                   "paper_2103_03517_gb300/csrc/device_common.cuh", "paper_2103_03517_gb300/csrc/kernels_f32.cu",
-                  "paper_2103_03517_gb300/csrc/mc_internal.h"]
+                  "paper_2103_03517_gb300/csrc/launchers_common.cuh", "paper_2103_03517_gb300/csrc/mc_internal.h"]
 
 
 def workload_config():
