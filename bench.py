@@ -268,9 +268,10 @@ def gpu_arm(args, cfg):
               for s in specs]
         g = mc.mc_group_create(hs)
         # launch shapes picked by the autotuner (the chains are left unchanged)
-        tuned = mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
-        cfg["autotuned"] = {"row_kernel_blocks_per_sm": [3, 2][tuned["row"]],
-                            "ms_per_sweep": [round(x, 4) for x in tuned["row_ms"][:2]]}
+        if not args.no_autotune:
+            tuned = mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
+            cfg["autotuned"] = {"row_kernel_blocks_per_sm": [3, 2][tuned["row"]],
+                                "ms_per_sweep": [round(x, 4) for x in tuned["row_ms"][:2]]}
         mc.mc_group_sweep(g, args.warmup, measure=True)
         torch.cuda.synchronize()
         if world > 1:
@@ -320,7 +321,7 @@ def gpu_arm(args, cfg):
         extra = {}
         side = "none" if args.quick else args.side
         if rank == 0 and side != "none":
-            extra = secondary(mc, torch, stream, local, side)
+            extra = secondary(mc, torch, stream, local, side, tune=not args.no_autotune)
             if side in ("all", "serving"):
                 extra["serving"] = serving(mc)
         mc.mc_group_destroy(g)
@@ -347,7 +348,7 @@ def gpu_arm(args, cfg):
         torch.distributed.destroy_process_group()
 
 
-def secondary(mc, torch, stream, dev, side="all"):
+def secondary(mc, torch, stream, dev, side="all", tune=True):
     """Side measurements reported with the headline: the same batch as 32
     sequential one-lattice FP64 runs (per-launch baseline of the batched
     path), and the constrained workload (80 x 64^3 pair sweeps)."""
@@ -355,7 +356,7 @@ def secondary(mc, torch, stream, dev, side="all"):
     if side in ("all", "fp64"):
         out.update(fp64_per_lattice(mc, torch, stream, dev))
     if side in ("all", "constrained"):
-        out.update(constrained(mc, torch, stream, dev))
+        out.update(constrained(mc, torch, stream, dev, tune))
     if side in ("all", "anisotropy"):
         out.update(anisotropy(mc, torch, stream, dev))
     if side in ("all", "general"):
@@ -392,7 +393,7 @@ def fp64_per_lattice(mc, torch, stream, dev):
     return out
 
 
-def constrained(mc, torch, stream, dev):
+def constrained(mc, torch, stream, dev, tune=True):
     out = {}
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sweeps = 10
@@ -408,7 +409,7 @@ def constrained(mc, torch, stream, dev):
     th = [r[1] for r in runs]
     ph = [r[2] for r in runs]
     mc.mc_group_constrained_sweep(g, th, ph, 4, measure=True)
-    tuned = mc.mc_group_autotune(g, 2, mc.MC_TUNE_CONSTRAINED)
+    tuned = mc.mc_group_autotune(g, 2, mc.MC_TUNE_CONSTRAINED) if tune else None
     torch.cuda.synchronize()
     a.record(stream)
     mc.mc_group_constrained_sweep(g, th, ph, sweeps, measure=True)
@@ -418,10 +419,11 @@ def constrained(mc, torch, stream, dev):
     out["constrained"] = {"value": nc * sweeps / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
                           "workload": "80 x 64^3 constrained runs (theta_c 0..90, phi_c 0/45, 4 T), FP32, "
                                       "pair halves counted as updates",
-                          "autotuned": {"field_tiles_per_step": [4, 8, 2][tuned["field"]],
-                                        "pair_tiles_per_step": [4, 8, 2][tuned["pair"]],
-                                        "field_ms": [round(x, 4) for x in tuned["field_ms"][:3]],
-                                        "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:3]]}}
+                          "autotuned": None if tuned is None else {
+                              "field_tiles_per_step": [4, 8, 2][tuned["field"]],
+                              "pair_tiles_per_step": [4, 8, 2][tuned["pair"]],
+                              "field_ms": [round(x, 4) for x in tuned["field_ms"][:3]],
+                              "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:3]]}}
     mc.mc_group_destroy(g)
     for h in hs:
         mc.mc_destroy(h)
@@ -684,6 +686,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (for profiler runs, whose timings would mislead the tuner)")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
                     choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "films",
