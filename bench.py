@@ -503,29 +503,32 @@ def stiffness(mc, torch, stream, dev):
 
 
 def films(mc, torch, stream, dev):
-    """Sec. 4 at reduced size: granular films 256 x 256 x Lz (Lz = 4, 8; x, y
-    periodic, z open), Voronoi grains of mean diameter 16, 32 and 64 sites
+    """Sec. 4 at reduced size: granular films 512 x 512 x Lz (Lz = 4, 8; x, y
+    periodic, z open), Voronoi grains of mean diameter 32, 64 and 128 sites
     with a random easy axis each (K_u = 0.02), m(T) at T = 0.1 .. 1.7 from
-    per-grain samples, and the average Curie temperature of Eq. 8 (20
-    terms); the continuous film of each thickness by Eq. 3.  1000 + 2000
-    sweeps per point, a grain sample every 20; wall time of each study."""
+    per-grain samples; the continuous film of each thickness by Eq. 3 (T_C
+    and beta), and the average Curie temperature of Eq. 8 (20 terms, every
+    term with the continuous film's beta).  1500 + 3000 sweeps per point, a
+    grain sample every 20; wall time of each study."""
     from paper_2103_03517_gb300.studies import film_curie_study
     temps = [round(0.1 * i, 2) for i in range(1, 18)]
+    kw = dict(n_eq=1500, n_meas=3000, stream=stream.cuda_stream, device=dev)
     out = {}
     for Lz in (4, 8):
-        dims = (256, 256, Lz)
-        c = film_curie_study(dims, None, None, None, temps, stream=stream.cuda_stream, device=dev)
-        row = {"continuous": {"T_C": round(c["fit"]["T_C"], 4), "seconds": round(c["seconds"], 2)}}
-        for d in (16, 32, 64):
-            gid, mask, axes = workloads.voronoi_film(256, 256, Lz, float(d), seed=d + Lz)
-            r = film_curie_study(dims, gid, mask, axes, temps, stream=stream.cuda_stream, device=dev)
+        dims = (512, 512, Lz)
+        c = film_curie_study(dims, None, None, None, temps, **kw)
+        row = {"continuous": {"T_C": round(c["fit"]["T_C"], 4), "beta": round(c["fit"]["beta"], 3),
+                              "seconds": round(c["seconds"], 2)}}
+        for d in (32, 64, 128):
+            gid, mask, axes = workloads.voronoi_film(512, 512, Lz, float(d), seed=d + Lz)
+            r = film_curie_study(dims, gid, mask, axes, temps, beta=c["fit"]["beta"], **kw)
             row[f"grains_d{d}"] = {"grains": int(gid.max()) + 1, "T_C_mean": round(r["fit"]["T_C_mean"], 4),
                                    "beta": r["fit"]["beta"], "rms": round(r["fit"]["rms"], 5),
                                    "m": [round(x, 4) for x in r["m"]], "seconds": round(r["seconds"], 2),
                                    "updates_per_s": r["updates"] / r["seconds"]}
         out[f"Lz{Lz}"] = row
-    return {"films": {"workload": "Sec. 4 at reduced size: 256x256xLz films, Lz = 4, 8; Voronoi grains d = 16, "
-                                  "32, 64; T = 0.1..1.7 (17 points), 1000 + 2000 sweeps, FP32",
+    return {"films": {"workload": "Sec. 4 at reduced size: 512x512xLz films, Lz = 4, 8; Voronoi grains d = 32, "
+                                  "64, 128; T = 0.1..1.7 (17 points), 1500 + 3000 sweeps, FP32",
                       "temperatures": temps, "results": out}}
 
 

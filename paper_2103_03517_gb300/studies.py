@@ -131,7 +131,7 @@ def exchange_stiffness_study(K_over_J, temps, wall_dims=(256, 64, 64), uniform_d
 
 
 def film_curie_study(dims, grain_id, bond_mask, grain_axis, temps, K_u=0.02, n_eq=1000, n_meas=2000, every=20,
-                     n_terms=20, seed=1, precision=mc.MC_FP32, stream=None, device=0):
+                     n_terms=20, beta=None, seed=1, precision=mc.MC_FP32, stream=None, device=0):
     """m(T) of a granular film and its average Curie temperature (Sec. 4,
     Eq. 8).  The film (x, y periodic, z open; grain tables as for
     mc_create_ex: bonds only inside a grain, one uniaxial easy axis per
@@ -139,9 +139,12 @@ def film_curie_study(dims, grain_id, bond_mask, grain_axis, temps, K_u=0.02, n_e
     every `every` measured sweeps each run takes a grain sample.  The film's
     m(T) = sum_g w_g <m_g>(T), w_g = N_g / N (columnar grains: weight by
     area), and the weighted Bloch series of Eq. 8 with n_terms terms gives
-    T_C_mean.  With grain_id None the film is continuous (one grain, no bond
-    mask, easy axis z): m(T) = <|m|> and Eq. 3 gives its T_C.  Returns a dict:
-    T, m, the fit, spin-updates and wall time."""
+    T_C_mean; beta fixes the exponent of every term (the continuous film's
+    own, from Eq. 3, is the natural choice: the grains are the same material
+    at the same thickness), None searches it.  With grain_id None the film is
+    continuous (one grain, no bond mask, easy axis z): m(T) = <|m|> and Eq. 3
+    gives its T_C and beta.  Returns a dict: T, m, the fit, spin-updates and
+    wall time."""
     temps = [float(t) for t in temps]
     N = int(np.prod(dims))
     grains = grain_id is not None
@@ -182,7 +185,7 @@ def film_curie_study(dims, grain_id, bond_mask, grain_axis, temps, K_u=0.02, n_e
             mc.mc_destroy(h)
     T = np.array(temps)
     if grains:
-        fit = an.multi_bloch_fit(T, m, n_terms)
+        fit = an.multi_bloch_fit(T, m, n_terms, betas=None if beta is None else [round(float(beta), 2)])
         fit = {"T_C_mean": fit["T_C_mean"], "beta": fit["beta"], "rms": fit["rms"],
                "w": fit["w"].tolist(), "T_C": fit["T_C"].tolist()}
     else:  # Eq. 3 over the ordered range (m above 0.3, below it the finite film's tail)
