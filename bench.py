@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -45,7 +46,7 @@ KERNEL_SOURCES = ["paper_2103_03517_gb300/csrc/row_pass.cuh", "paper_2103_03517_
 
 
 def workload_config():
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     n = sum(s.N for s in specs)
     return specs, n, {
         "workload": "batched m(T) sweep: 32 periodic sc lattices 16^3/32^3/64^3/128^3 cycled, "
@@ -100,7 +101,7 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mc_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -169,7 +170,7 @@ def _oracle_worker(args):
     idx, n_warm, n_steps, barrier = args
     import oracle
 
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     lats = []
     for i in idx:
         s = specs[i]
@@ -190,7 +191,7 @@ def run_oracle(lattice_ids, n_warm, n_steps):
     (updates per second over the timed sweeps, cores used)."""
     import oracle
     oracle.build()
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     cores = max(1, min(len(lattice_ids), os.cpu_count() or 1))
     # balance by size: largest first onto the least loaded core
     bins = [[] for _ in range(cores)]
@@ -221,7 +222,7 @@ def reference_arm(args, cfg):
         return
     sample = [i for i in range(32) if i % 4 in (0, 1)]
     rate, cores = run_oracle(sample, args.warmup, args.steps)
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     per_step = sum(specs[i].N for i in sample)
     sample_desc = f"{len(sample)} lattices (the 16^3 and 32^3 ones), {args.steps} measurement sweeps each"
     line = {
@@ -372,7 +373,7 @@ def secondary(mc, torch, stream, dev, side="all", tune=True):
 
 def fp64_per_lattice(mc, torch, stream, dev):
     out = {}
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     n = sum(s.N for s in specs)
     sweeps = 10
     hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP64,
@@ -397,7 +398,7 @@ def constrained(mc, torch, stream, dev, tune=True):
     out = {}
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sweeps = 10
-    runs = workloads.config3()
+    runs = workloads.constrained_64c_runs()
     hs = []
     for spec, th, ph in runs:
         t, p = math.radians(th), math.radians(ph)
@@ -533,12 +534,12 @@ def films(mc, torch, stream, dev):
 
 
 def precision(mc, torch, stream, dev):
-    """FP32 against FP64 (which is the oracle's chain bit for bit), as the
-    north star asks each FP32 result's error to be stated.  Config 1 (16^3,
-    K_u = 0.01, T = 0.5, 1000 + 1000 sweeps) over 8 seeds per precision:
+    """FP32 against FP64 (which is the oracle's chain bit for bit), so that
+    each FP32 result's error is stated.  The 16^3 point (K_u = 0.01,
+    T = 0.5, 1000 + 1000 sweeps) over 8 seeds per precision:
     differences of the seed means of <|m|>, <m_z>, chi_l and <E/N>, with the
     standard error of the difference from the spread between seeds.  The 32
-    lattices of config 2 (500 + 1000 sweeps, one run each): the difference of
+    lattices of the batched m(T) workload (500 + 1000 sweeps, one run each): the difference of
     <|m|> per lattice against its blocking error; the largest |difference| and
     the largest |difference| / sigma."""
     import numpy as np
@@ -571,8 +572,8 @@ def precision(mc, torch, stream, dev):
         c1[k] = {"fp32": round(float(a.mean()), 6), "fp64": round(float(b.mean()), 6),
                  "diff": float(a.mean() - b.mean()),
                  "sigma": float(np.hypot(a.std(ddof=1), b.std(ddof=1)) / np.sqrt(len(a)))}
-    out["config1_16c_T0.5_8_seeds"] = c1
-    specs = workloads.config2()
+    out["point_16c_T0.5_8_seeds"] = c1
+    specs = workloads.batched_mt_32()
     ser = {}
     for prec in (mc.MC_FP32, mc.MC_FP64):
         hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=prec, ring_capacity=1000,
@@ -587,7 +588,7 @@ def precision(mc, torch, stream, dev):
             mc.mc_destroy(h)
     d = np.array([a.mean() - b.mean() for a, b in zip(ser[mc.MC_FP32], ser[mc.MC_FP64])])
     sg = np.array([np.hypot(blocking_error(a), blocking_error(b)) for a, b in zip(ser[mc.MC_FP32], ser[mc.MC_FP64])])
-    out["config2_32_lattices"] = {"max_abs_diff_ml": float(np.abs(d).max()),
+    out["batched_mT_32_lattices"] = {"max_abs_diff_ml": float(np.abs(d).max()),
                                   "max_abs_diff_over_sigma": float(np.abs(d / np.maximum(sg, 1e-12)).max()),
                                   "lattices_within_2e-3_or_3sigma": int(np.sum((np.abs(d) <= 2e-3) | (np.abs(d) <= 3 * sg))),
                                   "diff_ml": [round(float(x), 5) for x in d], "sigma": [round(float(x), 5) for x in sg]}
@@ -601,7 +602,7 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
     mask and grain axes, z open) and an fcc lattice of 128^3 cells (8,388,608
     spins, T = 2.0), measured sweeps, CUDA events."""
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    spec = workloads.config4()[3]
+    spec = workloads.bloch_wall_1024()[3]
     gid, mask, axes = workloads.voronoi_film(1024, 1024, 15, 10.0, seed=1)
     cases = [("wall", spec.dims, mc.make_desc(spec.dims, K_u=spec.Ku, T=spec.T, seed=spec.seed, boundary=spec.bc,
                                               init=mc.MC_INIT_WALL, ring_capacity=16, stream=stream.cuda_stream,

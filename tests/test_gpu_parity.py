@@ -87,10 +87,10 @@ def assert_same_stats(h, o):
 
 
 # ------------------------------------------------------- FP64 bit-exactness
-def test_fp64_config1_bit_exact():
+def test_fp64_point_16c_bit_exact():
     """16^3 periodic, K_u = 0.01 z, T = 0.5, seed 0, all +z: 1, 10 and
     1000 + 1000 sweeps."""
-    c = workloads.config1()
+    c = workloads.point_16c()
     h, o = make_pair(c.dims, Ku=c.Ku, T=c.T, seed=c.seed, ring=1000)
     try:
         mc.mc_sweep(h, 1)
@@ -447,10 +447,10 @@ def test_checkpoint_resume_is_bit_exact(prec, tmp_path):
 
 
 # ------------------------------------------- full size, bench launch config
-def test_config2_full_size_fp64_two_sweeps_bit_exact():
+def test_batched_mt_full_size_fp64_two_sweeps_bit_exact():
     """All 32 lattices of the batched m(T) workload (19,169,280 spins) in one
     group, FP64: two sweeps agree with the oracle bit for bit."""
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, precision=mc.MC_FP64,
                                        ring_capacity=4)) for s in specs]
     g = mc.mc_group_create(hs)
@@ -462,7 +462,7 @@ def test_config2_full_size_fp64_two_sweeps_bit_exact():
             o = oracle.Lattice(s.dims, Ku=s.Ku, T=s.T, seed=s.seed, ring_cap=4)
             o.sweep(1)
             o.sweep(1, measure=True)
-            assert_same_state(h, o, f"config2 L={s.dims[0]} T={s.T:.2f}")
+            assert_same_state(h, o, f"batched m(T) L={s.dims[0]} T={s.T:.2f}")
             assert_same_stats(h, o)
     finally:
         mc.mc_group_destroy(g)
@@ -470,11 +470,11 @@ def test_config2_full_size_fp64_two_sweeps_bit_exact():
             mc.mc_destroy(h)
 
 
-def test_config2_full_size_fp32_properties():
+def test_batched_mt_full_size_fp32_properties():
     """The bench's FP32 group of 32 lattices: after 400 sweeps every spin is a
     unit vector, cone angles settled with acceptance near one half, and the
     coldest lattice obeys equipartition E/N = -3J - K_u + T (any size)."""
-    specs = workloads.config2()
+    specs = workloads.batched_mt_32()
     hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, ring_capacity=256)) for s in specs]
     g = mc.mc_group_create(hs)
     try:
@@ -621,13 +621,13 @@ def test_fp32_constrained_site_order_equals_pair_order(dims):
     assert abs(out[0][1].e - out[1][1].e) <= 1e-9
 
 
-# ------------------------- full size: configs 3, 4 and 5 (bench workloads)
-def test_config3_full_size_lattice_fp64_constrained_bit_exact():
+# ------------------------- full size: constrained 64^3, Bloch wall, granular film (bench workloads)
+def test_constrained_64c_full_size_lattice_fp64_bit_exact():
     """One lattice of the constrained workload at its full size (64^3,
     theta_c = 40, phi_c = 45, T = 0.2), FP64: two constrained sweeps, the
     second measured, equal the oracle's chain bit for bit (spins, theta,
     samples with the torque)."""
-    spec, th, ph = workloads.config3()[14]
+    spec, th, ph = workloads.constrained_64c_runs()[14]
     R = oracle.constraint_frame(th, ph)
     spins = workloads.uniform_spins(spec.N, R[0])
     h, o = make_pair(spec.dims, Ku=spec.Ku, Kc=spec.Kc, T=spec.T, seed=spec.seed, ring=4, spins=spins)
@@ -636,19 +636,19 @@ def test_config3_full_size_lattice_fp64_constrained_bit_exact():
         o.constrained_sweep(th, ph, 1)
         mc.mc_constrained_sweep(h, th, ph, 1, measure=True)
         o.constrained_sweep(th, ph, 1, measure=True)
-        assert_same_state(h, o, "config3 64^3")
+        assert_same_state(h, o, "constrained 64^3")
         assert_same_samples(h, o, 1)
     finally:
         mc.mc_destroy(h)
 
 
-def test_config3_full_size_fp32_batch_properties():
+def test_constrained_64c_full_size_fp32_batch_properties():
     """The bench's FP32 constrained batch (80 x 64^3, site order): after 20
     sweeps every lattice keeps its transverse magnetisation at zero and its
     projection on e_C positive (to FP32 rounding of the compensation), spins
     stay unit vectors (the partner is not renormalised: to FP32 rounding),
     and the acceptance sits at one half or the cone is fully open."""
-    runs = workloads.config3()
+    runs = workloads.constrained_64c_runs()
     hs = []
     for spec, th, ph in runs:
         R = oracle.constraint_frame(th, ph)
@@ -673,11 +673,11 @@ def test_config3_full_size_fp32_batch_properties():
             mc.mc_destroy(h)
 
 
-def test_config4_full_size_wall_fp64_bit_exact():
+def test_wall_1024x128x128_full_size_fp64_bit_exact():
     """The Bloch-wall lattice at its full size (1024 x 128 x 128, x pinned,
     16,777,216 spins, T = 0.66), FP64: one sweep and one measured sweep equal
     the oracle's chain bit for bit; the pinned planes keep +z and -z."""
-    spec = workloads.config4()[3]
+    spec = workloads.bloch_wall_1024()[3]
     spins = workloads.wall_spins(spec.dims)
     h, o = make_pair(spec.dims, Ku=spec.Ku, T=spec.T, seed=spec.seed, bc=spec.bc, ring=4, spins=spins)
     try:
@@ -685,7 +685,7 @@ def test_config4_full_size_wall_fp64_bit_exact():
         o.sweep(1)
         mc.mc_sweep(h, 1, measure=True)
         o.sweep(1, measure=True)
-        assert_same_state(h, o, "config4 wall")
+        assert_same_state(h, o, "Bloch wall 1024x128x128")
         assert_same_samples(h, o, 1)
         S = mc.mc_get_spins(h, spec.N).reshape(spec.dims[2], spec.dims[1], spec.dims[0], 3)
         assert np.all(S[:, :, 0, 2] == 1.0) and np.all(S[:, :, -1, 2] == -1.0)
@@ -693,7 +693,7 @@ def test_config4_full_size_wall_fp64_bit_exact():
         mc.mc_destroy(h)
 
 
-def test_config5_full_size_film_fp64_bit_exact():
+def test_film_1024x1024x15_full_size_fp64_bit_exact():
     """The serving mix's granular film at its full size (1024 x 1024 x 15,
     Voronoi grains of mean diameter 10, 15,728,640 spins), FP64: one sweep and
     one measured sweep equal the oracle's chain bit for bit."""
@@ -705,7 +705,7 @@ def test_config5_full_size_film_fp64_bit_exact():
         o.sweep(1)
         mc.mc_sweep(h, 1, measure=True)
         o.sweep(1, measure=True)
-        assert_same_state(h, o, "config5 film")
+        assert_same_state(h, o, "film 1024x1024x15")
         assert_same_samples(h, o, 1)
     finally:
         mc.mc_destroy(h)

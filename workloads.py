@@ -41,16 +41,16 @@ class LatticeSpec:
 # The five workloads (reduced units J = 1, k_B = 1).
 # --------------------------------------------------------------------------
 
-def config1() -> LatticeSpec:
+def point_16c() -> LatticeSpec:
     """16^3 periodic, FP64, K_u = 0.01 along z, T = 0.5, seed 0, all +z;
     1000 equilibration + 1000 measurement sweeps."""
     return LatticeSpec(dims=(16, 16, 16), Ku=0.01, T=0.5, seed=0)
 
 
-CONFIG1_SWEEPS = (1000, 1000)
+POINT_16C_SWEEPS = (1000, 1000)
 
 
-def config2() -> list:
+def batched_mt_32() -> list:
     """Batched m(T) sweep: 32 periodic lattices, L = 16, 32, 64, 128 cycled,
     T_i = 0.05 (i + 1), K_u = 0.01 along z, seed i; FP32 spins."""
     sizes = (16, 32, 64, 128)
@@ -58,10 +58,10 @@ def config2() -> list:
             for i in range(32)]
 
 
-CONFIG2_SWEEPS = (2000, 5000)
+BATCHED_MT_SWEEPS = (2000, 5000)
 
 
-def config3() -> list:
+def constrained_64c_runs() -> list:
     """Constrained anisotropy runs: 64^3 periodic, K_u = 0.05 along z,
     K_c = 0.02; theta_c in 0..90 (10 steps), phi_c in {0, 45},
     T in {0.2, 0.6, 1.0, 1.3}.  Returns (spec, theta_c, phi_c) tuples."""
@@ -75,10 +75,10 @@ def config3() -> list:
     return runs
 
 
-CONFIG3_SWEEPS = (3000, 5000)
+CONSTRAINED_64C_SWEEPS = (3000, 5000)
 
 
-def config4() -> list:
+def bloch_wall_1024() -> list:
     """Bloch wall: 1024 x 128 x 128, x pinned (x = 0 at +z, x = 1023 at -z),
     y, z periodic, K_u = 0.05 along z, 8 temperatures 0.1..1.4, seed = index."""
     Ts = np.linspace(0.1, 1.4, 8)
@@ -86,7 +86,7 @@ def config4() -> list:
                         bc=(PINNED, PERIODIC, PERIODIC)) for i, T in enumerate(Ts)]
 
 
-CONFIG4_SWEEPS = (2000, 4000)
+BLOCH_WALL_SWEEPS = (2000, 4000)
 
 
 # --------------------------------------------------------------------------
