@@ -300,7 +300,7 @@ def gpu_arm(args, cfg):
 
         # end to end through the C ABI with host buffers: per step the whole
         # spin state goes host -> device from pinned memory, one measurement
-        # sweep runs, and every lattice's observables come back
+        # sweep runs, and every lattice's observables come back (one wait)
         sizes = [mc.mc_state_bytes(h) for h in hs]
         host = [torch.empty(b, dtype=torch.uint8, pin_memory=True) for b in sizes]
         for h, buf, b in zip(hs, host, sizes):
@@ -312,8 +312,7 @@ def gpu_arm(args, cfg):
             for h, buf, b in zip(hs, host, sizes):
                 mc.mc_import_state(h, buf.data_ptr(), b)
             mc.mc_group_sweep(g, 1, measure=True)
-            for h in hs:
-                mc.mc_measure(h)
+            mc.mc_group_measure(g, len(hs))
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e = {"value": world * n_spins * e2e_steps / e2e_s, "unit": UNIT,

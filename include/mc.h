@@ -310,6 +310,16 @@ MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_d
 MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms,
                                 int* launches);
 
+/* Ensemble averages of every lattice of the group (Sec. 3, Eq. 6), as
+ * mc_measure gives them, read with one wait on the group stream instead of
+ * one per lattice.  out: caller-owned array of n = the group's size, in the
+ * order of the handles given to mc_group_create.  The first call allocates a
+ * pinned host staging area of n device-state records, freed with the group.
+ * Synchronises.  Errors: MC_ERR_ARG (null, n not the group's size),
+ * MC_ERR_CUDA; the first member's sticky device error after every entry is
+ * filled in. */
+MC_API int mc_group_measure(mc_group_handle g, mc_observables* out, int n);
+
 MC_API int mc_group_sync(mc_group_handle g);
 
 /* ------------------------------------------------------------- autotuner */

@@ -123,6 +123,7 @@ _SIGS = {
     "mc_group_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mc_group_constrained_sweep": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double), C.c_int, C.c_int]),
     "mc_group_time_passes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
+    "mc_group_measure": (C.c_int, [C.c_void_p, _P(mc_observables), C.c_int]),
     "mc_group_sync": (C.c_int, [C.c_void_p]),
     "mc_group_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
     "mc_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
@@ -388,6 +389,13 @@ def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):
     n = C.c_int()
     _check(lib().mc_group_time_passes(g, int(n_sweeps), int(bool(measure)), C.byref(avg), C.byref(n)))
     return avg.value, n.value
+
+
+def mc_group_measure(g, n: int) -> list:
+    """Observables of the group's n lattices (creation order), one wait."""
+    arr = (mc_observables * int(n))()
+    _check(lib().mc_group_measure(g, arr, int(n)))
+    return list(arr)
 
 
 def mc_group_sync(g) -> None:

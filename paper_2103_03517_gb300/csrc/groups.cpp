@@ -21,6 +21,7 @@ struct mc_group {
     LaunchSet ls;
     const void* cone = nullptr;
     SweepGraphs graphs;  // captured sweeps of the whole group
+    LatState* h_states = nullptr;  // pinned staging of mc_group_measure, one per member
 };
 
 static int group_run(mc_group* g, int n, int measure, bool constrained) {
@@ -134,6 +135,7 @@ MC_API int mc_group_destroy(mc_group_handle g) {
     cudaStreamSynchronize(g->stream);
     destroy_graphs(g->graphs);
     cudaFree(g->d_mem);
+    if (g->h_states) cudaFreeHost(g->h_states);
     for (size_t i = 0; i < g->lats.size(); ++i) g->lats[i]->stream = g->member_streams[i];
     delete g;
     return MC_OK;
@@ -191,6 +193,33 @@ MC_API int mc_group_autotune(mc_group_handle g, int sweeps, int what, mc_tune_re
     const int rc = autotune(g->precision, g->ls, g->lats, g->cone, sweeps, what, g->stream, out);
     if (rc) return rc;
     destroy_graphs(g->graphs);  // captured with the old shapes
+    return MC_OK;
+}
+
+MC_API int mc_group_measure(mc_group_handle g, mc_observables* out, int n) {
+    if (!g || !out || n != int(g->lats.size())) return fail(MC_ERR_ARG, "invalid argument");
+    cudaSetDevice(g->device);
+    if (!g->h_states) {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&g->h_states), sizeof(LatState) * size_t(n));
+        if (e != cudaSuccess) {
+            g->h_states = nullptr;
+            return cuda_fail(e, "cudaMallocHost(group measure)");
+        }
+    }
+    // every member runs on the group stream: one copy each, one wait
+    for (int i = 0; i < n; ++i) {
+        const cudaError_t e = cudaMemcpyAsync(&g->h_states[i], &g->lats[i]->d_lat->st, sizeof(LatState),
+                                              cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "group measure copy");
+    }
+    const cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "group measure sync");
+    int first = MC_OK;
+    for (int i = 0; i < n; ++i) {
+        const int rc = observables_from(g->lats[i], g->h_states[i], &out[i]);
+        if (rc && first == MC_OK) first = rc;
+    }
+    if (first != MC_OK) return fail(first, "device reported error %d", first);
     return MC_OK;
 }
 

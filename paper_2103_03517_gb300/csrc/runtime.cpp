@@ -722,6 +722,40 @@ int read_state(mc_lattice* h, LatState* st) {
     return MC_OK;
 }
 
+// Ensemble averages of Sec. 3 (Eq. 6 in reduced units) from a copy of the
+// lattice's device state; returns the sticky device error, if any.
+int observables_from(const mc_lattice* h, const LatState& st, mc_observables* out) {
+    std::memset(out, 0, sizeof *out);
+    const double* mo = st.moments;
+    const double n = mo[kMomN];
+    out->n_samples = (int64_t)n;
+    out->sweeps_done = st.sweep;
+    out->theta_deg = st.theta;
+    out->error = st.error;
+    out->accept_last = double(st.last_acc) / double(h->hp.n_mov > 0 ? h->hp.n_mov : 1);
+    if (n > 0) {
+        for (int a = 0; a < 3; ++a) {
+            out->m[a] = mo[kMomM + a] / n;
+            out->m2[a] = mo[kMomM2 + a] / n;
+            out->m_abs[a] = mo[kMomMabs + a] / n;
+            out->torque[a] = mo[kMomTq + a] / n;
+            out->torque2[a] = mo[kMomTq2 + a] / n;
+        }
+        out->ml = mo[kMomMl] / n;
+        out->ml2 = mo[kMomMl2] / n;
+        out->ml4 = mo[kMomMl4] / n;
+        out->e = mo[kMomE] / n;
+        out->e2 = mo[kMomE2] / n;
+        for (int a = 0; a < 4; ++a) out->e_parts[a] = mo[kMomParts + a] / n;
+        const double NT = double(h->hp.N) / h->hp.T;
+        out->chi[0] = NT * (out->ml2 - out->ml * out->ml);
+        for (int a = 0; a < 3; ++a) out->chi[1 + a] = NT * (out->m2[a] - out->m[a] * out->m[a]);
+        out->binder = out->ml2 > 0 ? 1.0 - out->ml4 / (3.0 * out->ml2 * out->ml2) : 0.0;
+    }
+    if (st.error) return fail(st.error, "device reported error %d", st.error);
+    return MC_OK;
+}
+
 }  // namespace mcgb
 
 using namespace mcgb;
@@ -839,35 +873,7 @@ MC_API int mc_measure(mc_handle h, mc_observables* out) {
     LatState st;
     int rc = read_state(h, &st);
     if (rc) return rc;
-    std::memset(out, 0, sizeof *out);
-    const double* mo = st.moments;
-    const double n = mo[kMomN];
-    out->n_samples = (int64_t)n;
-    out->sweeps_done = st.sweep;
-    out->theta_deg = st.theta;
-    out->error = st.error;
-    out->accept_last = double(st.last_acc) / double(h->hp.n_mov > 0 ? h->hp.n_mov : 1);
-    if (n > 0) {
-        for (int a = 0; a < 3; ++a) {
-            out->m[a] = mo[kMomM + a] / n;
-            out->m2[a] = mo[kMomM2 + a] / n;
-            out->m_abs[a] = mo[kMomMabs + a] / n;
-            out->torque[a] = mo[kMomTq + a] / n;
-            out->torque2[a] = mo[kMomTq2 + a] / n;
-        }
-        out->ml = mo[kMomMl] / n;
-        out->ml2 = mo[kMomMl2] / n;
-        out->ml4 = mo[kMomMl4] / n;
-        out->e = mo[kMomE] / n;
-        out->e2 = mo[kMomE2] / n;
-        for (int a = 0; a < 4; ++a) out->e_parts[a] = mo[kMomParts + a] / n;
-        const double NT = double(h->hp.N) / h->hp.T;
-        out->chi[0] = NT * (out->ml2 - out->ml * out->ml);
-        for (int a = 0; a < 3; ++a) out->chi[1 + a] = NT * (out->m2[a] - out->m[a] * out->m[a]);
-        out->binder = out->ml2 > 0 ? 1.0 - out->ml4 / (3.0 * out->ml2 * out->ml2) : 0.0;
-    }
-    if (st.error) return fail(st.error, "device reported error %d", st.error);
-    return MC_OK;
+    return observables_from(h, st, out);
 }
 
 MC_API int mc_profile_sample(mc_handle h) {

@@ -64,6 +64,7 @@ int ensure_aos(mc_lattice* h);
 void constraint_frame(double theta_deg, double phi_deg, double R[9]);
 const KernelSet& kernel_set(int precision);
 int read_state(mc_lattice* h, LatState* st);
+int observables_from(const mc_lattice* h, const LatState& st, mc_observables* out);
 // n sweeps of a launch set on stream s: whole graphs of kGraphSweeps
 // sweeps, then the remainder launched directly.
 int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* cone, int n, int measure,

@@ -283,15 +283,17 @@ def test_group_equals_alone_bitwise(prec):
     try:
         mc.mc_group_sweep(g, 37)
         mc.mc_group_sweep(g, 21, measure=True)
+        batch = mc.mc_group_measure(g, len(grouped))   # one wait, creation order
         mc.mc_group_sync(g)
         for h in alone:
             mc.mc_sweep(h, 37)
             mc.mc_sweep(h, 21, measure=True)
-        for (dims, _, _), a, b in zip(specs, grouped, alone):
+        for (dims, _, _), a, b, ga in zip(specs, grouped, alone, batch):
             N = dims[0] * dims[1] * dims[2]
             assert np.array_equal(mc.mc_get_spins(a, N), mc.mc_get_spins(b, N))
             oa, ob = mc.mc_measure(a).asdict(), mc.mc_measure(b).asdict()
             assert oa == ob
+            assert ga.asdict() == oa
     finally:
         mc.mc_group_destroy(g)
         for h in grouped + alone:
