@@ -359,6 +359,8 @@ def secondary(mc, torch, stream, dev, side="all", tune=True):
         out.update(constrained(mc, torch, stream, dev, tune))
     if side in ("all", "anisotropy"):
         out.update(anisotropy(mc, torch, stream, dev))
+    if side in ("all", "cubes"):
+        out.update(cubes(mc, torch, stream, dev, tune))
     if side in ("all", "general"):
         out.update(general_geometry(mc, torch, stream, dev))
     if side in ("all", "stiffness"):
@@ -594,6 +596,47 @@ def precision(mc, torch, stream, dev):
     return {"precision": out}
 
 
+def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
+    """The standard FP32 sweep on periodic cubes alone: one 128^3 lattice
+    (25 MB of spins, L2-resident), sixteen 128^3 lattices in one group
+    (403 MB, HBM-resident) and one 256^3 lattice (201 MB).  K_u = 0.01 z,
+    T = 0.5 .. 1.25, all +z.  Per case: spin-updates/s over measured sweeps
+    (CUDA events around the replayed graphs), and the colour pass timed
+    launch by launch against the HBM roofline (24 B per update)."""
+    peak, _ = measured_peak()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cases = [("128c_single", [128], 1), ("128c_x16", [128] * 16, 16), ("256c_single", [256], 1)]
+    out = {}
+    for name, sizes, _ in cases:
+        hs = [mc.mc_create_ex(mc.make_desc((L, L, L), K_u=0.01, T=0.5 + 0.05 * i, seed=100 + i,
+                                           ring_capacity=16, sample_torque=0, stream=stream.cuda_stream,
+                                           device=dev)) for i, L in enumerate(sizes)]
+        g = mc.mc_group_create(hs)
+        if tune:
+            mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
+        n = sum(L ** 3 for L in sizes)
+        mc.mc_group_sweep(g, 20, measure=True)
+        torch.cuda.synchronize()
+        res = {"spins": n}
+        for meas in (False, True):
+            a.record(stream)
+            mc.mc_group_sweep(g, sweeps, measure=meas)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res["measured" if meas else "unmeasured"] = n * sweeps / (a.elapsed_time(b) * 1e-3)
+            avg_ms, _ = mc.mc_group_time_passes(g, 100, measure=meas)
+            gbs = (n // 2) * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
+            res["pass_ms_measured" if meas else "pass_ms"] = round(avg_ms, 5)
+            res["frac_measured" if meas else "frac"] = round(gbs / peak, 4)
+        out[name] = res
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+    return {"cubes": {"unit": UNIT, "peak_gbs": peak, "cases": out,
+                      "workload": f"periodic FP32 cubes, {sweeps} sweeps timed per mode; frac = colour-pass "
+                                  "algorithmic bytes (24 B per update) / measured HBM peak"}}
+
+
 def general_geometry(mc, torch, stream, dev, sweeps=40):
     """FP32 throughput of the lattices that are not all-periodic simple
     cubes: the Bloch-wall lattice (1024 x 128 x 128, x pinned, T = 0.66), a
@@ -693,7 +736,7 @@ def main():
                     help="keep the default launch shapes (for profiler runs, whose timings would mislead the tuner)")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
-                    choices=["all", "none", "fp64", "constrained", "anisotropy", "general", "stiffness", "films",
+                    choices=["all", "none", "fp64", "constrained", "anisotropy", "cubes", "general", "stiffness", "films",
                              "precision", "serving"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
