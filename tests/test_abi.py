@@ -117,4 +117,7 @@ def test_null_handles_rejected():
         mc.mc_sweep(None, 1)
     with pytest.raises(mc.MCError):
         mc.mc_measure(None)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_group_measure(None, 4)
+    assert e.value.code == mc.MC_ERR_ARG
     assert mc.mc_destroy(None) is None
