@@ -516,16 +516,21 @@ __device__ __forceinline__ int lattice_of_tile(const GroupArgs& g, uint32_t tile
     return lo;
 }
 
-// Publish one warp's run of `tiles` tiles of lattice L: accepted moves,
-// fixed-point sums (lane i holds sum i), then the tile count; the warp that
-// completes the lattice's pass runs `last` on lane 0.
+// Publish one warp's run of `tiles` tiles of lattice L: accepted moves and
+// fixed-point sums (lane i holds sum i).  In a pass that closes the sweep
+// (closes != 0) the warp then counts its tiles, and the warp that completes
+// the lattice's pass runs `last` on lane 0 after a fence that orders every
+// warp's counts before it.  Any other pass stops after the counts: they are
+// read by a later launch, which the kernel boundary orders, so its warps
+// neither fence nor count.
 template <typename F>
 __device__ __forceinline__ void publish(LatState& st, int lane, unsigned nacc, bool with_sums, long long fix, int slot,
-                                        uint32_t tiles, uint32_t ntiles_lattice, F&& last) {
+                                        uint32_t tiles, uint32_t ntiles_lattice, bool closes, F&& last) {
     nacc = __reduce_add_sync(0xffffffffu, nacc);
     if (lane == 0 && nacc) atomicAdd(&st.acc, (unsigned long long)nacc);
     if (with_sums && lane < kNumSums && fix)
         atomicAdd(reinterpret_cast<unsigned long long*>(&st.sums[lane]), static_cast<unsigned long long>(fix));
+    if (!closes) return;
     __threadfence();
     __syncwarp();
     if (lane == 0) {
@@ -753,8 +758,8 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
             }
             if (measure) fix += warp_tile_fix<R, NS>(sums, lane);
         }
-        publish(L->st, lane, nacc, measure != 0, fix, colour, run, p.nblocks_site, [&] {
-            if (colour == 1) finalize_sweep(p, L->st, measure, p.sample_torque != 0);
+        publish(L->st, lane, nacc, measure != 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {
+            finalize_sweep(p, L->st, measure, p.sample_torque != 0);
         });
         ++l;
     }
@@ -1270,7 +1275,7 @@ __global__ void __launch_bounds__(kBlock) measure_kernel(GroupArgs g, uint32_t n
             }
             fix += warp_tile_fix(sums, lane);
         }
-        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, [&] { finalize_sweep(p, L->st, 1, true); });
+        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, true, [&] { finalize_sweep(p, L->st, 1, true); });
         ++l;
     }
 }

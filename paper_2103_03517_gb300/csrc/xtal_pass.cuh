@@ -109,9 +109,8 @@ __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t n
             ++nacc;
         }
     }
-    publish(L->st, lane, nacc, false, 0, colour, wc.end - wc.begin, ntiles, [&] {
-        if (finalize) finalize_sweep(p, L->st, 0, false);
-    });
+    publish(L->st, lane, nacc, false, 0, colour, wc.end - wc.begin, ntiles, finalize != 0,
+            [&] { finalize_sweep(p, L->st, 0, false); });
 }
 
 // Constrained sweeps (Table A2) of a crystal: the neighbour field of every
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t
             fix += warp_tile_fix<R, NS>(sums, lane);  // per-lane fixed point, integer warp sums
         }
     }
-    publish(L->st, lane, 0, true, fix, 3, wc.end - wc.begin, ntiles,
+    publish(L->st, lane, 0, true, fix, 3, wc.end - wc.begin, ntiles, true,
             [&] { finalize_sweep(p, L->st, 1, LEVEL >= 2); });
 }
 
