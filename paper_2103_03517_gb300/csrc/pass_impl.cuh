@@ -497,12 +497,13 @@ struct WarpChunk {
 };
 
 __device__ __forceinline__ WarpChunk warp_chunk(uint32_t ntiles) {
+    // even split: warp w takes [w T / W, (w + 1) T / W), so chunks differ by
+    // at most one tile and no warp of the launch idles while T >= W
     const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
     const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
-    const uint32_t chunk = (ntiles + nwarps - 1) / nwarps;
     WarpChunk c;
-    c.begin = min(w * chunk, ntiles);
-    c.end = min(c.begin + chunk, ntiles);
+    c.begin = uint32_t(uint64_t(w) * ntiles / nwarps);
+    c.end = uint32_t(uint64_t(w + 1) * ntiles / nwarps);
     c.lane = int(threadIdx.x & 31);
     return c;
 }
