@@ -39,7 +39,18 @@ constexpr int V = kSitesPerThreadF32;
 template <int B, int MEASURE, int GEN>
 void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
     static const uint32_t cap = resident_blocks(row_pass_kernel<B, MEASURE, GEN>);
-    row_pass_kernel<B, MEASURE, GEN><<<grid_for(ntiles, cap), kBlock, 0, s>>>(g, ntiles, cone, colour);
+    // programmatic serialisation: the pass starts its blocks while the
+    // previous launch drains and waits inside the kernel (griddepcontrol)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_for(ntiles, cap));
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, row_pass_kernel<B, MEASURE, GEN>, g, ntiles, cone, colour);
 }
 
 // launch shape 0: the default blocks per SM of the instance; 1: the other candidate

@@ -148,11 +148,18 @@ template <int MINB, int MEASURE, int GEN, int MOVE = 1>
 __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uint32_t ntiles,
                                                                 const float* __restrict__ cone, int colour) {
     constexpr int NS = MEASURE >= 2 ? kNumSums : kSumTux;  // sums sampled
+    // Programmatic dependent launch (a colour pass launched after another):
+    // the next launch's blocks may take the SM slots this launch frees, and
+    // this launch waits for the previous one to complete (its spins, cone
+    // angle and counters) before it reads any of them.  Launched without
+    // the attribute, both instructions do nothing.
+    asm volatile("griddepcontrol.launch_dependents;");
     const WarpChunk wc = warp_chunk(ntiles);
     const int lane = wc.lane;
     const uint32_t tag = tag_of(colour, kPurposeMove);
     uint32_t tile = wc.begin;
     int l = tile < wc.end ? lattice_of_tile(g, tile) : 0;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     while (tile < wc.end) {
         LatDev* L = g.lats[l];
         const LatParams& p = L->p;
