@@ -185,8 +185,24 @@ def _oracle_worker(args):
     return time.perf_counter() - t
 
 
+def oracle_single_thread():
+    """Single-thread cost of the serial oracle in ns per spin-update, in this
+    process: the 16^3 point (K_u = 0.01, T = 0.5) over 1 + 40 measured sweeps
+    and one 128^3 lattice of the batch (T = 0.2) over 1 + 2."""
+    import oracle
+    oracle.build()
+    out = {}
+    for name, spec, n in (("16^3", workloads.point_16c(), 40), ("128^3", workloads.batched_mt_32()[3], 2)):
+        o = oracle.Lattice(spec.dims, Ku=spec.Ku, T=spec.T, seed=spec.seed, ring_cap=1)
+        o.sweep(1, measure=True)
+        t = time.perf_counter()
+        o.sweep(n, measure=True)
+        out[name] = round((time.perf_counter() - t) / (spec.N * n) * 1e9, 2)
+    return out
+
+
 def run_oracle(lattice_ids, n_warm, n_steps):
-    """Run the serial oracle on the given config-2 lattices, one process per
+    """Run the serial oracle on the given batched m(T) lattices, one process per
     core (spawned), every lattice n_warm + n_steps measurement sweeps; return
     (updates per second over the timed sweeps, cores used)."""
     import oracle
@@ -259,7 +275,8 @@ def gpu_arm(args, cfg):
         rate, cores = run_oracle(list(range(32)), 1, 4)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "all 32 lattices of the workload, 4 measurement sweeps each after 1 warm-up "
-                         "(76.7M updates), one spawned process per core"}
+                         "(76.7M updates), one spawned process per core",
+               "single_thread_ns_per_update": oracle_single_thread()}
 
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
