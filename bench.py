@@ -568,12 +568,7 @@ def precision(mc, torch, stream, dev):
     the largest |difference| / sigma."""
     import numpy as np
 
-    def blocking_error(x):  # Flyvbjerg-Petersen: the largest naive error over levels with >= 32 blocks
-        x, best = np.asarray(x, np.float64), 0.0
-        while x.size >= 32:
-            best = max(best, float(np.sqrt(np.var(x, ddof=1) / x.size)))
-            x = 0.5 * (x[: x.size // 2 * 2: 2] + x[1: x.size // 2 * 2: 2])
-        return best
+    from paper_2103_03517_gb300.analysis import blocking_error
 
     out = {}
     res = {}

