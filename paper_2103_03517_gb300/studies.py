@@ -1,5 +1,6 @@
 """Studies of arXiv:2103.03517 driven through the library's public API: the
-exchange stiffness A(T) by the Bloch-wall method (Sec. 3, Eq. 5) with K(T)
+magnetisation curve m(T) with the susceptibilities of Eq. 6 and the Bloch law
+of Eq. 3 (Sec. 3, Fig. 1); the exchange stiffness A(T) by the Bloch-wall method (Sec. 3, Eq. 5) with K(T)
 from the easy-axis estimator (Eq. 4) and its low-temperature m^k exponent as a
 function of K/J (Table I); the average Curie temperature of granular films
 from the weighted Bloch series of Eq. 8 (Sec. 4).  Every sweep and sample runs
@@ -15,7 +16,84 @@ import numpy as np
 from . import _mc as mc
 from . import analysis as an
 
-__all__ = ["exchange_stiffness_study", "bloch_wall_spins", "film_curie_study"]
+__all__ = ["magnetization_curve", "exchange_stiffness_study", "bloch_wall_spins", "film_curie_study"]
+
+
+def magnetization_curve(dims, temps, K_u=0.01, K_c=0.0, n_eq=2000, n_meas=5000, seed=0, precision=mc.MC_FP32,
+                        m_fit_min=0.2, stream=None, device=0):
+    """m(T) of Sec. 3 (Fig. 1): one periodic lattice per temperature, all
+    advanced as one group (one launch per colour pass for every
+    temperature), easy axis z, all spins starting along +z.  dims is one
+    (Lx, Ly, Lz) for every temperature or a list with one per temperature
+    (uneven sizes batch like equal ones).  n_eq sweeps of equilibration, then
+    n_meas measured sweeps with one sample each; lattice i takes seed + i.
+
+    Per temperature: <|m|> and its blocking error, <m_z>, the susceptibilities
+    of Eq. 6 in reduced units (mu_S = 1): chi_par = N (<m_z^2> - <|m_z|>^2) / T
+    along the easy axis (the |m_z| form is not spoiled by the sign flips of a
+    small lattice near T_C), chi_perp = (chi_x + chi_y) / 2 over the hard
+    axes, chi_l from |m|; <E/N> and its error; k(T) of Eq. 4 (k_u if
+    K_u != 0, else k_c if K_c != 0); the acceptance of the last sweep.  Eq. 3
+    is fitted to the temperatures with <|m|> >= m_fit_min when at least three
+    qualify.  Returns a dict of per-temperature lists, the fit (T_C, beta or
+    None), spin-updates and wall time."""
+    temps = [float(t) for t in temps]
+    if not temps:
+        raise ValueError("no temperatures")
+    if n_eq < 0 or n_meas < 1:
+        raise ValueError("need n_eq >= 0 and n_meas >= 1")
+    sizes = [tuple(int(v) for v in dims)] * len(temps) if np.ndim(dims[0]) == 0 else [tuple(d) for d in dims]
+    if len(sizes) != len(temps):
+        raise ValueError("one dims per temperature")
+    hs = []
+    try:
+        for i, (d, T) in enumerate(zip(sizes, temps)):
+            hs.append(mc.mc_create_ex(mc.make_desc(d, K_u=K_u, K_c=K_c, T=T, seed=seed + i, precision=precision,
+                                                   ring_capacity=n_meas, sample_torque=0, stream=stream,
+                                                   device=device)))
+        g = mc.mc_group_create(hs)
+        t0 = time.perf_counter()
+        try:
+            mc.mc_group_sweep(g, n_eq)
+            for h in hs:
+                mc.mc_reset_stats(h)
+            mc.mc_group_sweep(g, n_meas, measure=True)
+            obs = mc.mc_group_measure(g, len(hs))
+        finally:
+            mc.mc_group_destroy(g)
+        wall = time.perf_counter() - t0
+        out = {k: [] for k in ("T", "N", "m", "m_err", "mz", "chi_par", "chi_perp", "chi_l", "e", "e_err", "k",
+                               "accept")}
+        for h, o, d, T in zip(hs, obs, sizes, temps):
+            N = int(np.prod(d))
+            err = an.sample_errors(mc.mc_samples(h, n_meas))
+            k = mc.mc_anisotropy_scaling(h)
+            out["T"].append(T)
+            out["N"].append(N)
+            out["m"].append(o.ml)
+            out["m_err"].append(err["ml"][1])
+            out["mz"].append(o.m[2])
+            out["chi_par"].append(N * (o.m2[2] - o.m_abs[2] ** 2) / T)
+            out["chi_perp"].append(0.5 * (o.chi[1] + o.chi[2]))
+            out["chi_l"].append(o.chi[0])
+            out["e"].append(o.e)
+            out["e_err"].append(err["e"][1])
+            out["k"].append(float(k[0] if K_u != 0.0 else k[1]))
+            out["accept"].append(o.accept_last)
+    finally:
+        for h in hs:
+            mc.mc_destroy(h)
+    Tf = [T for T, m in zip(out["T"], out["m"]) if m >= m_fit_min]
+    mf = [m for m in out["m"] if m >= m_fit_min]
+    out["T_C"], out["beta"] = None, None
+    if len(Tf) >= 3:
+        try:
+            out["T_C"], out["beta"], _ = an.bloch_fit(Tf, mf)
+        except RuntimeError:  # no convergence: leave the fit out
+            pass
+    out["updates"] = float(sum(out["N"])) * (n_eq + n_meas)
+    out["seconds"] = wall
+    return out
 
 
 def bloch_wall_spins(dims, K, J=1.0):

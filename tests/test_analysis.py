@@ -168,3 +168,13 @@ def test_sample_errors_of_a_sample_series():
     assert out["mz"][0] == pytest.approx(-0.8, abs=1e-3) and out["mz_abs"][0] == pytest.approx(0.8, abs=1e-3)
     assert out["e"][0] == pytest.approx(-2.01) and out["e"][1] == pytest.approx(0.0, abs=1e-15)
     assert 0.01 / math.sqrt(n) * 0.9 < out["mx"][1] < 0.01 / math.sqrt(n) * 1.3
+
+
+def test_magnetization_curve_rejects_bad_arguments_on_the_host():
+    from paper_2103_03517_gb300 import studies as st
+    with pytest.raises(ValueError):
+        st.magnetization_curve((16, 16, 16), [])
+    with pytest.raises(ValueError):
+        st.magnetization_curve([(16, 16, 16), (32, 32, 32)], [0.5])
+    with pytest.raises(ValueError):
+        st.magnetization_curve((16, 16, 16), [0.5], n_meas=0)
