@@ -55,6 +55,7 @@ def lib() -> C.CDLL:
         P = C.POINTER
         L.or_philox.argtypes = [P(u32), P(u32), P(u32)]
         L.or_exp.argtypes = [dbl]; L.or_exp.restype = dbl
+        L.or_exp_array.argtypes = [P(dbl), P(dbl), i64]; L.or_exp_array.restype = None
         L.or_cone_trial.argtypes = [P(dbl), i32, u32, u32, u32, P(u32), P(dbl), P(dbl)]
         L.or_cone_trial.restype = i32
         L.or_create.argtypes = [P(i32), P(i32), dbl, dbl, P(dbl), dbl, P(dbl), dbl, u64, i32, i32, i32]
@@ -114,6 +115,14 @@ def philox(ctr, key) -> np.ndarray:
 
 def exp(x: float) -> float:
     return lib().or_exp(float(x))
+
+
+def exp_array(xs) -> np.ndarray:
+    """exp_own elementwise over an array (float64)."""
+    x = np.ascontiguousarray(xs, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().or_exp_array(_p(x, C.c_double), _p(y, C.c_double), x.size)
+    return y
 
 
 def cone_trial(S, theta_deg: int, idx: int, sweep: int, tag: int, key):

@@ -113,6 +113,12 @@ static double exp_own(double x) {
 
 OR_EXPORT double or_exp(double x) { return exp_own(x); }
 
+/* exp_own over an array (for pinning it against a library exp on many
+   points): y[i] = exp_own(x[i]), i < n. */
+OR_EXPORT void or_exp_array(const double* x, double* y, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) y[i] = exp_own(x[i]);
+}
+
 /* --------------------------------------------------------------------- */
 /* Cone table: c(theta) = 1 - cos(theta) = 2 sin^2(theta/2) for integer     */
 /* degrees 0..180 (theta is the cone half-angle, Table A1                   */
