@@ -251,6 +251,33 @@ def test_constrained_low_temperature_torque():
         assert abs(tau / expect - 1) < 0.03, (th, tau, expect)
 
 
+def test_constrained_low_temperature_torque_at_45_degrees_azimuth():
+    """T -> 0 along e_C(theta, phi = 45): with e_C = (s/sqrt2, s/sqrt2, c),
+    s = sin theta, c = cos theta, the cubic energy per spin is
+    K_c (s^4/4 + s^2 c^2), so F = -K_u c^2 + K_c (s^4/4 + s^2 c^2) and
+    tau_theta / N = -dF/dtheta = -(K_u sin 2 theta + K_c s c (2 c^2 - s^2)),
+    tau_theta = n.tau with n = (-sin phi, cos phi, 0).  At theta = 60 this
+    differs from the phi = 0 law by 19%, so a frame that ignored phi fails."""
+    Ku, Kc, T, ph = 0.05, 0.02, 0.01, 45.0
+    for th in (30.0, 60.0):
+        R = oracle.constraint_frame(th, ph)
+        o = oracle.Lattice((8, 8, 8), J=1.0, Ku=Ku, Kc=Kc, T=T, seed=18, ring_cap=3000)
+        o.set_spins(workloads.uniform_spins(512, R[0]))
+        o.constrained_sweep(th, ph, 500)
+        o.constrained_sweep(th, ph, 2000, measure=True)
+        s = o.stats()
+        p = math.radians(ph)
+        n_hat = np.array([-math.sin(p), math.cos(p), 0.0])
+        tau = np.array([s["tqx"], s["tqy"], s["tqz"]]) / s["n"] @ n_hat
+        t = math.radians(th)
+        st, ct = math.sin(t), math.cos(t)
+        expect = -(Ku * math.sin(2 * t) + Kc * st * ct * (2 * ct * ct - st * st))
+        assert abs(tau / expect - 1) < 0.03, (th, tau, expect)
+        at_phi0 = -(Ku * math.sin(2 * t) + 0.5 * Kc * math.sin(4 * t))
+        if th == 60.0:
+            assert abs(tau / at_phi0 - 1) > 0.1
+
+
 def test_constrained_zero_angle_torque_vanishes():
     o = oracle.Lattice((8, 8, 8), J=1.0, Ku=0.05, T=0.6, seed=9, ring_cap=4000)
     o.constrained_sweep(0.0, 0.0, 500)
