@@ -690,7 +690,7 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
 
 
 def serving(mc, n_requests=40, rate=20.0, n_eq=200, n_meas=500):
-    """Config-5 style trace: Poisson arrivals (rate, seed 1) of m(T) points,
+    """The serving mix: Poisson arrivals (rate, seed 1) of m(T) points,
     constrained points and granular films (45/45/10%), cubes L in
     {8, ..., 256}, T uniform in (0.05, 1.6), 200 + 500 sweeps per job,
     submitted at their arrival times to one server; latency = finish -
