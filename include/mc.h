@@ -400,6 +400,13 @@ MC_API int mc_poll(mc_server* s, uint64_t job_id, mc_result* out);
  * if the job has already finished, MC_ERR_ARG for an unknown id. */
 MC_API int mc_cancel(mc_server* s, uint64_t job_id);
 
+/* Drop the record of a finished job (its result, its id), so that a server
+ * fed an endless stream of requests keeps only the jobs still in flight.
+ * Poll the result first: afterwards the id is unknown (MC_ERR_ARG).
+ * MC_ERR_STATE while the job is queued or running.  Serving bookkeeping
+ * around the paper's method; the paper has no counterpart. */
+MC_API int mc_forget(mc_server* s, uint64_t job_id);
+
 /* Current server clock (seconds), jobs queued / resident, bytes in use. */
 MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident, size_t* bytes);
 
@@ -416,9 +423,11 @@ MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident
  * no library routine that allocates.  The scratch the sweep kernels need
  * (lattice descriptor with its counters and sums, launch tables, cone table,
  * sample ring) is one static 32 KiB device array inside libmc, reserved on
- * every GPU that loads the library until the process exits.  The first call
- * on a device looks up the array's device address once (make that first
- * call before any stream capture).  Every call rewrites the whole scratch
+ * every GPU that loads the library until the process exits.  Each call
+ * looks up the array's device address in the current device's context (a
+ * lookup that allocates nothing); the first call on a device also loads
+ * libmc's kernels there, so make that first call before any stream
+ * capture.  Every call rewrites the whole scratch
  * and clears its counters; calls that overlap on the GPU (on different
  * streams, or from different threads) race on it.
  *

@@ -132,6 +132,7 @@ _SIGS = {
     "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
     "mc_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(mc_result)]),
     "mc_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "mc_forget": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mc_server_stats": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
     "mc_sweep_noalloc": (C.c_int, [C.c_void_p, _P(C.c_int), C.c_double, C.c_double, _P(C.c_double), C.c_double,
                                    _P(C.c_double), C.c_double, C.c_uint64, C.c_int64, C.c_int, _P(C.c_int),
@@ -443,6 +444,11 @@ def mc_poll(s, job_id: int):
 def mc_cancel(s, job_id: int) -> None:
     """Cancel a queued or resident job (its result then reads MC_ERR_CANCELLED)."""
     _check(lib().mc_cancel(s, int(job_id)))
+
+
+def mc_forget(s, job_id: int) -> None:
+    """Drop a finished job's record (poll its result first)."""
+    _check(lib().mc_forget(s, int(job_id)))
 
 
 def mc_server_stats(s):

@@ -37,7 +37,7 @@ constexpr int V = kSitesPerThreadF32;
 #include "launchers_common.cuh"
 
 template <int B, int MEASURE, int GEN>
-void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
+cudaError_t row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, cudaStream_t s) {
     static const uint32_t cap = resident_blocks(row_pass_kernel<B, MEASURE, GEN>);
     // programmatic serialisation: the pass starts its blocks while the
     // previous launch drains and waits inside the kernel (griddepcontrol)
@@ -50,29 +50,28 @@ void row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int colour, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, row_pass_kernel<B, MEASURE, GEN>, g, ntiles, cone, colour);
+    return cudaLaunchKernelEx(&cfg, row_pass_kernel<B, MEASURE, GEN>, g, ntiles, cone, colour);
 }
 
 // launch shape 0: the default blocks per SM of the instance; 1: the other candidate
 template <int GEN, int B0, int B1>
-void row_pass_g(const GroupArgs& g, uint32_t ntiles, const R* c, int colour, int measure, int shape,
-                cudaStream_t s) {
+cudaError_t row_pass_g(const GroupArgs& g, uint32_t ntiles, const R* c, int colour, int measure, int shape,
+                       cudaStream_t s) {
     if (shape == 1) {
-        if (measure >= 2) row_pass_t<B1, 2, GEN>(g, ntiles, c, colour, s);
-        else if (measure == 1) row_pass_t<B1, 1, GEN>(g, ntiles, c, colour, s);
-        else row_pass_t<B1, 0, GEN>(g, ntiles, c, colour, s);
-    } else {
-        if (measure >= 2) row_pass_t<B0, 2, GEN>(g, ntiles, c, colour, s);
-        else if (measure == 1) row_pass_t<B0, 1, GEN>(g, ntiles, c, colour, s);
-        else row_pass_t<B0, 0, GEN>(g, ntiles, c, colour, s);
+        if (measure >= 2) return row_pass_t<B1, 2, GEN>(g, ntiles, c, colour, s);
+        if (measure == 1) return row_pass_t<B1, 1, GEN>(g, ntiles, c, colour, s);
+        return row_pass_t<B1, 0, GEN>(g, ntiles, c, colour, s);
     }
+    if (measure >= 2) return row_pass_t<B0, 2, GEN>(g, ntiles, c, colour, s);
+    if (measure == 1) return row_pass_t<B0, 1, GEN>(g, ntiles, c, colour, s);
+    return row_pass_t<B0, 0, GEN>(g, ntiles, c, colour, s);
 }
 
-void row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen, int shape,
-              cudaStream_t s) {
+cudaError_t row_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure, int gen,
+                     int shape, cudaStream_t s) {
     const R* c = static_cast<const R*>(cone);
-    if (gen) row_pass_g<1, MINB_GEN, MINB_GEN + 1>(g, ntiles, c, colour, measure, shape, s);
-    else row_pass_g<0, MINB, MINB - 1>(g, ntiles, c, colour, measure, shape, s);
+    if (gen) return row_pass_g<1, MINB_GEN, MINB_GEN + 1>(g, ntiles, c, colour, measure, shape, s);
+    return row_pass_g<0, MINB, MINB - 1>(g, ntiles, c, colour, measure, shape, s);
 }
 
 // the all-periodic instance samples red sites first and stores their field

@@ -7,7 +7,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "runtime.h"
 
@@ -16,7 +15,6 @@ namespace {
 
 constexpr int kMaxSamples = 256;                     // samples one call can return
 constexpr size_t kScratchBytes = 32 * 1024;          // the whole scratch array
-constexpr int kMaxDevices = 64;
 
 // Layout of the scratch array (byte offsets, 256-aligned pieces).
 constexpr size_t kOffLat = 0;
@@ -32,21 +30,17 @@ static_assert(kUsed <= kScratchBytes, "scratch layout exceeds the array");
 // Shared by every call on a device; contents persist from call to call.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch for the current device, looked up once per
-// device (the name is only a host-side stand-in in host code).
-int scratch_address(int device, char** out) {
-    if (device < 0 || device >= kMaxDevices) return fail(MC_ERR_ARG, "device %d out of range", device);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_scratch_addr[device] = p;
-    }
-    *out = static_cast<char*>(g_scratch_addr[device]);
+// Device address of g_scratch in the current device's context (in host code
+// the name is only a stand-in).  Looked up on every call: the lookup
+// allocates nothing and is cheap once the module is loaded, and an address
+// kept from an earlier context would dangle after cudaDeviceReset.  The
+// first call on a device loads the module, so it belongs before any stream
+// capture.
+int scratch_address(char** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    *out = static_cast<char*>(p);
     return MC_OK;
 }
 
@@ -75,10 +69,8 @@ extern "C" MC_API int mc_sweep_noalloc(float* spins, const int dims[3], double J
     if (rc) return rc;
     if (n_sweeps == 0) return MC_OK;
 
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess) return fail(MC_ERR_CUDA, "cudaGetDevice failed");
     char* base = nullptr;
-    rc = scratch_address(device, &base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 

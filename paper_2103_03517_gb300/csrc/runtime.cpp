@@ -600,9 +600,16 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             launch();
         }
     };
+    cudaError_t launch_err = cudaSuccess;  // first failed launch of the row kernels
     auto colour_pass = [&](int colour, int meas) {
-        if (ls.nt_row) k.row_pass(ls.row, ls.nt_row, cone, colour, meas, 0, ls.shape.row, s);
-        if (ls.nt_rowx) k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, ls.shape.row, s);
+        if (ls.nt_row) {
+            const cudaError_t e = k.row_pass(ls.row, ls.nt_row, cone, colour, meas, 0, ls.shape.row, s);
+            if (launch_err == cudaSuccess) launch_err = e;
+        }
+        if (ls.nt_rowx) {
+            const cudaError_t e = k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, ls.shape.row, s);
+            if (launch_err == cudaSuccess) launch_err = e;
+        }
         if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
     };
     if (ls.xtal) {  // bcc / fcc / hcp: the 2 nsub sub-sets in turn, then the sample
@@ -673,6 +680,7 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             }
         }
     }
+    if (launch_err != cudaSuccess) return cuda_fail(launch_err, "row kernel launch");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return MC_OK;

@@ -61,7 +61,16 @@ struct mc_server {
     void run_epoch(std::vector<Job*>& res);
 };
 
+// The film tables are needed only until create_lattice has taken its own
+// device copy; a served film holds about 5 B of them per site.
+static void release_tables(Job* j) {
+    std::vector<uint8_t>().swap(j->bonds);
+    std::vector<int32_t>().swap(j->grain);
+    std::vector<double>().swap(j->axes);
+}
+
 static void finish(mc_server* s, Job* j, int status) {
+    release_tables(j);
     if (j->h) {
         if (status == MC_OK) {
             int rc = mc_measure(j->h, &j->obs);
@@ -156,6 +165,7 @@ void mc_server::loop() {
                 desc.grain_axis = j->axes.empty() ? nullptr : j->axes.data();
                 queue.pop_front();
                 int rc = create_lattice(&desc, &j->h);
+                release_tables(j);
                 if (rc) { j->h = nullptr; j->t_finish = now(); j->status = rc; continue; }
                 used += j->bytes;
                 j->t_admit = now();
@@ -271,12 +281,24 @@ MC_API int mc_cancel(mc_server* s, uint64_t job_id) {
     auto q = std::find(s->queue.begin(), s->queue.end(), j);
     if (q != s->queue.end()) {  // not admitted: drop it now
         s->queue.erase(q);
+        release_tables(j);
         j->t_finish = s->now();
         j->status = MC_ERR_CANCELLED;
     } else {
         j->cancel = true;  // resident: the worker retires it after the epoch
     }
     s->cv.notify_all();
+    return MC_OK;
+}
+
+MC_API int mc_forget(mc_server* s, uint64_t job_id) {
+    if (!s) return fail(MC_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return fail(MC_ERR_ARG, "unknown job id %llu", (unsigned long long)job_id);
+    if (it->second->status == MC_PENDING)
+        return fail(MC_ERR_STATE, "job %llu has not finished", (unsigned long long)job_id);
+    s->jobs.erase(it);
     return MC_OK;
 }
 

@@ -106,15 +106,17 @@ def result_to_dict(job_id, tag, res) -> dict:
     return out
 
 
-def serve(lines, write, submit, poll, poll_interval=0.002):
+def serve(lines, write, submit, poll, poll_interval=0.002, forget=None):
     """The request loop.  lines yields JSON job lines as they arrive (blank
     lines are skipped); each is parsed and submitted at once.  submit(job)
     returns a job id; poll(job_id) returns (status, result) with status
     MC_PENDING or MC_OK.  Finished jobs are written (write(dict)) as they
     complete, between reads and after the input ends.  A line that does not
     parse, or a job the server refuses, is written as an error record with its
-    line number and the loop goes on.  Returns the number of results written
-    (errors included)."""
+    line number and the loop goes on.  forget(job_id), if given, is called
+    once a result is written, so that the server drops the finished job's
+    record and a long stream keeps only the jobs in flight.  Returns the
+    number of results written (errors included)."""
     pending = {}  # job id -> caller's tag
     written = 0
 
@@ -125,6 +127,8 @@ def serve(lines, write, submit, poll, poll_interval=0.002):
             if rc == mc.MC_OK:
                 write(result_to_dict(jid, pending.pop(jid), res))
                 written += 1
+                if forget is not None:
+                    forget(jid)
 
     for n, line in enumerate(lines, 1):
         line = line.strip()
@@ -164,7 +168,8 @@ def main(argv=None) -> int:
             sys.stdout.write(json.dumps(rec) + "\n")
             sys.stdout.flush()
 
-        serve(sys.stdin, write, lambda job: mc.mc_submit(srv, job), lambda jid: mc.mc_poll(srv, jid))
+        serve(sys.stdin, write, lambda job: mc.mc_submit(srv, job), lambda jid: mc.mc_poll(srv, jid),
+              forget=lambda jid: mc.mc_forget(srv, jid))
     finally:
         mc.mc_server_destroy(srv)
     return 0

@@ -121,3 +121,16 @@ def test_null_handles_rejected():
         mc.mc_group_measure(None, 4)
     assert e.value.code == mc.MC_ERR_ARG
     assert mc.mc_destroy(None) is None
+
+
+def test_noalloc_object_calls_no_allocation_routine():
+    """The object of mc_sweep_noalloc references no allocating CUDA routine
+    (device, host or stream-ordered memory, streams, events, graphs); the GPU
+    test checks the free device memory across calls."""
+    obj = os.path.join(ROOT, "_build", "libmc", "noalloc.cu.o")
+    out = subprocess.run(["nm", "-u", obj], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    undefined = [ln.split()[-1] for ln in out.stdout.splitlines() if ln.strip()]
+    assert any("cudaGetSymbolAddress" in u for u in undefined)
+    banned = re.compile(r"cuda(Malloc|Free|HostAlloc|HostRegister|StreamCreate|EventCreate|Graph|MemPool)|cuMem")
+    assert not [u for u in undefined if banned.search(u)]

@@ -162,3 +162,29 @@ def test_cancel_queued_resident_and_finished_jobs():
             time.sleep(0.002)
     finally:
         mc.mc_server_destroy(s)
+
+
+def test_forget_drops_finished_records_only():
+    """A finished job's record goes with mc_forget (its id is then unknown);
+    a job still queued or running cannot be forgotten."""
+    s = mc.mc_server_create(max_resident=1, max_epoch_sweeps=8)
+    try:
+        long_job = mc.make_job(mc.make_desc((64, 64, 64), T=0.7, seed=1), n_equilibrate=100000, n_measure=10)
+        a = mc.mc_submit(s, long_job)
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_forget(s, a)
+        assert e.value.code == mc.MC_ERR_STATE
+        mc.mc_cancel(s, a)
+        _wait(s, [a])
+        mc.mc_forget(s, a)
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_poll(s, a)
+        assert e.value.code == mc.MC_ERR_ARG
+        c = mc.mc_submit(s, _probe_job())
+        assert _wait(s, [c])[c].status == mc.MC_OK
+        mc.mc_forget(s, c)
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_forget(s, c)
+        assert e.value.code == mc.MC_ERR_ARG
+    finally:
+        mc.mc_server_destroy(s)

@@ -89,3 +89,16 @@ def test_serve_loop_submits_as_lines_arrive_and_writes_every_result():
     assert results[102]["latency_s"] == pytest.approx(3.0)
     assert [j.lattice.dims[0] for j in srv.jobs] == [16, 8, 8]
     assert all(json.dumps(r) for r in out)   # every record is JSON-ready
+
+
+def test_serve_loop_forgets_each_job_once_its_result_is_written():
+    lines = [json.dumps({"dims": [16, 16, 16], "T": 0.5}), json.dumps({"dims": [8, 8, 8], "T": 1.0}),
+             json.dumps({"dims": [8, 8, 8], "T": 1.2})]
+    srv, out, forgotten = FakeServer(), [], []
+
+    def forget(jid):
+        assert any(r.get("job") == jid for r in out), "forgotten before its result was written"
+        forgotten.append(jid)
+
+    serve.serve(iter(lines), out.append, srv.submit, srv.poll, poll_interval=0.0, forget=forget)
+    assert sorted(forgotten) == [100, 101, 102]

@@ -46,7 +46,9 @@ def _reference(dims, kw, n1, n2):
     return start, out, samples
 
 
-@pytest.mark.parametrize("dims", [(16, 16, 16), (64, 32, 8)])
+# (16, 16, 16) and (64, 32, 8) take the row kernel; (12, 6, 4), with rows of
+# 6 sites per colour, takes the general colour kernel
+@pytest.mark.parametrize("dims", [(16, 16, 16), (64, 32, 8), (12, 6, 4)])
 def test_noalloc_matches_allocating_path_on_two_calls(dims):
     torch = pytest.importorskip("torch")
     kw = dict(J=1.0, K_u=0.05, K_c=0.02, H=(0.0, 0.0, 0.1), T=0.8, seed=21)
@@ -85,3 +87,29 @@ def test_noalloc_rejects_oversize_sample_request():
         mc.mc_sweep_noalloc(spins.data_ptr(), dims, 1.0, 0.0, (0, 0, 1.0), 0.0, (0, 0, 0), 1.0, 0, 0, 300, 30,
                             samples_ptr=samples.data_ptr())
     assert e.value.code == mc.MC_ERR_ARG and "256" in str(e.value)
+
+
+def test_noalloc_call_leaves_free_device_memory_unchanged():
+    """After a first call (which loads the kernels), further calls take no
+    device memory: the free bytes the driver reports do not move."""
+    torch = pytest.importorskip("torch")
+    dims = (32, 32, 32)
+    h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.01, T=0.9, seed=5))
+    try:
+        nbytes = mc.mc_state_bytes(h)
+        start = np.zeros(nbytes // 4, np.float32)
+        mc.mc_export_state(h, start.ctypes.data, nbytes)
+    finally:
+        mc.mc_destroy(h)
+    spins = torch.from_numpy(start).cuda()
+    samples = torch.zeros(16 * 14, dtype=torch.float64, device="cuda")
+    args = (dims, 1.0, 0.01, (0.0, 0.0, 1.0), 0.0, (0.0, 0.0, 0.0), 0.9, 5)
+    theta = mc.mc_sweep_noalloc(spins.data_ptr(), *args, 0, 8, 30, samples_ptr=samples.data_ptr())
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    first = 8
+    for _ in range(3):
+        theta = mc.mc_sweep_noalloc(spins.data_ptr(), *args, first, 16, theta, samples_ptr=samples.data_ptr())
+        first += 16
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
