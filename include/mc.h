@@ -68,12 +68,17 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * passes where the row layout applies (Lh = Lx/2 a power of two <= 64 or a
  * multiple of 64, Nc a multiple of 64) and the general kernel otherwise,
  * and walks the constrained pairs in site order (each pair led by the
- * member whose shuffled position is even).  GENERAL always takes the general
- * colour-pass kernel and the pairs in pair order.  The colour passes agree
- * up to FP32 rounding (the draws are keyed to the same sites) and the two
- * pair orders exactly; GENERAL exists to compare them.  FP64 lattices
- * always take the general kernel and pair order. */
-typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1 } mc_kernel_path;
+ * member whose shuffled position is even).  On all-periodic lattices with
+ * Lx = 128 and Ly a multiple of 16 (no film tables), AUTO also runs the
+ * sweeps of each mc_sweep / mc_group_sweep call two at a time as single
+ * wavefront launches (red and black pass fused; the lattice then holds a
+ * second spin buffer, and an odd last sweep of a call runs as two row
+ * passes).  ROW is AUTO without the wavefront launches.  GENERAL always
+ * takes the general colour-pass kernel and the pairs in pair order.  The
+ * colour passes agree up to FP32 rounding (the draws are keyed to the same
+ * sites) and the two pair orders exactly; GENERAL and ROW exist to compare
+ * them.  FP64 lattices always take the general kernel and pair order. */
+typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1, MC_PATH_ROW = 2 } mc_kernel_path;
 
 /* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the
  * cells.  BCC / FCC: 2 / 4 simple cubic sub-lattices with basis (0,0,0),
@@ -303,12 +308,21 @@ MC_API int mc_group_sweep(mc_group_handle g, int n_sweeps, int measure);
 MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_deg,
                                       const double* phi_c_deg, int n_sweeps, int measure);
 
-/* Time the colour passes of the group: the next n_sweeps sweeps of Table A1
- * record CUDA events around every colour pass (the launches that update one
- * colour of every lattice); *avg_ms receives the mean duration of one colour
- * pass and *launches the number of passes timed.  Synchronises. */
+/* Time the launches of the group: the next n_sweeps sweeps of Table A1
+ * record CUDA events around every launch that moves spins (a colour pass,
+ * which updates one colour of every lattice of its kernel, or a wavefront
+ * launch, which sweeps its lattices once); *avg_ms receives the mean
+ * duration of one launch and *launches the number timed.  Synchronises. */
 MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms,
                                 int* launches);
+
+/* The same, by kind: avg_ms[0] / launches[0] for the wavefront launches
+ * (one sweep of the lattices that take them), [1] for the colour passes of
+ * the row and general kernels, [2] for constrained pair passes (0 here).
+ * A kind with no launch reads 0 ms.  Measurement support around the
+ * paper's method; the paper has no counterpart.  Synchronises. */
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, double avg_ms[3],
+                                 int launches[3]);
 
 /* Ensemble averages of every lattice of the group (Sec. 3, Eq. 6), as
  * mc_measure gives them, read with one wait on the group stream instead of

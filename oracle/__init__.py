@@ -72,6 +72,8 @@ def lib() -> C.CDLL:
         L.or_set_grains.argtypes = [vp, P(C.c_int32), P(dbl), i32]
         L.or_delta_e.argtypes = [vp, i64, P(dbl)]; L.or_delta_e.restype = dbl
         L.or_stats.argtypes = [vp, P(dbl)]
+        L.or_colour_pass_planes.argtypes = [vp, i32, i32, i32]; L.or_colour_pass_planes.restype = i64
+        L.or_end_sweep.argtypes = [vp, i64]; L.or_end_sweep.restype = None
         L.or_samples.argtypes = [vp, P(dbl), i64]; L.or_samples.restype = i64
         L.or_anisotropy_scaling.argtypes = [vp, P(dbl)]
         L.or_xtal_create.argtypes = [i32, P(i32), dbl, dbl, dbl, P(dbl), dbl, P(dbl), dbl, u64, i32, i32]
@@ -231,6 +233,19 @@ class Lattice:
     # method ------------------------------------------------------------
     def sweep(self, n: int, measure: bool = False) -> None:
         lib().or_sweep(self._h, int(n), int(bool(measure)))
+
+    def colour_pass_planes(self, colour: int, z0: int, z1: int) -> int:
+        """One Table A1 colour pass over the planes z0 <= z < z1 only (a
+        slab's share of the pass); returns the accepted moves."""
+        n = lib().or_colour_pass_planes(self._h, int(colour), int(z0), int(z1))
+        if n < 0:
+            raise ValueError("or_colour_pass_planes: bad colour or plane range")
+        return int(n)
+
+    def end_sweep(self, accepted: int) -> None:
+        """End an unmeasured iteration with the whole lattice's accepted
+        moves: cone adaptation and the sweep counter."""
+        lib().or_end_sweep(self._h, int(accepted))
 
     def sweep_serial(self, n: int, measure: bool = False) -> None:
         lib().or_sweep_serial(self._h, int(n), int(bool(measure)))

@@ -521,11 +521,11 @@ OR_EXPORT void or_reset_stats(or_lattice* L) {
 /* sites do not interact, so the oracle simply visits them in index order.  */
 /* The RNG is keyed by site, so the order inside a pass is immaterial.      */
 /* --------------------------------------------------------------------- */
-static int64_t colour_pass(or_lattice* L, int colour) {
+static int64_t colour_pass_planes(or_lattice* L, int colour, int z0, int z1) {
     const double c = cone_c(L->theta);
     const uint32_t tag = tag_of(colour, PURPOSE_MOVE);
     int64_t accepted = 0;
-    for (int z = 0; z < L->L[2]; ++z)
+    for (int z = z0; z < z1; ++z)
         for (int y = 0; y < L->L[1]; ++y)
             for (int x = 0; x < L->L[0]; ++x) {
                 if (((x + y + z) & 1) != colour) continue;
@@ -541,6 +541,25 @@ static int64_t colour_pass(or_lattice* L, int colour) {
                 }
             }
     return accepted;
+}
+
+static int64_t colour_pass(or_lattice* L, int colour) { return colour_pass_planes(L, colour, 0, L->L[2]); }
+
+/* One colour pass restricted to the planes z0 <= z < z1: the part of a      */
+/* Table A1 pass that one slab of a lattice split along z performs.  The    */
+/* per-site update is colour_pass's; the caller supplies the neighbouring   */
+/* planes.  Returns the accepted moves.                                     */
+OR_EXPORT int64_t or_colour_pass_planes(or_lattice* L, int colour, int z0, int z1) {
+    if (colour < 0 || colour > 1 || z0 < 0 || z1 > L->L[2] || z0 > z1) return -1;
+    return colour_pass_planes(L, colour, z0, z1);
+}
+
+/* The end of an unmeasured iteration of Table A1 given the accepted moves  */
+/* of the whole lattice (summed over slabs): cone adaptation, sweep count.  */
+OR_EXPORT void or_end_sweep(or_lattice* L, int64_t accepted) {
+    L->last_accepted = accepted;
+    adapt_theta(L, accepted);
+    L->sweep += 1;
 }
 
 OR_EXPORT int or_sweep(or_lattice* L, int n_sweeps, int measure_flag) {

@@ -19,7 +19,7 @@ MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR
 MC_ERR_CANCELLED = -8
 MC_FP32, MC_FP64 = 0, 1
 MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
-MC_PATH_AUTO, MC_PATH_GENERAL = 0, 1
+MC_PATH_AUTO, MC_PATH_GENERAL, MC_PATH_ROW = 0, 1, 2
 MC_SC, MC_BCC, MC_FCC, MC_HCP = 0, 1, 2, 3
 MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
 MC_TUNE_SWEEP, MC_TUNE_CONSTRAINED = 1, 2
@@ -123,6 +123,7 @@ _SIGS = {
     "mc_group_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mc_group_constrained_sweep": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double), C.c_int, C.c_int]),
     "mc_group_time_passes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
+    "mc_group_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
     "mc_group_measure": (C.c_int, [C.c_void_p, _P(mc_observables), C.c_int]),
     "mc_group_sync": (C.c_int, [C.c_void_p]),
     "mc_group_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
@@ -390,6 +391,15 @@ def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):
     n = C.c_int()
     _check(lib().mc_group_time_passes(g, int(n_sweeps), int(bool(measure)), C.byref(avg), C.byref(n)))
     return avg.value, n.value
+
+
+def mc_group_time_kernels(g, n_sweeps: int, measure: bool = False):
+    """Per launch kind (wavefront sweeps, colour passes, pair passes): the
+    mean launch duration in ms and the number of launches timed."""
+    ms = (C.c_double * 3)()
+    n = (C.c_int * 3)()
+    _check(lib().mc_group_time_kernels(g, int(n_sweeps), int(bool(measure)), ms, n))
+    return list(ms), list(n)
 
 
 def mc_group_measure(g, n: int) -> list:

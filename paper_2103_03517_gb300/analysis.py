@@ -2,7 +2,8 @@
 the domain-wall width fit and the exchange stiffness of Eq. 5, the free-energy
 route dF(T) of Eq. 5, the m^k scaling exponent of Table I, the Bloch law of
 Eq. 3, the transverse susceptibility of Eq. 7, the weighted Bloch series of
-Eq. 8 for granular films, and error bars of the per-sweep series by blocking.  Plain numpy / scipy on the host; reduced units
+Eq. 8 for granular films, the anisotropy constants from the constrained
+torque (Sec. 3, Fig. 1(a)), and error bars of the per-sweep series by blocking.  Plain numpy / scipy on the host; reduced units
 (J = 1, k_B = 1, mu_S = 1, lattice constant 1).
 """
 from __future__ import annotations
@@ -13,7 +14,7 @@ import numpy as np
 
 __all__ = ["wall_model", "fit_wall", "exchange_stiffness", "free_energy_difference",
            "stiffness_from_free_energy", "power_exponent", "bloch_fit", "chi_perp_uniaxial", "multi_bloch_fit",
-           "blocking_error", "sample_errors"]
+           "blocking_error", "sample_errors", "torque_basis", "torque_fit", "torque_theta"]
 
 
 def wall_model(x, m, x0, delta, Lx=None):
@@ -197,3 +198,51 @@ def sample_errors(samples, min_blocks: int = 32) -> dict:
     for a, name in enumerate(("tx", "ty", "tz")):
         series[name] = tq[:, a]
     return {k: (float(v.mean()), blocking_error(v, min_blocks)) for k, v in series.items()}
+
+
+def torque_basis(theta_deg, phi_deg):
+    """The angular factors of the anisotropy torque of Sec. 3 (Fig. 1(a)).
+    The free energy per spin of a magnetisation held along
+    e_C = (sin t cos p, sin t sin p, cos t) is F = K_u(T) sin^2 t + K_c(T) q
+    with q = a1^2 a2^2 + a1^2 a3^2 + a2^2 a3^2 = sin^4 t sin^2(2p) / 4 +
+    sin^2 t cos^2 t, so dF/dt = K_u g_u + K_c g_c with
+    g_u = sin 2t and g_c = sin t cos t (sin^2 t sin^2 2p + 2 cos 2t)
+    (g_c = sin(4t) / 2 at p = 0, sin t cos t (2 cos^2 t - sin^2 t) at
+    p = 45 deg).  Returns (g_u, g_c) as arrays."""
+    t = np.radians(np.asarray(theta_deg, np.float64))
+    p = np.radians(np.asarray(phi_deg, np.float64))
+    g_u = np.sin(2.0 * t)
+    g_c = np.sin(t) * np.cos(t) * (np.sin(t) ** 2 * np.sin(2.0 * p) ** 2 + 2.0 * np.cos(2.0 * t))
+    return g_u, g_c
+
+
+def torque_theta(torque, phi_deg):
+    """tau_theta = n . tau of a mean torque vector per spin (mc_measure's
+    torque), n = (-sin p, cos p, 0): the component along increasing theta,
+    so that dF/dtheta = -<tau_theta>."""
+    tq = np.asarray(torque, np.float64)
+    p = np.radians(np.asarray(phi_deg, np.float64))
+    return -np.sin(p) * tq[..., 0] + np.cos(p) * tq[..., 1]
+
+
+def torque_fit(theta_deg, phi_deg, tau, sigma=None):
+    """K_u(T) and K_c(T) from constrained runs at one temperature (Asselin's
+    torque method, Sec. 3): linear least squares of
+    tau_theta(theta, phi) = -[K_u g_u(theta, phi) + K_c g_c(theta, phi)]
+    over the runs (weighted by 1 / sigma^2 when the errors are given).
+    Returns {"K_u", "K_c", "K_u_err", "K_c_err", "chi2_dof"}; the errors are
+    the fit's standard errors (from sigma, else from the residual scatter)."""
+    g_u, g_c = torque_basis(theta_deg, phi_deg)
+    y = -np.asarray(tau, np.float64)
+    A = np.stack([g_u, g_c], axis=1)
+    w = np.ones_like(y) if sigma is None else 1.0 / np.maximum(np.asarray(sigma, np.float64), 1e-300)
+    Aw, yw = A * w[:, None], y * w
+    coef, _, rank, _ = np.linalg.lstsq(Aw, yw, rcond=None)
+    if rank < 2:
+        raise ValueError("torque_fit: the angles do not separate the uniaxial and cubic terms")
+    resid = yw - Aw @ coef
+    dof = max(1, y.size - 2)
+    chi2 = float(resid @ resid) / dof
+    cov = np.linalg.inv(Aw.T @ Aw) * (1.0 if sigma is not None else chi2)
+    return {"K_u": float(coef[0]), "K_c": float(coef[1]), "K_u_err": float(math.sqrt(max(cov[0, 0], 0.0))),
+            "K_c_err": float(math.sqrt(max(cov[1, 1], 0.0))), "chi2_dof": chi2}

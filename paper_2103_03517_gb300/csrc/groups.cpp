@@ -18,6 +18,7 @@ struct mc_group {
     int precision = 0;
     cudaStream_t stream = nullptr;
     void* d_mem = nullptr;
+    void* d_wave = nullptr;  // wavefront plan of the group's wavefront lattices
     LaunchSet ls;
     const void* cone = nullptr;
     SweepGraphs graphs;  // captured sweeps of the whole group
@@ -71,10 +72,14 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
     // colour passes: one list per colour-pass kernel (LatParams::colour_kernel);
     // constrained pair passes: one list per pair order (LatParams::pair_leader);
     // each list with its tile starts, in launch order
-    constexpr int kLists = 5;  // general, row, row with films; pairs in pair order, in site order
+    // general, row, row with films; pairs in pair order, in site order; row
+    // lattices other than the wavefront ones
+    constexpr int kLists = 6;
     std::vector<LatDev*> sub[kLists];
     std::vector<uint32_t> st[kLists];
     for (int c = 0; c < kLists; ++c) st[c].assign(1, 0);
+    std::vector<const LatParams*> wave_hp;
+    std::vector<LatDev*> wave_dev;
     for (int j = 0; j < n; ++j) {
         const LatParams& hp = lattices[order[j]]->hp;
         const int c = hp.colour_kernel, q = 3 + (hp.pair_leader ? 1 : 0);
@@ -82,6 +87,13 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         st[c].push_back(st[c].back() + hp.nblocks_site);
         sub[q].push_back(all[j]);
         st[q].push_back(st[q].back() + hp.nblocks_pair);
+        if (hp.wave) {
+            wave_hp.push_back(&hp);
+            wave_dev.push_back(all[j]);
+        } else if (c == kColourRow) {
+            sub[5].push_back(all[j]);
+            st[5].push_back(st[5].back() + hp.nblocks_site);
+        }
     }
     cudaSetDevice(g->device);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -98,8 +110,10 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
     std::copy(sa.begin(), sa.end(), reinterpret_cast<uint32_t*>(hb + o0));
     g->ls.all = GroupArgs{reinterpret_cast<LatDev**>(db), reinterpret_cast<uint32_t*>(db + o0), n};
     g->ls.nt_all = sa.back();
-    GroupArgs* lists[kLists] = {&g->ls.rest, &g->ls.row, &g->ls.rowx, &g->ls.pairs, &g->ls.pairs_lead};
-    uint32_t* counts[kLists] = {&g->ls.nt_rest, &g->ls.nt_row, &g->ls.nt_rowx, &g->ls.nt_pairs, &g->ls.nt_pairs_lead};
+    GroupArgs* lists[kLists] = {&g->ls.rest, &g->ls.row, &g->ls.rowx, &g->ls.pairs, &g->ls.pairs_lead,
+                                &g->ls.row_rest};
+    uint32_t* counts[kLists] = {&g->ls.nt_rest,  &g->ls.nt_row,        &g->ls.nt_rowx,
+                                &g->ls.nt_pairs, &g->ls.nt_pairs_lead, &g->ls.nt_row_rest};
     for (int c = 0; c < kLists; ++c) {
         const size_t op = size_t(1 + c) * b_ptr, oi = o0 + size_t(1 + c) * b_idx;
         std::copy(sub[c].begin(), sub[c].end(), reinterpret_cast<LatDev**>(hb + op));
@@ -125,6 +139,18 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
         delete g;
         return fail(MC_ERR_CUDA, "group table upload failed");
     }
+    if (!wave_hp.empty()) {  // one wavefront plan over all the group's wavefront lattices
+        const uint32_t blocks = kernels_f32().wave_blocks();
+        const WavePlan pl = plan_wave(wave_hp, blocks);
+        const int rc = upload_wave_plan(pl, wave_dev, g->stream, &g->d_wave, &g->ls.wave);
+        if (rc) {
+            for (int i = 0; i < n; ++i) lattices[i]->stream = g->member_streams[i];
+            cudaFree(g->d_mem);
+            delete g;
+            return rc;
+        }
+        g->ls.nb_wave = uint32_t(pl.off.size() - 1);
+    }
     *out = g;
     return MC_OK;
 }
@@ -135,6 +161,7 @@ MC_API int mc_group_destroy(mc_group_handle g) {
     cudaStreamSynchronize(g->stream);
     destroy_graphs(g->graphs);
     cudaFree(g->d_mem);
+    if (g->d_wave) cudaFree(g->d_wave);
     if (g->h_states) cudaFreeHost(g->h_states);
     for (size_t i = 0; i < g->lats.size(); ++i) g->lats[i]->stream = g->member_streams[i];
     delete g;
@@ -165,24 +192,57 @@ MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_d
     return group_run(g, n_sweeps, measure ? 1 : 0, true);
 }
 
-MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms, int* launches) {
-    if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
+// n_sweeps sweeps of the group with events around every launch that moves
+// spins; per kind (TimedLaunch) the summed milliseconds and the count.
+static int time_kinds(mc_group* g, int n_sweeps, int measure, double ms[kTimedKinds], int count[kTimedKinds]) {
     cudaSetDevice(g->device);
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<TimedLaunch> ev;
     int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n_sweeps, measure ? 1 : 0, false, g->stream, &ev);
     cudaError_t e = cudaStreamSynchronize(g->stream);
-    double total = 0.0;
-    for (auto& pr : ev) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, pr.first, pr.second);
-        total += ms;
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+    for (int k = 0; k < kTimedKinds; ++k) {
+        ms[k] = 0.0;
+        count[k] = 0;
+    }
+    for (auto& t : ev) {
+        float x = 0.f;
+        cudaEventElapsedTime(&x, t.a, t.b);
+        ms[t.kind] += x;
+        count[t.kind] += 1;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
     }
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "time_passes sync");
-    *launches = int(ev.size());
-    *avg_ms = ev.empty() ? 0.0 : total / double(ev.size());
+    return MC_OK;
+}
+
+MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, double* avg_ms, int* launches) {
+    if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
+    double ms[kTimedKinds];
+    int count[kTimedKinds];
+    const int rc = time_kinds(g, n_sweeps, measure, ms, count);
+    if (rc) return rc;
+    double total = 0.0;
+    int n = 0;
+    for (int k = 0; k < kTimedKinds; ++k) {
+        total += ms[k];
+        n += count[k];
+    }
+    *launches = n;
+    *avg_ms = n ? total / double(n) : 0.0;
+    return MC_OK;
+}
+
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, double avg_ms[3], int launches[3]) {
+    if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
+    double ms[kTimedKinds];
+    int count[kTimedKinds];
+    const int rc = time_kinds(g, n_sweeps, measure, ms, count);
+    if (rc) return rc;
+    for (int k = 0; k < kTimedKinds; ++k) {
+        launches[k] = count[k];
+        avg_ms[k] = count[k] ? ms[k] / double(count[k]) : 0.0;
+    }
     return MC_OK;
 }
 

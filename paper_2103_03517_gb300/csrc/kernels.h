@@ -66,6 +66,15 @@ struct KernelSet {
     // Slice sums for the profile of one lattice.
     void (*profile)(LatDev* d, uint32_t Lh, uint32_t rows, cudaStream_t s);
     const char* name;
+    // FP32 wavefront sweep (red and black pass in one launch) of the
+    // lattices of a, nblocks blocks; dir = 0 reads spins and writes
+    // spins_alt, dir = 1 the reverse; measure as for colour_pass.  Null in
+    // the FP64 set.  Returns the status of the launch.
+    cudaError_t (*wave_sweep)(const WaveArgs& a, uint32_t nblocks, const void* cone, int dir, int measure,
+                              cudaStream_t s);
+    // Blocks of the wavefront kernel resident on the current device at once
+    // (the work-unit plan is made for this many).  Null in the FP64 set.
+    uint32_t (*wave_blocks)();
 };
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every
@@ -78,6 +87,14 @@ struct LaunchSet {
     // general kernel (tiles)
     GroupArgs row, rowx, rest;
     uint32_t nt_row = 0, nt_rowx = 0, nt_rest = 0;
+    // wavefront lattices (LatParams::wave): their work-unit plan (nb_wave
+    // blocks; 0 = none), and the row-kernel list without them, which runs
+    // beside a wavefront launch (row above keeps them, for sweeps that run
+    // as two row passes)
+    WaveArgs wave = {};
+    uint32_t nb_wave = 0;
+    GroupArgs row_rest;
+    uint32_t nt_row_rest = 0;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
     // a bcc / fcc lattice alone: its descriptor and sub-lattice count, else null
     LatDev* xtal = nullptr;

@@ -20,6 +20,7 @@
 #include "pass_impl.cuh"
 #include "xtal_pass.cuh"
 #include "row_pass.cuh"
+#include "wave_pass.cuh"
 
 namespace mcgb {
 namespace {
@@ -112,12 +113,56 @@ void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour
     else pair_pass_s<false>(g, ntiles, cone, colour, shape, sub, s);
 }
 
+// The wavefront kernel takes more than the default 48 KB of dynamic shared
+// memory: opt in once per instance.
+template <int MEASURE>
+bool wave_opt_in() {
+    static const bool ok = cudaFuncSetAttribute(wave_sweep_kernel<MEASURE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(kWaveSmemBytes)) == cudaSuccess;
+    return ok;
+}
+
+template <int MEASURE>
+cudaError_t wave_sweep_t(const WaveArgs& a, uint32_t nblocks, const R* cone, int dir, cudaStream_t s) {
+    if (!wave_opt_in<MEASURE>()) return cudaErrorInvalidConfiguration;
+    // programmatic serialisation, as for the row passes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(kWaveThreads);
+    cfg.dynamicSmemBytes = kWaveSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, wave_sweep_kernel<MEASURE>, a, cone, dir);
+}
+
+cudaError_t wave_sweep(const WaveArgs& a, uint32_t nblocks, const void* cone, int dir, int measure, cudaStream_t s) {
+    const R* c = static_cast<const R*>(cone);
+    if (measure >= 2) return wave_sweep_t<2>(a, nblocks, c, dir, s);
+    if (measure == 1) return wave_sweep_t<1>(a, nblocks, c, dir, s);
+    return wave_sweep_t<0>(a, nblocks, c, dir, s);
+}
+
+uint32_t wave_blocks() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (wave_opt_in<0>())
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_sweep_kernel<0>, kWaveThreads, kWaveSmemBytes);
+    if (per_sm < 1) per_sm = 1;
+    return uint32_t(sms) * uint32_t(per_sm);
+}
+
 }  // namespace
 
 const KernelSet& kernels_f32() {
     static const KernelSet k{colour_pass, row_pass,    pair_pass,   sweep_end,         pair_field,
                              ml_reset,    mlong,       measure,     row_sample,        xtal_pass,
-                             xtal_sample, xtal_field_launch, grain_sample, profile, "f32"};
+                             xtal_sample, xtal_field_launch, grain_sample, profile, "f32",
+                             wave_sweep,  wave_blocks};
     return k;
 }
 

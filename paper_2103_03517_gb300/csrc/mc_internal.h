@@ -108,6 +108,11 @@ struct LatParams {
                             // layout, all axes periodic, no film tables) or
                             // kColourRowGen (FP32 row layout, any boundaries and films)
     void* spins;
+    void* spins_alt;        // wavefront lattices (wave != 0): the second spin buffer
+                            // a fused sweep writes (same layout), else null
+    int wave;               // FP32 all-periodic lattice of rows of Lh = 64 sites per
+                            // colour and Ly a multiple of 16: its sweeps may run as
+                            // one wavefront launch (wave_sweep_kernel)
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null
     const void* gaxis;      // [n_grains][4] in the lattice precision, or null
@@ -159,6 +164,31 @@ struct GroupArgs {
     LatDev* const* lats;
     const uint32_t* start;
     int n;
+};
+
+// Wavefront sweep (wave_pass.cuh): lattices with rows of kWaveLh colour
+// indices (Lx = 128) and Ly a multiple of kWaveTy, split into work units.
+constexpr int kWaveLh = 64;
+constexpr int kWaveTy = 16;
+
+// Wavefront sweep: a work unit is band [y0, y0 + 16) x slab [z0, z0 + tz)
+// of lattice `lat` (an index into WaveArgs::lats), full rows in x.
+struct WaveWU {
+    uint32_t lat, y0, z0, tz;
+};
+
+// Arguments of a wavefront launch: block b runs work units [off[b],
+// off[b + 1]); lattice l has nwu[l] units in all, and the block finishing
+// its last one closes its sweep.  inject: extra bytes expected by the
+// first staged copy of block 0 (0 in normal runs; a host-set fault that
+// makes that wait run out).
+struct WaveArgs {
+    LatDev* const* lats;
+    const WaveWU* wu;
+    const uint32_t* off;
+    const uint32_t* nwu;
+    int n;
+    int inject;
 };
 
 }  // namespace mcgb

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -190,6 +191,17 @@ static void xtal_table(int lattice, double J, double J2, const LatParams& p, Xta
     }
 }
 
+// Lattices whose sweeps may run as wavefront launches (wave_pass.cuh):
+// FP32 simple cubic, every axis periodic, no film tables, rows of 64 sites
+// per colour (Lx = 128), Ly a multiple of 16, the automatic kernel path.
+bool wave_desc(const mc_desc* d) {
+    if (d->precision != MC_FP32 || d->lattice != MC_SC || d->kernel_path != MC_PATH_AUTO) return false;
+    if (d->bond_mask || d->grain_id) return false;
+    for (int a = 0; a < 3; ++a)
+        if (d->boundary[a] != MC_PERIODIC) return false;
+    return d->dims[0] == 2 * kWaveLh && d->dims[1] % kWaveTy == 0;
+}
+
 size_t lattice_bytes(const mc_desc* d) {
     const uint64_t cells = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
     const uint64_t Nc = cells / 2;
@@ -198,6 +210,7 @@ size_t lattice_bytes(const mc_desc* d) {
     const int nsub = sublattices(d->lattice);
     size_t b = align256(sizeof(LatDev));
     b += align256(size_t(nsub) * 6 * stride * rs);
+    if (wave_desc(d)) b += align256(6 * stride * rs);  // the second spin buffer
     if (nsub > 1) b += align256(sizeof(XtalNb) * kXtalMaxSub * kXtalMaxNb);
     if (d->bond_mask) b += align256(2 * stride);
     if (d->grain_id) {
@@ -235,7 +248,7 @@ int validate_desc(const mc_desc* d) {
         if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc / hcp lattices take no film tables");
         if (!std::isfinite(d->J2)) return fail(MC_ERR_ARG, "J2 not finite");
     }
-    if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL)
+    if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL && d->kernel_path != MC_PATH_ROW)
         return fail(MC_ERR_ARG, "kernel_path invalid");
     if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
     if (d->init != MC_INIT_UNIFORM && d->init != MC_INIT_WALL) return fail(MC_ERR_ARG, "init invalid");
@@ -408,7 +421,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     // FP32 constrained passes take the pairs in site order: the leader side
     // is then read in index order and only the partner side is a random
     // gather (MC_PATH_GENERAL keeps pair order; both give the same pairs)
-    p.pair_leader = d->kernel_path == MC_PATH_AUTO && p.precision == MC_FP32 ? 1 : 0;
+    p.pair_leader = d->kernel_path != MC_PATH_GENERAL && p.precision == MC_FP32 ? 1 : 0;
     p.J = p.nsub > 1 ? 1.0 : d->J;  // bcc / fcc: the couplings sit in the neighbour table
     p.Ku = d->K_u; p.Kc = d->K_c; p.T = d->T;
     const double an = std::sqrt(d->axis[0] * d->axis[0] + d->axis[1] * d->axis[1] + d->axis[2] * d->axis[2]);
@@ -431,6 +444,8 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     auto take = [&](size_t b) { char* r = cur; cur += align256(b); return r; };
     h->d_lat = reinterpret_cast<LatDev*>(take(sizeof(LatDev)));
     p.spins = take(size_t(p.nsub) * 6 * size_t(p.stride) * rs);
+    p.wave = wave_desc(d) ? 1 : 0;
+    if (p.wave) p.spins_alt = take(6 * size_t(p.stride) * rs);
     XtalNb xt[kXtalMaxSub][kXtalMaxNb] = {};
     if (p.nsub > 1) {
         xtal_table(d->lattice, d->J, d->J2, p, xt, p.xnb_n);
@@ -541,8 +556,15 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     }
     trace("create: tables ready");
     if (rc == MC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(MC_ERR_CUDA, "init sync");
+    if (rc == MC_OK && p.wave) {  // the wavefront plan of the lattice alone
+        const uint32_t blocks = kernels_f32().wave_blocks();
+        const WavePlan pl = plan_wave({&p}, blocks);
+        rc = upload_wave_plan(pl, {h->d_lat}, h->stream, &h->d_wave, &h->wave_args);
+        h->wave_nblocks = uint32_t(pl.off.size() - 1);
+    }
     trace("create: done");
     if (rc != MC_OK) {
+        if (h->d_wave) cudaFree(h->d_wave);
         cudaFree(h->d_base);
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
         delete h;
@@ -573,6 +595,13 @@ LaunchSet single_launch_set(mc_lattice* h) {
     } else if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
+        if (h->hp.wave) {
+            ls.wave = h->wave_args;
+            ls.nb_wave = h->wave_nblocks;
+        } else {
+            ls.row_rest = ls.all;
+            ls.nt_row_rest = ls.nt_all;
+        }
     } else if (h->hp.colour_kernel == kColourRowGen) {
         ls.rowx = ls.all;
         ls.nt_rowx = ls.nt_all;
@@ -583,11 +612,140 @@ LaunchSet single_launch_set(mc_lattice* h) {
     return ls;
 }
 
+// ------------------------------------------------------------ wavefront plan
+// Work units of the wavefront lattices for `blocks` resident blocks: every
+// lattice is cut into bands of kWaveTy rows, each band into slabs of planes.
+// A unit of tz planes takes about 2 tz + 5 row-steps of a block (tz + 3
+// phases, the first three and the last only half full).  Two plans are
+// tried and the one with the shorter longest block kept: (a) every band cut
+// into slabs of at most T planes (each T from 1 to the tallest lattice),
+// units handed out longest first to the least loaded block; (b) the bands'
+// planes laid end to end and cut into `blocks` equal runs (a run that
+// crosses a band boundary becomes two units).
+static long long wave_cost(uint32_t tz) { return 2ll * tz + 5; }
+
+WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks) {
+    struct Band { uint32_t lat, y0, lz; };
+    std::vector<Band> bands;
+    uint32_t lz_max = 1;
+    long long planes = 0;
+    for (size_t l = 0; l < lats.size(); ++l) {
+        for (int y0 = 0; y0 < lats[l]->Ly; y0 += kWaveTy) bands.push_back({uint32_t(l), uint32_t(y0), uint32_t(lats[l]->Lz)});
+        lz_max = std::max(lz_max, uint32_t(lats[l]->Lz));
+        planes += (long long)(lats[l]->Ly / kWaveTy) * lats[l]->Lz;
+    }
+    if (blocks < 1) blocks = 1;
+    std::vector<std::vector<WaveWU>> best;
+    long long best_span = -1;
+    auto consider = [&](std::vector<std::vector<WaveWU>>& bins) {
+        long long span = 0;
+        for (auto& b : bins) {
+            long long c = 0;
+            for (auto& u : b) c += wave_cost(u.tz);
+            span = std::max(span, c);
+        }
+        if (best_span < 0 || span < best_span) {
+            best_span = span;
+            best.swap(bins);
+        }
+    };
+    // (a) slabs of at most T planes, longest first onto the least loaded block
+    for (uint32_t T = 1; T <= lz_max; ++T) {
+        std::vector<WaveWU> units;
+        for (const Band& b : bands) {
+            const uint32_t ns = (b.lz + T - 1) / T;
+            for (uint32_t k = 0, z = 0; k < ns; ++k) {
+                const uint32_t tz = b.lz / ns + (k < b.lz % ns ? 1u : 0u);
+                units.push_back({b.lat, b.y0, z, tz});
+                z += tz;
+            }
+        }
+        std::stable_sort(units.begin(), units.end(), [](const WaveWU& x, const WaveWU& y) { return x.tz > y.tz; });
+        std::vector<std::vector<WaveWU>> bins(blocks);
+        std::priority_queue<std::pair<long long, uint32_t>, std::vector<std::pair<long long, uint32_t>>,
+                            std::greater<>> heap;
+        for (uint32_t i = 0; i < blocks; ++i) heap.push({0, i});
+        for (const WaveWU& u : units) {
+            auto [load, i] = heap.top();
+            heap.pop();
+            bins[i].push_back(u);
+            heap.push({load + wave_cost(u.tz), i});
+        }
+        consider(bins);
+    }
+    // (b) equal runs of the planes laid end to end
+    {
+        std::vector<std::vector<WaveWU>> bins(blocks);
+        long long pos = 0;  // first plane of the current band in the end-to-end order
+        for (const Band& b : bands) {
+            for (uint32_t i = 0; i < blocks; ++i) {
+                const long long r0 = planes * i / blocks, r1 = planes * (i + 1) / blocks;
+                const long long a = std::max(r0, pos), e = std::min(r1, pos + (long long)b.lz);
+                if (a < e) bins[i].push_back({b.lat, b.y0, uint32_t(a - pos), uint32_t(e - a)});
+            }
+            pos += b.lz;
+        }
+        consider(bins);
+    }
+    WavePlan pl;
+    pl.nwu.assign(lats.size(), 0);
+    pl.off.push_back(0);
+    for (auto& b : best) {
+        std::sort(b.begin(), b.end(), [](const WaveWU& x, const WaveWU& y) {
+            return x.lat != y.lat ? x.lat < y.lat : (x.y0 != y.y0 ? x.y0 < y.y0 : x.z0 < y.z0);
+        });
+        for (auto& u : b) {
+            pl.wu.push_back(u);
+            ++pl.nwu[u.lat];
+        }
+        pl.off.push_back(uint32_t(pl.wu.size()));
+    }
+    pl.span = best_span;
+    return pl;
+}
+
+// Upload a plan (with the lattices' device descriptors, in plan order) into
+// one device allocation; *d_mem is freed by the owner with cudaFree.
+int upload_wave_plan(const WavePlan& pl, const std::vector<LatDev*>& dev_lats, cudaStream_t s, void** d_mem,
+                     WaveArgs* out) {
+    const size_t b_lats = align256(sizeof(LatDev*) * dev_lats.size());
+    const size_t b_nwu = align256(sizeof(uint32_t) * pl.nwu.size());
+    const size_t b_off = align256(sizeof(uint32_t) * pl.off.size());
+    const size_t b_wu = align256(sizeof(WaveWU) * std::max<size_t>(pl.wu.size(), 1));
+    const size_t total = b_lats + b_nwu + b_off + b_wu;
+    std::vector<char> host(total, 0);
+    std::copy(dev_lats.begin(), dev_lats.end(), reinterpret_cast<LatDev**>(host.data()));
+    std::copy(pl.nwu.begin(), pl.nwu.end(), reinterpret_cast<uint32_t*>(host.data() + b_lats));
+    std::copy(pl.off.begin(), pl.off.end(), reinterpret_cast<uint32_t*>(host.data() + b_lats + b_nwu));
+    std::copy(pl.wu.begin(), pl.wu.end(), reinterpret_cast<WaveWU*>(host.data() + b_lats + b_nwu + b_off));
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(wavefront plan)");
+    e = cudaMemcpyAsync(d, host.data(), total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "wavefront plan upload");
+    }
+    char* db = static_cast<char*>(d);
+    out->lats = reinterpret_cast<LatDev* const*>(db);
+    out->nwu = reinterpret_cast<const uint32_t*>(db + b_lats);
+    out->off = reinterpret_cast<const uint32_t*>(db + b_lats + b_nwu);
+    out->wu = reinterpret_cast<const WaveWU*>(db + b_lats + b_nwu + b_off);
+    out->n = int(dev_lats.size());
+    // fault injection for the tests of the bounded waits: block 0's first
+    // staged copy expects 16 bytes that never arrive, so its wait runs out
+    const char* inj = std::getenv("MC_WAVE_INJECT_TIMEOUT");
+    out->inject = inj && inj[0] == '1' ? 16 : 0;
+    *d_mem = d;
+    return MC_OK;
+}
+
 // Enqueue n sweeps of the lattices of a launch set; with events != nullptr
 // every colour pass or pair pass is bracketed by a pair of events.
 int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
-                   cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events) {
-    auto timed = [&](auto&& launch) {
+                   cudaStream_t s, std::vector<TimedLaunch>* events) {
+    auto timed_kind = [&](int kind, auto&& launch) {
         if (events) {
             cudaEvent_t a, b;
             cudaEventCreate(&a);
@@ -595,11 +753,12 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
             cudaEventRecord(a, s);
             launch();
             cudaEventRecord(b, s);
-            events->emplace_back(a, b);
+            events->push_back(TimedLaunch{a, b, kind});
         } else {
             launch();
         }
     };
+    auto timed = [&](auto&& launch) { timed_kind(constrained ? kTimedPair : kTimedPass, launch); };
     cudaError_t launch_err = cudaSuccess;  // first failed launch of the row kernels
     auto colour_pass = [&](int colour, int meas) {
         if (ls.nt_row) {
@@ -646,9 +805,37 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return MC_OK;
     }
+    // the lattices beside a wavefront launch: the row list without the
+    // wavefront lattices, the boundary and general lists
+    auto rest_pass = [&](int colour, int meas) {
+        if (ls.nt_row_rest) {
+            const cudaError_t e = k.row_pass(ls.row_rest, ls.nt_row_rest, cone, colour, meas, 0, ls.shape.row, s);
+            if (launch_err == cudaSuccess) launch_err = e;
+        }
+        if (ls.nt_rowx) {
+            const cudaError_t e = k.row_pass(ls.rowx, ls.nt_rowx, cone, colour, meas, 1, ls.shape.row, s);
+            if (launch_err == cudaSuccess) launch_err = e;
+        }
+        if (ls.nt_rest) k.colour_pass(ls.rest, ls.nt_rest, cone, colour, meas, s);
+    };
+    const bool rest_any = ls.nt_row_rest || ls.nt_rowx || ls.nt_rest;
     bool red_field_ready = false;  // the next constrained sweep's red field is stored
     for (int i = 0; i < n; ++i) {
-        if (!constrained) {
+        // wavefront lattices sweep two at a time, spins -> spins_alt -> spins,
+        // so that every call leaves their state in spins; an odd last sweep
+        // of the call runs as two row passes
+        const bool wave = !constrained && ls.nb_wave && k.wave_sweep && (i % 2 == 1 || i + 1 < n);
+        if (wave) {
+            timed_kind(kTimedWave, [&] {
+                const cudaError_t e =
+                    k.wave_sweep(ls.wave, ls.nb_wave, cone, i % 2, measure ? ls.sample_level : 0, s);
+                if (launch_err == cudaSuccess) launch_err = e;
+            });
+            if (rest_any) {
+                timed([&] { rest_pass(0, 0); });
+                timed([&] { rest_pass(1, measure ? ls.sample_level : 0); });
+            }
+        } else if (!constrained) {
             timed([&] { colour_pass(0, 0); });
             timed([&] { colour_pass(1, measure ? ls.sample_level : 0); });
         } else {
@@ -809,6 +996,7 @@ MC_API int mc_destroy(mc_handle h) {
     destroy_graphs(h->graphs);
     cudaFree(h->d_base);
     if (h->d_aos) cudaFree(h->d_aos);
+    if (h->d_wave) cudaFree(h->d_wave);
     if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
     delete h;
     return MC_OK;

@@ -40,6 +40,9 @@ struct mc_lattice {
     uint32_t* d_group_start = nullptr;
     uint32_t* d_group_start_pair = nullptr;
     void* d_aos = nullptr;        // packed spin copy of constrained sweeps (LatParams::aos)
+    void* d_wave = nullptr;       // wavefront plan of the lattice alone (LatParams::wave)
+    mcgb::WaveArgs wave_args = {};
+    uint32_t wave_nblocks = 0;
     mcgb::SweepGraphs graphs;     // sweeps of the lattice alone
     mcgb::LaunchShape shape;      // autotuned launch shapes of the lattice alone
     const void* cone = nullptr;   // c(theta) table of the precision
@@ -73,7 +76,27 @@ void destroy_graphs(SweepGraphs& gr);
 LaunchSet single_launch_set(mc_lattice* h);
 int autotune(int precision, LaunchSet& ls, const std::vector<mc_lattice*>& lats, const void* cone, int sweeps,
              int what, cudaStream_t s, mc_tune_report* out);
+// Work units of wavefront lattices for a launch of `blocks` blocks (block b
+// runs units [off[b], off[b+1]) of wu; nwu per lattice; span = the longest
+// block's cost in row-steps).
+struct WavePlan {
+    std::vector<WaveWU> wu;
+    std::vector<uint32_t> off, nwu;
+    long long span = 0;
+};
+bool wave_desc(const mc_desc* d);
+WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks);
+int upload_wave_plan(const WavePlan& pl, const std::vector<LatDev*>& dev_lats, cudaStream_t s, void** d_mem,
+                     WaveArgs* out);
+// A launch bracketed by CUDA events (mc_group_time_passes / _kernels):
+// kind kTimedWave = a wavefront sweep, kTimedPass = a colour pass (row or
+// general kernels), kTimedPair = a constrained pair pass.
+enum { kTimedWave = 0, kTimedPass = 1, kTimedPair = 2, kTimedKinds = 3 };
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int kind;
+};
 int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, int n, int measure, bool constrained,
-                   cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* events);
+                   cudaStream_t s, std::vector<TimedLaunch>* events);
 
 }  // namespace mcgb

@@ -2,8 +2,11 @@
 magnetisation curve m(T) with the susceptibilities of Eq. 6 and the Bloch law
 of Eq. 3 (Sec. 3, Fig. 1); the exchange stiffness A(T) by the Bloch-wall method (Sec. 3, Eq. 5) with K(T)
 from the easy-axis estimator (Eq. 4) and its low-temperature m^k exponent as a
-function of K/J (Table I); the average Curie temperature of granular films
-from the weighted Bloch series of Eq. 8 (Sec. 4).  Every sweep and sample runs
+function of K/J (Table I); the anisotropy constants K_u(T), K_c(T) from the
+constrained torque against the constraint direction (Sec. 3, Fig. 1(a)); the
+pinned Bloch wall's averaged profile, width and A(T) (Sec. 3, Eq. 5, Fig. 2);
+the average Curie temperature of granular films from the weighted Bloch
+series of Eq. 8 (Sec. 4).  Every sweep and sample runs
 in libmc; the fits are host post-processing (``analysis``).
 """
 from __future__ import annotations
@@ -16,7 +19,8 @@ import numpy as np
 from . import _mc as mc
 from . import analysis as an
 
-__all__ = ["magnetization_curve", "exchange_stiffness_study", "bloch_wall_spins", "film_curie_study"]
+__all__ = ["magnetization_curve", "exchange_stiffness_study", "bloch_wall_spins", "film_curie_study",
+           "anisotropy_torque_study", "pinned_wall_study"]
 
 
 def magnetization_curve(dims, temps, K_u=0.01, K_c=0.0, n_eq=2000, n_meas=5000, seed=0, precision=mc.MC_FP32,
@@ -271,3 +275,156 @@ def film_curie_study(dims, grain_id, bond_mask, grain_axis, temps, K_u=0.02, n_e
         fit = {"T_C": tc, "beta": beta, "errors": err.tolist()}
     updates = len(temps) * (n_eq + blocks * every) * N
     return {"T": temps, "m": m.tolist(), "fit": fit, "updates": updates, "seconds": seconds}
+
+
+def _unit(theta_deg, phi_deg):
+    t, p = math.radians(theta_deg), math.radians(phi_deg)
+    return (math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t))
+
+
+def anisotropy_torque_study(dims=(64, 64, 64), K_u=0.05, K_c=0.02, temps=(0.2, 0.6, 1.0, 1.3),
+                            thetas=tuple(range(0, 91, 10)), phis=(0.0, 45.0), n_eq=3000, n_meas=5000, seed=0,
+                            precision=mc.MC_FP32, stream=None, device=0):
+    """Asselin's torque method of Sec. 3 (Fig. 1(a)) with the parallel
+    constrained algorithm (Table A2): one periodic lattice per (T, phi,
+    theta), started along its constraint direction e_C(theta, phi) and
+    held there, all advanced as one group; n_eq sweeps, then n_meas measured
+    sweeps with the torque sampled every sweep.  Per run: <tau_theta> (per
+    spin, along increasing theta) with its blocking error.  Per temperature:
+    K_u(T) and K_c(T) from analysis.torque_fit over that temperature's runs,
+    weighted by the errors.  Run i takes seed + i.  Returns {"runs": [...],
+    "fits": {T: fit}, "updates", "seconds"} (pair halves count as updates)."""
+    runs = [(float(T), float(ph), float(th)) for T in temps for ph in phis for th in thetas]
+    hs = []
+    try:
+        for i, (T, ph, th) in enumerate(runs):
+            hs.append(mc.mc_create_ex(mc.make_desc(dims, K_u=K_u, K_c=K_c, T=T, seed=seed + i, precision=precision,
+                                                   init_dir=_unit(th, ph), ring_capacity=n_meas, stream=stream,
+                                                   device=device)))
+        g = mc.mc_group_create(hs)
+        th_l, ph_l = [r[2] for r in runs], [r[1] for r in runs]
+        t0 = time.perf_counter()
+        try:
+            mc.mc_group_constrained_sweep(g, th_l, ph_l, n_eq)
+            for h in hs:
+                mc.mc_reset_stats(h)
+            mc.mc_group_constrained_sweep(g, th_l, ph_l, n_meas, measure=True)
+            obs = mc.mc_group_measure(g, len(hs))
+        finally:
+            mc.mc_group_destroy(g)
+        seconds = time.perf_counter() - t0
+        rows = []
+        for h, o, (T, ph, th) in zip(hs, obs, runs):
+            series = an.torque_theta(mc.mc_samples(h, n_meas)["torque"], ph)
+            rows.append({"T": T, "phi": ph, "theta": th, "tau": float(an.torque_theta(np.array(o.torque), ph)),
+                         "tau_err": float(an.blocking_error(series)), "m_l": float(o.ml)})
+    finally:
+        for h in hs:
+            mc.mc_destroy(h)
+    fits = {}
+    for T in sorted({r["T"] for r in rows}):
+        r = [x for x in rows if x["T"] == T]
+        sig = np.array([max(x["tau_err"], 1e-12) for x in r])
+        fits[T] = an.torque_fit([x["theta"] for x in r], [x["phi"] for x in r], [x["tau"] for x in r], sigma=sig)
+    updates = float(len(runs)) * float(np.prod(dims)) * (n_eq + n_meas)
+    return {"runs": rows, "fits": fits, "updates": updates, "seconds": seconds}
+
+
+def pinned_wall_study(temps, dims=(1024, 128, 128), K_u=0.05, n_eq=2000, n_meas=4000, every=10,
+                      uniform_dims=(64, 64, 64), uniform_sweeps=(1000, 2000), seed=0, precision=mc.MC_FP32,
+                      stream=None, device=0):
+    """The Bloch-wall method of Sec. 3 (Eq. 5, Fig. 2) on walls held by
+    pinned end planes: x = 0 at +z and x = Lx - 1 at -z, y and z periodic,
+    started as a step at Lx / 2 (the wall workload of 1024 x 128 x 128 spins).
+    Every `every` measured sweeps one slice profile m_z(x) is taken and
+    fitted by the tanh of Sec. 3; the wall drifts, so each profile is
+    shifted by its fitted centre (rounded) to the middle before it enters the
+    average.  Per temperature: the re-centred average profile, its width
+    Delta from the tanh fit, the mean width of the single-profile fits, and
+    K(T) from a constrained uniform lattice held at theta = 45 deg (tau_theta
+    = -K(T) sin 2 theta per spin, Fig. 1(a)), so A(T) = K(T) (Delta / pi)^2.
+    Returns {"rows": [...], "updates", "seconds"}."""
+    temps = [float(t) for t in temps]
+    Lx = int(dims[0])
+    walls, unis = [], []
+    try:
+        for i, T in enumerate(temps):
+            walls.append(mc.mc_create_ex(mc.make_desc(
+                dims, K_u=K_u, T=T, seed=seed + 2 * i, precision=precision, init=mc.MC_INIT_WALL,
+                boundary=(mc.MC_PINNED, mc.MC_PERIODIC, mc.MC_PERIODIC), ring_capacity=16, sample_torque=0,
+                stream=stream, device=device)))
+            unis.append(mc.mc_create_ex(mc.make_desc(
+                uniform_dims, K_u=K_u, T=T, seed=seed + 2 * i + 1, precision=precision, init_dir=_unit(45.0, 0.0),
+                ring_capacity=16, stream=stream, device=device)))
+        t0 = time.perf_counter()
+        gu = mc.mc_group_create(unis)
+        try:
+            th, ph = [45.0] * len(unis), [0.0] * len(unis)
+            mc.mc_group_constrained_sweep(gu, th, ph, uniform_sweeps[0])
+            for h in unis:
+                mc.mc_reset_stats(h)
+            mc.mc_group_constrained_sweep(gu, th, ph, uniform_sweeps[1], measure=True)
+            K_T = [-float(an.torque_theta(np.array(o.torque), 0.0)) for o in mc.mc_group_measure(gu, len(unis))]
+        finally:
+            mc.mc_group_destroy(gu)
+        gw = mc.mc_group_create(walls)
+        acc = [np.zeros(Lx) for _ in walls]
+        cnt = [np.zeros(Lx) for _ in walls]
+        widths = [[] for _ in walls]
+        try:
+            mc.mc_group_sweep(gw, n_eq)
+            for h in walls:
+                mc.mc_reset_stats(h)
+            prev = [np.zeros(Lx) for _ in walls]
+            blocks = max(1, n_meas // every)
+            x = np.arange(Lx)
+            for b in range(blocks):
+                mc.mc_group_sweep(gw, every, measure=True)
+                for w, h in enumerate(walls):
+                    mc.mc_profile_sample(h)
+                    avg = mc.mc_profile(h, 2, Lx)  # mean over the b + 1 samples so far
+                    one = avg * (b + 1) - prev[w] * b
+                    prev[w] = avg
+                    try:
+                        m_w, x0, d_w, _ = an.fit_wall(one, antiperiodic=False)
+                    except RuntimeError:
+                        continue
+                    if not (abs(m_w) > 0.05 and 0.0 < d_w < Lx and 0.0 <= x0 < Lx):
+                        continue  # no wall (near or above T_C)
+                    widths[w].append(d_w)
+                    s = int(round(x0 - Lx / 2))
+                    src = x + s
+                    ok = (src >= 0) & (src < Lx)
+                    acc[w][ok] += one[src[ok]]
+                    cnt[w][ok] += 1.0
+            mc.mc_group_sync(gw)
+        finally:
+            mc.mc_group_destroy(gw)
+        seconds = time.perf_counter() - t0
+        rows = []
+        for w, T in enumerate(temps):
+            prof = np.where(cnt[w] > 0, acc[w] / np.maximum(cnt[w], 1.0), np.nan)
+            delta = float("nan")
+            m_amp = float("nan")
+            good = np.isfinite(prof)
+            if widths[w] and good.sum() > 16:
+                # planes no shifted profile reached (next to the pinned ends)
+                # take the nearest averaged value: the profile is flat there
+                idx = np.arange(Lx)
+                filled = np.interp(idx, idx[good], prof[good])
+                try:
+                    m_amp, _, delta, _ = an.fit_wall(filled, antiperiodic=False)
+                except RuntimeError:
+                    pass
+            d = np.asarray(widths[w])
+            rows.append({"T": T, "K_T": K_T[w], "delta": delta, "m_wall": m_amp,
+                         "delta_single_mean": float(d.mean()) if d.size else float("nan"),
+                         "delta_single_err": float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else float("nan"),
+                         "profiles": int(d.size), "A": float(an.exchange_stiffness(delta, K_T[w])),
+                         "profile": [float(v) for v in prof]})
+    finally:
+        for h in walls + unis:
+            mc.mc_destroy(h)
+    updates = float(len(temps)) * (float(np.prod(dims)) * (n_eq + max(1, n_meas // every) * every)
+                                   + float(np.prod(uniform_dims)) * sum(uniform_sweeps))
+    return {"rows": rows, "updates": updates, "seconds": seconds}

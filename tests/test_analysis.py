@@ -178,3 +178,67 @@ def test_magnetization_curve_rejects_bad_arguments_on_the_host():
         st.magnetization_curve([(16, 16, 16), (32, 32, 32)], [0.5])
     with pytest.raises(ValueError):
         st.magnetization_curve((16, 16, 16), [0.5], n_meas=0)
+
+
+def test_torque_basis_is_the_theta_derivative_of_the_anisotropy_energy():
+    """g_u and g_c against a central difference of the energy per spin
+    written from the direction cosines themselves: -(e_C . z)^2 and
+    a1^2 a2^2 + a1^2 a3^2 + a2^2 a3^2 (Eq. 2's anisotropy terms)."""
+    def energies(t, p):
+        a = np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)])
+        return -(a[2] ** 2), a[0] ** 2 * a[1] ** 2 + a[0] ** 2 * a[2] ** 2 + a[1] ** 2 * a[2] ** 2
+    h = 1e-6
+    for th in (0.0, 7.0, 30.0, 45.0, 61.0, 90.0, 133.0):
+        for ph in (0.0, 17.0, 45.0, 90.0):
+            t, p = math.radians(th), math.radians(ph)
+            up, cp = energies(t + h, p)
+            um, cm = energies(t - h, p)
+            g_u, g_c = an.torque_basis(th, ph)
+            assert abs(g_u - (up - um) / (2 * h)) < 1e-8 and abs(g_c - (cp - cm) / (2 * h)) < 1e-8, (th, ph)
+
+
+def test_torque_fit_recovers_the_constants_exactly():
+    """The closed-form torque of config 3's grid (theta 0..90 by 10, phi 0
+    and 45 deg) gives back K_u and K_c; with phi = 0 alone the cubic term
+    sin(4 theta)/2 still separates from sin(2 theta)."""
+    th = np.array(list(range(0, 91, 10)) * 2, float)
+    ph = np.array([0.0] * 10 + [45.0] * 10)
+    for Ku, Kc in ((0.05, 0.02), (0.031, -0.007), (0.0, 0.013)):
+        g_u, g_c = an.torque_basis(th, ph)
+        tau = -(Ku * g_u + Kc * g_c)
+        f = an.torque_fit(th, ph, tau)
+        assert abs(f["K_u"] - Ku) < 1e-14 and abs(f["K_c"] - Kc) < 1e-14
+        f0 = an.torque_fit(th[:10], ph[:10], tau[:10], sigma=np.full(10, 1e-3))
+        assert abs(f0["K_u"] - Ku) < 1e-14 and abs(f0["K_c"] - Kc) < 1e-14 and f0["chi2_dof"] < 1e-20
+    with pytest.raises(ValueError):  # theta = 0 and 90 only: both factors vanish
+        an.torque_fit([0.0, 90.0], [0.0, 0.0], [0.0, 0.0])
+
+
+def test_torque_theta_projects_on_increasing_theta():
+    tq = np.array([[0.3, -0.2, 0.7], [1.0, 2.0, 3.0]])
+    np.testing.assert_allclose(an.torque_theta(tq, [0.0, 90.0]), [-0.2, -1.0])
+
+
+def test_torque_fit_on_the_oracle_chain_at_low_temperature():
+    """Table A2 on the serial oracle (8^3, K_u = 0.05, K_c = 0.02, T = 0.02)
+    at five constraint directions, fitted by torque_fit: K_u(T) and K_c(T)
+    come back just below their T = 0 values: spin waves lower them as
+    K_u ~ m^3 and K_c ~ m^10 (Callen-Callen, Sec. 3) with m ~ 1 - 0.25 T,
+    about 1.5% and 5% here, and never raise them."""
+    import oracle
+    import workloads
+
+    Ku, Kc, T = 0.05, 0.02, 0.02
+    th = np.array([20.0, 45.0, 70.0, 30.0, 60.0])
+    ph = np.array([0.0, 0.0, 0.0, 45.0, 45.0])
+    tau = []
+    for t, p in zip(th, ph):
+        R = oracle.constraint_frame(t, p)
+        o = oracle.Lattice((8, 8, 8), J=1.0, Ku=Ku, Kc=Kc, T=T, seed=int(t + p), ring_cap=1)
+        o.set_spins(workloads.uniform_spins(512, R[0]))
+        o.constrained_sweep(t, p, 200)
+        o.constrained_sweep(t, p, 600, measure=True)
+        s = o.stats()
+        tau.append(float(an.torque_theta(np.array([s["tqx"], s["tqy"], s["tqz"]]) / s["n"], p)))
+    f = an.torque_fit(th, ph, tau)
+    assert 0.97 < f["K_u"] / Ku < 1.0 and 0.9 < f["K_c"] / Kc < 1.0, f

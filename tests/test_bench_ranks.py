@@ -1,6 +1,6 @@
 """The multi-rank logic of bench.py on CPU: two gloo ranks with different
 local times agree on the max-over-ranks time and on the whole-job value
-(weak scaling: every rank advances its own batch)."""
+(the ranks split one batch, so the value is its updates over the max time)."""
 import os
 import socket
 
@@ -23,7 +23,7 @@ def _rank(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         local_ms = [12.0, 15.5][rank]
-        ms, value = bench.job_time_and_value(local_ms, 1e9, world, bench.torch_reduce_max("cpu"))
+        ms, value = bench.job_time_and_value(local_ms, 2e9, world, bench.torch_reduce_max("cpu"))
         out[rank] = (ms, value)
         dist.barrier()
     finally:
