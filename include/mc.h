@@ -68,17 +68,21 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * passes where the row layout applies (Lh = Lx/2 a power of two <= 64 or a
  * multiple of 64, Nc a multiple of 64) and the general kernel otherwise,
  * and walks the constrained pairs in site order (each pair led by the
- * member whose shuffled position is even).  On all-periodic lattices with
- * Lx = 128 and Ly a multiple of 16 (no film tables), AUTO also runs the
- * sweeps of each mc_sweep / mc_group_sweep call two at a time as single
- * wavefront launches (red and black pass fused; the lattice then holds a
- * second spin buffer, and an odd last sweep of a call runs as two row
- * passes).  ROW is AUTO without the wavefront launches.  GENERAL always
- * takes the general colour-pass kernel and the pairs in pair order.  The
- * colour passes agree up to FP32 rounding (the draws are keyed to the same
- * sites) and the two pair orders exactly; GENERAL and ROW exist to compare
- * them.  FP64 lattices always take the general kernel and pair order. */
-typedef enum mc_kernel_path { MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1, MC_PATH_ROW = 2 } mc_kernel_path;
+ * member whose shuffled position is even).  GENERAL always takes the
+ * general colour-pass kernel and the pairs in pair order.  ROW is AUTO.
+ * WAVE is AUTO, except that on an all-periodic lattice with Lx = 128 and
+ * Ly >= 16 (no film tables) the sweeps of each mc_sweep / mc_group_sweep
+ * call run two at a time as single wavefront launches (red and black pass
+ * fused, each spin read and written once per sweep; the lattice then holds
+ * a second spin buffer, and an odd last sweep of a call runs as two row
+ * passes).  The colour passes of AUTO, GENERAL and WAVE agree up to FP32
+ * rounding (the draws are keyed to the same sites; the wavefront and row
+ * kernels bit for bit) and the two pair orders exactly; GENERAL, ROW and
+ * WAVE exist to compare them.  FP64 lattices always take the general kernel
+ * and pair order. */
+typedef enum mc_kernel_path {
+    MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1, MC_PATH_ROW = 2, MC_PATH_WAVE = 3
+} mc_kernel_path;
 
 /* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the
  * cells.  BCC / FCC: 2 / 4 simple cubic sub-lattices with basis (0,0,0),

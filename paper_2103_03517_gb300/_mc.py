@@ -19,7 +19,7 @@ MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR
 MC_ERR_CANCELLED = -8
 MC_FP32, MC_FP64 = 0, 1
 MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
-MC_PATH_AUTO, MC_PATH_GENERAL, MC_PATH_ROW = 0, 1, 2
+MC_PATH_AUTO, MC_PATH_GENERAL, MC_PATH_ROW, MC_PATH_WAVE = 0, 1, 2, 3
 MC_SC, MC_BCC, MC_FCC, MC_HCP = 0, 1, 2, 3
 MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
 MC_TUNE_SWEEP, MC_TUNE_CONSTRAINED = 1, 2

@@ -22,6 +22,35 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
+// The round keys of philox(c, k0, k1) (the key before round r is k + r W),
+// computed once for a lattice, and the same ten rounds taking them from
+// registers: the same four words as philox(c, k0, k1).
+struct PhiloxKeys {
+    uint32_t a[10], b[10];
+};
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys K;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.a[r] = k0;
+        K.b[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = uint64_t(0xD2511F53u) * c.x, p1 = uint64_t(0xCD9E8D57u) * c.z;
+        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0), hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+        c = make_uint4(hi1 ^ c.y ^ K.a[r], lo1, hi0 ^ c.w ^ K.b[r], lo0);
+    }
+    return c;
+}
+
 // Philox stream tags: bit 0 = colour, bits 1.. = purpose.
 enum { kPurposeMove = 0, kPurposePair = 1, kPurposePerm = 2 };
 __device__ __forceinline__ uint32_t tag_of(int colour, int purpose) {

@@ -167,14 +167,16 @@ struct GroupArgs {
 };
 
 // Wavefront sweep (wave_pass.cuh): lattices with rows of kWaveLh colour
-// indices (Lx = 128) and Ly a multiple of kWaveTy, split into work units.
+// indices (Lx = 128) and Ly >= kWaveMinLy, cut into bands of at most
+// kWaveTyMax rows and slabs of planes (work units).
 constexpr int kWaveLh = 64;
-constexpr int kWaveTy = 16;
+constexpr int kWaveTyMax = 15;
+constexpr int kWaveMinLy = 16;
 
-// Wavefront sweep: a work unit is band [y0, y0 + 16) x slab [z0, z0 + tz)
-// of lattice `lat` (an index into WaveArgs::lats), full rows in x.
+// A work unit: band [y0, y0 + ty) x slab [z0, z0 + tz) of lattice `lat` (an
+// index into WaveArgs::lats), full rows in x.
 struct WaveWU {
-    uint32_t lat, y0, z0, tz;
+    uint32_t lat, y0, z0, tz, ty, pad;
 };
 
 // Arguments of a wavefront launch: block b runs work units [off[b],

@@ -21,7 +21,7 @@
 // every neighbour enters with a factor 1, -1 (across an anti-periodic face)
 // or 0 (absent: open face or missing bond), an exact product.
 #pragma once
-#include "pass_impl.cuh"
+#include "pair_math.cuh"
 
 namespace mcgb {
 
@@ -32,13 +32,13 @@ __device__ __forceinline__ float2 ld2(const float* a, size_t i) { return *reinte
 // Factor of a neighbour across a face of an axis with boundary mode bc.
 __device__ __forceinline__ float face_factor(int bc) { return bc == 0 ? 1.0f : (bc == 3 ? -1.0f : 0.0f); }
 
-// Spins and neighbour sums of lane L's pair in the tile starting at q0;
-// returns the lattice index of the pair's first site (its parity is the
-// row's x offset).  GEN: mov[v] = site v is not on a pinned plane.
+// Spins and neighbour sums of lane L's pair in the tile starting at q0,
+// packed (site 0 in .x, site 1 in .y, as loaded); returns the lattice index
+// of the pair's first site (its parity is the row's x offset).  GEN:
+// mov[v] = site v is not on a pinned plane.
 template <int GEN>
 __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const float* s, int colour, uint32_t q0,
-                                                  int lane, V3<float> S[2], V3<float> h[2], V3<float> O[2],
-                                                  bool mov[2]) {
+                                                  int lane, P3& S, P3& h, P3& O, bool mov[2]) {
     const uint32_t stride = p.stride;
     const float* own = s + size_t(3 * colour) * stride;
     const float* oth = s + size_t(3 * (colour ^ 1)) * stride;
@@ -77,17 +77,18 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
             rgt = V3<float>{oth[qe], oth[stride + qe], oth[2 * size_t(stride) + qe]};
         }
     }
-    const V3<float> o0{v[3].x, v[4].x, v[5].x}, o1{v[3].y, v[4].y, v[5].y};
+    // the other colour at the pair's own indices: one x neighbour of each
+    // site (and the site of the other colour the sample pairs with it)
+    O = P3{v[3], v[4], v[5]};
     if constexpr (GEN == 0) {
-        // x neighbours: site 0 has o0 and (xoff ? o1 : lft), site 1 has o1 and
+        // the other x neighbour: site 0 has (xoff ? o1 : lft), site 1 has
         // (xoff ? rgt : o0); the -x + +x sum is the same either way round
-        const V3<float> a0 = xoff ? o1 : lft, a1 = xoff ? rgt : o0;
-        h[0].x = ((((o0.x + a0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
-        h[0].y = ((((o0.y + a0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
-        h[0].z = ((((o0.z + a0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
-        h[1].x = ((((o1.x + a1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
-        h[1].y = ((((o1.y + a1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
-        h[1].z = ((((o1.z + a1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
+        const P3 a{make_float2(xoff ? v[3].y : lft.x, xoff ? rgt.x : v[3].x),
+                   make_float2(xoff ? v[4].y : lft.y, xoff ? rgt.y : v[4].x),
+                   make_float2(xoff ? v[5].y : lft.z, xoff ? rgt.z : v[5].x)};
+        h.x = p2add(p2add(p2add(p2add(p2add(O.x, a.x), v[6]), v[9]), v[12]), v[15]);
+        h.y = p2add(p2add(p2add(p2add(p2add(O.y, a.y), v[7]), v[10]), v[13]), v[16]);
+        h.z = p2add(p2add(p2add(p2add(p2add(O.z, a.z), v[8]), v[11]), v[14]), v[17]);
         mov[0] = mov[1] = true;
     } else {
         const int bx = p.bc[0], by = p.bc[1], bz = p.bc[2];
@@ -102,30 +103,25 @@ __device__ __forceinline__ uint32_t row_pair_sums(const LatParams& p, const floa
                                           p.bonds + size_t(colour) * stride + q)))
                                     : 0x3F3Fu;
         auto fac = [mm](int bit, float base) { return ((mm >> bit) & 1u) ? base : 0.0f; };
-        const V3<float> xm0 = xoff ? o0 : lft, xp0 = xoff ? o1 : o0;
-        const V3<float> xm1 = xoff ? o1 : o0, xp1 = xoff ? rgt : o1;
-        {
-            const float a = fac(0, fxm), b = fac(1, 1.0f), c = fac(2, fym), d = fac(3, fyp), e = fac(4, fzm),
-                        f = fac(5, fzp);
-            h[0].x = ((((a * xm0.x + b * xp0.x) + c * v[6].x) + d * v[9].x) + e * v[12].x) + f * v[15].x;
-            h[0].y = ((((a * xm0.y + b * xp0.y) + c * v[7].x) + d * v[10].x) + e * v[13].x) + f * v[16].x;
-            h[0].z = ((((a * xm0.z + b * xp0.z) + c * v[8].x) + d * v[11].x) + e * v[14].x) + f * v[17].x;
-        }
-        {
-            const float a = fac(8, 1.0f), b = fac(9, fxp), c = fac(10, fym), d = fac(11, fyp), e = fac(12, fzm),
-                        f = fac(13, fzp);
-            h[1].x = ((((a * xm1.x + b * xp1.x) + c * v[6].y) + d * v[9].y) + e * v[12].y) + f * v[15].y;
-            h[1].y = ((((a * xm1.y + b * xp1.y) + c * v[7].y) + d * v[10].y) + e * v[13].y) + f * v[16].y;
-            h[1].z = ((((a * xm1.z + b * xp1.z) + c * v[8].y) + d * v[11].y) + e * v[14].y) + f * v[17].y;
-        }
+        // -x and +x neighbours of the two sites, and each term's factor (an
+        // exact 1, -1 or 0), packed (site 0, site 1)
+        const P3 xm{make_float2(xoff ? v[3].x : lft.x, xoff ? v[3].y : v[3].x),
+                    make_float2(xoff ? v[4].x : lft.y, xoff ? v[4].y : v[4].x),
+                    make_float2(xoff ? v[5].x : lft.z, xoff ? v[5].y : v[5].x)};
+        const P3 xp{make_float2(xoff ? v[3].y : v[3].x, xoff ? rgt.x : v[3].y),
+                    make_float2(xoff ? v[4].y : v[4].x, xoff ? rgt.y : v[4].y),
+                    make_float2(xoff ? v[5].y : v[5].x, xoff ? rgt.z : v[5].y)};
+        const float2 Fxm = make_float2(fac(0, fxm), fac(8, 1.0f)), Fxp = make_float2(fac(1, 1.0f), fac(9, fxp));
+        const float2 Fym = make_float2(fac(2, fym), fac(10, fym)), Fyp = make_float2(fac(3, fyp), fac(11, fyp));
+        const float2 Fzm = make_float2(fac(4, fzm), fac(12, fzm)), Fzp = make_float2(fac(5, fzp), fac(13, fzp));
+        h.x = p2fma(Fzp, v[15], p2fma(Fzm, v[12], p2fma(Fyp, v[9], p2fma(Fym, v[6], p2fma(Fxp, xp.x, p2mul(Fxm, xm.x))))));
+        h.y = p2fma(Fzp, v[16], p2fma(Fzm, v[13], p2fma(Fyp, v[10], p2fma(Fym, v[7], p2fma(Fxp, xp.y, p2mul(Fxm, xm.y))))));
+        h.z = p2fma(Fzp, v[17], p2fma(Fzm, v[14], p2fma(Fyp, v[11], p2fma(Fym, v[8], p2fma(Fxp, xp.z, p2mul(Fxm, xm.z))))));
         const bool row_pinned = (by == 2 && (y == 0 || y + 1 == Ly)) || (bz == 2 && (z == 0 || z + 1 == Lz));
         mov[0] = !row_pinned && !(bx == 2 && x0 == 0);
         mov[1] = !row_pinned && !(bx == 2 && x0 + 3 == uint32_t(p.Lx));
     }
-    S[0] = V3<float>{v[0].x, v[1].x, v[2].x};
-    S[1] = V3<float>{v[0].y, v[1].y, v[2].y};
-    O[0] = o0;
-    O[1] = o1;
+    S = P3{v[0], v[1], v[2]};
     return xoff + 2u * k + uint32_t(p.Lx) * row;
 }
 
@@ -175,59 +171,46 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         long long fix = 0;
         for (; tile < t1; ++tile) {
             const uint32_t q0 = (tile - t0) * 64u;
-            V3<float> S[2], h[2], O[2];
+            P3 S, h, O;
             bool mov[2];
             const uint32_t site0 = row_pair_sums<GEN>(p, s, colour, q0, lane, S, h, O, mov);
-            V3<float> e[2] = {e_ax, e_ax};
+            P3 e, eo;  // per-site easy axes (films with grain axes)
+            const bool grains = GEN != 0 && p.grain;
             if constexpr (GEN != 0) {
-                if (p.grain)
+                if (grains) {
+                    V3<float> a[2], b[2];
 #pragma unroll
-                    for (int v = 0; v < 2; ++v) e[v] = grain_axis(p, colour, q0 + 2u * uint32_t(lane) + v);
+                    for (int v = 0; v < 2; ++v) {
+                        a[v] = grain_axis(p, colour, q0 + 2u * uint32_t(lane) + v);
+                        b[v] = grain_axis(p, colour ^ 1, q0 + 2u * uint32_t(lane) + v);
+                    }
+                    e = pack(a);
+                    eo = pack(b);
+                }
             }
-            V3<float> Sf[2] = {S[0], S[1]};
+            if (!grains) e = eo = P3{p2(e_ax.x), p2(e_ax.y), p2(e_ax.z)};
+            P3 Sf = S;
             bool any = false;
             if constexpr (MOVE != 0) {
                 const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), p.key0, p.key1);
-                float P[2], sd[2], cp[2], sp[2];
-                direct_draw_two(w, P, sd, cp, sp);
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
-                    const bool acc = mov[v] && metropolis(delta_e(par, S[v], Sn, h[v], e[v]), par, P[v]);
-                    Sf[v] = acc ? Sn : S[v];
-                    nacc += acc ? 1u : 0u;
-                    any = any || acc;
-                }
+                const unsigned n = pair_move(par, c, w, S, h, mov, grains ? &e : nullptr, Sf);
+                nacc += n;
+                any = n != 0;
             }
             if constexpr (MOVE == 0 && GEN == 0) {
                 if (colour == 0 && p.pfield) {
                     Spin4<float>* fld = static_cast<Spin4<float>*>(p.pfield) + q0 + 2u * uint32_t(lane);
-                    fld[0] = Spin4<float>{h[0].x, h[0].y, h[0].z, 0.0f};
-                    fld[1] = Spin4<float>{h[1].x, h[1].y, h[1].z, 0.0f};
+                    fld[0] = Spin4<float>{h.x.x, h.y.x, h.z.x, 0.0f};
+                    fld[1] = Spin4<float>{h.x.y, h.y.y, h.z.y, 0.0f};
                 }
             }
             if (any) {  // both sites of the pair in one 8-byte store per component
                 float* own = s + size_t(3 * colour) * p.stride + q0 + 2u * uint32_t(lane);
-                *reinterpret_cast<float2*>(own) = make_float2(Sf[0].x, Sf[1].x);
-                *reinterpret_cast<float2*>(own + p.stride) = make_float2(Sf[0].y, Sf[1].y);
-                *reinterpret_cast<float2*>(own + 2 * size_t(p.stride)) = make_float2(Sf[0].z, Sf[1].z);
+                *reinterpret_cast<float2*>(own) = Sf.x;
+                *reinterpret_cast<float2*>(own + p.stride) = Sf.y;
+                *reinterpret_cast<float2*>(own + 2 * size_t(p.stride)) = Sf.z;
             }
-            if constexpr (MEASURE > 0) {
-                Sums<float> sums;
-#pragma unroll
-                for (int i = 0; i < kNumSums; ++i) sums.v[i] = 0.0f;
-                const bool nu = par.Ku != 0.0f, nc = par.Kc != 0.0f;
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    V3<float> eo = e_ax;
-                    if constexpr (GEN != 0)
-                        if (p.grain) eo = grain_axis(p, colour ^ 1, q0 + 2u * uint32_t(lane) + v);
-                    add_site<float, MEASURE>(sums, Sf[v], e[v], nu, nc);
-                    sums.v[kSumEx] += Sf[v].x * h[v].x + Sf[v].y * h[v].y + Sf[v].z * h[v].z;
-                    add_site<float, MEASURE>(sums, O[v], eo, nu, nc);
-                }
-                fix += warp_tile_fix<float, NS>(sums, lane);
-            }
+            if constexpr (MEASURE > 0) fix += pair_tile_sample<MEASURE, NS>(par, Sf, h, e, O, eo, lane);
         }
         if constexpr (MOVE != 0) {
             publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {

@@ -193,13 +193,13 @@ static void xtal_table(int lattice, double J, double J2, const LatParams& p, Xta
 
 // Lattices whose sweeps may run as wavefront launches (wave_pass.cuh):
 // FP32 simple cubic, every axis periodic, no film tables, rows of 64 sites
-// per colour (Lx = 128), Ly a multiple of 16, the automatic kernel path.
+// per colour (Lx = 128), Ly >= 16, the wavefront kernel path asked for.
 bool wave_desc(const mc_desc* d) {
-    if (d->precision != MC_FP32 || d->lattice != MC_SC || d->kernel_path != MC_PATH_AUTO) return false;
+    if (d->precision != MC_FP32 || d->lattice != MC_SC || d->kernel_path != MC_PATH_WAVE) return false;
     if (d->bond_mask || d->grain_id) return false;
     for (int a = 0; a < 3; ++a)
         if (d->boundary[a] != MC_PERIODIC) return false;
-    return d->dims[0] == 2 * kWaveLh && d->dims[1] % kWaveTy == 0;
+    return d->dims[0] == 2 * kWaveLh && d->dims[1] >= kWaveMinLy;
 }
 
 size_t lattice_bytes(const mc_desc* d) {
@@ -248,7 +248,7 @@ int validate_desc(const mc_desc* d) {
         if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc / hcp lattices take no film tables");
         if (!std::isfinite(d->J2)) return fail(MC_ERR_ARG, "J2 not finite");
     }
-    if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_GENERAL && d->kernel_path != MC_PATH_ROW)
+    if (d->kernel_path < MC_PATH_AUTO || d->kernel_path > MC_PATH_WAVE)
         return fail(MC_ERR_ARG, "kernel_path invalid");
     if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
     if (d->init != MC_INIT_UNIFORM && d->init != MC_INIT_WALL) return fail(MC_ERR_ARG, "init invalid");
@@ -614,7 +614,8 @@ LaunchSet single_launch_set(mc_lattice* h) {
 
 // ------------------------------------------------------------ wavefront plan
 // Work units of the wavefront lattices for `blocks` resident blocks: every
-// lattice is cut into bands of kWaveTy rows, each band into slabs of planes.
+// lattice is cut into bands of at most kWaveTyMax rows, each band into slabs
+// of planes.
 // A unit of tz planes takes about 2 tz + 5 row-steps of a block (tz + 3
 // phases, the first three and the last only half full).  Two plans are
 // tried and the one with the shorter longest block kept: (a) every band cut
@@ -625,14 +626,20 @@ LaunchSet single_launch_set(mc_lattice* h) {
 static long long wave_cost(uint32_t tz) { return 2ll * tz + 5; }
 
 WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks) {
-    struct Band { uint32_t lat, y0, lz; };
+    struct Band { uint32_t lat, y0, lz, ty; };
     std::vector<Band> bands;
     uint32_t lz_max = 1;
     long long planes = 0;
     for (size_t l = 0; l < lats.size(); ++l) {
-        for (int y0 = 0; y0 < lats[l]->Ly; y0 += kWaveTy) bands.push_back({uint32_t(l), uint32_t(y0), uint32_t(lats[l]->Lz)});
+        // the fewest bands of at most kWaveTyMax rows, heights as equal as possible
+        const int Ly = lats[l]->Ly, nb = (Ly + kWaveTyMax - 1) / kWaveTyMax;
+        for (int b = 0, y0 = 0; b < nb; ++b) {
+            const int ty = Ly / nb + (b < Ly % nb ? 1 : 0);
+            bands.push_back({uint32_t(l), uint32_t(y0), uint32_t(lats[l]->Lz), uint32_t(ty)});
+            y0 += ty;
+        }
         lz_max = std::max(lz_max, uint32_t(lats[l]->Lz));
-        planes += (long long)(lats[l]->Ly / kWaveTy) * lats[l]->Lz;
+        planes += (long long)nb * lats[l]->Lz;
     }
     if (blocks < 1) blocks = 1;
     std::vector<std::vector<WaveWU>> best;
@@ -656,7 +663,7 @@ WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks) {
             const uint32_t ns = (b.lz + T - 1) / T;
             for (uint32_t k = 0, z = 0; k < ns; ++k) {
                 const uint32_t tz = b.lz / ns + (k < b.lz % ns ? 1u : 0u);
-                units.push_back({b.lat, b.y0, z, tz});
+                units.push_back({b.lat, b.y0, z, tz, b.ty, 0});
                 z += tz;
             }
         }
@@ -681,7 +688,7 @@ WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks) {
             for (uint32_t i = 0; i < blocks; ++i) {
                 const long long r0 = planes * i / blocks, r1 = planes * (i + 1) / blocks;
                 const long long a = std::max(r0, pos), e = std::min(r1, pos + (long long)b.lz);
-                if (a < e) bins[i].push_back({b.lat, b.y0, uint32_t(a - pos), uint32_t(e - a)});
+                if (a < e) bins[i].push_back({b.lat, b.y0, uint32_t(a - pos), uint32_t(e - a), b.ty, 0});
             }
             pos += b.lz;
         }

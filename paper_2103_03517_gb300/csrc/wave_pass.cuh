@@ -1,43 +1,49 @@
 // wave_pass.cuh -- one FP32 sweep of Table A1 (red pass, then black pass)
 // in a single launch, for all-periodic lattices whose rows hold Lh = 64
-// sites per colour (Lx = 128) and Ly a multiple of 16: the 128^3 lattices of
-// the batched m(T) workload.
+// sites per colour (Lx = 128) and Ly >= 16: the 128^3 lattices of the
+// batched m(T) workload.
 //
 // The sweep reads the spins from one buffer and writes every spin, moved or
 // not, to a second one (LatParams::spins_alt), so that the old state stays
-// readable for the whole launch.  A block owns a work unit: a band of 16
-// rows (y) times a slab of tz planes (z), full rows in x.  It marches up the
-// slab: in phase j it updates red plane z0 - 1 + j and black plane z0 + j - 3,
-// so that every black site sees its six red neighbours already moved, as the
-// black pass of Table A1 does.  The red sites one row outside the band and
-// one plane outside the slab are moved as well, from the old state, with
-// the same draws as their owner block uses (the Philox counter is the site
-// and the sweep): they are bit-identical to what the owner writes, and only
-// the owner writes them or counts them.
+// readable for the whole launch.  A block owns a work unit: a band of ty <=
+// 15 rows (y) times a slab of tz planes (z), full rows in x.  It marches up
+// the slab: in phase j it updates red plane z0 - 1 + j and black plane
+// z0 + j - 3, so that every black site sees its six red neighbours already
+// moved, as the black pass of Table A1 does.  The red sites one row outside
+// the band and one plane outside the slab are moved as well, from the old
+// state, with the same draws as their owner block uses (the Philox counter
+// is the site and the sweep): they are bit-identical to what the owner
+// writes, and only the owner writes them or counts them.
+//
+// Work split: 16 warps, 4 per scheduler; in a phase warp w moves red row w
+// and black row w of the band (row indices counted from the halo row below
+// it), and warp 0 also red row 16 of a 15-row band: 32 rows of 64 sites
+// per phase, two per warp, so that no warp or scheduler carries more of a
+// phase than another.
 //
 // Staging (per block, dynamic shared memory): the old black planes of the
 // band +- 2 rows (a ring of 6 planes, two phases ahead), the old red planes
 // of the band +- 1 row (a ring of 3) and the new red planes (a ring of 4).
 // The old planes arrive by bulk asynchronous copies (cp.async.bulk), issued
-// by one thread two phases before they are needed and tracked by one
-// mbarrier per ring slot; every wait is bounded and, when it runs out, the
-// lattice's error is set to MC_ERR_TIMEOUT and the block stops.
+// by the lanes of warp 0 two phases before they are needed and tracked by
+// one mbarrier per ring slot; every wait is bounded and, when it runs out,
+// the lattice's error is set to MC_ERR_TIMEOUT and the block stops.
 //
 // Each spin is read once from HBM and written once per sweep (24 B per
 // update, plus the halo rows and planes, which mostly hit L2).  The Philox
 // counters, the trial points, the energy change and the sample sums are
-// those of the two-pass row kernel (row_pass.cuh), term for term and in the
-// same order, so a wavefront sweep gives the spins of a red and a black row
-// pass.
+// those of the two-pass row kernel (row_pass.cuh, pair_math.cuh), term for
+// term and in the same order, so a wavefront sweep gives the spins of a red
+// and a black row pass.
 #pragma once
-#include "pass_impl.cuh"
+#include "pair_math.cuh"
 
 namespace mcgb {
 
-constexpr int kWaveWarps = 17;                    // 18 red + 16 black rows = 2 rows per warp a phase
+constexpr int kWaveWarps = 16;
 constexpr int kWaveThreads = 32 * kWaveWarps;
-constexpr int kWaveBRows = kWaveTy + 4;           // staged old black rows: band +- 2
-constexpr int kWaveRRows = kWaveTy + 2;           // red rows: band +- 1
+constexpr int kWaveBRows = kWaveTyMax + 4;        // staged old black rows: band +- 2
+constexpr int kWaveRRows = kWaveTyMax + 2;        // red rows: band +- 1
 constexpr int kWaveBSlots = 6, kWaveROSlots = 3, kWaveRNSlots = 4;
 constexpr int kWaveBComp = kWaveBRows * kWaveLh;  // floats of one component of a black slot
 constexpr int kWaveRComp = kWaveRRows * kWaveLh;
@@ -45,6 +51,7 @@ constexpr size_t kWaveSmemFloats =
     size_t(kWaveBSlots) * 3 * kWaveBComp + size_t(kWaveROSlots + kWaveRNSlots) * 3 * kWaveRComp;
 constexpr size_t kWaveSmemBytes = kWaveSmemFloats * 4 + 16 * 8;  // + the mbarriers
 constexpr long long kWaveWaitCycles = 1ll << 31;  // about one second at 2 GHz
+static_assert(kWaveTyMax + 2 <= 2 * kWaveWarps + 1, "the red rows of a band must fit the warps' tasks");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -91,25 +98,30 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// Stage rows y_first .. y_first + nrows - 1 (wrapped in Ly) of plane z of
-// one colour into a ring slot laid out [3][nrows][64]: one expect_tx for
-// the whole plane, then up to three contiguous pieces per component.
-__device__ __forceinline__ void wave_stage(float* slot, const float* colour_base, uint32_t stride, int Ly,
-                                           int y_first, int nrows, int z, uint64_t* bar, uint32_t extra) {
-    mbar_expect_tx(bar, uint32_t(3 * nrows * kWaveLh * 4) + extra);
-    const float* plane = colour_base + size_t(z) * size_t(Ly) * kWaveLh;
-    for (int a = 0; a < 3; ++a) {
-        const float* comp = plane + size_t(a) * stride;
-        float* d = slot + a * nrows * kWaveLh;
-        int y = y_first < 0 ? y_first + Ly : y_first, left = nrows;  // y_first in [-2, Ly)
-        while (left > 0) {
-            const int n = min(left, Ly - y);
-            bulk_g2s(d, comp + size_t(y) * kWaveLh, uint32_t(n * kWaveLh * 4), bar);
-            d += n * kWaveLh;
-            left -= n;
-            y = 0;
-        }
+// One staged plane: rows y_first .. y_first + nrows - 1 (wrapped in Ly) of
+// plane z of one colour, into a ring slot laid out [3][cap][64] (cap rows
+// per component), completing on bar.
+struct StagePlane {
+    float* slot;
+    const float* colour_base;
+    int cap, y_first, nrows, z;
+    uint64_t* bar;
+};
+
+// Piece `piece` (0, 1, 2) of component a of a staged plane: the rows of the
+// plane split where they wrap in Ly (y_first >= -2, nrows <= Ly + 4, so at
+// most three pieces).
+__device__ __forceinline__ void stage_piece(const StagePlane& s, uint32_t stride, int Ly, int a, int piece,
+                                            uint64_t* bar) {
+    int y = s.y_first < 0 ? s.y_first + Ly : s.y_first, done = 0, n = min(s.nrows, Ly - y);
+    for (int k = 0; k < piece; ++k) {  // skip to the piece
+        done += n;
+        y = 0;
+        n = min(s.nrows - done, Ly);
     }
+    if (n <= 0) return;
+    const float* src = s.colour_base + size_t(a) * stride + (size_t(s.z) * size_t(Ly) + size_t(y)) * kWaveLh;
+    bulk_g2s(s.slot + (a * s.cap + done) * kWaveLh, src, uint32_t(n * kWaveLh * 4), bar);
 }
 
 __device__ __forceinline__ float2 lds2(const float* row, int lane) {
@@ -117,14 +129,15 @@ __device__ __forceinline__ float2 lds2(const float* row, int lane) {
 }
 
 // Spins and neighbour sums of lane L's two sites (colour indices 2L, 2L + 1)
-// of one row, all rows in shared memory: own (the site's colour, component
-// stride cs_own), and of the other colour the same row xr and the rows -y,
-// +y (component stride cs_xy), -z (cs_zm) and +z (cs_zp).  The x neighbours
-// and the sums are those of the row kernel: -x + +x, then -y, +y, -z, +z.
+// of one row, all rows in shared memory, packed (site 0 in .x): own (the
+// site's colour, component stride cs_own), and of the other colour the same
+// row xr and the rows -y, +y (component stride cs_xy), -z (cs_zm) and +z
+// (cs_zp).  The x neighbours and the sums are those of the row kernel: -x +
+// +x, then -y, +y, -z, +z.
 __device__ __forceinline__ void wave_pair_sums(const float* own, int cs_own, const float* xr, const float* ym,
                                                const float* yp, int cs_xy, const float* zm, int cs_zm,
-                                               const float* zp, int cs_zp, int lane, uint32_t xoff, V3<float> S[2],
-                                               V3<float> h[2], V3<float> O[2]) {
+                                               const float* zp, int cs_zp, int lane, uint32_t xoff, P3& S, P3& h,
+                                               P3& O) {
     float2 v[18];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -140,49 +153,27 @@ __device__ __forceinline__ void wave_pair_sums(const float* own, int cs_own, con
                         __shfl_sync(0xffffffffu, v[5].y, left)};
     const V3<float> rgt{__shfl_sync(0xffffffffu, v[3].x, right), __shfl_sync(0xffffffffu, v[4].x, right),
                         __shfl_sync(0xffffffffu, v[5].x, right)};
-    const V3<float> o0{v[3].x, v[4].x, v[5].x}, o1{v[3].y, v[4].y, v[5].y};
-    const V3<float> a0 = xoff ? o1 : lft, a1 = xoff ? rgt : o0;
-    h[0].x = ((((o0.x + a0.x) + v[6].x) + v[9].x) + v[12].x) + v[15].x;
-    h[0].y = ((((o0.y + a0.y) + v[7].x) + v[10].x) + v[13].x) + v[16].x;
-    h[0].z = ((((o0.z + a0.z) + v[8].x) + v[11].x) + v[14].x) + v[17].x;
-    h[1].x = ((((o1.x + a1.x) + v[6].y) + v[9].y) + v[12].y) + v[15].y;
-    h[1].y = ((((o1.y + a1.y) + v[7].y) + v[10].y) + v[13].y) + v[16].y;
-    h[1].z = ((((o1.z + a1.z) + v[8].y) + v[11].y) + v[14].y) + v[17].y;
-    S[0] = V3<float>{v[0].x, v[1].x, v[2].x};
-    S[1] = V3<float>{v[0].y, v[1].y, v[2].y};
-    O[0] = o0;
-    O[1] = o1;
+    O = P3{v[3], v[4], v[5]};
+    const P3 a{make_float2(xoff ? v[3].y : lft.x, xoff ? rgt.x : v[3].x),
+               make_float2(xoff ? v[4].y : lft.y, xoff ? rgt.y : v[4].x),
+               make_float2(xoff ? v[5].y : lft.z, xoff ? rgt.z : v[5].x)};
+    h.x = p2add(p2add(p2add(p2add(p2add(O.x, a.x), v[6]), v[9]), v[12]), v[15]);
+    h.y = p2add(p2add(p2add(p2add(p2add(O.y, a.y), v[7]), v[10]), v[13]), v[16]);
+    h.z = p2add(p2add(p2add(p2add(p2add(O.z, a.z), v[8]), v[11]), v[14]), v[17]);
+    S = P3{v[0], v[1], v[2]};
 }
 
-// Trial moves and Metropolis tests of lane L's two sites (Table A1, Eq. 1-2),
-// with the draws of the row kernel: one Philox call keyed by the first site.
-__device__ __forceinline__ unsigned wave_move(const Par<float>& par, float c, uint32_t site0, uint32_t sweep,
-                                              uint32_t tag, uint32_t k0, uint32_t k1, const V3<float> S[2],
-                                              const V3<float> h[2], V3<float> Sf[2]) {
-    const V3<float> e_ax{par.e[0], par.e[1], par.e[2]};
-    const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), k0, k1);
-    float P[2], sd[2], cp[2], sp[2];
-    direct_draw_two(w, P, sd, cp, sp);
-    unsigned nacc = 0;
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-        const V3<float> Sn = cap_point_direct(S[v], c, sd[v], cp[v], sp[v]);
-        const bool acc = metropolis(delta_e(par, S[v], Sn, h[v], e_ax), par, P[v]);
-        Sf[v] = acc ? Sn : S[v];
-        nacc += acc ? 1u : 0u;
-    }
-    return nacc;
+__device__ __forceinline__ void sts_p3(float* row, int cs, int lane, const P3& v) {
+    *reinterpret_cast<float2*>(row + 2 * lane) = v.x;
+    *reinterpret_cast<float2*>(row + cs + 2 * lane) = v.y;
+    *reinterpret_cast<float2*>(row + 2 * cs + 2 * lane) = v.z;
 }
 
-__device__ __forceinline__ void sts2(float* row, int lane, float a, float b) {
-    *reinterpret_cast<float2*>(row + 2 * lane) = make_float2(a, b);
-}
-
-__device__ __forceinline__ void stg_pair(float* colour_base, uint32_t stride, uint32_t q, const V3<float> Sf[2]) {
+__device__ __forceinline__ void stg_pair(float* colour_base, uint32_t stride, uint32_t q, const P3& Sf) {
     float* d = colour_base + q;
-    *reinterpret_cast<float2*>(d) = make_float2(Sf[0].x, Sf[1].x);
-    *reinterpret_cast<float2*>(d + stride) = make_float2(Sf[0].y, Sf[1].y);
-    *reinterpret_cast<float2*>(d + 2 * size_t(stride)) = make_float2(Sf[0].z, Sf[1].z);
+    *reinterpret_cast<float2*>(d) = Sf.x;
+    *reinterpret_cast<float2*>(d + stride) = Sf.y;
+    *reinterpret_cast<float2*>(d + 2 * size_t(stride)) = Sf.z;
 }
 
 // dir = 0: read spins, write spins_alt; dir = 1: the reverse.  MEASURE as
@@ -193,9 +184,9 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                                                                      int dir) {
     constexpr int NS = MEASURE >= 2 ? kNumSums : kSumTux;
     extern __shared__ __align__(128) float wsm[];
-    float* bslot = wsm;                                               // [6][3][20][64] old black
-    float* roslot = bslot + kWaveBSlots * 3 * kWaveBComp;             // [3][3][18][64] old red
-    float* rnslot = roslot + kWaveROSlots * 3 * kWaveRComp;           // [4][3][18][64] new red
+    float* bslot = wsm;                                               // [6][3][19][64] old black
+    float* roslot = bslot + kWaveBSlots * 3 * kWaveBComp;             // [3][3][17][64] old red
+    float* rnslot = roslot + kWaveROSlots * 3 * kWaveRComp;           // [4][3][17][64] new red
     uint64_t* bar = reinterpret_cast<uint64_t*>(rnslot + kWaveRNSlots * 3 * kWaveRComp);  // 6 + 3
     __shared__ int abort_flag;
     asm volatile("griddepcontrol.launch_dependents;");
@@ -208,58 +199,69 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     uint32_t nb = 0, nr = 0;  // staged copies planned so far (old black, old red): ring slot and parity
-    uint32_t ib = 0, ir = 0;  // copies issued so far (thread 0)
+    uint32_t ib = 0, ir = 0;  // planes issued so far (warp 0)
     const uint32_t w_end = a.off[blockIdx.x + 1];
     bool aborted = false;
-    int extra = blockIdx.x == 0 ? a.inject : 0;
+    uint32_t extra = blockIdx.x == 0 ? uint32_t(a.inject) : 0u;  // warp 0 only
     for (uint32_t wi = a.off[blockIdx.x]; wi < w_end && !aborted; ++wi) {
         const WaveWU u = a.wu[wi];
         LatDev* L = a.lats[u.lat];
         const LatParams& p = L->p;
         const Par<float> par = load_par<float>(p);
-        const int Ly = p.Ly, Lz = p.Lz, tz = int(u.tz), y0 = int(u.y0), z0 = int(u.z0);
+        const int Ly = p.Ly, Lz = p.Lz, tz = int(u.tz), ty = int(u.ty), y0 = int(u.y0), z0 = int(u.z0);
         const uint32_t stride = p.stride, Lx = uint32_t(p.Lx);
-        const uint32_t sweep = L->st.sweep, k0 = p.key0, k1 = p.key1;
+        const uint32_t sweep = L->st.sweep;
+        const PhiloxKeys K = philox_keys(p.key0, p.key1);
         const float c = cone[L->st.theta];
         const float* src = static_cast<const float*>(dir ? p.spins_alt : p.spins);
         float* dst = static_cast<float*>(dir ? p.spins : p.spins_alt);
-        const float* src_red = src;
-        const float* src_blk = src + 3 * size_t(stride);
         float* dst_red = dst;
         float* dst_blk = dst + 3 * size_t(stride);
         const uint32_t nb0 = nb, nr0 = nr;
-        // old black plane index i = plane z0 - 2 + i (i = 0 .. tz + 3), old red
-        // index i = plane z0 - 1 + i (i = 0 .. tz + 1)
-        auto issue_b = [&](int i) {
+        // old black plane index i = plane z0 - 2 + i (i = 0 .. tz + 3), rows
+        // y0 - 2 .. y0 + ty + 1; old red index i = plane z0 - 1 + i (i = 0 ..
+        // tz + 1), rows y0 - 1 .. y0 + ty
+        auto b_plane = [&](int i) {
             const uint32_t g = nb0 + uint32_t(i);
             const int z = z0 - 2 + i;  // in [-2, Lz + 1], Lz >= 2
-            wave_stage(bslot + (g % kWaveBSlots) * 3 * kWaveBComp, src_blk, stride, Ly, y0 - 2, kWaveBRows,
-                       z < 0 ? z + Lz : (z >= Lz ? z - Lz : z), &bar[g % kWaveBSlots], uint32_t(extra));
-            extra = 0;
-            ib = g + 1;
+            return StagePlane{bslot + (g % kWaveBSlots) * 3 * kWaveBComp, src + 3 * size_t(stride), kWaveBRows,
+                              y0 - 2, ty + 4, z < 0 ? z + Lz : (z >= Lz ? z - Lz : z), &bar[g % kWaveBSlots]};
         };
-        auto issue_r = [&](int i) {
+        auto r_plane = [&](int i) {
             const uint32_t g = nr0 + uint32_t(i);
             const int z = z0 - 1 + i;  // in [-1, Lz]
-            wave_stage(roslot + (g % kWaveROSlots) * 3 * kWaveRComp, src_red, stride, Ly, y0 - 1, kWaveRRows,
-                       z < 0 ? z + Lz : (z >= Lz ? z - Lz : z), &bar[kWaveBSlots + g % kWaveROSlots], 0u);
-            ir = g + 1;
+            return StagePlane{roslot + (g % kWaveROSlots) * 3 * kWaveRComp, src, kWaveRRows, y0 - 1, ty + 2,
+                              z < 0 ? z + Lz : (z >= Lz ? z - Lz : z), &bar[kWaveBSlots + g % kWaveROSlots]};
         };
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int i = 0; i < 5; ++i) issue_b(i);
-            for (int i = 0; i < 3; ++i) issue_r(i);
-        }
+        // warp 0 stages old black planes b_lo .. b_hi - 1 and old red planes
+        // r_lo .. r_hi - 1: lane 0 arms each plane's barrier with its bytes,
+        // then the lanes issue the pieces (plane, piece, component) between them
+        auto stage = [&](int b_lo, int b_hi, int r_lo, int r_hi) {
+            const int nbp = max(b_hi - b_lo, 0), nrp = max(r_hi - r_lo, 0);
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                for (int i = 0; i < nbp + nrp; ++i) {
+                    const StagePlane sp = i < nbp ? b_plane(b_lo + i) : r_plane(r_lo + i - nbp);
+                    mbar_expect_tx(sp.bar, uint32_t(3 * sp.nrows * kWaveLh * 4) + extra);
+                    extra = 0;
+                }
+                if (nbp) ib = nb0 + uint32_t(b_hi);
+                if (nrp) ir = nr0 + uint32_t(r_hi);
+            }
+            __syncwarp();
+            for (int k = lane; k < 9 * (nbp + nrp); k += 32) {
+                const int i = k / 9, piece = (k % 9) / 3, comp = k % 3;
+                const StagePlane sp = i < nbp ? b_plane(b_lo + i) : r_plane(r_lo + i - nbp);
+                stage_piece(sp, stride, Ly, comp, piece, sp.bar);
+            }
+        };
+        if (warp == 0) stage(0, 5, 0, 3);
         nb += uint32_t(tz + 4);
         nr += uint32_t(tz + 2);
         unsigned nacc = 0;
         long long fix = 0;
         for (int j = 0; j <= tz + 2; ++j) {
-            if (j > 0 && tid == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (j + 4 <= tz + 3) issue_b(j + 4);
-                if (j + 2 <= tz + 1) issue_r(j + 2);
-            }
+            if (j > 0 && warp == 0) stage(j + 4, min(j + 5, tz + 4), j + 2, min(j + 3, tz + 2));
             const bool red = j <= tz + 1, black = j >= 3;
             if (red) {  // old black planes j .. j + 2 and old red plane j
                 bool ok = true;
@@ -271,7 +273,6 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                 ok = ok && mbar_wait(&bar[kWaveBSlots + g % kWaveROSlots], (g / kWaveROSlots) & 1u);
                 if (!ok) abort_flag = 1;
             }
-            const int nred = red ? kWaveRRows : 0, ntask = nred + (black ? kWaveTy : 0);
             // ring slots of this phase (uniform over the block): red plane
             // zr = z0 - 1 + j reads old black j .. j + 2 and old red j, writes
             // new red j; black plane zb = z0 + j - 3 reads old black j - 1 and
@@ -289,10 +290,16 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
             zr = zr < 0 ? zr + Lz : (zr >= Lz ? zr - Lz : zr);
             int zb = z0 + j - 3;
             zb = zb >= Lz ? zb - Lz : zb;
-            for (int t = warp; t < ntask; t += kWaveWarps) {
-                V3<float> S[2], h[2], O[2], Sf[2];
-                if (t < nred) {  // red row r of plane zr
-                    const int r = t;
+            // warp w: red row w, then black row w (rows counted from the halo
+            // row below the band: red 0 .. ty + 1, black 1 .. ty); warp 0 takes
+            // red row 16 of a 15-row band in place of a black row
+            for (int k = 0; k < 2; ++k) {
+                const bool is_red = k == 0 || warp == 0;
+                const int r = k == 0 ? warp : (warp == 0 ? kWaveWarps : warp);
+                if (is_red ? !(red && r <= ty + 1) : !(black && r <= ty)) continue;
+                P3 S, h, O, Sf;
+                const bool mov[2] = {true, true};
+                if (is_red) {  // red row r of plane zr
                     int y = y0 - 1 + r;  // in [-1, Ly]
                     y = y < 0 ? y + Ly : (y >= Ly ? y - Ly : y);
                     const uint32_t xoff = uint32_t(y + zr) & 1u;
@@ -301,17 +308,14 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                                    b2 + (r + 1) * kWaveLh, kWaveBComp, lane, xoff, S, h, O);
                     const uint32_t row = uint32_t(y) + uint32_t(Ly) * uint32_t(zr);
                     const uint32_t site0 = xoff + 4u * uint32_t(lane) + Lx * row;
-                    const unsigned n = wave_move(par, c, site0, sweep, tag_of(0, kPurposeMove), k0, k1, S, h, Sf);
-                    float* rw = rn + r * kWaveLh;
-                    sts2(rw, lane, Sf[0].x, Sf[1].x);
-                    sts2(rw + kWaveRComp, lane, Sf[0].y, Sf[1].y);
-                    sts2(rw + 2 * kWaveRComp, lane, Sf[0].z, Sf[1].z);
-                    if (r >= 1 && r <= kWaveTy && j >= 1 && j <= tz) {  // owned: in the band and the slab
+                    const uint4 w = philox_rk(make_uint4(site0, sweep, tag_of(0, kPurposeMove), 0u), K);
+                    const unsigned n = pair_move(par, c, w, S, h, mov, nullptr, Sf);
+                    sts_p3(rn + r * kWaveLh, kWaveRComp, lane, Sf);
+                    if (r >= 1 && r <= ty && j >= 1 && j <= tz) {  // owned: in the band and the slab
                         stg_pair(dst_red, stride, row * kWaveLh + 2u * uint32_t(lane), Sf);
                         nacc += n;
                     }
                 } else {  // black row r of plane zb
-                    const int r = t - nred + 1;
                     const int y = y0 - 1 + r;
                     const uint32_t xoff = uint32_t(y + zb + 1) & 1u;
                     wave_pair_sums(bo + (r + 1) * kWaveLh, kWaveBComp, r0 + r * kWaveLh, r0 + (r - 1) * kWaveLh,
@@ -319,21 +323,12 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                                    rp + r * kWaveLh, kWaveRComp, lane, xoff, S, h, O);
                     const uint32_t row = uint32_t(y) + uint32_t(Ly) * uint32_t(zb);
                     const uint32_t site0 = xoff + 4u * uint32_t(lane) + Lx * row;
-                    nacc += wave_move(par, c, site0, sweep, tag_of(1, kPurposeMove), k0, k1, S, h, Sf);
+                    const uint4 w = philox_rk(make_uint4(site0, sweep, tag_of(1, kPurposeMove), 0u), K);
+                    nacc += pair_move(par, c, w, S, h, mov, nullptr, Sf);
                     stg_pair(dst_blk, stride, row * kWaveLh + 2u * uint32_t(lane), Sf);
                     if constexpr (MEASURE > 0) {
-                        Sums<float> sums;
-#pragma unroll
-                        for (int i = 0; i < kNumSums; ++i) sums.v[i] = 0.0f;
-                        const bool nu = par.Ku != 0.0f, nc = par.Kc != 0.0f;
-                        const V3<float> e_ax{par.e[0], par.e[1], par.e[2]};
-#pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            add_site<float, MEASURE>(sums, Sf[v], e_ax, nu, nc);
-                            sums.v[kSumEx] += Sf[v].x * h[v].x + Sf[v].y * h[v].y + Sf[v].z * h[v].z;
-                            add_site<float, MEASURE>(sums, O[v], e_ax, nu, nc);
-                        }
-                        fix += warp_tile_fix<float, NS>(sums, lane);
+                        const P3 e{p2(par.e[0]), p2(par.e[1]), p2(par.e[2])};
+                        fix += pair_tile_sample<MEASURE, NS>(par, Sf, h, e, O, e, lane);
                     }
                 }
             }
@@ -365,7 +360,7 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
         }
     }
     // no copy may still be writing this block's shared memory when it exits:
-    // wait (bounded) on the last copy issued to every slot
+    // wait (bounded) on the last plane issued to every slot
     if (aborted && tid == 0) {
         for (int s = 0; s < kWaveBSlots; ++s)
             if (ib > uint32_t(s)) {

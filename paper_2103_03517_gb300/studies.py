@@ -20,7 +20,7 @@ from . import _mc as mc
 from . import analysis as an
 
 __all__ = ["magnetization_curve", "exchange_stiffness_study", "bloch_wall_spins", "film_curie_study",
-           "anisotropy_torque_study", "pinned_wall_study"]
+           "anisotropy_torque_study", "pinned_wall_study", "chain_ensembles"]
 
 
 def magnetization_curve(dims, temps, K_u=0.01, K_c=0.0, n_eq=2000, n_meas=5000, seed=0, precision=mc.MC_FP32,
@@ -428,3 +428,52 @@ def pinned_wall_study(temps, dims=(1024, 128, 128), K_u=0.05, n_eq=2000, n_meas=
     updates = float(len(temps)) * (float(np.prod(dims)) * (n_eq + max(1, n_meas // every) * every)
                                    + float(np.prod(uniform_dims)) * sum(uniform_sweeps))
     return {"rows": rows, "updates": updates, "seconds": seconds}
+
+
+def chain_ensembles(cases, n_chains, seed_of, sweeps_of, precision=mc.MC_FP32, max_group=4096, stream=None,
+                    device=0):
+    """Independent chains of Table A1 for each case: cases maps a name to a
+    lattice description (dims, K_u, T, J, axis attributes, as
+    workloads.LatticeSpec), n_chains maps a name to a chain count, seed_of(name,
+    k) gives chain k's seed and sweeps_of(name) its (n_eq, n_meas).  Every chain
+    starts along +z, runs n_eq sweeps, then n_meas measured sweeps (the cone
+    adapting in every sweep).  Chains run as groups of at most max_group
+    lattices.  Returns {name: {"ml", "ml2", "mabs_z", "mz", "e": arrays of the
+    per-chain means over the measured sweeps}}."""
+    jobs = [(name, k) for name in cases for k in range(int(n_chains[name]))]
+    out = {name: {key: [] for key in ("ml", "ml2", "mabs_z", "mz", "e")} for name in cases}
+    # chains of equal sweep counts share a group
+    by_sweeps = {}
+    for name, k in jobs:
+        by_sweeps.setdefault(tuple(sweeps_of(name)), []).append((name, k))
+    for (n_eq, n_meas), js in by_sweeps.items():
+        for i in range(0, len(js), max_group):
+            chunk = js[i:i + max_group]
+            hs = []
+            try:
+                for name, k in chunk:
+                    sp = cases[name]
+                    hs.append(mc.mc_create_ex(mc.make_desc(sp.dims, J=sp.J, K_u=sp.Ku, axis=sp.axis, T=sp.T,
+                                                           seed=seed_of(name, k), theta0_deg=sp.theta0,
+                                                           precision=precision, ring_capacity=1, sample_torque=0,
+                                                           stream=stream, device=device)))
+                g = mc.mc_group_create(hs)
+                try:
+                    mc.mc_group_sweep(g, n_eq)
+                    for h in hs:
+                        mc.mc_reset_stats(h)
+                    mc.mc_group_sweep(g, n_meas, measure=True)
+                    obs = mc.mc_group_measure(g, len(hs))
+                finally:
+                    mc.mc_group_destroy(g)
+                for (name, _), o in zip(chunk, obs):
+                    d = out[name]
+                    d["ml"].append(o.ml)
+                    d["ml2"].append(o.ml2)
+                    d["mabs_z"].append(o.m_abs[2])
+                    d["mz"].append(o.m[2])
+                    d["e"].append(o.e)
+            finally:
+                for h in hs:
+                    mc.mc_destroy(h)
+    return {name: {key: np.asarray(v) for key, v in d.items()} for name, d in out.items()}

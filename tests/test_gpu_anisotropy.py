@@ -57,19 +57,27 @@ def _eq4_series(h, K, n):
 
 
 def test_eq4_fp32_agrees_with_fp64():
-    K, n = 0.05, 3000
-    hs = [mc.mc_create_ex(mc.make_desc((16, 16, 16), K_u=K, T=0.9, seed=s, precision=p, ring_capacity=n))
-          for s, p in ((1, mc.MC_FP32), (2, mc.MC_FP64))]
-    try:
-        for h in hs:
-            mc.mc_sweep(h, 500)
-            mc.mc_sweep(h, n, measure=True)
-        k = [mc.mc_anisotropy_scaling(h)[0] for h in hs]
-        err = math.hypot(*(blocking_error(_eq4_series(h, K, n)) for h in hs))
-        assert abs(k[0] - k[1]) < max(4 * err, 2e-3), (k, err)
-    finally:
-        for h in hs:
-            mc.mc_destroy(h)
+    """k_u of Eq. 4 (16^3, T = 0.9) from eight independent runs per
+    precision: the FP32 and FP64 means agree within the 3-sigma-equivalent
+    bound (t3) of the spread between runs."""
+    from _stats import diff_within_t3
+    K, n, runs = 0.05, 3000, 8
+    k = {}
+    for p in (mc.MC_FP32, mc.MC_FP64):
+        hs = [mc.mc_create_ex(mc.make_desc((16, 16, 16), K_u=K, T=0.9, seed=1 + 2 * r + p, precision=p,
+                                           ring_capacity=16)) for r in range(runs)]
+        g = mc.mc_group_create(hs)
+        try:
+            mc.mc_group_sweep(g, 500)
+            mc.mc_group_sweep(g, n, measure=True)
+            mc.mc_group_sync(g)
+            k[p] = np.array([mc.mc_anisotropy_scaling(h)[0] for h in hs])
+        finally:
+            mc.mc_group_destroy(g)
+            for h in hs:
+                mc.mc_destroy(h)
+    d, se, bound = diff_within_t3(k[mc.MC_FP32], k[mc.MC_FP64])
+    assert abs(d) <= bound, (k, d, se)
 
 
 @pytest.mark.parametrize("T", [0.2, 0.4])

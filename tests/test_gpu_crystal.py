@@ -57,25 +57,29 @@ def test_crystal_fp64_bit_exact(lattice, cells, J2):
 @pytest.mark.parametrize("lattice", [mc.MC_BCC, mc.MC_FCC, mc.MC_HCP])
 def test_crystal_fp32_matches_fp64(lattice):
     """Below T_C (bcc 2.05, fcc and hcp near 3.2 for J = 1): FP32 and FP64
-    ensembles agree on <|m|> and <E> within 4 sigma of the blocking errors."""
-    cells, T, n = (8, 8, 8), (1.4 if lattice == mc.MC_BCC else 2.2), 3000
-    hs = [mc.mc_create_ex(mc.make_desc(cells, K_u=0.02, T=T, seed=s, precision=p, lattice=lattice, ring_capacity=n))
-          for s, p in ((1, mc.MC_FP32), (2, mc.MC_FP64))]
-    try:
-        series = []
-        for h in hs:
-            mc.mc_sweep(h, 500)
-            mc.mc_sweep(h, n, measure=True)
-            smp = mc.mc_samples(h, n)
-            series.append((np.linalg.norm(smp["m"], axis=1), smp["e_parts"].sum(axis=1)))
-        for k in range(2):
-            a, b = series[0][k], series[1][k]
-            err = np.hypot(blocking_error(a), blocking_error(b))
-            assert abs(a.mean() - b.mean()) < max(4 * err, 1e-4), (lattice, k, a.mean(), b.mean(), err)
-        assert series[0][0].mean() > 0.3  # ordered
-    finally:
-        for h in hs:
-            mc.mc_destroy(h)
+    ensembles, six independent runs each, agree on <|m|> and <E> within the
+    3-sigma-equivalent bound (t3) of the spread between runs."""
+    from _stats import diff_within_t3
+    cells, T, n, runs = (8, 8, 8), (1.4 if lattice == mc.MC_BCC else 2.2), 3000, 6
+    means = {}
+    for p in (mc.MC_FP32, mc.MC_FP64):
+        ml, e = [], []
+        for k in range(runs):
+            h = mc.mc_create_ex(mc.make_desc(cells, K_u=0.02, T=T, seed=1 + 2 * k + p, precision=p, lattice=lattice,
+                                             ring_capacity=16))
+            try:
+                mc.mc_sweep(h, 500)
+                mc.mc_sweep(h, n, measure=True)
+                o = mc.mc_measure(h)
+                ml.append(o.ml)
+                e.append(o.e)
+            finally:
+                mc.mc_destroy(h)
+        means[p] = (np.array(ml), np.array(e))
+    for k in range(2):
+        d, se, bound = diff_within_t3(means[mc.MC_FP32][k], means[mc.MC_FP64][k])
+        assert abs(d) <= max(bound, 1e-5), (lattice, k, d, se)
+    assert means[mc.MC_FP32][0].mean() > 0.3  # ordered
 
 
 def test_crystal_refused_where_simple_cubic_only():
@@ -148,7 +152,8 @@ def test_crystal_constrained_fp32_torque_matches_fp64():
             finally:
                 mc.mc_destroy(h)
         means[prec] = np.array(vals)
+    from _stats import diff_within_t3
     a, b = means[mc.MC_FP32], means[mc.MC_FP64]
-    sig = np.hypot(a.std(ddof=1), b.std(ddof=1)) / np.sqrt(len(a))
-    assert abs(a.mean() - b.mean()) <= 4 * sig + 1e-5, (a.mean(), b.mean(), sig)
+    d, se, bound = diff_within_t3(a, b)
+    assert abs(d) <= bound + 1e-6, (a.mean(), b.mean(), se)
     assert -Ku < b.mean() < -0.5 * Ku, b.mean()

@@ -5,7 +5,7 @@ Both key the same Philox draws to the same sites and evaluate the trial
 point, Eq. 2 and Eq. 1 with the same operations in the same order, so a
 wavefront sweep must give the spins, cone angle, accepted count and sample
 of a red and a black row pass bit for bit, on any band / slab split of the
-lattice (bands of 16 rows, slabs down to one plane, halo rows and planes
+lattice (bands of at most 15 rows, slabs down to one plane, halo rows and planes
 that wrap onto the band itself).  The per-sweep samples then agree too.  A
 host-set fault makes a staged copy's wait run out: the launch ends with
 MC_ERR_TIMEOUT instead of hanging.
@@ -44,7 +44,8 @@ def _run(dims, kw, spins, n_sweeps, path, calls=1):
         mc.mc_destroy(h)
 
 
-WAVE_DIMS = [(128, 16, 16), (128, 32, 8), (128, 48, 6), (128, 16, 2), (128, 64, 10), (128, 128, 128)]
+WAVE_DIMS = [(128, 16, 16), (128, 32, 8), (128, 48, 6), (128, 16, 2), (128, 64, 10), (128, 18, 4), (128, 30, 6),
+             (128, 128, 128)]
 
 
 @pytest.mark.parametrize("dims", WAVE_DIMS)
@@ -55,7 +56,7 @@ def test_wavefront_sweeps_equal_row_passes_bit_for_bit(dims):
     spins = workloads.random_spins(N, 11)
     kw = dict(K_u=0.05, K_c=0.02, H=(0.02, 0.0, 0.05), T=0.9, seed=5)
     for n in (2, 3, 16):
-        w = _run(dims, kw, spins, n, mc.MC_PATH_AUTO)
+        w = _run(dims, kw, spins, n, mc.MC_PATH_WAVE)
         r = _run(dims, kw, spins, n, mc.MC_PATH_ROW)
         moved = np.any(w[0] != spins, axis=1).mean()
         assert moved > 0.5, moved
@@ -66,12 +67,13 @@ def test_wavefront_sweeps_equal_row_passes_bit_for_bit(dims):
 
 
 def test_wavefront_lattice_in_a_group_equals_row_passes():
-    """The batched temperature sweep (32 lattices; the eight 128^3 ones take
-    the wavefront launch, the others the row passes beside it) equals the
-    same group with every lattice on row passes, lattice by lattice."""
+    """The batched temperature sweep with the wavefront path asked for (32
+    lattices; the eight 128^3 ones take the wavefront launch, the others the
+    row passes beside it) equals the same group on row passes, lattice by
+    lattice."""
     specs = workloads.batched_mt_32()
     res = {}
-    for path in (mc.MC_PATH_AUTO, mc.MC_PATH_ROW):
+    for path in (mc.MC_PATH_WAVE, mc.MC_PATH_ROW):
         hs = [mc.mc_create_ex(mc.make_desc(s.dims, K_u=s.Ku, T=s.T, seed=s.seed, kernel_path=path,
                                            ring_capacity=8, sample_torque=0)) for s in specs]
         g = mc.mc_group_create(hs)
@@ -85,7 +87,7 @@ def test_wavefront_lattice_in_a_group_equals_row_passes():
             mc.mc_group_destroy(g)
             for h in hs:
                 mc.mc_destroy(h)
-    for i, (a, b) in enumerate(zip(res[mc.MC_PATH_AUTO], res[mc.MC_PATH_ROW])):
+    for i, (a, b) in enumerate(zip(res[mc.MC_PATH_WAVE], res[mc.MC_PATH_ROW])):
         assert np.array_equal(a[0], b[0]), i
         assert a[1] == b[1] and a[2] == b[2], i
 
@@ -96,7 +98,7 @@ def test_wavefront_chain_continues_across_calls():
     dims = (128, 32, 12)
     spins = workloads.random_spins(128 * 32 * 12, 4)
     kw = dict(K_u=0.01, T=1.2, seed=8)
-    h = mc.mc_create_ex(mc.make_desc(dims, ring_capacity=16, **kw))
+    h = mc.mc_create_ex(mc.make_desc(dims, ring_capacity=16, kernel_path=mc.MC_PATH_WAVE, **kw))
     try:
         mc.mc_set_spins(h, spins)
         for n in (1, 2, 3):
@@ -112,7 +114,7 @@ _TIMEOUT_CHILD = r"""
 import sys
 sys.path.insert(0, {root!r})
 import paper_2103_03517_gb300 as mc
-h = mc.mc_create_ex(mc.make_desc((128, 16, 4), T=1.0, seed=1))
+h = mc.mc_create_ex(mc.make_desc((128, 16, 4), T=1.0, seed=1, kernel_path=mc.MC_PATH_WAVE))
 mc.mc_sweep(h, 2)
 try:
     mc.mc_sync(h)
