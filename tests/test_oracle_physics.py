@@ -8,6 +8,7 @@ constrained pair move.  A dropped term, a wrong sign or a transposed operand
 in the oracle moves one of these by many standard errors.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -159,6 +160,41 @@ def test_binder_cumulant_brackets_curie_point():
     assert above[0] < above[1], above
 
 
+@pytest.mark.slow
+def test_binder_cumulant_crossing_locates_the_curie_point():
+    """U_L(T) = 1 - <m^4>/(3 <m^2>^2) at T = 1.42, 1.445 and 1.47 for L = 8, 12
+    and 16; the crossing of L = 8 and 16, and of L = 12 and 16 (the root of
+    a quadratic through the three differences U_16 - U_L) lies within 0.02
+    of the classical simple-cubic Heisenberg T_C = 1.443 J/k_B (the paper's
+    theta_C = 0.723 gives 2 theta_C = 1.446, Sec. 3).  The moments pool
+    independent chains (8 per L and T for L = 12 and 16, 4 for L = 8) run in
+    parallel processes.  A straight line through two temperatures would put
+    the crossings about 0.01 low: U_L curves over this range."""
+    import multiprocessing as mp
+
+    import _binder
+
+    temps = (1.42, 1.445, 1.47)
+    jobs = [(L, T, 1000 * L + 10 * k + i, 1000, 16000)
+            for L, k_n in ((8, 4), (12, 8), (16, 8)) for i, T in enumerate(temps) for k in range(k_n)]
+    jobs.sort(key=lambda j: -j[0])
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        res = pool.map(_binder.binder_sums, jobs, chunksize=1)
+    acc = {}
+    for L, T, m2, m4, n in res:
+        a = acc.setdefault((L, T), [0.0, 0.0, 0.0])
+        a[0] += m2
+        a[1] += m4
+        a[2] += n
+    U = {k: 1 - (v[1] / v[2]) / (3 * (v[0] / v[2]) ** 2) for k, v in acc.items()}
+    for La in (8, 12):
+        d = np.array([U[(16, T)] - U[(La, T)] for T in temps])
+        assert d[0] > 0 > d[2], (La, d)  # the larger lattice orders more below T_C, less above
+        roots = [r.real for r in np.roots(np.polyfit(temps, d, 2)) if abs(r.imag) < 1e-12 and temps[0] <= r.real <= temps[2]]
+        assert len(roots) == 1, (La, d, roots)
+        assert abs(roots[0] - 1.443) < 0.02, (La, roots[0], U)
+
+
 # ------------------------------------------------- parallel vs serial (Sec. 2)
 def test_checkerboard_matches_serial_random_order():
     """The paper checks the parallel chain against the serial random-order
@@ -175,7 +211,7 @@ def test_checkerboard_matches_serial_random_order():
         res.append(((ml.mean(), blocking_error(ml)), (e.mean(), blocking_error(e))))
     for k in range(2):
         (a, ea), (b, eb) = res[0][k], res[1][k]
-        assert abs(a - b) < 4 * math.hypot(ea, eb), (k, a, b, ea, eb)
+        assert abs(a - b) < 3 * math.hypot(ea, eb), (k, a, b, ea, eb)
 
 
 def test_ordered_and_random_starts_agree():
@@ -189,7 +225,7 @@ def test_ordered_and_random_starts_agree():
             o.sweep(10000, measure=True)
             ml = np.linalg.norm(o.samples()[:, 3:6], axis=1)
             vals.append((ml.mean(), blocking_error(ml)))
-        assert abs(vals[0][0] - vals[1][0]) < 4 * math.hypot(vals[0][1], vals[1][1]), (T, vals)
+        assert abs(vals[0][0] - vals[1][0]) < 3 * math.hypot(vals[0][1], vals[1][1]), (T, vals)
 
 
 def test_cone_angle_adaptation_targets_half():
@@ -302,7 +338,7 @@ def test_parallel_constrained_matches_serial_asselin():
         tau = o.samples()[:, 10:13] @ np.array([0.0, 1.0, 0.0])
         res.append((tau.mean(), blocking_error(tau)))
     (a, ea), (b, eb) = res
-    assert abs(a - b) < 4 * math.hypot(ea, eb), res
+    assert abs(a - b) < 3 * math.hypot(ea, eb), res
 
 
 # ------------------------------------------------------ Eq. 4 anisotropy scaling

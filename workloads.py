@@ -41,6 +41,35 @@ class LatticeSpec:
 # The five workloads (reduced units J = 1, k_B = 1).
 # --------------------------------------------------------------------------
 
+# --------------------------------------------------------------------------
+# FP32-against-oracle precision check of the batched m(T) workload: the 32
+# lattices of batched_mt_32 plus two extra 16^3 points near T_C, each run from
+# the all +z state for n_eq unmeasured and n_meas measured sweeps (cone
+# adaptation in every sweep), over many independent seeds per side.  The
+# oracle's seeds and the GPU's seeds are disjoint ranges of the 64-bit key.
+# --------------------------------------------------------------------------
+
+PRECISION_SWEEPS = {16: (200, 500), 32: (200, 500), 64: (200, 500), 128: (100, 200)}
+PRECISION_ORACLE_SEED0 = 10 ** 6
+PRECISION_GPU_SEED0 = 1 << 40
+
+
+def precision_cases() -> dict:
+    """name -> LatticeSpec of the precision check: 'mT_i' for lattice i of
+    batched_mt_32, and 'extra_16c_T1.40', 'extra_16c_T1.50' (16^3 at the
+    temperatures either side of lattice 28's T = 1.45).  spec.seed is the
+    case's index in the seed ranges (precision_seed)."""
+    out = {f"mT_{i}": s for i, s in enumerate(batched_mt_32())}
+    out["extra_16c_T1.40"] = LatticeSpec(dims=(16, 16, 16), Ku=0.01, T=1.40, seed=40)
+    out["extra_16c_T1.50"] = LatticeSpec(dims=(16, 16, 16), Ku=0.01, T=1.50, seed=41)
+    return out
+
+
+def precision_seed(side_seed0: int, spec: LatticeSpec, k: int) -> int:
+    """Seed of run k of a precision case on one side (k < 10^5)."""
+    return side_seed0 + 100000 * int(spec.seed) + int(k)
+
+
 def point_16c() -> LatticeSpec:
     """16^3 periodic, FP64, K_u = 0.01 along z, T = 0.5, seed 0, all +z;
     1000 equilibration + 1000 measurement sweeps."""
