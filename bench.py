@@ -10,7 +10,7 @@ colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--side all|none|fp64|constrained|anisotropy|cubes|general|stiffness|films|precision|
-                               serving|torque|wall]
+                               serving|torque|wall|wave]
                        [--no-cpu]
 Under torchrun (N > 1) the ranks split the batch: each lattice runs on one
 rank, shares balanced by spins (strong scaling, no collective on the data
@@ -358,7 +358,7 @@ def gpu_arm(args, cfg):
         # around every launch over the same kind of sweeps, right after the
         # timed region (events between launches would change the timed region)
         n_time = max(8, min(args.steps, 200)) // 2 * 2
-        kern_ms, kern_n = mc.mc_group_time_kernels(g, n_time, measure=True)
+        kern_ms, kern_n = mc.mc_group_time_kernels(g, n_time, measure=True, constrained=False)
         wave_spins = sum(sp.N for sp in specs if sp.dims[0] == 128)
         if kern_n[0]:
             kernel_name, avg_ms, bytes_per_launch = "wave_sweep_kernel<float>", kern_ms[0], wave_spins * BYTES_PER_UPDATE
@@ -450,11 +450,46 @@ def secondary(mc, torch, stream, dev, side="all", tune=True):
         out.update(films(mc, torch, stream, dev))
     if side in ("all", "precision"):
         out.update(precision(mc, torch, stream, dev))
+    if side in ("all", "wave"):
+        out.update(wavefront(mc, torch, stream, dev))
     if side in ("all", "torque"):
         out.update(torque_study(stream, dev))
     if side in ("all", "wall"):
         out.update(wall_study(stream, dev))
     return out
+
+
+def wavefront(mc, torch, stream, dev, sweeps=200):
+    """The eight 128^3 lattices of the batched workload on the wavefront path
+    (kernel_path MC_PATH_WAVE: one launch per sweep, each spin read and
+    written once) and on the row passes, measured sweeps: time per sweep
+    (CUDA events around the replayed graphs) and the wavefront launch timed
+    alone, against 24 B per update and the measured HBM peak."""
+    peak, _ = measured_peak()
+    specs = [sp for sp in workloads.batched_mt_32() if sp.dims[0] == 128]
+    n = sum(sp.N for sp in specs)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, path in (("wavefront", mc.MC_PATH_WAVE), ("row", mc.MC_PATH_ROW)):
+        hs = [mc.mc_create_ex(mc.make_desc(sp.dims, K_u=sp.Ku, T=sp.T, seed=sp.seed, kernel_path=path,
+                                           ring_capacity=16, sample_torque=0, stream=stream.cuda_stream,
+                                           device=dev)) for sp in specs]
+        g = mc.mc_group_create(hs)
+        mc.mc_group_sweep(g, 10, measure=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        mc.mc_group_sweep(g, sweeps, measure=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / sweeps
+        kms, kn = mc.mc_group_time_kernels(g, 20, measure=True)
+        res[name] = {"us_per_sweep": round(ms * 1e3, 2), "sweep_frac": round(n * 24 / (ms * 1e-3) / 1e9 / peak, 4),
+                     "launch_ms": round(kms[0] if kn[0] else kms[1], 5)}
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+    return {"wavefront": {"workload": "the eight 128^3 lattices of the batch (16.8M spins), measured sweeps, FP32",
+                          **res}}
 
 
 def torque_study(stream, dev):
@@ -536,14 +571,25 @@ def constrained(mc, torch, stream, dev, tune=True):
     b.record(stream)
     torch.cuda.synchronize()
     nc = sum(r[0].N for r in runs)
+    # the pair pass against the HBM roofline: 24 B per pair-half update (each
+    # spin of the pass's colour read and written once), one launch per colour
+    kms, kn = mc.mc_group_time_kernels(g, 8, measure=True, constrained=True)
+    peak, _ = measured_peak()
+    pair_gbs = (nc // 2) * BYTES_PER_UPDATE / (kms[2] * 1e-3) / 1e9 if kn[2] else None
+    out["constrained_roofline"] = {
+        "kernel": "pair_pass_kernel<float> (site order)", "launch_avg_ms": kms[2], "launches": kn[2],
+        "algorithmic_bytes_per_launch": (nc // 2) * BYTES_PER_UPDATE, "achieved": pair_gbs, "peak": peak,
+        "unit": "GB/s", "frac": pair_gbs / peak if pair_gbs else None,
+        "sweep_frac": nc * sweeps / (a.elapsed_time(b) * 1e-3) * BYTES_PER_UPDATE / 1e9 / peak}
     out["constrained"] = {"value": nc * sweeps / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
                           "workload": "80 x 64^3 constrained runs (theta_c 0..90, phi_c 0/45, 4 T), FP32, "
                                       "pair halves counted as updates",
                           "autotuned": None if tuned is None else {
                               "field_tiles_per_step": [4, 8, 2][tuned["field"]],
-                              "pair_tiles_per_step": [4, 8, 2][tuned["pair"]],
+                              "pair_shape": ["4 tiles per step", "8 tiles per step", "2 tiles per step",
+                                             "4 tiles per step, one more block per SM"][tuned["pair"]],
                               "field_ms": [round(x, 4) for x in tuned["field_ms"][:3]],
-                              "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:3]]}}
+                              "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:4]]}}
     mc.mc_group_destroy(g)
     for h in hs:
         mc.mc_destroy(h)
@@ -908,7 +954,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
                     choices=["all", "none", "fp64", "constrained", "anisotropy", "cubes", "general", "stiffness", "films",
-                             "precision", "serving", "torque", "wall"],
+                             "precision", "serving", "torque", "wall", "wave"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -322,10 +322,12 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
 
 /* The same, by kind: avg_ms[0] / launches[0] for the wavefront launches
  * (one sweep of the lattices that take them), [1] for the colour passes of
- * the row and general kernels, [2] for constrained pair passes (0 here).
- * A kind with no launch reads 0 ms.  Measurement support around the
- * paper's method; the paper has no counterpart.  Synchronises. */
-MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, double avg_ms[3],
+ * the row and general kernels, [2] for the pair passes of Table A2.  With
+ * constrained != 0 the sweeps are constrained sweeps about each lattice's
+ * last constraint direction (MC_ERR_STATE before any constrained sweep of
+ * the group).  A kind with no launch reads 0 ms.  Measurement support
+ * around the paper's method; the paper has no counterpart.  Synchronises. */
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[3],
                                  int launches[3]);
 
 /* Ensemble averages of every lattice of the group (Sec. 3, Eq. 6), as

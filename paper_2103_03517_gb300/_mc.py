@@ -123,7 +123,7 @@ _SIGS = {
     "mc_group_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mc_group_constrained_sweep": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double), C.c_int, C.c_int]),
     "mc_group_time_passes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
-    "mc_group_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
+    "mc_group_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _P(C.c_double), _P(C.c_int)]),
     "mc_group_measure": (C.c_int, [C.c_void_p, _P(mc_observables), C.c_int]),
     "mc_group_sync": (C.c_int, [C.c_void_p]),
     "mc_group_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
@@ -393,12 +393,12 @@ def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):
     return avg.value, n.value
 
 
-def mc_group_time_kernels(g, n_sweeps: int, measure: bool = False):
+def mc_group_time_kernels(g, n_sweeps: int, measure: bool = False, constrained: bool = False):
     """Per launch kind (wavefront sweeps, colour passes, pair passes): the
     mean launch duration in ms and the number of launches timed."""
     ms = (C.c_double * 3)()
     n = (C.c_int * 3)()
-    _check(lib().mc_group_time_kernels(g, int(n_sweeps), int(bool(measure)), ms, n))
+    _check(lib().mc_group_time_kernels(g, int(n_sweeps), int(bool(measure)), int(bool(constrained)), ms, n))
     return list(ms), list(n)
 
 

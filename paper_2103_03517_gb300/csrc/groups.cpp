@@ -194,10 +194,12 @@ MC_API int mc_group_constrained_sweep(mc_group_handle g, const double* theta_c_d
 
 // n_sweeps sweeps of the group with events around every launch that moves
 // spins; per kind (TimedLaunch) the summed milliseconds and the count.
-static int time_kinds(mc_group* g, int n_sweeps, int measure, double ms[kTimedKinds], int count[kTimedKinds]) {
+static int time_kinds(mc_group* g, int n_sweeps, int measure, bool constrained, double ms[kTimedKinds],
+                      int count[kTimedKinds]) {
     cudaSetDevice(g->device);
     std::vector<TimedLaunch> ev;
-    int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n_sweeps, measure ? 1 : 0, false, g->stream, &ev);
+    int rc = enqueue_sweeps(kernel_set(g->precision), g->ls, g->cone, n_sweeps, measure ? 1 : 0, constrained, g->stream,
+                            &ev);
     cudaError_t e = cudaStreamSynchronize(g->stream);
     for (int k = 0; k < kTimedKinds; ++k) {
         ms[k] = 0.0;
@@ -220,7 +222,7 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
     if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
     double ms[kTimedKinds];
     int count[kTimedKinds];
-    const int rc = time_kinds(g, n_sweeps, measure, ms, count);
+    const int rc = time_kinds(g, n_sweeps, measure, false, ms, count);
     if (rc) return rc;
     double total = 0.0;
     int n = 0;
@@ -233,11 +235,14 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
     return MC_OK;
 }
 
-MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, double avg_ms[3], int launches[3]) {
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[3],
+                                 int launches[3]) {
     if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
+    for (mc_handle h : g->lats)
+        if (constrained && !h->d_aos) return fail(MC_ERR_STATE, "no constrained sweep has set the constraint yet");
     double ms[kTimedKinds];
     int count[kTimedKinds];
-    const int rc = time_kinds(g, n_sweeps, measure, ms, count);
+    const int rc = time_kinds(g, n_sweeps, measure, constrained != 0, ms, count);
     if (rc) return rc;
     for (int k = 0; k < kTimedKinds; ++k) {
         launches[k] = count[k];

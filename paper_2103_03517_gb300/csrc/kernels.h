@@ -11,9 +11,10 @@ namespace mcgb {
 // candidate list (0 = the default, measured best on the batched workloads).
 //   row:   FP32 row kernel, minimum resident blocks per SM (registers per
 //          thread): all-periodic {3, 2}, boundaries and films {2, 3};
-//   pair:  pair pass, consecutive tiles per grid-stride step {4, 8, 2};
+//   pair:  pair pass, consecutive tiles per grid-stride step {4, 8, 2}, and
+//          4 with one more resident block per SM;
 //   field: neighbour-field kernel, the same {4, 8, 2}.
-constexpr int kRowShapes = 2, kPairShapes = 3, kFieldShapes = 3;
+constexpr int kRowShapes = 2, kPairShapes = 4, kFieldShapes = 3;
 struct LaunchShape {
     int row = 0, pair = 0, field = 0;
 };

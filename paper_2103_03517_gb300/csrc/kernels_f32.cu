@@ -89,21 +89,24 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
     else row_sample_g<0>(g, ntiles, s);
 }
 
-template <bool LEADER, int C>
+template <bool LEADER, int C, int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR>
 void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int sub, cudaStream_t s) {
-    constexpr int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
     static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER>);
     pair_pass_kernel<R, B, C, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour, sub);
 }
 
-// launch shapes: tiles per grid-stride step {default, 8, 2}
+// launch shapes: tiles per grid-stride step {default, 8, 2}, and the
+// default step with one more resident block per SM (fewer registers, some
+// spilled; more warps to cover the random gathers)
 template <bool LEADER>
 void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int shape, int sub,
                  cudaStream_t s) {
     constexpr int C0 = LEADER ? kPairChunkLead : kPairChunk;
+    constexpr int B0 = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
     if (shape == 1) pair_pass_t<LEADER, 8>(g, ntiles, cone, colour, sub, s);
     else if (shape == 2) pair_pass_t<LEADER, 2>(g, ntiles, cone, colour, sub, s);
+    else if (shape == 3) pair_pass_t<LEADER, C0, B0 + 1>(g, ntiles, cone, colour, sub, s);
     else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, sub, s);
 }
 
