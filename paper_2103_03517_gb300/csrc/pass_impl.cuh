@@ -417,11 +417,10 @@ __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
 }
 
 // ------------------------------------------------------------------------
-// End of a sweep (Table A1 / A2, after the black pass): cone adaptation,
-// the sample of Sec. 3 (if measuring), the sweep counter.  Runs on one
-// thread of the last block to finish.
+// End of a sweep (Table A1 / A2, after the black pass): the cone adaptation
+// and the carried M_L on one thread; returns the sweep's accepted count.
 // ------------------------------------------------------------------------
-__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure, bool torque) {
+__device__ inline long long close_counts(const LatParams& p, LatState& st, int measure) {
     const long long acc = (long long)atomicExch(&st.acc, 0ull);
     st.last_acc = acc;
     if (!measure || p.adapt_in_measure) {
@@ -432,55 +431,114 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
     st.ml_lo += st.dml_lo;
     st.dml_hi = 0;
     st.dml_lo = 0;
-    if (measure) {
-        double v[kNumSums];
-        for (int i = 0; i < kNumSums; ++i) {
-            // two's complement fixed point: reinterpret the 64-bit word as signed
-            const long long raw =
-                (long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[i]), 0ull);
-            v[i] = double(raw) / (p.precision == 1 ? kFixScale : kFixScaleF32);
-        }
-        const double N = double(p.N);
-        const double m[3] = {v[kSumMx] / N, v[kSumMy] / N, v[kSumMz] / N};
-        const double ml2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-        const double ml = sqrt(ml2);
-        const double e_ex = -p.J * v[kSumEx] / N, e_u = -p.Ku * v[kSumU] / N, e_c = p.Kc * v[kSumC] / N;
-        const double e_z = -(p.H[0] * v[kSumMx] + p.H[1] * v[kSumMy] + p.H[2] * v[kSumMz]) / N;
-        const double e = e_ex + e_u + e_c + e_z;
-        double tq[3] = {0.0, 0.0, 0.0};
-        if (torque) {
-            tq[0] = (2.0 * p.Ku * v[kSumTux] - 2.0 * p.Kc * v[kSumTcx] + (v[kSumMy] * p.H[2] - v[kSumMz] * p.H[1])) / N;
-            tq[1] = (2.0 * p.Ku * v[kSumTuy] - 2.0 * p.Kc * v[kSumTcy] + (v[kSumMz] * p.H[0] - v[kSumMx] * p.H[2])) / N;
-            tq[2] = (2.0 * p.Ku * v[kSumTuz] - 2.0 * p.Kc * v[kSumTcz] + (v[kSumMx] * p.H[1] - v[kSumMy] * p.H[0])) / N;
-        }
-        double* mo = st.moments;
-        mo[kMomN] += 1.0;
-        for (int a = 0; a < 3; ++a) {
-            mo[kMomM + a] += m[a];
-            mo[kMomM2 + a] += m[a] * m[a];
-            mo[kMomMabs + a] += fabs(m[a]);
-            mo[kMomTq + a] += tq[a];
-            mo[kMomTq2 + a] += tq[a] * tq[a];
-        }
-        mo[kMomMl] += ml;
-        mo[kMomMl2] += ml2;
-        mo[kMomMl4] += ml2 * ml2;
-        mo[kMomE] += e;
-        mo[kMomE2] += e * e;
-        mo[kMomParts + 0] += e_ex;
-        mo[kMomParts + 1] += e_u;
-        mo[kMomParts + 2] += e_c;
-        mo[kMomParts + 3] += e_z;
-        if (p.ring) {
-            double* r = p.ring + (st.ring_count % p.ring_cap) * kRingWords;
-            r[0] = double(st.sweep); r[1] = double(st.theta); r[2] = double(acc);
-            r[3] = m[0]; r[4] = m[1]; r[5] = m[2];
-            r[6] = e_ex; r[7] = e_u; r[8] = e_c; r[9] = e_z;
-            r[10] = tq[0]; r[11] = tq[1]; r[12] = tq[2]; r[13] = 0.0;
-        }
-        st.ring_count += 1;
-    }
+    return acc;
+}
+
+// End of an unmeasured sweep, on one thread.
+__device__ inline void finalize_sweep_unmeasured(const LatParams& p, LatState& st) {
+    close_counts(p, st, 0);
     st.sweep += 1;
+}
+
+// End of a sweep on all 32 lanes of the warp that completed the lattice's
+// pass: lane 0 closes the counts; if measuring, the sample of Sec. 3 is
+// spread over the lanes.  Lane i takes fixed-point sum i; lanes 0-9 divide
+// one numerator each by N (m, the four energy parts, the torque); lane k
+// adds moment word k and writes ring word k.  Every quantity is the same
+// expression of the same sums as in a serial evaluation.  The sample then costs one
+// FP64 division and one memory round trip per lane instead of a serial
+// chain on one thread, which sat at the end of every measured pass.
+__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure, bool torque, int lane) {
+    constexpr unsigned kAll = 0xffffffffu;
+    long long acc = 0;
+    int theta = 0;
+    uint32_t sweep = 0;
+    long long slot = 0;
+    if (lane == 0) {
+        acc = close_counts(p, st, measure);
+        theta = st.theta;
+        sweep = st.sweep;
+        slot = p.ring_cap > 0 ? st.ring_count % p.ring_cap : 0;
+    }
+    if (measure) {
+        acc = __shfl_sync(kAll, acc, 0);
+        theta = __shfl_sync(kAll, theta, 0);
+        sweep = __shfl_sync(kAll, sweep, 0);
+        slot = __shfl_sync(kAll, slot, 0);
+        // the scales are powers of two, so the products are the quotients
+        const double inv_scale = p.precision == 1 ? 1.0 / kFixScale : 1.0 / kFixScaleF32;
+        double mine = 0.0;
+        if (lane < kNumSums)
+            mine = double((long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[lane]), 0ull)) *
+                   inv_scale;
+        // the sums each numerator needs, fetched by per-lane shuffles: lanes
+        // 0-2 m_a; 3-5 the exchange, uniaxial and cubic sums; 6 the three m
+        // components (Zeeman); 7 + a the torque sums of axis a and the two
+        // other m components (their field cross product)
+        const int a = lane - 7;  // torque axis of lanes 7-9
+        const int a1 = a == 0 ? 1 : (a == 1 ? 2 : 0), a2 = a == 0 ? 2 : (a == 1 ? 0 : 1);
+        const int i1 = lane < 3 ? kSumMx + lane
+                       : lane == 3 ? kSumEx
+                       : lane == 4 ? kSumU
+                       : lane == 5 ? kSumC
+                       : lane == 6 ? kSumMx
+                       : lane < 10 ? kSumTux + a
+                                   : 0;
+        const int i2 = lane == 6 ? kSumMy : (lane >= 7 && lane < 10 ? kSumTcx + a : 0);
+        const int i3 = lane == 6 ? kSumMz : (lane >= 7 && lane < 10 ? kSumMx + a1 : 0);
+        const int i4 = lane >= 7 && lane < 10 ? kSumMx + a2 : 0;
+        const double s1 = __shfl_sync(kAll, mine, i1), s2 = __shfl_sync(kAll, mine, i2);
+        const double s3 = __shfl_sync(kAll, mine, i3), s4 = __shfl_sync(kAll, mine, i4);
+        double num = 0.0;
+        if (lane < 3) num = s1;
+        else if (lane == 3) num = -p.J * s1;
+        else if (lane == 4) num = -p.Ku * s1;
+        else if (lane == 5) num = p.Kc * s1;
+        else if (lane == 6) num = -(p.H[0] * s1 + p.H[1] * s2 + p.H[2] * s3);
+        else if (lane < 10 && torque) num = 2.0 * p.Ku * s1 - 2.0 * p.Kc * s2 + (s3 * p.H[a2] - s4 * p.H[a1]);
+        const double quo = num / double(p.N);
+        // lanes 0-2: m; 3-6: the energy parts E_ex, E_u, E_c, E_Z; 7-9: tau
+        const double m0 = __shfl_sync(kAll, quo, 0), m1 = __shfl_sync(kAll, quo, 1), m2 = __shfl_sync(kAll, quo, 2);
+        const double e_ex = __shfl_sync(kAll, quo, 3), e_u = __shfl_sync(kAll, quo, 4);
+        const double e_c = __shfl_sync(kAll, quo, 5), e_z = __shfl_sync(kAll, quo, 6);
+        const double ml2 = m0 * m0 + m1 * m1 + m2 * m2;
+        const double ml = sqrt(ml2);
+        const double e = e_ex + e_u + e_c + e_z;
+        // moment word `lane`, in the order of the enum: N, m_a, m_a^2, |m_a|,
+        // |m|, |m|^2, |m|^4, E, E^2, the four parts, tau_a, tau_a^2; x is the
+        // quotient the word is built from (m_a, a part or tau_a)
+        const int src = lane < kMomM2     ? lane - kMomM
+                        : lane < kMomMabs ? lane - kMomM2
+                        : lane < kMomMl   ? lane - kMomMabs
+                        : lane < kMomParts ? 0
+                        : lane < kMomTq   ? 3 + lane - kMomParts
+                        : lane < kMomTq2  ? 7 + lane - kMomTq
+                        : lane < kMomTq2 + 3 ? 7 + lane - kMomTq2
+                                          : 0;
+        const double x = __shfl_sync(kAll, quo, src < 0 ? 0 : src);
+        const double inc = lane == kMomN      ? 1.0
+                           : lane < kMomM2    ? x
+                           : lane < kMomMabs  ? x * x
+                           : lane < kMomMl    ? fabs(x)
+                           : lane == kMomMl   ? ml
+                           : lane == kMomMl2  ? ml2
+                           : lane == kMomMl4  ? ml2 * ml2
+                           : lane == kMomE    ? e
+                           : lane == kMomE2   ? e * e
+                           : lane < kMomTq    ? x
+                           : lane < kMomTq2   ? x
+                                              : x * x;
+        if (lane < kMomTq2 + 3) st.moments[lane] += inc;
+        // ring word `lane`: sweep, theta, accepted, m, the four parts, tau, 0
+        const double y = __shfl_sync(kAll, quo, lane >= 3 && lane < 13 ? lane - 3 : 0);
+        if (p.ring && lane < kRingWords) {
+            const double w = lane == 0 ? double(sweep) : lane == 1 ? double(theta) : lane == 2 ? double(acc)
+                             : lane < 13 ? y : 0.0;
+            p.ring[slot * kRingWords + lane] = w;
+        }
+        if (lane == 0) st.ring_count += 1;
+    }
+    if (lane == 0) st.sweep += 1;
 }
 
 // ------------------------------------------------------------------------
@@ -520,8 +578,8 @@ __device__ __forceinline__ int lattice_of_tile(const GroupArgs& g, uint32_t tile
 // Publish one warp's run of `tiles` tiles of lattice L: accepted moves and
 // fixed-point sums (lane i holds sum i).  In a pass that closes the sweep
 // (closes != 0) the warp then counts its tiles, and the warp that completes
-// the lattice's pass runs `last` on lane 0 after a fence that orders every
-// warp's counts before it.  Any other pass stops after the counts: they are
+// the lattice's pass runs `last` on all its lanes after a fence that orders
+// every warp's counts before it.  Any other pass stops after the counts: they are
 // read by a later launch, which the kernel boundary orders, so its warps
 // neither fence nor count.
 template <typename F>
@@ -534,13 +592,18 @@ __device__ __forceinline__ void publish(LatState& st, int lane, unsigned nacc, b
     if (!closes) return;
     __threadfence();
     __syncwarp();
+    unsigned closing = 0;
     if (lane == 0) {
         const unsigned prev = atomicAdd(&st.done[slot], tiles);
         if (prev + tiles == ntiles_lattice) {
             __threadfence();
             st.done[slot] = 0;
-            last();
+            closing = 1;
         }
+    }
+    if (__shfl_sync(0xffffffffu, closing, 0)) {
+        __threadfence();  // every lane reads what the other warps published
+        last();
     }
     __syncwarp();
 }
@@ -760,7 +823,7 @@ __global__ void __launch_bounds__(kBlock, MINB) colour_pass_kernel(GroupArgs g, 
             if (measure) fix += warp_tile_fix<R, NS>(sums, lane);
         }
         publish(L->st, lane, nacc, measure != 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {
-            finalize_sweep(p, L->st, measure, p.sample_torque != 0);
+            finalize_sweep(p, L->st, measure, p.sample_torque != 0, lane);
         });
         ++l;
     }
@@ -849,7 +912,7 @@ __global__ void sweep_end_kernel(GroupArgs g) {
     const int l = int(blockIdx.x * blockDim.x + threadIdx.x);
     if (l >= g.n) return;
     LatDev* L = g.lats[l];
-    finalize_sweep(L->p, L->st, 0, true);
+    finalize_sweep_unmeasured(L->p, L->st);
 }
 
 // Zero M_L and its carried change before mlong_kernel sums M_L afresh (one
@@ -1276,7 +1339,7 @@ __global__ void __launch_bounds__(kBlock) measure_kernel(GroupArgs g, uint32_t n
             }
             fix += warp_tile_fix(sums, lane);
         }
-        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, true, [&] { finalize_sweep(p, L->st, 1, true); });
+        publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, true, [&] { finalize_sweep(p, L->st, 1, true, lane); });
         ++l;
     }
 }

@@ -214,11 +214,11 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         }
         if constexpr (MOVE != 0) {
             publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {
-                finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0);
+                finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0, lane);
             });
         } else {
             publish(L->st, lane, 0, true, fix, 3, run, p.nblocks_site, true,
-                    [&] { finalize_sweep(p, L->st, 1, true); });
+                    [&] { finalize_sweep(p, L->st, 1, true, lane); });
         }
         ++l;
     }

@@ -350,13 +350,29 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
         }
         __threadfence();
         __syncthreads();
-        if (tid == 0) {
+        if (MEASURE == 0 && tid == 0) {
             const unsigned prev = atomicAdd(&L->st.done[1], 1u);
             if (prev + 1 == a.nwu[u.lat]) {
                 __threadfence();
                 L->st.done[1] = 0;
-                finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0);
+                finalize_sweep_unmeasured(p, L->st);
             }
+        }
+        if (MEASURE > 0 && warp == 0) {  // the whole warp closes a measured sweep if this unit completes the lattice
+            unsigned closing = 0;
+            if (lane == 0) {
+                const unsigned prev = atomicAdd(&L->st.done[1], 1u);
+                if (prev + 1 == a.nwu[u.lat]) {
+                    __threadfence();
+                    L->st.done[1] = 0;
+                    closing = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, closing, 0)) {
+                __threadfence();
+                finalize_sweep(p, L->st, 1, p.sample_torque != 0, lane);
+            }
+            __syncwarp();
         }
     }
     // no copy may still be writing this block's shared memory when it exits:

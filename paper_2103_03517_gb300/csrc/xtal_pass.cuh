@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) xtal_pass_kernel(LatDev* L, uint32_t n
         }
     }
     publish(L->st, lane, nacc, false, 0, colour, wc.end - wc.begin, ntiles, finalize != 0,
-            [&] { finalize_sweep(p, L->st, 0, false); });
+            [&] { finalize_sweep(p, L->st, 0, false, lane); });
 }
 
 // Constrained sweeps (Table A2) of a crystal: the neighbour field of every
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) xtal_sample_kernel(LatDev* L, uint32_t
         }
     }
     publish(L->st, lane, 0, true, fix, 3, wc.end - wc.begin, ntiles, true,
-            [&] { finalize_sweep(p, L->st, 1, LEVEL >= 2); });
+            [&] { finalize_sweep(p, L->st, 1, LEVEL >= 2, lane); });
 }
 
 }  // namespace mcgb
