@@ -207,4 +207,42 @@ __device__ __forceinline__ long long pair_tile_sample(const Par<float>& par, con
     return pair_tile_fix<NS>(acc, lane);
 }
 
+// The same parts added into each lane's own accumulators (lf[i] for sum i)
+// instead of reduced per tile: the sums are exact integers, so reducing the
+// accumulators once per run of tiles (pair_parts_flush) gives the totals of
+// pair_tile_sample's per-tile reductions.  A lane's part of a tile is below
+// 2^26 in magnitude (at most 12 at scale 2^22), so an int32 holds the parts
+// of kPartTiles = 16 tiles.
+constexpr int kPartTiles = 16;
+
+template <int MEASURE, int NS>
+__device__ __forceinline__ void pair_tile_parts(const Par<float>& par, const P3& Sf, const P3& h, const P3& e,
+                                                const P3& O, const P3& eo, int lf[NS]) {
+    float2 acc[kNumSums];
+#pragma unroll
+    for (int i = 0; i < kNumSums; ++i) acc[i] = make_float2(0.0f, 0.0f);
+    const bool nu = par.Ku != 0.0f, nc = par.Kc != 0.0f;
+    pair_site_sums<MEASURE>(Sf, e, nu, nc, acc);
+    acc[kSumEx] = pdot(Sf, h);
+    pair_site_sums<MEASURE>(O, eo, nu, nc, acc);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) lf[i] += __float2int_rn((acc[i].x + acc[i].y) * float(kFixScaleF32));
+}
+
+// Warp totals of the accumulated parts: lane i receives sum i.  Each part
+// is split into a signed high and an unsigned low 16-bit half, so that
+// neither warp sum can overflow an int32; the accumulators are cleared.
+template <int NS>
+__device__ __forceinline__ long long pair_parts_flush(int lf[NS], int lane) {
+    long long mine = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int hi = __reduce_add_sync(0xffffffffu, lf[i] >> 16);
+        const int lo = __reduce_add_sync(0xffffffffu, lf[i] & 0xFFFF);
+        if (lane == i) mine = (long long)hi * 65536 + (long long)lo;
+        lf[i] = 0;
+    }
+    return mine;
+}
+
 }  // namespace mcgb

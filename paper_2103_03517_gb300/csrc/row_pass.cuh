@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         const V3<float> e_ax{par.e[0], par.e[1], par.e[2]};
         unsigned nacc = 0;
         long long fix = 0;
+        int lf[NS];  // this lane's fixed-point parts of the sample, kPartTiles tiles at a time
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lf[i] = 0;
+        uint32_t nparts = 0;
         for (; tile < t1; ++tile) {
             const uint32_t q0 = (tile - t0) * 64u;
             P3 S, h, O;
@@ -210,7 +214,16 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                 *reinterpret_cast<float2*>(own + p.stride) = Sf.y;
                 *reinterpret_cast<float2*>(own + 2 * size_t(p.stride)) = Sf.z;
             }
-            if constexpr (MEASURE > 0) fix += pair_tile_sample<MEASURE, NS>(par, Sf, h, e, O, eo, lane);
+            if constexpr (MEASURE > 0) {
+                pair_tile_parts<MEASURE, NS>(par, Sf, h, e, O, eo, lf);
+                if (++nparts == uint32_t(kPartTiles)) {
+                    fix += pair_parts_flush<NS>(lf, lane);
+                    nparts = 0;
+                }
+            }
+        }
+        if constexpr (MEASURE > 0) {
+            if (nparts) fix += pair_parts_flush<NS>(lf, lane);
         }
         if constexpr (MOVE != 0) {
             publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {
