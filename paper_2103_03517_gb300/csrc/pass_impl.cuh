@@ -987,21 +987,6 @@ __device__ __forceinline__ uint32_t permute_inv(uint32_t y, uint32_t n, int b, u
     return v;
 }
 
-// Position of the k-th (0-based) set bit of m, k < popc(m).
-__device__ __forceinline__ int select_bit(uint32_t m, int k) {
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        const int low = __popc(m & ((1u << w) - 1u));
-        if (k >= low) {
-            k -= low;
-            m >>= w;
-            pos += w;
-        }
-    }
-    return pos;
-}
-
 template <typename R>
 __device__ __forceinline__ V3<R> rotate(const R* Rm, V3<R> s) {
     return V3<R>{Rm[0] * s.x + Rm[1] * s.y + Rm[2] * s.z, Rm[3] * s.x + Rm[4] * s.y + Rm[5] * s.z,
@@ -1095,6 +1080,10 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     return 2;
 }
 
+// Slots of a warp's ring of waiting leaders in the site-order pair pass:
+// at most 31 wait between tiles, and a tile adds at most 64.
+constexpr uint32_t kLeaderRing = 128;
+
 // Tiles are taken in grid-stride order, CHUNK consecutive tiles per step: at
 // any moment the warps hold a window of about CHUNK tiles each, a few
 // lattices of the batch, so that the random gathers of partners and their
@@ -1141,49 +1130,43 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     // The 64 sites of each tile in index order; each site whose
                     // position r = pi^-1(q) is even leads the pair (pi(r),
                     // pi(r+1)).  A tile has about 32 leaders, rarely exactly, so
-                    // leaders wait in a queue (lane j < m holds one) until a
-                    // full warp of them is ready; the queue is emptied at the
-                    // end of the run.  The draws are keyed by pair, so the
-                    // grouping changes no result.
-                    uint32_t wq = 0, wr = 0;
-                    int m = 0;
+                    // leaders wait in a per-warp ring in shared memory (a leader
+                    // writes its (q, r) at its rank among the tile's leaders)
+                    // until a full warp of them is ready; the ring is emptied at
+                    // the end of the run.  The draws are keyed by pair, so the
+                    // grouping changes no result.  The ring holds at most 31
+                    // waiting leaders plus one tile's 64.
+                    __shared__ uint2 ring[kBlock / 32][kLeaderRing];
+                    uint2* lq = ring[threadIdx.x >> 5];
+                    const uint32_t below = (1u << lane) - 1u;
+                    uint32_t head = 0, tail = 0;  // leaders queued and taken (warp-uniform)
                     for (uint32_t t = tile; t < t1; ++t) {
                         const uint32_t qa = (t - t0) * 64u + uint32_t(lane), qb = qa + 32u;
                         const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_bits, rk) : 1u;
                         const uint32_t rb = qb < p.Nc ? permute_inv(qb, p.Nc, p.perm_bits, rk) : 1u;
-                        const uint32_t ma = __ballot_sync(0xffffffffu, !(ra & 1u) && ra + 1u < p.Nc);
-                        const uint32_t mb = __ballot_sync(0xffffffffu, !(rb & 1u) && rb + 1u < p.Nc);
-                        const int ca = __popc(ma), total = ca + __popc(mb);
-                        // leader k of this tile (0 <= k < total): its site and position
-                        auto leader = [&](int k, uint32_t& q, uint32_t& r) {
-                            const bool second = k >= ca;
-                            const int src = (k >= 0 && k < total) ? select_bit(second ? mb : ma, second ? k - ca : k) : 0;
-                            const uint32_t r_a = __shfl_sync(0xffffffffu, ra, src);
-                            const uint32_t r_b = __shfl_sync(0xffffffffu, rb, src);
-                            r = second ? r_b : r_a;
-                            q = (t - t0) * 64u + (second ? 32u : 0u) + uint32_t(src);
-                        };
-                        int used = 0;
-                        while (m + (total - used) >= 32) {  // a full warp: the queue, then this tile's next
-                            uint32_t q, r;
-                            leader(used + lane - m, q, r);
-                            if (lane < m) { q = wq; r = wr; }
-                            const uint32_t qj = permute(r + 1u, p.Nc, p.perm_bits, rk);
-                            nacc += pair_move<R>(p, par, s, own4, fld, r >> 1, q, qj, c, sweep, colour, set, tag, ML,
-                                                 dhi, dlo);
-                            used += 32 - m;
-                            m = 0;
+                        const bool la = !(ra & 1u) && ra + 1u < p.Nc, lb = !(rb & 1u) && rb + 1u < p.Nc;
+                        const uint32_t ma = __ballot_sync(0xffffffffu, la), mb = __ballot_sync(0xffffffffu, lb);
+                        const uint32_t ca = uint32_t(__popc(ma));
+                        __syncwarp();  // the slots taken by the last moves are free again
+                        if (la) lq[(head + uint32_t(__popc(ma & below))) % kLeaderRing] = make_uint2(qa, ra);
+                        if (lb) lq[(head + ca + uint32_t(__popc(mb & below))) % kLeaderRing] = make_uint2(qb, rb);
+                        head += ca + uint32_t(__popc(mb));
+                        __syncwarp();
+                        while (head - tail >= 32u) {  // a full warp of leaders, oldest first
+                            const uint2 e = lq[(tail + uint32_t(lane)) % kLeaderRing];
+                            const uint32_t qj = permute(e.y + 1u, p.Nc, p.perm_bits, rk);
+                            nacc += pair_move<R>(p, par, s, own4, fld, e.y >> 1, e.x, qj, c, sweep, colour, set, tag,
+                                                 ML, dhi, dlo);
+                            tail += 32u;
                         }
-                        uint32_t q, r;  // the rest of this tile joins the queue
-                        leader(used + lane - m, q, r);
-                        if (lane >= m && lane < m + (total - used)) { wq = q; wr = r; }
-                        m += total - used;
                     }
-                    if (lane < m) {
-                        const uint32_t qj = permute(wr + 1u, p.Nc, p.perm_bits, rk);
-                        nacc += pair_move<R>(p, par, s, own4, fld, wr >> 1, wq, qj, c, sweep, colour, set, tag, ML,
+                    if (uint32_t(lane) < head - tail) {
+                        const uint2 e = lq[(tail + uint32_t(lane)) % kLeaderRing];
+                        const uint32_t qj = permute(e.y + 1u, p.Nc, p.perm_bits, rk);
+                        nacc += pair_move<R>(p, par, s, own4, fld, e.y >> 1, e.x, qj, c, sweep, colour, set, tag, ML,
                                              dhi, dlo);
                     }
+                    __syncwarp();
                 } else {
                     for (uint32_t t = tile; t < t1; ++t) {
                         const uint32_t pr = (t - t0) * 32u + uint32_t(lane);
