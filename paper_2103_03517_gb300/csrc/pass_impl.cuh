@@ -1020,13 +1020,14 @@ __device__ __forceinline__ V3<R> rotate_back(const R* Rm, V3<R> h) {
 // its neighbour field, both gathered from packed 4-vectors (the field was
 // summed for every site of the colour by pair_field_kernel, in the order of
 // neighbour_sum4), and issued together before the move is drawn.
+// pair_move_with takes the four gathered items (spins and fields of i
+// and j) from the caller, which may have staged them ahead of the move.
 template <typename R>
-__device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
-                                              Spin4<R>* own4, const Spin4<R>* fld, uint32_t pr, uint32_t qi,
-                                              uint32_t qj, R c, uint32_t sweep, int colour, int set, uint32_t tag,
-                                              double ML, long long& dhi, long long& dlo) {
-    const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
-    const Spin4<R> fi4 = fld[qi], fj4 = fld[qj];
+__device__ __forceinline__ unsigned pair_move_with(const LatParams& p, const Par<R>& par, R* __restrict__ s,
+                                                   Spin4<R>* own4, const Spin4<R>& si4, const Spin4<R>& sj4,
+                                                   const Spin4<R>& fi4, const Spin4<R>& fj4, uint32_t pr, uint32_t qi,
+                                                   uint32_t qj, R c, uint32_t sweep, int colour, int set, uint32_t tag,
+                                                   double ML, long long& dhi, long long& dlo) {
     const V3<R> h_i{fi4.x, fi4.y, fi4.z};
     const V3<R> h_j{fj4.x, fj4.y, fj4.z};
     const V3<R> Si{si4.x, si4.y, si4.z};
@@ -1079,6 +1080,26 @@ __device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& 
     ml_add<R>(dhi, dlo, ml_term<R>(par.Rm, Sj), -1);
     return 2;
 }
+
+template <typename R>
+__device__ __forceinline__ unsigned pair_move(const LatParams& p, const Par<R>& par, R* __restrict__ s,
+                                              Spin4<R>* own4, const Spin4<R>* fld, uint32_t pr, uint32_t qi,
+                                              uint32_t qj, R c, uint32_t sweep, int colour, int set, uint32_t tag,
+                                              double ML, long long& dhi, long long& dlo) {
+    const Spin4<R> si4 = own4[qi], sj4 = own4[qj];
+    const Spin4<R> fi4 = fld[qi], fj4 = fld[qj];
+    return pair_move_with<R>(p, par, s, own4, si4, sj4, fi4, fj4, pr, qi, qj, c, sweep, colour, set, tag, ML, dhi,
+                             dlo);
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), and its groups
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Slots of a warp's ring of waiting leaders in the site-order pair pass:
 // at most 31 wait between tiles, and a tile adds at most 64.
@@ -1133,13 +1154,63 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     // leaders wait in a per-warp ring in shared memory (a leader
                     // writes its (q, r) at its rank among the tile's leaders)
                     // until a full warp of them is ready; the ring is emptied at
-                    // the end of the run.  The draws are keyed by pair, so the
-                    // grouping changes no result.  The ring holds at most 31
-                    // waiting leaders plus one tile's 64.
+                    // the end of the run.  The ring holds at most 31 waiting
+                    // leaders plus one tile's 64.  A batch of 32 leaders first
+                    // finds its partners and starts the four 16-byte gathers of
+                    // each pair (spins and fields of i and j) into one of two
+                    // shared-memory stages; its moves are made one batch later,
+                    // while the next batch's gathers are in flight.  The pairs
+                    // of a pass are disjoint and their draws are keyed by pair,
+                    // so neither the grouping nor the order changes a result.
+                    static_assert(sizeof(Spin4<R>) == 16, "the staged gathers copy 16-byte items");
                     __shared__ uint2 ring[kBlock / 32][kLeaderRing];
-                    uint2* lq = ring[threadIdx.x >> 5];
+                    __shared__ Spin4<R> stage[kBlock / 32][2][4][32];  // [warp][stage][item][lane]
+                    const int wid = int(threadIdx.x >> 5);
+                    uint2* lq = ring[wid];
                     const uint32_t below = (1u << lane) - 1u;
                     uint32_t head = 0, tail = 0;  // leaders queued and taken (warp-uniform)
+                    uint32_t pend_pr = 0, pend_qi = 0, pend_qj = 0;
+                    bool pend = false, pend_lane = false;  // a batch in flight; this lane has a pair of it
+                    int sl = 0;                            // the stage of the next batch
+                    // take the n <= 32 oldest leaders and start their gathers into stage sl
+                    auto issue = [&](uint32_t n, uint32_t& pr, uint32_t& qi, uint32_t& qj) {
+                        const bool mine = uint32_t(lane) < n;
+                        if (mine) {
+                            const uint2 e = lq[(tail + uint32_t(lane)) % kLeaderRing];
+                            qi = e.x;
+                            pr = e.y >> 1;
+                            qj = permute(e.y + 1u, p.Nc, p.perm_bits, rk);
+                            cp_async16(&stage[wid][sl][0][lane], own4 + qi);
+                            cp_async16(&stage[wid][sl][1][lane], own4 + qj);
+                            cp_async16(&stage[wid][sl][2][lane], fld + qi);
+                            cp_async16(&stage[wid][sl][3][lane], fld + qj);
+                        }
+                        cp_async_commit();
+                        tail += n;
+                        return mine;
+                    };
+                    // the moves of the batch in flight, from the other stage
+                    auto finish = [&]() {
+                        const int st = sl ^ 1;
+                        if (pend_lane)
+                            nacc += pair_move_with<R>(p, par, s, own4, stage[wid][st][0][lane], stage[wid][st][1][lane],
+                                                      stage[wid][st][2][lane], stage[wid][st][3][lane], pend_pr,
+                                                      pend_qi, pend_qj, c, sweep, colour, set, tag, ML, dhi, dlo);
+                    };
+                    auto take = [&](uint32_t n) {
+                        uint32_t pr = 0, qi = 0, qj = 0;
+                        const bool mine = issue(n, pr, qi, qj);
+                        if (pend) {
+                            cp_async_wait<1>();  // all but the batch just started
+                            finish();
+                        }
+                        pend = true;
+                        pend_lane = mine;
+                        pend_pr = pr;
+                        pend_qi = qi;
+                        pend_qj = qj;
+                        sl ^= 1;
+                    };
                     for (uint32_t t = tile; t < t1; ++t) {
                         const uint32_t qa = (t - t0) * 64u + uint32_t(lane), qb = qa + 32u;
                         const uint32_t ra = qa < p.Nc ? permute_inv(qa, p.Nc, p.perm_bits, rk) : 1u;
@@ -1147,24 +1218,17 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                         const bool la = !(ra & 1u) && ra + 1u < p.Nc, lb = !(rb & 1u) && rb + 1u < p.Nc;
                         const uint32_t ma = __ballot_sync(0xffffffffu, la), mb = __ballot_sync(0xffffffffu, lb);
                         const uint32_t ca = uint32_t(__popc(ma));
-                        __syncwarp();  // the slots taken by the last moves are free again
+                        __syncwarp();  // the ring slots taken by the last batch are free again
                         if (la) lq[(head + uint32_t(__popc(ma & below))) % kLeaderRing] = make_uint2(qa, ra);
                         if (lb) lq[(head + ca + uint32_t(__popc(mb & below))) % kLeaderRing] = make_uint2(qb, rb);
                         head += ca + uint32_t(__popc(mb));
                         __syncwarp();
-                        while (head - tail >= 32u) {  // a full warp of leaders, oldest first
-                            const uint2 e = lq[(tail + uint32_t(lane)) % kLeaderRing];
-                            const uint32_t qj = permute(e.y + 1u, p.Nc, p.perm_bits, rk);
-                            nacc += pair_move<R>(p, par, s, own4, fld, e.y >> 1, e.x, qj, c, sweep, colour, set, tag,
-                                                 ML, dhi, dlo);
-                            tail += 32u;
-                        }
+                        while (head - tail >= 32u) take(32u);  // full batches, oldest leaders first
                     }
-                    if (uint32_t(lane) < head - tail) {
-                        const uint2 e = lq[(tail + uint32_t(lane)) % kLeaderRing];
-                        const uint32_t qj = permute(e.y + 1u, p.Nc, p.perm_bits, rk);
-                        nacc += pair_move<R>(p, par, s, own4, fld, e.y >> 1, e.x, qj, c, sweep, colour, set, tag, ML,
-                                             dhi, dlo);
+                    if (head != tail) take(head - tail);
+                    if (pend) {
+                        cp_async_wait<0>();
+                        finish();
                     }
                     __syncwarp();
                 } else {
