@@ -587,7 +587,7 @@ def constrained(mc, torch, stream, dev, tune=True):
                           "autotuned": None if tuned is None else {
                               "field_tiles_per_step": [4, 8, 2][tuned["field"]],
                               "pair_shape": ["4 tiles per step", "8 tiles per step", "2 tiles per step",
-                                             "4 tiles per step, one more block per SM"][tuned["pair"]],
+                                             "4 tiles per step, more resident warps"][tuned["pair"]],
                               "field_ms": [round(x, 4) for x in tuned["field_ms"][:3]],
                               "pair_ms": [round(x, 4) for x in tuned["pair_ms"][:4]]}}
     mc.mc_group_destroy(g)

@@ -350,7 +350,9 @@ MC_API int mc_group_sync(mc_group_handle g);
  *          thread): all-periodic lattices {3, 2}, boundaries and films {2, 3};
  *   field: constrained neighbour-field kernel, tiles per grid-stride step
  *          {4, 8, 2};
- *   pair:  constrained pair pass, the same {4, 8, 2}.
+ *   pair:  constrained pair pass, the same {4, 8, 2}, then 4 tiles per step
+ *          with more resident warps (site order: blocks of 128 threads, five
+ *          per SM; pair order: one more block of 256 threads per SM).
  * what: MC_TUNE_SWEEP tunes the row kernel on sweeps of Table A1,
  * MC_TUNE_CONSTRAINED the field and pair kernels on sweeps of Table A2 (with
  * each lattice's present constraint direction; a lattice that has not run a

@@ -89,16 +89,18 @@ void row_sample(const GroupArgs& g, uint32_t ntiles, int gen, cudaStream_t s) {
     else row_sample_g<0>(g, ntiles, s);
 }
 
-template <bool LEADER, int C, int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR>
+template <bool LEADER, int C, int B = LEADER ? MINB_PAIR_LEAD : MINB_PAIR, int NT = kBlock>
 void pair_pass_t(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int sub, cudaStream_t s) {
-    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER>);
-    pair_pass_kernel<R, B, C, LEADER><<<grid_for(ntiles, cap), kBlock, 0, s>>>(
+    static const uint32_t cap = resident_blocks(pair_pass_kernel<R, B, C, LEADER, NT>, NT);
+    pair_pass_kernel<R, B, C, LEADER, NT><<<grid_for(ntiles, cap, NT), NT, 0, s>>>(
         g, ntiles, static_cast<const R*>(cone), colour, sub);
 }
 
 // launch shapes: tiles per grid-stride step {default, 8, 2}, and the
-// default step with one more resident block per SM (fewer registers, some
-// spilled; more warps to cover the random gathers)
+// default step with more resident warps per SM: pair order one more block
+// of 256 threads (fewer registers, some spilled), site order blocks of 128
+// threads, five per SM (20 warps at up to 102 registers, against 16 warps
+// in two blocks of 256)
 template <bool LEADER>
 void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int shape, int sub,
                  cudaStream_t s) {
@@ -106,8 +108,10 @@ void pair_pass_s(const GroupArgs& g, uint32_t ntiles, const void* cone, int colo
     constexpr int B0 = LEADER ? MINB_PAIR_LEAD : MINB_PAIR;
     if (shape == 1) pair_pass_t<LEADER, 8>(g, ntiles, cone, colour, sub, s);
     else if (shape == 2) pair_pass_t<LEADER, 2>(g, ntiles, cone, colour, sub, s);
-    else if (shape == 3) pair_pass_t<LEADER, C0, B0 + 1>(g, ntiles, cone, colour, sub, s);
-    else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, sub, s);
+    else if (shape == 3) {
+        if constexpr (LEADER) pair_pass_t<LEADER, C0, 5, 128>(g, ntiles, cone, colour, sub, s);
+        else pair_pass_t<LEADER, C0, B0 + 1>(g, ntiles, cone, colour, sub, s);
+    } else pair_pass_t<LEADER, C0>(g, ntiles, cone, colour, sub, s);
 }
 
 void pair_pass(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int leader, int shape, int sub,

@@ -9,18 +9,19 @@
 // Blocks of a persistent launch: resident blocks per SM x SMs (device 0 of
 // the process is assumed representative; computed once per kernel).
 template <typename K>
-uint32_t resident_blocks(K kernel) {
+uint32_t resident_blocks(K kernel, int threads = kBlock) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
     if (per_sm < 1) per_sm = 1;
     return uint32_t(sms) * uint32_t(per_sm);
 }
 
 // blocks for ntiles warp tiles: one warp per tile at most, capped at residency
-uint32_t grid_for(uint32_t ntiles, uint32_t cap) {
-    const uint32_t want = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
+uint32_t grid_for(uint32_t ntiles, uint32_t cap, int threads = kBlock) {
+    const uint32_t wpb = uint32_t(threads / 32);
+    const uint32_t want = (ntiles + wpb - 1) / wpb;
     return want < cap ? (want > 0 ? want : 1) : cap;
 }
 

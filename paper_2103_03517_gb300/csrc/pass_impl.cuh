@@ -1110,12 +1110,12 @@ constexpr uint32_t kLeaderRing = 128;
 // lattices of the batch, so that the random gathers of partners and their
 // neighbours stay in L2.  A warp adds its accepted moves and M_L change
 // once per lattice in a chunk.
-template <typename R, int MINB, int CHUNK, bool LEADER>
-__global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
-                                                                 const R* __restrict__ cone, int colour, int sub) {
+template <typename R, int MINB, int CHUNK, bool LEADER, int NT = kBlock>
+__global__ void __launch_bounds__(NT, MINB) pair_pass_kernel(GroupArgs g, uint32_t ntiles,
+                                                             const R* __restrict__ cone, int colour, int sub) {
     const int lane = int(threadIdx.x & 31);
-    const uint32_t nwarps = gridDim.x * uint32_t(kBlock / 32);
-    const uint32_t w = blockIdx.x * uint32_t(kBlock / 32) + (threadIdx.x >> 5);
+    const uint32_t nwarps = gridDim.x * uint32_t(NT / 32);
+    const uint32_t w = blockIdx.x * uint32_t(NT / 32) + (threadIdx.x >> 5);
     int l = 0;
     for (uint32_t c0 = w * CHUNK; c0 < ntiles; c0 += nwarps * CHUNK) {
         const uint32_t c1 = min(c0 + uint32_t(CHUNK), ntiles);
@@ -1163,8 +1163,8 @@ __global__ void __launch_bounds__(kBlock, MINB) pair_pass_kernel(GroupArgs g, ui
                     // of a pass are disjoint and their draws are keyed by pair,
                     // so neither the grouping nor the order changes a result.
                     static_assert(sizeof(Spin4<R>) == 16, "the staged gathers copy 16-byte items");
-                    __shared__ uint2 ring[kBlock / 32][kLeaderRing];
-                    __shared__ Spin4<R> stage[kBlock / 32][2][4][32];  // [warp][stage][item][lane]
+                    __shared__ uint2 ring[NT / 32][kLeaderRing];
+                    __shared__ Spin4<R> stage[NT / 32][2][4][32];  // [warp][stage][item][lane]
                     const int wid = int(threadIdx.x >> 5);
                     uint2* lq = ring[wid];
                     const uint32_t below = (1u << lane) - 1u;
