@@ -432,6 +432,66 @@ MC_API int mc_forget(mc_server* s, uint64_t job_id);
 /* Current server clock (seconds), jobs queued / resident, bytes in use. */
 MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident, size_t* bytes);
 
+/* ------------------------------------------------------------ slabs */
+
+/* One lattice split along z into slabs, for devices that each hold a part
+ * (the domain decomposition behind the paper's multi-GPU projection, Sec. 2:
+ * without dipolar coupling the parts exchange only their boundary planes).
+ * A slab holds global planes [z0, z0 + nz) of the lattice described by d
+ * (FP32, simple cubic, periodic in z, no film tables; x and y as in d) plus
+ * one halo plane below and above: its spin arrays (mc_set_spins /
+ * mc_get_spins) are Lx x Ly x (nz + 2) sites, local plane 0 = global plane
+ * z0 - 1, plane nz + 1 = global plane z0 + nz (mod Lz).  The local lattice
+ * must have the FP32 row layout (Lx/2 a power of two <= 64 or a multiple of
+ * 64; Lx Ly (nz + 2) / 2 a multiple of 64), else MC_ERR_ARG.  Draws are keyed
+ * by global site index and colour, the halo planes never move and are left
+ * out of the sample, so a split chain equals the unsplit chain bit for bit.
+ * A slab is not swept by mc_sweep or in a group (MC_ERR_STATE / MC_ERR_ARG);
+ * one sweep of Table A1 is, on every slab in turn:
+ *   mc_slab_pass(colour 0); exchange colour 0's boundary planes;
+ *   mc_slab_pass(colour 1, measure); exchange colour 1's boundary planes;
+ *   mc_slab_export; sum the exported words over all slabs; mc_slab_close.
+ * The caller moves planes and sums words between devices (e.g. with NCCL
+ * send/recv and all-reduce on the device addresses these calls return);
+ * mc_slab_sweep does it all for slabs on one device.  mc_measure and
+ * mc_samples of every slab then give the whole lattice's observables. */
+MC_API int mc_slab_create(const mc_desc* d, int z0, int nz, mc_handle* out);
+
+/* The slab's planes: z0, nz and the lattice's Lz (any may be NULL).
+ * MC_ERR_ARG if h is not a slab. */
+MC_API int mc_slab_info(mc_handle h, int* z0, int* nz, int* Lz);
+
+/* Queue one colour pass (colour 0 red, 1 black: the lattice's global
+ * colours) over the slab's own planes; measure (black pass only) adds the
+ * sample sums of the own planes.  Does not close the sweep. */
+MC_API int mc_slab_pass(mc_handle h, int colour, int measure);
+
+/* Device addresses of one plane of the given colour: ptrs[a] = component a
+ * (a = 0, 1, 2), *count sites of that colour per plane (FP32 each).  which:
+ * 0 the first own plane (sent to the slab below), 1 the last own plane
+ * (sent above), 2 the lower halo plane (received from below), 3 the upper
+ * halo plane (received from above).  Owned by the slab; valid until
+ * mc_destroy. */
+MC_API int mc_slab_plane(mc_handle h, int colour, int which, void* ptrs[3], size_t* count);
+
+/* Queue the export of the sweep's counts: MC_SLAB_WORDS int64 words at the
+ * device address *counts (accepted moves, movable sites, own sites, then
+ * the fixed-point sample sums), cleared from the slab.  Sum them over all
+ * slabs of the lattice, elementwise, in place, before mc_slab_close. */
+#define MC_SLAB_WORDS 16
+MC_API int mc_slab_export(mc_handle h, int64_t** counts);
+
+/* Queue the end of the sweep from the summed words: the cone rule of Table
+ * A1 with the total accepted count, the sample (measure != 0) with the total
+ * sums, the sweep counter. */
+MC_API int mc_slab_close(mc_handle h, int measure);
+
+/* n_sweeps sweeps of the n slabs of one lattice held on one device and one
+ * stream (slabs[0] starts at plane 0, each slab ends where the next begins,
+ * the last ends at Lz): passes, halo copies (cudaMemcpyAsync device to
+ * device), export, sum and close as above.  n <= 64. */
+MC_API int mc_slab_sweep(const mc_handle* slabs, int n, int n_sweeps, int measure);
+
 /* ------------------------------------------------------ no allocation */
 
 /* FP32 sweeps of Table A1 on a lattice whose spin memory the caller owns,

@@ -135,6 +135,13 @@ _SIGS = {
     "mc_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mc_forget": (C.c_int, [C.c_void_p, C.c_uint64]),
     "mc_server_stats": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
+    "mc_slab_create": (C.c_int, [_P(mc_desc), C.c_int, C.c_int, _P(C.c_void_p)]),
+    "mc_slab_info": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_int)]),
+    "mc_slab_pass": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mc_slab_plane": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(C.c_void_p), _P(C.c_size_t)]),
+    "mc_slab_export": (C.c_int, [C.c_void_p, _P(C.c_void_p)]),
+    "mc_slab_close": (C.c_int, [C.c_void_p, C.c_int]),
+    "mc_slab_sweep": (C.c_int, [_P(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "mc_sweep_noalloc": (C.c_int, [C.c_void_p, _P(C.c_int), C.c_double, C.c_double, _P(C.c_double), C.c_double,
                                    _P(C.c_double), C.c_double, C.c_uint64, C.c_int64, C.c_int, _P(C.c_int),
                                    C.c_void_p, C.c_void_p]),
@@ -454,6 +461,54 @@ def mc_poll(s, job_id: int):
 def mc_cancel(s, job_id: int) -> None:
     """Cancel a queued or resident job (its result then reads MC_ERR_CANCELLED)."""
     _check(lib().mc_cancel(s, int(job_id)))
+
+
+MC_SLAB_WORDS = 16
+
+
+def mc_slab_create(desc: mc_desc, z0: int, nz: int) -> int:
+    """Slab of global planes [z0, z0 + nz) of the lattice desc describes,
+    with one halo plane each side (Lx x Ly x (nz + 2) local sites)."""
+    h = C.c_void_p()
+    _check(lib().mc_slab_create(C.byref(desc), int(z0), int(nz), C.byref(h)))
+    return h.value
+
+
+def mc_slab_info(h):
+    z0, nz, Lz = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().mc_slab_info(h, C.byref(z0), C.byref(nz), C.byref(Lz)))
+    return z0.value, nz.value, Lz.value
+
+
+def mc_slab_pass(h, colour: int, measure: bool = False) -> None:
+    _check(lib().mc_slab_pass(h, int(colour), int(bool(measure))))
+
+
+def mc_slab_plane(h, colour: int, which: int):
+    """((x, y, z) component device addresses, sites) of one plane: which = 0
+    first own, 1 last own, 2 lower halo, 3 upper halo."""
+    ptrs = (C.c_void_p * 3)()
+    n = C.c_size_t()
+    _check(lib().mc_slab_plane(h, int(colour), int(which), ptrs, C.byref(n)))
+    return tuple(int(p) for p in ptrs), n.value
+
+
+def mc_slab_export(h) -> int:
+    """Queue the export of the sweep's counts; returns the device address of
+    the MC_SLAB_WORDS int64 words."""
+    p = C.c_void_p()
+    _check(lib().mc_slab_export(h, C.byref(p)))
+    return int(p.value)
+
+
+def mc_slab_close(h, measure: bool = False) -> None:
+    _check(lib().mc_slab_close(h, int(bool(measure))))
+
+
+def mc_slab_sweep(slabs, n_sweeps: int, measure: bool = False) -> None:
+    """Sweeps of the slabs of one lattice held on one device and stream."""
+    arr = (C.c_void_p * len(slabs))(*slabs)
+    _check(lib().mc_slab_sweep(arr, len(slabs), int(n_sweeps), int(bool(measure))))
 
 
 def mc_forget(s, job_id: int) -> None:

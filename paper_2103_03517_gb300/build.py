@@ -31,6 +31,7 @@ SOURCES = {
     "groups.cpp": [],
     "tune.cpp": [],
     "server.cpp": [],
+    "slabs.cpp": [],
     "noalloc.cu": [],
 }
 

@@ -50,6 +50,10 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
             delete g;
             return fail(MC_ERR_ARG, "group members must be simple cubic lattices");
         }
+        if (lattices[i]->slab_nz) {
+            delete g;
+            return fail(MC_ERR_ARG, "a slab sweeps with its lattice's other slabs (mc_slab_sweep), not in a group");
+        }
     }
     // launch tables: the lattices in launch order (general-path and small
     // lattices first, so their few tiles start early and overlap the rest),

@@ -76,6 +76,13 @@ struct KernelSet {
     // Blocks of the wavefront kernel resident on the current device at once
     // (the work-unit plan is made for this many).  Null in the FP64 set.
     uint32_t (*wave_blocks)();
+    // Slabs of a lattice split along z (FP32 row layout; null in the FP64
+    // set): export slab L's counts to LatParams::slab_counts, sum the count
+    // words of n <= 64 slabs on this device into each, close L's sweep from
+    // its (summed) counts.
+    void (*slab_export)(LatDev* L, cudaStream_t s);
+    cudaError_t (*slab_sum)(long long* const* counts, int n, cudaStream_t s);
+    void (*slab_close)(LatDev* L, int measure, cudaStream_t s);
 };
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every

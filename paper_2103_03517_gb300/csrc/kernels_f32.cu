@@ -163,13 +163,26 @@ uint32_t wave_blocks() {
     return uint32_t(sms) * uint32_t(per_sm);
 }
 
+void slab_export(LatDev* L, cudaStream_t s) { slab_export_kernel<<<1, 32, 0, s>>>(L); }
+
+cudaError_t slab_sum(long long* const* counts, int n, cudaStream_t s) {
+    if (n < 1 || n > kMaxSlabs) return cudaErrorInvalidValue;
+    SlabList l{};
+    for (int i = 0; i < n; ++i) l.counts[i] = counts[i];
+    l.n = n;
+    slab_sum_kernel<<<1, 32, 0, s>>>(l);
+    return cudaGetLastError();
+}
+
+void slab_close(LatDev* L, int measure, cudaStream_t s) { slab_close_kernel<<<1, 32, 0, s>>>(L, measure); }
+
 }  // namespace
 
 const KernelSet& kernels_f32() {
     static const KernelSet k{colour_pass, row_pass,    pair_pass,   sweep_end,         pair_field,
                              ml_reset,    mlong,       measure,     row_sample,        xtal_pass,
                              xtal_sample, xtal_field_launch, grain_sample, profile, "f32",
-                             wave_sweep,  wave_blocks};
+                             wave_sweep,  wave_blocks, slab_export,       slab_sum,     slab_close};
     return k;
 }
 

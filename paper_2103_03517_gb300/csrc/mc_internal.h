@@ -26,6 +26,7 @@ constexpr int kSitesPerThreadF64 = 1;
 constexpr int sites_per_thread(int precision) { return precision == 1 ? kSitesPerThreadF64 : kSitesPerThreadF32; }
 constexpr int kNumSums = 12;         // per-sample lattice sums, see kSum*
 constexpr int kRingWords = 14;       // doubles per ring sample
+constexpr int kSlabWords = 16;       // slab count words: accepted, n_mov, N, the kNumSums sums
 constexpr int kMomentWords = 26;     // running sums of per-sample observables
 constexpr double kFixScale = 268435456.0;   // 2^28: fixed point of the FP64 sums
 constexpr double kFixScaleF32 = 4194304.0;  // 2^22: fixed point of the FP32 sums
@@ -130,6 +131,15 @@ struct LatParams {
     void* pfield;           // constrained sweeps: [stride] (h_x, h_y, h_z, 0) neighbour
                             // field of every site of the colour being updated, written by
                             // pair_field_kernel before each pair pass
+    int slab;               // a z slab of a larger lattice (mc_slab_create): planes 0 and
+                            // Lz - 1 are halo copies of the neighbouring slabs' planes,
+                            // pinned and left out of the sample; passes never close
+                            // the sweep (mc_slab_close does, from counts summed over slabs)
+    int cflip;              // slab: global colour = local colour ^ cflip (the parity of
+                            // the global plane under local plane 0)
+    uint32_t site_off;      // slab: global site index - local site index (mod 2^32)
+    long long* slab_counts; // slab: [kSlabWords] accepted, n_mov, N and the sums of the
+                            // slab's own planes, exported by a pass for the sum over slabs
     double J, Ku, e[3], Kc, H[3], T;
     float fJ, fKu, fe[3], fKc, fH[3], fT;
     float fBeta2;           // FP32 Metropolis test: -log2(e) / T, so exp(-dE/T) = 2^(dE fBeta2)

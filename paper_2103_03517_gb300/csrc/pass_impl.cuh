@@ -420,11 +420,11 @@ __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
 // End of a sweep (Table A1 / A2, after the black pass): the cone adaptation
 // and the carried M_L on one thread; returns the sweep's accepted count.
 // ------------------------------------------------------------------------
-__device__ inline long long close_counts(const LatParams& p, LatState& st, int measure) {
+__device__ inline long long close_counts(const LatParams& p, LatState& st, int measure, long long n_mov) {
     const long long acc = (long long)atomicExch(&st.acc, 0ull);
     st.last_acc = acc;
     if (!measure || p.adapt_in_measure) {
-        if (2 * acc > p.n_mov) { if (st.theta < 180) st.theta += 1; }
+        if (2 * acc > n_mov) { if (st.theta < 180) st.theta += 1; }
         else { if (st.theta > 1) st.theta -= 1; }
     }
     st.ml_hi += st.dml_hi;  // M_L of the next sweep (exact: integer sums)
@@ -436,7 +436,7 @@ __device__ inline long long close_counts(const LatParams& p, LatState& st, int m
 
 // End of an unmeasured sweep, on one thread.
 __device__ inline void finalize_sweep_unmeasured(const LatParams& p, LatState& st) {
-    close_counts(p, st, 0);
+    close_counts(p, st, 0, p.n_mov);
     st.sweep += 1;
 }
 
@@ -448,14 +448,18 @@ __device__ inline void finalize_sweep_unmeasured(const LatParams& p, LatState& s
 // expression of the same sums as in a serial evaluation.  The sample then costs one
 // FP64 division and one memory round trip per lane instead of a serial
 // chain on one thread, which sat at the end of every measured pass.
-__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure, bool torque, int lane) {
+// n_mov and N (the movable sites of the cone rule and the sites of the
+// sample) default to the lattice's own; a slab closes with the totals over
+// all slabs of its lattice.
+__device__ inline void finalize_sweep(const LatParams& p, LatState& st, int measure, bool torque, int lane,
+                                      long long n_mov = -1, long long N = -1) {
     constexpr unsigned kAll = 0xffffffffu;
     long long acc = 0;
     int theta = 0;
     uint32_t sweep = 0;
     long long slot = 0;
     if (lane == 0) {
-        acc = close_counts(p, st, measure);
+        acc = close_counts(p, st, measure, n_mov < 0 ? p.n_mov : n_mov);
         theta = st.theta;
         sweep = st.sweep;
         slot = p.ring_cap > 0 ? st.ring_count % p.ring_cap : 0;
@@ -496,7 +500,7 @@ __device__ inline void finalize_sweep(const LatParams& p, LatState& st, int meas
         else if (lane == 5) num = p.Kc * s1;
         else if (lane == 6) num = -(p.H[0] * s1 + p.H[1] * s2 + p.H[2] * s3);
         else if (lane < 10 && torque) num = 2.0 * p.Ku * s1 - 2.0 * p.Kc * s2 + (s3 * p.H[a2] - s4 * p.H[a1]);
-        const double quo = num / double(p.N);
+        const double quo = num / double(N < 0 ? p.N : N);
         // lanes 0-2: m; 3-6: the energy parts E_ex, E_u, E_c, E_Z; 7-9: tau
         const double m0 = __shfl_sync(kAll, quo, 0), m1 = __shfl_sync(kAll, quo, 1), m2 = __shfl_sync(kAll, quo, 2);
         const double e_ex = __shfl_sync(kAll, quo, 3), e_u = __shfl_sync(kAll, quo, 4);

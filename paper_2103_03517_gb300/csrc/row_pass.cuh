@@ -195,8 +195,20 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
             if (!grains) e = eo = P3{p2(e_ax.x), p2(e_ax.y), p2(e_ax.z)};
             P3 Sf = S;
             bool any = false;
+            // a slab draws with its sites' global indices and colours, and
+            // leaves its halo planes out of the sample
+            uint32_t key_site = site0, key_tag = tag;
+            bool sampled = true;
+            if constexpr (GEN != 0) {
+                if (p.slab) {
+                    key_site = site0 + p.site_off;
+                    key_tag = tag_of(colour ^ p.cflip, kPurposeMove);
+                    const uint32_t plane = uint32_t(p.Lx) * uint32_t(p.Ly);
+                    sampled = site0 >= plane && site0 < plane * uint32_t(p.Lz - 1);
+                }
+            }
             if constexpr (MOVE != 0) {
-                const uint4 w = philox(make_uint4(site0, sweep, tag, 0u), p.key0, p.key1);
+                const uint4 w = philox(make_uint4(key_site, sweep, key_tag, 0u), p.key0, p.key1);
                 const unsigned n = pair_move(par, c, w, S, h, mov, grains ? &e : nullptr, Sf);
                 nacc += n;
                 any = n != 0;
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                 *reinterpret_cast<float2*>(own + 2 * size_t(p.stride)) = Sf.z;
             }
             if constexpr (MEASURE > 0) {
-                pair_tile_parts<MEASURE, NS>(par, Sf, h, e, O, eo, lf);
+                if (sampled) pair_tile_parts<MEASURE, NS>(par, Sf, h, e, O, eo, lf);
                 if (++nparts == uint32_t(kPartTiles)) {
                     fix += pair_parts_flush<NS>(lf, lane);
                     nparts = 0;
@@ -226,7 +238,8 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
             if (nparts) fix += pair_parts_flush<NS>(lf, lane);
         }
         if constexpr (MOVE != 0) {
-            publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, colour == 1, [&] {
+            const bool closes = colour == 1 && !(GEN != 0 && p.slab);  // slabs close in mc_slab_close
+            publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, closes, [&] {
                 finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0, lane);
             });
         } else {
@@ -235,6 +248,63 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         }
         ++l;
     }
+}
+
+// ------------------------------------------------------------------------
+// Slabs of one lattice split along z (the decomposition of Sec. 2's
+// multi-GPU projection).  A slab's passes publish their accepted moves and
+// sample sums but never close the sweep.  After the black pass each slab
+// exports its counts (slab_export_kernel), the counts are summed over all
+// slabs (slab_sum_kernel for slabs on one device, an all-reduce between
+// devices), and every slab closes the sweep from the totals
+// (slab_close_kernel): the cone rule of Table A1 with the total accepted
+// count and movable sites, the sample with the total sums and sites, so
+// that every slab keeps the same cone angle, sweep counter and samples as
+// the unsplit lattice.
+// ------------------------------------------------------------------------
+constexpr int kMaxSlabs = 64;
+struct SlabList {
+    long long* counts[kMaxSlabs];
+    int n;
+};
+
+// One warp: accepted moves, movable sites, own sites and the sums, moved
+// out of the lattice's accumulators (which are cleared).
+__global__ void slab_export_kernel(LatDev* L) {
+    const int lane = int(threadIdx.x & 31);
+    LatState& st = L->st;
+    const LatParams& p = L->p;
+    long long* c = p.slab_counts;
+    if (lane == 0) {
+        c[0] = (long long)atomicExch(&st.acc, 0ull);
+        c[1] = p.n_mov;
+        c[2] = p.N - 2ll * p.Lx * p.Ly;  // the halo planes are not the slab's
+    }
+    if (lane < kNumSums)
+        c[3 + lane] = (long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[lane]), 0ull);
+    if (lane >= 3 + kNumSums && lane < kSlabWords) c[lane] = 0;
+}
+
+// One warp: lane i sums word i over the slabs and writes the total back to
+// every slab (integer sums: exact, in any order).
+__global__ void slab_sum_kernel(SlabList s) {
+    const int lane = int(threadIdx.x & 31);
+    if (lane >= kSlabWords) return;
+    long long t = 0;
+    for (int j = 0; j < s.n; ++j) t += s.counts[j][lane];
+    for (int j = 0; j < s.n; ++j) s.counts[j][lane] = t;
+}
+
+// One warp: the sweep's end from the summed counts.
+__global__ void slab_close_kernel(LatDev* L, int measure) {
+    const int lane = int(threadIdx.x & 31);
+    LatState& st = L->st;
+    const LatParams& p = L->p;
+    const long long* c = p.slab_counts;
+    if (lane == 0) st.acc = (unsigned long long)c[0];
+    if (lane < kNumSums) st.sums[lane] = c[3 + lane];
+    __syncwarp();
+    finalize_sweep(p, st, measure, p.sample_torque != 0, lane, c[1], c[2]);
 }
 
 }  // namespace mcgb

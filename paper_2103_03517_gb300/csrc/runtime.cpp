@@ -202,7 +202,7 @@ bool wave_desc(const mc_desc* d) {
     return d->dims[0] == 2 * kWaveLh && d->dims[1] >= kWaveMinLy;
 }
 
-size_t lattice_bytes(const mc_desc* d) {
+size_t lattice_bytes(const mc_desc* d, bool slab) {
     const uint64_t cells = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
     const uint64_t Nc = cells / 2;
     const uint64_t stride = (Nc + 63) / 64 * 64;
@@ -223,6 +223,7 @@ size_t lattice_bytes(const mc_desc* d) {
     b += align256(3 * size_t(d->dims[0]) * 8);
     // launch tables of the lattice alone: lattice pointer, site and pair starts
     b += align256(sizeof(void*)) + 2 * align256(2 * sizeof(uint32_t));
+    if (slab) b += align256(kSlabWords * 8);
     return b;
 }
 
@@ -360,7 +361,7 @@ int upload_params(mc_lattice* h) {
     return MC_OK;
 }
 
-int create_lattice(const mc_desc* din, mc_handle* out) {
+int create_lattice(const mc_desc* din, mc_handle* out, const SlabSpec* slab) {
     if (!din || !out) return fail(MC_ERR_ARG, "null argument");
     int rc = validate_desc(din);
     if (rc) return rc;
@@ -429,11 +430,24 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     constraint_frame(0.0, 0.0, p.R);
     p.ring_cap = d->ring_capacity > 0 ? d->ring_capacity : 4096;
     h->desc.ring_capacity = p.ring_cap;
+    if (slab) {
+        // local plane 0 is global plane z0 - 1: colours and draw keys are the
+        // global ones (global site = local site + Lx Ly (z0 - 1), mod 2^32;
+        // the own planes, local z >= 1, land on global z >= z0 >= 0)
+        p.slab = 1;
+        p.cflip = (slab->z0 + 1) & 1;
+        p.site_off = uint32_t(int64_t(p.Lx) * p.Ly * (slab->z0 - 1));
+        h->slab_z0 = slab->z0;
+        h->slab_nz = slab->nz;
+        h->slab_lz = slab->Lz;
+        h->slab_n = (long long)p.Lx * p.Ly * slab->Lz;
+        h->slab_n_mov = p.n_mov / slab->nz * slab->Lz;  // the same movable sites in every plane
+    }
     const size_t rs = d->precision == MC_FP64 ? 8 : 4;
 
     // one allocation, carved into 256-byte aligned pieces
     trace("create: parameters computed");
-    h->bytes = lattice_bytes(d);
+    h->bytes = lattice_bytes(d, slab != nullptr);
     cudaError_t e = cudaMalloc(&h->d_base, h->bytes);
     if (e != cudaSuccess) {
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -488,6 +502,7 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
     h->d_group_lats = reinterpret_cast<LatDev**>(take(sizeof(void*)));
     h->d_group_start = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
     h->d_group_start_pair = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
+    if (slab) p.slab_counts = reinterpret_cast<long long*>(take(kSlabWords * 8));
     if (size_t(cur - static_cast<char*>(h->d_base)) > h->bytes) {
         cudaFree(h->d_base);
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -541,6 +556,8 @@ int create_lattice(const mc_desc* din, mc_handle* out) {
         rc = fail(MC_ERR_CUDA, "memset ring");
     if (rc == MC_OK && cudaMemsetAsync(p.profile, 0, 3 * size_t(p.Lx) * 8, h->stream) != cudaSuccess)
         rc = fail(MC_ERR_CUDA, "memset profile");
+    if (rc == MC_OK && p.slab_counts && cudaMemsetAsync(p.slab_counts, 0, kSlabWords * 8, h->stream) != cudaSuccess)
+        rc = fail(MC_ERR_CUDA, "memset slab counts");
     LatDev* one = h->d_lat;
     const uint32_t st_site[2] = {0, p.nblocks_site};
     const uint32_t st_pair[2] = {0, p.nblocks_pair};
@@ -934,7 +951,9 @@ int observables_from(const mc_lattice* h, const LatState& st, mc_observables* ou
     out->sweeps_done = st.sweep;
     out->theta_deg = st.theta;
     out->error = st.error;
-    out->accept_last = double(st.last_acc) / double(h->hp.n_mov > 0 ? h->hp.n_mov : 1);
+    // a slab's count and sample are the whole lattice's
+    const long long n_mov = h->slab_nz ? h->slab_n_mov : h->hp.n_mov;
+    out->accept_last = double(st.last_acc) / double(n_mov > 0 ? n_mov : 1);
     if (n > 0) {
         for (int a = 0; a < 3; ++a) {
             out->m[a] = mo[kMomM + a] / n;
@@ -949,7 +968,7 @@ int observables_from(const mc_lattice* h, const LatState& st, mc_observables* ou
         out->e = mo[kMomE] / n;
         out->e2 = mo[kMomE2] / n;
         for (int a = 0; a < 4; ++a) out->e_parts[a] = mo[kMomParts + a] / n;
-        const double NT = double(h->hp.N) / h->hp.T;
+        const double NT = double(h->slab_nz ? h->slab_n : h->hp.N) / h->hp.T;
         out->chi[0] = NT * (out->ml2 - out->ml * out->ml);
         for (int a = 0; a < 3; ++a) out->chi[1 + a] = NT * (out->m2[a] - out->m[a] * out->m[a]);
         out->binder = out->ml2 > 0 ? 1.0 - out->ml4 / (3.0 * out->ml2 * out->ml2) : 0.0;
@@ -1025,6 +1044,7 @@ MC_API int mc_set_field(mc_handle h, const double H[3]) {
 
 MC_API int mc_sweep(mc_handle h, int n_sweeps, int measure) {
     if (!h || n_sweeps < 0) return fail(MC_ERR_ARG, "invalid argument");
+    if (h->slab_nz) return fail(MC_ERR_STATE, "a slab sweeps through mc_slab_pass / mc_slab_close or mc_slab_sweep");
     NvtxRange range("mc_sweep");
     cudaSetDevice(h->device);
     return run_sweeps(h->graphs, h->hp.precision, single_launch_set(h), h->cone, n_sweeps, measure ? 1 : 0, false,
@@ -1081,6 +1101,7 @@ MC_API int mc_measure(mc_handle h, mc_observables* out) {
 
 MC_API int mc_profile_sample(mc_handle h) {
     if (h && h->hp.nsub > 1) return fail(MC_ERR_ARG, "profiles need a simple cubic lattice");
+    if (h && h->slab_nz) return fail(MC_ERR_ARG, "a slab's planes include halo copies: profile the whole lattice");
     if (!h) return fail(MC_ERR_ARG, "null handle");
     cudaSetDevice(h->device);
     kernel_set(h->hp.precision).profile(h->d_lat, uint32_t(h->hp.Lh), uint32_t(h->hp.Ly) * h->hp.Lz, h->stream);

@@ -46,6 +46,9 @@ struct mc_lattice {
     mcgb::SweepGraphs graphs;     // sweeps of the lattice alone
     mcgb::LaunchShape shape;      // autotuned launch shapes of the lattice alone
     const void* cone = nullptr;   // c(theta) table of the precision
+    int slab_z0 = 0, slab_nz = 0, slab_lz = 0;  // a slab (mc_slab_create): its planes and the
+                                                // lattice's Lz (slab_nz = 0: not a slab)
+    long long slab_n = 0, slab_n_mov = 0;       // the whole lattice's sites and movable sites
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;
     std::vector<double> film_axes;
@@ -55,12 +58,16 @@ namespace mcgb {
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
-int create_lattice(const mc_desc* d, mc_handle* out);
+// A z slab of a larger lattice: global planes [z0, z0 + nz) of Lz.
+struct SlabSpec {
+    int z0, nz, Lz;
+};
+int create_lattice(const mc_desc* d, mc_handle* out, const SlabSpec* slab = nullptr);
 int validate_desc(const mc_desc* d);
 int row_fast(const LatParams& p, bool film);
 int sublattices(int lattice);
 int colour_kernel(const LatParams& p, bool film, int path);
-size_t lattice_bytes(const mc_desc* d);
+size_t lattice_bytes(const mc_desc* d, bool slab = false);
 int upload_params(mc_lattice* h);
 size_t aos_bytes(const mc_desc* d);
 int ensure_aos(mc_lattice* h);

@@ -13,12 +13,15 @@ coupling the ranks exchange little).
   The draws are keyed by global site indices, so the split chain equals the
   unsplit one bit for bit.
 
-Host logic only: the partitions and the exchanges use torch.distributed
-(gloo on the CPU, NCCL between GPUs).
+The partitions and the exchanges use torch.distributed (gloo on the CPU,
+NCCL between GPUs).  slab_sweep_ranks drives one rank's GPU slab of the
+library (mc_slab_create): the library's kernels move the spins, this module
+only moves boundary planes and count words between ranks.
 """
 from __future__ import annotations
 
-__all__ = ["partition_by_cost", "slab_planes", "exchange_halo", "sum_over_ranks"]
+__all__ = ["partition_by_cost", "slab_planes", "exchange_halo", "sum_over_ranks", "device_array",
+           "slab_sweep_ranks"]
 
 
 def partition_by_cost(costs, world: int) -> list:
@@ -88,3 +91,54 @@ def sum_over_ranks(value: int, world: int) -> int:
     t = torch.tensor([int(value)], dtype=torch.int64)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return int(t.item())
+
+
+class _DeviceBuffer:
+    """A device address as a CUDA array (no copy, not owned)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def device_array(ptr: int, n: int, dtype):
+    """A torch tensor viewing n elements at device address ptr (float32 or
+    int64); the memory stays the library's."""
+    import torch
+
+    typestr = {torch.float32: "<f4", torch.int64: "<i8"}[dtype]
+    return torch.as_tensor(_DeviceBuffer(ptr, n, typestr), device="cuda")
+
+
+def slab_sweep_ranks(h, n_sweeps: int, measure: bool = False, rank: int = 0, world: int = 1) -> None:
+    """n_sweeps sweeps of Table A1 of this rank's slab h (mc_slab_create, the
+    rank's planes of slab_planes), the slabs of the other ranks advancing in
+    step: per colour the library's pass, then this colour's boundary planes
+    to the neighbouring ranks and their planes into h's halo planes
+    (exchange_halo); per sweep the library's count words summed over the
+    ranks (all-reduce) and the library's close.  h must run on torch's
+    current stream (desc.stream), so that the library's kernels and the
+    exchanges are ordered.  With world = 1 the slab is its own neighbour."""
+    import torch
+    import torch.distributed as dist
+
+    from . import _mc as mc
+
+    for _ in range(int(n_sweeps)):
+        for colour in (0, 1):
+            mc.mc_slab_pass(h, colour, measure and colour == 1)
+            planes = []
+            for which in range(4):
+                ptrs, n = mc.mc_slab_plane(h, colour, which)
+                planes.append([device_array(p, n, torch.float32) for p in ptrs])
+            first = torch.cat(planes[0])
+            last = torch.cat(planes[1])
+            below, above = exchange_halo(first, last, rank, world)
+            n = planes[0][0].numel()
+            for a in range(3):
+                planes[2][a].copy_(below[a * n:(a + 1) * n])
+                planes[3][a].copy_(above[a * n:(a + 1) * n])
+        words = device_array(mc.mc_slab_export(h), mc.MC_SLAB_WORDS, torch.int64)
+        if world > 1:
+            dist.all_reduce(words, op=dist.ReduceOp.SUM)
+        mc.mc_slab_close(h, measure)
