@@ -10,7 +10,7 @@ colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--side all|none|fp64|constrained|anisotropy|cubes|general|stiffness|films|precision|
-                               serving|torque|wall|wave]
+                               serving|torque|wall|wave|slabs]
                        [--no-cpu]
 Under torchrun (N > 1) the ranks split the batch: each lattice runs on one
 rank, shares balanced by spins (strong scaling, no collective on the data
@@ -456,6 +456,8 @@ def secondary(mc, torch, stream, dev, side="all", tune=True):
         out.update(torque_study(stream, dev))
     if side in ("all", "wall"):
         out.update(wall_study(stream, dev))
+    if side in ("all", "slabs"):
+        out.update(slabs_side(mc, torch, stream, dev))
     return out
 
 
@@ -490,6 +492,49 @@ def wavefront(mc, torch, stream, dev, sweeps=200):
             mc.mc_destroy(h)
     return {"wavefront": {"workload": "the eight 128^3 lattices of the batch (16.8M spins), measured sweeps, FP32",
                           **res}}
+
+
+def slabs_side(mc, torch, stream, dev, sweeps=40):
+    """The Bloch-wall lattice (1024 x 128 x 128, x pinned, z periodic) swept
+    whole and split along z into 1, 2 and 4 slabs on this one GPU
+    (mc_slab_sweep: the slab passes, the halo-plane copies after each colour
+    pass, the count export, sum and close of every sweep), measured sweeps,
+    CUDA events: the cost of the multi-device decomposition's protocol
+    without the interconnect."""
+    spec = workloads.bloch_wall_1024()[3]
+    dims = spec.dims
+    n = dims[0] * dims[1] * dims[2]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def desc():
+        return mc.make_desc(dims, K_u=spec.Ku, T=spec.T, seed=spec.seed, boundary=spec.bc, init=mc.MC_INIT_WALL,
+                            ring_capacity=16, stream=stream.cuda_stream, device=dev)
+
+    def timed(run):
+        run(4)
+        torch.cuda.synchronize()
+        a.record(stream)
+        run(sweeps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return n * sweeps / (a.elapsed_time(b) * 1e-3)
+
+    out = {}
+    h = mc.mc_create_ex(desc())
+    out["whole"] = timed(lambda k: mc.mc_sweep(h, k, measure=True))
+    mc.mc_destroy(h)
+    for ns in (1, 2, 4):
+        nz = dims[2] // ns
+        hs = [mc.mc_slab_create(desc(), i * nz, nz) for i in range(ns)]
+        out[f"slabs_{ns}"] = timed(lambda k: mc.mc_slab_sweep(hs, k, measure=True))
+        for x in hs:
+            mc.mc_destroy(x)
+    plane_bytes = dims[0] * dims[1] // 2 * 12
+    return {"slabs": {"unit": UNIT, **{k: round(v, 1) for k, v in out.items()},
+                      "halo_bytes_per_slab_per_sweep": 4 * plane_bytes,
+                      "workload": f"Bloch-wall lattice {dims[0]}x{dims[1]}x{dims[2]}, x pinned, FP32, {sweeps} "
+                                  "measured sweeps; slabs of equal planes on one GPU, halo planes copied device "
+                                  "to device"}}
 
 
 def torque_study(stream, dev):
@@ -954,7 +999,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
                     choices=["all", "none", "fp64", "constrained", "anisotropy", "cubes", "general", "stiffness", "films",
-                             "precision", "serving", "torque", "wall", "wave"],
+                             "precision", "serving", "torque", "wall", "wave", "slabs"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:

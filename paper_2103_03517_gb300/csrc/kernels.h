@@ -77,12 +77,16 @@ struct KernelSet {
     // (the work-unit plan is made for this many).  Null in the FP64 set.
     uint32_t (*wave_blocks)();
     // Slabs of a lattice split along z (FP32 row layout; null in the FP64
-    // set): export slab L's counts to LatParams::slab_counts, sum the count
-    // words of n <= 64 slabs on this device into each, close L's sweep from
-    // its (summed) counts.
+    // set): export slab L's counts to LatParams::slab_counts, close L's
+    // sweep from its (summed) counts.
     void (*slab_export)(LatDev* L, cudaStream_t s);
-    cudaError_t (*slab_sum)(long long* const* counts, int n, cudaStream_t s);
     void (*slab_close)(LatDev* L, int measure, cudaStream_t s);
+    // Slabs on one device: the halo planes of one colour of n slabs, each
+    // from its neighbours (dst / src: [slab][lower, upper] plane bases,
+    // strides per slab), and export, sum and close of n slabs in one launch.
+    cudaError_t (*slab_halo)(float* const (*dst)[2], const float* const (*src)[2], const uint32_t* stride,
+                             const uint32_t (*src_stride)[2], uint32_t plane, int n, cudaStream_t s);
+    cudaError_t (*slab_close_all)(LatDev* const* lats, int n, int measure, cudaStream_t s);
 };
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every

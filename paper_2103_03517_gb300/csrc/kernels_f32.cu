@@ -165,16 +165,35 @@ uint32_t wave_blocks() {
 
 void slab_export(LatDev* L, cudaStream_t s) { slab_export_kernel<<<1, 32, 0, s>>>(L); }
 
-cudaError_t slab_sum(long long* const* counts, int n, cudaStream_t s) {
+void slab_close(LatDev* L, int measure, cudaStream_t s) { slab_close_kernel<<<1, 32, 0, s>>>(L, measure); }
+
+cudaError_t slab_halo(float* const (*dst)[2], const float* const (*src)[2], const uint32_t* stride,
+                      const uint32_t (*src_stride)[2], uint32_t plane, int n, cudaStream_t s) {
     if (n < 1 || n > kMaxSlabs) return cudaErrorInvalidValue;
-    SlabList l{};
-    for (int i = 0; i < n; ++i) l.counts[i] = counts[i];
-    l.n = n;
-    slab_sum_kernel<<<1, 32, 0, s>>>(l);
+    SlabHaloArgs a{};
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 2; ++k) {
+            a.dst[i][k] = dst[i][k];
+            a.src[i][k] = src[i][k];
+            a.src_stride[i][k] = src_stride[i][k];
+        }
+        a.stride[i] = stride[i];
+    }
+    a.plane = plane;
+    a.n = n;
+    const uint32_t bx = (plane + 255) / 256;
+    slab_halo_kernel<<<dim3(bx < 64 ? bx : 64, 2, uint32_t(n)), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-void slab_close(LatDev* L, int measure, cudaStream_t s) { slab_close_kernel<<<1, 32, 0, s>>>(L, measure); }
+cudaError_t slab_close_all(LatDev* const* lats, int n, int measure, cudaStream_t s) {
+    if (n < 1 || n > kMaxSlabs) return cudaErrorInvalidValue;
+    SlabDevs d{};
+    for (int i = 0; i < n; ++i) d.lat[i] = lats[i];
+    d.n = n;
+    slab_close_all_kernel<<<1, 32 * (n < 32 ? n : 32), 0, s>>>(d, measure);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -182,7 +201,8 @@ const KernelSet& kernels_f32() {
     static const KernelSet k{colour_pass, row_pass,    pair_pass,   sweep_end,         pair_field,
                              ml_reset,    mlong,       measure,     row_sample,        xtal_pass,
                              xtal_sample, xtal_field_launch, grain_sample, profile, "f32",
-                             wave_sweep,  wave_blocks, slab_export,       slab_sum,     slab_close};
+                             wave_sweep,  wave_blocks, slab_export,       slab_close,   slab_halo,
+                             slab_close_all};
     return k;
 }
 

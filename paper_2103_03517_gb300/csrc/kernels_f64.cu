@@ -39,7 +39,8 @@ const KernelSet& kernels_f64() {
     static const KernelSet k{colour_pass, nullptr,     pair_pass,   sweep_end,         pair_field,
                              ml_reset,    mlong,       measure,     nullptr,           xtal_pass,
                              xtal_sample, xtal_field_launch, grain_sample, profile, "f64",
-                             nullptr,     nullptr,     nullptr,           nullptr,      nullptr};
+                             nullptr,     nullptr,     nullptr,           nullptr,      nullptr,
+                             nullptr};
     return k;
 }
 

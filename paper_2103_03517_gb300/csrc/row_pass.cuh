@@ -255,18 +255,77 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
 // multi-GPU projection).  A slab's passes publish their accepted moves and
 // sample sums but never close the sweep.  After the black pass each slab
 // exports its counts (slab_export_kernel), the counts are summed over all
-// slabs (slab_sum_kernel for slabs on one device, an all-reduce between
-// devices), and every slab closes the sweep from the totals
-// (slab_close_kernel): the cone rule of Table A1 with the total accepted
+// slabs (an all-reduce between devices), and every slab closes the sweep
+// from the totals (slab_close_kernel; slab_close_all_kernel does all three
+// for slabs on one device): the cone rule of Table A1 with the total accepted
 // count and movable sites, the sample with the total sums and sites, so
 // that every slab keeps the same cone angle, sweep counter and samples as
 // the unsplit lattice.
 // ------------------------------------------------------------------------
 constexpr int kMaxSlabs = 64;
-struct SlabList {
-    long long* counts[kMaxSlabs];
+// Halo planes of one colour of n slabs on one device: slab i's lower halo
+// from slab i-1's last own plane and its upper halo from slab i+1's first
+// own plane (periodic), component a at offset a * stride[i] of each base.
+struct SlabHaloArgs {
+    float* dst[kMaxSlabs][2];       // lower, upper halo plane (component 0)
+    const float* src[kMaxSlabs][2]; // the neighbours' boundary planes
+    uint32_t stride[kMaxSlabs];     // component stride of slab i (floats)
+    uint32_t src_stride[kMaxSlabs][2];
+    uint32_t plane;                 // sites of the colour per plane
     int n;
 };
+
+// Grid: (chunks of the plane, 2 sides, n slabs); a thread copies one site
+// of the plane in all three components per step.
+__global__ void slab_halo_kernel(SlabHaloArgs a) {
+    const int i = int(blockIdx.z), side = int(blockIdx.y);
+    float* dst = a.dst[i][side];
+    const float* src = a.src[i][side];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.plane; v += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[size_t(c) * a.stride[i] + v] = src[size_t(c) * a.src_stride[i][side] + v];
+}
+
+// Export, sum over the n slabs and close, fused for slabs on one device:
+// warp w takes slabs w, w + 32, ...; the counts meet in shared memory.
+struct SlabDevs {
+    LatDev* lat[kMaxSlabs];
+    int n;
+};
+
+__global__ void slab_close_all_kernel(SlabDevs d, int measure) {
+    __shared__ long long words[kMaxSlabs][kSlabWords];
+    __shared__ long long total[kSlabWords];
+    const int lane = int(threadIdx.x & 31), warp = int(threadIdx.x >> 5), nw = int(blockDim.x >> 5);
+    for (int i = warp; i < d.n; i += nw) {
+        LatState& st = d.lat[i]->st;
+        const LatParams& p = d.lat[i]->p;
+        if (lane == 0) {
+            words[i][0] = (long long)atomicExch(&st.acc, 0ull);
+            words[i][1] = p.n_mov;
+            words[i][2] = p.N - 2ll * p.Lx * p.Ly;
+        }
+        if (lane < kNumSums)
+            words[i][3 + lane] = (long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[lane]), 0ull);
+        if (lane >= 3 + kNumSums && lane < kSlabWords) words[i][lane] = 0;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < kSlabWords) {
+        long long t = 0;
+        for (int j = 0; j < d.n; ++j) t += words[j][lane];
+        total[lane] = t;
+    }
+    __syncthreads();
+    for (int i = warp; i < d.n; i += nw) {
+        LatState& st = d.lat[i]->st;
+        const LatParams& p = d.lat[i]->p;
+        if (lane < kSlabWords) p.slab_counts[lane] = total[lane];
+        if (lane == 0) st.acc = (unsigned long long)total[0];
+        if (lane < kNumSums) st.sums[lane] = total[3 + lane];
+        __syncwarp();
+        finalize_sweep(p, st, measure, p.sample_torque != 0, lane, total[1], total[2]);
+    }
+}
 
 // One warp: accepted moves, movable sites, own sites and the sums, moved
 // out of the lattice's accumulators (which are cleared).
@@ -283,16 +342,6 @@ __global__ void slab_export_kernel(LatDev* L) {
     if (lane < kNumSums)
         c[3 + lane] = (long long)atomicExch(reinterpret_cast<unsigned long long*>(&st.sums[lane]), 0ull);
     if (lane >= 3 + kNumSums && lane < kSlabWords) c[lane] = 0;
-}
-
-// One warp: lane i sums word i over the slabs and writes the total back to
-// every slab (integer sums: exact, in any order).
-__global__ void slab_sum_kernel(SlabList s) {
-    const int lane = int(threadIdx.x & 31);
-    if (lane >= kSlabWords) return;
-    long long t = 0;
-    for (int j = 0; j < s.n; ++j) t += s.counts[j][lane];
-    for (int j = 0; j < s.n; ++j) s.counts[j][lane] = t;
 }
 
 // One warp: the sweep's end from the summed counts.

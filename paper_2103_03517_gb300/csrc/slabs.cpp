@@ -141,8 +141,31 @@ MC_API int mc_slab_sweep(const mc_handle* slabs, int n, int n_sweeps, int measur
     cudaSetDevice(slabs[0]->device);
     const cudaStream_t s = slabs[0]->stream;
     const KernelSet& k = kernels_f32();
-    std::vector<long long*> counts(n);
-    for (int i = 0; i < n; ++i) counts[i] = slabs[i]->hp.slab_counts;
+    // halo copies of each colour: slab i's lower halo from slab i-1's last
+    // own plane, its upper halo from slab i+1's first own plane
+    float* dst[2][64][2];
+    const float* src[2][64][2];
+    uint32_t stride[64], src_stride[64][2];
+    std::vector<LatDev*> lats(n);
+    size_t plane = 0;
+    for (int colour = 0; colour < 2; ++colour)
+        for (int i = 0; i < n; ++i) {
+            const mc_lattice* up = slabs[(i + 1) % n];
+            const mc_lattice* dn = slabs[(i + n - 1) % n];
+            void* p[3];
+            plane_ptrs(slabs[i], colour ^ slabs[i]->hp.cflip, plane_of(slabs[i], 2), p, &plane);
+            dst[colour][i][0] = static_cast<float*>(p[0]);
+            plane_ptrs(slabs[i], colour ^ slabs[i]->hp.cflip, plane_of(slabs[i], 3), p, nullptr);
+            dst[colour][i][1] = static_cast<float*>(p[0]);
+            plane_ptrs(dn, colour ^ dn->hp.cflip, plane_of(dn, 1), p, nullptr);
+            src[colour][i][0] = static_cast<const float*>(p[0]);
+            plane_ptrs(up, colour ^ up->hp.cflip, plane_of(up, 0), p, nullptr);
+            src[colour][i][1] = static_cast<const float*>(p[0]);
+            stride[i] = slabs[i]->hp.stride;
+            src_stride[i][0] = dn->hp.stride;
+            src_stride[i][1] = up->hp.stride;
+            lats[i] = slabs[i]->d_lat;
+        }
     for (int it = 0; it < n_sweeps; ++it) {
         for (int colour = 0; colour < 2; ++colour) {
             const int meas = measure && colour == 1;
@@ -150,29 +173,11 @@ MC_API int mc_slab_sweep(const mc_handle* slabs, int n, int n_sweeps, int measur
                 int rc = mc_slab_pass(slabs[i], colour, meas);
                 if (rc) return rc;
             }
-            // the colour just moved: each slab's halo planes from its
-            // neighbours' boundary planes (periodic in z)
-            for (int i = 0; i < n; ++i) {
-                const mc_lattice* up = slabs[(i + 1) % n];
-                const mc_lattice* dn = slabs[(i + n - 1) % n];
-                void *dst_hi[3], *dst_lo[3], *src_hi[3], *src_lo[3];
-                size_t cnt = 0;
-                plane_ptrs(slabs[i], colour ^ slabs[i]->hp.cflip, plane_of(slabs[i], 3), dst_hi, &cnt);
-                plane_ptrs(slabs[i], colour ^ slabs[i]->hp.cflip, plane_of(slabs[i], 2), dst_lo, nullptr);
-                plane_ptrs(up, colour ^ up->hp.cflip, plane_of(up, 0), src_hi, nullptr);
-                plane_ptrs(dn, colour ^ dn->hp.cflip, plane_of(dn, 1), src_lo, nullptr);
-                for (int a = 0; a < 3; ++a) {
-                    cudaError_t e = cudaMemcpyAsync(dst_hi[a], src_hi[a], cnt * 4, cudaMemcpyDeviceToDevice, s);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(dst_lo[a], src_lo[a], cnt * 4, cudaMemcpyDeviceToDevice, s);
-                    if (e != cudaSuccess) return cuda_fail(e, "slab halo copy");
-                }
-            }
+            const cudaError_t e = k.slab_halo(dst[colour], src[colour], stride, src_stride, uint32_t(plane), n, s);
+            if (e != cudaSuccess) return cuda_fail(e, "slab halo copy");
         }
-        for (int i = 0; i < n; ++i) k.slab_export(slabs[i]->d_lat, s);
-        const cudaError_t e = k.slab_sum(counts.data(), n, s);
-        if (e != cudaSuccess) return cuda_fail(e, "slab count sum");
-        for (int i = 0; i < n; ++i) k.slab_close(slabs[i]->d_lat, measure ? 1 : 0, s);
+        const cudaError_t e = k.slab_close_all(lats.data(), n, measure ? 1 : 0, s);
+        if (e != cudaSuccess) return cuda_fail(e, "slab close");
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "slab sweep");
