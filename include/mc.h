@@ -446,7 +446,9 @@ MC_API int mc_server_stats(mc_server* s, double* now, int* queued, int* resident
  * 64; Lx Ly (nz + 2) / 2 a multiple of 64), else MC_ERR_ARG.  Draws are keyed
  * by global site index and colour, the halo planes never move and are left
  * out of the sample, so a split chain equals the unsplit chain bit for bit.
- * A slab is not swept by mc_sweep or in a group (MC_ERR_STATE / MC_ERR_ARG);
+ * A slab is not swept by mc_sweep or in a group (MC_ERR_STATE / MC_ERR_ARG),
+ * nor saved by mc_save or profiled by mc_profile_sample (its planes include
+ * the halo copies);
  * one sweep of Table A1 is, on every slab in turn:
  *   mc_slab_pass(colour 0); exchange colour 0's boundary planes;
  *   mc_slab_pass(colour 1, measure); exchange colour 1's boundary planes;

@@ -1245,6 +1245,7 @@ static const char kMagic[8] = {'M', 'C', 'G', 'B', 'C', 'K', '0', '4'};
 
 MC_API int mc_save(mc_handle h, const char* path) {
     if (!h || !path) return fail(MC_ERR_ARG, "null argument");
+    if (h->slab_nz) return fail(MC_ERR_STATE, "a slab is checkpointed through its lattice (mc_get_spins of every slab)");
     cudaSetDevice(h->device);
     LatState st;
     int rc = read_state(h, &st);

@@ -218,6 +218,11 @@ def test_slab_misuse_is_refused():
         with pytest.raises(mc.MCError) as e:
             mc.mc_slab_sweep([h], 1)  # one slab of 8 planes does not cover Lz = 16
         assert e.value.code == mc.MC_ERR_ARG
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_save(h, "/dev/null")
+        assert e.value.code == mc.MC_ERR_STATE
+        with pytest.raises(mc.MCError):
+            mc.mc_profile_sample(h)
     finally:
         mc.mc_destroy(h)
     for bad in (dict(precision=mc.MC_FP64), dict(boundary=(0, 0, mc.MC_PINNED))):
