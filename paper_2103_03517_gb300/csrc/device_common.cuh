@@ -51,6 +51,19 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys& K) {
     return c;
 }
 
+// The same ten rounds with the round keys read from shared memory (rk[r] =
+// the key pair before round r, written once per lattice by the warp).
+__device__ __forceinline__ uint4 philox_smem(uint4 c, const uint2* rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint2 k = rk[r];
+        const uint64_t p0 = uint64_t(0xD2511F53u) * c.x, p1 = uint64_t(0xCD9E8D57u) * c.z;
+        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0), hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
 // Philox stream tags: bit 0 = colour, bits 1.. = purpose.
 enum { kPurposeMove = 0, kPurposePair = 1, kPurposePerm = 2 };
 __device__ __forceinline__ uint32_t tag_of(int colour, int purpose) {

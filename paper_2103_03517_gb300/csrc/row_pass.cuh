@@ -167,6 +167,17 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         const uint32_t sweep = L->st.sweep;
         float* __restrict__ s = static_cast<float*>(p.spins);
         const V3<float> e_ax{par.e[0], par.e[1], par.e[2]};
+        // unmeasured passes: the lattice's Philox round keys, once per run, in
+        // the warp's slots (ten shared loads per draw instead of twenty adds;
+        // the measured pass keeps the adds, which need no registers there)
+        __shared__ uint2 round_keys[kBlock / 32][10];
+        uint2* rk = round_keys[threadIdx.x >> 5];
+        if constexpr (MEASURE == 0) {
+            __syncwarp();  // the previous run's keys are no longer read
+            if (lane < 10)
+                rk[lane] = make_uint2(p.key0 + uint32_t(lane) * 0x9E3779B9u, p.key1 + uint32_t(lane) * 0xBB67AE85u);
+            __syncwarp();
+        }
         unsigned nacc = 0;
         long long fix = 0;
         int lf[NS];  // this lane's fixed-point parts of the sample, kPartTiles tiles at a time
@@ -208,7 +219,8 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
                 }
             }
             if constexpr (MOVE != 0) {
-                const uint4 w = philox(make_uint4(key_site, sweep, key_tag, 0u), p.key0, p.key1);
+                const uint4 w = MEASURE == 0 ? philox_smem(make_uint4(key_site, sweep, key_tag, 0u), rk)
+                                             : philox(make_uint4(key_site, sweep, key_tag, 0u), p.key0, p.key1);
                 const unsigned n = pair_move(par, c, w, S, h, mov, grains ? &e : nullptr, Sf);
                 nacc += n;
                 any = n != 0;
