@@ -51,7 +51,12 @@ cudaError_t row_pass_t(const GroupArgs& g, uint32_t ntiles, const R* cone, int c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, row_pass_kernel<B, MEASURE, GEN>, g, ntiles, cone, colour);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, row_pass_kernel<B, MEASURE, GEN>, g, ntiles, cone, colour);
+    if (e != cudaSuccess || colour != 1 || MEASURE > 0) return e;  // the unmeasured sweep's end
+    cudaLaunchConfig_t cc = cfg;
+    cc.gridDim = dim3(uint32_t(g.n));
+    cc.blockDim = dim3(32);
+    return cudaLaunchKernelEx(&cc, row_close_kernel, g, 0);
 }
 
 // launch shape 0: the default blocks per SM of the instance; 1: the other candidate

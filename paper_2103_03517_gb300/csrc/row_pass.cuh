@@ -250,7 +250,10 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
             if (nparts) fix += pair_parts_flush<NS>(lf, lane);
         }
         if constexpr (MOVE != 0) {
-            const bool closes = colour == 1 && !(GEN != 0 && p.slab);  // slabs close in mc_slab_close
+            // a measured black pass closes the sweep itself; after an unmeasured
+            // one row_close_kernel does (its warps then need no fence), and
+            // slabs close in mc_slab_close
+            const bool closes = MEASURE > 0 && colour == 1 && !(GEN != 0 && p.slab);
             publish(L->st, lane, nacc, MEASURE > 0, fix, colour, run, p.nblocks_site, closes, [&] {
                 finalize_sweep(p, L->st, MEASURE > 0 ? 1 : 0, p.sample_torque != 0, lane);
             });
@@ -260,6 +263,20 @@ __global__ void __launch_bounds__(kBlock, MINB) row_pass_kernel(GroupArgs g, uin
         }
         ++l;
     }
+}
+
+// End of an unmeasured sweep of every lattice of g after its black pass, one
+// warp per lattice (slabs are closed by mc_slab_close instead).  Launched
+// after the pass with programmatic serialisation: it waits for the pass to
+// complete, so the pass's warps publish their counts with no fence.
+__global__ void row_close_kernel(GroupArgs g, int measure) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int l = int(blockIdx.x);
+    if (l >= g.n) return;
+    LatDev* L = g.lats[l];
+    if (L->p.slab) return;
+    finalize_sweep(L->p, L->st, measure, L->p.sample_torque != 0, int(threadIdx.x & 31));
 }
 
 // ------------------------------------------------------------------------
