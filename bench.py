@@ -902,9 +902,13 @@ def general_geometry(mc, torch, stream, dev, sweeps=40):
         n = dims[0] * dims[1] * dims[2] * (4 if name == "fcc" else 1)
         out[name] = n * sweeps / (a.elapsed_time(b) * 1e-3)
         mc.mc_destroy(h)
+    peak, _ = measured_peak()
     return {"general_geometry": {"unit": UNIT, "wall_1024x128x128_pinned_x": out["wall"],
                                  "film_1024x1024x15": out["film"], "fcc_128c": out["fcc"],
-                                 "workload": f"{sweeps} measured sweeps each, FP32"}}
+                                 "wall_sweep_frac": round(out["wall"] * BYTES_PER_UPDATE / 1e9 / peak, 4),
+                                 "film_sweep_frac": round(out["film"] * BYTES_PER_UPDATE / 1e9 / peak, 4),
+                                 "workload": f"{sweeps} measured sweeps each, FP32; sweep_frac = updates/s x 24 B "
+                                             "over the measured HBM peak"}}
 
 
 def _serve_trace(mc, trace, n_eq, n_meas, film_tables):
