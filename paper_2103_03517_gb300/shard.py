@@ -21,7 +21,7 @@ only moves boundary planes and count words between ranks.
 from __future__ import annotations
 
 __all__ = ["partition_by_cost", "slab_planes", "exchange_halo", "sum_over_ranks", "device_array",
-           "slab_sweep_ranks"]
+           "LibrarySlab", "slab_sweep_ranks"]
 
 
 def partition_by_cost(costs, world: int) -> list:
@@ -110,35 +110,66 @@ def device_array(ptr: int, n: int, dtype):
     return torch.as_tensor(_DeviceBuffer(ptr, n, typestr), device="cuda")
 
 
-def slab_sweep_ranks(h, n_sweeps: int, measure: bool = False, rank: int = 0, world: int = 1) -> None:
+class LibrarySlab:
+    """The calls slab_sweep_ranks makes on a slab of the library
+    (mc_slab_create): its colour pass, its boundary and halo planes as
+    tensors viewing device memory, its exported count words, its close."""
+
+    def pass_(self, h, colour: int, measure: bool) -> None:
+        from . import _mc as mc
+
+        mc.mc_slab_pass(h, colour, measure)
+
+    def planes(self, h, colour: int):
+        """[first own, last own, lower halo, upper halo], each three
+        component tensors of one plane of the colour."""
+        import torch
+
+        from . import _mc as mc
+
+        out = []
+        for which in range(4):
+            ptrs, n = mc.mc_slab_plane(h, colour, which)
+            out.append([device_array(p, n, torch.float32) for p in ptrs])
+        return out
+
+    def words(self, h):
+        import torch
+
+        from . import _mc as mc
+
+        return device_array(mc.mc_slab_export(h), mc.MC_SLAB_WORDS, torch.int64)
+
+    def close(self, h, measure: bool) -> None:
+        from . import _mc as mc
+
+        mc.mc_slab_close(h, measure)
+
+
+def slab_sweep_ranks(h, n_sweeps: int, measure: bool = False, rank: int = 0, world: int = 1, api=None) -> None:
     """n_sweeps sweeps of Table A1 of this rank's slab h (mc_slab_create, the
     rank's planes of slab_planes), the slabs of the other ranks advancing in
-    step: per colour the library's pass, then this colour's boundary planes
-    to the neighbouring ranks and their planes into h's halo planes
-    (exchange_halo); per sweep the library's count words summed over the
-    ranks (all-reduce) and the library's close.  h must run on torch's
-    current stream (desc.stream), so that the library's kernels and the
-    exchanges are ordered.  With world = 1 the slab is its own neighbour."""
+    step: per colour the slab's pass, then this colour's boundary planes to
+    the neighbouring ranks and their planes into h's halo planes
+    (exchange_halo); per sweep the slab's count words summed over the ranks
+    (all-reduce) and the slab's close.  api makes the slab calls (default
+    LibrarySlab); with the library, h must run on torch's current stream
+    (desc.stream), so that its kernels and the exchanges are ordered.  With
+    world = 1 the slab is its own neighbour."""
     import torch
     import torch.distributed as dist
 
-    from . import _mc as mc
-
+    api = api or LibrarySlab()
     for _ in range(int(n_sweeps)):
         for colour in (0, 1):
-            mc.mc_slab_pass(h, colour, measure and colour == 1)
-            planes = []
-            for which in range(4):
-                ptrs, n = mc.mc_slab_plane(h, colour, which)
-                planes.append([device_array(p, n, torch.float32) for p in ptrs])
-            first = torch.cat(planes[0])
-            last = torch.cat(planes[1])
-            below, above = exchange_halo(first, last, rank, world)
+            api.pass_(h, colour, measure and colour == 1)
+            planes = api.planes(h, colour)
+            below, above = exchange_halo(torch.cat(planes[0]), torch.cat(planes[1]), rank, world)
             n = planes[0][0].numel()
             for a in range(3):
                 planes[2][a].copy_(below[a * n:(a + 1) * n])
                 planes[3][a].copy_(above[a * n:(a + 1) * n])
-        words = device_array(mc.mc_slab_export(h), mc.MC_SLAB_WORDS, torch.int64)
+        words = api.words(h)
         if world > 1:
             dist.all_reduce(words, op=dist.ReduceOp.SUM)
-        mc.mc_slab_close(h, measure)
+        api.close(h, measure)

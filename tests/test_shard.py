@@ -3,7 +3,9 @@ gloo ranks, driving the serial oracle: a batch of independent lattices split
 by cost gives every lattice's own chain, and one lattice split into two slabs
 of z planes, with the boundary planes exchanged after each colour pass and
 the accepted counts summed, gives the unsplit chain of Table A1 bit for bit
-(the draws are keyed by global site indices)."""
+(the draws are keyed by global site indices), both with the exchange written
+out here and through shard.slab_sweep_ranks, the driver of the library's GPU
+slabs, given oracle slabs."""
 import os
 import socket
 
@@ -125,6 +127,80 @@ def test_two_slabs_with_halo_exchange_equal_the_unsplit_chain():
     with tmp.Manager() as man:
         out = man.dict()
         tmp.spawn(_slab_rank, args=(2, port, out), nprocs=2, join=True)
+        slabs = dict(out)["slabs"]
+    Lx, Ly, Lz = SLAB_DIMS
+    ref = oracle.Lattice(SLAB_DIMS, Ku=0.05, Kc=0.02, H=(0.0, 0.02, 0.01), T=0.8, seed=9)
+    ref.set_spins(workloads.random_spins(Lx * Ly * Lz, 6))
+    ref.sweep(6)
+    R = ref.spins().reshape(Lz, Ly * Lx, 3)
+    for z0, z1, S, theta in slabs:
+        assert np.array_equal(np.array(S), R[z0:z1])
+        assert theta == ref.theta
+
+
+class _OracleSlab:
+    """The slab calls of shard.slab_sweep_ranks on the serial oracle: the
+    rank's lattice holds every plane but moves only its own (z0 .. z1 - 1);
+    the planes are views of a host copy of the spins, so the driver's halo
+    writes reach the oracle before the next pass (whole planes: the other
+    colour of a boundary plane is unchanged since its own exchange)."""
+
+    def __init__(self, o, z0, z1, dims):
+        self.o, self.z0, self.z1 = o, z0, z1
+        Lx, Ly, Lz = dims
+        self.Lz = Lz
+        self.S = torch.from_numpy(o.spins().reshape(Lz, Ly * Lx, 3).copy())
+        self.acc = 0
+
+    def pass_(self, h, colour, measure):
+        self.o.set_spins(self.S.numpy().reshape(-1, 3))
+        self.acc += self.o.colour_pass_planes(colour, self.z0, self.z1)
+        self.S.copy_(torch.from_numpy(self.o.spins().reshape(self.S.shape)))
+
+    def planes(self, h, colour):
+        zs = [self.z0, self.z1 - 1, (self.z0 - 1) % self.Lz, self.z1 % self.Lz]
+        return [[self.S[z, :, a] for a in range(3)] for z in zs]
+
+    def words(self, h):
+        # the driver sums these words over the ranks in place before close
+        self.w = torch.zeros(16, dtype=torch.int64)
+        self.w[0] = self.acc
+        self.acc = 0
+        return self.w
+
+    def close(self, h, measure):
+        self.o.set_spins(self.S.numpy().reshape(-1, 3))
+        self.o.end_sweep(int(self.w[0]))
+
+
+def _driver_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        Lx, Ly, Lz = SLAB_DIMS
+        z0, z1 = shard.slab_planes(Lz, world)[rank]
+        o = oracle.Lattice(SLAB_DIMS, Ku=0.05, Kc=0.02, H=(0.0, 0.02, 0.01), T=0.8, seed=9)
+        o.set_spins(workloads.random_spins(Lx * Ly * Lz, 6))
+        api = _OracleSlab(o, z0, z1, SLAB_DIMS)
+        shard.slab_sweep_ranks(None, 6, rank=rank, world=world, api=api)
+        S = o.spins().reshape(Lz, Ly * Lx, 3)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (z0, z1, S[z0:z1].tolist(), o.theta))
+        if rank == 0:
+            out["slabs"] = gathered
+    finally:
+        dist.destroy_process_group()
+
+
+def test_slab_rank_driver_on_two_ranks_equals_the_unsplit_chain():
+    """shard.slab_sweep_ranks (the driver of the library's GPU slabs) run on
+    two gloo ranks with slabs of the serial oracle: its routing of boundary
+    planes into halo planes and its all-reduce of the count words give the
+    unsplit chain bit for bit."""
+    port = _free_port()
+    with tmp.Manager() as man:
+        out = man.dict()
+        tmp.spawn(_driver_rank, args=(2, port, out), nprocs=2, join=True)
         slabs = dict(out)["slabs"]
     Lx, Ly, Lz = SLAB_DIMS
     ref = oracle.Lattice(SLAB_DIMS, Ku=0.05, Kc=0.02, H=(0.0, 0.02, 0.01), T=0.8, seed=9)
