@@ -38,6 +38,8 @@ import workloads  # noqa: E402
 
 METRIC = "spin-updates/s & HBM roofline frac (128^3 FP32); served m(T) req/s, p50/p99"
 UNIT = "spin-updates/s"
+# launch shapes of the FP32 row kernel (mc_group_autotune's row candidates)
+ROW_SHAPES = ["3 blocks per SM", "2 blocks per SM"]
 BYTES_PER_UPDATE = 24          # FP32: read + write 3 x 4 B of every spin once per sweep
 FALLBACK_HBM_GBS = 6800.0
 LATSTATE_BYTES = 400           # device state block read back by mc_measure
@@ -327,7 +329,7 @@ def gpu_arm(args, cfg):
         # launch shapes picked by the autotuner (the chains are left unchanged)
         if not args.no_autotune:
             tuned = mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
-            cfg["autotuned"] = {"row_kernel_blocks_per_sm": [3, 2][tuned["row"]],
+            cfg["autotuned"] = {"row_shape": ROW_SHAPES[tuned["row"]],
                                 "ms_per_sweep": [round(x, 4) for x in tuned["row_ms"][:2]]}
         mc.mc_group_sweep(g, args.warmup, measure=True)
         torch.cuda.synchronize()
@@ -840,12 +842,11 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
                                            ring_capacity=16, sample_torque=0, stream=stream.cuda_stream,
                                            device=dev, kernel_path=path)) for i, L in enumerate(sizes)]
         g = mc.mc_group_create(hs)
-        if tune:
-            mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP)
+        tuned = mc.mc_group_autotune(g, 4, mc.MC_TUNE_SWEEP) if tune else None
         n = sum(L ** 3 for L in sizes)
         mc.mc_group_sweep(g, 20, measure=True)
         torch.cuda.synchronize()
-        res = {"spins": n}
+        res = {"spins": n, "row_shape": ROW_SHAPES[tuned["row"]] if tuned else ROW_SHAPES[0]}
         for meas in (False, True):
             a.record(stream)
             mc.mc_group_sweep(g, sweeps, measure=meas)

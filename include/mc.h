@@ -379,6 +379,12 @@ MC_API int mc_group_autotune(mc_group_handle g, int sweeps, int what, mc_tune_re
  * Crystal lattices (bcc, fcc, hcp) have no tunable shape: MC_ERR_ARG. */
 MC_API int mc_autotune(mc_handle h, int sweeps, int what, mc_tune_report* out);
 
+/* Set the group's launch shapes directly (candidate indices as in the
+ * report: row 0..1, field 0..2, pair 0..3), e.g. from an earlier tuning.
+ * No result depends on them.  Errors: MC_ERR_ARG (null group, index out of
+ * range). */
+MC_API int mc_group_set_shapes(mc_group_handle g, int row, int field, int pair);
+
 /* ------------------------------------------------------------- serving */
 
 typedef struct mc_server_desc {

@@ -128,6 +128,7 @@ _SIGS = {
     "mc_group_sync": (C.c_int, [C.c_void_p]),
     "mc_group_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
     "mc_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(mc_tune_report)]),
+    "mc_group_set_shapes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "mc_server_create": (C.c_int, [_P(mc_server_desc), _P(C.c_void_p)]),
     "mc_server_destroy": (C.c_int, [C.c_void_p]),
     "mc_submit": (C.c_int, [C.c_void_p, _P(mc_job), _P(C.c_uint64)]),
@@ -377,6 +378,11 @@ def mc_group_constrained_sweep(g, theta_c_deg, phi_c_deg, n_sweeps: int, measure
     th = np.ascontiguousarray(theta_c_deg, dtype=np.float64)
     ph = np.ascontiguousarray(phi_c_deg, dtype=np.float64)
     _check(lib().mc_group_constrained_sweep(g, _dp(th), _dp(ph), int(n_sweeps), int(bool(measure))))
+
+
+def mc_group_set_shapes(g, row: int = 0, field: int = 0, pair: int = 0) -> None:
+    """Launch shapes of the group's kernels by candidate index (see mc_group_autotune)."""
+    _check(lib().mc_group_set_shapes(g, int(row), int(field), int(pair)))
 
 
 def mc_group_autotune(g, sweeps: int = 4, what: int = MC_TUNE_SWEEP | MC_TUNE_CONSTRAINED) -> dict:

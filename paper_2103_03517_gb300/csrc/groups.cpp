@@ -265,6 +265,17 @@ MC_API int mc_group_autotune(mc_group_handle g, int sweeps, int what, mc_tune_re
     return MC_OK;
 }
 
+MC_API int mc_group_set_shapes(mc_group_handle g, int row, int field, int pair) {
+    if (!g) return fail(MC_ERR_ARG, "null group");
+    if (row < 0 || row >= kRowShapes || field < 0 || field >= kFieldShapes || pair < 0 || pair >= kPairShapes)
+        return fail(MC_ERR_ARG, "launch shape out of range");
+    g->ls.shape.row = row;
+    g->ls.shape.field = field;
+    g->ls.shape.pair = pair;
+    destroy_graphs(g->graphs);  // captured with the old shapes
+    return MC_OK;
+}
+
 MC_API int mc_group_measure(mc_group_handle g, mc_observables* out, int n) {
     if (!g || !out || n != int(g->lats.size())) return fail(MC_ERR_ARG, "invalid argument");
     cudaSetDevice(g->device);

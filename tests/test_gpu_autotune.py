@@ -29,8 +29,8 @@ def test_group_autotune_leaves_chains_unchanged(prec):
             mc.mc_group_constrained_sweep(g, [40.0] * 4, [10.0] * 4, 3)
             if tune:
                 rep = mc.mc_group_autotune(g, 2)
-                assert 0 <= rep["row"] < 2 and 0 <= rep["field"] < 3 and 0 <= rep["pair"] < 3
-                assert all(t > 0 for t in rep["field_ms"][:3]) and all(t > 0 for t in rep["pair_ms"][:3])
+                assert 0 <= rep["row"] < 2 and 0 <= rep["field"] < 3 and 0 <= rep["pair"] < 4
+                assert all(t > 0 for t in rep["field_ms"][:3]) and all(t > 0 for t in rep["pair_ms"][:4])
                 if prec == mc.MC_FP32:
                     assert all(t > 0 for t in rep["row_ms"][:2])
             mc.mc_group_sweep(g, 20, measure=True)
@@ -72,3 +72,41 @@ def test_lone_lattice_autotune_and_errors():
             mc.mc_autotune(x, 2)
     finally:
         mc.mc_destroy(x)
+
+
+def test_every_row_shape_gives_the_same_chain():
+    """The row kernel's launch shapes (3 or 2 blocks per SM) change no bit:
+    rows of 64, 128, 32 and 8 sites per colour, unmeasured and measured
+    sweeps, runs of tiles of every length."""
+    dims = [(128, 32, 16), (256, 16, 8), (64, 64, 16), (16, 16, 16), (32, 8, 8)]
+    ref = None
+    for shape in range(2):
+        hs = [mc.mc_create_ex(mc.make_desc(d, K_u=0.05, K_c=0.01, H=(0.0, 0.02, 0.0), T=0.6 + 0.1 * i, seed=i + 3,
+                                           init_dir=(0.3, 0.0, 0.95), ring_capacity=16)) for i, d in enumerate(dims)]
+        g = mc.mc_group_create(hs)
+        try:
+            mc.mc_group_set_shapes(g, row=shape)
+            mc.mc_group_sweep(g, 5)
+            mc.mc_group_sweep(g, 6, measure=True)
+            mc.mc_group_sync(g)
+            got = [(mc.mc_get_spins(h, int(np.prod(d))), mc.mc_measure(h).asdict(), mc.mc_get_theta(h),
+                    mc.mc_samples(h, 16)) for h, d in zip(hs, dims)]
+        finally:
+            mc.mc_group_destroy(g)
+            for h in hs:
+                mc.mc_destroy(h)
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(ref, got):
+            assert np.array_equal(a[0], b[0]), shape
+            assert a[1] == b[1] and a[2] == b[2], shape
+            assert np.array_equal(a[3], b[3]), shape
+    with pytest.raises(mc.MCError):
+        hs = [mc.mc_create_ex(mc.make_desc((16, 16, 16)))]
+        g = mc.mc_group_create(hs)
+        try:
+            mc.mc_group_set_shapes(g, row=2)
+        finally:
+            mc.mc_group_destroy(g)
+            mc.mc_destroy(hs[0])
