@@ -716,3 +716,63 @@ def test_film_1024x1024x15_full_size_fp64_bit_exact():
         assert_same_samples(h, o, 1)
     finally:
         mc.mc_destroy(h)
+
+
+# ---------------------------------------------- degenerate cone angles
+@pytest.mark.parametrize("T,theta0,limit", [(60.0, 176, 180), (1e-4, 4, 1)])
+def test_fp64_cone_at_its_limits_bit_exact(T, theta0, limit):
+    """Table A1's cone rule at its ends: far above T_C nearly every move is
+    accepted and theta climbs to 180 degrees (the trial point is uniform on
+    the whole sphere) and stays; near T = 0 nearly every move is rejected and
+    theta falls to 1 degree.  The GPU follows the oracle bit for bit there."""
+    dims = (24, 6, 4)
+    h, o = make_pair(dims, Ku=0.05, Kc=0.02, H=(0.0, 0.01, 0.03), T=T, seed=13, theta0=theta0, ring=64)
+    try:
+        mc.mc_sweep(h, 30)
+        o.sweep(30)
+        mc.mc_sweep(h, 40, measure=True)
+        o.sweep(40, measure=True)
+        assert_same_state(h, o, f"T = {T}")
+        assert_same_samples(h, o, 40)
+        assert_same_stats(h, o)
+        assert mc.mc_get_theta(h)[0] == limit
+    finally:
+        mc.mc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [mc.MC_FP64, mc.MC_FP32])
+def test_cone_frozen_in_measurement_sweeps(prec):
+    """adapt_in_measure = 0: the cone angle adapts in the unmeasured sweeps
+    only; FP64 follows the oracle bit for bit, FP32 keeps the angle of the
+    last unmeasured sweep through every sample."""
+    dims = (64, 6, 4)
+    h, o = make_pair(dims, prec=prec, Ku=0.02, T=0.9, seed=4, theta0=60, adapt=0, ring=64)
+    try:
+        mc.mc_sweep(h, 12)
+        theta = mc.mc_get_theta(h)[0]
+        mc.mc_sweep(h, 25, measure=True)
+        s = mc.mc_samples(h, 25)
+        assert np.all(s["theta_deg"] == theta)
+        if prec == mc.MC_FP64:
+            o.sweep(12)
+            o.sweep(25, measure=True)
+            assert_same_state(h, o, "frozen cone")
+            assert_same_samples(h, o, 25)
+    finally:
+        mc.mc_destroy(h)
+
+
+def test_fp32_spins_stay_unit_at_the_cone_limits():
+    """FP32 renormalises every trial point: after sweeps with theta at 180
+    and at 1 degree every spin has unit length to FP32 accuracy."""
+    for T, theta0 in ((60.0, 176), (1e-4, 4)):
+        dims = (128, 8, 8)
+        h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.05, T=T, seed=2, theta0_deg=theta0, ring_capacity=8))
+        try:
+            mc.mc_sweep(h, 40, measure=True)
+            S = mc.mc_get_spins(h, dims[0] * dims[1] * dims[2])
+            n = np.linalg.norm(S, axis=1)
+            assert np.all(np.abs(n - 1.0) < 2e-6), float(np.max(np.abs(n - 1.0)))
+            assert mc.mc_get_theta(h)[0] == (180 if T > 1 else 1)
+        finally:
+            mc.mc_destroy(h)
