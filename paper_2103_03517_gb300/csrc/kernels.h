@@ -27,8 +27,10 @@ struct KernelSet {
                         cudaStream_t s);
     // FP32 colour pass over lattices in the row layout (adjacent site pairs
     // per lane); gen = 0: all axes periodic, no film tables; gen = 1: any
-    // boundaries and film tables.  Null in the FP64 set.  Returns the
-    // status of the launch (launched with programmatic serialisation).
+    // boundaries and film tables.  Null in the FP64 set.  After an
+    // unmeasured black pass (colour 1) it also launches the close of the
+    // lattices' sweeps (row_close_kernel).  Returns the status of the
+    // launches (made with programmatic serialisation).
     cudaError_t (*row_pass)(const GroupArgs& g, uint32_t ntiles, const void* cone, int colour, int measure,
                             int gen, int shape, cudaStream_t s);
     // Table A2 pair pass over sub-set (sub, colour) (sub = 0 for simple cubic
