@@ -838,6 +838,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
              ("128c_x16_wavefront", [128] * 16, mc.MC_PATH_WAVE)]
     out = {}
     for name, sizes, path in cases:
+        torch.cuda.nvtx.range_push(f"cubes_{name}")  # lets a profiler select one case
         hs = [mc.mc_create_ex(mc.make_desc((L, L, L), K_u=0.01, T=0.5 + 0.05 * i, seed=100 + i,
                                            ring_capacity=16, sample_torque=0, stream=stream.cuda_stream,
                                            device=dev, kernel_path=path)) for i, L in enumerate(sizes)]
@@ -868,6 +869,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
         mc.mc_group_destroy(g)
         for h in hs:
             mc.mc_destroy(h)
+        torch.cuda.nvtx.range_pop()
     return {"cubes": {"unit": UNIT, "peak_gbs": peak, "cases": out,
                       "workload": f"periodic FP32 cubes, {sweeps} sweeps timed per mode; sweep_frac = updates/s x "
                                   "24 B / measured HBM peak over the timed sweeps; frac = one launch timed alone "
