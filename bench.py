@@ -10,7 +10,7 @@ colour pass.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--side all|none|fp64|constrained|anisotropy|cubes|general|stiffness|films|precision|
-                               serving|torque|wall|wave|slabs]
+                               serving|torque|wall|wave|slabs|paper]
                        [--no-cpu]
 Under torchrun (N > 1) the ranks split the batch: each lattice runs on one
 rank, shares balanced by spins (strong scaling, no collective on the data
@@ -460,6 +460,8 @@ def secondary(mc, torch, stream, dev, side="all", tune=True):
         out.update(wall_study(stream, dev))
     if side in ("all", "slabs"):
         out.update(slabs_side(mc, torch, stream, dev))
+    if side == "paper":  # not in "all": about ten minutes
+        out.update(paper_size(mc, torch, stream, dev))
     return out
 
 
@@ -745,6 +747,51 @@ def films(mc, torch, stream, dev):
                       "temperatures": temps, "results": out}}
 
 
+def paper_size(mc, torch, stream, dev):
+    """The two studies of the paper at its own sizes and run lengths (not part
+    of `--side all`: about ten minutes of GPU time).
+
+    * Table I (Sec. 3): 5 K/J x 7 T, a 256 x 128 x 128 wall (x anti-periodic,
+      4.2M spins, as many as the paper's 160^3 mesh) and a 128^3 uniform
+      lattice per point, 10,000 + 40,000 sweeps (the paper's 50,000 steps),
+      a profile fit every 100 sweeps; A(T) and the exponent of A ~ m^k.
+    * Granular films (Sec. 4): 768 x 768 x Lz, Lz = 4, 8, 16, 24 (the paper's
+      1 - 6 nm), Voronoi grains of mean diameter 20, 40, 80 and 160 sites (its
+      5 - 40 nm), K_u = 0.02 random axes, T = 0.1 .. 1.7, 1500 + 3000 sweeps,
+      a grain sample every 20; T_C of the continuous film of each thickness
+      (Eq. 3) and the average T_C of the granular films (Eq. 8)."""
+    from paper_2103_03517_gb300.studies import exchange_stiffness_study, film_curie_study
+    table1 = [8.33e-3, 1.67e-2, 2.5e-2, 3.33e-2, 4.2e-2]
+    temps = [0.2, 0.35, 0.5, 0.65, 0.8, 0.95, 1.1]
+    r = exchange_stiffness_study(table1, temps, wall_dims=(256, 128, 128), uniform_dims=(128, 128, 128),
+                                 n_eq=10000, n_meas=40000, every=100, stream=stream.cuda_stream, device=dev)
+    t1 = {"workload": "Table I: 5 K/J x 7 T, wall 256x128x128 (x anti-periodic) + uniform 128^3 per point, FP32, "
+                      "10000 + 40000 sweeps, profile fit every 100 sweeps",
+          "k": {f"{K:.4g}": [round(v[0], 3), round(v[1], 3)] for K, v in r["exponents"].items()},
+          "paper_k": {"0.00833": 1.48, "0.0167": 1.55, "0.025": 1.75, "0.0333": 1.75, "0.042": 1.79},
+          "seconds": round(r["seconds"], 1), "updates_per_s": r["updates"] / r["seconds"],
+          "points": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in x.items()} for x in r["rows"]]}
+    ftemps = [round(0.1 * i, 2) for i in range(1, 18)]
+    kw = dict(n_eq=1500, n_meas=3000, stream=stream.cuda_stream, device=dev)
+    films_out = {}
+    for Lz in (4, 8, 16, 24):
+        dims = (768, 768, Lz)
+        c = film_curie_study(dims, None, None, None, ftemps, **kw)
+        row = {"continuous": {"T_C": round(c["fit"]["T_C"], 4), "beta": round(c["fit"]["beta"], 3),
+                              "seconds": round(c["seconds"], 1)}}
+        for d in (20, 40, 80, 160):
+            gid, mask, axes = workloads.voronoi_film(768, 768, Lz, float(d), seed=d + Lz)
+            g = film_curie_study(dims, gid, mask, axes, ftemps, beta=c["fit"]["beta"], **kw)
+            row[f"grains_d{d}"] = {"grains": int(gid.max()) + 1, "T_C_mean": round(g["fit"]["T_C_mean"], 4),
+                                   "rms": round(g["fit"]["rms"], 5), "m": [round(x, 4) for x in g["m"]],
+                                   "seconds": round(g["seconds"], 1)}
+            del gid, mask, axes
+        films_out[f"Lz{Lz}"] = row
+    return {"paper_size": {"table1": t1, "films": {
+        "workload": "768x768xLz films, Lz = 4, 8, 16, 24; Voronoi grains d = 20, 40, 80, 160; T = 0.1..1.7 "
+                    "(17 points), 1500 + 3000 sweeps, FP32", "temperatures": ftemps, "results": films_out}}}
+
+
 def precision(mc, torch, stream, dev):
     """FP32 against FP64, so that each FP32 result's error is stated.  The
     16^3 point (K_u = 0.01, T = 0.5, 1000 + 1000 sweeps) over 8 seeds per
@@ -1006,7 +1053,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (same as --side none)")
     ap.add_argument("--side", default="all",
                     choices=["all", "none", "fp64", "constrained", "anisotropy", "cubes", "general", "stiffness", "films",
-                             "precision", "serving", "torque", "wall", "wave", "slabs"],
+                             "precision", "serving", "torque", "wall", "wave", "slabs", "paper"],
                     help="which side measurements to add to the line")
     args = ap.parse_args()
     if args.warmup < 3:
