@@ -40,6 +40,7 @@ METRIC = "spin-updates/s & HBM roofline frac (128^3 FP32); served m(T) req/s, p5
 UNIT = "spin-updates/s"
 # launch shapes of the FP32 row kernel (mc_group_autotune's row candidates)
 ROW_SHAPES = ["3 blocks per SM", "2 blocks per SM"]
+RESIDENT_SHAPES = ["blocks of 512 threads", "blocks of 640 threads"]
 BYTES_PER_UPDATE = 24          # FP32: read + write 3 x 4 B of every spin once per sweep
 FALLBACK_HBM_GBS = 6800.0
 LATSTATE_BYTES = 400           # device state block read back by mc_measure
@@ -873,14 +874,17 @@ def precision(mc, torch, stream, dev):
 
 def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
     """The standard FP32 sweep on periodic cubes alone: one 128^3 lattice
-    (25 MB of spins, L2-resident), sixteen 128^3 lattices in one group
-    (403 MB, HBM-resident) and one 256^3 lattice (201 MB).  K_u = 0.01 z,
-    T = 0.5 .. 1.25, all +z.  Per case: spin-updates/s over measured sweeps
-    (CUDA events around the replayed graphs), and the colour pass timed
-    launch by launch against the HBM roofline (24 B per update)."""
+    (25 MB of spins, L2-resident) on row passes and held in shared memory
+    (resident sweeps), sixteen 128^3 lattices in one group (403 MB,
+    HBM-resident) and one 256^3 lattice (201 MB).  K_u = 0.01 z, T = 0.5 ..
+    1.25, all +z.  Per case: spin-updates/s over unmeasured and measured
+    sweeps (CUDA events around the calls), and one launch timed alone
+    against the HBM roofline (24 B per update): a colour pass, a wavefront
+    sweep, or a resident launch of 100 sweeps."""
     peak, _ = measured_peak()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cases = [("128c_single", [128], mc.MC_PATH_AUTO), ("128c_x16", [128] * 16, mc.MC_PATH_AUTO),
+    cases = [("128c_single", [128], mc.MC_PATH_AUTO), ("128c_single_resident", [128], mc.MC_PATH_RESIDENT),
+             ("128c_x16", [128] * 16, mc.MC_PATH_AUTO),
              ("256c_single", [256], mc.MC_PATH_AUTO), ("128c_single_wavefront", [128], mc.MC_PATH_WAVE),
              ("128c_x16_wavefront", [128] * 16, mc.MC_PATH_WAVE)]
     out = {}
@@ -894,7 +898,8 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
         n = sum(L ** 3 for L in sizes)
         mc.mc_group_sweep(g, 20, measure=True)
         torch.cuda.synchronize()
-        res = {"spins": n, "row_shape": ROW_SHAPES[tuned["row"]] if tuned else ROW_SHAPES[0]}
+        shapes = RESIDENT_SHAPES if path == mc.MC_PATH_RESIDENT else ROW_SHAPES
+        res = {"spins": n, "row_shape": shapes[tuned["row"]] if tuned else shapes[0]}
         for meas in (False, True):
             a.record(stream)
             mc.mc_group_sweep(g, sweeps, measure=meas)
@@ -903,13 +908,16 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
             rate = n * sweeps / (a.elapsed_time(b) * 1e-3)
             res["measured" if meas else "unmeasured"] = rate
             res["sweep_frac_measured" if meas else "sweep_frac"] = round(rate * BYTES_PER_UPDATE / 1e9 / peak, 4)
-            # one launch timed alone: a wavefront sweep (128-wide lattices) or a colour pass
+            # one launch timed alone: a resident launch of 100 sweeps, a
+            # wavefront sweep (128-wide lattices) or a colour pass
             kms, kn = mc.mc_group_time_kernels(g, 100, measure=meas)
-            wave = kn[0] > 0
-            avg_ms = kms[0] if wave else kms[1]
-            per_launch = (n if wave else n // 2) * BYTES_PER_UPDATE
+            wave, resident = kn[0] > 0, kn[3] > 0
+            avg_ms = kms[3] if resident else (kms[0] if wave else kms[1])
+            per_launch = (n * 100 if resident else (n if wave else n // 2)) * BYTES_PER_UPDATE
             gbs = per_launch / (avg_ms * 1e-3) / 1e9
-            res["kernel"] = "wave_sweep_kernel (one sweep per launch)" if wave else "row_pass_kernel (one colour per launch)"
+            res["kernel"] = ("resident_sweep_kernel (100 sweeps per launch)" if resident else
+                             "wave_sweep_kernel (one sweep per launch)" if wave else
+                             "row_pass_kernel (one colour per launch)")
             res["launch_ms_measured" if meas else "launch_ms"] = round(avg_ms, 5)
             res["frac_measured" if meas else "frac"] = round(gbs / peak, 4)
         out[name] = res

@@ -75,13 +75,20 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * call run two at a time as single wavefront launches (red and black pass
  * fused, each spin read and written once per sweep; the lattice then holds
  * a second spin buffer, and an odd last sweep of a call runs as two row
- * passes).  The colour passes of AUTO, GENERAL and WAVE agree up to FP32
- * rounding (the draws are keyed to the same sites; the wavefront and row
- * kernels bit for bit) and the two pair orders exactly; GENERAL, ROW and
- * WAVE exist to compare them.  FP64 lattices always take the general kernel
- * and pair order. */
+ * passes).  RESIDENT is AUTO, except that an all-periodic lattice with
+ * Lx = 128 (no film tables) whose rows fit the SMs' shared memory (about
+ * 30 MB of spins on 152 SMs, e.g. 128^3) sweeps, when it runs alone
+ * (mc_sweep, or a group of that one lattice), held in shared memory: one
+ * cooperative launch per run of up to 2048 unconstrained sweeps, one block
+ * per brick of rows, the blocks waiting on their neighbours between colour
+ * passes and on all blocks between sweeps (each wait bounded; a wait that
+ * runs out gives MC_ERR_TIMEOUT).  The colour passes of AUTO, GENERAL,
+ * WAVE and RESIDENT agree up to FP32 rounding (the draws are keyed to the
+ * same sites; the wavefront, resident and row kernels bit for bit) and the
+ * two pair orders exactly; GENERAL, ROW, WAVE and RESIDENT exist to compare
+ * them.  FP64 lattices always take the general kernel and pair order. */
 typedef enum mc_kernel_path {
-    MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1, MC_PATH_ROW = 2, MC_PATH_WAVE = 3
+    MC_PATH_AUTO = 0, MC_PATH_GENERAL = 1, MC_PATH_ROW = 2, MC_PATH_WAVE = 3, MC_PATH_RESIDENT = 4
 } mc_kernel_path;
 
 /* Crystal structure (Sec. 2).  SC: the simple cubic lattice, sites at the
@@ -322,13 +329,16 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
 
 /* The same, by kind: avg_ms[0] / launches[0] for the wavefront launches
  * (one sweep of the lattices that take them), [1] for the colour passes of
- * the row and general kernels, [2] for the pair passes of Table A2.  With
+ * the row and general kernels, [2] for the pair passes of Table A2, [3] for
+ * the resident launches (MC_PATH_RESIDENT: each runs up to 2048 of the
+ * n_sweeps sweeps, so a launch's time per sweep is avg_ms[3] times
+ * launches[3] over n_sweeps).  With
  * constrained != 0 the sweeps are constrained sweeps about each lattice's
  * last constraint direction (MC_ERR_STATE before any constrained sweep of
  * the group).  A kind with no launch reads 0 ms.  Measurement support
  * around the paper's method; the paper has no counterpart.  Synchronises. */
-MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[3],
-                                 int launches[3]);
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[4],
+                                 int launches[4]);
 
 /* Ensemble averages of every lattice of the group (Sec. 3, Eq. 6), as
  * mc_measure gives them, read with one wait on the group stream instead of
@@ -348,6 +358,8 @@ MC_API int mc_group_sync(mc_group_handle g);
  * a persistent launch).  Candidates, in the order of the report's arrays:
  *   row:   FP32 row kernel, minimum resident blocks per SM (so registers per
  *          thread): all-periodic lattices {3, 2}, boundaries and films {2, 3};
+ *          a lattice swept resident (MC_PATH_RESIDENT): threads per block
+ *          {512, 640};
  *   field: constrained neighbour-field kernel, tiles per grid-stride step
  *          {4, 8, 2};
  *   pair:  constrained pair pass, the same {4, 8, 2}, then 4 tiles per step

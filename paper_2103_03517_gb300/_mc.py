@@ -19,7 +19,7 @@ MC_ERR_ARG, MC_ERR_NOMEM, MC_ERR_CUDA, MC_ERR_TIMEOUT, MC_ERR_CONSTRAINT, MC_ERR
 MC_ERR_CANCELLED = -8
 MC_FP32, MC_FP64 = 0, 1
 MC_PERIODIC, MC_OPEN, MC_PINNED, MC_ANTIPERIODIC = 0, 1, 2, 3
-MC_PATH_AUTO, MC_PATH_GENERAL, MC_PATH_ROW, MC_PATH_WAVE = 0, 1, 2, 3
+MC_PATH_AUTO, MC_PATH_GENERAL, MC_PATH_ROW, MC_PATH_WAVE, MC_PATH_RESIDENT = 0, 1, 2, 3, 4
 MC_SC, MC_BCC, MC_FCC, MC_HCP = 0, 1, 2, 3
 MC_INIT_UNIFORM, MC_INIT_WALL = 0, 1
 MC_TUNE_SWEEP, MC_TUNE_CONSTRAINED = 1, 2
@@ -407,10 +407,11 @@ def mc_group_time_passes(g, n_sweeps: int, measure: bool = False):
 
 
 def mc_group_time_kernels(g, n_sweeps: int, measure: bool = False, constrained: bool = False):
-    """Per launch kind (wavefront sweeps, colour passes, pair passes): the
-    mean launch duration in ms and the number of launches timed."""
-    ms = (C.c_double * 3)()
-    n = (C.c_int * 3)()
+    """Per launch kind (wavefront sweeps, colour passes, pair passes,
+    resident launches of up to 2048 sweeps): the mean launch duration in ms
+    and the number of launches timed."""
+    ms = (C.c_double * 4)()
+    n = (C.c_int * 4)()
     _check(lib().mc_group_time_kernels(g, int(n_sweeps), int(bool(measure)), int(bool(constrained)), ms, n))
     return list(ms), list(n)
 

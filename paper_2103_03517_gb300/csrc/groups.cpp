@@ -126,6 +126,7 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
                               int(sub[c].size())};
         *counts[c] = st[c].back();
     }
+    if (n == 1) g->ls.res = lattices[0]->res;  // a resident lattice alone
     g->ls.sample_level = 1;
     for (int i = 0; i < n; ++i)
         if (lattices[i]->hp.sample_torque) g->ls.sample_level = 2;
@@ -239,8 +240,8 @@ MC_API int mc_group_time_passes(mc_group_handle g, int n_sweeps, int measure, do
     return MC_OK;
 }
 
-MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[3],
-                                 int launches[3]) {
+MC_API int mc_group_time_kernels(mc_group_handle g, int n_sweeps, int measure, int constrained, double avg_ms[4],
+                                 int launches[4]) {
     if (!g || n_sweeps < 1 || !avg_ms || !launches) return fail(MC_ERR_ARG, "invalid argument");
     for (mc_handle h : g->lats)
         if (constrained && !h->d_aos) return fail(MC_ERR_STATE, "no constrained sweep has set the constraint yet");

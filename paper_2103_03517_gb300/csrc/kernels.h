@@ -10,13 +10,24 @@ namespace mcgb {
 // Launch shapes the autotuner chooses among: an index into each kernel's
 // candidate list (0 = the default, measured best on the batched workloads).
 //   row:   FP32 row kernel, minimum resident blocks per SM (registers per
-//          thread): all-periodic {3, 2}, boundaries and films {2, 3};
+//          thread): all-periodic {3, 2}, boundaries and films {2, 3}; for a
+//          resident lattice, threads per block {512, 640};
 //   pair:  pair pass, consecutive tiles per grid-stride step {4, 8, 2}, and
 //          4 with one more resident block per SM;
 //   field: neighbour-field kernel, the same {4, 8, 2}.
 constexpr int kRowShapes = 2, kPairShapes = 4, kFieldShapes = 3;
 struct LaunchShape {
     int row = 0, pair = 0, field = 0;
+};
+
+// A resident lattice's launch: its arguments and two TMA descriptors
+// (CUtensorMap, 128 bytes each) of its spins seen as a 64 x Ly x Lz x 6
+// array (x, y, z, colour and component), with the boxes of a y face (64 x 1
+// x bz x 3) and of a z face (64 x by x 1 x 3) of a brick.
+struct alignas(128) ResidentPlan {
+    unsigned char map_y[128];
+    unsigned char map_z[128];
+    ResidentArgs args;
 };
 
 struct KernelSet {
@@ -89,6 +100,17 @@ struct KernelSet {
     cudaError_t (*slab_halo)(float* const (*dst)[2], const float* const (*src)[2], const uint32_t* stride,
                              const uint32_t (*src_stride)[2], uint32_t plane, int n, cudaStream_t s);
     cudaError_t (*slab_close_all)(LatDev* const* lats, int n, int measure, cudaStream_t s);
+    // Resident sweeps (resident_pass.cuh) of the lattice of a plan: n sweeps
+    // in cooperative launches of at most kResMaxSweeps, measure as for
+    // colour_pass, shape 0 or 1 (blocks of 512 or 640 threads).  Null in the
+    // FP64 set.  Returns the status of the launches.
+    cudaError_t (*resident_sweeps)(const ResidentPlan& r, const void* cone, int n, int measure, int shape,
+                                   cudaStream_t s);
+    // The brick split of FP32 lattice p (host copy: dims, stride, spins) on
+    // the current device and the tensor maps of its halo faces: fills
+    // everything but args.lat and args.ctl; false when its rows do not fit
+    // the SMs' shared memory.  Null in the FP64 set.
+    bool (*resident_plan)(const LatParams& p, ResidentPlan* out);
 };
 
 // Launch tables of a set of lattices: site tiles and pair tiles of every
@@ -109,6 +131,10 @@ struct LaunchSet {
     uint32_t nb_wave = 0;
     GroupArgs row_rest;
     uint32_t nt_row_rest = 0;
+    // a resident lattice alone (LatParams::rctl): its launch plan, owned by
+    // the lattice (null: none); its unconstrained sweeps run as resident
+    // launches
+    const ResidentPlan* res = nullptr;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
     // a bcc / fcc lattice alone: its descriptor and sub-lattice count, else null
     LatDev* xtal = nullptr;

@@ -16,11 +16,14 @@
 #ifndef MC_PAIR_CHUNK_LEAD
 #define MC_PAIR_CHUNK_LEAD 4
 #endif
+#include <algorithm>
+
 #include "kernels.h"
 #include "pass_impl.cuh"
 #include "xtal_pass.cuh"
 #include "row_pass.cuh"
 #include "wave_pass.cuh"
+#include "resident_pass.cuh"
 
 namespace mcgb {
 namespace {
@@ -168,6 +171,146 @@ uint32_t wave_blocks() {
     return uint32_t(sms) * uint32_t(per_sm);
 }
 
+// Resident sweeps: shape 0 = blocks of 512 threads (16 warps, up to 128
+// registers), 1 = 640 threads (20 warps, up to 96 registers; 768 threads
+// would spill at 80); one block per SM, opted in to the shared memory of the
+// largest brick.
+template <int NT, int MEASURE>
+bool resident_opt_in() {
+    static const bool ok = [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(resident_sweep_kernel<NT, MEASURE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - int(kResStaticSmem)) == cudaSuccess;
+    }();
+    return ok;
+}
+
+template <int NT, int MEASURE>
+cudaError_t resident_t(const ResidentPlan& r, const ResidentArgs& a, const R* cone, cudaStream_t s) {
+    if (!resident_opt_in<NT, MEASURE>()) return cudaErrorInvalidConfiguration;
+    // cooperative: the launch fails rather than run with a block not resident,
+    // since the blocks wait for one another at the grid barriers
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(uint32_t(a.nyc * a.nzc));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = a.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resident_sweep_kernel<NT, MEASURE>, a,
+                              *reinterpret_cast<const CUtensorMap*>(r.map_y),
+                              *reinterpret_cast<const CUtensorMap*>(r.map_z), cone);
+}
+
+template <int NT>
+cudaError_t resident_m(const ResidentPlan& r, const ResidentArgs& a, const R* cone, int measure, cudaStream_t s) {
+    if (measure >= 2) return resident_t<NT, 2>(r, a, cone, s);
+    if (measure == 1) return resident_t<NT, 1>(r, a, cone, s);
+    return resident_t<NT, 0>(r, a, cone, s);
+}
+
+// n sweeps in launches of at most kResMaxSweeps, each after its control
+// words are zeroed
+cudaError_t resident_sweeps(const ResidentPlan& r, const void* cone, int n, int measure, int shape, cudaStream_t s) {
+    const R* c = static_cast<const R*>(cone);
+    for (int done = 0; done < n;) {
+        ResidentArgs a = r.args;
+        a.n_sweeps = n - done < kResMaxSweeps ? n - done : kResMaxSweeps;
+        cudaError_t e = cudaMemsetAsync(a.ctl, 0, sizeof(ResCtl), s);
+        if (e == cudaSuccess)
+            e = shape == 1 ? resident_m<640>(r, a, c, measure, s) : resident_m<512>(r, a, c, measure, s);
+        if (e != cudaSuccess) return e;
+        done += a.n_sweeps;
+    }
+    return cudaSuccess;
+}
+
+// cuTensorMapEncodeTiled, taken from the driver at run time (the library
+// links the CUDA runtime only).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// The bricks of a resident lattice of Ly x Lz rows on the current device:
+// the split (nyc, nzc) with the fewest rows in the largest brick, then the
+// fewest halo rows, then the fewest blocks, among those with one block per
+// SM at most whose brick fits a block's shared memory (both launch shapes
+// must keep a block resident).  Then the tensor maps of the halo faces: the
+// spins as a 64 x Ly x Lz x 6 array of floats (x, y, z, 3 colour + component;
+// strides 256 B, 256 Ly B, 4 stride B).  False if no split fits or a map
+// cannot be made.
+bool resident_plan(const LatParams& p, ResidentPlan* r) {
+    const int Ly = p.Ly, Lz = p.Lz;
+    ResidentArgs* out = &r->args;
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const long long cap = (long long)optin - (long long)kResStaticSmem;
+    long long best[3] = {0, 0, 0};
+    bool found = false;
+    for (int nyc = 1; nyc <= Ly && nyc <= sms; ++nyc)
+        for (int nzc = 1; nzc <= Lz && nyc * nzc <= sms && nyc * nzc <= kResMaxBlocks; ++nzc) {
+            const int by = (Ly + nyc - 1) / nyc, bz = (Lz + nzc - 1) / nzc;
+            if (by > 255 || bz > 255) continue;
+            const uint32_t smem = resident_smem_bytes(by, bz, nyc, nzc);
+            if ((long long)smem > cap) continue;
+            const long long key[3] = {(long long)by * bz, (long long)resident_halo_rows(by, bz, nyc, nzc),
+                                      (long long)nyc * nzc};
+            if (!found || std::lexicographical_compare(key, key + 3, best, best + 3)) {
+                found = true;
+                std::copy(key, key + 3, best);
+                *out = ResidentArgs{};
+                out->nyc = nyc;
+                out->nzc = nzc;
+                out->by = by;
+                out->bz = bz;
+                out->smem = smem;
+            }
+        }
+    if (!found) return false;
+    int per_sm = 0;
+    if (!resident_opt_in<512, 0>() || !resident_opt_in<640, 0>()) return false;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_sweep_kernel<640, 0>, 640, out->smem);
+    if (per_sm < 1) return false;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_sweep_kernel<512, 0>, 512, out->smem);
+    if (per_sm < 1) return false;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dim[4] = {cuuint64_t(kResLh), cuuint64_t(Ly), cuuint64_t(Lz), 6};
+    const cuuint64_t strides[3] = {cuuint64_t(kResLh) * 4, cuuint64_t(kResLh) * 4 * cuuint64_t(Ly),
+                                   cuuint64_t(p.stride) * 4};
+    const cuuint32_t box_y[4] = {cuuint32_t(kResLh), 1, cuuint32_t(out->bz), 3};
+    const cuuint32_t box_z[4] = {cuuint32_t(kResLh), cuuint32_t(out->by), 1, 3};
+    const cuuint32_t unit[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult e = enc(reinterpret_cast<CUtensorMap*>(k == 0 ? r->map_y : r->map_z),
+                               CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.spins, dim, strides, k == 0 ? box_y : box_z,
+                               unit, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (e != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
 void slab_export(LatDev* L, cudaStream_t s) { slab_export_kernel<<<1, 32, 0, s>>>(L); }
 
 void slab_close(LatDev* L, int measure, cudaStream_t s) { slab_close_kernel<<<1, 32, 0, s>>>(L, measure); }
@@ -207,7 +350,7 @@ const KernelSet& kernels_f32() {
                              ml_reset,    mlong,       measure,     row_sample,        xtal_pass,
                              xtal_sample, xtal_field_launch, grain_sample, profile, "f32",
                              wave_sweep,  wave_blocks, slab_export,       slab_close,   slab_halo,
-                             slab_close_all};
+                             slab_close_all, resident_sweeps, resident_plan};
     return k;
 }
 

@@ -40,7 +40,7 @@ const KernelSet& kernels_f64() {
                              ml_reset,    mlong,       measure,     nullptr,           xtal_pass,
                              xtal_sample, xtal_field_launch, grain_sample, profile, "f64",
                              nullptr,     nullptr,     nullptr,           nullptr,      nullptr,
-                             nullptr};
+                             nullptr,     nullptr,     nullptr};
     return k;
 }
 

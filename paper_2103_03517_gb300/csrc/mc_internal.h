@@ -114,6 +114,7 @@ struct LatParams {
     int wave;               // FP32 all-periodic lattice of rows of Lh = 64 sites per
                             // colour and Ly a multiple of 16: its sweeps may run as
                             // one wavefront launch (wave_sweep_kernel)
+    void* rctl;             // resident lattices: their ResCtl, else null
     const uint8_t* bonds;   // [2][stride] or null
     const int32_t* grain;   // [2][stride] or null
     const void* gaxis;      // [n_grains][4] in the lattice precision, or null
@@ -200,6 +201,44 @@ struct WaveArgs {
     const uint32_t* off;
     const uint32_t* nwu;
     int n;
+    int inject;
+};
+
+// Resident sweeps (resident_pass.cuh): a lattice with rows of kResLh colour
+// indices (Lx = 128) held in the shared memory of one block per brick of
+// rows for a whole run of sweeps.
+constexpr int kResLh = 64;
+constexpr int kResMaxSweeps = 2048;  // sweeps per launch; longer runs take several
+
+// Control words of one lattice's resident launch, in device memory, zeroed
+// before every launch: the abort flag a block sets when one of its waits
+// runs out; for sweep s, in slot s mod 3 (one slot fills, one is read, one
+// is cleared), the blocks that have completed their black pass (high 32
+// bits) and their accepted moves (low 32 bits) in one word, and the
+// fixed-point sample sums; per block, the passes whose face rows it has
+// written.
+constexpr int kResMaxBlocks = 256;
+constexpr int kResSlots = 3;
+struct ResCtl {
+    int abort;
+    int pad;
+    unsigned long long arrive_acc[kResSlots];
+    long long sums[kResSlots][kNumSums];
+    unsigned int done[kResMaxBlocks];
+};
+
+// A resident launch: nyc x nzc blocks, block b holding the rows [y0, y1) x
+// [z0, z1) of its brick (y split into nyc near-equal parts, z into nzc);
+// by, bz = the largest brick extents, which size the shared memory (smem
+// bytes per block); n_sweeps sweeps; inject: an extra arrival the first
+// grid barrier waits for (0 in normal runs; a host-set fault that makes
+// that wait run out).
+struct ResidentArgs {
+    LatDev* lat;
+    ResCtl* ctl;
+    int nyc, nzc, by, bz;
+    uint32_t smem;
+    int n_sweeps;
     int inject;
 };
 

@@ -420,13 +420,17 @@ __device__ __forceinline__ long long warp_tile_fix(const Sums<R>& s, int lane) {
 // End of a sweep (Table A1 / A2, after the black pass): the cone adaptation
 // and the carried M_L on one thread; returns the sweep's accepted count.
 // ------------------------------------------------------------------------
+// The cone rule of Table A1: theta one degree up when more than half of the
+// movable sites accepted, else one degree down, within [1, 180].
+__device__ __forceinline__ int cone_rule(int theta, long long acc, long long n_mov) {
+    if (2 * acc > n_mov) return theta < 180 ? theta + 1 : theta;
+    return theta > 1 ? theta - 1 : theta;
+}
+
 __device__ inline long long close_counts(const LatParams& p, LatState& st, int measure, long long n_mov) {
     const long long acc = (long long)atomicExch(&st.acc, 0ull);
     st.last_acc = acc;
-    if (!measure || p.adapt_in_measure) {
-        if (2 * acc > n_mov) { if (st.theta < 180) st.theta += 1; }
-        else { if (st.theta > 1) st.theta -= 1; }
-    }
+    if (!measure || p.adapt_in_measure) st.theta = cone_rule(st.theta, acc, n_mov);
     st.ml_hi += st.dml_hi;  // M_L of the next sweep (exact: integer sums)
     st.ml_lo += st.dml_lo;
     st.dml_hi = 0;

@@ -202,6 +202,18 @@ bool wave_desc(const mc_desc* d) {
     return d->dims[0] == 2 * kWaveLh && d->dims[1] >= kWaveMinLy;
 }
 
+// Lattices whose sweeps may run held in shared memory (resident_pass.cuh):
+// FP32 simple cubic, every axis periodic, no film tables, rows of 64 sites
+// per colour (Lx = 128), not a slab, the resident kernel path asked for;
+// whether its rows fit is decided on the device (KernelSet::resident_plan).
+bool resident_desc(const mc_desc* d, bool slab) {
+    if (slab || d->precision != MC_FP32 || d->lattice != MC_SC || d->kernel_path != MC_PATH_RESIDENT) return false;
+    if (d->bond_mask || d->grain_id) return false;
+    for (int a = 0; a < 3; ++a)
+        if (d->boundary[a] != MC_PERIODIC) return false;
+    return d->dims[0] == 2 * kResLh;
+}
+
 size_t lattice_bytes(const mc_desc* d, bool slab) {
     const uint64_t cells = uint64_t(d->dims[0]) * d->dims[1] * d->dims[2];
     const uint64_t Nc = cells / 2;
@@ -224,6 +236,7 @@ size_t lattice_bytes(const mc_desc* d, bool slab) {
     // launch tables of the lattice alone: lattice pointer, site and pair starts
     b += align256(sizeof(void*)) + 2 * align256(2 * sizeof(uint32_t));
     if (slab) b += align256(kSlabWords * 8);
+    if (resident_desc(d, slab)) b += align256(sizeof(ResCtl));
     return b;
 }
 
@@ -249,7 +262,7 @@ int validate_desc(const mc_desc* d) {
         if (d->bond_mask || d->grain_id) return fail(MC_ERR_ARG, "bcc / fcc / hcp lattices take no film tables");
         if (!std::isfinite(d->J2)) return fail(MC_ERR_ARG, "J2 not finite");
     }
-    if (d->kernel_path < MC_PATH_AUTO || d->kernel_path > MC_PATH_WAVE)
+    if (d->kernel_path < MC_PATH_AUTO || d->kernel_path > MC_PATH_RESIDENT)
         return fail(MC_ERR_ARG, "kernel_path invalid");
     if (d->theta0_deg < 1 || d->theta0_deg > 180) return fail(MC_ERR_ARG, "theta0 must be in 1..180");
     if (d->init != MC_INIT_UNIFORM && d->init != MC_INIT_WALL) return fail(MC_ERR_ARG, "init invalid");
@@ -503,6 +516,22 @@ int create_lattice(const mc_desc* din, mc_handle* out, const SlabSpec* slab) {
     h->d_group_start = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
     h->d_group_start_pair = reinterpret_cast<uint32_t*>(take(2 * sizeof(uint32_t)));
     if (slab) p.slab_counts = reinterpret_cast<long long*>(take(kSlabWords * 8));
+    if (resident_desc(d, slab != nullptr)) {  // its control words, if its rows fit the SMs
+        void* ctl = take(sizeof(ResCtl));
+        ResidentPlan* rp = new ResidentPlan();
+        if (kernels_f32().resident_plan(p, rp)) {
+            p.rctl = ctl;
+            rp->args.lat = h->d_lat;
+            rp->args.ctl = static_cast<ResCtl*>(ctl);
+            // fault injection for the tests of the bounded waits: the wait for
+            // every block's count of a sweep expects one arrival too many
+            const char* inj = std::getenv("MC_RESIDENT_INJECT_TIMEOUT");
+            rp->args.inject = inj && inj[0] == '1' ? 1 : 0;
+            h->res = rp;
+        } else {
+            delete rp;
+        }
+    }
     if (size_t(cur - static_cast<char*>(h->d_base)) > h->bytes) {
         cudaFree(h->d_base);
         if (h->owned_stream) cudaStreamDestroy(h->owned_stream);
@@ -612,6 +641,7 @@ LaunchSet single_launch_set(mc_lattice* h) {
     } else if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
+        ls.res = h->res;
         if (h->hp.wave) {
             ls.wave = h->wave_args;
             ls.nb_wave = h->wave_nblocks;
@@ -783,6 +813,16 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto timed = [&](auto&& launch) { timed_kind(constrained ? kTimedPair : kTimedPass, launch); };
+    if (!constrained && ls.res && k.resident_sweeps && n > 0) {  // all n sweeps held in shared memory
+        cudaError_t e = cudaSuccess;
+        for (int done = 0; done < n && e == cudaSuccess; done += kResMaxSweeps) {
+            const int m = std::min(n - done, kResMaxSweeps);
+            timed_kind(kTimedResident, [&] { e = k.resident_sweeps(*ls.res, cone, m, measure ? ls.sample_level : 0,
+                                                                  ls.shape.row, s); });
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "resident sweep launch");
+        return MC_OK;
+    }
     cudaError_t launch_err = cudaSuccess;  // first failed launch of the row kernels
     auto colour_pass = [&](int colour, int meas) {
         if (ls.nt_row) {
@@ -900,6 +940,8 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
 int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* cone, int n, int measure,
                bool constrained, cudaStream_t s) {
     const KernelSet& k = kernel_set(precision);
+    // resident sweeps run many to a launch: nothing to capture
+    if (!constrained && ls.res) return enqueue_sweeps(k, ls, cone, n, measure, constrained, s, nullptr);
     const int reps = n / kGraphSweeps;
     if (reps > 0) {
         cudaGraphExec_t& ex = gr.exec[constrained ? 1 : 0][measure ? 1 : 0];

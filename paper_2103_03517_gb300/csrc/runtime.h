@@ -43,6 +43,7 @@ struct mc_lattice {
     void* d_wave = nullptr;       // wavefront plan of the lattice alone (LatParams::wave)
     mcgb::WaveArgs wave_args = {};
     uint32_t wave_nblocks = 0;
+    mcgb::ResidentPlan* res = nullptr;  // resident sweeps of the lattice alone (null: none)
     mcgb::SweepGraphs graphs;     // sweeps of the lattice alone
     mcgb::LaunchShape shape;      // autotuned launch shapes of the lattice alone
     const void* cone = nullptr;   // c(theta) table of the precision
@@ -52,6 +53,10 @@ struct mc_lattice {
     std::vector<uint8_t> film_bonds;   // kept for checkpoints
     std::vector<int32_t> film_grain;
     std::vector<double> film_axes;
+    mc_lattice() = default;
+    mc_lattice(const mc_lattice&) = delete;
+    mc_lattice& operator=(const mc_lattice&) = delete;
+    ~mc_lattice() { delete res; }
 };
 
 namespace mcgb {
@@ -92,13 +97,15 @@ struct WavePlan {
     long long span = 0;
 };
 bool wave_desc(const mc_desc* d);
+bool resident_desc(const mc_desc* d, bool slab);
 WavePlan plan_wave(const std::vector<const LatParams*>& lats, uint32_t blocks);
 int upload_wave_plan(const WavePlan& pl, const std::vector<LatDev*>& dev_lats, cudaStream_t s, void** d_mem,
                      WaveArgs* out);
 // A launch bracketed by CUDA events (mc_group_time_passes / _kernels):
 // kind kTimedWave = a wavefront sweep, kTimedPass = a colour pass (row or
-// general kernels), kTimedPair = a constrained pair pass.
-enum { kTimedWave = 0, kTimedPass = 1, kTimedPair = 2, kTimedKinds = 3 };
+// general kernels), kTimedPair = a constrained pair pass, kTimedResident =
+// a resident launch (up to kResMaxSweeps sweeps).
+enum { kTimedWave = 0, kTimedPass = 1, kTimedPair = 2, kTimedResident = 3, kTimedKinds = 4 };
 struct TimedLaunch {
     cudaEvent_t a, b;
     int kind;

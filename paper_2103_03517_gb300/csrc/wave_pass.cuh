@@ -130,21 +130,21 @@ __device__ __forceinline__ float2 lds2(const float* row, int lane) {
 
 // Spins and neighbour sums of lane L's two sites (colour indices 2L, 2L + 1)
 // of one row, all rows in shared memory, packed (site 0 in .x): own (the
-// site's colour, component stride cs_own), and of the other colour the same
-// row xr and the rows -y, +y (component stride cs_xy), -z (cs_zm) and +z
-// (cs_zp).  The x neighbours and the sums are those of the row kernel: -x +
-// +x, then -y, +y, -z, +z.
-__device__ __forceinline__ void wave_pair_sums(const float* own, int cs_own, const float* xr, const float* ym,
-                                               const float* yp, int cs_xy, const float* zm, int cs_zm,
-                                               const float* zp, int cs_zp, int lane, uint32_t xoff, P3& S, P3& h,
-                                               P3& O) {
+// site's colour), and of the other colour the same row xr and the rows -y,
+// +y, -z and +z, each row with its own component stride (cs_*, floats).
+// The x neighbours and the sums are those of the row kernel: -x + +x, then
+// -y, +y, -z, +z.
+__device__ __forceinline__ void wave_pair_sums(const float* own, int cs_own, const float* xr, int cs_xr,
+                                               const float* ym, int cs_ym, const float* yp, int cs_yp,
+                                               const float* zm, int cs_zm, const float* zp, int cs_zp, int lane,
+                                               uint32_t xoff, P3& S, P3& h, P3& O) {
     float2 v[18];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         v[a] = lds2(own + a * cs_own, lane);
-        v[3 + a] = lds2(xr + a * cs_xy, lane);
-        v[6 + a] = lds2(ym + a * cs_xy, lane);
-        v[9 + a] = lds2(yp + a * cs_xy, lane);
+        v[3 + a] = lds2(xr + a * cs_xr, lane);
+        v[6 + a] = lds2(ym + a * cs_ym, lane);
+        v[9 + a] = lds2(yp + a * cs_yp, lane);
         v[12 + a] = lds2(zm + a * cs_zm, lane);
         v[15 + a] = lds2(zp + a * cs_zp, lane);
     }
@@ -303,9 +303,10 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                     int y = y0 - 1 + r;  // in [-1, Ly]
                     y = y < 0 ? y + Ly : (y >= Ly ? y - Ly : y);
                     const uint32_t xoff = uint32_t(y + zr) & 1u;
-                    wave_pair_sums(ro + r * kWaveLh, kWaveRComp, b1 + (r + 1) * kWaveLh, b1 + r * kWaveLh,
-                                   b1 + (r + 2) * kWaveLh, kWaveBComp, b0 + (r + 1) * kWaveLh, kWaveBComp,
-                                   b2 + (r + 1) * kWaveLh, kWaveBComp, lane, xoff, S, h, O);
+                    wave_pair_sums(ro + r * kWaveLh, kWaveRComp, b1 + (r + 1) * kWaveLh, kWaveBComp,
+                                   b1 + r * kWaveLh, kWaveBComp, b1 + (r + 2) * kWaveLh, kWaveBComp,
+                                   b0 + (r + 1) * kWaveLh, kWaveBComp, b2 + (r + 1) * kWaveLh, kWaveBComp, lane,
+                                   xoff, S, h, O);
                     const uint32_t row = uint32_t(y) + uint32_t(Ly) * uint32_t(zr);
                     const uint32_t site0 = xoff + 4u * uint32_t(lane) + Lx * row;
                     const uint4 w = philox_rk(make_uint4(site0, sweep, tag_of(0, kPurposeMove), 0u), K);
@@ -318,9 +319,9 @@ __global__ void __launch_bounds__(kWaveThreads, 1) wave_sweep_kernel(WaveArgs a,
                 } else {  // black row r of plane zb
                     const int y = y0 - 1 + r;
                     const uint32_t xoff = uint32_t(y + zb + 1) & 1u;
-                    wave_pair_sums(bo + (r + 1) * kWaveLh, kWaveBComp, r0 + r * kWaveLh, r0 + (r - 1) * kWaveLh,
-                                   r0 + (r + 1) * kWaveLh, kWaveRComp, rm + r * kWaveLh, kWaveRComp,
-                                   rp + r * kWaveLh, kWaveRComp, lane, xoff, S, h, O);
+                    wave_pair_sums(bo + (r + 1) * kWaveLh, kWaveBComp, r0 + r * kWaveLh, kWaveRComp,
+                                   r0 + (r - 1) * kWaveLh, kWaveRComp, r0 + (r + 1) * kWaveLh, kWaveRComp,
+                                   rm + r * kWaveLh, kWaveRComp, rp + r * kWaveLh, kWaveRComp, lane, xoff, S, h, O);
                     const uint32_t row = uint32_t(y) + uint32_t(Ly) * uint32_t(zb);
                     const uint32_t site0 = xoff + 4u * uint32_t(lane) + Lx * row;
                     const uint4 w = philox_rk(make_uint4(site0, sweep, tag_of(1, kPurposeMove), 0u), K);
