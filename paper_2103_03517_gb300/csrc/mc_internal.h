@@ -230,8 +230,8 @@ struct ResCtl {
 // A resident launch: nyc x nzc blocks, block b holding the rows [y0, y1) x
 // [z0, z1) of its brick (y split into nyc near-equal parts, z into nzc);
 // by, bz = the largest brick extents, which size the shared memory (smem
-// bytes per block); n_sweeps sweeps; inject: an extra arrival the first
-// grid barrier waits for (0 in normal runs; a host-set fault that makes
+// bytes per block); n_sweeps sweeps; inject: an extra arrival the wait for a
+// sweep's counts expects (0 in normal runs; a host-set fault that makes
 // that wait run out).
 struct ResidentArgs {
     LatDev* lat;
@@ -240,6 +240,7 @@ struct ResidentArgs {
     uint32_t smem;
     int n_sweeps;
     int inject;
+    uint32_t key0, key1;  // the lattice's Philox key, a launch constant
 };
 
 }  // namespace mcgb

@@ -145,7 +145,6 @@ __global__ void __launch_bounds__(NT, 1)
     constexpr int NW = NT / 32;
     extern __shared__ __align__(128) float rsm_raw[];
     __shared__ uint64_t hbar;                  // the halo copies of the current pass
-    __shared__ uint2 rk[10];                   // Philox round keys of the lattice
     __shared__ int claim[2];                   // next row of the pass, by pass parity
     __shared__ int fdone[2];                   // face rows moved in the pass, by pass parity
     __shared__ unsigned cta_acc;               // accepted moves of the block in the sweep
@@ -199,7 +198,6 @@ __global__ void __launch_bounds__(NT, 1)
                 }
     }
     if (tid < kNumSums) cta_sums[tid] = 0;
-    if (tid < 10) rk[tid] = make_uint2(p.key0 + uint32_t(tid) * 0x9E3779B9u, p.key1 + uint32_t(tid) * 0xBB67AE85u);
     // the brick, both colours: row component (c, r, comp) as 16 float4
     const int n4 = 2 * nr * 3 * (kResLh / 4);
     for (int i = tid; i < n4; i += NT) {
@@ -319,7 +317,8 @@ __global__ void __launch_bounds__(NT, 1)
                                zi0 ? kResLh : cz, zp, zi1 ? kResLh : cz, lane, xoff, S, h, O);
                 const uint32_t row = uint32_t(y) + uint32_t(Ly) * uint32_t(z);
                 const uint32_t site0 = xoff + 4u * uint32_t(lane) + 2u * uint32_t(kResLh) * row;
-                const uint4 w = philox_smem(make_uint4(site0, sweep, tag_of(c, kPurposeMove), 0u), rk);
+                // the key is a kernel parameter, so its round keys are launch constants
+                const uint4 w = philox(make_uint4(site0, sweep, tag_of(c, kPurposeMove), 0u), a.key0, a.key1);
                 const bool mov[2] = {true, true};
                 nacc += pair_move(par, cval, w, S, h, mov, nullptr, Sf);
                 sts_p3(own, kResLh, lane, Sf);

@@ -523,6 +523,8 @@ int create_lattice(const mc_desc* din, mc_handle* out, const SlabSpec* slab) {
             p.rctl = ctl;
             rp->args.lat = h->d_lat;
             rp->args.ctl = static_cast<ResCtl*>(ctl);
+            rp->args.key0 = p.key0;
+            rp->args.key1 = p.key1;
             // fault injection for the tests of the bounded waits: the wait for
             // every block's count of a sweep expects one arrival too many
             const char* inj = std::getenv("MC_RESIDENT_INJECT_TIMEOUT");
