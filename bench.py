@@ -874,8 +874,8 @@ def precision(mc, torch, stream, dev):
 
 def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
     """The standard FP32 sweep on periodic cubes alone: one 128^3 lattice
-    (25 MB of spins, L2-resident) on row passes and held in shared memory
-    (resident sweeps), sixteen 128^3 lattices in one group (403 MB,
+    (25 MB of spins) held in shared memory (resident sweeps, the automatic
+    path) and on row passes, sixteen 128^3 lattices in one group (403 MB,
     HBM-resident) and one 256^3 lattice (201 MB).  K_u = 0.01 z, T = 0.5 ..
     1.25, all +z.  Per case: spin-updates/s over unmeasured and measured
     sweeps (CUDA events around the calls), and one launch timed alone
@@ -883,7 +883,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
     sweep, or a resident launch of 100 sweeps."""
     peak, _ = measured_peak()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cases = [("128c_single", [128], mc.MC_PATH_AUTO), ("128c_single_resident", [128], mc.MC_PATH_RESIDENT),
+    cases = [("128c_single", [128], mc.MC_PATH_AUTO), ("128c_single_row", [128], mc.MC_PATH_ROW),
              ("128c_x16", [128] * 16, mc.MC_PATH_AUTO),
              ("256c_single", [256], mc.MC_PATH_AUTO), ("128c_single_wavefront", [128], mc.MC_PATH_WAVE),
              ("128c_x16_wavefront", [128] * 16, mc.MC_PATH_WAVE)]
@@ -898,7 +898,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
         n = sum(L ** 3 for L in sizes)
         mc.mc_group_sweep(g, 20, measure=True)
         torch.cuda.synchronize()
-        shapes = RESIDENT_SHAPES if path == mc.MC_PATH_RESIDENT else ROW_SHAPES
+        shapes = RESIDENT_SHAPES if name == "128c_single" else ROW_SHAPES
         res = {"spins": n, "row_shape": shapes[tuned["row"]] if tuned else shapes[0]}
         for meas in (False, True):
             a.record(stream)

@@ -68,21 +68,25 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * passes where the row layout applies (Lh = Lx/2 a power of two <= 64 or a
  * multiple of 64, Nc a multiple of 64) and the general kernel otherwise,
  * and walks the constrained pairs in site order (each pair led by the
- * member whose shuffled position is even).  GENERAL always takes the
- * general colour-pass kernel and the pairs in pair order.  ROW is AUTO.
- * WAVE is AUTO, except that on an all-periodic lattice with Lx = 128 and
+ * member whose shuffled position is even); an all-periodic lattice with
+ * Lx = 128 and no film tables whose rows fit the SMs' shared memory sweeps
+ * resident when it runs alone (see RESIDENT).  GENERAL always takes the
+ * general colour-pass kernel and the pairs in pair order.  ROW is AUTO
+ * without the resident sweeps: the row kernels for every colour pass.
+ * WAVE is ROW, except that on an all-periodic lattice with Lx = 128 and
  * Ly >= 16 (no film tables) the sweeps of each mc_sweep / mc_group_sweep
  * call run two at a time as single wavefront launches (red and black pass
  * fused, each spin read and written once per sweep; the lattice then holds
  * a second spin buffer, and an odd last sweep of a call runs as two row
- * passes).  RESIDENT is AUTO, except that an all-periodic lattice with
- * Lx = 128 (no film tables) whose rows fit the SMs' shared memory (about
- * 30 MB of spins on 152 SMs, e.g. 128^3) sweeps, when it runs alone
- * (mc_sweep, or a group of that one lattice), held in shared memory: one
- * cooperative launch per run of up to 2048 unconstrained sweeps, one block
- * per brick of rows, the blocks waiting on their neighbours between colour
- * passes and on all blocks between sweeps (each wait bounded; a wait that
- * runs out gives MC_ERR_TIMEOUT).  The colour passes of AUTO, GENERAL,
+ * passes).  RESIDENT is AUTO, named: an all-periodic lattice with Lx = 128
+ * (no film tables) whose rows fit the SMs' shared memory (about 30 MB of
+ * spins on 152 SMs, e.g. 128^3) sweeps, when it runs alone (mc_sweep, or a
+ * group of that one lattice), held in shared memory: one cooperative launch
+ * per run of up to 2048 unconstrained sweeps, one block per brick of rows,
+ * the blocks waiting on their neighbours between colour passes and on all
+ * blocks between sweeps (each wait bounded; a wait that runs out gives
+ * MC_ERR_TIMEOUT).  Its constrained sweeps, and its sweeps in a group of
+ * several lattices, take the row kernels.  The colour passes of AUTO, GENERAL,
  * WAVE and RESIDENT agree up to FP32 rounding (the draws are keyed to the
  * same sites; the wavefront, resident and row kernels bit for bit) and the
  * two pair orders exactly; GENERAL, ROW, WAVE and RESIDENT exist to compare

@@ -204,10 +204,11 @@ bool wave_desc(const mc_desc* d) {
 
 // Lattices whose sweeps may run held in shared memory (resident_pass.cuh):
 // FP32 simple cubic, every axis periodic, no film tables, rows of 64 sites
-// per colour (Lx = 128), not a slab, the resident kernel path asked for;
+// per colour (Lx = 128), not a slab, the automatic or resident kernel path;
 // whether its rows fit is decided on the device (KernelSet::resident_plan).
 bool resident_desc(const mc_desc* d, bool slab) {
-    if (slab || d->precision != MC_FP32 || d->lattice != MC_SC || d->kernel_path != MC_PATH_RESIDENT) return false;
+    if (slab || d->precision != MC_FP32 || d->lattice != MC_SC) return false;
+    if (d->kernel_path != MC_PATH_AUTO && d->kernel_path != MC_PATH_RESIDENT) return false;
     if (d->bond_mask || d->grain_id) return false;
     for (int a = 0; a < 3; ++a)
         if (d->boundary[a] != MC_PERIODIC) return false;

@@ -97,14 +97,15 @@ def test_resident_run_longer_than_one_launch():
                  "two launches")
 
 
-def test_resident_lattice_in_a_group_of_one_takes_resident_launches():
-    """A group of the one lattice sweeps resident (the timed launches are of
-    the resident kind) and equals the lattice swept by row passes."""
+def test_automatic_path_sweeps_a_lone_lattice_resident():
+    """On the automatic path a group of the one 128-wide lattice sweeps
+    resident (the timed launches are of the resident kind) and equals the
+    lattice swept by row passes."""
     dims = (128, 64, 32)
     N = dims[0] * dims[1] * dims[2]
     spins = workloads.random_spins(N, 8)
     kw = dict(K_u=0.01, T=1.1, seed=4, sample_torque=0)
-    h = mc.mc_create_ex(mc.make_desc(dims, kernel_path=mc.MC_PATH_RESIDENT, ring_capacity=8, **kw))
+    h = mc.mc_create_ex(mc.make_desc(dims, kernel_path=mc.MC_PATH_AUTO, ring_capacity=8, **kw))
     g = mc.mc_group_create([h])
     try:
         mc.mc_set_spins(h, spins)
@@ -170,7 +171,7 @@ try:
 except mc.MCError as e:
     print("CODE", e.code)
 mc.mc_destroy(h)
-h = mc.mc_create_ex(mc.make_desc((128, 16, 16), T=1.0, seed=1))
+h = mc.mc_create_ex(mc.make_desc((128, 16, 16), T=1.0, seed=1, kernel_path=mc.MC_PATH_ROW))
 mc.mc_sweep(h, 3)
 mc.mc_sync(h)
 print("CONTEXT_OK")
@@ -183,7 +184,8 @@ def test_a_missing_arrival_ends_in_a_timeout_error():
     for every block's count of a sweep expects one arrival more than there
     are blocks.  Every block's bounded wait gives up after about a second (or
     on the abort flag the first one raises), the launch ends, the lattice
-    reports MC_ERR_TIMEOUT, and the context still runs other work."""
+    reports MC_ERR_TIMEOUT, and the context still runs other work (row
+    passes: every resident lattice of the process has the fault)."""
     env = dict(os.environ, MC_RESIDENT_INJECT_TIMEOUT="1")
     r = subprocess.run([sys.executable, "-c", _TIMEOUT_CHILD.format(root=ROOT)], env=env, capture_output=True,
                        text=True, timeout=120)
