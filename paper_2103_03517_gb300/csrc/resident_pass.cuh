@@ -31,8 +31,8 @@
 // block adds its sample sums (measured sweeps) into slot s mod 3 of the
 // control words and then, in one atomic with release semantics, its accepted
 // count and its arrival into the slot's count word.  At the start of the next
-// red pass, after issuing its halo copies, a block waits until every block
-// has arrived and applies the cone rule to the total itself.  Warp 0 of block
+// red pass the block's last warp waits until every block has arrived (while
+// warp 0 issues the halo copies) and applies the cone rule to the total.  Warp 0 of block
 // 0 then closes sweep s in the lattice state (cone angle, sample, moments,
 // ring, sweep counter) from the same totals, as the closing warp of a row
 // pass does, and clears slot s + 2 mod 3 (read by every block before it
@@ -259,15 +259,17 @@ __global__ void __launch_bounds__(NT, 1)
                     }
                     if (ok) issued = t + 1;
                 }
-                if (c == 0 && sw > 0 && lane == 0 && ok) {  // every block's count of the last sweep
-                    unsigned long long w = 0;
-                    ok = res_wait_arrivals(&ctl->arrive_acc[(sw - 1) % kResSlots], G, &ctl->abort, &w);
-                    if (ok)
-                        s_theta = (MEASURE == 0 || p.adapt_in_measure)
-                                      ? cone_rule(theta, (long long)(w & 0xFFFFFFFFull), p.n_mov)
-                                      : theta;
-                }
                 if (lane == 0 && !ok) s_fail = 1;
+            }
+            // the last warp, at the same time: every block's count of the last sweep
+            if (c == 0 && sw > 0 && warp == NW - 1 && lane == 0) {
+                unsigned long long w = 0;
+                if (res_wait_arrivals(&ctl->arrive_acc[(sw - 1) % kResSlots], G, &ctl->abort, &w))
+                    s_theta = (MEASURE == 0 || p.adapt_in_measure)
+                                  ? cone_rule(theta, (long long)(w & 0xFFFFFFFFull), p.n_mov)
+                                  : theta;
+                else
+                    s_fail = 1;
             }
             if (c == 0 && sw > 0) {
                 __syncthreads();  // the cone angle of this sweep
