@@ -816,7 +816,8 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto timed = [&](auto&& launch) { timed_kind(constrained ? kTimedPair : kTimedPass, launch); };
-    if (!constrained && ls.res && k.resident_sweeps && n > 0) {  // all n sweeps held in shared memory
+    // all n sweeps held in shared memory (see kResMinSweeps)
+    if (!constrained && ls.res && k.resident_sweeps && n >= kResMinSweeps) {
         cudaError_t e = cudaSuccess;
         for (int done = 0; done < n && e == cudaSuccess; done += kResMaxSweeps) {
             const int m = std::min(n - done, kResMaxSweeps);
@@ -944,7 +945,8 @@ int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* 
                bool constrained, cudaStream_t s) {
     const KernelSet& k = kernel_set(precision);
     // resident sweeps run many to a launch: nothing to capture
-    if (!constrained && ls.res) return enqueue_sweeps(k, ls, cone, n, measure, constrained, s, nullptr);
+    if (!constrained && ls.res && n >= kResMinSweeps)
+        return enqueue_sweeps(k, ls, cone, n, measure, constrained, s, nullptr);
     const int reps = n / kGraphSweeps;
     if (reps > 0) {
         cudaGraphExec_t& ex = gr.exec[constrained ? 1 : 0][measure ? 1 : 0];

@@ -22,6 +22,10 @@ struct NvtxRange {
 // Captured CUDA graphs of kGraphSweeps sweeps of one launch set, by
 // [constrained][measure]; built on first use and replayed.
 constexpr int kGraphSweeps = 16;
+// A resident lattice (LatParams::rctl) sweeps held in shared memory in calls
+// of at least this many sweeps; shorter calls, which would not pay for the
+// lattice's load and store, take the row passes (the same chain).
+constexpr int kResMinSweeps = 3;
 struct SweepGraphs {
     cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };

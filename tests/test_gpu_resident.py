@@ -121,6 +121,64 @@ def test_automatic_path_sweeps_a_lone_lattice_resident():
     _assert_same(a, _run(dims, kw, spins, [(5, True), (3, False)], mc.MC_PATH_ROW), "group")
 
 
+def test_short_calls_mix_with_resident_launches():
+    """Calls of one and two sweeps take the row passes (too short to pay for
+    the lattice's load and store), longer ones resident launches; the chain
+    is the row passes' chain throughout."""
+    dims = (128, 32, 16)
+    spins = workloads.random_spins(128 * 32 * 16, 14)
+    kw = dict(K_u=0.03, K_c=0.01, T=0.8, seed=13)
+    plan = [(1, False), (2, True), (5, False), (1, True), (4, True), (3, False)]
+    _assert_same(_run(dims, kw, spins, plan, mc.MC_PATH_AUTO), _run(dims, kw, spins, plan, mc.MC_PATH_ROW),
+                 "short calls")
+
+
+def test_temperature_and_field_changes_between_resident_runs():
+    """mc_set_temperature and mc_set_field between calls reach the next
+    resident launch (the parameters are read from the lattice, not cached)."""
+    dims = (128, 16, 32)
+    N = dims[0] * dims[1] * dims[2]
+    spins = workloads.random_spins(N, 15)
+    out = []
+    for path in (mc.MC_PATH_AUTO, mc.MC_PATH_ROW):
+        h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.02, T=1.2, seed=17, ring_capacity=8, kernel_path=path))
+        try:
+            mc.mc_set_spins(h, spins)
+            mc.mc_sweep(h, 4)
+            mc.mc_set_temperature(h, 0.6)
+            mc.mc_set_field(h, (0.0, 0.05, 0.1))
+            mc.mc_sweep(h, 5, measure=True)
+            out.append((mc.mc_get_spins(h, N), mc.mc_get_theta(h), mc.mc_measure(h).asdict(), mc.mc_samples(h, 5)))
+        finally:
+            mc.mc_destroy(h)
+    _assert_same(out[0], out[1], "T and H changes")
+
+
+def test_resident_run_resumes_from_a_checkpoint(tmp_path):
+    """A lattice saved between resident runs and loaded again continues the
+    same chain as the one that kept running."""
+    dims = (128, 32, 32)
+    N = dims[0] * dims[1] * dims[2]
+    spins = workloads.random_spins(N, 16)
+    path = str(tmp_path / "res.ckpt")
+    h = mc.mc_create_ex(mc.make_desc(dims, K_u=0.01, T=1.0, seed=18, ring_capacity=8))
+    try:
+        mc.mc_set_spins(h, spins)
+        mc.mc_sweep(h, 6)
+        mc.mc_save(h, path)
+        mc.mc_sweep(h, 5, measure=True)
+        a = (mc.mc_get_spins(h, N), mc.mc_get_theta(h), mc.mc_measure(h).asdict(), mc.mc_samples(h, 5))
+    finally:
+        mc.mc_destroy(h)
+    c = mc.mc_load(path)
+    try:
+        mc.mc_sweep(c, 5, measure=True)
+        b = (mc.mc_get_spins(c, N), mc.mc_get_theta(c), mc.mc_measure(c).asdict(), mc.mc_samples(c, 5))
+    finally:
+        mc.mc_destroy(c)
+    _assert_same(a, b, "resume")
+
+
 def test_both_resident_shapes_give_the_same_chain():
     """Blocks of 512 and of 640 threads (the tuner's two candidates) hand
     the rows out differently and give the same chain."""
