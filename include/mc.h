@@ -46,8 +46,12 @@ typedef enum mc_status {
     MC_ERR_ARG = -1,        /* invalid argument (checked on the host)            */
     MC_ERR_NOMEM = -2,      /* device memory exhausted / job can never fit       */
     MC_ERR_CUDA = -3,       /* a CUDA call failed (message in mc_last_error)     */
-    MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up (no kernel waits    */
-                            /* in this version; kept for the ABI)                */
+    MC_ERR_TIMEOUT = -4,    /* a bounded device wait gave up (the wavefront and  */
+                            /* resident kernels' waits, about one second each;   */
+                            /* MC_WAVE_INJECT_TIMEOUT=1 or                       */
+                            /* MC_RESIDENT_INJECT_TIMEOUT=1 in the environment   */
+                            /* when a lattice is created makes its first wait    */
+                            /* run out: a test hook)                             */
     MC_ERR_CONSTRAINT = -5, /* constrained run with M_L <= 0 (Table A2)          */
     MC_ERR_STATE = -6,      /* call not valid in the current state               */
     MC_ERR_IO = -7,         /* checkpoint file could not be read or written      */
