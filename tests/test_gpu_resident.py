@@ -179,6 +179,36 @@ def test_resident_run_resumes_from_a_checkpoint(tmp_path):
     _assert_same(a, b, "resume")
 
 
+def test_two_resident_lattices_on_two_streams():
+    """Two resident lattices swept at the same time on two streams: each
+    launch wants every SM and neither waits on the other, so the second
+    starts as the first drains; both give their row-pass chains."""
+    import torch
+    dims = [(128, 128, 64), (128, 64, 96)]
+    spins = [workloads.random_spins(d[0] * d[1] * d[2], 20 + i) for i, d in enumerate(dims)]
+    kws = [dict(K_u=0.02, T=0.7, seed=21), dict(K_u=0.01, K_c=0.01, T=1.1, seed=22)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hs = [mc.mc_create_ex(mc.make_desc(d, ring_capacity=8, stream=int(st.cuda_stream), **kw))
+          for d, kw, st in zip(dims, kws, streams)]
+    try:
+        for h, sp in zip(hs, spins):
+            mc.mc_set_spins(h, sp)
+        for _ in range(3):
+            for h in hs:
+                mc.mc_sweep(h, 40)
+        for h in hs:
+            mc.mc_sweep(h, 6, measure=True)
+        got = []
+        for h, d in zip(hs, dims):
+            N = d[0] * d[1] * d[2]
+            got.append((mc.mc_get_spins(h, N), mc.mc_get_theta(h), mc.mc_measure(h).asdict(), mc.mc_samples(h, 6)))
+    finally:
+        for h in hs:
+            mc.mc_destroy(h)
+    for d, kw, sp, g in zip(dims, kws, spins, got):
+        _assert_same(g, _run(d, kw, sp, [(40, False)] * 3 + [(6, True)], mc.MC_PATH_ROW), d)
+
+
 def test_both_resident_shapes_give_the_same_chain():
     """Blocks of 512 and of 640 threads (the tuner's two candidates) hand
     the rows out differently and give the same chain."""
