@@ -875,8 +875,9 @@ def precision(mc, torch, stream, dev):
 def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
     """The standard FP32 sweep on periodic cubes alone: one 128^3 lattice
     (25 MB of spins) held in shared memory (resident sweeps, the automatic
-    path) and on row passes, sixteen 128^3 lattices in one group (403 MB,
-    HBM-resident) and one 256^3 lattice (201 MB).  K_u = 0.01 z, T = 0.5 ..
+    path) and on row passes, sixteen 128^3 lattices in one group (403 MB;
+    the automatic path sweeps them resident one after another, and on
+    batched row passes) and one 256^3 lattice (201 MB).  K_u = 0.01 z, T = 0.5 ..
     1.25, all +z.  Per case: spin-updates/s over unmeasured and measured
     sweeps (CUDA events around the calls), and one launch timed alone
     against the HBM roofline (24 B per update): a colour pass, a wavefront
@@ -884,7 +885,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
     peak, _ = measured_peak()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cases = [("128c_single", [128], mc.MC_PATH_AUTO), ("128c_single_row", [128], mc.MC_PATH_ROW),
-             ("128c_x16", [128] * 16, mc.MC_PATH_AUTO),
+             ("128c_x16", [128] * 16, mc.MC_PATH_AUTO), ("128c_x16_row", [128] * 16, mc.MC_PATH_ROW),
              ("256c_single", [256], mc.MC_PATH_AUTO), ("128c_single_wavefront", [128], mc.MC_PATH_WAVE),
              ("128c_x16_wavefront", [128] * 16, mc.MC_PATH_WAVE)]
     out = {}
@@ -898,8 +899,7 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
         n = sum(L ** 3 for L in sizes)
         mc.mc_group_sweep(g, 20, measure=True)
         torch.cuda.synchronize()
-        shapes = RESIDENT_SHAPES if name == "128c_single" else ROW_SHAPES
-        res = {"spins": n, "row_shape": shapes[tuned["row"]] if tuned else shapes[0]}
+        res = {"spins": n}
         for meas in (False, True):
             a.record(stream)
             mc.mc_group_sweep(g, sweeps, measure=meas)
@@ -913,11 +913,15 @@ def cubes(mc, torch, stream, dev, tune=True, sweeps=400):
             kms, kn = mc.mc_group_time_kernels(g, 100, measure=meas)
             wave, resident = kn[0] > 0, kn[3] > 0
             avg_ms = kms[3] if resident else (kms[0] if wave else kms[1])
-            per_launch = (n * 100 if resident else (n if wave else n // 2)) * BYTES_PER_UPDATE
+            # a resident launch runs one lattice's 100 sweeps (the group's
+            # lattices one after another)
+            per_launch = (n * 100 // kn[3] if resident else (n if wave else n // 2)) * BYTES_PER_UPDATE
             gbs = per_launch / (avg_ms * 1e-3) / 1e9
-            res["kernel"] = ("resident_sweep_kernel (100 sweeps per launch)" if resident else
+            res["kernel"] = ("resident_sweep_kernel (100 sweeps of one lattice per launch)" if resident else
                              "wave_sweep_kernel (one sweep per launch)" if wave else
                              "row_pass_kernel (one colour per launch)")
+            shapes = RESIDENT_SHAPES if resident else ROW_SHAPES
+            res["row_shape"] = shapes[tuned["row"]] if tuned else shapes[0]
             res["launch_ms_measured" if meas else "launch_ms"] = round(avg_ms, 5)
             res["frac_measured" if meas else "frac"] = round(gbs / peak, 4)
         out[name] = res

@@ -89,8 +89,10 @@ typedef enum mc_boundary { MC_PERIODIC = 0, MC_OPEN = 1, MC_PINNED = 2, MC_ANTIP
  * per run of up to 2048 unconstrained sweeps, one block per brick of rows,
  * the blocks waiting on their neighbours between colour passes and on all
  * blocks between sweeps (each wait bounded; a wait that runs out gives
- * MC_ERR_TIMEOUT).  Its constrained sweeps, calls of fewer than 3 sweeps
- * and its sweeps in a group of several lattices take the row kernels.  The colour passes of AUTO, GENERAL,
+ * MC_ERR_TIMEOUT).  A group made only of such lattices of at least 2^21
+ * spins each (128^3 and larger) sweeps them resident one after another.
+ * Constrained sweeps, calls of fewer than 3 sweeps and other groups take
+ * the row kernels.  The colour passes of AUTO, GENERAL,
  * WAVE and RESIDENT agree up to FP32 rounding (the draws are keyed to the
  * same sites; the wavefront, resident and row kernels bit for bit) and the
  * two pair orders exactly; GENERAL, ROW, WAVE and RESIDENT exist to compare

@@ -23,6 +23,7 @@ struct mc_group {
     const void* cone = nullptr;
     SweepGraphs graphs;  // captured sweeps of the whole group
     LatState* h_states = nullptr;  // pinned staging of mc_group_measure, one per member
+    std::vector<ResidentPlan*> res_plans;  // members' resident plans (LaunchSet::res)
 };
 
 static int group_run(mc_group* g, int n, int measure, bool constrained) {
@@ -126,7 +127,16 @@ MC_API int mc_group_create(const mc_handle* lattices, int n, mc_group_handle* ou
                               int(sub[c].size())};
         *counts[c] = st[c].back();
     }
-    if (n == 1) g->ls.res = lattices[0]->res;  // a resident lattice alone
+    // resident lattices: alone, or a group made only of large ones (swept one
+    // after another, each held in shared memory)
+    bool all_res = true;
+    for (int i = 0; i < n; ++i)
+        all_res = all_res && lattices[i]->res && (n == 1 || lattices[i]->hp.N >= kResGroupMinSpins);
+    if (all_res) {
+        for (int i = 0; i < n; ++i) g->res_plans.push_back(lattices[i]->res);
+        g->ls.res = g->res_plans.data();
+        g->ls.n_res = n;
+    }
     g->ls.sample_level = 1;
     for (int i = 0; i < n; ++i)
         if (lattices[i]->hp.sample_torque) g->ls.sample_level = 2;

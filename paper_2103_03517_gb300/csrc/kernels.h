@@ -131,10 +131,12 @@ struct LaunchSet {
     uint32_t nb_wave = 0;
     GroupArgs row_rest;
     uint32_t nt_row_rest = 0;
-    // a resident lattice alone (LatParams::rctl): its launch plan, owned by
-    // the lattice (null: none); its unconstrained sweeps run as resident
-    // launches
-    const ResidentPlan* res = nullptr;
+    // resident lattices (LatParams::rctl) whose unconstrained sweeps run as
+    // resident launches, one lattice after another: a lattice alone, or every
+    // lattice of a group made only of large resident lattices; n_res launch
+    // plans, owned by the lattices (none: n_res = 0)
+    ResidentPlan* const* res = nullptr;
+    int n_res = 0;
     int sample_level = 2;  // sample of a measured colour pass: 1 or 2 (torques)
     // a bcc / fcc lattice alone: its descriptor and sub-lattice count, else null
     LatDev* xtal = nullptr;

@@ -644,7 +644,10 @@ LaunchSet single_launch_set(mc_lattice* h) {
     } else if (h->hp.colour_kernel == kColourRow) {
         ls.row = ls.all;
         ls.nt_row = ls.nt_all;
-        ls.res = h->res;
+        if (h->res) {
+            ls.res = &h->res;
+            ls.n_res = 1;
+        }
         if (h->hp.wave) {
             ls.wave = h->wave_args;
             ls.nb_wave = h->wave_nblocks;
@@ -816,14 +819,16 @@ int enqueue_sweeps(const KernelSet& k, const LaunchSet& ls, const void* cone, in
         }
     };
     auto timed = [&](auto&& launch) { timed_kind(constrained ? kTimedPair : kTimedPass, launch); };
-    // all n sweeps held in shared memory (see kResMinSweeps)
-    if (!constrained && ls.res && k.resident_sweeps && n >= kResMinSweeps) {
+    // all n sweeps held in shared memory, lattice after lattice (see kResMinSweeps)
+    if (!constrained && ls.n_res && k.resident_sweeps && n >= kResMinSweeps) {
         cudaError_t e = cudaSuccess;
-        for (int done = 0; done < n && e == cudaSuccess; done += kResMaxSweeps) {
-            const int m = std::min(n - done, kResMaxSweeps);
-            timed_kind(kTimedResident, [&] { e = k.resident_sweeps(*ls.res, cone, m, measure ? ls.sample_level : 0,
-                                                                  ls.shape.row, s); });
-        }
+        for (int i = 0; i < ls.n_res && e == cudaSuccess; ++i)
+            for (int done = 0; done < n && e == cudaSuccess; done += kResMaxSweeps) {
+                const int m = std::min(n - done, kResMaxSweeps);
+                timed_kind(kTimedResident, [&] {
+                    e = k.resident_sweeps(*ls.res[i], cone, m, measure ? ls.sample_level : 0, ls.shape.row, s);
+                });
+            }
         if (e != cudaSuccess) return cuda_fail(e, "resident sweep launch");
         return MC_OK;
     }
@@ -945,7 +950,7 @@ int run_sweeps(SweepGraphs& gr, int precision, const LaunchSet& ls, const void* 
                bool constrained, cudaStream_t s) {
     const KernelSet& k = kernel_set(precision);
     // resident sweeps run many to a launch: nothing to capture
-    if (!constrained && ls.res && n >= kResMinSweeps)
+    if (!constrained && ls.n_res && n >= kResMinSweeps)
         return enqueue_sweeps(k, ls, cone, n, measure, constrained, s, nullptr);
     const int reps = n / kGraphSweeps;
     if (reps > 0) {

@@ -26,6 +26,11 @@ constexpr int kGraphSweeps = 16;
 // of at least this many sweeps; shorter calls, which would not pay for the
 // lattice's load and store, take the row passes (the same chain).
 constexpr int kResMinSweeps = 3;
+// A group sweeps its lattices resident one after another only when every
+// member is resident and holds at least this many spins (a 128^3 lattice:
+// held in shared memory it sweeps faster than its share of a batched row
+// pass; smaller lattices sweep faster batched).
+constexpr long long kResGroupMinSpins = 1ll << 21;
 struct SweepGraphs {
     cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };

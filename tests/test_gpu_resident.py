@@ -209,6 +209,44 @@ def test_two_resident_lattices_on_two_streams():
         _assert_same(g, _run(d, kw, sp, [(40, False)] * 3 + [(6, True)], mc.MC_PATH_ROW), d)
 
 
+def test_group_of_large_resident_lattices_sweeps_them_one_after_another():
+    """A group made only of resident lattices of at least 2^21 spins (two
+    128^3) sweeps each held in shared memory in turn: one resident launch
+    per lattice per call, each lattice on its row-pass chain.  A group with
+    a smaller member keeps the batched row passes."""
+    dims = (128, 128, 128)
+    N = dims[0] * dims[1] * dims[2]
+    spins = [workloads.random_spins(N, 30 + i) for i in range(2)]
+    kws = [dict(K_u=0.01, T=0.9, seed=31), dict(K_u=0.02, K_c=0.01, T=1.2, seed=32)]
+    hs = [mc.mc_create_ex(mc.make_desc(dims, ring_capacity=8, **kw)) for kw in kws]
+    g = mc.mc_group_create(hs)
+    try:
+        for h, sp in zip(hs, spins):
+            mc.mc_set_spins(h, sp)
+        _, n = mc.mc_group_time_kernels(g, 4)
+        assert n[3] == 2 and n[1] == 0, n
+        mc.mc_group_sweep(g, 5, measure=True)
+        mc.mc_group_sync(g)
+        got = [(mc.mc_get_spins(h, N), mc.mc_get_theta(h), mc.mc_measure(h).asdict(), mc.mc_samples(h, 5))
+               for h in hs]
+    finally:
+        mc.mc_group_destroy(g)
+        for h in hs:
+            mc.mc_destroy(h)
+    for kw, sp, gt in zip(kws, spins, got):
+        _assert_same(gt, _run(dims, kw, sp, [(4, False), (5, True)], mc.MC_PATH_ROW), "group")
+    small = mc.mc_create_ex(mc.make_desc((128, 32, 32), T=1.0, seed=33))
+    big = mc.mc_create_ex(mc.make_desc(dims, T=1.0, seed=34))
+    g = mc.mc_group_create([small, big])
+    try:
+        _, n = mc.mc_group_time_kernels(g, 4)
+        assert n[3] == 0 and n[1] == 8, n
+    finally:
+        mc.mc_group_destroy(g)
+        mc.mc_destroy(small)
+        mc.mc_destroy(big)
+
+
 def test_both_resident_shapes_give_the_same_chain():
     """Blocks of 512 and of 640 threads (the tuner's two candidates) hand
     the rows out differently and give the same chain."""
