@@ -133,8 +133,9 @@ def test_crystal_constrained_fp64_bit_exact(lattice, cells, J2):
 
 def test_crystal_constrained_fp32_torque_matches_fp64():
     """fcc 6^3 cells at T = 0.6, theta_c = 45 deg: the FP32 torque tau_y
-    (site order, FP32 moves) agrees with the FP64 chain's within 4 sigma of
-    the spread between 6 runs per precision; both near the T -> 0 law
+    (site order, FP32 moves) agrees with the FP64 chain's within the
+    3-sigma-equivalent Student-t bound of the spread between 6 runs per
+    precision (10 degrees of freedom, 3.96 standard errors); both near the T -> 0 law
     -(K_u sin 2 theta) softened by temperature."""
     th, Ku = 45.0, 0.05
     R = oracle.constraint_frame(th, 0.0)
