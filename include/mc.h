@@ -381,7 +381,8 @@ MC_API int mc_group_sync(mc_group_handle g);
  * constrained sweep yet gets its packed copy here), both or-ed together.
  * Each candidate runs 1 + sweeps sweeps, the last `sweeps` timed with CUDA
  * events; knobs are tuned one after the other, each at the best choice of the
- * ones before.  The lattices' spins and device state (theta, sweep counter,
+ * ones before.  Another candidate replaces a knob's first (its default) only if
+ * it is more than 1% faster.  The lattices' spins and device state (theta, sweep counter,
  * accumulators) are saved first and restored after, so the chains continue as
  * if no tuning had run; the chosen shapes apply to later sweeps (captured
  * graphs are rebuilt).  Synchronises.  out (may be null) receives the choices

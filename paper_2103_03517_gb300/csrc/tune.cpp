@@ -16,6 +16,8 @@ namespace mcgb {
 
 namespace {
 
+constexpr double kTuneMargin = 0.01;  // relative gain a candidate needs over the default
+
 // Device copy of the spins and LatState of every lattice, for restoring.
 struct Snapshot {
     void* mem = nullptr;
@@ -112,7 +114,10 @@ int autotune(int precision, LaunchSet& ls, const std::vector<mc_lattice*>& lats,
             const int rr = copy_state(lats, snap, false, s);
             return r ? r : rr;
         };
-        // one knob: time every candidate, keep the fastest
+        // one knob: time every candidate, keep the fastest; another candidate
+        // replaces the default (candidate 0) only if it is faster by more than
+        // kTuneMargin, so that timing noise between near-equal shapes does not
+        // decide
         auto knob = [&](int& choice, int n, double* ms, bool constrained) -> int {
             double best = 0.0;
             int pick = choice;
@@ -120,7 +125,7 @@ int autotune(int precision, LaunchSet& ls, const std::vector<mc_lattice*>& lats,
                 choice = c;
                 const int r = trial(constrained, ms[c]);
                 if (r) return r;
-                if (c == 0 || ms[c] < best) {
+                if (c == 0 || ms[c] < best * (pick == 0 ? 1.0 - kTuneMargin : 1.0)) {
                     best = ms[c];
                     pick = c;
                 }
